@@ -1,0 +1,157 @@
+"""One implicit time step of graph-based FEM fracture (oracle).
+
+Order of Algorithm 1 (Sec. 4.3), minus the visualisation remesh and the
+collision response, which are not part of the computational step:
+  1. stresses along the edges at the start-of-step positions, non-local
+     average, fracture check and relabel (Eq. 14-21), then chi (Eq. 22-25);
+  2. build the system with f* = chi f and K* = sum chi k (Eq. 32-34), mass
+     (Eq. 5, lumped) and damping b* = alpha m + beta k* (Sec. 3.6);
+  3. solve for the velocity (implicit backward Euler + CG, Sec. 4.3);
+  4. x += dt v.
+
+The backward-Euler update is linearised once about the start of the step
+(one Newton iteration), with unknown dv = v_{n+1} - v_n:
+  [(1 + dt alpha) M + (dt beta + dt^2) K*] dv
+      = dt [ f_ext + f*(x_n) - alpha M v_n - (beta + dt) K* v_n ]
+which is Eq. 2 with f_int(x_{n+1}) ~ f_int(x_n) + K* dt v_{n+1}.
+Pinned nodes have all three velocity components prescribed (zero by default).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import damage, elastic, mesh, solve
+
+
+@dataclasses.dataclass
+class Material:
+    young: float
+    poisson: float
+    density: float
+    threshold: float = np.inf
+    radius: float = 0.0
+    alpha: float = 0.0
+    beta: float = 0.0
+    driver_mode: str = "strain"       # "strain" (sigma*/E) or "stress"
+    shear_coef: float = 2.0           # 2: tensor n.S.n; 1: Eq. 16 as printed
+    average_degraded: bool = True     # Eq. 20 averages chi_j S_j (True) or S_j
+
+
+@dataclasses.dataclass
+class State:
+    x: np.ndarray          # (n, 3)
+    v: np.ndarray          # (n, 3)
+    labels: np.ndarray     # (ne,) uint8, 1 = broken
+    chi: np.ndarray        # (t,) energy degradation in force during the last step
+
+
+class Model:
+    """Rest-state precompute of one mesh (Sec. 3.1-3.3)."""
+
+    def __init__(self, nodes, tets, mat: Material, nonlocal_lists=True):
+        self.X = np.asarray(nodes, np.float64)
+        self.tets = np.asarray(tets, np.int64)
+        self.mat = mat
+        self.lam, self.mu = elastic.lame(mat.young, mat.poisson)
+        self.edges, self.tet_edges = mesh.edges_of(self.tets)
+        self.V, self.D2, self.q = mesh.rest_geometry(self.X, self.tets)
+        self.mass = mesh.lumped_mass(self.X, self.tets, mat.density, self.V)
+        self.centroids = mesh.centroids(self.X, self.tets)
+        self.nbrs = self.weights = None
+        if nonlocal_lists:
+            self.nbrs = mesh.nonlocal_neighbours(self.X, self.tets, mat.radius)
+            self.weights = damage.nonlocal_weights(self.centroids, self.V, self.nbrs, mat.radius)
+
+    @property
+    def n_nodes(self):
+        return self.X.shape[0]
+
+    def rest_state(self) -> State:
+        return State(self.X.copy(), np.zeros_like(self.X), np.zeros(len(self.edges), np.uint8),
+                     np.ones(len(self.tets)))
+
+    # ---- damage (Eq. 14-25) ------------------------------------------------
+    def stresses(self, x):
+        """Per-tet S (Voigt, Eq. 14) and local edge-normal stress sigma_f = T S (Eq. 18)."""
+        s = elastic.squared_edge_lengths(x, self.tets)
+        C = elastic.cauchy_green_lsq(s, self.D2, self.q)
+        S = damage.stress_voigt(C, self.lam, self.mu)
+        T = damage.projection_T(x, self.tets, self.mat.shear_coef)
+        return S, T, np.einsum("tkc,tc->tk", T, S)
+
+    def damage_update(self, state: State):
+        """Returns (driver per edge, new labels, new chi, sigma* per (tet, edge))."""
+        S, T, sigf = self.stresses(state.x)
+        sig_in = S * state.chi[:, None] if self.mat.average_degraded else S
+        sig_bar = damage.nonlocal_average(sig_in, self.nbrs, self.weights)     # Eq. 20 sum
+        sig_star = np.einsum("tkc,tc->tk", T, sig_bar)                          # Eq. 20 T(...)
+        drv = damage.edge_driver(sig_star, self.tet_edges, len(self.edges), self.mat.young,
+                                 self.mat.driver_mode)
+        labels = damage.relabel(state.labels, drv, self.mat.threshold)          # Eq. 21
+        chi = damage.chi(labels, self.tet_edges, sigf, self.mat.young)          # Eq. 25
+        return drv, labels, chi, sig_star
+
+    def chi_from_labels(self, x, labels):
+        """chi of Eq. 25 for given labels at positions x."""
+        _, _, sigf = self.stresses(x)
+        return damage.chi(labels, self.tet_edges, sigf, self.mat.young)
+
+    # ---- system (Eq. 2, 32-34) ---------------------------------------------
+    def assemble(self, x, chi):
+        """Global K* = sum chi k_e (Eq. 34, CSR) and f* = sum chi f_e (Eq. 32)."""
+        Ke = elastic.element_tangent(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi)
+        fe = elastic.element_forces(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi)
+        dof = (3 * self.tets[:, :, None] + np.arange(3)).reshape(-1, 12)
+        rows = np.repeat(dof, 12, axis=1).ravel()
+        cols = np.tile(dof, (1, 12)).ravel()
+        n3 = 3 * self.n_nodes
+        K = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n3, n3)).tocsr()
+        f = np.zeros(n3)
+        np.add.at(f, dof.ravel(), fe.reshape(-1))
+        return K, f
+
+    def linear_system(self, x, v, chi, dt, f_ext):
+        """A dv = b of the linearised backward-Euler step (module docstring)."""
+        mt = self.mat
+        K, f = self.assemble(x, chi)
+        M = sp.diags(np.repeat(self.mass, 3))
+        A = ((1.0 + dt * mt.alpha) * M + (dt * mt.beta + dt * dt) * K).tocsr()
+        vv = v.ravel()
+        b = dt * (np.asarray(f_ext, np.float64).ravel() + f - mt.alpha * (M @ vv)
+                  - (mt.beta + dt) * (K @ vv))
+        return A, b, K, f
+
+    def step(self, state: State, dt: float, f_ext, pinned=None, pinned_vel=None,
+             solver: str = "direct", rtol: float = 1e-13, maxit: int = 100000):
+        """One step; returns (new State, info dict)."""
+        drv, labels, chi, sig_star = self.damage_update(state)
+        A, b, K, f = self.linear_system(state.x, state.v, chi, dt, f_ext)
+        n = self.n_nodes
+        fixed = np.zeros(n, bool)
+        dv = np.zeros(3 * n)
+        if pinned is not None and len(pinned):
+            pinned = np.asarray(pinned, np.int64)
+            fixed[pinned] = True
+            target = np.zeros((len(pinned), 3)) if pinned_vel is None else np.asarray(pinned_vel).reshape(-1, 3)
+            dv.reshape(-1, 3)[pinned] = target - state.v[pinned]
+        free = np.repeat(~fixed, 3)
+        rhs = b[free] - A[free][:, ~free] @ dv[~free]
+        Aff = A[free][:, free].tocsr()
+        info = {"driver": drv, "labels": labels, "chi": chi, "sig_star": sig_star, "A": A, "b": b,
+                "K": K, "f": f}
+        if solver == "direct":
+            dv[free] = solve.direct(Aff, rhs) if rhs.size else rhs
+            info.update(iters=0, status="ok")
+        else:
+            sol, it, rel, status = solve.pcg(Aff, rhs, rtol=rtol, maxit=maxit)
+            dv[free] = sol
+            info.update(iters=it, rel_res=rel, status=status)
+        rn = np.linalg.norm(rhs)
+        info["rel_res"] = np.linalg.norm(rhs - Aff @ dv[free]) / rn if rn > 0 else 0.0
+        v_new = state.v + dv.reshape(-1, 3)
+        x_new = state.x + dt * v_new
+        info["dv"] = dv.reshape(-1, 3)
+        return State(x_new, v_new, labels, chi), info
