@@ -1,0 +1,270 @@
+#!/usr/bin/env python
+"""Benchmark: ms per implicit step of graph-FEM fracture on the 620k-tet loaf.
+
+Default (``--impl ours``): the CUDA library through its C ABI on one GPU per
+rank.  The workload is the loaf stand-in (619,300 tets, 111,283 nodes, BCC
+lattice in an ellipsoid, end caps pulled apart), FP64, CG to 1e-6 relative
+residual, one full step of Algorithm 1 per timed step (damage, assembly, PCG,
+update).  Prints one JSON line on rank 0.
+
+``--impl reference``: the CPU FP64 oracle (numpy/scipy, the checker the CUDA
+path is tested against) stepping a bounded sample of the same workload (the
+same generator with the ellipsoid axes scaled down), scaled per tet to the
+full mesh.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per implicit step at 620k tets to 1e-6 rel. residual, plain vs learned/mixed"
+UNIT = "ms/step"
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+SAMPLE_SCALE = 0.4          # oracle sample: loaf axes x 0.4 (~40k tets)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, traffic=None):
+    """Roofline entry of one kernel group: algorithmic work per launch / mean launch time."""
+    T, NB, N, pairs = info["n_tets"], info["n_blocks"], info["n_nodes"], info["n_nbr_pairs"]
+    t = ms / max(launches, 1) * 1e-3
+    if group == "nonlocal_avg":
+        # 6 FMA per (tet, neighbour) pair: the Eq. 20 weighted sum of six stress components
+        flops = 12.0 * pairs
+        return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
+                "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
+    if group == "assemble":
+        # per launch = all colours of one assembly; FP64 operations counted in the kernel source per tet
+        flops = 2.0 * 1000.0 * T
+        return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
+                "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
+    if group == "pcg_spmv":
+        flops = 18.0 * NB
+        return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
+                "work_per_launch": {"fp64_flop": flops, "bytes": 76.0 * NB + 4.0 * (N + 1) + 48.0 * N},
+                "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
+    # streaming kernels: bytes
+    bytes_per = {"tet_stress": T * (16 + 37 * 8 + 8 + 96) + 24 * N,
+                 "edge_driver": info["n_edges"] * (8 + 8 + 8 + 1) + 6 * T * (4 + 48) + 24 * N,
+                 "tet_chi": T * (24 + 6 + 48 + 8)}.get(group, 0.0)
+    gbs = bytes_per / t / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "traffic": traffic, "kernel": group, "work_per_launch": {"bytes": bytes_per}}
+
+
+def cpu_sample_child(steps: int) -> None:
+    """Run in a subprocess with one BLAS/OpenMP thread: oracle steps on the sample."""
+    import numpy as np
+    from oracle.step import Material, Model
+    from workloads import LOAF_AXES, loaf_config
+    w = loaf_config(axes=tuple(a * SAMPLE_SCALE for a in LOAF_AXES))
+    m = Model(w.nodes, w.tets, Material(w.young, w.poisson, w.density, w.threshold, w.radius))
+    st = m.rest_state()
+    st, _ = m.step(st, w.dt, w.f_ext, None, solver="pcg", rtol=w.cg_rtol)   # warm-up
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st, info = m.step(st, w.dt, w.f_ext, None, solver="pcg", rtol=w.cg_rtol)
+    dt = (time.perf_counter() - t0) / steps
+    print(json.dumps({"sec_per_step": dt, "tets": w.n_tets, "steps": steps, "cg_iters": info["iters"]}))
+
+
+def cpu_sample(steps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-child", str(steps)],
+                         capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(steps: int, full_tets: int) -> dict:
+    s = cpu_sample(steps)
+    ms = s["sec_per_step"] * 1e3 * full_tets / s["tets"]
+    return {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{s['steps']} oracle steps on the loaf generator with axes x{SAMPLE_SCALE} ({s['tets']} tets), "
+                      f"same material/dt/R_d/loads, PCG rtol 1e-6 ({s['cg_iters']} iterations), "
+                      f"{s['sec_per_step']:.2f} s/step scaled per tet to {full_tets} tets; numpy/scipy, 1 thread"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from workloads import loaf_config
+    w_tets = 619300
+    s = cpu_sample(args.steps + args.warmup)
+    ms = s["sec_per_step"] * 1e3 * w_tets / s["tets"]
+    cb = {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"{s['steps']} oracle steps on a {s['tets']}-tet sample (loaf axes x{SAMPLE_SCALE}), scaled per tet"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "loaf_bcc_620k_fp64", "n_tets": w_tets, "cg_rtol": 1e-6},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+    import paper_2103_14870_gb300 as gf
+    from workloads import loaf_config
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = loaf_config()
+    mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius)
+    m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
+    info = m.info
+    f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        m.step(w.dt, f_dev)
+    m.profile_reset()
+    m.profile_enable(True)
+    stream = torch.cuda.current_stream()
+    iters = []
+    clk = ClockSampler(local)
+    l0 = m.launch_count()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s = m.step(w.dt, f_dev)
+        iters.append(s["cg_iters"])
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    launches = m.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    m.profile_enable(False)
+    prof = m.profile_get()
+    # end to end through the public API with host buffers: pinned f_ext in, positions out, every step
+    f_host = torch.tensor(w.f_ext.ravel(), dtype=torch.float64).pin_memory()
+    x_host = torch.empty(3 * w.n_nodes, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m.step(w.dt, f_host)
+        m.positions_get(out=x_host)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    t_all = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = float(t_all[0]), float(t_all[1])
+    if rank != 0:
+        return
+    dom = max(prof, key=lambda k: prof[k][0])
+    pk = peaks()
+    traffic = None
+    roof = roofline_for(dom, prof[dom][0], prof[dom][1], info, pk, traffic)
+    cpu = None if args.no_cpu_baseline else cpu_baseline_entry(3, w.n_tets)
+    out = {
+        "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "loaf_bcc_620k_fp64", "n_tets": info["n_tets"], "n_nodes": info["n_nodes"],
+                   "n_edges": info["n_edges"], "n_nbr_pairs": info["n_nbr_pairs"], "precision": "fp64",
+                   "cg_rtol": w.cg_rtol, "radius": w.radius, "dt": w.dt,
+                   "l2": f"inputs larger than L2: {info['device_bytes'] / 1e9:.2f} GB of mesh data resident",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "element_updates_per_s": info["n_tets"] / (ms * 1e-3),
+        "cg_iters_per_step": statistics.mean(iters),
+        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * w.n_nodes,
+                "d2h_bytes_per_step": 8 * 3 * w.n_nodes + 48},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "kernel_launches": {k: v[1] for k, v in prof.items()},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_sample_child:
+        cpu_sample_child(args.cpu_sample_child)
+        return
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

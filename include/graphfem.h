@@ -1,0 +1,200 @@
+/*
+ * graphfem.h -- C ABI of the GB300 graph-based FEM fracture step.
+ *
+ * Method: Mandal, Chaudhuri & Chaudhuri, "Remeshing-Free Graph-Based Finite
+ * Element Method for Ductile and Brittle Fracture".  One call to gf_step()
+ * performs one implicit time step of Algorithm 1 (Sec. 4.3) on a fixed
+ * tetrahedral mesh graph:
+ *   1. stresses along the mesh edges at the start-of-step positions (Eq. 14-19),
+ *      non-local average (Eq. 20), irreversible edge relabel (Eq. 21) and the
+ *      energy degradation chi of every tet (Eq. 22-25);
+ *   2. element forces in squared edge lengths (Eq. 12, Thm 3.1 / Eq. 27-31,
+ *      StVK Eq. 37) and 12x12 tangents, scaled by chi (Eq. 32-34), scattered
+ *      into a block-CSR matrix whose sparsity never changes (Sec. 1, Sec. 5.4);
+ *   3. the linearised backward-Euler system of Eq. 2 with Rayleigh damping
+ *      (Sec. 3.1, Sec. 3.6) solved by preconditioned conjugate gradients
+ *      (Sec. 4.3), then v += dv, x += dt v.
+ *
+ * Conventions shared by every entry point
+ *   - Node arrays are node-major: x[3*i + c], c in {0,1,2}.
+ *   - Edges are the unique node pairs of the tets, numbered in ascending
+ *     lexicographic order of (min id, max id); gf_edges_get() returns them.
+ *   - Tets keep the caller's numbering at the ABI (the library reorders them
+ *     internally and maps back).
+ *   - `mem` arguments say where the caller's pointers live: GF_MEM_HOST (any
+ *     host memory; pinned memory makes the copies faster) or GF_MEM_DEVICE
+ *     (device memory of the mesh's device; the pointer must stay valid until
+ *     the call returns).
+ *   - The library owns every device buffer of a mesh.  The caller owns what it
+ *     passes in; arrays are copied during the call and not retained.
+ *   - Every call returns a gf_status; nothing is thrown across the ABI.  On
+ *     error, gf_last_error() gives a message for the calling thread.
+ *   - Calls on one mesh are not thread-safe; distinct meshes are independent.
+ *   - All device work runs on the mesh's stream; every call returns after
+ *     that work has completed.
+ */
+#ifndef GRAPHFEM_H
+#define GRAPHFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gf_status {
+  GF_OK = 0,
+  GF_BAD_ARG = 1,        /* invalid argument (null, out of range, degenerate tet, ...) */
+  GF_CUDA_ERR = 2,       /* a CUDA runtime call or kernel launch failed */
+  GF_CG_BREAKDOWN = 3,   /* p^T A p <= 0: the tangent is not positive definite (StVK under compression) */
+  GF_CG_MAXITER = 4,     /* CG did not reach the tolerance within cg_maxit iterations */
+  GF_NAN = 5,            /* a non-finite residual or state appeared */
+  GF_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  GF_OOM = 7,            /* device allocation failed */
+  GF_UNSUPPORTED = 8     /* option combination not built */
+} gf_status;
+
+enum { GF_MEM_HOST = 0, GF_MEM_DEVICE = 1 };
+enum { GF_DRIVER_STRAIN = 0, GF_DRIVER_STRESS = 1 };
+enum { GF_FP64 = 0, GF_MIXED = 1 };
+enum { GF_PRECOND_BJACOBI = 0 };
+
+/* Material and damage parameters (Sec. 3.1, 3.3, 5.2). */
+typedef struct gf_material {
+  double young;          /* Young's modulus E (Pa) */
+  double poisson;        /* Poisson ratio nu, in (-1, 0.5) */
+  double density;        /* rho (kg/m^3); lumped mass rho V_e / 4 per node and tet (Eq. 5, lumped) */
+  double alpha;          /* Rayleigh mass damping (b_e = alpha m_e + beta k_e*, Sec. 3.6) */
+  double beta;           /* Rayleigh stiffness damping */
+  double threshold;      /* sigma_thres of Eq. 21 in driver units; +inf disables fracture */
+  double radius;         /* kernel support R_d of Eq. 20 (length units); 0 = local criterion */
+  int32_t driver_mode;   /* GF_DRIVER_STRAIN: driver = sigma_star divided by E (dimensionless); GF_DRIVER_STRESS: sigma_star */
+  int32_t shear_coef;    /* 2: normal stress n.S.n (default); 1: Eq. 16 as printed */
+  int32_t average_degraded; /* 1: Eq. 20 averages chi_j S_j (default); 0: raw S_j */
+  int32_t reserved;      /* set to 0 */
+} gf_material;
+
+typedef void* (*gf_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*gf_free_fn)(void* ptr, void* ctx);
+
+/* Solver and runtime options. Zero-initialise and set what you need. */
+typedef struct gf_options {
+  int32_t precision;     /* GF_FP64 (default) or GF_MIXED */
+  int32_t cg_maxit;      /* 0 -> 10000 */
+  double cg_rtol;        /* stop when ||r|| <= cg_rtol ||b|| on free DOFs; 0 -> 1e-6 */
+  int32_t precond;       /* GF_PRECOND_BJACOBI */
+  int32_t device;        /* CUDA device ordinal; -1 -> the current device */
+  void* stream;          /* cudaStream_t for all work; NULL -> a stream the library creates */
+  gf_alloc_fn alloc;     /* optional device allocator (e.g. a caching allocator); NULL -> cudaMalloc */
+  gf_free_fn free;       /* matching free; required when alloc is set */
+  void* alloc_ctx;       /* passed to alloc/free */
+} gf_options;
+
+/* Per-step diagnostics (all counts after the step). */
+typedef struct gf_step_stats {
+  int32_t status;        /* gf_status of the step */
+  int32_t cg_iters;      /* CG iterations of the step (all refinement sweeps in GF_MIXED) */
+  double rel_res;        /* final ||b - A dv|| / ||b|| on free DOFs, FP64 */
+  int64_t n_broken;      /* edges with zeta = 1 */
+  int64_t n_new_broken;  /* edges that broke in this step */
+  int64_t n_chi_zero;    /* tets split into disjoint pieces (chi = 0) */
+  int32_t refine_sweeps; /* GF_MIXED: FP64 refinement sweeps; 0 in GF_FP64 */
+  int32_t reserved;
+} gf_step_stats;
+
+typedef struct gf_mesh_info {
+  int64_t n_nodes;
+  int64_t n_tets;
+  int64_t n_edges;
+  int64_t n_blocks;      /* 3x3 blocks of the fixed block-CSR pattern (node adjacency incl. diagonal) */
+  int64_t n_colours;     /* tet colours of the conflict-free assembly scatter */
+  int64_t n_nbr_pairs;   /* (tet, neighbour) pairs of Eq. 20 within R_d */
+  int64_t device_bytes;  /* device memory held by the mesh */
+} gf_mesh_info;
+
+typedef struct gf_mesh gf_mesh;
+
+/* Build a mesh from rest nodes (host, float64 [3*n_nodes]) and tets (host,
+ * int32 [4*n_tets], node ids in [0, n_nodes)).  Precomputes edges, rest data,
+ * lumped mass, the fixed block-CSR pattern, the tet colouring and the Eq. 20
+ * neighbour lists, then uploads them.  The state starts at rest: x = nodes,
+ * v = 0, no broken edge, chi = 1.  Degenerate (zero-volume) tets -> GF_BAD_ARG.
+ * `opt` may be NULL (defaults).  On success *out owns device memory until
+ * gf_mesh_destroy(). */
+gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const gf_material* mat, const gf_options* opt, gf_mesh** out);
+
+/* Host-only planning: runs the mesh_create precompute on the CPU without
+ * touching a GPU and reports its sizes in *info (device_bytes is an estimate).
+ * Optional outputs (host memory, NULL to skip): edges int32 [2*n_edges] (call
+ * once with NULL to learn n_edges), colour int32 [n_tets] (the colour of each
+ * caller tet in the conflict-free scatter), nbr_count int32 [n_tets] (Eq. 20
+ * neighbours within R_d of each caller tet, itself included). */
+gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                       const gf_material* mat, gf_mesh_info* info, int32_t* edges, int32_t* colour,
+                       int32_t* nbr_count);
+
+/* Release a mesh (NULL is ignored). */
+void gf_mesh_destroy(gf_mesh* mesh);
+
+gf_status gf_mesh_info_get(const gf_mesh* mesh, gf_mesh_info* info);
+
+/* Overwrite the state.  x, v: float64 [3*n_nodes]; labels: uint8 [n_edges]
+ * (0 unbroken, 1 broken, Eq. 21); chi: float64 [n_tets] in caller tet order.
+ * Any pointer may be NULL to keep that part.  When labels are given and chi is
+ * NULL, chi is recomputed from the labels at the (new) positions by Eq. 25. */
+gf_status gf_state_set(gf_mesh* mesh, const double* x, const double* v, const uint8_t* labels,
+                       const double* chi, int32_t mem);
+
+/* One implicit time step (Algorithm 1).  dt > 0.  f_ext: float64 [3*n_nodes]
+ * external nodal forces (NULL = none).  pinned: int32 [n_pinned] node ids whose
+ * velocity is prescribed: pinned_vel float64 [3*n_pinned] (NULL = zero).
+ * Pointers follow `mem`.  stats may be NULL.  A CG failure leaves the step
+ * applied with the last iterate and returns GF_CG_BREAKDOWN / GF_CG_MAXITER. */
+gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
+                  const double* pinned_vel, int32_t mem, gf_step_stats* stats);
+
+/* Change the solver tolerance and iteration cap between steps (rtol > 0). */
+gf_status gf_solver_set(gf_mesh* mesh, double cg_rtol, int32_t cg_maxit);
+
+/* Current positions / velocities, float64 [3*n_nodes]. */
+gf_status gf_positions_get(gf_mesh* mesh, double* x, int32_t mem);
+gf_status gf_velocities_get(gf_mesh* mesh, double* v, int32_t mem);
+
+/* Damage of the last step: driver float64 [n_edges] (max over incident tets of
+ * the Eq. 20 edge stress, divided by E in strain mode; -inf before any step),
+ * labels uint8 [n_edges].  Either pointer may be NULL. */
+gf_status gf_damage_get(gf_mesh* mesh, double* driver, uint8_t* labels, int32_t mem);
+
+/* chi of every tet (Eq. 25) in caller tet order, float64 [n_tets]. */
+gf_status gf_chi_get(gf_mesh* mesh, double* chi, int32_t mem);
+
+/* Edge list, int32 [2*n_edges] host memory, (min, max) pairs in edge order. */
+gf_status gf_edges_get(const gf_mesh* mesh, int32_t* edges);
+
+/* The last assembled linear system A dv = b (host memory): block-CSR pattern
+ * row_ptr int32 [n_nodes+1], col int32 [n_blocks], values float64
+ * [9*n_blocks] (row-major 3x3 blocks; in GF_MIXED the FP32 tangent widened),
+ * rhs float64 [3*n_nodes].  Any pointer may be NULL.  For tests and tools. */
+gf_status gf_system_get(gf_mesh* mesh, int32_t* row_ptr, int32_t* col, double* values, double* rhs);
+
+/* Kernel timing: when enabled, every kernel group of gf_step() is bracketed by
+ * CUDA events on the mesh's stream.  gf_profile_get() fills up to `n` entries
+ * of total milliseconds and launch counts since the last reset, in the order
+ * of gf_profile_names(); returns the number of groups. */
+gf_status gf_profile_enable(gf_mesh* mesh, int32_t on);
+int32_t gf_profile_get(gf_mesh* mesh, double* total_ms, int64_t* launches, int32_t n);
+const char* gf_profile_name(int32_t i);
+gf_status gf_profile_reset(gf_mesh* mesh);
+
+/* Kernel launches this mesh has issued since creation (all entry points). */
+int64_t gf_launch_count(const gf_mesh* mesh);
+
+const char* gf_status_string(gf_status s);
+const char* gf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRAPHFEM_H */

@@ -1,0 +1,9 @@
+"""GB300-native graph-based FEM fracture (remeshing-free, edge-length hyperelasticity).
+
+The compute path is the CUDA library under ``csrc/`` behind the C ABI in
+``include/graphfem.h``; ``graphfem`` is its Python binding.
+"""
+from .graphfem import (  # noqa: F401
+    DRIVER_STRAIN, DRIVER_STRESS, FP64, MEM_DEVICE, MEM_HOST, MIXED, GraphFEMError, Mesh, load_library,
+    material, mesh_create, mesh_plan,
+)

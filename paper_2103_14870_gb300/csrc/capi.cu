@@ -1,0 +1,701 @@
+// C ABI of the graph-FEM fracture step: mesh lifetime, state, one implicit step.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gf_device.h"
+
+namespace gf {
+
+thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+enum ProfGroup : int {
+  kPStress = 0, kPNonlocal, kPEdge, kPChi, kPAssemble, kPPcgInit, kPSpmv, kPPcgUpdate, kPPcgP, kPResidual,
+  kPIntegrate, kPCount
+};
+const char* kProfNames[kPCount] = {"tet_stress",  "nonlocal_avg", "edge_driver", "tet_chi",     "assemble",
+                                   "pcg_init",    "pcg_spmv",     "pcg_update",  "pcg_p",       "true_residual",
+                                   "integrate"};
+
+__global__ void k_fill(double* p, int64_t n, double v) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+// internal[i] = caller[perm[i]]
+__global__ void k_gather(const double* src, const int32_t* perm, double* dst, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+// caller[perm[i]] = internal[i]
+__global__ void k_scatter(const double* src, const int32_t* perm, double* dst, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) dst[perm[i]] = src[i];
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (dev != prev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+}  // namespace gf
+
+using namespace gf;
+
+struct gf_mesh {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  gf_alloc_fn alloc = nullptr;
+  gf_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<void*> blocks;
+  int64_t bytes = 0;
+
+  gf_material mat{};
+  gf_options opt{};
+  gf::Material mt{};
+  uint64_t lut = 0;
+  HostMesh hm;          // host copies kept for getters (pattern, edges, perm, colours)
+  DevMesh dm;
+  int32_t* perm_dev = nullptr;
+  int last_iters = 4;
+  int64_t launches = 0;
+  int64_t nbr_pairs = 0;
+
+  PcgState* h_pcg = nullptr;               // pinned host mirror
+  unsigned long long* h_cnt = nullptr;     // pinned host mirror of counters
+
+  bool prof = false;
+  double prof_ms[kPCount] = {};
+  int64_t prof_n[kPCount] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int group; int ev0; int ev1; int iter; };
+  std::vector<Rec> recs;
+  int ev_next = 0;
+};
+
+namespace {
+
+#define GF_CK(call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return e_ == cudaErrorMemoryAllocation ? GF_OOM : GF_CUDA_ERR;                        \
+    }                                                                                       \
+  } while (0)
+
+gf_status dev_alloc(gf_mesh* m, size_t bytes, void** out) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (m->alloc) {
+    p = m->alloc(bytes, m->alloc_ctx);
+    if (!p) {
+      set_last_error("device allocator returned NULL for " + std::to_string(bytes) + " bytes");
+      return GF_OOM;
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return GF_OOM;
+    }
+  }
+  m->blocks.push_back(p);
+  m->bytes += int64_t(bytes);
+  *out = p;
+  return GF_OK;
+}
+
+template <class T>
+gf_status upload(gf_mesh* m, const std::vector<T>& h, const T** out) {
+  void* p = nullptr;
+  gf_status st = dev_alloc(m, h.size() * sizeof(T), &p);
+  if (st != GF_OK) return st;
+  if (!h.empty()) GF_CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, m->stream));
+  *out = static_cast<const T*>(p);
+  return GF_OK;
+}
+
+template <class T>
+gf_status scratch(gf_mesh* m, size_t n, T** out) {
+  void* p = nullptr;
+  gf_status st = dev_alloc(m, n * sizeof(T), &p);
+  if (st != GF_OK) return st;
+  *out = static_cast<T*>(p);
+  return GF_OK;
+}
+
+void release(gf_mesh* m) {
+  if (!m) return;
+  for (void* p : m->blocks) {
+    if (m->free_fn) m->free_fn(p, m->alloc_ctx);
+    else cudaFree(p);
+  }
+  m->blocks.clear();
+  for (auto e : m->ev_pool) cudaEventDestroy(e);
+  if (m->h_pcg) cudaFreeHost(m->h_pcg);
+  if (m->h_cnt) cudaFreeHost(m->h_cnt);
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+}
+
+// profiling helpers: an event pair around each launch of a group
+int prof_mark(gf_mesh* m) {
+  if (m->ev_next == int(m->ev_pool.size())) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    m->ev_pool.push_back(e);
+  }
+  int i = m->ev_next++;
+  cudaEventRecord(m->ev_pool[i], m->stream);
+  return i;
+}
+struct Prof {
+  gf_mesh* m;
+  int group, ev0 = -1, iter;
+  Prof(gf_mesh* mm, int g, int it = -1) : m(mm), group(g), iter(it) {
+    if (m->prof) ev0 = prof_mark(m);
+  }
+  ~Prof() {
+    if (m->prof) m->recs.push_back({group, ev0, prof_mark(m), iter});
+  }
+};
+
+void prof_collect(gf_mesh* m, int cg_iters, bool converged) {
+  if (!m->prof) return;
+  for (auto& r : m->recs) {
+    // early-exit PCG launches after convergence did no work: do not count them
+    if (r.iter >= 0) {
+      bool worked = (r.group == kPSpmv || r.group == kPPcgUpdate) ? r.iter < cg_iters
+                                                                    : r.iter < (converged ? cg_iters - 1 : cg_iters);
+      if (!worked) continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m->ev_pool[r.ev0], m->ev_pool[r.ev1]);
+    m->prof_ms[r.group] += ms;
+    m->prof_n[r.group] += 1;
+  }
+  m->recs.clear();
+  m->ev_next = 0;
+}
+
+bool material_ok(const gf_material& M) {
+  if (!(M.young > 0) || !(M.poisson > -1.0 && M.poisson < 0.5) || !(M.density > 0) || !(M.radius >= 0) ||
+      std::isnan(M.threshold) || !(M.alpha >= 0) || !(M.beta >= 0) || (M.shear_coef != 1 && M.shear_coef != 2) ||
+      (M.driver_mode != GF_DRIVER_STRAIN && M.driver_mode != GF_DRIVER_STRESS)) {
+    set_last_error("invalid material (need E > 0, -1 < nu < 0.5, rho > 0, R_d >= 0, alpha, beta >= 0, shear_coef 1|2)");
+    return false;
+  }
+  return true;
+}
+
+bool valid_mem(int32_t mem) { return mem == GF_MEM_HOST || mem == GF_MEM_DEVICE; }
+
+cudaMemcpyKind to_dev(int32_t mem) { return mem == GF_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind from_dev(int32_t mem) { return mem == GF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+gf_status recompute_chi(gf_mesh* m) {
+  m->launches += launch_tet_stress(m->dm, m->mt, m->stream);
+  m->launches += launch_tet_chi(m->dm, m->mt, m->lut, m->stream);
+  GF_CK(cudaGetLastError());
+  return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gf_status_string(gf_status s) {
+  switch (s) {
+    case GF_OK: return "ok";
+    case GF_BAD_ARG: return "bad argument";
+    case GF_CUDA_ERR: return "CUDA error";
+    case GF_CG_BREAKDOWN: return "CG breakdown (p^T A p <= 0)";
+    case GF_CG_MAXITER: return "CG reached the iteration cap";
+    case GF_NAN: return "non-finite value";
+    case GF_TIMEOUT: return "device wait timed out";
+    case GF_OOM: return "out of device memory";
+    case GF_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+const char* gf_last_error(void) { return gf::g_last_error.c_str(); }
+
+gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const gf_material* mat, const gf_options* opt_in, gf_mesh** out) {
+  if (!out) {
+    set_last_error("out is NULL");
+    return GF_BAD_ARG;
+  }
+  *out = nullptr;
+  if (!nodes || !tets || !mat) {
+    set_last_error("nodes, tets and mat must not be NULL");
+    return GF_BAD_ARG;
+  }
+  gf_options opt{};
+  if (opt_in) opt = *opt_in;
+  if (opt.cg_maxit <= 0) opt.cg_maxit = 10000;
+  if (!(opt.cg_rtol > 0)) opt.cg_rtol = 1e-6;
+  if (opt.precision != GF_FP64) {
+    set_last_error("only GF_FP64 is available in this build");
+    return GF_UNSUPPORTED;
+  }
+  if (opt.precond != GF_PRECOND_BJACOBI) {
+    set_last_error("unknown preconditioner");
+    return GF_UNSUPPORTED;
+  }
+  if ((opt.alloc == nullptr) != (opt.free == nullptr)) {
+    set_last_error("alloc and free must be given together");
+    return GF_BAD_ARG;
+  }
+  const gf_material& M = *mat;
+  if (!material_ok(M)) return GF_BAD_ARG;
+  int dev = opt.device;
+  if (dev < 0) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      set_last_error("no CUDA device");
+      return GF_CUDA_ERR;
+    }
+  }
+  DeviceGuard guard(dev);
+
+  gf_mesh* m = new gf_mesh();
+  m->device = dev;
+  m->mat = M;
+  m->opt = opt;
+  m->alloc = opt.alloc;
+  m->free_fn = opt.free;
+  m->alloc_ctx = opt.alloc_ctx;
+  auto fail = [&](gf_status st) {
+    release(m);
+    delete m;
+    return st;
+  };
+  if (opt.stream) {
+    m->stream = static_cast<cudaStream_t>(opt.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      set_last_error("cudaStreamCreate failed");
+      return fail(GF_CUDA_ERR);
+    }
+    m->own_stream = true;
+  }
+  std::string err;
+  gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, M, m->hm, err);
+  if (st != GF_OK) {
+    set_last_error(err);
+    return fail(st);
+  }
+  const double lam = M.young * M.poisson / ((1.0 + M.poisson) * (1.0 - 2.0 * M.poisson));
+  const double mu = M.young / (2.0 * (1.0 + M.poisson));
+  m->mt = gf::Material{lam, mu, M.young, M.alpha, M.beta, M.threshold, M.radius, double(M.shear_coef),
+                       M.driver_mode == GF_DRIVER_STRESS ? 1 : 0, M.average_degraded ? 1 : 0};
+  m->lut = disconnect_table();
+
+  HostMesh& hm = m->hm;
+  DevMesh& d = m->dm;
+  d.N = hm.n_nodes;
+  d.T = hm.n_tets;
+  d.NE = hm.n_edges;
+  d.NB = hm.n_blocks;
+  d.G = int64_t(hm.nbr.group_off.size());
+#define UP(field, vec, type)                                                     \
+  do {                                                                           \
+    const type* p_ = nullptr;                                                    \
+    if ((st = upload(m, vec, &p_)) != GF_OK) return fail(st);                    \
+    d.field = reinterpret_cast<decltype(d.field)>(p_);                           \
+  } while (0)
+  UP(tets, hm.tets, int32_t);
+  UP(tet_edges, hm.tet_edges, int32_t);
+  UP(slot, hm.slot, int32_t);
+  UP(rest, hm.rest, double);
+  UP(mass, hm.mass, double);
+  UP(row_ptr, hm.row_ptr, int32_t);
+  UP(col, hm.col, int32_t);
+  UP(diag_blk, hm.diag_blk, int32_t);
+  UP(edges, hm.edges, int32_t);
+  UP(et_ptr, hm.et_ptr, int32_t);
+  UP(et_tet, hm.et_tet, int32_t);
+  UP(nb_off, hm.nbr.group_off, int64_t);
+  UP(nb_len, hm.nbr.group_len, int32_t);
+  UP(nb_idx, hm.nbr.idx, int32_t);
+  UP(nb_w, hm.nbr.w, double);
+#undef UP
+  {
+    const int32_t* pp = nullptr;
+    if ((st = upload(m, hm.perm, &pp)) != GF_OK) return fail(st);
+    m->perm_dev = const_cast<int32_t*>(pp);
+  }
+  const int64_t N = d.N, T = d.T, NE = d.NE, NB = d.NB;
+  if ((st = scratch(m, 3 * N, &d.x)) || (st = scratch(m, 3 * N, &d.v)) || (st = scratch(m, NE, &d.labels)) ||
+      (st = scratch(m, T, &d.chi)) || (st = scratch(m, NE, &d.driver)) || (st = scratch(m, 6 * T, &d.sig_in)) ||
+      (st = scratch(m, 6 * T, &d.sig_bar)) || (st = scratch(m, 6 * T, &d.sigf)) || (st = scratch(m, 9 * NB, &d.val)) ||
+      (st = scratch(m, 3 * N, &d.rhs)) || (st = scratch(m, 3 * N, &d.dv)) || (st = scratch(m, 3 * N, &d.r)) ||
+      (st = scratch(m, 3 * N, &d.z)) || (st = scratch(m, 3 * N, &d.p)) || (st = scratch(m, 3 * N, &d.q)) ||
+      (st = scratch(m, 9 * N, &d.pinv)) || (st = scratch(m, N, &d.pinned)) || (st = scratch(m, 3 * N, &d.f_ext)) ||
+      (st = scratch(m, N, &d.pin_ids)) || (st = scratch(m, 3 * N, &d.pin_vel)) || (st = scratch(m, 1, &d.pcg)) ||
+      (st = scratch(m, 2 * kMaxPartials, &d.partials)) || (st = scratch(m, kTickets, &d.tickets)) ||
+      (st = scratch(m, kCntMax, &d.counters)))
+    return fail(st);
+  if (cudaMallocHost(&m->h_pcg, sizeof(PcgState)) != cudaSuccess ||
+      cudaMallocHost(&m->h_cnt, sizeof(unsigned long long) * kCntMax) != cudaSuccess) {
+    set_last_error("cudaMallocHost failed");
+    return fail(GF_OOM);
+  }
+  // rest state: x = nodes, v = 0, no broken edge, chi = 1, driver = -inf
+  GF_CK(cudaMemcpyAsync(d.x, nodes, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, m->stream));
+  GF_CK(cudaMemsetAsync(d.v, 0, sizeof(double) * 3 * N, m->stream));
+  GF_CK(cudaMemsetAsync(d.labels, 0, NE, m->stream));
+  GF_CK(cudaMemsetAsync(d.tickets, 0, sizeof(unsigned) * kTickets, m->stream));
+  GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, m->stream));
+  GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * NB, m->stream));
+  GF_CK(cudaMemsetAsync(d.rhs, 0, sizeof(double) * 3 * N, m->stream));
+  k_fill<<<unsigned((T + 255) / 256), 256, 0, m->stream>>>(d.chi, T, 1.0);
+  k_fill<<<unsigned((NE + 255) / 256), 256, 0, m->stream>>>(d.driver, NE, -INFINITY);
+  m->launches += 2;
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaStreamSynchronize(m->stream));
+  // drop host copies not needed after upload
+  m->nbr_pairs = hm.nbr.pairs;
+  hm.rest = {};
+  hm.slot = {};
+  hm.nbr = {};
+  hm.et_tet = {};
+  hm.tets = {};
+  hm.tet_edges = {};
+  hm.mass = {};
+  *out = m;
+  return GF_OK;
+}
+
+gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                       const gf_material* mat, gf_mesh_info* info, int32_t* edges, int32_t* colour,
+                       int32_t* nbr_count) {
+  if (!nodes || !tets || !mat || !info) {
+    set_last_error("nodes, tets, mat and info must not be NULL");
+    return GF_BAD_ARG;
+  }
+  if (!material_ok(*mat)) return GF_BAD_ARG;
+  HostMesh hm;
+  std::string err;
+  gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, *mat, hm, err);
+  if (st != GF_OK) {
+    set_last_error(err);
+    return st;
+  }
+  info->n_nodes = hm.n_nodes;
+  info->n_tets = hm.n_tets;
+  info->n_edges = hm.n_edges;
+  info->n_blocks = hm.n_blocks;
+  info->n_colours = int64_t(hm.colour_ptr.size()) - 1;
+  info->n_nbr_pairs = hm.nbr.pairs;
+  const int64_t N = hm.n_nodes, T = hm.n_tets;
+  info->device_bytes = int64_t(hm.tets.size() * 4 + hm.tet_edges.size() * 4 + hm.slot.size() * 4 +
+                               hm.rest.size() * 8 + hm.row_ptr.size() * 4 + hm.col.size() * 4 +
+                               hm.edges.size() * 4 + hm.et_ptr.size() * 4 + hm.et_tet.size() * 4 +
+                               hm.nbr.idx.size() * 12 + hm.nbr.group_off.size() * 12) +
+                       N * (8 + 8 * 3 * 12 + 9 * 8 + 8) + T * (8 + 18 * 8 + 4) + hm.n_edges * 9 + hm.n_blocks * 72;
+  if (edges) std::memcpy(edges, hm.edges.data(), sizeof(int32_t) * hm.edges.size());
+  if (colour)
+    for (size_t c = 0; c + 1 < hm.colour_ptr.size(); ++c)
+      for (int32_t i = hm.colour_ptr[c]; i < hm.colour_ptr[c + 1]; ++i) colour[hm.perm[i]] = int32_t(c);
+  if (nbr_count) {
+    const NeighbourSell& S = hm.nbr;
+    for (int64_t i = 0; i < T; ++i) {
+      int64_t g = i / 32, l = i % 32;
+      int32_t cnt = 0;
+      for (int32_t k = 0; k < S.group_len[g]; ++k) cnt += S.w[S.group_off[g] + 32 * k + l] > 0.0 ? 1 : 0;
+      nbr_count[hm.perm[i]] = cnt;
+    }
+  }
+  return GF_OK;
+}
+
+void gf_mesh_destroy(gf_mesh* mesh) {
+  if (!mesh) return;
+  DeviceGuard guard(mesh->device);
+  cudaStreamSynchronize(mesh->stream);
+  release(mesh);
+  delete mesh;
+}
+
+gf_status gf_mesh_info_get(const gf_mesh* m, gf_mesh_info* info) {
+  if (!m || !info) {
+    set_last_error("NULL argument");
+    return GF_BAD_ARG;
+  }
+  info->n_nodes = m->dm.N;
+  info->n_tets = m->dm.T;
+  info->n_edges = m->dm.NE;
+  info->n_blocks = m->dm.NB;
+  info->n_colours = int64_t(m->hm.colour_ptr.size()) - 1;
+  info->n_nbr_pairs = m->nbr_pairs;
+  info->device_bytes = m->bytes;
+  return GF_OK;
+}
+
+gf_status gf_state_set(gf_mesh* m, const double* x, const double* v, const uint8_t* labels, const double* chi,
+                       int32_t mem) {
+  if (!m || !valid_mem(mem)) {
+    set_last_error("NULL mesh or bad mem kind");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  DevMesh& d = m->dm;
+  if (x) GF_CK(cudaMemcpyAsync(d.x, x, sizeof(double) * 3 * d.N, to_dev(mem), m->stream));
+  if (v) GF_CK(cudaMemcpyAsync(d.v, v, sizeof(double) * 3 * d.N, to_dev(mem), m->stream));
+  if (labels) GF_CK(cudaMemcpyAsync(d.labels, labels, d.NE, to_dev(mem), m->stream));
+  if (chi) {
+    const double* src = chi;
+    if (mem == GF_MEM_HOST) {
+      GF_CK(cudaMemcpyAsync(d.sig_in, chi, sizeof(double) * d.T, cudaMemcpyHostToDevice, m->stream));
+      src = d.sig_in;
+    }
+    k_gather<<<unsigned((d.T + 255) / 256), 256, 0, m->stream>>>(src, m->perm_dev, d.chi, d.T);
+    m->launches += 1;
+    GF_CK(cudaGetLastError());
+  } else if (labels) {
+    gf_status st = recompute_chi(m);
+    if (st != GF_OK) return st;
+  }
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_solver_set(gf_mesh* m, double rtol, int32_t maxit) {
+  if (!m || !(rtol > 0) || maxit <= 0) {
+    set_last_error("need rtol > 0 and maxit > 0");
+    return GF_BAD_ARG;
+  }
+  m->opt.cg_rtol = rtol;
+  m->opt.cg_maxit = maxit;
+  return GF_OK;
+}
+
+gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
+                  const double* pinned_vel, int32_t mem, gf_step_stats* stats) {
+  if (!m || !valid_mem(mem) || !(dt > 0) || !std::isfinite(dt) || n_pinned < 0 || n_pinned > m->dm.N ||
+      (n_pinned > 0 && !pinned)) {
+    set_last_error("bad step arguments (need dt > 0, 0 <= n_pinned <= n_nodes, pinned when n_pinned > 0)");
+    return GF_BAD_ARG;
+  }
+  if (mem == GF_MEM_HOST)
+    for (int64_t i = 0; i < n_pinned; ++i)
+      if (pinned[i] < 0 || pinned[i] >= m->dm.N) {
+        set_last_error("pinned node id out of range");
+        return GF_BAD_ARG;
+      }
+  DeviceGuard guard(m->device);
+  cudaStream_t s = m->stream;
+  DevMesh d = m->dm;   // per-step view (input pointers may be overridden)
+  const int64_t N = d.N;
+
+  GF_CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long) * kCntMax, s));
+  if (f_ext && mem == GF_MEM_HOST) {
+    GF_CK(cudaMemcpyAsync(d.f_ext, f_ext, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+  } else if (f_ext) {
+    d.f_ext = const_cast<double*>(f_ext);
+  }
+  if (n_pinned > 0) {
+    if (mem == GF_MEM_HOST) {
+      GF_CK(cudaMemcpyAsync(d.pin_ids, pinned, sizeof(int32_t) * n_pinned, cudaMemcpyHostToDevice, s));
+      if (pinned_vel)
+        GF_CK(cudaMemcpyAsync(d.pin_vel, pinned_vel, sizeof(double) * 3 * n_pinned, cudaMemcpyHostToDevice, s));
+    } else {
+      d.pin_ids = const_cast<int32_t*>(pinned);
+      if (pinned_vel) d.pin_vel = const_cast<double*>(pinned_vel);
+    }
+  }
+  const gf::Material& mt = m->mt;
+  int64_t L = 0;
+  // ---- 1. damage at the start-of-step positions (Eq. 14-25) ----
+  { Prof p(m, kPStress); L += launch_tet_stress(d, mt, s); }
+  if (mt.radius > 0.0) {
+    Prof p(m, kPNonlocal);
+    L += launch_nonlocal(d, s);
+  } else {
+    d.sig_bar = d.sig_in;   // R_d = 0: the tet alone (local criterion)
+  }
+  { Prof p(m, kPEdge); L += launch_edge_driver(d, mt, s); }
+  { Prof p(m, kPChi); L += launch_tet_chi(d, mt, m->lut, s); }
+  // ---- 2. system A dv = b (Eq. 2, 12, 32-34) ----
+  {
+    Prof p(m, kPAssemble);
+    GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
+    L += launch_node_init(d, dt, mt, f_ext != nullptr, s);
+    const auto& cp = m->hm.colour_ptr;
+    for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble(d, mt, dt, cp[c], cp[c + 1], s);
+  }
+  // ---- 3. projected block-Jacobi PCG ----
+  PcgState init{};
+  init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+  init.maxit = m->opt.cg_maxit;
+  *m->h_pcg = init;
+  GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+  GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
+  GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
+  L += launch_set_pinned(d, n_pinned, pinned_vel != nullptr, s);
+  { Prof p(m, kPPcgInit); L += launch_pcg_init(d, s); }
+  int launched_iters = 0;
+  int chunk = std::max(1, std::min(m->last_iters + 1, 64));
+  for (;;) {
+    for (int j = 0; j < chunk; ++j, ++launched_iters) {
+      { Prof p(m, kPSpmv, launched_iters); L += launch_pcg_iter(d, s, 0); }
+      { Prof p(m, kPPcgUpdate, launched_iters); L += launch_pcg_iter(d, s, 1); }
+      { Prof p(m, kPPcgP, launched_iters); L += launch_pcg_iter(d, s, 2); }
+    }
+    GF_CK(cudaGetLastError());
+    GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaStreamSynchronize(s));
+    if (m->h_pcg->done || launched_iters >= m->opt.cg_maxit) break;
+    chunk = 8;
+  }
+  { Prof p(m, kPResidual); L += launch_true_residual(d, s); }
+  // ---- 4. v += dv, x += dt v ----
+  { Prof p(m, kPIntegrate); L += launch_integrate(d, dt, s); }
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaMemcpyAsync(m->h_cnt, d.counters, sizeof(unsigned long long) * kCntMax, cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaStreamSynchronize(s));
+  m->launches += L;
+  const PcgState& ps = *m->h_pcg;
+  m->last_iters = ps.iters;
+  prof_collect(m, ps.iters, ps.status == GF_OK);
+  gf_status status = gf_status(ps.status);
+  const double rel = ps.bb > 0 ? std::sqrt(ps.true_rr / ps.bb) : 0.0;
+  if (status == GF_OK && !std::isfinite(rel)) status = GF_NAN;
+  if (m->h_cnt[3] != 0) {
+    set_last_error("pinned node id out of range (skipped)");
+    status = GF_BAD_ARG;
+  }
+  if (stats) {
+    stats->status = status;
+    stats->cg_iters = ps.iters;
+    stats->rel_res = rel;
+    stats->n_broken = int64_t(m->h_cnt[kCntBroken]);
+    stats->n_new_broken = int64_t(m->h_cnt[kCntNewBroken]);
+    stats->n_chi_zero = int64_t(m->h_cnt[kCntChiZero]);
+    stats->refine_sweeps = 0;
+    stats->reserved = 0;
+  }
+  if (status != GF_OK && status != GF_BAD_ARG)
+    set_last_error(std::string("step: ") + gf_status_string(status));
+  return status;
+}
+
+gf_status gf_positions_get(gf_mesh* m, double* x, int32_t mem) {
+  if (!m || !x || !valid_mem(mem)) {
+    set_last_error("bad arguments");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  GF_CK(cudaMemcpyAsync(x, m->dm.x, sizeof(double) * 3 * m->dm.N, from_dev(mem), m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_velocities_get(gf_mesh* m, double* v, int32_t mem) {
+  if (!m || !v || !valid_mem(mem)) {
+    set_last_error("bad arguments");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  GF_CK(cudaMemcpyAsync(v, m->dm.v, sizeof(double) * 3 * m->dm.N, from_dev(mem), m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_damage_get(gf_mesh* m, double* driver, uint8_t* labels, int32_t mem) {
+  if (!m || !valid_mem(mem)) {
+    set_last_error("bad arguments");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  if (driver) GF_CK(cudaMemcpyAsync(driver, m->dm.driver, sizeof(double) * m->dm.NE, from_dev(mem), m->stream));
+  if (labels) GF_CK(cudaMemcpyAsync(labels, m->dm.labels, m->dm.NE, from_dev(mem), m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_chi_get(gf_mesh* m, double* chi, int32_t mem) {
+  if (!m || !chi || !valid_mem(mem)) {
+    set_last_error("bad arguments");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  DevMesh& d = m->dm;
+  // scatter to caller order through a scratch buffer
+  k_scatter<<<unsigned((d.T + 255) / 256), 256, 0, m->stream>>>(d.chi, m->perm_dev, d.sigf, d.T);
+  m->launches += 1;
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaMemcpyAsync(chi, d.sigf, sizeof(double) * d.T, from_dev(mem), m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_edges_get(const gf_mesh* m, int32_t* edges) {
+  if (!m || !edges) {
+    set_last_error("bad arguments");
+    return GF_BAD_ARG;
+  }
+  std::memcpy(edges, m->hm.edges.data(), sizeof(int32_t) * m->hm.edges.size());
+  return GF_OK;
+}
+
+gf_status gf_system_get(gf_mesh* m, int32_t* row_ptr, int32_t* col, double* values, double* rhs) {
+  if (!m) {
+    set_last_error("NULL mesh");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  if (row_ptr) std::memcpy(row_ptr, m->hm.row_ptr.data(), sizeof(int32_t) * m->hm.row_ptr.size());
+  if (col) std::memcpy(col, m->hm.col.data(), sizeof(int32_t) * m->hm.col.size());
+  if (values) GF_CK(cudaMemcpyAsync(values, m->dm.val, sizeof(double) * 9 * m->dm.NB, cudaMemcpyDeviceToHost, m->stream));
+  if (rhs) GF_CK(cudaMemcpyAsync(rhs, m->dm.rhs, sizeof(double) * 3 * m->dm.N, cudaMemcpyDeviceToHost, m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_profile_enable(gf_mesh* m, int32_t on) {
+  if (!m) return GF_BAD_ARG;
+  m->prof = on != 0;
+  return GF_OK;
+}
+
+int32_t gf_profile_get(gf_mesh* m, double* total_ms, int64_t* launches, int32_t n) {
+  if (!m) return 0;
+  for (int i = 0; i < std::min<int32_t>(n, kPCount); ++i) {
+    if (total_ms) total_ms[i] = m->prof_ms[i];
+    if (launches) launches[i] = m->prof_n[i];
+  }
+  return kPCount;
+}
+
+const char* gf_profile_name(int32_t i) { return (i >= 0 && i < kPCount) ? kProfNames[i] : ""; }
+
+gf_status gf_profile_reset(gf_mesh* m) {
+  if (!m) return GF_BAD_ARG;
+  std::fill(std::begin(m->prof_ms), std::end(m->prof_ms), 0.0);
+  std::fill(std::begin(m->prof_n), std::end(m->prof_n), int64_t(0));
+  return GF_OK;
+}
+
+int64_t gf_launch_count(const gf_mesh* m) { return m ? m->launches : 0; }
+
+}  // extern "C"

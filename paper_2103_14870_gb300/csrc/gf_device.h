@@ -1,0 +1,93 @@
+// Device-side data of one mesh and the kernel launchers (FP64 path).
+#pragma once
+
+#include "gf_internal.h"
+
+namespace gf {
+
+// Scalars of one PCG solve, resident in device memory so the iteration loop
+// needs no host round trip; kernels read them and the last CTA of each
+// reduction writes them.
+struct PcgState {
+  double bb;      // ||b_free||^2 (reference of the relative tolerance)
+  double rz;      // r . z
+  double pq;      // p . A p
+  double rr;      // r . r
+  double alpha, beta;
+  double tol2;    // rtol^2
+  double true_rr; // ||b - A dv||^2 after the solve
+  int32_t iters, maxit, done, status;
+};
+
+enum Counter : int { kCntBroken = 0, kCntNewBroken = 1, kCntChiZero = 2, kCntMax = 4 };
+
+struct DevMesh {
+  int64_t N = 0, T = 0, NE = 0, NB = 0, G = 0;    // nodes, tets, edges, blocks, neighbour groups
+  // fixed mesh data
+  const int4* tets = nullptr;          // [T] internal order
+  const int32_t* tet_edges = nullptr;  // [T][6]
+  const int32_t* slot = nullptr;       // [T][16]
+  const double* rest = nullptr;        // [kRestFields][T]
+  const double* mass = nullptr;        // [N]
+  const int32_t* row_ptr = nullptr;    // [N+1]
+  const int32_t* col = nullptr;        // [NB]
+  const int32_t* diag_blk = nullptr;   // [N]
+  const int2* edges = nullptr;         // [NE]
+  const int32_t* et_ptr = nullptr;     // [NE+1]
+  const int32_t* et_tet = nullptr;
+  const int64_t* nb_off = nullptr;     // [G]
+  const int32_t* nb_len = nullptr;     // [G]
+  const int32_t* nb_idx = nullptr;
+  const double* nb_w = nullptr;
+  // state
+  double* x = nullptr;                 // [3N]
+  double* v = nullptr;                 // [3N]
+  uint8_t* labels = nullptr;           // [NE]
+  double* chi = nullptr;               // [T] internal order
+  double* driver = nullptr;            // [NE]
+  // per-step work
+  double* sig_in = nullptr;            // [T][6] averaged field (chi S or S)
+  double* sig_bar = nullptr;           // [T][6] Eq. 20 averages
+  double* sigf = nullptr;              // [T][6] local edge-normal stresses
+  double* val = nullptr;               // [NB][9] system matrix A
+  double* rhs = nullptr;               // [3N] b
+  double* dv = nullptr;                // [3N] unknown
+  double* r = nullptr;
+  double* z = nullptr;
+  double* p = nullptr;
+  double* q = nullptr;
+  double* pinv = nullptr;              // [N][9] block-Jacobi inverses
+  uint8_t* pinned = nullptr;           // [N] 1 = velocity prescribed
+  double* f_ext = nullptr;             // [3N] staging
+  int32_t* pin_ids = nullptr;          // [N] staging
+  double* pin_vel = nullptr;           // [3N] staging
+  PcgState* pcg = nullptr;
+  double* partials = nullptr;          // reduction partials
+  unsigned* tickets = nullptr;         // reduction tickets (one per reduction site)
+  unsigned long long* counters = nullptr;  // [kCntMax]
+};
+
+struct Material {
+  double lam, mu, young, alpha, beta, threshold, radius;
+  double kappa;       // shear coefficient of Eq. 16
+  int driver_stress;  // 0: driver = sigma*/E, 1: sigma*
+  int average_degraded;
+};
+
+constexpr int kMaxPartials = 4096;     // max CTAs of a reducing launch
+constexpr int kTickets = 8;
+
+// launchers (return the number of kernels launched)
+int launch_tet_stress(const DevMesh& m, const Material& mt, cudaStream_t s);
+int launch_nonlocal(const DevMesh& m, cudaStream_t s);
+int launch_edge_driver(const DevMesh& m, const Material& mt, cudaStream_t s);
+int launch_tet_chi(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s);
+int launch_node_init(const DevMesh& m, double dt, const Material& mt, bool has_fext, cudaStream_t s);
+int launch_assemble(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s);
+int launch_set_pinned(const DevMesh& m, int64_t n_pinned, bool has_vel, cudaStream_t s);
+int launch_pcg_init(const DevMesh& m, cudaStream_t s);
+int launch_pcg_iter(const DevMesh& m, cudaStream_t s, int kernel /*0 spmv, 1 update, 2 p*/);
+int launch_true_residual(const DevMesh& m, cudaStream_t s);
+int launch_integrate(const DevMesh& m, double dt, cudaStream_t s);
+
+}  // namespace gf

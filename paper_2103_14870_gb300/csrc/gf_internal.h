@@ -1,0 +1,74 @@
+// Internal declarations shared by the graph-FEM library translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "graphfem.h"
+
+#ifdef __CUDACC__
+#define GF_HD __host__ __device__
+#else
+#define GF_HD
+#endif
+
+namespace gf {
+
+// Local edge order of a tet (Eq. 15): (0,1) (0,2) (0,3) (1,2) (1,3) (2,3).
+// Edge k joins local nodes edge_a(k) -> edge_b(k).
+GF_HD constexpr int edge_a(int k) { return k < 3 ? 0 : (k < 5 ? 1 : 2); }
+GF_HD constexpr int edge_b(int k) { return k < 3 ? k + 1 : (k == 3 ? 2 : 3); }
+
+// Field offsets of the per-tet rest data (field-major, field f of tet t at f*T + t).
+enum RestField : int {
+  kRestB = 0,    // B = Dm^-1, 9 values row-major (Dm columns X1-X0, X2-X0, X3-X0)
+  kRestS0 = 9,   // rest squared edge lengths, 6
+  kRestH = 15,   // V * d2Psi/ds ds (Eq. 37 in edge lengths), 21 upper-triangle values row-major
+  kRestV = 36,   // rest volume
+  kRestFields = 37
+};
+
+// Index of (k, l), k <= l, in the packed upper triangle of a 6x6 matrix.
+GF_HD constexpr int tri6(int k, int l) { return k * 6 - k * (k - 1) / 2 + (l - k); }
+
+struct NeighbourSell {            // Eq. 20 neighbour lists, 32 tets per group, entry-major in a group
+  std::vector<int64_t> group_off; // [G] first entry of the group
+  std::vector<int32_t> group_len; // [G] entries per lane (max count in the group)
+  std::vector<int32_t> idx;       // [sum 32*len] neighbour tet (internal order); padding -> own tet
+  std::vector<double> w;          // normalised weights; padding -> 0
+  int64_t pairs = 0;              // real (unpadded) pairs
+};
+
+// Everything mesh_create computes on the host before upload.
+struct HostMesh {
+  int64_t n_nodes = 0, n_tets = 0, n_edges = 0, n_blocks = 0;
+  std::vector<int32_t> tets;       // [T][4] internal (colour-major) order
+  std::vector<int32_t> perm;       // internal tet -> caller tet
+  std::vector<int32_t> colour_ptr; // [C+1] internal ranges of each colour
+  std::vector<int32_t> edges;      // [NE][2]
+  std::vector<int32_t> tet_edges;  // [T][6] internal order
+  std::vector<int32_t> row_ptr;    // [N+1] block-CSR pattern
+  std::vector<int32_t> col;        // [NB]
+  std::vector<int32_t> diag_blk;   // [N] block index of (i, i)
+  std::vector<int32_t> slot;       // [T][16] block index of local (a, b), internal order
+  std::vector<int32_t> et_ptr;     // [NE+1] edge -> incident tets
+  std::vector<int32_t> et_tet;     // internal tet ids
+  std::vector<double> rest;        // [kRestFields][T]
+  std::vector<double> mass;        // [N] lumped
+  NeighbourSell nbr;
+};
+
+// Host precompute; returns GF_OK or GF_BAD_ARG with `err` set.
+gf_status build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                          const gf_material& mat, HostMesh& hm, std::string& err);
+
+// 64-bit table: bit m set when the broken-edge mask m (bit k = local edge k)
+// leaves the tet's four nodes in two or more pieces (Eq. 25's disjoint rule).
+uint64_t disconnect_table();
+
+void set_last_error(const std::string& msg);
+
+}  // namespace gf

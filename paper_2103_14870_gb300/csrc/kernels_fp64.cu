@@ -1,0 +1,620 @@
+// FP64 kernels of one graph-FEM fracture step (sm_103a).
+//
+// Order inside a step (Algorithm 1, Sec. 4.3):
+//   k_tet_stress -> k_nonlocal -> k_edge_driver -> k_tet_chi     (Eq. 14-25)
+//   memset(A) -> k_node_init -> k_assemble per colour            (Eq. 2, 12, 32-34)
+//   k_set_pinned -> k_pcg_init -> {k_pcg_spmv, k_pcg_update, k_pcg_p}* -> k_true_residual -> k_integrate
+//
+// FP64 on GB300 runs at ~1/61 of the FP32 rate (measured 1.19 TFLOP/s), so
+// these kernels are FP64-pipe bound rather than HBM bound; they are written to
+// minimise FP64 operations: StVK in edge lengths is an exact quadratic form
+// V Psi = 1/2 (s - s0)^T Hs (s - s0) with a per-tet constant Hs (precomputed),
+// so forces and tangents need no C or F at all.
+#include <cfloat>
+#include <cmath>
+
+#include "gf_device.h"
+
+namespace gf {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void ld3(const double* __restrict__ a, int64_t i, double o[3]) {
+  const double* p = a + 3 * i;
+  o[0] = p[0];
+  o[1] = p[1];
+  o[2] = p[2];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic grid reduction of NV doubles: per-CTA partials, then the last
+// CTA to arrive sums all partials in CTA order.  Every thread of every CTA must
+// call it.  Returns true in the last CTA, with the totals in out[] (valid in
+// thread 0).  Nothing waits on another CTA.
+template <int NV>
+__device__ bool grid_reduce(double (&v)[NV], double* partials, unsigned* ticket, double (&out)[NV]) {
+  __shared__ double sh[NV][32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = warp_sum(v[i]);
+    if (lane == 0) sh[i][wid] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = warp_sum(lane < nw ? sh[i][lane] : 0.0);
+      if (lane == 0) partials[blockIdx.x * NV + i] = t;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned k = atomicAdd(ticket, 1u);
+    last = (k == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = 0.0;
+    for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) t += __ldcg(&partials[j * NV + i]);
+    t = warp_sum(t);
+    __syncthreads();
+    if (lane == 0) sh[i][wid] = t;
+    __syncthreads();
+    if (wid == 0) {
+      t = warp_sum(lane < nw ? sh[i][lane] : 0.0);
+      if (lane == 0) out[i] = t;
+    }
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+__device__ __forceinline__ void warp_count(unsigned long long c, unsigned long long* dst) {
+  unsigned v = __reduce_add_sync(0xffffffffu, unsigned(c));
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, (unsigned long long)v);
+}
+
+// C = B^T G B, G_ij = (s_0i + s_0j - s_ij)/2 (Thm 3.1 in closed form); Voigt out.
+__device__ __forceinline__ void cauchy_green(const double s[6], const double B[9], double C[6]) {
+  double G[3][3];
+  G[0][0] = s[0];
+  G[1][1] = s[1];
+  G[2][2] = s[2];
+  G[0][1] = G[1][0] = 0.5 * (s[0] + s[1] - s[3]);
+  G[0][2] = G[2][0] = 0.5 * (s[0] + s[2] - s[4]);
+  G[1][2] = G[2][1] = 0.5 * (s[1] + s[2] - s[5]);
+  double Y[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Y[r][c] = G[r][0] * B[c] + G[r][1] * B[3 + c] + G[r][2] * B[6 + c];
+  const int I[6] = {0, 1, 2, 0, 0, 1}, J[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int v = 0; v < 6; ++v) C[v] = B[I[v]] * Y[0][J[v]] + B[3 + I[v]] * Y[1][J[v]] + B[6 + I[v]] * Y[2][J[v]];
+}
+
+// Normal stress along e (Eq. 16 with the current direction, Eq. 17): (e.S.e)/|e|^2,
+// shear terms weighted by kappa.
+__device__ __forceinline__ double normal_stress(const double e[3], double s, const double S[6], double kappa) {
+  double q = e[0] * e[0] * S[0] + e[1] * e[1] * S[1] + e[2] * e[2] * S[2] +
+             kappa * (e[0] * e[1] * S[3] + e[0] * e[2] * S[4] + e[1] * e[2] * S[5]);
+  return q / s;
+}
+
+// ---------------------------------------------------------------------------
+// Damage: stress, non-local average, edge driver + relabel, chi
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) k_tet_stress(DevMesh m, Material mt) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
+  const int4 n = m.tets[t];
+  const int nid[4] = {n.x, n.y, n.z, n.w};
+  double P[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) ld3(m.x, nid[a], P[a]);
+  double e[6][3], s[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e[k][c] = P[edge_b(k)][c] - P[edge_a(k)][c];
+    s[k] = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2];
+  }
+  double B[9];
+#pragma unroll
+  for (int f = 0; f < 9; ++f) B[f] = m.rest[(kRestB + f) * m.T + t];
+  double C[6];
+  cauchy_green(s, B, C);
+  // second Piola-Kirchhoff stress of Eq. 37: lam/2 (tr C - 3) I + mu (C - I)
+  const double h = 0.5 * mt.lam * (C[0] + C[1] + C[2] - 3.0);
+  double S[6] = {h + mt.mu * (C[0] - 1.0), h + mt.mu * (C[1] - 1.0), h + mt.mu * (C[2] - 1.0),
+                 mt.mu * C[3], mt.mu * C[4], mt.mu * C[5]};
+  const double w = mt.average_degraded ? m.chi[t] : 1.0;
+  double2* si = reinterpret_cast<double2*>(m.sig_in + 6 * t);
+  si[0] = make_double2(w * S[0], w * S[1]);
+  si[1] = make_double2(w * S[2], w * S[3]);
+  si[2] = make_double2(w * S[4], w * S[5]);
+  double sf[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sf[k] = normal_stress(e[k], s[k], S, mt.kappa);
+  double2* so = reinterpret_cast<double2*>(m.sigf + 6 * t);
+  so[0] = make_double2(sf[0], sf[1]);
+  so[1] = make_double2(sf[2], sf[3]);
+  so[2] = make_double2(sf[4], sf[5]);
+}
+
+// Eq. 20 sum: thread per tet, neighbour lists in SELL-32 layout (coalesced
+// index/weight loads; the neighbour stresses are gathered from L2).
+__global__ void __launch_bounds__(kThreads) k_nonlocal(DevMesh m) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
+  const int64_t g = t >> 5;
+  const int lane = int(t & 31);
+  const int64_t off = m.nb_off[g] + lane;
+  const int len = m.nb_len[g];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < len; ++k) {
+    const int j = __ldg(m.nb_idx + off + 32 * int64_t(k));
+    const double w = __ldg(m.nb_w + off + 32 * int64_t(k));
+    const double2* sj = reinterpret_cast<const double2*>(m.sig_in + 6 * int64_t(j));
+    const double2 a = sj[0], b = sj[1], c = sj[2];
+    acc[0] += w * a.x;
+    acc[1] += w * a.y;
+    acc[2] += w * b.x;
+    acc[3] += w * b.y;
+    acc[4] += w * c.x;
+    acc[5] += w * c.y;
+  }
+  double2* o = reinterpret_cast<double2*>(m.sig_bar + 6 * t);
+  o[0] = make_double2(acc[0], acc[1]);
+  o[1] = make_double2(acc[2], acc[3]);
+  o[2] = make_double2(acc[4], acc[5]);
+}
+
+// Per edge: sigma* = max over incident tets of the projected average (Eq. 20),
+// driver = sigma*/E (or sigma*), then zeta |= (driver >= threshold) (Eq. 21).
+__global__ void __launch_bounds__(kThreads) k_edge_driver(DevMesh m, Material mt) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  unsigned long long nb = 0, nn = 0;
+  if (i < m.NE) {
+    const int2 ab = m.edges[i];
+    double pa[3], pb[3];
+    ld3(m.x, ab.x, pa);
+    ld3(m.x, ab.y, pb);
+    const double e[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+    const double s = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    double mx = -INFINITY;
+    for (int p = m.et_ptr[i]; p < m.et_ptr[i + 1]; ++p) {
+      const double2* sb = reinterpret_cast<const double2*>(m.sig_bar + 6 * int64_t(m.et_tet[p]));
+      const double2 a = sb[0], b = sb[1], c = sb[2];
+      const double S[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
+      mx = fmax(mx, normal_stress(e, s, S, mt.kappa));
+    }
+    const double d = mt.driver_stress ? mx : mx / mt.young;
+    m.driver[i] = d;
+    const uint8_t old = m.labels[i];
+    const uint8_t now = (old || d >= mt.threshold) ? 1 : 0;
+    if (now != old) m.labels[i] = now;
+    nb = now;
+    nn = now && !old;
+  }
+  warp_count(nb, m.counters + kCntBroken);
+  warp_count(nn, m.counters + kCntNewBroken);
+}
+
+// Eq. 22-25: chi from the tet's broken-edge mask and its local edge stresses.
+__global__ void __launch_bounds__(kThreads) k_tet_chi(DevMesh m, Material mt, uint64_t lut) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  unsigned long long zero = 0;
+  if (t < m.T) {
+    int mask = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mask |= int(m.labels[m.tet_edges[6 * t + k]] != 0) << k;
+    double c = 1.0;
+    if (mask) {
+      if ((lut >> mask) & 1ull) {
+        c = 0.0;
+      } else {
+        double num = 0.0, den = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const double a = fabs(m.sigf[6 * t + k]);
+          den += a;
+          if (!((mask >> k) & 1)) num += a;
+        }
+        c = (den <= 1e-12 * mt.young) ? double(6 - __popc(mask)) / 6.0 : num / den;
+      }
+    }
+    m.chi[t] = c;
+    zero = (c == 0.0);
+  }
+  warp_count(zero, m.counters + kCntChiZero);
+}
+
+// ---------------------------------------------------------------------------
+// Assembly of A = (1 + dt alpha) M + (dt beta + dt^2) K*, b = dt (f_ext + f* - alpha M v - (beta + dt) K* v)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) k_node_init(DevMesh m, double dt, double alpha, const double* f_ext) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= m.N) return;
+  const double mi = m.mass[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    m.rhs[3 * i + c] = dt * ((f_ext ? f_ext[3 * i + c] : 0.0) - alpha * mi * m.v[3 * i + c]);
+  double* d = m.val + 9 * int64_t(m.diag_blk[i]);
+  const double cm = (1.0 + dt * alpha) * mi;
+  d[0] += cm;
+  d[4] += cm;
+  d[8] += cm;
+}
+
+// One colour: no two tets share a node, so the read-modify-write scatter into
+// the block-CSR slots and into b is conflict-free without atomics.
+__global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double beta, int t0, int t1) {
+  const int64_t t = t0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= t1) return;
+  const double chi = m.chi[t];
+  if (chi == 0.0) return;   // chi = 0: the element carries no energy (Eq. 25)
+  const int4 n = m.tets[t];
+  const int nid[4] = {n.x, n.y, n.z, n.w};
+  // incident local edges of each node and the sign of ds_k/dx_a = 2 sgn e_k
+  const int inc[4][3] = {{0, 1, 2}, {0, 3, 4}, {1, 3, 5}, {2, 4, 5}};
+  const double sgn[4][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {1, 1, 1}};
+  const int kab[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
+
+  double P[4][3], U[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ld3(m.x, nid[a], P[a]);
+    ld3(m.v, nid[a], U[a]);
+  }
+  double e[6][3], ds[6], Dv[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double du[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      e[k][c] = P[edge_b(k)][c] - P[edge_a(k)][c];
+      du[c] = U[edge_b(k)][c] - U[edge_a(k)][c];
+    }
+    ds[k] = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2] - m.rest[(kRestS0 + k) * m.T + t];
+    Dv[k] = 2.0 * (e[k][0] * du[0] + e[k][1] * du[1] + e[k][2] * du[2]);
+  }
+  double H[21];
+#pragma unroll
+  for (int f = 0; f < 21; ++f) H[f] = m.rest[(kRestH + f) * m.T + t];
+  auto h = [&](int k, int l) { return k <= l ? H[tri6(k, l)] : H[tri6(l, k)]; };
+  // g = dV Psi/ds = Hs (s - s0);  w = Hs (ds/dx . v)
+  double g[6], w[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double gk = 0.0, wk = 0.0;
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      gk += h(k, l) * ds[l];
+      wk += h(k, l) * Dv[l];
+    }
+    g[k] = gk;
+    w[k] = wk;
+  }
+  // right-hand side: per edge k (a->b), t_k = 2 dt chi [e_k (g_k + c w_k) + c g_k (v_b - v_a)], c = beta + dt
+  {
+    const double cv = beta + dt, sc = 2.0 * dt * chi;
+    double f[4][3] = {};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double a1 = sc * (g[k] + cv * w[k]), a2 = sc * cv * g[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double tk = a1 * e[k][c] + a2 * (U[edge_b(k)][c] - U[edge_a(k)][c]);
+        f[edge_a(k)][c] += tk;
+        f[edge_b(k)][c] -= tk;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m.rhs[3 * int64_t(nid[a]) + c] += f[a][c];
+  }
+  // tangent blocks: (a,b) = 4 sK sum_{k in a, l in b} sgn sgn H_kl e_k e_l^T + geometric part
+  const double sK = (dt * beta + dt * dt) * chi;
+  const int* sl = m.slot + 16 * t;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    double Y[6][3];   // Y[k][c] = 4 sK sum_j H(k, l_j) sgn_bj e_{l_j}[c]
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double y = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y += sgn[b][j] * h(k, inc[b][j]) * e[inc[b][j]][c];
+        Y[k][c] = 4.0 * sK * y;
+      }
+#pragma unroll
+    for (int a = 0; a <= b; ++a) {
+      double blk[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double v = 0.0;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) v += sgn[a][i] * e[inc[a][i]][r] * Y[inc[a][i]][c];
+          blk[r][c] = v;
+        }
+      double geo;
+      if (a == b) {
+        geo = 2.0 * sK * (g[inc[a][0]] + g[inc[a][1]] + g[inc[a][2]]);
+      } else {
+        geo = -2.0 * sK * g[kab[a][b]];
+      }
+      blk[0][0] += geo;
+      blk[1][1] += geo;
+      blk[2][2] += geo;
+      double* dst = m.val + 9 * int64_t(sl[4 * a + b]);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[3 * r + c] += blk[r][c];
+      if (a != b) {
+        double* dt2 = m.val + 9 * int64_t(sl[4 * b + a]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) dt2[3 * r + c] += blk[c][r];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Projected block-Jacobi PCG (Sec. 4.3), all scalars on the device
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void spmv_row(const DevMesh& m, int64_t i, const double* __restrict__ x, double y[3]) {
+  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+  const int b1 = m.row_ptr[i + 1];
+  for (int b = m.row_ptr[i]; b < b1; ++b) {
+    const int64_t j = m.col[b];
+    const double* a = m.val + 9 * int64_t(b);
+    const double x0 = x[3 * j], x1 = x[3 * j + 1], x2 = x[3 * j + 2];
+    y0 += a[0] * x0 + a[1] * x1 + a[2] * x2;
+    y1 += a[3] * x0 + a[4] * x1 + a[5] * x2;
+    y2 += a[6] * x0 + a[7] * x1 + a[8] * x2;
+  }
+  y[0] = y0;
+  y[1] = y1;
+  y[2] = y2;
+}
+
+__global__ void __launch_bounds__(kThreads) k_set_pinned(DevMesh m, int64_t n_pinned, const double* pin_vel) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p >= n_pinned) return;
+  const int64_t id = m.pin_ids[p];
+  if (id < 0 || id >= m.N) {
+    atomicAdd(m.counters + 3, 1ull);   // reported as GF_BAD_ARG after the step
+    return;
+  }
+  m.pinned[id] = 1;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) m.dv[3 * id + c] = (pin_vel ? pin_vel[3 * p + c] : 0.0) - m.v[3 * id + c];
+}
+
+// r = b - A dv on free nodes, block-Jacobi inverse, z = P r, p = z; rz, rr.
+__global__ void __launch_bounds__(kThreads) k_pcg_init(DevMesh m) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
+    if (!m.pinned[i]) {
+      double ad[3];
+      spmv_row(m, i, m.dv, ad);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[c] = m.rhs[3 * i + c] - ad[c];
+      const double* a = m.val + 9 * int64_t(m.diag_blk[i]);
+      const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[2] * a[7] - a[1] * a[8], c02 = a[1] * a[5] - a[2] * a[4];
+      const double c10 = a[5] * a[6] - a[3] * a[8], c11 = a[0] * a[8] - a[2] * a[6], c12 = a[2] * a[3] - a[0] * a[5];
+      const double c20 = a[3] * a[7] - a[4] * a[6], c21 = a[1] * a[6] - a[0] * a[7], c22 = a[0] * a[4] - a[1] * a[3];
+      const double id = 1.0 / (a[0] * c00 + a[1] * c10 + a[2] * c20);
+      double* pi = m.pinv + 9 * i;
+      const double inv[9] = {c00 * id, c01 * id, c02 * id, c10 * id, c11 * id, c12 * id, c20 * id, c21 * id, c22 * id};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) pi[k] = inv[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) z[c] = inv[3 * c] * r[0] + inv[3 * c + 1] * r[1] + inv[3 * c + 2] * r[2];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.r[3 * i + c] = r[c];
+      m.z[3 * i + c] = z[c];
+      m.p[3 * i + c] = z[c];
+      v[0] += r[c] * z[c];
+      v[1] += r[c] * r[c];
+    }
+  }
+  double out[2];
+  if (grid_reduce<2>(v, m.partials, m.tickets + 0, out) && threadIdx.x == 0) {
+    PcgState* s = m.pcg;
+    s->rz = out[0];
+    s->rr = out[1];
+    s->bb = out[1];
+    s->iters = 0;
+    s->status = GF_OK;
+    s->done = (out[1] == 0.0 || out[1] <= s->tol2 * out[1]) ? 1 : 0;
+    if (!isfinite(out[1])) {
+      s->status = GF_NAN;
+      s->done = 1;
+    }
+  }
+}
+
+// q = A p; pq = p . q; alpha = rz / pq (breakdown when pq <= 0)
+__global__ void __launch_bounds__(kThreads) k_pcg_spmv(DevMesh m) {
+  if (m.pcg->done) return;
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double y[3];
+    spmv_row(m, i, m.p, y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.q[3 * i + c] = y[c];
+      v[0] += m.p[3 * i + c] * y[c];
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(v, m.partials, m.tickets + 1, out) && threadIdx.x == 0) {
+    PcgState* s = m.pcg;
+    s->pq = out[0];
+    if (!(out[0] > 0.0)) {
+      s->status = isfinite(out[0]) ? GF_CG_BREAKDOWN : GF_NAN;
+      s->done = 1;
+    } else {
+      s->alpha = s->rz / out[0];
+    }
+  }
+}
+
+// dv += alpha p; r -= alpha q; z = P r; rz_new, rr; convergence test
+__global__ void __launch_bounds__(kThreads) k_pcg_update(DevMesh m) {
+  if (m.pcg->done) return;
+  const double alpha = m.pcg->alpha;
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    if (m.pinned[i]) continue;
+    double r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.dv[3 * i + c] += alpha * m.p[3 * i + c];
+      r[c] = m.r[3 * i + c] - alpha * m.q[3 * i + c];
+      m.r[3 * i + c] = r[c];
+    }
+    const double* pi = m.pinv + 9 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
+      m.z[3 * i + c] = z;
+      v[0] += r[c] * z;
+      v[1] += r[c] * r[c];
+    }
+  }
+  double out[2];
+  if (grid_reduce<2>(v, m.partials, m.tickets + 2, out) && threadIdx.x == 0) {
+    PcgState* s = m.pcg;
+    s->iters += 1;
+    s->beta = out[0] / s->rz;
+    s->rz = out[0];
+    s->rr = out[1];
+    if (!isfinite(out[1])) {
+      s->status = GF_NAN;
+      s->done = 1;
+    } else if (out[1] <= s->tol2 * s->bb) {
+      s->done = 1;
+    } else if (s->iters >= s->maxit) {
+      s->status = GF_CG_MAXITER;
+      s->done = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pcg_p(DevMesh m) {
+  if (m.pcg->done) return;
+  const double beta = m.pcg->beta;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(gridDim.x) * blockDim.x)
+    m.p[i] = m.z[i] + beta * m.p[i];
+}
+
+// ||b - A dv||^2 over free nodes, recomputed from scratch after the solve.
+__global__ void __launch_bounds__(kThreads) k_true_residual(DevMesh m) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    if (m.pinned[i]) continue;
+    double y[3];
+    spmv_row(m, i, m.dv, y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double r = m.rhs[3 * i + c] - y[c];
+      v[0] += r * r;
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(v, m.partials, m.tickets + 3, out) && threadIdx.x == 0) m.pcg->true_rr = out[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_integrate(DevMesh m, double dt) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= 3 * m.N) return;
+  const double v = m.v[i] + m.dv[i];
+  m.v[i] = v;
+  m.x[i] += dt * v;
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
+inline unsigned reduce_grid(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  return unsigned(b < 1 ? 1 : (b > kMaxPartials ? kMaxPartials : b));
+}
+
+}  // namespace
+
+int launch_tet_stress(const DevMesh& m, const Material& mt, cudaStream_t s) {
+  k_tet_stress<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, mt);
+  return 1;
+}
+int launch_nonlocal(const DevMesh& m, cudaStream_t s) {
+  k_nonlocal<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_edge_driver(const DevMesh& m, const Material& mt, cudaStream_t s) {
+  k_edge_driver<<<blocks_for(m.NE, kThreads), kThreads, 0, s>>>(m, mt);
+  return 1;
+}
+int launch_tet_chi(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s) {
+  k_tet_chi<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, mt, lut);
+  return 1;
+}
+int launch_node_init(const DevMesh& m, double dt, const Material& mt, bool has_fext, cudaStream_t s) {
+  k_node_init<<<blocks_for(m.N, kThreads), kThreads, 0, s>>>(m, dt, mt.alpha, has_fext ? m.f_ext : nullptr);
+  return 1;
+}
+int launch_assemble(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s) {
+  if (t1 <= t0) return 0;
+  k_assemble<<<blocks_for(t1 - t0, 128), 128, 0, s>>>(m, dt, mt.beta, t0, t1);
+  return 1;
+}
+int launch_set_pinned(const DevMesh& m, int64_t n_pinned, bool has_vel, cudaStream_t s) {
+  if (n_pinned <= 0) return 0;
+  k_set_pinned<<<blocks_for(n_pinned, kThreads), kThreads, 0, s>>>(m, n_pinned, has_vel ? m.pin_vel : nullptr);
+  return 1;
+}
+int launch_pcg_init(const DevMesh& m, cudaStream_t s) {
+  k_pcg_init<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_pcg_iter(const DevMesh& m, cudaStream_t s, int which) {
+  if (which == 0) k_pcg_spmv<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
+  else if (which == 1) k_pcg_update<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
+  else k_pcg_p<<<reduce_grid(3 * m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_true_residual(const DevMesh& m, cudaStream_t s) {
+  k_true_residual<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_integrate(const DevMesh& m, double dt, cudaStream_t s) {
+  k_integrate<<<blocks_for(3 * m.N, kThreads), kThreads, 0, s>>>(m, dt);
+  return 1;
+}
+
+}  // namespace gf

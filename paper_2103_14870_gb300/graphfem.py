@@ -1,0 +1,333 @@
+"""Thin Python binding of the graph-FEM fracture C ABI (include/graphfem.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Host arrays (numpy, or CPU torch tensors) are passed as GF_MEM_HOST; CUDA
+torch tensors as GF_MEM_DEVICE.  By default the library allocates through
+torch's caching allocator and runs on torch's current stream, so torch is the
+device-memory and stream plumbing.  There is no CPU fallback: without the
+built library or a CUDA device, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MEM_HOST, MEM_DEVICE = 0, 1
+DRIVER_STRAIN, DRIVER_STRESS = 0, 1
+FP64, MIXED = 0, 1
+
+STATUS = {0: "ok", 1: "bad argument", 2: "CUDA error", 3: "CG breakdown", 4: "CG max iterations", 5: "non-finite",
+          6: "timeout", 7: "out of memory", 8: "unsupported"}
+
+
+class GraphFEMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("young", ctypes.c_double), ("poisson", ctypes.c_double), ("density", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("threshold", ctypes.c_double),
+                ("radius", ctypes.c_double), ("driver_mode", ctypes.c_int32), ("shear_coef", ctypes.c_int32),
+                ("average_degraded", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("cg_maxit", ctypes.c_int32), ("cg_rtol", ctypes.c_double),
+                ("precond", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cg_iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("n_broken", ctypes.c_int64), ("n_new_broken", ctypes.c_int64), ("n_chi_zero", ctypes.c_int64),
+                ("refine_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("n_nodes", "n_tets", "n_edges", "n_blocks", "n_colours",
+                                              "n_nbr_pairs", "device_bytes")]
+
+
+_LIB = None
+P = ctypes.c_void_p
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load the built shared library (building it first if the sources are newer)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    sig = {
+        "gf_mesh_create": (ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.POINTER(Material),
+                                          ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "gf_mesh_destroy": (None, [P]),
+        "gf_mesh_plan": (ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.POINTER(Material),
+                                        ctypes.POINTER(MeshInfo), P, P, P]),
+        "gf_mesh_info_get": (ctypes.c_int, [P, ctypes.POINTER(MeshInfo)]),
+        "gf_state_set": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int32]),
+        "gf_step": (ctypes.c_int, [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int32,
+                                   ctypes.POINTER(StepStats)]),
+        "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
+        "gf_positions_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
+        "gf_velocities_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
+        "gf_damage_get": (ctypes.c_int, [P, P, P, ctypes.c_int32]),
+        "gf_chi_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
+        "gf_edges_get": (ctypes.c_int, [P, P]),
+        "gf_system_get": (ctypes.c_int, [P, P, P, P, P]),
+        "gf_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
+        "gf_profile_get": (ctypes.c_int32, [P, P, P, ctypes.c_int32]),
+        "gf_profile_name": (ctypes.c_char_p, [ctypes.c_int32]),
+        "gf_profile_reset": (ctypes.c_int, [P]),
+        "gf_launch_count": (ctypes.c_int64, [P]),
+        "gf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "gf_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise GraphFEMError(status, load_library().gf_last_error().decode())
+
+
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _arg(a, dtype, count: int, name: str):
+    """(pointer, mem kind, keep-alive object) for an array argument."""
+    if a is None:
+        return None, None, None
+    if type(a).__module__.startswith("torch"):
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"{name}: expected a contiguous {tdt} tensor")
+        if a.numel() != count:
+            raise ValueError(f"{name}: expected {count} elements, got {a.numel()}")
+        return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.size != count:
+        raise ValueError(f"{name}: expected {count} elements, got {arr.size}")
+    return arr.ctypes.data, MEM_HOST, arr
+
+
+def _one_kind(*kinds) -> int:
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ks.pop() if ks else MEM_HOST
+
+
+def material(young, poisson, density, threshold=math.inf, radius=0.0, alpha=0.0, beta=0.0,
+             driver_mode=DRIVER_STRAIN, shear_coef=2, average_degraded=True) -> Material:
+    return Material(young, poisson, density, alpha, beta, threshold, radius, driver_mode, shear_coef,
+                    1 if average_degraded else 0, 0)
+
+
+class Mesh:
+    """One mesh on one GPU (opaque gf_mesh handle)."""
+
+    def __init__(self, handle, n_nodes, n_tets, n_edges, keep):
+        self._h = handle
+        self.n_nodes, self.n_tets, self.n_edges = n_nodes, n_tets, n_edges
+        self._keep = keep
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if self._h:
+            load_library().gf_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def info(self) -> dict:
+        inf = MeshInfo()
+        _check(load_library().gf_mesh_info_get(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in MeshInfo._fields_}
+
+    # -- state ------------------------------------------------------------
+    def state_set(self, x=None, v=None, labels=None, chi=None):
+        px, kx, kx_ = _arg(x, np.float64, 3 * self.n_nodes, "x")
+        pv, kv, kv_ = _arg(v, np.float64, 3 * self.n_nodes, "v")
+        pl, kl, kl_ = _arg(labels, np.uint8, self.n_edges, "labels")
+        pc, kc, kc_ = _arg(chi, np.float64, self.n_tets, "chi")
+        _check(load_library().gf_state_set(self._h, px, pv, pl, pc, _one_kind(kx, kv, kl, kc)))
+
+    def step(self, dt: float, f_ext=None, pinned=None, pinned_vel=None) -> dict:
+        pf, kf, kf_ = _arg(f_ext, np.float64, 3 * self.n_nodes, "f_ext")
+        n_pin = 0 if pinned is None else int(np.prod(pinned.shape)) if hasattr(pinned, "shape") else len(pinned)
+        pp, kp, kp_ = _arg(pinned, np.int32, n_pin, "pinned") if n_pin else (None, None, None)
+        pq, kq, kq_ = _arg(pinned_vel, np.float64, 3 * n_pin, "pinned_vel") if n_pin else (None, None, None)
+        st = StepStats()
+        status = load_library().gf_step(self._h, float(dt), pf, pp, n_pin, pq, _one_kind(kf, kp, kq),
+                                         ctypes.byref(st))
+        _check(status)
+        return st.as_dict()
+
+    def solver_set(self, rtol: float, maxit: int = 10000):
+        _check(load_library().gf_solver_set(self._h, float(rtol), int(maxit)))
+
+    # -- getters ----------------------------------------------------------
+    def _get(self, fn, n, dtype, out):
+        if out is None:
+            out = np.empty(n, dtype)
+        p, k, keep = _arg(out, dtype, n, "out")
+        if isinstance(out, np.ndarray) and p != out.ctypes.data:
+            raise ValueError("out must be a contiguous array of the right dtype")
+        _check(fn(self._h, p, k))
+        return out
+
+    def positions_get(self, out=None):
+        return self._get(load_library().gf_positions_get, 3 * self.n_nodes, np.float64, out)
+
+    def velocities_get(self, out=None):
+        return self._get(load_library().gf_velocities_get, 3 * self.n_nodes, np.float64, out)
+
+    def chi_get(self, out=None):
+        return self._get(load_library().gf_chi_get, self.n_tets, np.float64, out)
+
+    def damage_get(self):
+        drv = np.empty(self.n_edges, np.float64)
+        lab = np.empty(self.n_edges, np.uint8)
+        _check(load_library().gf_damage_get(self._h, drv.ctypes.data, lab.ctypes.data, MEM_HOST))
+        return drv, lab
+
+    def edges_get(self):
+        e = np.empty((self.n_edges, 2), np.int32)
+        _check(load_library().gf_edges_get(self._h, e.ctypes.data))
+        return e
+
+    def system_get(self):
+        nb = self.info["n_blocks"]
+        rp = np.empty(self.n_nodes + 1, np.int32)
+        col = np.empty(nb, np.int32)
+        val = np.empty((nb, 3, 3), np.float64)
+        rhs = np.empty(3 * self.n_nodes, np.float64)
+        _check(load_library().gf_system_get(self._h, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                            rhs.ctypes.data))
+        return rp, col, val, rhs
+
+    # -- profiling --------------------------------------------------------
+    def profile_enable(self, on: bool = True):
+        _check(load_library().gf_profile_enable(self._h, 1 if on else 0))
+
+    def profile_reset(self):
+        _check(load_library().gf_profile_reset(self._h))
+
+    def profile_get(self) -> dict:
+        lib = load_library()
+        n = 32
+        ms = np.zeros(n)
+        cnt = np.zeros(n, np.int64)
+        k = lib.gf_profile_get(self._h, ms.ctypes.data, cnt.ctypes.data, n)
+        return {lib.gf_profile_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
+
+    def launch_count(self) -> int:
+        return int(load_library().gf_launch_count(self._h))
+
+
+def mesh_plan(nodes, tets, mat: Material) -> dict:
+    """gf_mesh_plan: the host precompute alone (no GPU needed)."""
+    lib = load_library()
+    nodes = np.ascontiguousarray(nodes, np.float64).reshape(-1, 3)
+    tets = np.ascontiguousarray(tets, np.int32).reshape(-1, 4)
+    inf = MeshInfo()
+    colour = np.empty(tets.shape[0], np.int32)
+    cnt = np.empty(tets.shape[0], np.int32)
+    _check(lib.gf_mesh_plan(nodes.ctypes.data, nodes.shape[0], tets.ctypes.data, tets.shape[0],
+                            ctypes.byref(mat), ctypes.byref(inf), None, colour.ctypes.data, cnt.ctypes.data))
+    edges = np.empty((inf.n_edges, 2), np.int32)
+    _check(lib.gf_mesh_plan(nodes.ctypes.data, nodes.shape[0], tets.ctypes.data, tets.shape[0],
+                            ctypes.byref(mat), ctypes.byref(inf), edges.ctypes.data, None, None))
+    out = {f: getattr(inf, f) for f, _ in MeshInfo._fields_}
+    out.update(edges=edges, colour=colour, nbr_count=cnt)
+    return out
+
+
+def _torch_plumbing(device: int, stream):
+    """Allocator callbacks over torch's caching allocator and the stream to use."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free), sptr
+
+
+def mesh_create(nodes, tets, mat: Material, precision: int = FP64, cg_rtol: float = 1e-6, cg_maxit: int = 10000,
+                device: Optional[int] = None, stream=None, torch_allocator: bool = True) -> Mesh:
+    """gf_mesh_create: nodes (n,3) float64 host, tets (t,4) int32 host."""
+    lib = load_library()
+    nodes = np.ascontiguousarray(nodes, np.float64).reshape(-1, 3)
+    tets = np.ascontiguousarray(tets, np.int32).reshape(-1, 4)
+    opt = Options()
+    opt.precision = precision
+    opt.cg_maxit = cg_maxit
+    opt.cg_rtol = cg_rtol
+    opt.precond = 0
+    keep = []
+    try:
+        import torch
+        have_torch = torch.cuda.is_available()
+    except Exception:
+        have_torch = False
+    if device is None:
+        device = torch.cuda.current_device() if have_torch else -1
+    opt.device = device
+    if have_torch and torch_allocator:
+        a, f, sptr = _torch_plumbing(device, stream)
+        opt.alloc, opt.free, opt.stream = a, f, sptr
+        keep += [a, f]
+    elif stream is not None:
+        opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    h = P()
+    _check(lib.gf_mesh_create(nodes.ctypes.data, nodes.shape[0], tets.ctypes.data, tets.shape[0],
+                              ctypes.byref(mat), ctypes.byref(opt), ctypes.byref(h)))
+    inf = MeshInfo()
+    _check(lib.gf_mesh_info_get(h, ctypes.byref(inf)))
+    return Mesh(h, inf.n_nodes, inf.n_tets, inf.n_edges, keep)

@@ -8,5 +8,5 @@ computation they are compared on.
 """
 from .meshes import (  # noqa: F401
     kuhn_box, bcc_ellipsoid, jitter, beam_config, loaf_config, glass_config,
-    batch_configs, two_tet_fig4, single_tet, Workload,
+    batch_configs, two_tet_fig4, single_tet, Workload, LOAF_AXES,
 )
