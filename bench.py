@@ -53,7 +53,7 @@ class ClockSampler:
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                                       "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
@@ -246,17 +246,37 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_profile_step(args) -> None:
+    """Minimal command for ncu captures: build the loaf mesh, run `--steps` steps, no timing."""
+    import torch
+    import paper_2103_14870_gb300 as gf
+    from workloads import loaf_config
+    torch.cuda.set_device(0)
+    w = loaf_config()
+    m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=w.threshold,
+                                                    radius=w.radius), cg_rtol=w.cg_rtol)
+    f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
+    for _ in range(args.steps):
+        s = m.step(w.dt, f_dev)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_step": True, "steps": args.steps, "last": s, "launches": m.launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
     args = ap.parse_args()
     if args.cpu_sample_child:
         cpu_sample_child(args.cpu_sample_child)
+        return
+    if args.profile_step:
+        run_profile_step(args)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

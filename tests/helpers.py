@@ -44,12 +44,13 @@ def deformed_state(w, seed=0, amp=0.05, vamp=0.2) -> State:
     return State(X + u, v, np.zeros(ne, np.uint8), np.ones(w.n_tets))
 
 
-def assert_close(got, want, rtol=RTOL64, floor=1e-12, what=""):
+def assert_close(got, want, rtol=RTOL64, floor=1e-12, what="", abs_floor=0.0):
+    """|got - want| <= rtol |want| + floor * max|want| + abs_floor, element-wise."""
     got = np.asarray(got, np.float64)
     want = np.asarray(want, np.float64)
     scale = max(np.abs(want).max(), 1e-300)
     err = np.abs(got - want)
-    bad = err > rtol * np.abs(want) + floor * scale
+    bad = err > rtol * np.abs(want) + floor * scale + abs_floor
     assert not bad.any(), (f"{what}: {bad.sum()} of {bad.size} entries differ; worst abs {err.max():.3e} "
                            f"(scale {scale:.3e}) at {np.argmax(err)}")
 
@@ -79,3 +80,21 @@ def block_values_from_csr(A, row_ptr, col):
         for b in range(3):
             out[:, a, b] = np.asarray(A[3 * rows + a, 3 * col + b]).ravel()
     return out
+
+
+def assert_positions_close(got, want, start, rtol=RTOL64, ulps=4.0, what="x", noise=1e-10):
+    """Positions after a step: |got - want| <= rtol |dx| + noise max|dx| + ulps eps |want|.
+    The ulp term covers the rounding of x + dt v itself (x ~ 10 m, dx ~ 1e-6 m); the
+    noise term covers nodes the load has not reached yet, whose displacement (1e-17 m
+    after one step) is the rounding noise of the rest-state forces on either side."""
+    got = np.asarray(got, np.float64).ravel()
+    want = np.asarray(want, np.float64).ravel()
+    start = np.asarray(start, np.float64).ravel()
+    err = np.abs(got - want)
+    dx = np.abs(want - start)
+    bound = rtol * dx + noise * dx.max() + ulps * np.finfo(np.float64).eps * np.abs(want)
+    bad = err > bound
+    idx = np.nonzero(bad)[0][:6]
+    assert not bad.any(), (f"{what}: {bad.sum()} entries beyond rtol*|dx| + {ulps} ulp; worst {err.max():.3e}; "
+                           f"first: idx {idx.tolist()} got {got[idx].tolist()} want {want[idx].tolist()} "
+                           f"start {start[idx].tolist()}")

@@ -1,0 +1,154 @@
+"""Full-size parity on the 620k-tet loaf, in the configuration bench.py times
+(FP64, CG to 1e-6).  The oracle cannot step the whole mesh in seconds, so it
+recomputes sampled outputs one by one: four compact regions of tets, whose
+edge drivers and labels (Eq. 20-21), chi (Eq. 25), and the matrix rows and
+right-hand sides of their interior nodes (Eq. 2, 12, 32-34) it evaluates from
+the same start state.  Properties that hold at any size are checked on the
+whole mesh: the solver residual recomputed on the host from the GPU's own
+system, the position update, and monotone labels."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from helpers import LABEL_BAND, assert_close
+from oracle import damage, elastic, mesh as omesh
+from workloads import loaf_config
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2103_14870_gb300 as gf  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def loaf():
+    w = loaf_config()
+    rng = np.random.default_rng(21)
+    X = w.nodes
+    L = X.max(0) - X.min(0)
+    u = np.zeros_like(X)
+    ph = rng.uniform(0, 2 * np.pi, size=(3, 3))
+    for c in range(3):
+        for d in range(3):
+            u[:, c] += 0.004 * L[d] / 6 * np.sin(2 * np.pi * X[:, d] / L[d] + ph[c, d])
+    x = X + u + 1e-4 * rng.normal(size=X.shape)
+    v = 0.01 * rng.normal(size=X.shape)
+    edges, tet_edges = omesh.edges_of(w.tets)
+    labels0 = (rng.uniform(size=len(edges)) < 0.003).astype(np.uint8)
+    return w, x, v, edges, tet_edges, labels0
+
+
+def oracle_region_state(w, x, labels, edges, tet_edges, centres, lam, mu, radius):
+    """Oracle quantities around the sample regions (global tet / edge ids)."""
+    X, tets = w.nodes, w.tets.astype(np.int64)
+    cen = omesh.centroids(X, tets)
+    V_all, _, _ = omesh.rest_geometry(X, tets)
+    d_reg = np.min(np.linalg.norm(cen[:, None, :] - centres[None], axis=2), axis=1)
+    T_s = np.nonzero(d_reg <= 2.5)[0]                                  # sampled tets
+    E_s = np.unique(tet_edges[T_s])                                    # their edges
+    # tets incident to the sampled edges (their sigma-bar enters the edge driver)
+    inc = np.nonzero(np.isin(tet_edges, E_s).any(1))[0]
+    # stresses and chi_old are needed for every neighbour of those tets
+    need = np.nonzero(d_reg <= 2.5 + 2.0 + radius)[0]
+    V, D2, q = omesh.rest_geometry(X, tets[need])
+    s = elastic.squared_edge_lengths(x, tets[need])
+    C = elastic.cauchy_green_lsq(s, D2, q)
+    S = damage.stress_voigt(C, lam, mu)
+    T = damage.projection_T(x, tets[need], 2.0)
+    sigf = np.einsum("tkc,tc->tk", T, S)
+    chi_old = damage.chi(labels, tet_edges[need], sigf, w.young)
+    sig_in = np.full((len(tets), 6), np.nan)
+    sig_in[need] = S * chi_old[:, None]
+    nb = omesh.nonlocal_neighbours(X, tets, radius, subset=inc)
+    wts = damage.nonlocal_weights(cen, V_all, nb, radius, subset=inc)
+    sig_bar = damage.nonlocal_average(sig_in, nb, wts)
+    assert np.isfinite(sig_bar).all()
+    T_inc = damage.projection_T(x, tets[inc], 2.0)
+    sig_star = np.einsum("tkc,tc->tk", T_inc, sig_bar)
+    drv = np.full(len(edges), -np.inf)
+    np.maximum.at(drv, tet_edges[inc].ravel(), sig_star.ravel())
+    drv /= w.young
+    pos = {t: i for i, t in enumerate(need)}
+    return dict(T_s=T_s, E_s=E_s, driver=drv, need=need, pos=pos, sigf=sigf)
+
+
+def test_loaf_fullsize_sampled_parity(loaf):
+    w, x, v, edges, tet_edges, labels0 = loaf
+    lam, mu = elastic.lame(w.young, w.poisson)
+    rng = np.random.default_rng(7)
+    centres = w.nodes[rng.choice(w.n_nodes, 4, replace=False)]
+    reg = oracle_region_state(w, x, labels0, edges, tet_edges, centres, lam, mu, w.radius)
+    E_s, T_s = reg["E_s"], reg["T_s"]
+    theta = float(np.quantile(reg["driver"][E_s], 0.9))
+    m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=theta,
+                                                    radius=w.radius), cg_rtol=1e-6)
+    np.testing.assert_array_equal(m.edges_get(), edges)
+    m.state_set(x=x.ravel(), v=v.ravel(), labels=labels0)
+    f = w.f_ext
+    stats = m.step(w.dt, f.ravel())
+    drv, lab = m.damage_get()
+    # (1) drivers and labels of the sampled edges
+    assert_close(drv[E_s], reg["driver"][E_s], floor=0.0, abs_floor=1e-13, what="driver")
+    want_lab = labels0 | (reg["driver"] >= theta)
+    diff = E_s[lab[E_s] != want_lab[E_s]]
+    assert np.all(np.abs(reg["driver"][diff] - theta) <= LABEL_BAND * theta)
+    assert lab[E_s].sum() > 0
+    # labels never heal anywhere
+    assert np.all(lab >= labels0)
+    # (2) chi of the sampled tets from the new labels of their edges
+    new_lab = labels0.copy()
+    new_lab[E_s] = want_lab[E_s]
+    sigf_s = reg["sigf"][[reg["pos"][t] for t in T_s]]
+    chi_s = damage.chi(new_lab, tet_edges[T_s], sigf_s, w.young)
+    chi_gpu = m.chi_get()
+    assert_close(chi_gpu[T_s], chi_s, floor=1e-12, what="chi")
+    assert (chi_s < 1).any()
+    # (3) matrix rows and rhs of nodes whose incident tets all lie in T_s
+    tets = w.tets.astype(np.int64)
+    in_s = np.zeros(w.n_tets, bool)
+    in_s[T_s] = True
+    node_all_in = np.ones(w.n_nodes, bool)
+    np.logical_and.at(node_all_in, tets.ravel(), np.repeat(in_s, 4))
+    N_s = np.nonzero(node_all_in & np.isin(np.arange(w.n_nodes), tets[T_s].ravel()))[0]
+    assert len(N_s) >= 4
+    V, D2, q = omesh.rest_geometry(w.nodes, tets[T_s])
+    Ke = elastic.element_tangent(x, tets[T_s], V, D2, q, lam, mu, chi_s)
+    fe = elastic.element_forces(x, tets[T_s], V, D2, q, lam, mu, chi_s)
+    mass = omesh.lumped_mass(w.nodes, tets, w.density, omesh.rest_geometry(w.nodes, tets)[0])
+    dt = w.dt
+    rp, col, val, rhs = m.system_get()
+    for n in N_s:
+        want_row = {}
+        want_b = dt * (f[n] - 0.0 * v[n])
+        for e_i, t in enumerate(T_s):
+            loc = np.nonzero(tets[t] == n)[0]
+            if not len(loc):
+                continue
+            a = loc[0]
+            ve = v[tets[t]].ravel()
+            Kv = Ke[e_i] @ ve
+            want_b = want_b + dt * (fe[e_i, a] - dt * Kv[3 * a:3 * a + 3])
+            for b in range(4):
+                blk = dt * dt * Ke[e_i][3 * a:3 * a + 3, 3 * b:3 * b + 3]
+                want_row[tets[t, b]] = want_row.get(tets[t, b], 0.0) + blk
+        want_row[n] = want_row[n] + mass[n] * np.eye(3)
+        cols = col[rp[n]:rp[n + 1]]
+        assert sorted(want_row) == list(cols)
+        got = val[rp[n]:rp[n + 1]]
+        want = np.stack([want_row[c] for c in cols])
+        assert_close(got, want, floor=1e-12, what=f"A row {n}")
+        assert_close(rhs[3 * n:3 * n + 3], want_b, floor=1e-9, what=f"rhs row {n}")
+    # (4) the solve: residual recomputed on the host from the GPU's own system
+    rows = np.repeat(np.arange(w.n_nodes), np.diff(rp))
+    r3 = (3 * rows[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
+    c3 = (3 * col[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
+    A = sp.csr_matrix((val.ravel(), (r3.ravel(), c3.ravel())), shape=(3 * w.n_nodes, 3 * w.n_nodes))
+    v_new = m.velocities_get()
+    dv = v_new - v.ravel()
+    res = np.linalg.norm(rhs - A @ dv) / np.linalg.norm(rhs)
+    assert res <= 1e-6
+    assert abs(res - stats["rel_res"]) <= 1e-3 * res + 1e-15
+    # (5) position update x_new = x + dt v_new
+    np.testing.assert_allclose(m.positions_get(), x.ravel() + dt * v_new, rtol=1e-15, atol=1e-15)
