@@ -191,6 +191,32 @@ gf_status gf_profile_reset(gf_mesh* mesh);
 /* Kernel launches this mesh has issued since creation (all entry points). */
 int64_t gf_launch_count(const gf_mesh* mesh);
 
+/* Allocation-free solve of a caller's block-CSR system A x = b by projected
+ * block-Jacobi PCG.  The paper has no counterpart of this entry point: it is
+ * for callers that cannot allocate device memory while they solve (cudaMalloc
+ * and cudaFree can synchronise the device and stall other streams; some host
+ * programs give all device memory to one pool up front).  It calls no
+ * allocator: its scratch is a fixed array of about 5.5 MB in the library's
+ * device memory, held by every GPU that loads the library until exit, which
+ * limits n_rows to 32768 block rows (98,304 unknowns); larger systems return
+ * GF_BAD_ARG.  All pointers are device memory of the current device:
+ * row_ptr int32 [n_rows+1], col int32 [row_ptr[n_rows]] (each in [0, n_rows),
+ * else GF_BAD_ARG), values float64 [9 * row_ptr[n_rows]] row-major 3x3 blocks of
+ * a symmetric positive definite matrix, b float64 [3 * n_rows], x float64
+ * [3 * n_rows] (in: prescribed values on fixed rows, free rows ignored and
+ * started from 0; out: the solution), fixed uint8 [n_rows] (1 = row held at
+ * x, NULL = none).  Stops when ||b - A x|| <= rtol ||b - A x_fixed|| on free
+ * rows.  stream: cudaStream_t (NULL = legacy default); returns after the
+ * solve completes.  iters and rel_res (host, may be NULL) receive the CG
+ * iterations and the final relative residual.  The scratch array is shared by
+ * all calls on a device and keeps the last call's contents (each call clears
+ * what must start at zero); calls whose work overlaps on the GPU race on it.
+ * The first call on a device looks up the array's device address, so that call
+ * should come before any stream capture. */
+gf_status gf_bsr_pcg_solve_static(const int32_t* row_ptr, const int32_t* col, const double* values, int64_t n_rows,
+                                  const double* b, double* x, const uint8_t* fixed, double rtol, int32_t maxit,
+                                  void* stream, int32_t* iters, double* rel_res);
+
 const char* gf_status_string(gf_status s);
 const char* gf_last_error(void);
 

@@ -5,5 +5,5 @@ The compute path is the CUDA library under ``csrc/`` behind the C ABI in
 """
 from .graphfem import (  # noqa: F401
     DRIVER_STRAIN, DRIVER_STRESS, FP64, MEM_DEVICE, MEM_HOST, MIXED, GraphFEMError, Mesh, load_library,
-    material, mesh_create, mesh_plan,
+    bsr_pcg_solve_static, material, mesh_create, mesh_plan,
 )

@@ -98,6 +98,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_profile_name": (ctypes.c_char_p, [ctypes.c_int32]),
         "gf_profile_reset": (ctypes.c_int, [P]),
         "gf_launch_count": (ctypes.c_int64, [P]),
+        "gf_bsr_pcg_solve_static": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_double,
+                                                   ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32),
+                                                   ctypes.POINTER(ctypes.c_double)]),
         "gf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "gf_last_error": (ctypes.c_char_p, []),
     }
@@ -278,6 +281,34 @@ def mesh_plan(nodes, tets, mat: Material) -> dict:
     out = {f: getattr(inf, f) for f, _ in MeshInfo._fields_}
     out.update(edges=edges, colour=colour, nbr_count=cnt)
     return out
+
+
+def bsr_pcg_solve_static(row_ptr, col, values, b, x, fixed=None, rtol: float = 1e-6, maxit: int = 10000,
+                         stream=None):
+    """gf_bsr_pcg_solve_static: solve a block-CSR system without any device
+    allocation (for callers that must not allocate while solving).  All arrays
+    are CUDA tensors on the current device; x is overwritten with the solution.
+    Returns (iterations, relative residual)."""
+    import torch
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col", col, torch.int32), ("values", values, torch.float64),
+                        ("b", b, torch.float64), ("x", x, torch.float64)):
+        if not (_is_torch_cuda(t) and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"{name}: expected a contiguous CUDA tensor of {dt}")
+    if fixed is not None and not (_is_torch_cuda(fixed) and fixed.dtype == torch.uint8):
+        raise TypeError("fixed: expected a CUDA uint8 tensor")
+    n_rows = row_ptr.numel() - 1
+    if b.numel() != 3 * n_rows or x.numel() != 3 * n_rows or (fixed is not None and fixed.numel() != n_rows):
+        raise ValueError("b and x need 3 * n_rows entries, fixed n_rows")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    _check(load_library().gf_bsr_pcg_solve_static(row_ptr.data_ptr(), col.data_ptr(), values.data_ptr(), n_rows,
+                                                  b.data_ptr(), x.data_ptr(),
+                                                  None if fixed is None else fixed.data_ptr(), float(rtol),
+                                                  int(maxit), sptr, ctypes.byref(it), ctypes.byref(rel)))
+    return it.value, rel.value
 
 
 def _torch_plumbing(device: int, stream):
