@@ -73,6 +73,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# Algorithmic bytes per launch of the mixed-precision kernels (each array read or
+# written once; gathers of node data counted once per node).
+MIXED_BYTES = {
+    "m:tet_stress": lambda i: i["n_tets"] * (16 + 72 + 4 + 24 + 24) + 12 * i["n_nodes"],
+    "m:nonlocal_avg": lambda i: 8.0 * i["n_nbr_pairs"] + i["n_tets"] * (24 + 24),
+    "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
+    "m:assemble": lambda i: i["n_tets"] * (16 + 120 + 4 + 16 + 32) + i["n_blocks"] * 36 + i["n_nodes"] * (24 + 36 + 24 + 8),
+    "m:pcg_spmv": lambda i: i["n_blocks"] * 40 + i["n_nodes"] * (4 + 12 + 12 + 12),
+}
+
+
 def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, traffic=None):
     """Roofline entry of one kernel group: algorithmic work per launch / mean launch time."""
     T, NB, N, pairs = info["n_tets"], info["n_blocks"], info["n_nodes"], info["n_nbr_pairs"]
@@ -95,6 +106,12 @@ def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, tra
                 "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
                 "work_per_launch": {"fp64_flop": flops, "bytes": 76.0 * NB + 4.0 * (N + 1) + 48.0 * N},
                 "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
+    if group in MIXED_BYTES:
+        bytes_per = MIXED_BYTES[group](info)
+        gbs = bytes_per / t / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                "traffic": traffic, "kernel": group, "work_per_launch": {"bytes": bytes_per},
+                "peak_kind": "measured HBM copy bandwidth"}
     # streaming kernels: bytes
     bytes_per = {"tet_stress": T * (16 + 37 * 8 + 8 + 96) + 24 * N,
                  "edge_driver": info["n_edges"] * (8 + 8 + 8 + 1) + 6 * T * (4 + 48) + 24 * N,
@@ -176,30 +193,36 @@ def run_ours(args) -> None:
 
     w = loaf_config()
     mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius)
+    f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(m, steps):
+        iters, sweeps = [], []
+        for _ in range(args.warmup):
+            m.step(w.dt, f_dev)
+        m.profile_reset()
+        m.profile_enable(True)
+        l0 = m.launch_count()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s = m.step(w.dt, f_dev)
+            iters.append(s["cg_iters"])
+            sweeps.append(s["refine_sweeps"])
+            assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
+        e1.record(stream)
+        barrier()
+        m.profile_enable(False)
+        return (e0.elapsed_time(e1) / steps, m.launch_count() - l0, m.profile_get(), statistics.mean(iters),
+                statistics.mean(sweeps))
+
+    # plain FP64 form (the headline)
     m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
     info = m.info
-    f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
-    for _ in range(args.warmup):
-        m.step(w.dt, f_dev)
-    m.profile_reset()
-    m.profile_enable(True)
-    stream = torch.cuda.current_stream()
-    iters = []
     clk = ClockSampler(local)
-    l0 = m.launch_count()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        s = m.step(w.dt, f_dev)
-        iters.append(s["cg_iters"])
-    e1.record(stream)
-    barrier()
+    ms, launches, prof, it_mean, _ = timed(m, args.steps)
     clocks = clk.stop()
-    launches = m.launch_count() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    m.profile_enable(False)
-    prof = m.profile_get()
     # end to end through the public API with host buffers: pinned f_ext in, positions out, every step
     f_host = torch.tensor(w.f_ext.ravel(), dtype=torch.float64).pin_memory()
     x_host = torch.empty(3 * w.n_nodes, dtype=torch.float64).pin_memory()
@@ -210,16 +233,24 @@ def run_ours(args) -> None:
         m.positions_get(out=x_host)
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    t_all = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+    m.close()
+    # mixed-precision form on the same workload and tolerance
+    mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
+    mix_ms, mix_launches, mix_prof, mix_it, mix_sw = timed(mm, args.steps)
+    mm.close()
+    t_all = torch.tensor([ms, e2e_ms, mix_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    ms, e2e_ms = float(t_all[0]), float(t_all[1])
+    ms, e2e_ms, mix_ms = float(t_all[0]), float(t_all[1]), float(t_all[2])
+    iters = [it_mean]
     if rank != 0:
         return
     dom = max(prof, key=lambda k: prof[k][0])
     pk = peaks()
     traffic = None
     roof = roofline_for(dom, prof[dom][0], prof[dom][1], info, pk, traffic)
+    mdom = max(("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "pcg_spmv"), key=lambda k: mix_prof[k][0])
+    mix_roof = roofline_for("m:" + mdom, mix_prof[mdom][0], mix_prof[mdom][1], info, pk, None)
     cpu = None if args.no_cpu_baseline else cpu_baseline_entry(3, w.n_tets)
     out = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -231,11 +262,16 @@ def run_ours(args) -> None:
                    "l2": f"inputs larger than L2: {info['device_bytes'] / 1e9:.2f} GB of mesh data resident",
                    "parallelism": "replicas" if world > 1 else "single"},
         "element_updates_per_s": info["n_tets"] / (ms * 1e-3),
-        "cg_iters_per_step": statistics.mean(iters),
+        "cg_iters_per_step": it_mean,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * w.n_nodes,
                 "d2h_bytes_per_step": 8 * 3 * w.n_nodes + 48},
         "gpu_launches": launches,
         "roofline": roof,
+        "mixed": {"ms_per_step": mix_ms, "speedup_vs_fp64": ms / mix_ms, "cg_iters_per_step": mix_it,
+                  "refine_sweeps_per_step": mix_sw, "element_updates_per_s": info["n_tets"] / (mix_ms * 1e-3),
+                  "gpu_launches": mix_launches, "dtype": "f32 tangents/SpMV/PCG, f64 state/residual/dots/threshold",
+                  "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mix_prof.items()},
+                  "roofline": mix_roof},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "kernel_launches": {k: v[1] for k, v in prof.items()},
         "clocks": clocks,
@@ -254,7 +290,8 @@ def run_profile_step(args) -> None:
     torch.cuda.set_device(0)
     w = loaf_config()
     m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=w.threshold,
-                                                    radius=w.radius), cg_rtol=w.cg_rtol)
+                                                    radius=w.radius), cg_rtol=w.cg_rtol,
+                       precision=gf.MIXED if args.precision == "mixed" else gf.FP64)
     f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
         s = m.step(w.dt, f_dev)
@@ -271,6 +308,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="form run by --profile-step")
     args = ap.parse_args()
     if args.cpu_sample_child:
         cpu_sample_child(args.cpu_sample_child)

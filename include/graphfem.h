@@ -155,6 +155,11 @@ gf_status gf_state_set(gf_mesh* mesh, const double* x, const double* v, const ui
 gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
                   const double* pinned_vel, int32_t mem, gf_step_stats* stats);
 
+/* GF_MIXED: relative tolerance of each inner FP32 PCG solve of the FP64
+ * iterative refinement (default 1e-4; 0 < inner_rtol < 1).  The outer FP64
+ * tolerance stays cg_rtol. */
+gf_status gf_refine_set(gf_mesh* mesh, double inner_rtol);
+
 /* Change the solver tolerance and iteration cap between steps (rtol > 0). */
 gf_status gf_solver_set(gf_mesh* mesh, double cg_rtol, int32_t cg_maxit);
 

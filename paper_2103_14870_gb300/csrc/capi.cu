@@ -16,11 +16,11 @@ namespace {
 
 enum ProfGroup : int {
   kPStress = 0, kPNonlocal, kPEdge, kPChi, kPAssemble, kPPcgInit, kPSpmv, kPPcgUpdate, kPPcgP, kPResidual,
-  kPIntegrate, kPCount
+  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPCount
 };
 const char* kProfNames[kPCount] = {"tet_stress",  "nonlocal_avg", "edge_driver", "tet_chi",     "assemble",
                                    "pcg_init",    "pcg_spmv",     "pcg_update",  "pcg_p",       "true_residual",
-                                   "integrate"};
+                                   "integrate",   "ir_residual",  "ir_inner_init", "ir_apply"};
 
 __global__ void k_fill(double* p, int64_t n, double v) {
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -73,10 +73,14 @@ struct gf_mesh {
   DevMesh dm;
   int32_t* perm_dev = nullptr;
   int last_iters = 4;
+  bool mixed = false;
+  int last_inner = 3;
+  double in_rtol = 1e-4;
   int64_t launches = 0;
   int64_t nbr_pairs = 0;
 
   PcgState* h_pcg = nullptr;               // pinned host mirror
+  IrState* h_ir = nullptr;                 // pinned host mirror (mixed)
   unsigned long long* h_cnt = nullptr;     // pinned host mirror of counters
 
   bool prof = false;
@@ -150,6 +154,7 @@ void release(gf_mesh* m) {
   m->blocks.clear();
   for (auto e : m->ev_pool) cudaEventDestroy(e);
   if (m->h_pcg) cudaFreeHost(m->h_pcg);
+  if (m->h_ir) cudaFreeHost(m->h_ir);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
 }
@@ -180,7 +185,7 @@ void prof_collect(gf_mesh* m, int cg_iters, bool converged) {
   if (!m->prof) return;
   for (auto& r : m->recs) {
     // early-exit PCG launches after convergence did no work: do not count them
-    if (r.iter >= 0) {
+    if (r.iter >= 0 && cg_iters < (1 << 30)) {
       bool worked = (r.group == kPSpmv || r.group == kPPcgUpdate) ? r.iter < cg_iters
                                                                     : r.iter < (converged ? cg_iters - 1 : cg_iters);
       if (!worked) continue;
@@ -210,8 +215,13 @@ cudaMemcpyKind to_dev(int32_t mem) { return mem == GF_MEM_HOST ? cudaMemcpyHostT
 cudaMemcpyKind from_dev(int32_t mem) { return mem == GF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
 
 gf_status recompute_chi(gf_mesh* m) {
-  m->launches += launch_tet_stress(m->dm, m->mt, m->stream);
-  m->launches += launch_tet_chi(m->dm, m->mt, m->lut, m->stream);
+  if (m->mixed) {
+    m->launches += launch_tet_stress32(m->dm, m->mt, m->stream);
+    m->launches += launch_tet_chi32(m->dm, m->mt, m->lut, m->stream);
+  } else {
+    m->launches += launch_tet_stress(m->dm, m->mt, m->stream);
+    m->launches += launch_tet_chi(m->dm, m->mt, m->lut, m->stream);
+  }
   GF_CK(cudaGetLastError());
   return GF_OK;
 }
@@ -252,8 +262,8 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   if (opt_in) opt = *opt_in;
   if (opt.cg_maxit <= 0) opt.cg_maxit = 10000;
   if (!(opt.cg_rtol > 0)) opt.cg_rtol = 1e-6;
-  if (opt.precision != GF_FP64) {
-    set_last_error("only GF_FP64 is available in this build");
+  if (opt.precision != GF_FP64 && opt.precision != GF_MIXED) {
+    set_last_error("precision must be GF_FP64 or GF_MIXED");
     return GF_UNSUPPORTED;
   }
   if (opt.precond != GF_PRECOND_BJACOBI) {
@@ -297,7 +307,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     m->own_stream = true;
   }
   std::string err;
-  gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, M, m->hm, err);
+  gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, M, m->hm, err, opt.precision == GF_FP64);
   if (st != GF_OK) {
     set_last_error(err);
     return fail(st);
@@ -310,6 +320,16 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
 
   HostMesh& hm = m->hm;
   DevMesh& d = m->dm;
+  const bool mixed = opt.precision == GF_MIXED;
+  m->mixed = mixed;
+  MixedHost mxh;
+  if (mixed) {
+    st = build_mixed_host(nodes, hm, mxh, err);
+    if (st != GF_OK) {
+      set_last_error(err);
+      return fail(st);
+    }
+  }
   d.N = hm.n_nodes;
   d.T = hm.n_tets;
   d.NE = hm.n_edges;
@@ -319,23 +339,37 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   do {                                                                           \
     const type* p_ = nullptr;                                                    \
     if ((st = upload(m, vec, &p_)) != GF_OK) return fail(st);                    \
-    d.field = reinterpret_cast<decltype(d.field)>(p_);                           \
+    field = reinterpret_cast<decltype(field)>(p_);                               \
   } while (0)
-  UP(tets, hm.tets, int32_t);
-  UP(tet_edges, hm.tet_edges, int32_t);
-  UP(slot, hm.slot, int32_t);
-  UP(rest, hm.rest, double);
-  UP(mass, hm.mass, double);
-  UP(row_ptr, hm.row_ptr, int32_t);
-  UP(col, hm.col, int32_t);
-  UP(diag_blk, hm.diag_blk, int32_t);
-  UP(edges, hm.edges, int32_t);
-  UP(et_ptr, hm.et_ptr, int32_t);
-  UP(et_tet, hm.et_tet, int32_t);
-  UP(nb_off, hm.nbr.group_off, int64_t);
-  UP(nb_len, hm.nbr.group_len, int32_t);
-  UP(nb_idx, hm.nbr.idx, int32_t);
-  UP(nb_w, hm.nbr.w, double);
+  UP(d.tets, hm.tets, int32_t);
+  UP(d.tet_edges, hm.tet_edges, int32_t);
+  UP(d.mass, hm.mass, double);
+  UP(d.row_ptr, hm.row_ptr, int32_t);
+  UP(d.col, hm.col, int32_t);
+  UP(d.diag_blk, hm.diag_blk, int32_t);
+  UP(d.edges, hm.edges, int32_t);
+  UP(d.et_ptr, hm.et_ptr, int32_t);
+  UP(d.et_tet, hm.et_tet, int32_t);
+  UP(d.nb_off, hm.nbr.group_off, int64_t);
+  UP(d.nb_len, hm.nbr.group_len, int32_t);
+  UP(d.nb_idx, hm.nbr.idx, int32_t);
+  if (!mixed) {
+    UP(d.slot, hm.slot, int32_t);
+    UP(d.rest, hm.rest, double);
+    UP(d.nb_w, hm.nbr.w, double);
+  } else {
+    UP(d.mx.restA, mxh.restA, float);
+    UP(d.mx.restB, mxh.restB, float);
+    UP(d.mx.edge_e0, mxh.edge_e0, float);
+    UP(d.mx.np_ptr, mxh.np_ptr, int32_t);
+    UP(d.mx.np_pair, mxh.np_pair, int32_t);
+    UP(d.mx.rl_ptr, mxh.rl_ptr, int32_t);
+    UP(d.mx.rl_ent, mxh.rl_ent, uint16_t);
+    UP(d.mx.nb_w32, mxh.nb_w32, float);
+    std::vector<double> Xv(nodes, nodes + 3 * n_nodes);
+    UP(d.mx.X, Xv, double);
+    d.mx.max_deg = mxh.max_deg;
+  }
 #undef UP
   {
     const int32_t* pp = nullptr;
@@ -344,16 +378,30 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   }
   const int64_t N = d.N, T = d.T, NE = d.NE, NB = d.NB;
   if ((st = scratch(m, 3 * N, &d.x)) || (st = scratch(m, 3 * N, &d.v)) || (st = scratch(m, NE, &d.labels)) ||
-      (st = scratch(m, T, &d.chi)) || (st = scratch(m, NE, &d.driver)) || (st = scratch(m, 6 * T, &d.sig_in)) ||
-      (st = scratch(m, 6 * T, &d.sig_bar)) || (st = scratch(m, 6 * T, &d.sigf)) || (st = scratch(m, 9 * NB, &d.val)) ||
-      (st = scratch(m, 3 * N, &d.rhs)) || (st = scratch(m, 3 * N, &d.dv)) || (st = scratch(m, 3 * N, &d.r)) ||
-      (st = scratch(m, 3 * N, &d.z)) || (st = scratch(m, 3 * N, &d.p)) || (st = scratch(m, 3 * N, &d.q)) ||
-      (st = scratch(m, 9 * N, &d.pinv)) || (st = scratch(m, N, &d.pinned)) || (st = scratch(m, 3 * N, &d.f_ext)) ||
+      (st = scratch(m, T, &d.chi)) || (st = scratch(m, NE, &d.driver)) || (st = scratch(m, 3 * N, &d.rhs)) ||
+      (st = scratch(m, 3 * N, &d.dv)) || (st = scratch(m, N, &d.pinned)) || (st = scratch(m, 3 * N, &d.f_ext)) ||
       (st = scratch(m, N, &d.pin_ids)) || (st = scratch(m, 3 * N, &d.pin_vel)) || (st = scratch(m, 1, &d.pcg)) ||
       (st = scratch(m, 2 * kMaxPartials, &d.partials)) || (st = scratch(m, kTickets, &d.tickets)) ||
-      (st = scratch(m, kCntMax, &d.counters)))
+      (st = scratch(m, kCntMax, &d.counters)) || (st = scratch(m, 6 * T, &d.sigf)))
     return fail(st);
+  if (!mixed) {
+    if ((st = scratch(m, 6 * T, &d.sig_in)) || (st = scratch(m, 6 * T, &d.sig_bar)) ||
+        (st = scratch(m, 9 * NB, &d.val)) || (st = scratch(m, 3 * N, &d.r)) || (st = scratch(m, 3 * N, &d.z)) ||
+        (st = scratch(m, 3 * N, &d.p)) || (st = scratch(m, 3 * N, &d.q)) || (st = scratch(m, 9 * N, &d.pinv)))
+      return fail(st);
+  } else {
+    MixDev& x = d.mx;
+    if ((st = scratch(m, 3 * N, &x.u32)) || (st = scratch(m, 3 * N, &x.v32)) || (st = scratch(m, T, &x.chi32)) ||
+        (st = scratch(m, 8 * T, &x.sig_in32)) || (st = scratch(m, 8 * T, &x.sig_bar32)) ||
+        (st = scratch(m, 6 * T, &x.sigf32)) || (st = scratch(m, 9 * NB, &x.val32)) ||
+        (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
+        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
+        (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) || (st = scratch(m, 3 * N, &x.r64)) ||
+        (st = scratch(m, 1, &x.ir)))
+      return fail(st);
+  }
   if (cudaMallocHost(&m->h_pcg, sizeof(PcgState)) != cudaSuccess ||
+      cudaMallocHost(&m->h_ir, sizeof(IrState)) != cudaSuccess ||
       cudaMallocHost(&m->h_cnt, sizeof(unsigned long long) * kCntMax) != cudaSuccess) {
     set_last_error("cudaMallocHost failed");
     return fail(GF_OOM);
@@ -364,11 +412,16 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   GF_CK(cudaMemsetAsync(d.labels, 0, NE, m->stream));
   GF_CK(cudaMemsetAsync(d.tickets, 0, sizeof(unsigned) * kTickets, m->stream));
   GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, m->stream));
-  GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * NB, m->stream));
+  if (!mixed) GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * NB, m->stream));
+  else GF_CK(cudaMemsetAsync(d.mx.val32, 0, sizeof(float) * 9 * NB, m->stream));
   GF_CK(cudaMemsetAsync(d.rhs, 0, sizeof(double) * 3 * N, m->stream));
   k_fill<<<unsigned((T + 255) / 256), 256, 0, m->stream>>>(d.chi, T, 1.0);
   k_fill<<<unsigned((NE + 255) / 256), 256, 0, m->stream>>>(d.driver, NE, -INFINITY);
   m->launches += 2;
+  if (mixed) {
+    m->launches += launch_refresh32(d, m->stream);
+    m->launches += launch_chi_to32(d, m->stream);
+  }
   GF_CK(cudaGetLastError());
   GF_CK(cudaStreamSynchronize(m->stream));
   // drop host copies not needed after upload
@@ -461,20 +514,31 @@ gf_status gf_state_set(gf_mesh* m, const double* x, const double* v, const uint8
   if (x) GF_CK(cudaMemcpyAsync(d.x, x, sizeof(double) * 3 * d.N, to_dev(mem), m->stream));
   if (v) GF_CK(cudaMemcpyAsync(d.v, v, sizeof(double) * 3 * d.N, to_dev(mem), m->stream));
   if (labels) GF_CK(cudaMemcpyAsync(d.labels, labels, d.NE, to_dev(mem), m->stream));
+  if (m->mixed && (x || v)) m->launches += launch_refresh32(d, m->stream);
   if (chi) {
     const double* src = chi;
     if (mem == GF_MEM_HOST) {
-      GF_CK(cudaMemcpyAsync(d.sig_in, chi, sizeof(double) * d.T, cudaMemcpyHostToDevice, m->stream));
-      src = d.sig_in;
+      GF_CK(cudaMemcpyAsync(d.sigf, chi, sizeof(double) * d.T, cudaMemcpyHostToDevice, m->stream));
+      src = d.sigf;
     }
     k_gather<<<unsigned((d.T + 255) / 256), 256, 0, m->stream>>>(src, m->perm_dev, d.chi, d.T);
     m->launches += 1;
+    if (m->mixed) m->launches += launch_chi_to32(d, m->stream);
     GF_CK(cudaGetLastError());
   } else if (labels) {
     gf_status st = recompute_chi(m);
     if (st != GF_OK) return st;
   }
   GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
+}
+
+gf_status gf_refine_set(gf_mesh* m, double inner_rtol) {
+  if (!m || !(inner_rtol > 0) || !(inner_rtol < 1)) {
+    set_last_error("need 0 < inner_rtol < 1");
+    return GF_BAD_ARG;
+  }
+  m->in_rtol = inner_rtol;
   return GF_OK;
 }
 
@@ -487,6 +551,124 @@ gf_status gf_solver_set(gf_mesh* m, double rtol, int32_t maxit) {
   m->opt.cg_maxit = maxit;
   return GF_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// FP64 path: damage, colour-ordered assembly, projected PCG (all FP64).
+gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_pinned, bool has_pvel,
+                    int64_t& L) {
+  cudaStream_t s = m->stream;
+  const gf::Material& mt = m->mt;
+  const int64_t N = d.N;
+  { Prof p(m, kPStress); L += launch_tet_stress(d, mt, s); }
+  if (mt.radius > 0.0) {
+    Prof p(m, kPNonlocal);
+    L += launch_nonlocal(d, s);
+  } else {
+    d.sig_bar = d.sig_in;   // R_d = 0: the tet alone (local criterion)
+  }
+  { Prof p(m, kPEdge); L += launch_edge_driver(d, mt, s); }
+  { Prof p(m, kPChi); L += launch_tet_chi(d, mt, m->lut, s); }
+  {
+    Prof p(m, kPAssemble);
+    GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
+    L += launch_node_init(d, dt, mt, has_fext, s);
+    const auto& cp = m->hm.colour_ptr;
+    for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble(d, mt, dt, cp[c], cp[c + 1], s);
+  }
+  PcgState init{};
+  init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+  init.maxit = m->opt.cg_maxit;
+  *m->h_pcg = init;
+  GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+  GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
+  GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
+  L += launch_set_pinned(d, n_pinned, has_pvel, s);
+  { Prof p(m, kPPcgInit); L += launch_pcg_init(d, s); }
+  int launched_iters = 0;
+  int chunk = std::max(1, std::min(m->last_iters + 1, 64));
+  for (;;) {
+    for (int j = 0; j < chunk; ++j, ++launched_iters) {
+      { Prof p(m, kPSpmv, launched_iters); L += launch_pcg_iter(d, s, 0); }
+      { Prof p(m, kPPcgUpdate, launched_iters); L += launch_pcg_iter(d, s, 1); }
+      { Prof p(m, kPPcgP, launched_iters); L += launch_pcg_iter(d, s, 2); }
+    }
+    GF_CK(cudaGetLastError());
+    GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaStreamSynchronize(s));
+    if (m->h_pcg->done || launched_iters >= m->opt.cg_maxit) break;
+    chunk = 8;
+  }
+  { Prof p(m, kPResidual); L += launch_true_residual(d, s); }
+  { Prof p(m, kPIntegrate); L += launch_integrate(d, dt, s); }
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  return GF_OK;
+}
+
+// Mixed path: FP32 damage and tangents, row-gather assembly, FP64 iterative
+// refinement around FP32 PCG with FP64 dot products.
+gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_pinned, bool has_pvel, int64_t& L) {
+  cudaStream_t s = m->stream;
+  const gf::Material& mt = m->mt;
+  const int64_t N = d.N;
+  { Prof p(m, kPStress); L += launch_tet_stress32(d, mt, s); }
+  if (mt.radius > 0.0) {
+    Prof p(m, kPNonlocal);
+    L += launch_nonlocal32(d, s);
+  } else {
+    d.mx.sig_bar32 = d.mx.sig_in32;
+  }
+  { Prof p(m, kPEdge); L += launch_edge_driver32(d, mt, s); }
+  { Prof p(m, kPChi); L += launch_tet_chi32(d, mt, m->lut, s); }
+  { Prof p(m, kPAssemble); L += launch_assemble32(d, mt, dt, has_fext, s); }
+  IrState init{};
+  init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+  init.in_tol2 = m->in_rtol * m->in_rtol;
+  init.maxit = m->opt.cg_maxit;
+  init.in_maxit = 32;         // numerics: each inner solve stops at in_rtol or 32 iterations
+  init.applied = 1;
+  init.in_done = 1;
+  // launches per block only: an unfinished inner solve continues in the next block
+  const int K = std::max(2, std::min(m->last_inner + 1, 32));
+  *m->h_ir = init;
+  GF_CK(cudaMemcpyAsync(d.mx.ir, m->h_ir, sizeof(IrState), cudaMemcpyHostToDevice, s));
+  GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
+  GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
+  L += launch_set_pinned(d, n_pinned, has_pvel, s);
+  L += launch_refresh32(d, s);
+  { Prof p(m, kPIrResidual); L += launch_ir_residual(d, 1, s); }
+  int it = 0;
+  int max_inner = 0;
+  for (int round = 0;; ++round) {
+    for (int sw = 0; sw < 2; ++sw) {
+      { Prof p(m, kPIrInit); L += launch_ir_inner_init(d, s); }
+      for (int j = 0; j < K; ++j, ++it) {
+        { Prof p(m, kPSpmv, -2); L += launch_ir_inner_iter(d, s, 0); }
+        { Prof p(m, kPPcgUpdate, -2); L += launch_ir_inner_iter(d, s, 1); }
+        { Prof p(m, kPPcgP, -2); L += launch_ir_inner_iter(d, s, 2); }
+      }
+      { Prof p(m, kPIrApply); L += launch_ir_apply(d, s); }
+      { Prof p(m, kPIrResidual); L += launch_ir_residual(d, 0, s); }
+    }
+    GF_CK(cudaGetLastError());
+    GF_CK(cudaMemcpyAsync(m->h_ir, d.mx.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaStreamSynchronize(s));
+    max_inner = std::max(max_inner, m->h_ir->in_iters);
+    if (m->h_ir->done || m->h_ir->total_iters >= m->opt.cg_maxit || round >= 4096) break;
+  }
+  m->last_inner = std::max(1, std::min(max_inner, 32));
+  { Prof p(m, kPIntegrate); L += launch_integrate32(d, dt, s); }
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaMemcpyAsync(m->h_ir, d.mx.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+  return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
                   const double* pinned_vel, int32_t mem, gf_step_stats* stats) {
@@ -505,7 +687,6 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
   cudaStream_t s = m->stream;
   DevMesh d = m->dm;   // per-step view (input pointers may be overridden)
   const int64_t N = d.N;
-
   GF_CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long) * kCntMax, s));
   if (f_ext && mem == GF_MEM_HOST) {
     GF_CK(cudaMemcpyAsync(d.f_ext, f_ext, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
@@ -522,63 +703,32 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
       if (pinned_vel) d.pin_vel = const_cast<double*>(pinned_vel);
     }
   }
-  const gf::Material& mt = m->mt;
   int64_t L = 0;
-  // ---- 1. damage at the start-of-step positions (Eq. 14-25) ----
-  { Prof p(m, kPStress); L += launch_tet_stress(d, mt, s); }
-  if (mt.radius > 0.0) {
-    Prof p(m, kPNonlocal);
-    L += launch_nonlocal(d, s);
-  } else {
-    d.sig_bar = d.sig_in;   // R_d = 0: the tet alone (local criterion)
-  }
-  { Prof p(m, kPEdge); L += launch_edge_driver(d, mt, s); }
-  { Prof p(m, kPChi); L += launch_tet_chi(d, mt, m->lut, s); }
-  // ---- 2. system A dv = b (Eq. 2, 12, 32-34) ----
-  {
-    Prof p(m, kPAssemble);
-    GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
-    L += launch_node_init(d, dt, mt, f_ext != nullptr, s);
-    const auto& cp = m->hm.colour_ptr;
-    for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble(d, mt, dt, cp[c], cp[c + 1], s);
-  }
-  // ---- 3. projected block-Jacobi PCG ----
-  PcgState init{};
-  init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
-  init.maxit = m->opt.cg_maxit;
-  *m->h_pcg = init;
-  GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
-  GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
-  GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
-  L += launch_set_pinned(d, n_pinned, pinned_vel != nullptr, s);
-  { Prof p(m, kPPcgInit); L += launch_pcg_init(d, s); }
-  int launched_iters = 0;
-  int chunk = std::max(1, std::min(m->last_iters + 1, 64));
-  for (;;) {
-    for (int j = 0; j < chunk; ++j, ++launched_iters) {
-      { Prof p(m, kPSpmv, launched_iters); L += launch_pcg_iter(d, s, 0); }
-      { Prof p(m, kPPcgUpdate, launched_iters); L += launch_pcg_iter(d, s, 1); }
-      { Prof p(m, kPPcgP, launched_iters); L += launch_pcg_iter(d, s, 2); }
-    }
-    GF_CK(cudaGetLastError());
-    GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-    GF_CK(cudaStreamSynchronize(s));
-    if (m->h_pcg->done || launched_iters >= m->opt.cg_maxit) break;
-    chunk = 8;
-  }
-  { Prof p(m, kPResidual); L += launch_true_residual(d, s); }
-  // ---- 4. v += dv, x += dt v ----
-  { Prof p(m, kPIntegrate); L += launch_integrate(d, dt, s); }
-  GF_CK(cudaGetLastError());
-  GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  gf_status st = m->mixed ? step_mixed(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L)
+                          : step_fp64(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L);
+  if (st != GF_OK) return st;
   GF_CK(cudaMemcpyAsync(m->h_cnt, d.counters, sizeof(unsigned long long) * kCntMax, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
   m->launches += L;
-  const PcgState& ps = *m->h_pcg;
-  m->last_iters = ps.iters;
-  prof_collect(m, ps.iters, ps.status == GF_OK);
-  gf_status status = gf_status(ps.status);
-  const double rel = ps.bb > 0 ? std::sqrt(ps.true_rr / ps.bb) : 0.0;
+  gf_status status;
+  int iters, sweeps = 0;
+  double rel;
+  if (m->mixed) {
+    const IrState& ir = *m->h_ir;
+    status = gf_status(ir.status);
+    iters = ir.total_iters;
+    sweeps = ir.sweeps;
+    rel = ir.bb > 0 ? std::sqrt(ir.rr / ir.bb) : 0.0;
+    if (status == GF_OK && !ir.done) status = GF_CG_MAXITER;
+    prof_collect(m, 1 << 30, false);
+  } else {
+    const PcgState& ps = *m->h_pcg;
+    m->last_iters = ps.iters;
+    prof_collect(m, ps.iters, ps.status == GF_OK);
+    status = gf_status(ps.status);
+    iters = ps.iters;
+    rel = ps.bb > 0 ? std::sqrt(ps.true_rr / ps.bb) : 0.0;
+  }
   if (status == GF_OK && !std::isfinite(rel)) status = GF_NAN;
   if (m->h_cnt[3] != 0) {
     set_last_error("pinned node id out of range (skipped)");
@@ -586,12 +736,12 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
   }
   if (stats) {
     stats->status = status;
-    stats->cg_iters = ps.iters;
+    stats->cg_iters = iters;
     stats->rel_res = rel;
     stats->n_broken = int64_t(m->h_cnt[kCntBroken]);
     stats->n_new_broken = int64_t(m->h_cnt[kCntNewBroken]);
     stats->n_chi_zero = int64_t(m->h_cnt[kCntChiZero]);
-    stats->refine_sweeps = 0;
+    stats->refine_sweeps = sweeps;
     stats->reserved = 0;
   }
   if (status != GF_OK && status != GF_BAD_ARG)
@@ -666,9 +816,16 @@ gf_status gf_system_get(gf_mesh* m, int32_t* row_ptr, int32_t* col, double* valu
   DeviceGuard guard(m->device);
   if (row_ptr) std::memcpy(row_ptr, m->hm.row_ptr.data(), sizeof(int32_t) * m->hm.row_ptr.size());
   if (col) std::memcpy(col, m->hm.col.data(), sizeof(int32_t) * m->hm.col.size());
-  if (values) GF_CK(cudaMemcpyAsync(values, m->dm.val, sizeof(double) * 9 * m->dm.NB, cudaMemcpyDeviceToHost, m->stream));
+  std::vector<float> v32;
+  if (values && !m->mixed)
+    GF_CK(cudaMemcpyAsync(values, m->dm.val, sizeof(double) * 9 * m->dm.NB, cudaMemcpyDeviceToHost, m->stream));
+  if (values && m->mixed) {
+    v32.resize(9 * m->dm.NB);
+    GF_CK(cudaMemcpyAsync(v32.data(), m->dm.mx.val32, sizeof(float) * 9 * m->dm.NB, cudaMemcpyDeviceToHost, m->stream));
+  }
   if (rhs) GF_CK(cudaMemcpyAsync(rhs, m->dm.rhs, sizeof(double) * 3 * m->dm.N, cudaMemcpyDeviceToHost, m->stream));
   GF_CK(cudaStreamSynchronize(m->stream));
+  for (size_t i = 0; i < v32.size(); ++i) values[i] = double(v32[i]);
   return GF_OK;
 }
 

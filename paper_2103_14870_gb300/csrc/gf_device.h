@@ -21,6 +21,46 @@ struct PcgState {
 
 enum Counter : int { kCntBroken = 0, kCntNewBroken = 1, kCntChiZero = 2, kCntMax = 4 };
 
+// Scalars of the mixed-precision solve: FP64 iterative refinement (outer)
+// around an FP32 PCG (inner) whose dot products accumulate in FP64.
+struct IrState {
+  double bb;        // ||b_free - A dv_fixed||^2 (reference)
+  double rr;        // ||r64||^2 of the last FP64 residual
+  double tol2;      // outer rtol^2
+  double in_tol2;   // inner rtol^2
+  double rz, pq, alpha, beta, in_rr, in_rr0;
+  int32_t done;     // outer converged (or failed)
+  int32_t in_done;  // inner converged for this sweep
+  int32_t sweeps, in_iters, total_iters, in_maxit, maxit, status;
+  int32_t applied;  // the last inner correction was applied and a new residual is due
+};
+
+// Device arrays of the mixed-precision path.
+struct MixDev {
+  const float* restA = nullptr;       // [T][kRAStride] (128-byte aligned rows)
+  const float* restB = nullptr;       // [T][kRBStride]
+  const float* edge_e0 = nullptr;     // [NE][3]
+  const int32_t* np_ptr = nullptr;    // [N+1]
+  const int32_t* np_pair = nullptr;   // [4T]
+  const int32_t* rl_ptr = nullptr;    // [NB+1]
+  const uint16_t* rl_ent = nullptr;   // [16T]
+  const float* nb_w32 = nullptr;      // SELL-32 weights
+  const double* X = nullptr;          // [3N] rest positions
+  int32_t max_deg = 0;
+  float* u32 = nullptr;               // [3N] displacement x - X
+  float* v32 = nullptr;               // [3N] velocity
+  float* chi32 = nullptr;             // [T]
+  float* sig_in32 = nullptr;          // [T][8] (6 used; 32-byte rows for single-sector gathers)
+  float* sig_bar32 = nullptr;         // [T][8]
+  float* sigf32 = nullptr;            // [T][6]
+  float* val32 = nullptr;             // [NB][9]
+  float* pinv32 = nullptr;            // [N][9]
+  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;   // [3N]
+  float *dv_hi = nullptr, *dv_lo = nullptr;   // [3N] double-float split of dv
+  double* r64 = nullptr;              // [3N]
+  IrState* ir = nullptr;
+};
+
 struct DevMesh {
   int64_t N = 0, T = 0, NE = 0, NB = 0, G = 0;    // nodes, tets, edges, blocks, neighbour groups
   // fixed mesh data
@@ -62,6 +102,7 @@ struct DevMesh {
   int32_t* pin_ids = nullptr;          // [N] staging
   double* pin_vel = nullptr;           // [3N] staging
   PcgState* pcg = nullptr;
+  MixDev mx;                           // mixed-precision arrays (GF_MIXED only)
   double* partials = nullptr;          // reduction partials
   unsigned* tickets = nullptr;         // reduction tickets (one per reduction site)
   unsigned long long* counters = nullptr;  // [kCntMax]
@@ -75,7 +116,7 @@ struct Material {
 };
 
 constexpr int kMaxPartials = 4096;     // max CTAs of a reducing launch
-constexpr int kTickets = 8;
+constexpr int kTickets = 16;
 
 // launchers (return the number of kernels launched)
 int launch_tet_stress(const DevMesh& m, const Material& mt, cudaStream_t s);
@@ -89,5 +130,19 @@ int launch_pcg_init(const DevMesh& m, cudaStream_t s);
 int launch_pcg_iter(const DevMesh& m, cudaStream_t s, int kernel /*0 spmv, 1 update, 2 p*/);
 int launch_true_residual(const DevMesh& m, cudaStream_t s);
 int launch_integrate(const DevMesh& m, double dt, cudaStream_t s);
+
+// mixed-precision path
+int launch_tet_stress32(const DevMesh& m, const Material& mt, cudaStream_t s);
+int launch_nonlocal32(const DevMesh& m, cudaStream_t s);
+int launch_edge_driver32(const DevMesh& m, const Material& mt, cudaStream_t s);
+int launch_tet_chi32(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s);
+int launch_assemble32(const DevMesh& m, const Material& mt, double dt, bool has_fext, cudaStream_t s);
+int launch_ir_residual(const DevMesh& m, int first, cudaStream_t s);
+int launch_ir_inner_init(const DevMesh& m, cudaStream_t s);
+int launch_ir_inner_iter(const DevMesh& m, cudaStream_t s, int which);
+int launch_ir_apply(const DevMesh& m, cudaStream_t s);
+int launch_integrate32(const DevMesh& m, double dt, cudaStream_t s);
+int launch_refresh32(const DevMesh& m, cudaStream_t s);
+int launch_chi_to32(const DevMesh& m, cudaStream_t s);
 
 }  // namespace gf

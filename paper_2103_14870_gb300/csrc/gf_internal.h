@@ -42,6 +42,27 @@ struct NeighbourSell {            // Eq. 20 neighbour lists, 32 tets per group, 
   int64_t pairs = 0;              // real (unpadded) pairs
 };
 
+// FP32 rest data of the mixed-precision path, tet-major (one 128-byte line per
+// tet for the gathers of the row-gather assembly):
+//   restA [T][32]: rest edge vectors X1-X0, X2-X0, X3-X0 (9), Hs packed (21), V, pad
+//   restB [T][12]: B = Dm^-1 row-major (9), pad
+enum Rest32Field : int { kRAE0 = 0, kRAH = 9, kRAV = 30, kRAStride = 32, kRBStride = 12 };
+
+// Extra host data of the mixed-precision path (row-gather assembly).
+struct MixedHost {
+  std::vector<float> restA;         // [T][kRAStride]
+  std::vector<float> restB;         // [T][kRBStride]
+  std::vector<float> edge_e0;       // [NE][3] rest edge vectors (b - a)
+  std::vector<int32_t> np_ptr;      // [N+1] node -> incident (tet, local node) pairs
+  std::vector<int32_t> np_pair;     // [4T] (internal tet << 2) | local node
+  std::vector<int32_t> rl_ptr;      // [NB+1] block -> ordered contribution list
+  std::vector<uint16_t> rl_ent;     // [16T] (pair index within the row << 2) | local b
+  int32_t max_deg = 0;              // max incident tets of a node
+  std::vector<float> nb_w32;        // SELL-32 weights in FP32 (same layout as the FP64 lists)
+};
+
+gf_status build_mixed_host(const double* X, const struct HostMesh& hm, MixedHost& mx, std::string& err);
+
 // Everything mesh_create computes on the host before upload.
 struct HostMesh {
   int64_t n_nodes = 0, n_tets = 0, n_edges = 0, n_blocks = 0;
@@ -62,8 +83,10 @@ struct HostMesh {
 };
 
 // Host precompute; returns GF_OK or GF_BAD_ARG with `err` set.
+// colour_order: order tets colour-major (conflict-free scatter of the FP64 path);
+// otherwise keep the caller's (spatial) order with a single range.
 gf_status build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
-                          const gf_material& mat, HostMesh& hm, std::string& err);
+                          const gf_material& mat, HostMesh& hm, std::string& err, bool colour_order = true);
 
 // 64-bit table: bit m set when the broken-edge mask m (bit k = local edge k)
 // leaves the tet's four nodes in two or more pieces (Eq. 25's disjoint rule).

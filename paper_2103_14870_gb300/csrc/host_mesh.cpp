@@ -82,7 +82,7 @@ uint64_t disconnect_table() {
 }
 
 gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, int64_t T, const gf_material& mat,
-                          HostMesh& hm, std::string& err) {
+                          HostMesh& hm, std::string& err, bool colour_order) {
   if (N <= 0 || T <= 0 || N > (int64_t(1) << 30) || T > (int64_t(1) << 30)) {
     err = "n_nodes and n_tets must be in [1, 2^30]";
     return GF_BAD_ARG;
@@ -171,6 +171,7 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
       colour[t] = c;
     }
   }
+  if (!colour_order) std::fill(colour.begin(), colour.end(), 0);
   int32_t n_col = *std::max_element(colour.begin(), colour.end()) + 1;
   hm.colour_ptr.assign(n_col + 1, 0);
   for (int64_t t = 0; t < T; ++t) hm.colour_ptr[colour[t] + 1]++;
@@ -399,6 +400,64 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
         }
       }
     }
+  return GF_OK;
+}
+
+gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, std::string& err) {
+  const int64_t N = hm.n_nodes, T = hm.n_tets, NE = hm.n_edges;
+  mx.restA.assign(size_t(kRAStride) * T, 0.f);
+  mx.restB.assign(size_t(kRBStride) * T, 0.f);
+  for (int64_t i = 0; i < T; ++i) {
+    const int32_t* n = &hm.tets[4 * i];
+    float* A = &mx.restA[size_t(kRAStride) * i];
+    for (int k = 0; k < 3; ++k)
+      for (int c = 0; c < 3; ++c) A[kRAE0 + 3 * k + c] = float(X[3 * n[k + 1] + c] - X[3 * n[0] + c]);
+    for (int f = 0; f < 21; ++f) A[kRAH + f] = float(hm.rest[size_t(kRestH + f) * T + i]);
+    A[kRAV] = float(hm.rest[size_t(kRestV) * T + i]);
+    for (int f = 0; f < 9; ++f) mx.restB[size_t(kRBStride) * i + f] = float(hm.rest[size_t(kRestB + f) * T + i]);
+  }
+  mx.edge_e0.resize(3 * NE);
+  for (int64_t e = 0; e < NE; ++e)
+    for (int c = 0; c < 3; ++c)
+      mx.edge_e0[3 * e + c] = float(X[3 * hm.edges[2 * e + 1] + c] - X[3 * hm.edges[2 * e] + c]);
+  // node -> (tet, local node) pairs, tets in ascending internal order
+  mx.np_ptr.assign(N + 1, 0);
+  for (int64_t i = 0; i < 4 * T; ++i) mx.np_ptr[hm.tets[i] + 1]++;
+  for (int64_t i = 0; i < N; ++i) mx.np_ptr[i + 1] += mx.np_ptr[i];
+  mx.np_pair.resize(4 * T);
+  {
+    std::vector<int32_t> pos(mx.np_ptr.begin(), mx.np_ptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a) mx.np_pair[pos[hm.tets[4 * t + a]]++] = int32_t((t << 2) | a);
+  }
+  mx.max_deg = 0;
+  for (int64_t i = 0; i < N; ++i) mx.max_deg = std::max(mx.max_deg, mx.np_ptr[i + 1] - mx.np_ptr[i]);
+  if (mx.max_deg > 64) {
+    err = "mixed precision supports at most 64 tets per node (found " + std::to_string(mx.max_deg) + ")";
+    return GF_UNSUPPORTED;
+  }
+  // ordered contribution lists per block: entry (k << 2) | b for pair k of the row's node
+  mx.rl_ptr.assign(hm.n_blocks + 1, 0);
+  for (int64_t i = 0; i < N; ++i)
+    for (int32_t k = mx.np_ptr[i]; k < mx.np_ptr[i + 1]; ++k) {
+      int64_t t = mx.np_pair[k] >> 2;
+      int a = mx.np_pair[k] & 3;
+      for (int b = 0; b < 4; ++b) mx.rl_ptr[hm.slot[16 * t + 4 * a + b] + 1]++;
+    }
+  for (int64_t b = 0; b < hm.n_blocks; ++b) mx.rl_ptr[b + 1] += mx.rl_ptr[b];
+  mx.rl_ent.resize(16 * T);
+  {
+    std::vector<int32_t> pos(mx.rl_ptr.begin(), mx.rl_ptr.end() - 1);
+    for (int64_t i = 0; i < N; ++i)
+      for (int32_t k = mx.np_ptr[i]; k < mx.np_ptr[i + 1]; ++k) {
+        int64_t t = mx.np_pair[k] >> 2;
+        int a = mx.np_pair[k] & 3;
+        for (int b = 0; b < 4; ++b)
+          mx.rl_ent[pos[hm.slot[16 * t + 4 * a + b]]++] = uint16_t(((k - mx.np_ptr[i]) << 2) | b);
+      }
+  }
+  mx.nb_w32.resize(hm.nbr.w.size());
+  for (size_t i = 0; i < hm.nbr.w.size(); ++i) mx.nb_w32[i] = float(hm.nbr.w[i]);
   return GF_OK;
 }
 

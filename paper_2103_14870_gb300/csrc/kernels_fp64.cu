@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "gf_device.h"
+#include "gf_reduce.cuh"
 
 namespace gf {
 namespace {
@@ -25,64 +26,6 @@ __device__ __forceinline__ void ld3(const double* __restrict__ a, int64_t i, dou
   o[0] = p[0];
   o[1] = p[1];
   o[2] = p[2];
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic grid reduction of NV doubles: per-CTA partials, then the last
-// CTA to arrive sums all partials in CTA order.  Every thread of every CTA must
-// call it.  Returns true in the last CTA, with the totals in out[] (valid in
-// thread 0).  Nothing waits on another CTA.
-template <int NV>
-__device__ bool grid_reduce(double (&v)[NV], double* partials, unsigned* ticket, double (&out)[NV]) {
-  __shared__ double sh[NV][32];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double t = warp_sum(v[i]);
-    if (lane == 0) sh[i][wid] = t;
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double t = warp_sum(lane < nw ? sh[i][lane] : 0.0);
-      if (lane == 0) partials[blockIdx.x * NV + i] = t;
-    }
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned k = atomicAdd(ticket, 1u);
-    last = (k == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double t = 0.0;
-    for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) t += __ldcg(&partials[j * NV + i]);
-    t = warp_sum(t);
-    __syncthreads();
-    if (lane == 0) sh[i][wid] = t;
-    __syncthreads();
-    if (wid == 0) {
-      t = warp_sum(lane < nw ? sh[i][lane] : 0.0);
-      if (lane == 0) out[i] = t;
-    }
-  }
-  if (threadIdx.x == 0) *ticket = 0u;
-  return true;
-}
-
-__device__ __forceinline__ void warp_count(unsigned long long c, unsigned long long* dst) {
-  unsigned v = __reduce_add_sync(0xffffffffu, unsigned(c));
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, (unsigned long long)v);
 }
 
 // C = B^T G B, G_ij = (s_0i + s_0j - s_ij)/2 (Thm 3.1 in closed form); Voigt out.

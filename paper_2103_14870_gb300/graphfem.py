@@ -87,6 +87,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_step": (ctypes.c_int, [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int32,
                                    ctypes.POINTER(StepStats)]),
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
+        "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_positions_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
         "gf_velocities_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
         "gf_damage_get": (ctypes.c_int, [P, P, P, ctypes.c_int32]),
@@ -202,6 +203,9 @@ class Mesh:
                                          ctypes.byref(st))
         _check(status)
         return st.as_dict()
+
+    def refine_set(self, inner_rtol: float):
+        _check(load_library().gf_refine_set(self._h, float(inner_rtol)))
 
     def solver_set(self, rtol: float, maxit: int = 10000):
         _check(load_library().gf_solver_set(self._h, float(rtol), int(maxit)))
