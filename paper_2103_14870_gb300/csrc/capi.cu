@@ -350,10 +350,10 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   UP(d.edges, hm.edges, int32_t);
   UP(d.et_ptr, hm.et_ptr, int32_t);
   UP(d.et_tet, hm.et_tet, int32_t);
-  UP(d.nb_off, hm.nbr.group_off, int64_t);
-  UP(d.nb_len, hm.nbr.group_len, int32_t);
-  UP(d.nb_idx, hm.nbr.idx, int32_t);
   if (!mixed) {
+    UP(d.nb_off, hm.nbr.group_off, int64_t);
+    UP(d.nb_len, hm.nbr.group_len, int32_t);
+    UP(d.nb_idx, hm.nbr.idx, int32_t);
     UP(d.slot, hm.slot, int32_t);
     UP(d.rest, hm.rest, double);
     UP(d.nb_w, hm.nbr.w, double);
@@ -363,12 +363,15 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.edge_e0, mxh.edge_e0, float);
     UP(d.mx.np_ptr, mxh.np_ptr, int32_t);
     UP(d.mx.np_pair, mxh.np_pair, int32_t);
-    UP(d.mx.rl_ptr, mxh.rl_ptr, int32_t);
-    UP(d.mx.rl_ent, mxh.rl_ent, uint16_t);
-    UP(d.mx.nb_w32, mxh.nb_w32, float);
+    UP(d.mx.nb_ptr, mxh.nb_ptr, int64_t);
+    UP(d.mx.nb_csr, mxh.nb_csr, int32_t);
+    UP(d.mx.nb_wc, mxh.nb_wc, float);
+    UP(d.mx.sc_ptr, mxh.sc_ptr, int32_t);
+    UP(d.mx.sc_ent, mxh.sc_ent, int32_t);
+    std::vector<float> m32(hm.mass.begin(), hm.mass.end());
+    UP(d.mx.mass32, m32, float);
     std::vector<double> Xv(nodes, nodes + 3 * n_nodes);
     UP(d.mx.X, Xv, double);
-    d.mx.max_deg = mxh.max_deg;
   }
 #undef UP
   {
@@ -394,9 +397,11 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     if ((st = scratch(m, 3 * N, &x.u32)) || (st = scratch(m, 3 * N, &x.v32)) || (st = scratch(m, T, &x.chi32)) ||
         (st = scratch(m, 8 * T, &x.sig_in32)) || (st = scratch(m, 8 * T, &x.sig_bar32)) ||
         (st = scratch(m, 6 * T, &x.sigf32)) || (st = scratch(m, 9 * NB, &x.val32)) ||
+        (st = scratch(m, 104 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
+        (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
         (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
-        (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) || (st = scratch(m, 3 * N, &x.r64)) ||
+        (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) ||
         (st = scratch(m, 1, &x.ir)))
       return fail(st);
   }
@@ -623,7 +628,7 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   }
   { Prof p(m, kPEdge); L += launch_edge_driver32(d, mt, s); }
   { Prof p(m, kPChi); L += launch_tet_chi32(d, mt, m->lut, s); }
-  { Prof p(m, kPAssemble); L += launch_assemble32(d, mt, dt, has_fext, s); }
+  { Prof p(m, kPAssemble); L += launch_assemble32(d, mt, dt, has_fext ? d.f_ext : nullptr, s); }
   IrState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
   init.in_tol2 = m->in_rtol * m->in_rtol;
@@ -823,9 +828,16 @@ gf_status gf_system_get(gf_mesh* m, int32_t* row_ptr, int32_t* col, double* valu
     v32.resize(9 * m->dm.NB);
     GF_CK(cudaMemcpyAsync(v32.data(), m->dm.mx.val32, sizeof(float) * 9 * m->dm.NB, cudaMemcpyDeviceToHost, m->stream));
   }
-  if (rhs) GF_CK(cudaMemcpyAsync(rhs, m->dm.rhs, sizeof(double) * 3 * m->dm.N, cudaMemcpyDeviceToHost, m->stream));
+  std::vector<float> r32;
+  if (rhs && !m->mixed)
+    GF_CK(cudaMemcpyAsync(rhs, m->dm.rhs, sizeof(double) * 3 * m->dm.N, cudaMemcpyDeviceToHost, m->stream));
+  if (rhs && m->mixed) {
+    r32.resize(3 * m->dm.N);
+    GF_CK(cudaMemcpyAsync(r32.data(), m->dm.mx.rhs32, sizeof(float) * 3 * m->dm.N, cudaMemcpyDeviceToHost, m->stream));
+  }
   GF_CK(cudaStreamSynchronize(m->stream));
   for (size_t i = 0; i < v32.size(); ++i) values[i] = double(v32[i]);
+  for (size_t i = 0; i < r32.size(); ++i) rhs[i] = double(r32[i]);
   return GF_OK;
 }
 

@@ -29,6 +29,7 @@ struct IrState {
   double tol2;      // outer rtol^2
   double in_tol2;   // inner rtol^2
   double rz, pq, alpha, beta, in_rr, in_rr0;
+  float alpha32, beta32;
   int32_t done;     // outer converged (or failed)
   int32_t in_done;  // inner converged for this sweep
   int32_t sweeps, in_iters, total_iters, in_maxit, maxit, status;
@@ -42,11 +43,13 @@ struct MixDev {
   const float* edge_e0 = nullptr;     // [NE][3]
   const int32_t* np_ptr = nullptr;    // [N+1]
   const int32_t* np_pair = nullptr;   // [4T]
-  const int32_t* rl_ptr = nullptr;    // [NB+1]
-  const uint16_t* rl_ent = nullptr;   // [16T]
-  const float* nb_w32 = nullptr;      // SELL-32 weights
+  const int64_t* nb_ptr = nullptr;    // [T+1] CSR Eq. 20 lists
+  const int32_t* nb_csr = nullptr;
+  const float* nb_wc = nullptr;
+  const int32_t* sc_ptr = nullptr;    // [NB+1] block slot -> element-block contributions
+  const int32_t* sc_ent = nullptr;    // [16T] (tet << 5) | q | 16 * transposed
+  const float* mass32 = nullptr;      // [N]
   const double* X = nullptr;          // [3N] rest positions
-  int32_t max_deg = 0;
   float* u32 = nullptr;               // [3N] displacement x - X
   float* v32 = nullptr;               // [3N] velocity
   float* chi32 = nullptr;             // [T]
@@ -54,10 +57,13 @@ struct MixDev {
   float* sig_bar32 = nullptr;         // [T][8]
   float* sigf32 = nullptr;            // [T][6]
   float* val32 = nullptr;             // [NB][9]
+  float* ebuf = nullptr;              // [T][104] element blocks + rhs shares (two-phase assembly)
+  float* rhs32 = nullptr;             // [3N]
+  float* rres = nullptr;              // [3N] leading float of the refinement residual
+  float* fext32 = nullptr;            // [3N]
   float* pinv32 = nullptr;            // [N][9]
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;   // [3N]
   float *dv_hi = nullptr, *dv_lo = nullptr;   // [3N] double-float split of dv
-  double* r64 = nullptr;              // [3N]
   IrState* ir = nullptr;
 };
 
@@ -136,7 +142,7 @@ int launch_tet_stress32(const DevMesh& m, const Material& mt, cudaStream_t s);
 int launch_nonlocal32(const DevMesh& m, cudaStream_t s);
 int launch_edge_driver32(const DevMesh& m, const Material& mt, cudaStream_t s);
 int launch_tet_chi32(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s);
-int launch_assemble32(const DevMesh& m, const Material& mt, double dt, bool has_fext, cudaStream_t s);
+int launch_assemble32(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s);
 int launch_ir_residual(const DevMesh& m, int first, cudaStream_t s);
 int launch_ir_inner_init(const DevMesh& m, cudaStream_t s);
 int launch_ir_inner_iter(const DevMesh& m, cudaStream_t s, int which);

@@ -48,18 +48,29 @@ struct NeighbourSell {            // Eq. 20 neighbour lists, 32 tets per group, 
 //   restB [T][12]: B = Dm^-1 row-major (9), pad
 enum Rest32Field : int { kRAE0 = 0, kRAH = 9, kRAV = 30, kRAStride = 32, kRBStride = 12 };
 
-// Extra host data of the mixed-precision path (row-gather assembly).
+// Extra host data of the mixed-precision path (two-phase assembly).
 struct MixedHost {
   std::vector<float> restA;         // [T][kRAStride]
   std::vector<float> restB;         // [T][kRBStride]
   std::vector<float> edge_e0;       // [NE][3] rest edge vectors (b - a)
   std::vector<int32_t> np_ptr;      // [N+1] node -> incident (tet, local node) pairs
   std::vector<int32_t> np_pair;     // [4T] (internal tet << 2) | local node
-  std::vector<int32_t> rl_ptr;      // [NB+1] block -> ordered contribution list
-  std::vector<uint16_t> rl_ent;     // [16T] (pair index within the row << 2) | local b
-  int32_t max_deg = 0;              // max incident tets of a node
-  std::vector<float> nb_w32;        // SELL-32 weights in FP32 (same layout as the FP64 lists)
+  // CSR neighbour lists (one warp per tet): nb_ptr [T+1], nb_csr (neighbour << 0), nb_wc FP32 weights
+  std::vector<int64_t> nb_ptr;
+  std::vector<int32_t> nb_csr;
+  std::vector<float> nb_wc;
+  // two-phase assembly: per block slot, contributions (tet << 5) | code, code = q (0..9) or q + 16
+  // (transposed) for the tet's upper-triangle block q; per node, (tet << 2) | local node
+  std::vector<int32_t> sc_ptr;      // [NB+1]
+  std::vector<int32_t> sc_ent;      // [16T]
 };
+
+// Upper-triangle block order of a tet's 4x4 node blocks: q -> (a, b), a <= b.
+GF_HD constexpr int blk_a(int q) { return q < 4 ? 0 : (q < 7 ? 1 : (q < 9 ? 2 : 3)); }
+GF_HD constexpr int blk_b(int q) { return q < 4 ? q : (q < 7 ? q - 3 : (q < 9 ? q - 5 : 3)); }
+GF_HD constexpr int blk_q(int a, int b) {   // a <= b
+  return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
+}
 
 gf_status build_mixed_host(const double* X, const struct HostMesh& hm, MixedHost& mx, std::string& err);
 

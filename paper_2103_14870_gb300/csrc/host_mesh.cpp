@@ -430,34 +430,55 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
     for (int64_t t = 0; t < T; ++t)
       for (int a = 0; a < 4; ++a) mx.np_pair[pos[hm.tets[4 * t + a]]++] = int32_t((t << 2) | a);
   }
-  mx.max_deg = 0;
-  for (int64_t i = 0; i < N; ++i) mx.max_deg = std::max(mx.max_deg, mx.np_ptr[i + 1] - mx.np_ptr[i]);
-  if (mx.max_deg > 64) {
-    err = "mixed precision supports at most 64 tets per node (found " + std::to_string(mx.max_deg) + ")";
+  // CSR copy of the neighbour lists (from the SELL-32 layout: real entries have w > 0
+  // or are the tet itself)
+  {
+    const NeighbourSell& S = hm.nbr;
+    mx.nb_ptr.assign(T + 1, 0);
+    for (int64_t i = 0; i < T; ++i) {
+      int64_t g = i / 32, l = i % 32;
+      int32_t cnt = 0;
+      for (int32_t k = 0; k < S.group_len[g]; ++k) {
+        int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
+        if (S.w[o] > 0.0) cnt++;
+      }
+      mx.nb_ptr[i + 1] = mx.nb_ptr[i] + cnt;
+    }
+    mx.nb_csr.resize(mx.nb_ptr[T]);
+    mx.nb_wc.resize(mx.nb_ptr[T]);
+    for (int64_t i = 0; i < T; ++i) {
+      int64_t g = i / 32, l = i % 32, p = mx.nb_ptr[i];
+      for (int32_t k = 0; k < S.group_len[g]; ++k) {
+        int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
+        if (S.w[o] > 0.0) {
+          mx.nb_csr[p] = S.idx[o];
+          mx.nb_wc[p] = float(S.w[o]);
+          ++p;
+        }
+      }
+    }
+  }
+  // block slot -> (tet, upper-triangle block, transposed) contributions, ascending tet
+  mx.sc_ptr.assign(hm.n_blocks + 1, 0);
+  for (int64_t t = 0; t < T; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) mx.sc_ptr[hm.slot[16 * t + 4 * a + b] + 1]++;
+  for (int64_t b = 0; b < hm.n_blocks; ++b) mx.sc_ptr[b + 1] += mx.sc_ptr[b];
+  mx.sc_ent.resize(16 * T);
+  {
+    std::vector<int32_t> pos(mx.sc_ptr.begin(), mx.sc_ptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          const int q = a <= b ? blk_q(a, b) : blk_q(b, a);
+          const int code = a <= b ? q : q + 16;
+          mx.sc_ent[pos[hm.slot[16 * t + 4 * a + b]]++] = int32_t((t << 5) | code);
+        }
+  }
+  if (T >= (int64_t(1) << 26)) {
+    err = "mixed precision supports at most 2^26 tets";
     return GF_UNSUPPORTED;
   }
-  // ordered contribution lists per block: entry (k << 2) | b for pair k of the row's node
-  mx.rl_ptr.assign(hm.n_blocks + 1, 0);
-  for (int64_t i = 0; i < N; ++i)
-    for (int32_t k = mx.np_ptr[i]; k < mx.np_ptr[i + 1]; ++k) {
-      int64_t t = mx.np_pair[k] >> 2;
-      int a = mx.np_pair[k] & 3;
-      for (int b = 0; b < 4; ++b) mx.rl_ptr[hm.slot[16 * t + 4 * a + b] + 1]++;
-    }
-  for (int64_t b = 0; b < hm.n_blocks; ++b) mx.rl_ptr[b + 1] += mx.rl_ptr[b];
-  mx.rl_ent.resize(16 * T);
-  {
-    std::vector<int32_t> pos(mx.rl_ptr.begin(), mx.rl_ptr.end() - 1);
-    for (int64_t i = 0; i < N; ++i)
-      for (int32_t k = mx.np_ptr[i]; k < mx.np_ptr[i + 1]; ++k) {
-        int64_t t = mx.np_pair[k] >> 2;
-        int a = mx.np_pair[k] & 3;
-        for (int b = 0; b < 4; ++b)
-          mx.rl_ent[pos[hm.slot[16 * t + 4 * a + b]]++] = uint16_t(((k - mx.np_ptr[i]) << 2) | b);
-      }
-  }
-  mx.nb_w32.resize(hm.nbr.w.size());
-  for (size_t i = 0; i < hm.nbr.w.size(); ++i) mx.nb_w32[i] = float(hm.nbr.w[i]);
   return GF_OK;
 }
 

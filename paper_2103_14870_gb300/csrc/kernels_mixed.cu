@@ -16,8 +16,13 @@ namespace gf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kAsmWarps = 4;        // warps per CTA of the row-gather assembly
-constexpr int kStage = 40;          // floats staged per (node, tet) pair: 4 blocks + rhs + pad
+
+// one 32-byte row in a single 256-bit load (sm_100+; the row must be 32-byte aligned)
+__device__ __forceinline__ void ld8f(const float* p, float o[8]) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+      : "l"(p));
+}
 
 __device__ __forceinline__ void ld3f(const float* __restrict__ a, int64_t i, float o[3]) {
   const float* p = a + 3 * i;
@@ -130,35 +135,37 @@ __global__ void __launch_bounds__(kThreads) k_tet_stress32(DevMesh m, float lam,
     sf[k] = normal_stress32(e[k], e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2], S, kappa);
 }
 
-// Eq. 20 sum in FP32 with compensated (Kahan) accumulation.
+// Eq. 20 sum in FP32: one warp per tet over its CSR neighbour list (coalesced
+// index and weight loads; the gathered 32-byte stress rows of a tet's
+// neighbours come from short runs of consecutive tets), then a fixed-order
+// warp reduction (deterministic).
 __global__ void __launch_bounds__(kThreads) k_nonlocal32(DevMesh m) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= m.T) return;
-  const int64_t g = t >> 5;
-  const int lane = int(t & 31);
-  const int64_t off = m.nb_off[g] + lane;
-  const int len = m.nb_len[g];
-  float acc[6] = {0, 0, 0, 0, 0, 0}, cmp[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = 0; k < len; ++k) {
-    const int j = __ldg(m.nb_idx + off + 32 * int64_t(k));
-    const float w = __ldg(m.mx.nb_w32 + off + 32 * int64_t(k));
-    const float4* sj = reinterpret_cast<const float4*>(m.mx.sig_in32 + 8 * int64_t(j));
-    const float4 a = sj[0], b = sj[1];
-    const float v[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t t = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; t < m.T; t += nw) {
+    const int64_t beg = m.mx.nb_ptr[t], end = m.mx.nb_ptr[t + 1];
+    float acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t p = beg + lane; p < end; p += 32) {
+      const int j = __ldg(m.mx.nb_csr + p);
+      const float w = __ldg(m.mx.nb_wc + p);
+      float sj[8];
+      ld8f(m.mx.sig_in32 + 8 * int64_t(j), sj);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const float y = w * v[q] - cmp[q];
-      const float s = acc[q] + y;
-      cmp[q] = (s - acc[q]) - y;
-      acc[q] = s;
+      for (int q = 0; q < 6; ++q) acc[q] += w * sj[q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0) {
+      float4* o = reinterpret_cast<float4*>(m.mx.sig_bar32 + 8 * t);
+      o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      o[1] = make_float4(acc[4], acc[5], 0.f, 0.f);
     }
   }
-  float4* o = reinterpret_cast<float4*>(m.mx.sig_bar32 + 8 * t);
-  o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-  o[1] = make_float4(acc[4], acc[5], 0.f, 0.f);
 }
 
-__global__ void __launch_bounds__(kThreads) k_edge_driver32(DevMesh m, float kappa, double young, int stress_mode,
+__global__ void __launch_bounds__(kThreads) k_edge_driver32(DevMesh m, float kappa, float inv_young, int stress_mode,
                                                             double threshold) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   unsigned long long nb = 0, nn = 0;
@@ -172,12 +179,11 @@ __global__ void __launch_bounds__(kThreads) k_edge_driver32(DevMesh m, float kap
     const float s = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
     float mx = -INFINITY;
     for (int p = m.et_ptr[i]; p < m.et_ptr[i + 1]; ++p) {
-      const float4* sb = reinterpret_cast<const float4*>(m.mx.sig_bar32 + 8 * int64_t(m.et_tet[p]));
-      const float4 s0 = sb[0], s1 = sb[1];
-      const float S[6] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y};
+      float S[8];
+      ld8f(m.mx.sig_bar32 + 8 * int64_t(m.et_tet[p]), S);
       mx = fmaxf(mx, normal_stress32(e, s, S, kappa));
     }
-    const double d = stress_mode ? double(mx) : double(mx) / young;
+    const double d = double(stress_mode ? mx : mx * inv_young);
     m.driver[i] = d;
     const uint8_t old = m.labels[i];
     const uint8_t now = (old || d >= threshold) ? 1 : 0;   // threshold test in FP64
@@ -219,153 +225,170 @@ __global__ void __launch_bounds__(kThreads) k_tet_chi32(DevMesh m, float young, 
 }
 
 // ---------------------------------------------------------------------------
-// Row-gather assembly: one warp per node row, no colours, no atomics.
-// Each lane takes one (tet, local node a) pair of the row's node, evaluates the
-// four 3x3 blocks (a, b) and the rhs share of that tet, and stages them in
-// shared memory; the lanes then sum the staged blocks into the row's slots in
-// a fixed, precomputed order (deterministic), add the lumped mass and the
-// external force, and lane 0 inverts the diagonal block (block Jacobi).
+// Two-phase assembly, no colours and no atomics.
+// Phase 1 (k_elem32, one thread per tet): the tet's ten upper-triangle 3x3
+// blocks (a <= b) of (dt beta + dt^2) chi k_e and its four nodal rhs shares
+// dt chi (f_a - (beta + dt) (k_e v)_a), written to a per-tet row of kElemW floats.
+// Phase 2 (k_gather32, one warp per node row): lane p sums the contributions of
+// block slot p in a fixed, precomputed order (transposing lower blocks), adds
+// the lumped mass, and lane 0 inverts the diagonal block (block Jacobi); lanes
+// 0..2 sum the node's rhs shares and add the external and damping terms.
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kAsmWarps * 32) k_assemble32(DevMesh m, float sKv, float cv, float dtf, double dt,
-                                                              double alpha, const double* f_ext) {
-  extern __shared__ float smem[];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = blockIdx.x * int64_t(kAsmWarps) + wib;
-  if (i >= m.N) return;                              // whole warp leaves together
+constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad (16-byte rows)
+
+__global__ void __launch_bounds__(128) k_elem32(DevMesh m, float sKv, float cv, float dtf) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
   const MixDev& x = m.mx;
-  float* st = smem + int64_t(wib) * (x.max_deg * kStage + 12);
-  float* diag = st + x.max_deg * kStage;
-  const int beg = x.np_ptr[i], deg = x.np_ptr[i + 1] - beg;
-  for (int k = lane; k < deg; k += 32) {
-    float* o = st + k * kStage;
-    const int pr = x.np_pair[beg + k];
-    const int64_t t = pr >> 2;
-    const int a = pr & 3;
-    const float chi = x.chi32[t];
-    if (chi == 0.f) {
+  float4* out = reinterpret_cast<float4*>(x.ebuf + kElemW * t);
+  const float chi = x.chi32[t];
+  if (chi == 0.f) {
 #pragma unroll
-      for (int q = 0; q < 39; ++q) o[q] = 0.f;
-      continue;
-    }
-    const int4 n = m.tets[t];
-    const int nid[4] = {n.x, n.y, n.z, n.w};
-    float du[4][3], vv[4][3];
+    for (int q = 0; q < kElemW / 4; ++q) out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const int4 n = m.tets[t];
+  const int nid[4] = {n.x, n.y, n.z, n.w};
+  float du[4][3], vv[4][3];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      ld3f(x.u32, nid[b], du[b]);
-      ld3f(x.v32, nid[b], vv[b]);
-    }
-    float va[3];   // velocity of local node a, by selects (no runtime-indexed arrays)
+  for (int b = 0; b < 4; ++b) {
+    ld3f(x.u32, nid[b], du[b]);
+    ld3f(x.v32, nid[b], vv[b]);
+  }
+  float A[32];
+  load_restA(x.restA, t, A);
+  float E0[6][3], e[6][3], ds[6];
+  rest_edges(A, E0);
+  edge_state(E0, du, e, ds);
+  const float* H = A + kRAH;
+  auto h = [&](int k, int l) { return k <= l ? H[tri6(k, l)] : H[tri6(l, k)]; };
+  float g[6];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) va[c] = a == 0 ? vv[0][c] : (a == 1 ? vv[1][c] : (a == 2 ? vv[2][c] : vv[3][c]));
-    float A[32];
-    load_restA(x.restA, t, A);
-    float E0[6][3], e[6][3], ds[6];
-    rest_edges(A, E0);
-    edge_state(E0, du, e, ds);
-    const float* H = A + kRAH;
-    auto h = [&](int k, int l) { return k <= l ? H[tri6(k, l)] : H[tri6(l, k)]; };
-    float g[6];
+  for (int k = 0; k < 6; ++k) {
+    float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      float s = 0.f;
+    for (int l = 0; l < 6; ++l) s += h(k, l) * ds[l];
+    g[k] = s;
+  }
+  // Y_b[k][c] = sum_{l in b} H_kl sgn_lb e_l[c]  (sgn = -1 if b is the first node of l)
+  float o[kElemW];
+  float Kv[4][3] = {};
 #pragma unroll
-      for (int l = 0; l < 6; ++l) s += h(k, l) * ds[l];
-      g[k] = s;
-    }
-    // w_k = sgn_ka e_k for the edges that contain a (-(x_other - x_a)), 0 otherwise
-    float w[6][3];
+  for (int b = 0; b < 4; ++b) {
+    float Y[6][3];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const float sg = (a == edge_a(k)) ? -1.f : ((a == edge_b(k)) ? 1.f : 0.f);
+    for (int k = 0; k < 6; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) w[k][c] = sg * e[k][c];
-    }
-    // W[r][l] = sum_k w_k[r] H_kl
-    float W[3][6];
+      for (int c = 0; c < 3; ++c) {
+        float y = 0.f;
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int l = 0; l < 6; ++l) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s += w[k][r] * h(k, l);
-        W[r][l] = s;
+        for (int l = 0; l < 6; ++l) {
+          if (edge_a(l) != b && edge_b(l) != b) continue;
+          y += (edge_a(l) == b ? -h(k, l) : h(k, l)) * e[l][c];
+        }
+        Y[k][c] = y;
       }
-    float Kv[3] = {0.f, 0.f, 0.f};
-    const float sk = sKv * chi;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int a = 0; a <= b; ++a) {
       float blk[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float s = 0.f;
+          float v = 0.f;
 #pragma unroll
           for (int k = 0; k < 6; ++k) {
-            if (edge_a(k) != b && edge_b(k) != b) continue;
-            const float sgb = (edge_a(k) == b) ? -1.f : 1.f;
-            s += W[r][k] * sgb * e[k][c];
+            if (edge_a(k) != a && edge_b(k) != a) continue;
+            v += (edge_a(k) == a ? -e[k][r] : e[k][r]) * Y[k][c];
           }
-          blk[r][c] = 4.f * s;
+          blk[r][c] = 4.f * v;
         }
-      // geometric part: sum_k g_k d2 s_k / dx_a dx_b
       float geo = 0.f;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        if (edge_a(k) != b && edge_b(k) != b) continue;
-        const int other = (edge_a(k) == b) ? edge_b(k) : edge_a(k);
-        geo += (a == b) ? 2.f * g[k] : ((a == other) ? -2.f * g[k] : 0.f);
+        const bool ina = edge_a(k) == a || edge_b(k) == a, inb = edge_a(k) == b || edge_b(k) == b;
+        if (a == b && ina) geo += 2.f * g[k];
+        if (a != b && ina && inb) geo -= 2.f * g[k];
       }
       blk[0][0] += geo;
       blk[1][1] += geo;
       blk[2][2] += geo;
-      const float dvb[3] = {vv[b][0] - va[0], vv[b][1] - va[1], vv[b][2] - va[2]};
+      // K v with relative velocities (rigid translations are in the null space)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) Kv[r] += blk[r][0] * dvb[0] + blk[r][1] * dvb[1] + blk[r][2] * dvb[2];
+      for (int r = 0; r < 3; ++r) {
+        Kv[a][r] += blk[r][0] * (vv[b][0] - vv[a][0]) + blk[r][1] * (vv[b][1] - vv[a][1]) +
+                    blk[r][2] * (vv[b][2] - vv[a][2]);
+        if (a != b)
+          Kv[b][r] += blk[0][r] * (vv[a][0] - vv[b][0]) + blk[1][r] * (vv[a][1] - vv[b][1]) +
+                      blk[2][r] * (vv[a][2] - vv[b][2]);
+      }
+      const int q = blk_q(a, b);
+      const float sk = sKv * chi;
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) o[9 * b + 3 * r + c] = sk * blk[r][c];
+        for (int c = 0; c < 3; ++c) o[9 * q + 3 * r + c] = sk * blk[r][c];
     }
-    // rhs share of node a: dt chi (f_a - (beta + dt) K v), f_a = -2 sum_k g_k w_k
+  }
+  // rhs shares: dt chi (f_a - cv (K v)_a), f_a = -2 sum_{k in a} sgn_ka g_k e_k
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       float f = 0.f;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) f += g[k] * w[k][r];
-      o[36 + r] = dtf * chi * (-2.f * f - cv * Kv[r]);
+      for (int k = 0; k < 6; ++k) {
+        if (edge_a(k) == a) f += 2.f * g[k] * e[k][r];
+        if (edge_b(k) == a) f -= 2.f * g[k] * e[k][r];
+      }
+      o[90 + 3 * a + r] = dtf * chi * (f - cv * Kv[a][r]);
     }
-  }
-  __syncwarp();
+  o[102] = 0.f;
+  o[103] = 0.f;
+#pragma unroll
+  for (int q = 0; q < kElemW / 4; ++q) out[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+}
+
+__global__ void __launch_bounds__(256) k_gather32(DevMesh m, float dtf, float alphaf, float cmf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (i >= m.N) return;                               // whole warp leaves together
+  __shared__ float dg[8][9];
+  const int wib = threadIdx.x >> 5;
+  const MixDev& x = m.mx;
   const int rb = m.row_ptr[i], rl = m.row_ptr[i + 1] - rb;
   const int dslot = m.diag_blk[i];
-  const float cm = float((1.0 + dt * alpha) * m.mass[i]);
-  for (int o = lane; o < rl * 9; o += 32) {
-    const int p = o / 9, ee = o - 9 * p;
+  const float mi = x.mass32[i];
+  // lane o takes entry (r, c) = o % 9 of block slot rb + o / 9: the lanes of one
+  // pass read 3-4 whole element blocks per request
+  for (int o = lane; o < 9 * rl; o += 32) {
+    const int p = o / 9, e = o - 9 * p;
     const int slot = rb + p;
+    const int et = 3 * (e % 3) + e / 3;          // entry of the transposed block
     float acc = 0.f;
-    for (int q = x.rl_ptr[slot]; q < x.rl_ptr[slot + 1]; ++q) {
-      const int ent = x.rl_ent[q];
-      acc += st[(ent >> 2) * kStage + 9 * (ent & 3) + ee];
+    for (int c = x.sc_ptr[slot]; c < x.sc_ptr[slot + 1]; ++c) {
+      const int ent = x.sc_ent[c];
+      acc += x.ebuf[kElemW * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
     }
     if (slot == dslot) {
-      if (ee == 0 || ee == 4 || ee == 8) acc += cm;
-      diag[ee] = acc;
+      if (e == 0 || e == 4 || e == 8) acc += cmf * mi;
+      dg[wib][e] = acc;
     }
-    x.val32[9 * int64_t(slot) + ee] = acc;
+    x.val32[9 * int64_t(slot) + e] = acc;
   }
   if (lane < 3) {
     float acc = 0.f;
-    for (int k = 0; k < deg; ++k) acc += st[k * kStage + 36 + lane];
-    const double fe = f_ext ? f_ext[3 * i + lane] : 0.0;
-    m.rhs[3 * i + lane] = double(acc) + dt * (fe - alpha * m.mass[i] * m.v[3 * i + lane]);
+    for (int k = x.np_ptr[i]; k < x.np_ptr[i + 1]; ++k) {
+      const int pr = x.np_pair[k];
+      acc += x.ebuf[kElemW * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
+    }
+    const float fe = x.fext32 ? x.fext32[3 * i + lane] : 0.f;
+    x.rhs32[3 * i + lane] = acc + dtf * (fe - alphaf * mi * x.v32[3 * i + lane]);
   }
   __syncwarp();
   if (lane == 0) {
-    const float* d = diag;
+    const float* d = dg[wib];
     const float c00 = d[4] * d[8] - d[5] * d[7], c01 = d[2] * d[7] - d[1] * d[8], c02 = d[1] * d[5] - d[2] * d[4];
     const float c10 = d[5] * d[6] - d[3] * d[8], c11 = d[0] * d[8] - d[2] * d[6], c12 = d[2] * d[3] - d[0] * d[5];
     const float c20 = d[3] * d[7] - d[4] * d[6], c21 = d[1] * d[6] - d[0] * d[7], c22 = d[0] * d[4] - d[1] * d[3];
@@ -375,6 +398,12 @@ __global__ void __launch_bounds__(kAsmWarps * 32) k_assemble32(DevMesh m, float 
     pi[3] = c10 * id; pi[4] = c11 * id; pi[5] = c12 * id;
     pi[6] = c20 * id; pi[7] = c21 * id; pi[8] = c22 * id;
   }
+}
+
+// f_ext in FP32 for the gather (one conversion per entry)
+__global__ void __launch_bounds__(kThreads) k_fext32(DevMesh m, const double* f) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < 3 * m.N) m.mx.fext32[i] = float(f[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -399,19 +428,93 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float p, float pe) 
   lo = e - (hi - s);
 }
 
-// r64 = b - A32 dv on free rows with A32 x dv formed in double-float on the FP32
-// pipe (dv = dv_hi + dv_lo); half a warp per block row (lane j takes blocks
-// j, j+16, ...: coalesced block loads), then a 16-lane double-float reduction.
-// ||r64||^2 accumulates in FP64.
+// Double-float (float pair) warp and grid reductions: ~48-bit sums on the FP32
+// pipe.  The FP64 pipe of GB300 costs a full 64-cycle slot per warp
+// instruction even with one active lane, so the refinement keeps FP64-level
+// accuracy with float pairs and converts to double only for the final scalars.
+__device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, oh, ol);
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_reduce_df(float (&hi)[NV], float (&lo)[NV], double* partials, unsigned* ticket,
+                                               double (&out)[NV]) {
+  __shared__ float sh[NV][2][32];
+  __shared__ bool last;
+  float2* part = reinterpret_cast<float2*>(partials);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    df_warp_sum(hi[i], lo[i]);
+    if (lane == 0) {
+      sh[i][0][wid] = hi[i];
+      sh[i][1][wid] = lo[i];
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      float h = lane < nw ? sh[i][0][lane] : 0.f, l = lane < nw ? sh[i][1][lane] : 0.f;
+      df_warp_sum(h, l);
+      if (lane == 0) part[blockIdx.x * NV + i] = make_float2(h, l);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float h = 0.f, l = 0.f;
+    for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) {
+      const float2 v = __ldcg(&part[j * NV + i]);
+      df_add(h, l, v.x, v.y);
+    }
+    df_warp_sum(h, l);
+    __syncthreads();
+    if (lane == 0) {
+      sh[i][0][wid] = h;
+      sh[i][1][wid] = l;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      h = lane < nw ? sh[i][0][lane] : 0.f;
+      l = lane < nw ? sh[i][1][lane] : 0.f;
+      df_warp_sum(h, l);
+      if (lane == 0) out[i] = double(h) + double(l);
+    }
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+__device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float b) {
+  float p, pe;
+  two_prod(a, b, p, pe);
+  df_add(hi, lo, p, pe);
+}
+
+// r = b - A32 dv on free rows, with A32 dv formed in double-float (dv = dv_hi +
+// dv_lo) and b - A dv in double-float; half a warp per block row (lane j takes
+// blocks j, j+16, ...), then a 16-lane double-float reduction.  The inner
+// solve's right-hand side is the leading float of r; ||r||^2 accumulates in
+// double-float.
 __global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, int first) {
   IrState* S = m.mx.ir;
   if (!first && (S->done || !S->applied)) return;   // no new correction yet: nothing to check
   const MixDev& x = m.mx;
   const int j16 = threadIdx.x & 15;
-  // the two half-warps of a warp may run different trip counts at the tail:
-  // shuffles name only the own half-warp
   const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
-  double v[1] = {0.0};
+  float nh_[1] = {0.f}, nl_[1] = {0.f};
   const int64_t nh = (int64_t(gridDim.x) * blockDim.x) >> 4;
   for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
     float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
@@ -445,14 +548,19 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, int first) 
     if (j16 == 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double r = fixed ? 0.0 : m.rhs[3 * i + c] - (double(hi[c]) + double(lo[c]));
-        x.r64[3 * i + c] = r;
-        v[0] += r * r;
+        float rh = 0.f, rl = 0.f;
+        if (!fixed) {
+          rh = x.rhs32[3 * i + c];
+          df_add(rh, rl, -hi[c], -lo[c]);
+        }
+        x.rres[3 * i + c] = rh;
+        df_acc_prod(nh_[0], nl_[0], rh, rh);
+        df_add(nh_[0], nl_[0], 2.f * rh * rl, 0.f);
       }
     }
   }
   double out[1];
-  if (grid_reduce<1>(v, m.partials, m.tickets + 4, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<1>(nh_, nl_, m.partials, m.tickets + 4, out) && threadIdx.x == 0) {
     if (first) {
       S->bb = out[0];
       S->sweeps = 0;
@@ -473,18 +581,18 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, int first) 
   }
 }
 
-// inner PCG start: r32 = float(r64), z = P r, p = z, d = 0 (only after a fresh
-// residual; otherwise the current inner solve simply continues)
+// inner PCG start (only after a fresh residual; otherwise the current inner
+// solve continues): r32 = r, z = P r, p = z, d = 0
 __global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m) {
   IrState* S = m.mx.ir;
   if (S->done || !S->applied) return;
   const MixDev& x = m.mx;
-  double v[1] = {0.0};
+  float h[1] = {0.f}, l[1] = {0.f};
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
     float r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
     if (!m.pinned[i]) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r[c] = float(x.r64[3 * i + c]);
+      for (int c = 0; c < 3; ++c) r[c] = x.rres[3 * i + c];
       const float* pi = x.pinv32 + 9 * i;
 #pragma unroll
       for (int c = 0; c < 3; ++c) z[c] = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
@@ -495,11 +603,11 @@ __global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m) {
       x.z32[3 * i + c] = z[c];
       x.p32[3 * i + c] = z[c];
       x.d32[3 * i + c] = 0.f;
-      v[0] += double(r[c] * z[c]);
+      df_acc_prod(h[0], l[0], r[c], z[c]);
     }
   }
   double out[1];
-  if (grid_reduce<1>(v, m.partials, m.tickets + 5, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 5, out) && threadIdx.x == 0) {
     S->rz = out[0];
     S->in_rr0 = S->rr;
     S->in_iters = 0;
@@ -508,16 +616,14 @@ __global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m) {
   }
 }
 
-// q = A32 p with half a warp per block row (coalesced block loads), p . q in FP64
+// q = A32 p with half a warp per block row (coalesced block loads), p . q in double-float
 __global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m) {
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
   const MixDev& x = m.mx;
   const int j16 = threadIdx.x & 15;
-  // the two half-warps of a warp may run different trip counts at the tail:
-  // shuffles name only the own half-warp
   const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
-  double v[1] = {0.0};
+  float h[1] = {0.f}, l[1] = {0.f};
   const int64_t nh = (int64_t(gridDim.x) * blockDim.x) >> 4;
   for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
@@ -540,12 +646,12 @@ __global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         x.q32[3 * i + c] = y[c];
-        v[0] += double(x.p32[3 * i + c] * y[c]);
+        df_acc_prod(h[0], l[0], x.p32[3 * i + c], y[c]);
       }
     }
   }
   double out[1];
-  if (grid_reduce<1>(v, m.partials, m.tickets + 6, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 6, out) && threadIdx.x == 0) {
     S->pq = out[0];
     if (!(out[0] > 0.0)) {
       if (!isfinite(out[0])) {
@@ -555,9 +661,10 @@ __global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m) {
         S->status = GF_CG_BREAKDOWN;
         S->done = 1;
       }
-      S->in_done = 1;   // lost positive definiteness in FP32: hand back to the FP64 refinement
+      S->in_done = 1;   // lost positive definiteness in FP32: hand back to the refinement
     } else {
       S->alpha = S->rz / out[0];
+      S->alpha32 = float(S->alpha);
     }
   }
 }
@@ -566,8 +673,8 @@ __global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m) {
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
   const MixDev& x = m.mx;
-  const float alpha = float(S->alpha);
-  double v[2] = {0.0, 0.0};
+  const float alpha = S->alpha32;
+  float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
     if (m.pinned[i]) continue;
     float r[3];
@@ -582,15 +689,16 @@ __global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m) {
     for (int c = 0; c < 3; ++c) {
       const float z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
       x.z32[3 * i + c] = z;
-      v[0] += double(r[c] * z);
-      v[1] += double(r[c]) * double(r[c]);
+      df_acc_prod(h[0], l[0], r[c], z);
+      df_acc_prod(h[1], l[1], r[c], r[c]);
     }
   }
   double out[2];
-  if (grid_reduce<2>(v, m.partials, m.tickets + 7, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<2>(h, l, m.partials, m.tickets + 7, out) && threadIdx.x == 0) {
     S->in_iters += 1;
     S->total_iters += 1;
     S->beta = out[0] / S->rz;
+    S->beta32 = float(S->beta);
     S->rz = out[0];
     S->in_rr = out[1];
     if (!(out[1] > S->in_tol2 * S->in_rr0) || S->in_iters >= S->in_maxit || S->total_iters >= S->maxit)
@@ -601,32 +709,32 @@ __global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m) {
 __global__ void __launch_bounds__(kThreads) k_ir_p(DevMesh m) {
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
-  const float beta = float(S->beta);
+  const float beta = S->beta32;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(gridDim.x) * blockDim.x)
     m.mx.p32[i] = m.mx.z32[i] + beta * m.mx.p32[i];
 }
 
-// dv += d (free rows) once the inner solve has finished, and refresh the
-// double-float split of dv
+// dv += d on free rows, kept as a float pair (dv_hi + dv_lo) on the FP32 pipe
 __global__ void __launch_bounds__(kThreads) k_ir_apply(DevMesh m) {
   IrState* S = m.mx.ir;
   if (S->done || !S->in_done || S->applied) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) S->applied = 1;   // read by the next kernels only
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(gridDim.x) * blockDim.x) {
-    double d = m.dv[i];
-    if (!m.pinned[i / 3]) d += double(m.mx.d32[i]);
-    m.dv[i] = d;
-    const float hi = float(d);
+    if (m.pinned[i / 3]) continue;
+    float hi = m.mx.dv_hi[i], lo = m.mx.dv_lo[i];
+    df_add(hi, lo, m.mx.d32[i], 0.f);
     m.mx.dv_hi[i] = hi;
-    m.mx.dv_lo[i] = float(d - double(hi));
+    m.mx.dv_lo[i] = lo;
   }
 }
 
-// v += dv, x += dt v; refresh the FP32 copies of u = x - X and v
+// v += dv (dv = dv_hi + dv_lo), x += dt v; refresh the FP32 copies of u = x - X and v
 __global__ void __launch_bounds__(kThreads) k_integrate32(DevMesh m, double dt) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i >= 3 * m.N) return;
-  const double v = m.v[i] + m.dv[i];
+  const double dv = double(m.mx.dv_hi[i]) + double(m.mx.dv_lo[i]);
+  m.dv[i] = dv;
+  const double v = m.v[i] + dv;
   m.v[i] = v;
   const double xn = m.x[i] + dt * v;
   m.x[i] = xn;
@@ -634,7 +742,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate32(DevMesh m, double dt) 
   m.mx.v32[i] = float(v);
 }
 
-// FP32 copies after a state change; also the double-float split of dv
+// FP32 copies after a state change; also the float-pair split of dv
 __global__ void __launch_bounds__(kThreads) k_refresh32(DevMesh m) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i >= 3 * m.N) return;
@@ -652,6 +760,12 @@ __global__ void k_chi_to32(DevMesh m) {
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
+// reducing kernels of the refinement: at most 4 CTAs per SM (grid-stride loops),
+// so the final double-float pass over the partials stays short
+inline unsigned ir_grid(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  return unsigned(b < 1 ? 1 : (b > 4 * 152 ? 4 * 152 : b));
+}
 inline unsigned reduce_grid(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   return unsigned(b < 1 ? 1 : (b > kMaxPartials ? kMaxPartials : b));
@@ -665,40 +779,48 @@ int launch_tet_stress32(const DevMesh& m, const Material& mt, cudaStream_t s) {
   return 1;
 }
 int launch_nonlocal32(const DevMesh& m, cudaStream_t s) {
-  k_nonlocal32<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m);
+  k_nonlocal32<<<blocks_for(32 * m.T, kThreads), kThreads, 0, s>>>(m);
   return 1;
 }
 int launch_edge_driver32(const DevMesh& m, const Material& mt, cudaStream_t s) {
-  k_edge_driver32<<<blocks_for(m.NE, kThreads), kThreads, 0, s>>>(m, float(mt.kappa), mt.young, mt.driver_stress,
-                                                                 mt.threshold);
+  k_edge_driver32<<<blocks_for(m.NE, kThreads), kThreads, 0, s>>>(m, float(mt.kappa), float(1.0 / mt.young),
+                                                                 mt.driver_stress, mt.threshold);
   return 1;
 }
 int launch_tet_chi32(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s) {
   k_tet_chi32<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, float(mt.young), lut);
   return 1;
 }
-int launch_assemble32(const DevMesh& m, const Material& mt, double dt, bool has_fext, cudaStream_t s) {
-  const size_t smem = size_t(kAsmWarps) * (m.mx.max_deg * kStage + 12) * sizeof(float);
-  k_assemble32<<<unsigned((m.N + kAsmWarps - 1) / kAsmWarps), kAsmWarps * 32, smem, s>>>(
-      m, float(dt * mt.beta + dt * dt), float(mt.beta + dt), float(dt), dt, mt.alpha, has_fext ? m.f_ext : nullptr);
-  return 1;
+int launch_assemble32(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s) {
+  int n = 0;
+  k_elem32<<<blocks_for(m.T, 128), 128, 0, s>>>(m, float(dt * mt.beta + dt * dt), float(mt.beta + dt), float(dt));
+  ++n;
+  DevMesh v = m;
+  if (f_ext) {
+    k_fext32<<<blocks_for(3 * m.N, kThreads), kThreads, 0, s>>>(m, f_ext);
+    ++n;
+  } else {
+    v.mx.fext32 = nullptr;
+  }
+  k_gather32<<<blocks_for(32 * m.N, 256), 256, 0, s>>>(v, float(dt), float(mt.alpha), float(1.0 + dt * mt.alpha));
+  return n + 1;
 }
 int launch_ir_residual(const DevMesh& m, int first, cudaStream_t s) {
-  k_ir_residual<<<reduce_grid(16 * m.N), kThreads, 0, s>>>(m, first);
+  k_ir_residual<<<ir_grid(16 * m.N), kThreads, 0, s>>>(m, first);
   return 1;
 }
 int launch_ir_inner_init(const DevMesh& m, cudaStream_t s) {
-  k_ir_inner_init<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
+  k_ir_inner_init<<<ir_grid(m.N), kThreads, 0, s>>>(m);
   return 1;
 }
 int launch_ir_inner_iter(const DevMesh& m, cudaStream_t s, int which) {
-  if (which == 0) k_ir_spmv<<<reduce_grid(16 * m.N), kThreads, 0, s>>>(m);
-  else if (which == 1) k_ir_update<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
-  else k_ir_p<<<reduce_grid(3 * m.N), kThreads, 0, s>>>(m);
+  if (which == 0) k_ir_spmv<<<ir_grid(16 * m.N), kThreads, 0, s>>>(m);
+  else if (which == 1) k_ir_update<<<ir_grid(m.N), kThreads, 0, s>>>(m);
+  else k_ir_p<<<ir_grid(3 * m.N), kThreads, 0, s>>>(m);
   return 1;
 }
 int launch_ir_apply(const DevMesh& m, cudaStream_t s) {
-  k_ir_apply<<<reduce_grid(3 * m.N), kThreads, 0, s>>>(m);
+  k_ir_apply<<<ir_grid(3 * m.N), kThreads, 0, s>>>(m);
   return 1;
 }
 int launch_integrate32(const DevMesh& m, double dt, cudaStream_t s) {
