@@ -59,6 +59,7 @@ enum { GF_MEM_HOST = 0, GF_MEM_DEVICE = 1 };
 enum { GF_DRIVER_STRAIN = 0, GF_DRIVER_STRESS = 1 };
 enum { GF_FP64 = 0, GF_MIXED = 1 };
 enum { GF_PRECOND_BJACOBI = 0 };
+enum { GF_ASSEMBLY_GATHER = 0, GF_ASSEMBLY_COLOUR = 1 };
 
 /* Material and damage parameters (Sec. 3.1, 3.3, 5.2). */
 typedef struct gf_material {
@@ -154,6 +155,18 @@ gf_status gf_state_set(gf_mesh* mesh, const double* x, const double* v, const ui
  * applied with the last iterate and returns GF_CG_BREAKDOWN / GF_CG_MAXITER. */
 gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
                   const double* pinned_vel, int32_t mem, gf_step_stats* stats);
+
+/* Execution schedule of a mesh (no effect on results beyond rounding order).
+ * assembly: GF_ASSEMBLY_GATHER (default) computes every tet's blocks once into
+ * an element buffer and gathers each matrix row in a fixed order (one launch
+ * per phase); GF_ASSEMBLY_COLOUR scatters tet by tet in colour order (no two
+ * tets of a colour share a node), one launch per colour (GF_FP64 only). */
+typedef struct gf_tuning {
+  int32_t assembly;
+  int32_t reserved[7];   /* set to 0 */
+} gf_tuning;
+gf_status gf_tuning_set(gf_mesh* mesh, const gf_tuning* tuning);
+gf_status gf_tuning_get(const gf_mesh* mesh, gf_tuning* tuning);
 
 /* GF_MIXED: relative tolerance of each inner FP32 PCG solve of the FP64
  * iterative refinement (default 1e-4; 0 < inner_rtol < 1).  The outer FP64

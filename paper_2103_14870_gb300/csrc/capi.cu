@@ -73,6 +73,7 @@ struct gf_mesh {
   DevMesh dm;
   int32_t* perm_dev = nullptr;
   int last_iters = 4;
+  gf_tuning tune{};           // assembly schedule etc. (defaults: two-phase gather)
   bool mixed = false;
   int last_inner = 3;
   double in_rtol = 1e-4;
@@ -307,7 +308,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     m->own_stream = true;
   }
   std::string err;
-  gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, M, m->hm, err, opt.precision == GF_FP64);
+  gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, M, m->hm, err);
   if (st != GF_OK) {
     set_last_error(err);
     return fail(st);
@@ -350,6 +351,11 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   UP(d.edges, hm.edges, int32_t);
   UP(d.et_ptr, hm.et_ptr, int32_t);
   UP(d.et_tet, hm.et_tet, int32_t);
+  UP(d.colour_tets, hm.colour_tets, int32_t);
+  UP(d.sc_ptr, hm.sc_ptr, int32_t);
+  UP(d.sc_ent, hm.sc_ent, int32_t);
+  UP(d.np_ptr, hm.np_ptr, int32_t);
+  UP(d.np_pair, hm.np_pair, int32_t);
   if (!mixed) {
     UP(d.nb_off, hm.nbr.group_off, int64_t);
     UP(d.nb_len, hm.nbr.group_len, int32_t);
@@ -361,13 +367,9 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.restA, mxh.restA, float);
     UP(d.mx.restB, mxh.restB, float);
     UP(d.mx.edge_e0, mxh.edge_e0, float);
-    UP(d.mx.np_ptr, mxh.np_ptr, int32_t);
-    UP(d.mx.np_pair, mxh.np_pair, int32_t);
     UP(d.mx.nb_ptr, mxh.nb_ptr, int64_t);
     UP(d.mx.nb_csr, mxh.nb_csr, int32_t);
     UP(d.mx.nb_wc, mxh.nb_wc, float);
-    UP(d.mx.sc_ptr, mxh.sc_ptr, int32_t);
-    UP(d.mx.sc_ent, mxh.sc_ent, int32_t);
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());
     UP(d.mx.mass32, m32, float);
     std::vector<double> Xv(nodes, nodes + 3 * n_nodes);
@@ -389,7 +391,8 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     return fail(st);
   if (!mixed) {
     if ((st = scratch(m, 6 * T, &d.sig_in)) || (st = scratch(m, 6 * T, &d.sig_bar)) ||
-        (st = scratch(m, 9 * NB, &d.val)) || (st = scratch(m, 3 * N, &d.r)) || (st = scratch(m, 3 * N, &d.z)) ||
+        (st = scratch(m, 9 * NB, &d.val)) || (st = scratch(m, 104 * T, &d.ebuf)) ||
+        (st = scratch(m, 3 * N, &d.r)) || (st = scratch(m, 3 * N, &d.z)) ||
         (st = scratch(m, 3 * N, &d.p)) || (st = scratch(m, 3 * N, &d.q)) || (st = scratch(m, 9 * N, &d.pinv)))
       return fail(st);
   } else {
@@ -472,7 +475,7 @@ gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets
   if (edges) std::memcpy(edges, hm.edges.data(), sizeof(int32_t) * hm.edges.size());
   if (colour)
     for (size_t c = 0; c + 1 < hm.colour_ptr.size(); ++c)
-      for (int32_t i = hm.colour_ptr[c]; i < hm.colour_ptr[c + 1]; ++i) colour[hm.perm[i]] = int32_t(c);
+      for (int32_t i = hm.colour_ptr[c]; i < hm.colour_ptr[c + 1]; ++i) colour[hm.colour_tets[i]] = int32_t(c);
   if (nbr_count) {
     const NeighbourSell& S = hm.nbr;
     for (int64_t i = 0; i < T; ++i) {
@@ -538,6 +541,25 @@ gf_status gf_state_set(gf_mesh* m, const double* x, const double* v, const uint8
   return GF_OK;
 }
 
+gf_status gf_tuning_set(gf_mesh* m, const gf_tuning* t) {
+  if (!m || !t || (t->assembly != GF_ASSEMBLY_GATHER && t->assembly != GF_ASSEMBLY_COLOUR)) {
+    set_last_error("bad tuning (assembly must be GF_ASSEMBLY_GATHER or GF_ASSEMBLY_COLOUR)");
+    return GF_BAD_ARG;
+  }
+  if (m->mixed && t->assembly != GF_ASSEMBLY_GATHER) {
+    set_last_error("GF_MIXED assembles by gather only");
+    return GF_UNSUPPORTED;
+  }
+  m->tune = *t;
+  return GF_OK;
+}
+
+gf_status gf_tuning_get(const gf_mesh* m, gf_tuning* t) {
+  if (!m || !t) return GF_BAD_ARG;
+  *t = m->tune;
+  return GF_OK;
+}
+
 gf_status gf_refine_set(gf_mesh* m, double inner_rtol) {
   if (!m || !(inner_rtol > 0) || !(inner_rtol < 1)) {
     set_last_error("need 0 < inner_rtol < 1");
@@ -578,10 +600,14 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
   { Prof p(m, kPChi); L += launch_tet_chi(d, mt, m->lut, s); }
   {
     Prof p(m, kPAssemble);
-    GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
-    L += launch_node_init(d, dt, mt, has_fext, s);
-    const auto& cp = m->hm.colour_ptr;
-    for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble(d, mt, dt, cp[c], cp[c + 1], s);
+    if (m->tune.assembly == GF_ASSEMBLY_COLOUR) {
+      GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
+      L += launch_node_init(d, dt, mt, has_fext, s);
+      const auto& cp = m->hm.colour_ptr;
+      for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble(d, mt, dt, cp[c], cp[c + 1], s);
+    } else {
+      L += launch_assemble_2phase(d, mt, dt, has_fext ? d.f_ext : nullptr, s);
+    }
   }
   PcgState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;

@@ -41,13 +41,9 @@ struct MixDev {
   const float* restA = nullptr;       // [T][kRAStride] (128-byte aligned rows)
   const float* restB = nullptr;       // [T][kRBStride]
   const float* edge_e0 = nullptr;     // [NE][3]
-  const int32_t* np_ptr = nullptr;    // [N+1]
-  const int32_t* np_pair = nullptr;   // [4T]
   const int64_t* nb_ptr = nullptr;    // [T+1] CSR Eq. 20 lists
   const int32_t* nb_csr = nullptr;
   const float* nb_wc = nullptr;
-  const int32_t* sc_ptr = nullptr;    // [NB+1] block slot -> element-block contributions
-  const int32_t* sc_ent = nullptr;    // [16T] (tet << 5) | q | 16 * transposed
   const float* mass32 = nullptr;      // [N]
   const double* X = nullptr;          // [3N] rest positions
   float* u32 = nullptr;               // [3N] displacement x - X
@@ -81,6 +77,11 @@ struct DevMesh {
   const int2* edges = nullptr;         // [NE]
   const int32_t* et_ptr = nullptr;     // [NE+1]
   const int32_t* et_tet = nullptr;
+  const int32_t* colour_tets = nullptr;  // [T] tets grouped by colour
+  const int32_t* sc_ptr = nullptr;     // [NB+1] block slot -> element-block contributions
+  const int32_t* sc_ent = nullptr;     // [16T] (tet << 5) | q | 16 * transposed
+  const int32_t* np_ptr = nullptr;     // [N+1] node -> (tet << 2) | local node
+  const int32_t* np_pair = nullptr;    // [4T]
   const int64_t* nb_off = nullptr;     // [G]
   const int32_t* nb_len = nullptr;     // [G]
   const int32_t* nb_idx = nullptr;
@@ -96,6 +97,7 @@ struct DevMesh {
   double* sig_bar = nullptr;           // [T][6] Eq. 20 averages
   double* sigf = nullptr;              // [T][6] local edge-normal stresses
   double* val = nullptr;               // [NB][9] system matrix A
+  double* ebuf = nullptr;              // [T][104] element blocks + rhs shares (two-phase assembly)
   double* rhs = nullptr;               // [3N] b
   double* dv = nullptr;                // [3N] unknown
   double* r = nullptr;
@@ -131,6 +133,7 @@ int launch_edge_driver(const DevMesh& m, const Material& mt, cudaStream_t s);
 int launch_tet_chi(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s);
 int launch_node_init(const DevMesh& m, double dt, const Material& mt, bool has_fext, cudaStream_t s);
 int launch_assemble(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s);
+int launch_assemble_2phase(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s);
 int launch_set_pinned(const DevMesh& m, int64_t n_pinned, bool has_vel, cudaStream_t s);
 int launch_pcg_init(const DevMesh& m, cudaStream_t s);
 int launch_pcg_iter(const DevMesh& m, cudaStream_t s, int kernel /*0 spmv, 1 update, 2 p*/);

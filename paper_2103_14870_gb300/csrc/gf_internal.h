@@ -53,17 +53,15 @@ struct MixedHost {
   std::vector<float> restA;         // [T][kRAStride]
   std::vector<float> restB;         // [T][kRBStride]
   std::vector<float> edge_e0;       // [NE][3] rest edge vectors (b - a)
-  std::vector<int32_t> np_ptr;      // [N+1] node -> incident (tet, local node) pairs
-  std::vector<int32_t> np_pair;     // [4T] (internal tet << 2) | local node
   // CSR neighbour lists (one warp per tet): nb_ptr [T+1], nb_csr (neighbour << 0), nb_wc FP32 weights
   std::vector<int64_t> nb_ptr;
   std::vector<int32_t> nb_csr;
   std::vector<float> nb_wc;
-  // two-phase assembly: per block slot, contributions (tet << 5) | code, code = q (0..9) or q + 16
-  // (transposed) for the tet's upper-triangle block q; per node, (tet << 2) | local node
-  std::vector<int32_t> sc_ptr;      // [NB+1]
-  std::vector<int32_t> sc_ent;      // [16T]
 };
+
+
+
+gf_status build_mixed_host(const double* X, const struct HostMesh& hm, MixedHost& mx, std::string& err);
 
 // Upper-triangle block order of a tet's 4x4 node blocks: q -> (a, b), a <= b.
 GF_HD constexpr int blk_a(int q) { return q < 4 ? 0 : (q < 7 ? 1 : (q < 9 ? 2 : 3)); }
@@ -72,14 +70,18 @@ GF_HD constexpr int blk_q(int a, int b) {   // a <= b
   return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
 }
 
-gf_status build_mixed_host(const double* X, const struct HostMesh& hm, MixedHost& mx, std::string& err);
-
 // Everything mesh_create computes on the host before upload.
 struct HostMesh {
   int64_t n_nodes = 0, n_tets = 0, n_edges = 0, n_blocks = 0;
-  std::vector<int32_t> tets;       // [T][4] internal (colour-major) order
-  std::vector<int32_t> perm;       // internal tet -> caller tet
-  std::vector<int32_t> colour_ptr; // [C+1] internal ranges of each colour
+  std::vector<int32_t> tets;       // [T][4] internal order (the caller's order)
+  std::vector<int32_t> perm;       // internal tet -> caller tet (identity)
+  std::vector<int32_t> colour_ptr; // [C+1] ranges of colour_tets
+  std::vector<int32_t> colour_tets;// [T] tets grouped by colour (no two share a node within a colour)
+  // two-phase assembly: block slot -> (tet << 5) | q | 16*transposed, node -> (tet << 2) | local node
+  std::vector<int32_t> sc_ptr;     // [NB+1]
+  std::vector<int32_t> sc_ent;     // [16T]
+  std::vector<int32_t> np_ptr;     // [N+1]
+  std::vector<int32_t> np_pair;    // [4T]
   std::vector<int32_t> edges;      // [NE][2]
   std::vector<int32_t> tet_edges;  // [T][6] internal order
   std::vector<int32_t> row_ptr;    // [N+1] block-CSR pattern
@@ -94,10 +96,8 @@ struct HostMesh {
 };
 
 // Host precompute; returns GF_OK or GF_BAD_ARG with `err` set.
-// colour_order: order tets colour-major (conflict-free scatter of the FP64 path);
-// otherwise keep the caller's (spatial) order with a single range.
 gf_status build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
-                          const gf_material& mat, HostMesh& hm, std::string& err, bool colour_order = true);
+                          const gf_material& mat, HostMesh& hm, std::string& err);
 
 // 64-bit table: bit m set when the broken-edge mask m (bit k = local edge k)
 // leaves the tet's four nodes in two or more pieces (Eq. 25's disjoint rule).

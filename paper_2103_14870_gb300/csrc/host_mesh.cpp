@@ -82,7 +82,7 @@ uint64_t disconnect_table() {
 }
 
 gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, int64_t T, const gf_material& mat,
-                          HostMesh& hm, std::string& err, bool colour_order) {
+                          HostMesh& hm, std::string& err) {
   if (N <= 0 || T <= 0 || N > (int64_t(1) << 30) || T > (int64_t(1) << 30)) {
     err = "n_nodes and n_tets must be in [1, 2^30]";
     return GF_BAD_ARG;
@@ -171,16 +171,18 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
       colour[t] = c;
     }
   }
-  if (!colour_order) std::fill(colour.begin(), colour.end(), 0);
   int32_t n_col = *std::max_element(colour.begin(), colour.end()) + 1;
   hm.colour_ptr.assign(n_col + 1, 0);
   for (int64_t t = 0; t < T; ++t) hm.colour_ptr[colour[t] + 1]++;
   for (int c = 0; c < n_col; ++c) hm.colour_ptr[c + 1] += hm.colour_ptr[c];
-  hm.perm.resize(T);
+  hm.colour_tets.resize(T);
   {
     std::vector<int32_t> pos(hm.colour_ptr.begin(), hm.colour_ptr.end() - 1);
-    for (int64_t t = 0; t < T; ++t) hm.perm[pos[colour[t]]++] = int32_t(t);   // stable within a colour
+    for (int64_t t = 0; t < T; ++t) hm.colour_tets[pos[colour[t]]++] = int32_t(t);   // ascending within a colour
   }
+  // tets keep the caller's order (spatially coherent for the gathers)
+  hm.perm.resize(T);
+  for (int64_t t = 0; t < T; ++t) hm.perm[t] = int32_t(t);
 
   // ---- internal-order tets, tet->edge, block slots ----
   hm.tets.resize(4 * T);
@@ -199,6 +201,36 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
         }
     }
   });
+
+  // ---- two-phase assembly lists ----
+  hm.np_ptr.assign(N + 1, 0);
+  for (int64_t i = 0; i < 4 * T; ++i) hm.np_ptr[hm.tets[i] + 1]++;
+  for (int64_t i = 0; i < N; ++i) hm.np_ptr[i + 1] += hm.np_ptr[i];
+  hm.np_pair.resize(4 * T);
+  {
+    std::vector<int32_t> pos(hm.np_ptr.begin(), hm.np_ptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a) hm.np_pair[pos[hm.tets[4 * t + a]]++] = int32_t((t << 2) | a);
+  }
+  hm.sc_ptr.assign(hm.n_blocks + 1, 0);
+  for (int64_t t = 0; t < T; ++t)
+    for (int q = 0; q < 16; ++q) hm.sc_ptr[hm.slot[16 * t + q] + 1]++;
+  for (int64_t b = 0; b < hm.n_blocks; ++b) hm.sc_ptr[b + 1] += hm.sc_ptr[b];
+  hm.sc_ent.resize(16 * T);
+  {
+    std::vector<int32_t> pos(hm.sc_ptr.begin(), hm.sc_ptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          const int q = a <= b ? blk_q(a, b) : blk_q(b, a);
+          const int code = a <= b ? q : q + 16;
+          hm.sc_ent[pos[hm.slot[16 * t + 4 * a + b]]++] = int32_t((t << 5) | code);
+        }
+  }
+  if (T >= (int64_t(1) << 26)) {
+    err = "at most 2^26 tets per mesh";
+    return GF_BAD_ARG;
+  }
 
   // ---- rest data per tet (internal order) ----
   const double lam = mat.young * mat.poisson / ((1.0 + mat.poisson) * (1.0 - 2.0 * mat.poisson));
@@ -420,16 +452,6 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
   for (int64_t e = 0; e < NE; ++e)
     for (int c = 0; c < 3; ++c)
       mx.edge_e0[3 * e + c] = float(X[3 * hm.edges[2 * e + 1] + c] - X[3 * hm.edges[2 * e] + c]);
-  // node -> (tet, local node) pairs, tets in ascending internal order
-  mx.np_ptr.assign(N + 1, 0);
-  for (int64_t i = 0; i < 4 * T; ++i) mx.np_ptr[hm.tets[i] + 1]++;
-  for (int64_t i = 0; i < N; ++i) mx.np_ptr[i + 1] += mx.np_ptr[i];
-  mx.np_pair.resize(4 * T);
-  {
-    std::vector<int32_t> pos(mx.np_ptr.begin(), mx.np_ptr.end() - 1);
-    for (int64_t t = 0; t < T; ++t)
-      for (int a = 0; a < 4; ++a) mx.np_pair[pos[hm.tets[4 * t + a]]++] = int32_t((t << 2) | a);
-  }
   // CSR copy of the neighbour lists (from the SELL-32 layout: real entries have w > 0
   // or are the tet itself)
   {
@@ -457,27 +479,6 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
         }
       }
     }
-  }
-  // block slot -> (tet, upper-triangle block, transposed) contributions, ascending tet
-  mx.sc_ptr.assign(hm.n_blocks + 1, 0);
-  for (int64_t t = 0; t < T; ++t)
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) mx.sc_ptr[hm.slot[16 * t + 4 * a + b] + 1]++;
-  for (int64_t b = 0; b < hm.n_blocks; ++b) mx.sc_ptr[b + 1] += mx.sc_ptr[b];
-  mx.sc_ent.resize(16 * T);
-  {
-    std::vector<int32_t> pos(mx.sc_ptr.begin(), mx.sc_ptr.end() - 1);
-    for (int64_t t = 0; t < T; ++t)
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-          const int q = a <= b ? blk_q(a, b) : blk_q(b, a);
-          const int code = a <= b ? q : q + 16;
-          mx.sc_ent[pos[hm.slot[16 * t + 4 * a + b]]++] = int32_t((t << 5) | code);
-        }
-  }
-  if (T >= (int64_t(1) << 26)) {
-    err = "mixed precision supports at most 2^26 tets";
-    return GF_UNSUPPORTED;
   }
   return GF_OK;
 }

@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(kThreads) k_node_init(DevMesh m, double dt, do
 // One colour: no two tets share a node, so the read-modify-write scatter into
 // the block-CSR slots and into b is conflict-free without atomics.
 __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double beta, int t0, int t1) {
-  const int64_t t = t0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= t1) return;
+  const int64_t ct = t0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (ct >= t1) return;
+  const int64_t t = m.colour_tets[ct];
   const double chi = m.chi[t];
   if (chi == 0.0) return;   // chi = 0: the element carries no energy (Eq. 25)
   const int4 n = m.tets[t];
@@ -320,6 +321,150 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
           for (int c = 0; c < 3; ++c) dt2[3 * r + c] += blk[c][r];
       }
     }
+  }
+}
+
+// Two-phase FP64 assembly (no colours, no atomics, one launch per phase).
+// k_elem64 (thread per tet) writes the tet's ten upper-triangle blocks of
+// (dt beta + dt^2) chi k_e and its four rhs shares dt chi (f_a - (beta+dt)(k_e v)_a)
+// to its row of the element buffer; k_gather64 (warp per node row, lane per
+// block entry) sums them in a fixed precomputed order and adds mass, external
+// force and mass damping.
+constexpr int kElemW64 = 104;
+
+__global__ void __launch_bounds__(128) k_elem64(DevMesh m, double dt, double beta) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
+  double* out = m.ebuf + kElemW64 * t;
+  const double chi = m.chi[t];
+  if (chi == 0.0) {
+    for (int q = 0; q < kElemW64; ++q) out[q] = 0.0;
+    return;
+  }
+  const int4 n = m.tets[t];
+  const int nid[4] = {n.x, n.y, n.z, n.w};
+  const int inc[4][3] = {{0, 1, 2}, {0, 3, 4}, {1, 3, 5}, {2, 4, 5}};
+  const double sgn[4][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {1, 1, 1}};
+  const int kab[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
+  double P[4][3], U[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ld3(m.x, nid[a], P[a]);
+    ld3(m.v, nid[a], U[a]);
+  }
+  double e[6][3], ds[6], Dv[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double du[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      e[k][c] = P[edge_b(k)][c] - P[edge_a(k)][c];
+      du[c] = U[edge_b(k)][c] - U[edge_a(k)][c];
+    }
+    ds[k] = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2] - m.rest[(kRestS0 + k) * m.T + t];
+    Dv[k] = 2.0 * (e[k][0] * du[0] + e[k][1] * du[1] + e[k][2] * du[2]);
+  }
+  double H[21];
+#pragma unroll
+  for (int f = 0; f < 21; ++f) H[f] = m.rest[(kRestH + f) * m.T + t];
+  auto h = [&](int k, int l) { return k <= l ? H[tri6(k, l)] : H[tri6(l, k)]; };
+  double g[6], w[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double gk = 0.0, wk = 0.0;
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      gk += h(k, l) * ds[l];
+      wk += h(k, l) * Dv[l];
+    }
+    g[k] = gk;
+    w[k] = wk;
+  }
+  {
+    const double cv = beta + dt, sc = 2.0 * dt * chi;
+    double f[4][3] = {};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double a1 = sc * (g[k] + cv * w[k]), a2 = sc * cv * g[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double tk = a1 * e[k][c] + a2 * (U[edge_b(k)][c] - U[edge_a(k)][c]);
+        f[edge_a(k)][c] += tk;
+        f[edge_b(k)][c] -= tk;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[90 + 3 * a + c] = f[a][c];
+  }
+  const double sK = (dt * beta + dt * dt) * chi;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    double Y[6][3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double y = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y += sgn[b][j] * h(k, inc[b][j]) * e[inc[b][j]][c];
+        Y[k][c] = 4.0 * sK * y;
+      }
+#pragma unroll
+    for (int a = 0; a <= b; ++a) {
+      double blk[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double v = 0.0;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) v += sgn[a][i] * e[inc[a][i]][r] * Y[inc[a][i]][c];
+          blk[r][c] = v;
+        }
+      const double geo = (a == b) ? 2.0 * sK * (g[inc[a][0]] + g[inc[a][1]] + g[inc[a][2]])
+                                  : -2.0 * sK * g[kab[a][b]];
+      blk[0][0] += geo;
+      blk[1][1] += geo;
+      blk[2][2] += geo;
+      double* dst = out + 9 * blk_q(a, b);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[3 * r + c] = blk[r][c];
+    }
+  }
+  out[102] = 0.0;
+  out[103] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_gather64(DevMesh m, double dt, double alpha, const double* f_ext) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (i >= m.N) return;                               // whole warp leaves together
+  const int rb = m.row_ptr[i], rl = m.row_ptr[i + 1] - rb;
+  const int dslot = m.diag_blk[i];
+  const double mi = m.mass[i];
+  for (int o = lane; o < 9 * rl; o += 32) {
+    const int p = o / 9, e = o - 9 * p;
+    const int slot = rb + p;
+    const int et = 3 * (e % 3) + e / 3;
+    double acc = 0.0;
+    for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
+      const int ent = m.sc_ent[c];
+      acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
+    }
+    if (slot == dslot && (e == 0 || e == 4 || e == 8)) acc += (1.0 + dt * alpha) * mi;
+    m.val[9 * int64_t(slot) + e] = acc;
+  }
+  if (lane < 3) {
+    double acc = 0.0;
+    for (int k = m.np_ptr[i]; k < m.np_ptr[i + 1]; ++k) {
+      const int pr = m.np_pair[k];
+      acc += m.ebuf[kElemW64 * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
+    }
+    m.rhs[3 * i + lane] = acc + dt * ((f_ext ? f_ext[3 * i + lane] : 0.0) - alpha * mi * m.v[3 * i + lane]);
   }
 }
 
@@ -535,6 +680,11 @@ int launch_assemble(const DevMesh& m, const Material& mt, double dt, int t0, int
   if (t1 <= t0) return 0;
   k_assemble<<<blocks_for(t1 - t0, 128), 128, 0, s>>>(m, dt, mt.beta, t0, t1);
   return 1;
+}
+int launch_assemble_2phase(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s) {
+  k_elem64<<<blocks_for(m.T, 128), 128, 0, s>>>(m, dt, mt.beta);
+  k_gather64<<<blocks_for(32 * m.N, 256), 256, 0, s>>>(m, dt, mt.alpha, f_ext);
+  return 2;
 }
 int launch_set_pinned(const DevMesh& m, int64_t n_pinned, bool has_vel, cudaStream_t s) {
   if (n_pinned <= 0) return 0;

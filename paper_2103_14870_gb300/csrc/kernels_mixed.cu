@@ -367,8 +367,8 @@ __global__ void __launch_bounds__(256) k_gather32(DevMesh m, float dtf, float al
     const int slot = rb + p;
     const int et = 3 * (e % 3) + e / 3;          // entry of the transposed block
     float acc = 0.f;
-    for (int c = x.sc_ptr[slot]; c < x.sc_ptr[slot + 1]; ++c) {
-      const int ent = x.sc_ent[c];
+    for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
+      const int ent = m.sc_ent[c];
       acc += x.ebuf[kElemW * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
     }
     if (slot == dslot) {
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(256) k_gather32(DevMesh m, float dtf, float al
   }
   if (lane < 3) {
     float acc = 0.f;
-    for (int k = x.np_ptr[i]; k < x.np_ptr[i + 1]; ++k) {
-      const int pr = x.np_pair[k];
+    for (int k = m.np_ptr[i]; k < m.np_ptr[i + 1]; ++k) {
+      const int pr = m.np_pair[k];
       acc += x.ebuf[kElemW * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
     }
     const float fe = x.fext32 ? x.fext32[3 * i + lane] : 0.f;

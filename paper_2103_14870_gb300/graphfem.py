@@ -58,6 +58,13 @@ class StepStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("assembly", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
+
+
 class MeshInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_nodes", "n_tets", "n_edges", "n_blocks", "n_colours",
                                               "n_nbr_pairs", "device_bytes")]
@@ -88,6 +95,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
                                    ctypes.POINTER(StepStats)]),
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
+        "gf_tuning_set": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
+        "gf_tuning_get": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
         "gf_positions_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
         "gf_velocities_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
         "gf_damage_get": (ctypes.c_int, [P, P, P, ctypes.c_int32]),
@@ -203,6 +212,16 @@ class Mesh:
                                          ctypes.byref(st))
         _check(status)
         return st.as_dict()
+
+    def tuning_set(self, assembly: int):
+        t = Tuning()
+        t.assembly = assembly
+        _check(load_library().gf_tuning_set(self._h, ctypes.byref(t)))
+
+    def tuning_get(self) -> dict:
+        t = Tuning()
+        _check(load_library().gf_tuning_get(self._h, ctypes.byref(t)))
+        return {"assembly": t.assembly}
 
     def refine_set(self, inner_rtol: float):
         _check(load_library().gf_refine_set(self._h, float(inner_rtol)))

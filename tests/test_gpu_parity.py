@@ -196,3 +196,24 @@ def test_device_inputs_match_host_inputs():
     xd = torch.empty(3 * w.n_nodes, dtype=torch.float64, device="cuda")
     b.positions_get(out=xd)
     np.testing.assert_array_equal(xd.cpu().numpy(), a.positions_get())
+
+
+def test_assembly_schedules_agree():
+    """Two-phase gather and colour-ordered scatter assemble the same system
+    (up to summation order) and both match the oracle."""
+    w = beam_config()
+    model0 = oracle_model(w, threshold=math.inf)
+    st = deformed_state(w, seed=17)
+    d0, _, _, _ = model0.damage_update(st)
+    theta = float(np.quantile(d0, 0.95))
+    model = oracle_model(w, threshold=theta)
+    out = {}
+    for sched in (gf.graphfem.ASSEMBLY_GATHER, gf.graphfem.ASSEMBLY_COLOUR):
+        m = gpu_mesh(w, gpu_material(gf, w, threshold=theta))
+        m.tuning_set(sched)
+        assert m.tuning_get()["assembly"] == sched
+        new, info, stats, same = compare_step(m, model, st, w, w.dt, w.f_ext, w.pinned)
+        assert same
+        out[sched] = (m.system_get()[2], m.velocities_get())
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-12, atol=1e-12 * np.abs(out[0][0]).max())
+    assert np.linalg.norm(out[0][1] - out[1][1]) <= 1e-12 * np.linalg.norm(out[0][1])
