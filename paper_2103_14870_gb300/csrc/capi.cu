@@ -12,6 +12,65 @@ namespace gf {
 thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+StepScalars step_scalars(const Material& mt, double dt, bool has_fext, int64_t n_pinned, bool has_pvel) {
+  StepScalars sp{};
+  sp.dt = dt;
+  sp.dtf = float(dt);
+  sp.sKv = float(dt * mt.beta + dt * dt);
+  sp.cv = float(mt.beta + dt);
+  sp.alphaf = float(mt.alpha);
+  sp.cmf = float(1.0 + dt * mt.alpha);
+  sp.has_fext = has_fext ? 1 : 0;
+  sp.has_pvel = has_pvel ? 1 : 0;
+  sp.n_pinned = n_pinned;
+  return sp;
+}
+
+namespace {
+inline unsigned cdiv(int64_t n, int d) { return unsigned((n + d - 1) / d); }
+inline unsigned red_grid(int64_t n) {   // FP64 reducing kernels: one thread per row, <= kMaxPartials CTAs
+  const int64_t b = (n + 255) / 256;
+  return unsigned(b < 1 ? 1 : (b > kMaxPartials ? kMaxPartials : b));
+}
+inline unsigned ir_grid(int64_t n) {    // refinement kernels: <= 4 CTAs per SM, grid-stride
+  const int64_t b = (n + 255) / 256;
+  return unsigned(b < 1 ? 1 : (b > 4 * 152 ? 4 * 152 : b));
+}
+}  // namespace
+
+LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp) {
+  const int64_t N = m.N, T = m.T, NE = m.NE;
+  switch (kind) {
+    case kB_tet_stress: case kB_tet_chi: case kB_tet_stress32: case kB_tet_chi32: case kB_chi_to32:
+      return {cdiv(T, 256), 256};
+    case kB_nonlocal: return {mt.radius > 0.0 ? cdiv(T, 256) : 0u, 256};
+    case kB_nonlocal32: return {mt.radius > 0.0 ? cdiv(32 * T, 256) : 0u, 256};
+    case kB_edge_driver: case kB_edge_driver32: return {cdiv(NE, 256), 256};
+    case kB_node_init: return {cdiv(N, 256), 256};
+    case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
+    case kB_gather64: case kB_gather32: return {cdiv(32 * N, 256), 256};
+    case kB_set_pinned: return {cdiv(sp.n_pinned, 256), 256};
+    case kB_pcg_init: case kB_pcg_spmv: case kB_pcg_update: case kB_true_residual: return {red_grid(N), 256};
+    case kB_pcg_p: return {red_grid(3 * N), 256};
+    case kB_integrate: case kB_integrate32: case kB_refresh32: return {cdiv(3 * N, 256), 256};
+    case kB_fext32: return {sp.has_fext ? cdiv(3 * N, 256) : 0u, 256};
+    case kB_ir_residual: case kB_ir_spmv: return {ir_grid(16 * N), 256};
+    case kB_ir_inner_init: case kB_ir_update: return {ir_grid(N), 256};
+    case kB_ir_p: case kB_ir_apply: return {ir_grid(3 * N), 256};
+  }
+  return {0u, 256};
+}
+
+int launch_kind(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first) {
+  return kind < kB_tet_stress32 ? launch_kind_fp64(kind, m, mt, sp, s) : launch_kind_mixed(kind, m, mt, sp, s, first);
+}
+
+int launch_batch(int kind, const BatchTab* tab, unsigned blocks, cudaStream_t s, int first) {
+  const unsigned threads = (kind == kB_elem64 || kind == kB_elem32) ? 128u : 256u;
+  return kind < kB_tet_stress32 ? launch_batch_fp64(kind, tab, blocks, threads, s)
+                                : launch_batch_mixed(kind, tab, blocks, threads, s, first);
+}
+
 namespace {
 
 enum ProfGroup : int {
@@ -217,11 +276,13 @@ cudaMemcpyKind from_dev(int32_t mem) { return mem == GF_MEM_HOST ? cudaMemcpyDev
 
 gf_status recompute_chi(gf_mesh* m) {
   if (m->mixed) {
-    m->launches += launch_tet_stress32(m->dm, m->mt, m->stream);
-    m->launches += launch_tet_chi32(m->dm, m->mt, m->lut, m->stream);
+    const StepScalars sp = step_scalars(m->mt, 1.0, false, 0, false);
+    m->launches += launch_kind(kB_tet_stress32, m->dm, m->mt, sp, m->stream);
+    m->launches += launch_kind(kB_tet_chi32, m->dm, m->mt, sp, m->stream);
   } else {
-    m->launches += launch_tet_stress(m->dm, m->mt, m->stream);
-    m->launches += launch_tet_chi(m->dm, m->mt, m->lut, m->stream);
+    const StepScalars sp = step_scalars(m->mt, 1.0, false, 0, false);
+    m->launches += launch_kind(kB_tet_stress, m->dm, m->mt, sp, m->stream);
+    m->launches += launch_kind(kB_tet_chi, m->dm, m->mt, sp, m->stream);
   }
   GF_CK(cudaGetLastError());
   return GF_OK;
@@ -318,6 +379,12 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   m->mt = gf::Material{lam, mu, M.young, M.alpha, M.beta, M.threshold, M.radius, double(M.shear_coef),
                        M.driver_mode == GF_DRIVER_STRESS ? 1 : 0, M.average_degraded ? 1 : 0};
   m->lut = disconnect_table();
+  m->mt.lut = m->lut;
+  m->mt.lam32 = float(m->mt.lam);
+  m->mt.mu32 = float(m->mt.mu);
+  m->mt.kappa32 = float(m->mt.kappa);
+  m->mt.young32 = float(m->mt.young);
+  m->mt.inv_young32 = float(1.0 / m->mt.young);
 
   HostMesh& hm = m->hm;
   DevMesh& d = m->dm;
@@ -427,8 +494,9 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   k_fill<<<unsigned((NE + 255) / 256), 256, 0, m->stream>>>(d.driver, NE, -INFINITY);
   m->launches += 2;
   if (mixed) {
-    m->launches += launch_refresh32(d, m->stream);
-    m->launches += launch_chi_to32(d, m->stream);
+    const StepScalars sp0 = step_scalars(m->mt, 1.0, false, 0, false);
+    m->launches += launch_kind(kB_refresh32, d, m->mt, sp0, m->stream);
+    m->launches += launch_kind(kB_chi_to32, d, m->mt, sp0, m->stream);
   }
   GF_CK(cudaGetLastError());
   GF_CK(cudaStreamSynchronize(m->stream));
@@ -522,7 +590,8 @@ gf_status gf_state_set(gf_mesh* m, const double* x, const double* v, const uint8
   if (x) GF_CK(cudaMemcpyAsync(d.x, x, sizeof(double) * 3 * d.N, to_dev(mem), m->stream));
   if (v) GF_CK(cudaMemcpyAsync(d.v, v, sizeof(double) * 3 * d.N, to_dev(mem), m->stream));
   if (labels) GF_CK(cudaMemcpyAsync(d.labels, labels, d.NE, to_dev(mem), m->stream));
-  if (m->mixed && (x || v)) m->launches += launch_refresh32(d, m->stream);
+  const StepScalars sp0 = step_scalars(m->mt, 1.0, false, 0, false);
+  if (m->mixed && (x || v)) m->launches += launch_kind(kB_refresh32, d, m->mt, sp0, m->stream);
   if (chi) {
     const double* src = chi;
     if (mem == GF_MEM_HOST) {
@@ -531,7 +600,7 @@ gf_status gf_state_set(gf_mesh* m, const double* x, const double* v, const uint8
     }
     k_gather<<<unsigned((d.T + 255) / 256), 256, 0, m->stream>>>(src, m->perm_dev, d.chi, d.T);
     m->launches += 1;
-    if (m->mixed) m->launches += launch_chi_to32(d, m->stream);
+    if (m->mixed) m->launches += launch_kind(kB_chi_to32, d, m->mt, sp0, m->stream);
     GF_CK(cudaGetLastError());
   } else if (labels) {
     gf_status st = recompute_chi(m);
@@ -588,25 +657,26 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
                     int64_t& L) {
   cudaStream_t s = m->stream;
   const gf::Material& mt = m->mt;
+  const StepScalars sp = step_scalars(mt, dt, has_fext, n_pinned, has_pvel);
   const int64_t N = d.N;
-  { Prof p(m, kPStress); L += launch_tet_stress(d, mt, s); }
+  if (!(mt.radius > 0.0)) d.sig_bar = d.sig_in;   // R_d = 0: the tet alone (local criterion)
+  { Prof p(m, kPStress); L += launch_kind(kB_tet_stress, d, mt, sp, s); }
   if (mt.radius > 0.0) {
     Prof p(m, kPNonlocal);
-    L += launch_nonlocal(d, s);
-  } else {
-    d.sig_bar = d.sig_in;   // R_d = 0: the tet alone (local criterion)
+    L += launch_kind(kB_nonlocal, d, mt, sp, s);
   }
-  { Prof p(m, kPEdge); L += launch_edge_driver(d, mt, s); }
-  { Prof p(m, kPChi); L += launch_tet_chi(d, mt, m->lut, s); }
+  { Prof p(m, kPEdge); L += launch_kind(kB_edge_driver, d, mt, sp, s); }
+  { Prof p(m, kPChi); L += launch_kind(kB_tet_chi, d, mt, sp, s); }
   {
     Prof p(m, kPAssemble);
     if (m->tune.assembly == GF_ASSEMBLY_COLOUR) {
       GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
-      L += launch_node_init(d, dt, mt, has_fext, s);
+      L += launch_kind(kB_node_init, d, mt, sp, s);
       const auto& cp = m->hm.colour_ptr;
-      for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble(d, mt, dt, cp[c], cp[c + 1], s);
+      for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble_colour(d, mt, dt, cp[c], cp[c + 1], s);
     } else {
-      L += launch_assemble_2phase(d, mt, dt, has_fext ? d.f_ext : nullptr, s);
+      L += launch_kind(kB_elem64, d, mt, sp, s);
+      L += launch_kind(kB_gather64, d, mt, sp, s);
     }
   }
   PcgState init{};
@@ -616,15 +686,15 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
   GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
   GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
   GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
-  L += launch_set_pinned(d, n_pinned, has_pvel, s);
-  { Prof p(m, kPPcgInit); L += launch_pcg_init(d, s); }
+  L += launch_kind(kB_set_pinned, d, mt, sp, s);
+  { Prof p(m, kPPcgInit); L += launch_kind(kB_pcg_init, d, mt, sp, s); }
   int launched_iters = 0;
   int chunk = std::max(1, std::min(m->last_iters + 1, 64));
   for (;;) {
     for (int j = 0; j < chunk; ++j, ++launched_iters) {
-      { Prof p(m, kPSpmv, launched_iters); L += launch_pcg_iter(d, s, 0); }
-      { Prof p(m, kPPcgUpdate, launched_iters); L += launch_pcg_iter(d, s, 1); }
-      { Prof p(m, kPPcgP, launched_iters); L += launch_pcg_iter(d, s, 2); }
+      { Prof p(m, kPSpmv, launched_iters); L += launch_kind(kB_pcg_spmv, d, mt, sp, s); }
+      { Prof p(m, kPPcgUpdate, launched_iters); L += launch_kind(kB_pcg_update, d, mt, sp, s); }
+      { Prof p(m, kPPcgP, launched_iters); L += launch_kind(kB_pcg_p, d, mt, sp, s); }
     }
     GF_CK(cudaGetLastError());
     GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
@@ -632,8 +702,8 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
     if (m->h_pcg->done || launched_iters >= m->opt.cg_maxit) break;
     chunk = 8;
   }
-  { Prof p(m, kPResidual); L += launch_true_residual(d, s); }
-  { Prof p(m, kPIntegrate); L += launch_integrate(d, dt, s); }
+  { Prof p(m, kPResidual); L += launch_kind(kB_true_residual, d, mt, sp, s); }
+  { Prof p(m, kPIntegrate); L += launch_kind(kB_integrate, d, mt, sp, s); }
   GF_CK(cudaGetLastError());
   GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
   return GF_OK;
@@ -644,17 +714,22 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
 gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_pinned, bool has_pvel, int64_t& L) {
   cudaStream_t s = m->stream;
   const gf::Material& mt = m->mt;
+  const StepScalars sp = step_scalars(mt, dt, has_fext, n_pinned, has_pvel);
   const int64_t N = d.N;
-  { Prof p(m, kPStress); L += launch_tet_stress32(d, mt, s); }
+  if (!(mt.radius > 0.0)) d.mx.sig_bar32 = d.mx.sig_in32;
+  { Prof p(m, kPStress); L += launch_kind(kB_tet_stress32, d, mt, sp, s); }
   if (mt.radius > 0.0) {
     Prof p(m, kPNonlocal);
-    L += launch_nonlocal32(d, s);
-  } else {
-    d.mx.sig_bar32 = d.mx.sig_in32;
+    L += launch_kind(kB_nonlocal32, d, mt, sp, s);
   }
-  { Prof p(m, kPEdge); L += launch_edge_driver32(d, mt, s); }
-  { Prof p(m, kPChi); L += launch_tet_chi32(d, mt, m->lut, s); }
-  { Prof p(m, kPAssemble); L += launch_assemble32(d, mt, dt, has_fext ? d.f_ext : nullptr, s); }
+  { Prof p(m, kPEdge); L += launch_kind(kB_edge_driver32, d, mt, sp, s); }
+  { Prof p(m, kPChi); L += launch_kind(kB_tet_chi32, d, mt, sp, s); }
+  {
+    Prof p(m, kPAssemble);
+    L += launch_kind(kB_elem32, d, mt, sp, s);
+    L += launch_kind(kB_fext32, d, mt, sp, s);
+    L += launch_kind(kB_gather32, d, mt, sp, s);
+  }
   IrState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
   init.in_tol2 = m->in_rtol * m->in_rtol;
@@ -668,21 +743,20 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   GF_CK(cudaMemcpyAsync(d.mx.ir, m->h_ir, sizeof(IrState), cudaMemcpyHostToDevice, s));
   GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
   GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
-  L += launch_set_pinned(d, n_pinned, has_pvel, s);
-  L += launch_refresh32(d, s);
-  { Prof p(m, kPIrResidual); L += launch_ir_residual(d, 1, s); }
-  int it = 0;
+  L += launch_kind(kB_set_pinned, d, mt, sp, s);
+  L += launch_kind(kB_refresh32, d, mt, sp, s);
+  { Prof p(m, kPIrResidual); L += launch_kind(kB_ir_residual, d, mt, sp, s, 1); }
   int max_inner = 0;
   for (int round = 0;; ++round) {
     for (int sw = 0; sw < 2; ++sw) {
-      { Prof p(m, kPIrInit); L += launch_ir_inner_init(d, s); }
-      for (int j = 0; j < K; ++j, ++it) {
-        { Prof p(m, kPSpmv, -2); L += launch_ir_inner_iter(d, s, 0); }
-        { Prof p(m, kPPcgUpdate, -2); L += launch_ir_inner_iter(d, s, 1); }
-        { Prof p(m, kPPcgP, -2); L += launch_ir_inner_iter(d, s, 2); }
+      { Prof p(m, kPIrInit); L += launch_kind(kB_ir_inner_init, d, mt, sp, s); }
+      for (int j = 0; j < K; ++j) {
+        { Prof p(m, kPSpmv, -2); L += launch_kind(kB_ir_spmv, d, mt, sp, s); }
+        { Prof p(m, kPPcgUpdate, -2); L += launch_kind(kB_ir_update, d, mt, sp, s); }
+        { Prof p(m, kPPcgP, -2); L += launch_kind(kB_ir_p, d, mt, sp, s); }
       }
-      { Prof p(m, kPIrApply); L += launch_ir_apply(d, s); }
-      { Prof p(m, kPIrResidual); L += launch_ir_residual(d, 0, s); }
+      { Prof p(m, kPIrApply); L += launch_kind(kB_ir_apply, d, mt, sp, s); }
+      { Prof p(m, kPIrResidual); L += launch_kind(kB_ir_residual, d, mt, sp, s, 0); }
     }
     GF_CK(cudaGetLastError());
     GF_CK(cudaMemcpyAsync(m->h_ir, d.mx.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
@@ -691,7 +765,7 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
     if (m->h_ir->done || m->h_ir->total_iters >= m->opt.cg_maxit || round >= 4096) break;
   }
   m->last_inner = std::max(1, std::min(max_inner, 32));
-  { Prof p(m, kPIntegrate); L += launch_integrate32(d, dt, s); }
+  { Prof p(m, kPIntegrate); L += launch_kind(kB_integrate32, d, mt, sp, s); }
   GF_CK(cudaGetLastError());
   GF_CK(cudaMemcpyAsync(m->h_ir, d.mx.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
   return GF_OK;

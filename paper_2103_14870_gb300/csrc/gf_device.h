@@ -121,37 +121,78 @@ struct Material {
   double kappa;       // shear coefficient of Eq. 16
   int driver_stress;  // 0: driver = sigma*/E, 1: sigma*
   int average_degraded;
+  uint64_t lut;       // disconnection table of Eq. 25
+  float lam32, mu32, kappa32, young32, inv_young32;
 };
+
+// Per-step scalars of one mesh, formed on the host (no FP64 scalar work per
+// thread on the device).
+struct StepScalars {
+  double dt;
+  float dtf, sKv, cv, alphaf, cmf;   // dt, dt beta + dt^2, beta + dt, alpha, 1 + dt alpha
+  int has_fext, has_pvel;
+  int64_t n_pinned;
+};
+
+StepScalars step_scalars(const Material& mt, double dt, bool has_fext, int64_t n_pinned, bool has_pvel);
 
 constexpr int kMaxPartials = 4096;     // max CTAs of a reducing launch
 constexpr int kTickets = 16;
 
-// launchers (return the number of kernels launched)
-int launch_tet_stress(const DevMesh& m, const Material& mt, cudaStream_t s);
-int launch_nonlocal(const DevMesh& m, cudaStream_t s);
-int launch_edge_driver(const DevMesh& m, const Material& mt, cudaStream_t s);
-int launch_tet_chi(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s);
-int launch_node_init(const DevMesh& m, double dt, const Material& mt, bool has_fext, cudaStream_t s);
-int launch_assemble(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s);
-int launch_assemble_2phase(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s);
-int launch_set_pinned(const DevMesh& m, int64_t n_pinned, bool has_vel, cudaStream_t s);
-int launch_pcg_init(const DevMesh& m, cudaStream_t s);
-int launch_pcg_iter(const DevMesh& m, cudaStream_t s, int kernel /*0 spmv, 1 update, 2 p*/);
-int launch_true_residual(const DevMesh& m, cudaStream_t s);
-int launch_integrate(const DevMesh& m, double dt, cudaStream_t s);
+// ---------------------------------------------------------------------------
+// Batched execution: one launch per kernel kind covers every mesh of a batch.
+// Block b of a batched launch belongs to the mesh k with off[kind][k] <= b <
+// off[kind][k+1]; inside, the kernel body sees that mesh's data and its local
+// block index and count (reductions and grid-stride loops stay per mesh).
+// ---------------------------------------------------------------------------
+enum BatchKind : int {
+  kB_tet_stress = 0, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_node_init, kB_elem64, kB_gather64, kB_set_pinned,
+  kB_pcg_init, kB_pcg_spmv, kB_pcg_update, kB_pcg_p, kB_true_residual, kB_integrate,
+  kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_fext32,
+  kB_ir_residual, kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_integrate32, kB_refresh32,
+  kB_chi_to32, kBKinds
+};
+constexpr int kMaxBatch = 256;
 
-// mixed-precision path
-int launch_tet_stress32(const DevMesh& m, const Material& mt, cudaStream_t s);
-int launch_nonlocal32(const DevMesh& m, cudaStream_t s);
-int launch_edge_driver32(const DevMesh& m, const Material& mt, cudaStream_t s);
-int launch_tet_chi32(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s);
-int launch_assemble32(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s);
-int launch_ir_residual(const DevMesh& m, int first, cudaStream_t s);
-int launch_ir_inner_init(const DevMesh& m, cudaStream_t s);
-int launch_ir_inner_iter(const DevMesh& m, cudaStream_t s, int which);
-int launch_ir_apply(const DevMesh& m, cudaStream_t s);
-int launch_integrate32(const DevMesh& m, double dt, cudaStream_t s);
-int launch_refresh32(const DevMesh& m, cudaStream_t s);
-int launch_chi_to32(const DevMesh& m, cudaStream_t s);
+struct BatchTab {
+  int32_t n;
+  int32_t off[kBKinds][kMaxBatch + 1];
+  DevMesh mesh[kMaxBatch];
+  Material mt[kMaxBatch];
+  StepScalars sp[kMaxBatch];
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int batch_locate(const BatchTab* __restrict__ tab, int kind, unsigned b, unsigned& bid,
+                                            unsigned& nb) {
+  const int32_t* off = tab->off[kind];
+  int lo = 0, hi = tab->n;            // off[lo] <= b < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (unsigned(off[mid]) <= b) lo = mid;
+    else hi = mid;
+  }
+  bid = b - unsigned(off[lo]);
+  nb = unsigned(off[lo + 1] - off[lo]);
+  return lo;
+}
+#endif
+
+// Launch geometry of each kind for one mesh: (blocks, threads).
+struct LaunchDims {
+  unsigned blocks, threads;
+};
+LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp);
+// One batched launch of `kind` over all meshes of the device table `tab`
+// (`blocks` = total over the meshes, from the host copy of the offsets).
+int launch_batch(int kind, const BatchTab* tab, unsigned blocks, cudaStream_t s, int first = 0);
+int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s);
+int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first);
+int launch_batch_fp64(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s);
+int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s, int first);
+
+// single-mesh launches (return the number of kernels launched)
+int launch_kind(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first = 0);
+int launch_assemble_colour(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s);
 
 }  // namespace gf

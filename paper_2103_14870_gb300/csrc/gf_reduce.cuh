@@ -17,7 +17,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // call it.  Returns true in the last CTA, with the totals in out[] (valid in
 // thread 0).  Nothing waits on another CTA.
 template <int NV>
-__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials, unsigned* ticket, double (&out)[NV]) {
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials, unsigned* ticket, double (&out)[NV],
+                                            unsigned bid, unsigned nb) {
   __shared__ double sh[NV][32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -31,13 +32,13 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials, u
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       double t = warp_sum(lane < nw ? sh[i][lane] : 0.0);
-      if (lane == 0) partials[blockIdx.x * NV + i] = t;
+      if (lane == 0) partials[bid * NV + i] = t;
     }
   }
   if (threadIdx.x == 0) {
     __threadfence();
     unsigned k = atomicAdd(ticket, 1u);
-    last = (k == gridDim.x - 1);
+    last = (k == nb - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -45,7 +46,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials, u
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     double t = 0.0;
-    for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) t += __ldcg(&partials[j * NV + i]);
+    for (unsigned j = threadIdx.x; j < nb; j += blockDim.x) t += __ldcg(&partials[j * NV + i]);
     t = warp_sum(t);
     __syncthreads();
     if (lane == 0) sh[i][wid] = t;

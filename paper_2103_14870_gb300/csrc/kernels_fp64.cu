@@ -59,8 +59,9 @@ __device__ __forceinline__ double normal_stress(const double e[3], double s, con
 // Damage: stress, non-local average, edge driver + relabel, chi
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads) k_tet_stress(DevMesh m, Material mt) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
   const int4 n = m.tets[t];
   const int nid[4] = {n.x, n.y, n.z, n.w};
@@ -96,11 +97,20 @@ __global__ void __launch_bounds__(kThreads) k_tet_stress(DevMesh m, Material mt)
   so[1] = make_double2(sf[2], sf[3]);
   so[2] = make_double2(sf[4], sf[5]);
 }
+__global__ void __launch_bounds__(kThreads) k_tet_stress(DevMesh m, Material mt, StepScalars sp) {
+  tet_stress_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_tet_stress(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_tet_stress, blockIdx.x, bid, nb);
+  tet_stress_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // Eq. 20 sum: thread per tet, neighbour lists in SELL-32 layout (coalesced
 // index/weight loads; the neighbour stresses are gathered from L2).
-__global__ void __launch_bounds__(kThreads) k_nonlocal(DevMesh m) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void nonlocal_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
   const int64_t g = t >> 5;
   const int lane = int(t & 31);
@@ -124,12 +134,21 @@ __global__ void __launch_bounds__(kThreads) k_nonlocal(DevMesh m) {
   o[1] = make_double2(acc[2], acc[3]);
   o[2] = make_double2(acc[4], acc[5]);
 }
+__global__ void __launch_bounds__(kThreads) k_nonlocal(DevMesh m, Material mt, StepScalars sp) {
+  nonlocal_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_nonlocal(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_nonlocal, blockIdx.x, bid, nb);
+  nonlocal_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // Per edge: sigma* = max over incident tets of the projected average (Eq. 20),
 // driver = sigma*/E (or sigma*), then zeta |= (driver >= threshold) (Eq. 21).
-__global__ void __launch_bounds__(kThreads) k_edge_driver(DevMesh m, Material mt) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  unsigned long long nb = 0, nn = 0;
+__device__ __forceinline__ void edge_driver_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
+  unsigned long long n_brk = 0, n_new = 0;
   if (i < m.NE) {
     const int2 ab = m.edges[i];
     double pa[3], pb[3];
@@ -149,16 +168,26 @@ __global__ void __launch_bounds__(kThreads) k_edge_driver(DevMesh m, Material mt
     const uint8_t old = m.labels[i];
     const uint8_t now = (old || d >= mt.threshold) ? 1 : 0;
     if (now != old) m.labels[i] = now;
-    nb = now;
-    nn = now && !old;
+    n_brk = now;
+    n_new = now && !old;
   }
-  warp_count(nb, m.counters + kCntBroken);
-  warp_count(nn, m.counters + kCntNewBroken);
+  warp_count(n_brk, m.counters + kCntBroken);
+  warp_count(n_new, m.counters + kCntNewBroken);
+}
+__global__ void __launch_bounds__(kThreads) k_edge_driver(DevMesh m, Material mt, StepScalars sp) {
+  edge_driver_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_edge_driver(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_edge_driver, blockIdx.x, bid, nb);
+  edge_driver_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // Eq. 22-25: chi from the tet's broken-edge mask and its local edge stresses.
-__global__ void __launch_bounds__(kThreads) k_tet_chi(DevMesh m, Material mt, uint64_t lut) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void tet_chi_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const uint64_t lut = mt.lut;
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   unsigned long long zero = 0;
   if (t < m.T) {
     int mask = 0;
@@ -184,13 +213,24 @@ __global__ void __launch_bounds__(kThreads) k_tet_chi(DevMesh m, Material mt, ui
   }
   warp_count(zero, m.counters + kCntChiZero);
 }
+__global__ void __launch_bounds__(kThreads) k_tet_chi(DevMesh m, Material mt, StepScalars sp) {
+  tet_chi_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_tet_chi(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_tet_chi, blockIdx.x, bid, nb);
+  tet_chi_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // ---------------------------------------------------------------------------
 // Assembly of A = (1 + dt alpha) M + (dt beta + dt^2) K*, b = dt (f_ext + f* - alpha M v - (beta + dt) K* v)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads) k_node_init(DevMesh m, double dt, double alpha, const double* f_ext) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void node_init_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const double dt = sp.dt, alpha = mt.alpha;
+  const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
   if (i >= m.N) return;
   const double mi = m.mass[i];
 #pragma unroll
@@ -201,6 +241,14 @@ __global__ void __launch_bounds__(kThreads) k_node_init(DevMesh m, double dt, do
   d[0] += cm;
   d[4] += cm;
   d[8] += cm;
+}
+__global__ void __launch_bounds__(kThreads) k_node_init(DevMesh m, Material mt, StepScalars sp) {
+  node_init_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_node_init(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_node_init, blockIdx.x, bid, nb);
+  node_init_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // One colour: no two tets share a node, so the read-modify-write scatter into
@@ -332,8 +380,10 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
 // force and mass damping.
 constexpr int kElemW64 = 104;
 
-__global__ void __launch_bounds__(128) k_elem64(DevMesh m, double dt, double beta) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const double dt = sp.dt, beta = mt.beta;
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
   double* out = m.ebuf + kElemW64 * t;
   const double chi = m.chi[t];
@@ -438,10 +488,21 @@ __global__ void __launch_bounds__(128) k_elem64(DevMesh m, double dt, double bet
   out[102] = 0.0;
   out[103] = 0.0;
 }
+__global__ void __launch_bounds__(128) k_elem64(DevMesh m, Material mt, StepScalars sp) {
+  elem64_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(128) kb_elem64(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_elem64, blockIdx.x, bid, nb);
+  elem64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void __launch_bounds__(256) k_gather64(DevMesh m, double dt, double alpha, const double* f_ext) {
+__device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const double dt = sp.dt, alpha = mt.alpha;
+  const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
+
   const int lane = threadIdx.x & 31;
-  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 5;
   if (i >= m.N) return;                               // whole warp leaves together
   const int rb = m.row_ptr[i], rl = m.row_ptr[i + 1] - rb;
   const int dslot = m.diag_blk[i];
@@ -467,6 +528,14 @@ __global__ void __launch_bounds__(256) k_gather64(DevMesh m, double dt, double a
     m.rhs[3 * i + lane] = acc + dt * ((f_ext ? f_ext[3 * i + lane] : 0.0) - alpha * mi * m.v[3 * i + lane]);
   }
 }
+__global__ void __launch_bounds__(256) k_gather64(DevMesh m, Material mt, StepScalars sp) {
+  gather64_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256) kb_gather64(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_gather64, blockIdx.x, bid, nb);
+  gather64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // ---------------------------------------------------------------------------
 // Projected block-Jacobi PCG (Sec. 4.3), all scalars on the device
@@ -488,8 +557,11 @@ __device__ __forceinline__ void spmv_row(const DevMesh& m, int64_t i, const doub
   y[2] = y2;
 }
 
-__global__ void __launch_bounds__(kThreads) k_set_pinned(DevMesh m, int64_t n_pinned, const double* pin_vel) {
-  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void set_pinned_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const int64_t n_pinned = sp.n_pinned;
+  const double* pin_vel = sp.has_pvel ? m.pin_vel : nullptr;
+
+  const int64_t p = bid * int64_t(blockDim.x) + threadIdx.x;
   if (p >= n_pinned) return;
   const int64_t id = m.pin_ids[p];
   if (id < 0 || id >= m.N) {
@@ -500,11 +572,20 @@ __global__ void __launch_bounds__(kThreads) k_set_pinned(DevMesh m, int64_t n_pi
 #pragma unroll
   for (int c = 0; c < 3; ++c) m.dv[3 * id + c] = (pin_vel ? pin_vel[3 * p + c] : 0.0) - m.v[3 * id + c];
 }
+__global__ void __launch_bounds__(kThreads) k_set_pinned(DevMesh m, Material mt, StepScalars sp) {
+  set_pinned_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_set_pinned(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_set_pinned, blockIdx.x, bid, nb);
+  set_pinned_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // r = b - A dv on free nodes, block-Jacobi inverse, z = P r, p = z; rz, rr.
-__global__ void __launch_bounds__(kThreads) k_pcg_init(DevMesh m) {
+__device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     double r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
     if (!m.pinned[i]) {
       double ad[3];
@@ -533,7 +614,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(DevMesh m) {
     }
   }
   double out[2];
-  if (grid_reduce<2>(v, m.partials, m.tickets + 0, out) && threadIdx.x == 0) {
+  if (grid_reduce<2>(v, m.partials, m.tickets + 0, out, bid, nb) && threadIdx.x == 0) {
     PcgState* s = m.pcg;
     s->rz = out[0];
     s->rr = out[1];
@@ -547,12 +628,21 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(DevMesh m) {
     }
   }
 }
+__global__ void __launch_bounds__(kThreads) k_pcg_init(DevMesh m, Material mt, StepScalars sp) {
+  pcg_init_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_pcg_init(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_pcg_init, blockIdx.x, bid, nb);
+  pcg_init_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // q = A p; pq = p . q; alpha = rz / pq (breakdown when pq <= 0)
-__global__ void __launch_bounds__(kThreads) k_pcg_spmv(DevMesh m) {
+__device__ __forceinline__ void pcg_spmv_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   if (m.pcg->done) return;
   double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     double y[3];
     spmv_row(m, i, m.p, y);
 #pragma unroll
@@ -562,7 +652,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(DevMesh m) {
     }
   }
   double out[1];
-  if (grid_reduce<1>(v, m.partials, m.tickets + 1, out) && threadIdx.x == 0) {
+  if (grid_reduce<1>(v, m.partials, m.tickets + 1, out, bid, nb) && threadIdx.x == 0) {
     PcgState* s = m.pcg;
     s->pq = out[0];
     if (!(out[0] > 0.0)) {
@@ -573,13 +663,22 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(DevMesh m) {
     }
   }
 }
+__global__ void __launch_bounds__(kThreads) k_pcg_spmv(DevMesh m, Material mt, StepScalars sp) {
+  pcg_spmv_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_pcg_spmv(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_pcg_spmv, blockIdx.x, bid, nb);
+  pcg_spmv_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // dv += alpha p; r -= alpha q; z = P r; rz_new, rr; convergence test
-__global__ void __launch_bounds__(kThreads) k_pcg_update(DevMesh m) {
+__device__ __forceinline__ void pcg_update_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   if (m.pcg->done) return;
   const double alpha = m.pcg->alpha;
   double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i]) continue;
     double r[3];
 #pragma unroll
@@ -598,7 +697,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(DevMesh m) {
     }
   }
   double out[2];
-  if (grid_reduce<2>(v, m.partials, m.tickets + 2, out) && threadIdx.x == 0) {
+  if (grid_reduce<2>(v, m.partials, m.tickets + 2, out, bid, nb) && threadIdx.x == 0) {
     PcgState* s = m.pcg;
     s->iters += 1;
     s->beta = out[0] / s->rz;
@@ -615,18 +714,36 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(DevMesh m) {
     }
   }
 }
+__global__ void __launch_bounds__(kThreads) k_pcg_update(DevMesh m, Material mt, StepScalars sp) {
+  pcg_update_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_pcg_update(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_pcg_update, blockIdx.x, bid, nb);
+  pcg_update_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void __launch_bounds__(kThreads) k_pcg_p(DevMesh m) {
+__device__ __forceinline__ void pcg_p_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   if (m.pcg->done) return;
   const double beta = m.pcg->beta;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(gridDim.x) * blockDim.x)
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(nb) * blockDim.x)
     m.p[i] = m.z[i] + beta * m.p[i];
+}
+__global__ void __launch_bounds__(kThreads) k_pcg_p(DevMesh m, Material mt, StepScalars sp) {
+  pcg_p_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_pcg_p(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_pcg_p, blockIdx.x, bid, nb);
+  pcg_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // ||b - A dv||^2 over free nodes, recomputed from scratch after the solve.
-__global__ void __launch_bounds__(kThreads) k_true_residual(DevMesh m) {
+__device__ __forceinline__ void true_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i]) continue;
     double y[3];
     spmv_row(m, i, m.dv, y);
@@ -637,76 +754,86 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(DevMesh m) {
     }
   }
   double out[1];
-  if (grid_reduce<1>(v, m.partials, m.tickets + 3, out) && threadIdx.x == 0) m.pcg->true_rr = out[0];
+  if (grid_reduce<1>(v, m.partials, m.tickets + 3, out, bid, nb) && threadIdx.x == 0) m.pcg->true_rr = out[0];
+}
+__global__ void __launch_bounds__(kThreads) k_true_residual(DevMesh m, Material mt, StepScalars sp) {
+  true_residual_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_true_residual(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_true_residual, blockIdx.x, bid, nb);
+  true_residual_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-__global__ void __launch_bounds__(kThreads) k_integrate(DevMesh m, double dt) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void integrate_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const double dt = sp.dt;
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
   if (i >= 3 * m.N) return;
   const double v = m.v[i] + m.dv[i];
   m.v[i] = v;
   m.x[i] += dt * v;
 }
-
-inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
-inline unsigned reduce_grid(int64_t n) {
-  int64_t b = (n + kThreads - 1) / kThreads;
-  return unsigned(b < 1 ? 1 : (b > kMaxPartials ? kMaxPartials : b));
+__global__ void __launch_bounds__(kThreads) k_integrate(DevMesh m, Material mt, StepScalars sp) {
+  integrate_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_integrate(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_integrate, blockIdx.x, bid, nb);
+  integrate_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 }  // namespace
 
-int launch_tet_stress(const DevMesh& m, const Material& mt, cudaStream_t s) {
-  k_tet_stress<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, mt);
-  return 1;
-}
-int launch_nonlocal(const DevMesh& m, cudaStream_t s) {
-  k_nonlocal<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_edge_driver(const DevMesh& m, const Material& mt, cudaStream_t s) {
-  k_edge_driver<<<blocks_for(m.NE, kThreads), kThreads, 0, s>>>(m, mt);
-  return 1;
-}
-int launch_tet_chi(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s) {
-  k_tet_chi<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, mt, lut);
-  return 1;
-}
-int launch_node_init(const DevMesh& m, double dt, const Material& mt, bool has_fext, cudaStream_t s) {
-  k_node_init<<<blocks_for(m.N, kThreads), kThreads, 0, s>>>(m, dt, mt.alpha, has_fext ? m.f_ext : nullptr);
-  return 1;
-}
-int launch_assemble(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s) {
+int launch_assemble_colour(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s) {
   if (t1 <= t0) return 0;
-  k_assemble<<<blocks_for(t1 - t0, 128), 128, 0, s>>>(m, dt, mt.beta, t0, t1);
+  k_assemble<<<unsigned((t1 - t0 + 127) / 128), 128, 0, s>>>(m, dt, mt.beta, t0, t1);
   return 1;
 }
-int launch_assemble_2phase(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s) {
-  k_elem64<<<blocks_for(m.T, 128), 128, 0, s>>>(m, dt, mt.beta);
-  k_gather64<<<blocks_for(32 * m.N, 256), 256, 0, s>>>(m, dt, mt.alpha, f_ext);
-  return 2;
-}
-int launch_set_pinned(const DevMesh& m, int64_t n_pinned, bool has_vel, cudaStream_t s) {
-  if (n_pinned <= 0) return 0;
-  k_set_pinned<<<blocks_for(n_pinned, kThreads), kThreads, 0, s>>>(m, n_pinned, has_vel ? m.pin_vel : nullptr);
+
+// launches of the kinds implemented in this file
+int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s) {
+  const LaunchDims d = launch_dims(kind, m, mt, sp);
+  if (d.blocks == 0) return 0;
+  switch (kind) {
+    case kB_tet_stress: k_tet_stress<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_nonlocal: k_nonlocal<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_edge_driver: k_edge_driver<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_tet_chi: k_tet_chi<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_node_init: k_node_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_elem64: k_elem64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_gather64: k_gather64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_set_pinned: k_set_pinned<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_pcg_init: k_pcg_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_pcg_spmv: k_pcg_spmv<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_pcg_update: k_pcg_update<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_pcg_p: k_pcg_p<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_true_residual: k_true_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_integrate: k_integrate<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    default: return -1;
+  }
   return 1;
 }
-int launch_pcg_init(const DevMesh& m, cudaStream_t s) {
-  k_pcg_init<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_pcg_iter(const DevMesh& m, cudaStream_t s, int which) {
-  if (which == 0) k_pcg_spmv<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
-  else if (which == 1) k_pcg_update<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
-  else k_pcg_p<<<reduce_grid(3 * m.N), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_true_residual(const DevMesh& m, cudaStream_t s) {
-  k_true_residual<<<reduce_grid(m.N), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_integrate(const DevMesh& m, double dt, cudaStream_t s) {
-  k_integrate<<<blocks_for(3 * m.N, kThreads), kThreads, 0, s>>>(m, dt);
+
+int launch_batch_fp64(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s) {
+  if (blocks == 0) return 0;
+  switch (kind) {
+    case kB_tet_stress: kb_tet_stress<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_nonlocal: kb_nonlocal<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_edge_driver: kb_edge_driver<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_tet_chi: kb_tet_chi<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_node_init: kb_node_init<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_elem64: kb_elem64<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_gather64: kb_gather64<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_set_pinned: kb_set_pinned<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_pcg_init: kb_pcg_init<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_pcg_spmv: kb_pcg_spmv<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_pcg_update: kb_pcg_update<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_pcg_p: kb_pcg_p<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_true_residual: kb_true_residual<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_integrate: kb_integrate<<<blocks, threads, 0, s>>>(tab); break;
+    default: return -1;
+  }
   return 1;
 }
 

@@ -82,8 +82,11 @@ __device__ __forceinline__ float normal_stress32(const float e[3], float s, cons
 // damage (Eq. 14-25) in FP32, threshold test in FP64
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads) k_tet_stress32(DevMesh m, float lam, float mu, float kappa, int avg) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void tet_stress32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const float lam = mt.lam32, mu = mt.mu32, kappa = mt.kappa32;
+  const int avg = mt.average_degraded;
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
   const MixDev& x = m.mx;
   const int4 n = m.tets[t];
@@ -134,15 +137,24 @@ __global__ void __launch_bounds__(kThreads) k_tet_stress32(DevMesh m, float lam,
   for (int k = 0; k < 6; ++k)
     sf[k] = normal_stress32(e[k], e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2], S, kappa);
 }
+__global__ void __launch_bounds__(kThreads) k_tet_stress32(DevMesh m, Material mt, StepScalars sp) {
+  tet_stress32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_tet_stress32, blockIdx.x, bid, nb);
+  tet_stress32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // Eq. 20 sum in FP32: one warp per tet over its CSR neighbour list (coalesced
 // index and weight loads; the gathered 32-byte stress rows of a tet's
 // neighbours come from short runs of consecutive tets), then a fixed-order
 // warp reduction (deterministic).
-__global__ void __launch_bounds__(kThreads) k_nonlocal32(DevMesh m) {
+__device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t t = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; t < m.T; t += nw) {
+  const int64_t nw = (int64_t(nb) * blockDim.x) >> 5;
+  for (int64_t t = (bid * int64_t(blockDim.x) + threadIdx.x) >> 5; t < m.T; t += nw) {
     const int64_t beg = m.mx.nb_ptr[t], end = m.mx.nb_ptr[t + 1];
     float acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t p = beg + lane; p < end; p += 32) {
@@ -164,11 +176,22 @@ __global__ void __launch_bounds__(kThreads) k_nonlocal32(DevMesh m) {
     }
   }
 }
+__global__ void __launch_bounds__(kThreads) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
+  nonlocal32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_nonlocal32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_nonlocal32, blockIdx.x, bid, nb);
+  nonlocal32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void __launch_bounds__(kThreads) k_edge_driver32(DevMesh m, float kappa, float inv_young, int stress_mode,
-                                                            double threshold) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  unsigned long long nb = 0, nn = 0;
+__device__ __forceinline__ void edge_driver32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const float kappa = mt.kappa32, inv_young = mt.inv_young32;
+  const int stress_mode = mt.driver_stress;
+  const double threshold = mt.threshold;
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
+  unsigned long long n_brk = 0, n_new = 0;
   if (i < m.NE) {
     const int2 ab = m.edges[i];
     float ua[3], ub[3], e0[3];
@@ -188,15 +211,26 @@ __global__ void __launch_bounds__(kThreads) k_edge_driver32(DevMesh m, float kap
     const uint8_t old = m.labels[i];
     const uint8_t now = (old || d >= threshold) ? 1 : 0;   // threshold test in FP64
     if (now != old) m.labels[i] = now;
-    nb = now;
-    nn = now && !old;
+    n_brk = now;
+    n_new = now && !old;
   }
-  warp_count(nb, m.counters + kCntBroken);
-  warp_count(nn, m.counters + kCntNewBroken);
+  warp_count(n_brk, m.counters + kCntBroken);
+  warp_count(n_new, m.counters + kCntNewBroken);
+}
+__global__ void __launch_bounds__(kThreads) k_edge_driver32(DevMesh m, Material mt, StepScalars sp) {
+  edge_driver32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_edge_driver32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_edge_driver32, blockIdx.x, bid, nb);
+  edge_driver32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-__global__ void __launch_bounds__(kThreads) k_tet_chi32(DevMesh m, float young, uint64_t lut) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void tet_chi32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const float young = mt.young32;
+  const uint64_t lut = mt.lut;
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   unsigned long long zero = 0;
   if (t < m.T) {
     int mask = 0;
@@ -223,6 +257,14 @@ __global__ void __launch_bounds__(kThreads) k_tet_chi32(DevMesh m, float young, 
   }
   warp_count(zero, m.counters + kCntChiZero);
 }
+__global__ void __launch_bounds__(kThreads) k_tet_chi32(DevMesh m, Material mt, StepScalars sp) {
+  tet_chi32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_tet_chi32, blockIdx.x, bid, nb);
+  tet_chi32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // ---------------------------------------------------------------------------
 // Two-phase assembly, no colours and no atomics.
@@ -237,8 +279,10 @@ __global__ void __launch_bounds__(kThreads) k_tet_chi32(DevMesh m, float young, 
 
 constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad (16-byte rows)
 
-__global__ void __launch_bounds__(128) k_elem32(DevMesh m, float sKv, float cv, float dtf) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const float sKv = sp.sKv, cv = sp.cv, dtf = sp.dtf;
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
   const MixDev& x = m.mx;
   float4* out = reinterpret_cast<float4*>(x.ebuf + kElemW * t);
@@ -349,10 +393,20 @@ __global__ void __launch_bounds__(128) k_elem32(DevMesh m, float sKv, float cv, 
 #pragma unroll
   for (int q = 0; q < kElemW / 4; ++q) out[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
+__global__ void __launch_bounds__(128) k_elem32(DevMesh m, Material mt, StepScalars sp) {
+  elem32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(128) kb_elem32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_elem32, blockIdx.x, bid, nb);
+  elem32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void __launch_bounds__(256) k_gather32(DevMesh m, float dtf, float alphaf, float cmf) {
+__device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const float dtf = sp.dtf, alphaf = sp.alphaf, cmf = sp.cmf;
+
   const int lane = threadIdx.x & 31;
-  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 5;
   if (i >= m.N) return;                               // whole warp leaves together
   __shared__ float dg[8][9];
   const int wib = threadIdx.x >> 5;
@@ -383,7 +437,7 @@ __global__ void __launch_bounds__(256) k_gather32(DevMesh m, float dtf, float al
       const int pr = m.np_pair[k];
       acc += x.ebuf[kElemW * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
     }
-    const float fe = x.fext32 ? x.fext32[3 * i + lane] : 0.f;
+    const float fe = sp.has_fext ? x.fext32[3 * i + lane] : 0.f;
     x.rhs32[3 * i + lane] = acc + dtf * (fe - alphaf * mi * x.v32[3 * i + lane]);
   }
   __syncwarp();
@@ -399,11 +453,29 @@ __global__ void __launch_bounds__(256) k_gather32(DevMesh m, float dtf, float al
     pi[6] = c20 * id; pi[7] = c21 * id; pi[8] = c22 * id;
   }
 }
+__global__ void __launch_bounds__(256) k_gather32(DevMesh m, Material mt, StepScalars sp) {
+  gather32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256) kb_gather32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_gather32, blockIdx.x, bid, nb);
+  gather32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // f_ext in FP32 for the gather (one conversion per entry)
-__global__ void __launch_bounds__(kThreads) k_fext32(DevMesh m, const double* f) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void fext32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const double* f = m.f_ext;
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
   if (i < 3 * m.N) m.mx.fext32[i] = float(f[i]);
+}
+__global__ void __launch_bounds__(kThreads) k_fext32(DevMesh m, Material mt, StepScalars sp) {
+  fext32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_fext32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_fext32, blockIdx.x, bid, nb);
+  fext32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +515,7 @@ __device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
 
 template <int NV>
 __device__ __forceinline__ bool grid_reduce_df(float (&hi)[NV], float (&lo)[NV], double* partials, unsigned* ticket,
-                                               double (&out)[NV]) {
+                                               double (&out)[NV], unsigned bid, unsigned nb) {
   __shared__ float sh[NV][2][32];
   __shared__ bool last;
   float2* part = reinterpret_cast<float2*>(partials);
@@ -462,12 +534,12 @@ __device__ __forceinline__ bool grid_reduce_df(float (&hi)[NV], float (&lo)[NV],
     for (int i = 0; i < NV; ++i) {
       float h = lane < nw ? sh[i][0][lane] : 0.f, l = lane < nw ? sh[i][1][lane] : 0.f;
       df_warp_sum(h, l);
-      if (lane == 0) part[blockIdx.x * NV + i] = make_float2(h, l);
+      if (lane == 0) part[bid * NV + i] = make_float2(h, l);
     }
   }
   if (threadIdx.x == 0) {
     __threadfence();
-    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    last = (atomicAdd(ticket, 1u) == nb - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -475,7 +547,7 @@ __device__ __forceinline__ bool grid_reduce_df(float (&hi)[NV], float (&lo)[NV],
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     float h = 0.f, l = 0.f;
-    for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) {
+    for (unsigned j = threadIdx.x; j < nb; j += blockDim.x) {
       const float2 v = __ldcg(&part[j * NV + i]);
       df_add(h, l, v.x, v.y);
     }
@@ -508,15 +580,16 @@ __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float
 // blocks j, j+16, ...), then a 16-lane double-float reduction.  The inner
 // solve's right-hand side is the leading float of r; ||r||^2 accumulates in
 // double-float.
-__global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, int first) {
+__device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb, int first) {
+
   IrState* S = m.mx.ir;
   if (!first && (S->done || !S->applied)) return;   // no new correction yet: nothing to check
   const MixDev& x = m.mx;
   const int j16 = threadIdx.x & 15;
   const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
   float nh_[1] = {0.f}, nl_[1] = {0.f};
-  const int64_t nh = (int64_t(gridDim.x) * blockDim.x) >> 4;
-  for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
+  const int64_t nh = (int64_t(nb) * blockDim.x) >> 4;
+  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
     float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
     const bool fixed = m.pinned[i];
     if (!fixed) {
@@ -560,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, int first) 
     }
   }
   double out[1];
-  if (grid_reduce_df<1>(nh_, nl_, m.partials, m.tickets + 4, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<1>(nh_, nl_, m.partials, m.tickets + 4, out, bid, nb) && threadIdx.x == 0) {
     if (first) {
       S->bb = out[0];
       S->sweeps = 0;
@@ -580,15 +653,24 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, int first) 
     }
   }
 }
+__global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, Material mt, StepScalars sp, int first) {
+  ir_residual_body(m, mt, sp, blockIdx.x, gridDim.x, first);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_residual(const BatchTab* __restrict__ tab, int first) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_residual, blockIdx.x, bid, nb);
+  ir_residual_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb, first);
+}
 
 // inner PCG start (only after a fresh residual; otherwise the current inner
 // solve continues): r32 = r, z = P r, p = z, d = 0
-__global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m) {
+__device__ __forceinline__ void ir_inner_init_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   IrState* S = m.mx.ir;
   if (S->done || !S->applied) return;
   const MixDev& x = m.mx;
   float h[1] = {0.f}, l[1] = {0.f};
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     float r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
     if (!m.pinned[i]) {
 #pragma unroll
@@ -607,7 +689,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m) {
     }
   }
   double out[1];
-  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 5, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 5, out, bid, nb) && threadIdx.x == 0) {
     S->rz = out[0];
     S->in_rr0 = S->rr;
     S->in_iters = 0;
@@ -615,17 +697,26 @@ __global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m) {
     S->applied = 0;
   }
 }
+__global__ void __launch_bounds__(kThreads) k_ir_inner_init(DevMesh m, Material mt, StepScalars sp) {
+  ir_inner_init_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_inner_init(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_inner_init, blockIdx.x, bid, nb);
+  ir_inner_init_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // q = A32 p with half a warp per block row (coalesced block loads), p . q in double-float
-__global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m) {
+__device__ __forceinline__ void ir_spmv_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
   const MixDev& x = m.mx;
   const int j16 = threadIdx.x & 15;
   const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
   float h[1] = {0.f}, l[1] = {0.f};
-  const int64_t nh = (int64_t(gridDim.x) * blockDim.x) >> 4;
-  for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
+  const int64_t nh = (int64_t(nb) * blockDim.x) >> 4;
+  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
     for (int b = m.row_ptr[i] + j16; b < m.row_ptr[i + 1]; b += 16) {
       const int64_t j = m.col[b];
@@ -651,7 +742,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m) {
     }
   }
   double out[1];
-  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 6, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 6, out, bid, nb) && threadIdx.x == 0) {
     S->pq = out[0];
     if (!(out[0] > 0.0)) {
       if (!isfinite(out[0])) {
@@ -668,14 +759,23 @@ __global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m) {
     }
   }
 }
+__global__ void __launch_bounds__(kThreads) k_ir_spmv(DevMesh m, Material mt, StepScalars sp) {
+  ir_spmv_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_spmv(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_spmv, blockIdx.x, bid, nb);
+  ir_spmv_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m) {
+__device__ __forceinline__ void ir_update_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
   const MixDev& x = m.mx;
   const float alpha = S->alpha32;
   float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i]) continue;
     float r[3];
 #pragma unroll
@@ -694,7 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m) {
     }
   }
   double out[2];
-  if (grid_reduce_df<2>(h, l, m.partials, m.tickets + 7, out) && threadIdx.x == 0) {
+  if (grid_reduce_df<2>(h, l, m.partials, m.tickets + 7, out, bid, nb) && threadIdx.x == 0) {
     S->in_iters += 1;
     S->total_iters += 1;
     S->beta = out[0] / S->rz;
@@ -705,21 +805,39 @@ __global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m) {
       S->in_done = 1;
   }
 }
+__global__ void __launch_bounds__(kThreads) k_ir_update(DevMesh m, Material mt, StepScalars sp) {
+  ir_update_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_update(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_update, blockIdx.x, bid, nb);
+  ir_update_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void __launch_bounds__(kThreads) k_ir_p(DevMesh m) {
+__device__ __forceinline__ void ir_p_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
   const float beta = S->beta32;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(gridDim.x) * blockDim.x)
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(nb) * blockDim.x)
     m.mx.p32[i] = m.mx.z32[i] + beta * m.mx.p32[i];
+}
+__global__ void __launch_bounds__(kThreads) k_ir_p(DevMesh m, Material mt, StepScalars sp) {
+  ir_p_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_p(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_p, blockIdx.x, bid, nb);
+  ir_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // dv += d on free rows, kept as a float pair (dv_hi + dv_lo) on the FP32 pipe
-__global__ void __launch_bounds__(kThreads) k_ir_apply(DevMesh m) {
+__device__ __forceinline__ void ir_apply_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
   IrState* S = m.mx.ir;
   if (S->done || !S->in_done || S->applied) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) S->applied = 1;   // read by the next kernels only
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(gridDim.x) * blockDim.x) {
+  if (bid == 0 && threadIdx.x == 0) S->applied = 1;   // read by the next kernels only
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i / 3]) continue;
     float hi = m.mx.dv_hi[i], lo = m.mx.dv_lo[i];
     df_add(hi, lo, m.mx.d32[i], 0.f);
@@ -727,10 +845,20 @@ __global__ void __launch_bounds__(kThreads) k_ir_apply(DevMesh m) {
     m.mx.dv_lo[i] = lo;
   }
 }
+__global__ void __launch_bounds__(kThreads) k_ir_apply(DevMesh m, Material mt, StepScalars sp) {
+  ir_apply_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_apply(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_apply, blockIdx.x, bid, nb);
+  ir_apply_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // v += dv (dv = dv_hi + dv_lo), x += dt v; refresh the FP32 copies of u = x - X and v
-__global__ void __launch_bounds__(kThreads) k_integrate32(DevMesh m, double dt) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void integrate32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const double dt = sp.dt;
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
   if (i >= 3 * m.N) return;
   const double dv = double(m.mx.dv_hi[i]) + double(m.mx.dv_lo[i]);
   m.dv[i] = dv;
@@ -741,10 +869,19 @@ __global__ void __launch_bounds__(kThreads) k_integrate32(DevMesh m, double dt) 
   m.mx.u32[i] = float(xn - m.mx.X[i]);
   m.mx.v32[i] = float(v);
 }
+__global__ void __launch_bounds__(kThreads) k_integrate32(DevMesh m, Material mt, StepScalars sp) {
+  integrate32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_integrate32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_integrate32, blockIdx.x, bid, nb);
+  integrate32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 // FP32 copies after a state change; also the float-pair split of dv
-__global__ void __launch_bounds__(kThreads) k_refresh32(DevMesh m) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void refresh32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
   if (i >= 3 * m.N) return;
   m.mx.u32[i] = float(m.x[i] - m.mx.X[i]);
   m.mx.v32[i] = float(m.v[i]);
@@ -753,86 +890,77 @@ __global__ void __launch_bounds__(kThreads) k_refresh32(DevMesh m) {
   m.mx.dv_hi[i] = hi;
   m.mx.dv_lo[i] = float(d - double(hi));
 }
+__global__ void __launch_bounds__(kThreads) k_refresh32(DevMesh m, Material mt, StepScalars sp) {
+  refresh32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_refresh32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_refresh32, blockIdx.x, bid, nb);
+  refresh32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
-__global__ void k_chi_to32(DevMesh m) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void chi_to32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t < m.T) m.mx.chi32[t] = float(m.chi[t]);
 }
-
-inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
-// reducing kernels of the refinement: at most 4 CTAs per SM (grid-stride loops),
-// so the final double-float pass over the partials stays short
-inline unsigned ir_grid(int64_t n) {
-  int64_t b = (n + kThreads - 1) / kThreads;
-  return unsigned(b < 1 ? 1 : (b > 4 * 152 ? 4 * 152 : b));
+__global__ void k_chi_to32(DevMesh m, Material mt, StepScalars sp) {
+  chi_to32_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
-inline unsigned reduce_grid(int64_t n) {
-  int64_t b = (n + kThreads - 1) / kThreads;
-  return unsigned(b < 1 ? 1 : (b > kMaxPartials ? kMaxPartials : b));
+__global__ void kb_chi_to32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_chi_to32, blockIdx.x, bid, nb);
+  chi_to32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 }  // namespace
 
-int launch_tet_stress32(const DevMesh& m, const Material& mt, cudaStream_t s) {
-  k_tet_stress32<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, float(mt.lam), float(mt.mu), float(mt.kappa),
-                                                               mt.average_degraded);
-  return 1;
-}
-int launch_nonlocal32(const DevMesh& m, cudaStream_t s) {
-  k_nonlocal32<<<blocks_for(32 * m.T, kThreads), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_edge_driver32(const DevMesh& m, const Material& mt, cudaStream_t s) {
-  k_edge_driver32<<<blocks_for(m.NE, kThreads), kThreads, 0, s>>>(m, float(mt.kappa), float(1.0 / mt.young),
-                                                                 mt.driver_stress, mt.threshold);
-  return 1;
-}
-int launch_tet_chi32(const DevMesh& m, const Material& mt, uint64_t lut, cudaStream_t s) {
-  k_tet_chi32<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m, float(mt.young), lut);
-  return 1;
-}
-int launch_assemble32(const DevMesh& m, const Material& mt, double dt, const double* f_ext, cudaStream_t s) {
-  int n = 0;
-  k_elem32<<<blocks_for(m.T, 128), 128, 0, s>>>(m, float(dt * mt.beta + dt * dt), float(mt.beta + dt), float(dt));
-  ++n;
-  DevMesh v = m;
-  if (f_ext) {
-    k_fext32<<<blocks_for(3 * m.N, kThreads), kThreads, 0, s>>>(m, f_ext);
-    ++n;
-  } else {
-    v.mx.fext32 = nullptr;
+int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first) {
+  const LaunchDims d = launch_dims(kind, m, mt, sp);
+  if (d.blocks == 0) return 0;
+  switch (kind) {
+    case kB_tet_stress32: k_tet_stress32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_nonlocal32: k_nonlocal32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_edge_driver32: k_edge_driver32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_tet_chi32: k_tet_chi32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_elem32: k_elem32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_gather32: k_gather32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_fext32: k_fext32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_residual: k_ir_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp, first); break;
+    case kB_ir_inner_init: k_ir_inner_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_spmv: k_ir_spmv<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_update: k_ir_update<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_p: k_ir_p<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_apply: k_ir_apply<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_integrate32: k_integrate32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_refresh32: k_refresh32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_chi_to32: k_chi_to32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    default: return -1;
   }
-  k_gather32<<<blocks_for(32 * m.N, 256), 256, 0, s>>>(v, float(dt), float(mt.alpha), float(1.0 + dt * mt.alpha));
-  return n + 1;
-}
-int launch_ir_residual(const DevMesh& m, int first, cudaStream_t s) {
-  k_ir_residual<<<ir_grid(16 * m.N), kThreads, 0, s>>>(m, first);
   return 1;
 }
-int launch_ir_inner_init(const DevMesh& m, cudaStream_t s) {
-  k_ir_inner_init<<<ir_grid(m.N), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_ir_inner_iter(const DevMesh& m, cudaStream_t s, int which) {
-  if (which == 0) k_ir_spmv<<<ir_grid(16 * m.N), kThreads, 0, s>>>(m);
-  else if (which == 1) k_ir_update<<<ir_grid(m.N), kThreads, 0, s>>>(m);
-  else k_ir_p<<<ir_grid(3 * m.N), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_ir_apply(const DevMesh& m, cudaStream_t s) {
-  k_ir_apply<<<ir_grid(3 * m.N), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_integrate32(const DevMesh& m, double dt, cudaStream_t s) {
-  k_integrate32<<<blocks_for(3 * m.N, kThreads), kThreads, 0, s>>>(m, dt);
-  return 1;
-}
-int launch_chi_to32(const DevMesh& m, cudaStream_t s) {
-  k_chi_to32<<<blocks_for(m.T, kThreads), kThreads, 0, s>>>(m);
-  return 1;
-}
-int launch_refresh32(const DevMesh& m, cudaStream_t s) {
-  k_refresh32<<<blocks_for(3 * m.N, kThreads), kThreads, 0, s>>>(m);
+
+int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s, int first) {
+  if (blocks == 0) return 0;
+  switch (kind) {
+    case kB_tet_stress32: kb_tet_stress32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_nonlocal32: kb_nonlocal32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_edge_driver32: kb_edge_driver32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_tet_chi32: kb_tet_chi32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_elem32: kb_elem32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_gather32: kb_gather32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_fext32: kb_fext32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_residual: kb_ir_residual<<<blocks, threads, 0, s>>>(tab, first); break;
+    case kB_ir_inner_init: kb_ir_inner_init<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_spmv: kb_ir_spmv<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_update: kb_ir_update<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_p: kb_ir_p<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_apply: kb_ir_apply<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_integrate32: kb_integrate32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_refresh32: kb_refresh32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_chi_to32: kb_chi_to32<<<blocks, threads, 0, s>>>(tab); break;
+    default: return -1;
+  }
   return 1;
 }
 
