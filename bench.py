@@ -171,6 +171,51 @@ def run_reference(args) -> None:
                       "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_batch(args, gf, torch, barrier, stream) -> dict:
+    """64 Kuhn boxes of uneven size (2k-80k tets, log-uniform, seed 2), mixed
+    precision, stepped together: autotuned schedule, then timed."""
+    from workloads import batch_configs
+    ws = batch_configs()
+    meshes = [gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=w.threshold,
+                                                          radius=w.radius), precision=gf.MIXED, cg_rtol=1e-6)
+              for w in ws]
+    b = gf.Batch(meshes)
+    f = [torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda") for w in ws]
+    pins = [torch.tensor(w.pinned, dtype=torch.int32, device="cuda") for w in ws]
+    dt = ws[0].dt
+    tuned, tuned_ms = b.autotune(dt, f, pins, trial_steps=3)
+    out = {"workload": "64 Kuhn boxes, 2k-80k tets (log-uniform, seed 2), E in [1e4, 1e8]",
+           "n_meshes": len(ws), "n_tets_total": int(sum(w.n_tets for w in ws)), "precision": "mixed",
+           "cg_rtol": 1e-6, "tuning": tuned, "autotune_ms_per_step": tuned_ms}
+    per_mode = {}
+    for graph in (1, 0):
+        b.tuning_set(graph=graph, chunk=tuned["chunk"] if tuned["graph"] == 0 else 8)
+        for _ in range(args.warmup):
+            b.step(dt, f, pins)
+        l0 = b.launch_count()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            st = b.step(dt, f, pins)
+            iters.append(sum(x["cg_iters"] for x in st) / len(st))
+            assert all(x["status"] == 0 and x["rel_res"] <= 1e-6 for x in st)
+        e1.record(stream)
+        barrier()
+        ms_b = e0.elapsed_time(e1) / args.steps
+        per_mode["graph" if graph else "stream"] = {"ms_per_step": ms_b, "gpu_launches": b.launch_count() - l0,
+                                                    "cg_iters_mean": statistics.mean(iters)}
+    b.tuning_set(graph=tuned["graph"], chunk=tuned["chunk"])
+    best = per_mode["graph" if tuned["graph"] else "stream"]
+    out.update(ms_per_step=best["ms_per_step"], element_updates_per_s=out["n_tets_total"] / (best["ms_per_step"] * 1e-3),
+               modes=per_mode)
+    b.close()
+    for m in meshes:
+        m.close()
+    return out
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -238,6 +283,7 @@ def run_ours(args) -> None:
     mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
     mix_ms, mix_launches, mix_prof, mix_it, mix_sw = timed(mm, args.steps)
     mm.close()
+    batch = run_batch(args, gf, torch, barrier, stream) if not args.no_batch else None
     t_all = torch.tensor([ms, e2e_ms, mix_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
@@ -272,6 +318,7 @@ def run_ours(args) -> None:
                   "gpu_launches": mix_launches, "dtype": "f32 tangents/SpMV/PCG, f64 state/residual/dots/threshold",
                   "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mix_prof.items()},
                   "roofline": mix_roof},
+        "batch": batch,
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "kernel_launches": {k: v[1] for k, v in prof.items()},
         "clocks": clocks,
@@ -306,6 +353,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched form")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="form run by --profile-step")

@@ -235,6 +235,56 @@ gf_status gf_bsr_pcg_solve_static(const int32_t* row_ptr, const int32_t* col, co
                                   const double* b, double* x, const uint8_t* fixed, double rtol, int32_t maxit,
                                   void* stream, int32_t* iters, double* rel_res);
 
+/* ---------------------------------------------------------------------------
+ * Batched stepping (many independent meshes per launch).
+ *
+ * A batch groups meshes created on one device with one precision; each mesh
+ * keeps its own state, options and getters.  gf_batch_step() advances every
+ * mesh by one step of Algorithm 1 with one launch per kernel kind for the whole
+ * batch (each CTA maps to one mesh), and, by default, replays the step as a
+ * single CUDA graph whose solver loop is a device-side conditional node: the
+ * meshes converge independently and the host is not consulted between
+ * iterations.  All work runs on the first mesh's stream; do not step the
+ * member meshes individually while the batch is stepping.
+ * ------------------------------------------------------------------------- */
+typedef struct gf_batch gf_batch;
+
+typedef struct gf_batch_tuning {
+  int32_t graph;        /* 1: whole step as one CUDA graph with a device-side solve loop (default)
+                           0: stream launches, host checks convergence every `chunk` iterations */
+  int32_t chunk;        /* iterations between host checks when graph = 0 (0 -> 8) */
+  int32_t reserved[6];  /* set to 0 */
+} gf_batch_tuning;
+
+/* meshes: n handles (1 <= n <= 256), same device and precision.  The batch
+ * does not own the meshes: destroy it before them. */
+gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out);
+void gf_batch_destroy(gf_batch* batch);
+
+/* One step of every mesh with a common dt.  Per-mesh inputs are arrays of n
+ * pointers (the array itself may be NULL for none, entries may be NULL):
+ * f_ext[k] float64 [3 * n_nodes_k], pinned[k] int32 [n_pinned[k]], pinned_vel[k]
+ * float64 [3 * n_pinned[k]] (NULL = zero); n_pinned may be NULL (no pins).  The
+ * pointed-to arrays follow `mem`.  stats: n entries or NULL.  Returns the first
+ * non-OK status of any mesh (every mesh is stepped). */
+gf_status gf_batch_step(gf_batch* batch, double dt, const double* const* f_ext, const int32_t* const* pinned,
+                        const int64_t* n_pinned, const double* const* pinned_vel, int32_t mem, gf_step_stats* stats);
+
+gf_status gf_batch_tuning_set(gf_batch* batch, const gf_batch_tuning* tuning);
+gf_status gf_batch_tuning_get(const gf_batch* batch, gf_batch_tuning* tuning);
+
+/* Autotuner: times `trial_steps` batch steps under each candidate schedule
+ * (graph replay vs stream launches with several host-check intervals) on a
+ * copy of the current state, restores the state, keeps the fastest schedule
+ * and returns it in *best (may be NULL) and its time per step in *ms (may be
+ * NULL).  Inputs as in gf_batch_step. */
+gf_status gf_batch_autotune(gf_batch* batch, double dt, const double* const* f_ext, const int32_t* const* pinned,
+                            const int64_t* n_pinned, const double* const* pinned_vel, int32_t mem,
+                            int32_t trial_steps, gf_batch_tuning* best, double* ms);
+
+/* Kernel launches issued by the batch (graph replays count the kernels run). */
+int64_t gf_batch_launch_count(const gf_batch* batch);
+
 const char* gf_status_string(gf_status s);
 const char* gf_last_error(void);
 

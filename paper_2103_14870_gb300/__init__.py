@@ -4,6 +4,6 @@ The compute path is the CUDA library under ``csrc/`` behind the C ABI in
 ``include/graphfem.h``; ``graphfem`` is its Python binding.
 """
 from .graphfem import (  # noqa: F401
-    DRIVER_STRAIN, DRIVER_STRESS, FP64, MEM_DEVICE, MEM_HOST, MIXED, GraphFEMError, Mesh, load_library,
+    Batch, DRIVER_STRAIN, DRIVER_STRESS, FP64, MEM_DEVICE, MEM_HOST, MIXED, GraphFEMError, Mesh, load_library,
     bsr_pcg_solve_static, material, mesh_create, mesh_plan,
 )

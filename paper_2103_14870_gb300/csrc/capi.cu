@@ -57,6 +57,7 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_ir_residual: case kB_ir_spmv: return {ir_grid(16 * N), 256};
     case kB_ir_inner_init: case kB_ir_update: return {ir_grid(N), 256};
     case kB_ir_p: case kB_ir_apply: return {ir_grid(3 * N), 256};
+    case kB_step_begin: return {cdiv(3 * N, 256), 256};
   }
   return {0u, 256};
 }
@@ -966,5 +967,512 @@ gf_status gf_profile_reset(gf_mesh* m) {
 }
 
 int64_t gf_launch_count(const gf_mesh* m) { return m ? m->launches : 0; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched stepping
+// ===========================================================================
+namespace gf {
+namespace {
+
+// Solver scalars every mesh starts a step from.
+struct BatchInit {
+  PcgState pcg;
+  IrState ir;
+};
+
+// What the host reads back after a batch step, per mesh.
+struct BatchOut {
+  PcgState pcg;
+  IrState ir;
+  unsigned long long cnt[kCntMax];
+};
+
+// Per-step reset of every mesh's solver scalars, counters, pinned flags and dv.
+__global__ void __launch_bounds__(256) kb_step_begin(const BatchTab* __restrict__ tab, const BatchInit* init,
+                                                      int mixed, int* iter) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_step_begin, blockIdx.x, bid, nb);
+  const DevMesh& m = tab->mesh[k];
+  const int64_t i0 = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (i0 == 0) {
+    if (mixed) *m.mx.ir = init[k].ir;
+    else *m.pcg = init[k].pcg;
+#pragma unroll
+    for (int c = 0; c < kCntMax; ++c) m.counters[c] = 0ull;
+    if (k == 0) *iter = 0;
+  }
+  for (int64_t i = i0; i < 3 * m.N; i += int64_t(nb) * blockDim.x) {
+    m.dv[i] = 0.0;
+    if (i < m.N) m.pinned[i] = 0;
+  }
+}
+
+// Solve-loop condition: continue while any mesh is unconverged (and below the cap).
+__global__ void __launch_bounds__(256) kb_any_active(const BatchTab* __restrict__ tab, int mixed, int* iter, int cap,
+                                                      cudaGraphConditionalHandle h) {
+  int active = 0;
+  for (int k = threadIdx.x; k < tab->n; k += blockDim.x)
+    active |= mixed ? !tab->mesh[k].mx.ir->done : !tab->mesh[k].pcg->done;
+  active = __syncthreads_or(active);
+  if (threadIdx.x == 0) {
+    const int it = ++(*iter);
+    cudaGraphSetConditional(h, (active && it < cap) ? 1u : 0u);
+  }
+}
+
+__global__ void kb_collect(const BatchTab* __restrict__ tab, int mixed, BatchOut* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= tab->n) return;
+  const DevMesh& m = tab->mesh[k];
+  if (mixed) out[k].ir = *m.mx.ir;
+  else out[k].pcg = *m.pcg;
+#pragma unroll
+  for (int c = 0; c < kCntMax; ++c) out[k].cnt[c] = m.counters[c];
+}
+
+}  // namespace
+}  // namespace gf
+
+struct gf_batch {
+  std::vector<gf_mesh*> ms;
+  int n = 0;
+  bool mixed = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t body_stream = nullptr;
+  BatchTab* htab = nullptr;          // pinned host mirror
+  BatchTab* dtab = nullptr;
+  BatchInit* dinit = nullptr;
+  BatchOut* hout = nullptr;
+  BatchOut* dout = nullptr;
+  int* d_iter = nullptr;
+  int* h_iter = nullptr;
+  unsigned blocks[kBKinds] = {};
+  std::vector<int32_t> shape;        // offsets the graph was captured with
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  gf_batch_tuning tune{};
+  int cap = 0;
+  int64_t launches = 0;
+  int64_t prefix_kernels = 0, body_kernels = 0, suffix_kernels = 0;
+};
+
+namespace {
+
+void batch_free(gf_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->dtab) cudaFree(b->dtab);
+  if (b->dinit) cudaFree(b->dinit);
+  if (b->dout) cudaFree(b->dout);
+  if (b->d_iter) cudaFree(b->d_iter);
+  if (b->htab) cudaFreeHost(b->htab);
+  if (b->hout) cudaFreeHost(b->hout);
+  if (b->h_iter) cudaFreeHost(b->h_iter);
+  if (b->body_stream) cudaStreamDestroy(b->body_stream);
+}
+
+const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64,
+                           kB_set_pinned, kB_pcg_init};
+const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
+const int kSuffixFp64[] = {kB_true_residual, kB_integrate};
+const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32,
+                            kB_gather32, kB_set_pinned, kB_refresh32};
+const int kBodyMixed[] = {kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_ir_residual};
+const int kSuffixMixed[] = {kB_integrate32};
+
+template <size_t K>
+int64_t enqueue_kinds(gf_batch* b, const int (&kinds)[K], cudaStream_t s) {
+  int64_t L = 0;
+  for (int kind : kinds) L += launch_batch(kind, b->dtab, b->blocks[kind], s, 0);
+  return L;
+}
+
+int64_t enqueue_prefix(gf_batch* b, cudaStream_t s) {
+  int64_t L = 0;
+  kb_step_begin<<<b->blocks[kB_step_begin], 256, 0, s>>>(b->dtab, b->dinit, b->mixed ? 1 : 0, b->d_iter);
+  ++L;
+  if (b->mixed) {
+    L += enqueue_kinds(b, kPrefixMixed, s);
+    L += launch_batch(kB_ir_residual, b->dtab, b->blocks[kB_ir_residual], s, 1);
+  } else {
+    L += enqueue_kinds(b, kPrefixFp64, s);
+  }
+  return L;
+}
+
+int64_t enqueue_body(gf_batch* b, cudaStream_t s) {
+  if (b->mixed) {
+    int64_t L = 0;
+    for (int kind : kBodyMixed) L += launch_batch(kind, b->dtab, b->blocks[kind], s, 0);
+    return L;
+  }
+  return enqueue_kinds(b, kBodyFp64, s);
+}
+
+int64_t enqueue_suffix(gf_batch* b, cudaStream_t s) {
+  int64_t L = b->mixed ? enqueue_kinds(b, kSuffixMixed, s) : enqueue_kinds(b, kSuffixFp64, s);
+  kb_collect<<<unsigned((b->n + 127) / 128), 128, 0, s>>>(b->dtab, b->mixed ? 1 : 0, b->dout);
+  return L + 1;
+}
+
+#define GB_CK(call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return GF_CUDA_ERR;                                                                   \
+    }                                                                                       \
+  } while (0)
+
+gf_status build_graph(gf_batch* b) {
+  cudaStream_t s = b->stream;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaGraph_t g;
+  GB_CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  GB_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  GB_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  b->prefix_kernels = enqueue_prefix(b, s);
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  GB_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, &ed, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t wn;
+  GB_CK(cudaGraphAddNode(&wn, g, deps, ed, nd, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  GB_CK(cudaStreamBeginCaptureToGraph(b->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  b->body_kernels = enqueue_body(b, b->body_stream);
+  kb_any_active<<<1, 256, 0, b->body_stream>>>(b->dtab, b->mixed ? 1 : 0, b->d_iter, b->cap, h);
+  ++b->body_kernels;
+  GB_CK(cudaStreamEndCapture(b->body_stream, &body));
+  GB_CK(cudaStreamUpdateCaptureDependencies(s, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  b->suffix_kernels = enqueue_suffix(b, s);
+  GB_CK(cudaMemcpyAsync(b->h_iter, b->d_iter, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamEndCapture(s, &g));
+  GB_CK(cudaGraphInstantiate(&b->exec, g, 0));
+  b->graph = g;
+  return GF_OK;
+}
+
+// stage the per-mesh inputs, step scalars and launch shape; rebuild the graph if the shape changed
+gf_status batch_prepare(gf_batch* b, double dt, const double* const* f_ext, const int32_t* const* pinned,
+                        const int64_t* n_pinned, const double* const* pinned_vel, int32_t mem) {
+  cudaStream_t s = b->stream;
+  const cudaMemcpyKind kind = mem == GF_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int k = 0; k < b->n; ++k) {
+    gf_mesh* m = b->ms[k];
+    const int64_t np = n_pinned ? n_pinned[k] : 0;
+    const int32_t* pk = pinned ? pinned[k] : nullptr;
+    if (np < 0 || np > m->dm.N || (np > 0 && !pk)) {
+      set_last_error("batch step: bad pinned list of mesh " + std::to_string(k));
+      return GF_BAD_ARG;
+    }
+    if (mem == GF_MEM_HOST)
+      for (int64_t i = 0; i < np; ++i)
+        if (pk[i] < 0 || pk[i] >= m->dm.N) {
+          set_last_error("batch step: pinned node id out of range in mesh " + std::to_string(k));
+          return GF_BAD_ARG;
+        }
+    const double* fk = f_ext ? f_ext[k] : nullptr;
+    const double* vk = (pinned_vel && np > 0) ? pinned_vel[k] : nullptr;
+    if (fk) GB_CK(cudaMemcpyAsync(m->dm.f_ext, fk, sizeof(double) * 3 * m->dm.N, kind, s));
+    if (np > 0) GB_CK(cudaMemcpyAsync(m->dm.pin_ids, pk, sizeof(int32_t) * np, kind, s));
+    if (vk) GB_CK(cudaMemcpyAsync(m->dm.pin_vel, vk, sizeof(double) * 3 * np, kind, s));
+    b->htab->sp[k] = step_scalars(m->mt, dt, fk != nullptr, np, vk != nullptr);
+  }
+  std::vector<int32_t> shape;
+  shape.reserve(size_t(kBKinds) * (b->n + 1));
+  for (int kind = 0; kind < kBKinds; ++kind) {
+    int32_t acc = 0;
+    b->htab->off[kind][0] = 0;
+    for (int k = 0; k < b->n; ++k) {
+      acc += int32_t(launch_dims(kind, b->htab->mesh[k], b->htab->mt[k], b->htab->sp[k]).blocks);
+      b->htab->off[kind][k + 1] = acc;
+    }
+    b->blocks[kind] = unsigned(acc);
+    shape.insert(shape.end(), b->htab->off[kind], b->htab->off[kind] + b->n + 1);
+  }
+  const size_t sp_off = offsetof(BatchTab, sp);
+  GB_CK(cudaMemcpyAsync(reinterpret_cast<char*>(b->dtab) + sp_off, &b->htab->sp[0], sizeof(StepScalars) * b->n,
+                        cudaMemcpyHostToDevice, s));
+  if (shape != b->shape) {
+    GB_CK(cudaMemcpyAsync(reinterpret_cast<char*>(b->dtab) + offsetof(BatchTab, off), &b->htab->off[0][0],
+                          sizeof(b->htab->off), cudaMemcpyHostToDevice, s));
+    b->shape = shape;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  return GF_OK;
+}
+
+gf_status batch_run(gf_batch* b, gf_step_stats* stats) {
+  cudaStream_t s = b->stream;
+  int64_t L = 0;
+  if (b->tune.graph) {
+    if (!b->exec) {
+      gf_status st = build_graph(b);
+      if (st != GF_OK) return st;
+    }
+    GB_CK(cudaGraphLaunch(b->exec, s));
+    GB_CK(cudaMemcpyAsync(b->hout, b->dout, sizeof(BatchOut) * b->n, cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));
+    L = b->prefix_kernels + b->suffix_kernels + int64_t(*b->h_iter) * b->body_kernels;
+  } else {
+    L += enqueue_prefix(b, s);
+    const int chunk = b->tune.chunk > 0 ? b->tune.chunk : 8;
+    int it = 0;
+    for (;;) {
+      for (int j = 0; j < chunk; ++j, ++it) L += enqueue_body(b, s);
+      kb_collect<<<unsigned((b->n + 127) / 128), 128, 0, s>>>(b->dtab, b->mixed ? 1 : 0, b->dout);
+      ++L;
+      GB_CK(cudaGetLastError());
+      GB_CK(cudaMemcpyAsync(b->hout, b->dout, sizeof(BatchOut) * b->n, cudaMemcpyDeviceToHost, s));
+      GB_CK(cudaStreamSynchronize(s));
+      bool active = false;
+      for (int k = 0; k < b->n; ++k) active |= b->mixed ? !b->hout[k].ir.done : !b->hout[k].pcg.done;
+      if (!active || it >= b->cap) break;
+    }
+    L += enqueue_suffix(b, s);
+    GB_CK(cudaGetLastError());
+    GB_CK(cudaMemcpyAsync(b->hout, b->dout, sizeof(BatchOut) * b->n, cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));
+  }
+  b->launches += L;
+  gf_status first_bad = GF_OK;
+  for (int k = 0; k < b->n; ++k) {
+    const BatchOut& o = b->hout[k];
+    gf_step_stats st{};
+    if (b->mixed) {
+      st.status = o.ir.status;
+      if (st.status == GF_OK && !o.ir.done) st.status = GF_CG_MAXITER;
+      st.cg_iters = o.ir.total_iters;
+      st.refine_sweeps = o.ir.sweeps;
+      st.rel_res = o.ir.bb > 0 ? std::sqrt(o.ir.rr / o.ir.bb) : 0.0;
+    } else {
+      st.status = o.pcg.status;
+      if (st.status == GF_OK && !o.pcg.done) st.status = GF_CG_MAXITER;
+      st.cg_iters = o.pcg.iters;
+      st.rel_res = o.pcg.bb > 0 ? std::sqrt(o.pcg.true_rr / o.pcg.bb) : 0.0;
+    }
+    if (st.status == GF_OK && !std::isfinite(st.rel_res)) st.status = GF_NAN;
+    if (o.cnt[3] != 0) st.status = GF_BAD_ARG;
+    st.n_broken = int64_t(o.cnt[kCntBroken]);
+    st.n_new_broken = int64_t(o.cnt[kCntNewBroken]);
+    st.n_chi_zero = int64_t(o.cnt[kCntChiZero]);
+    if (stats) stats[k] = st;
+    if (st.status != GF_OK && first_bad == GF_OK) first_bad = gf_status(st.status);
+  }
+  if (first_bad != GF_OK) set_last_error(std::string("batch step: ") + gf_status_string(first_bad));
+  return first_bad;
+}
+
+}  // namespace
+
+extern "C" {
+
+gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out) {
+  if (!out || !meshes || n < 1 || n > kMaxBatch) {
+    set_last_error("batch: need 1 <= n <= 256 meshes and an output pointer");
+    return GF_BAD_ARG;
+  }
+  *out = nullptr;
+  for (int k = 0; k < n; ++k)
+    if (!meshes[k] || meshes[k]->device != meshes[0]->device || meshes[k]->mixed != meshes[0]->mixed) {
+      set_last_error("batch: meshes must be non-NULL, on one device, with one precision");
+      return GF_BAD_ARG;
+    }
+  DeviceGuard guard(meshes[0]->device);
+  gf_batch* b = new gf_batch();
+  b->ms.assign(meshes, meshes + n);
+  b->n = n;
+  b->mixed = meshes[0]->mixed;
+  b->device = meshes[0]->device;
+  b->stream = meshes[0]->stream;
+  b->tune.graph = 1;
+  b->tune.chunk = 8;
+  auto fail = [&](const char* what) {
+    set_last_error(std::string("batch create: ") + what);
+    batch_free(b);
+    delete b;
+    return GF_CUDA_ERR;
+  };
+  if (cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking) != cudaSuccess) return fail("stream");
+  if (cudaMallocHost(&b->htab, sizeof(BatchTab)) != cudaSuccess || cudaMalloc(&b->dtab, sizeof(BatchTab)) != cudaSuccess ||
+      cudaMalloc(&b->dinit, sizeof(BatchInit) * n) != cudaSuccess ||
+      cudaMallocHost(&b->hout, sizeof(BatchOut) * n) != cudaSuccess ||
+      cudaMalloc(&b->dout, sizeof(BatchOut) * n) != cudaSuccess || cudaMalloc(&b->d_iter, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&b->h_iter, sizeof(int)) != cudaSuccess)
+    return fail("allocation");
+  std::memset(b->htab, 0, sizeof(BatchTab));
+  b->htab->n = n;
+  std::vector<BatchInit> init(n);
+  int maxit = 1;
+  for (int k = 0; k < n; ++k) {
+    gf_mesh* m = meshes[k];
+    DevMesh d = m->dm;
+    if (!(m->mt.radius > 0.0)) {
+      d.sig_bar = d.sig_in;
+      d.mx.sig_bar32 = d.mx.sig_in32;
+    }
+    b->htab->mesh[k] = d;
+    b->htab->mt[k] = m->mt;
+    BatchInit& bi = init[k];
+    std::memset(&bi, 0, sizeof(bi));
+    bi.pcg.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+    bi.pcg.maxit = m->opt.cg_maxit;
+    bi.ir.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+    bi.ir.in_tol2 = m->in_rtol * m->in_rtol;
+    bi.ir.maxit = m->opt.cg_maxit;
+    bi.ir.in_maxit = 32;
+    bi.ir.applied = 1;
+    bi.ir.in_done = 1;
+    maxit = std::max(maxit, m->opt.cg_maxit);
+  }
+  // body iterations: one PCG iteration (FP64) or one inner iteration / sweep transition (mixed)
+  b->cap = 2 * maxit + 64;
+  if (cudaMemcpy(b->dtab, b->htab, sizeof(BatchTab), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dinit, init.data(), sizeof(BatchInit) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail("upload");
+  *out = b;
+  return GF_OK;
+}
+
+void gf_batch_destroy(gf_batch* b) {
+  if (!b) return;
+  DeviceGuard guard(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  delete b;
+}
+
+gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, const int32_t* const* pinned,
+                        const int64_t* n_pinned, const double* const* pinned_vel, int32_t mem, gf_step_stats* stats) {
+  if (!b || !(dt > 0) || !std::isfinite(dt) || !valid_mem(mem)) {
+    set_last_error("batch step: need a batch, dt > 0 and a memory kind");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(b->device);
+  gf_status st = batch_prepare(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem);
+  if (st != GF_OK) return st;
+  return batch_run(b, stats);
+}
+
+gf_status gf_batch_tuning_set(gf_batch* b, const gf_batch_tuning* t) {
+  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0) {
+    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0");
+    return GF_BAD_ARG;
+  }
+  b->tune = *t;
+  return GF_OK;
+}
+
+gf_status gf_batch_tuning_get(const gf_batch* b, gf_batch_tuning* t) {
+  if (!b || !t) return GF_BAD_ARG;
+  *t = b->tune;
+  return GF_OK;
+}
+
+int64_t gf_batch_launch_count(const gf_batch* b) { return b ? b->launches : 0; }
+
+gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, const int32_t* const* pinned,
+                            const int64_t* n_pinned, const double* const* pinned_vel, int32_t mem, int32_t trial_steps,
+                            gf_batch_tuning* best, double* best_ms) {
+  if (!b || trial_steps < 1) {
+    set_last_error("autotune: need a batch and trial_steps >= 1");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(b->device);
+  cudaStream_t s = b->stream;
+  // save every mesh's state (x, v, labels, chi, FP32 copies) on the device
+  struct Saved {
+    void* p;
+    const void* src;
+    size_t bytes;
+  };
+  std::vector<Saved> saved;
+  auto keep = [&](const void* src, size_t bytes) -> gf_status {
+    void* p = nullptr;
+    if (bytes == 0) return GF_OK;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      set_last_error("autotune: cannot save state");
+      return GF_OOM;
+    }
+    saved.push_back({p, src, bytes});
+    return cudaMemcpyAsync(p, src, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? GF_OK : GF_CUDA_ERR;
+  };
+  gf_status st = GF_OK;
+  for (int k = 0; k < b->n && st == GF_OK; ++k) {
+    const DevMesh& d = b->ms[k]->dm;
+    if ((st = keep(d.x, sizeof(double) * 3 * d.N)) || (st = keep(d.v, sizeof(double) * 3 * d.N)) ||
+        (st = keep(d.labels, d.NE)) || (st = keep(d.chi, sizeof(double) * d.T)))
+      break;
+    if (b->mixed && ((st = keep(d.mx.u32, sizeof(float) * 3 * d.N)) || (st = keep(d.mx.v32, sizeof(float) * 3 * d.N)) ||
+                     (st = keep(d.mx.chi32, sizeof(float) * d.T))))
+      break;
+  }
+  auto restore = [&]() {
+    for (auto& sv : saved) cudaMemcpyAsync(const_cast<void*>(sv.src), sv.p, sv.bytes, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+  };
+  const gf_batch_tuning orig = b->tune;
+  std::vector<gf_batch_tuning> cands;
+  {
+    gf_batch_tuning t{};
+    t.graph = 1;
+    t.chunk = 8;
+    cands.push_back(t);
+    for (int c : {2, 4, 8, 16}) {
+      t.graph = 0;
+      t.chunk = c;
+      cands.push_back(t);
+    }
+  }
+  double best_t = 1e300;
+  gf_batch_tuning best_c = orig;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (size_t ci = 0; ci < cands.size() && st == GF_OK; ++ci) {
+    b->tune = cands[ci];
+    // one untimed step (graph build, caches), then the timed trial
+    st = gf_batch_step(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
+    restore();
+    if (st != GF_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < trial_steps && st == GF_OK; ++r)
+      st = gf_batch_step(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    restore();
+    if (st == GF_OK && ms / trial_steps < best_t) {
+      best_t = ms / trial_steps;
+      best_c = cands[ci];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto& sv : saved) cudaFree(sv.p);
+  b->tune = st == GF_OK ? best_c : orig;
+  if (best) *best = b->tune;
+  if (best_ms) *best_ms = best_t;
+  return st;
+}
 
 }  // extern "C"

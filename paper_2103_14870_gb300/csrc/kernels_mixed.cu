@@ -583,7 +583,9 @@ __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float
 __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb, int first) {
 
   IrState* S = m.mx.ir;
-  if (!first && (S->done || !S->applied)) return;   // no new correction yet: nothing to check
+  // after the first call: only right after a correction was applied (inner solve
+  // finished, residual not yet formed); flags are written by the last CTA only
+  if (!first && (S->done || !S->in_done || S->applied)) return;
   const MixDev& x = m.mx;
   const int j16 = threadIdx.x & 15;
   const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
@@ -642,6 +644,7 @@ __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Materia
     } else {
       S->sweeps += 1;
     }
+    S->applied = 1;   // a fresh residual is ready for the next inner solve
     S->rr = out[0];
     S->done = (out[0] == 0.0 || out[0] <= S->tol2 * S->bb) ? 1 : 0;
     if (!isfinite(out[0])) {
@@ -831,12 +834,13 @@ __global__ void __launch_bounds__(kThreads) kb_ir_p(const BatchTab* __restrict__
   ir_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-// dv += d on free rows, kept as a float pair (dv_hi + dv_lo) on the FP32 pipe
+// dv += d on free rows once the inner solve has finished, kept as a float pair
+// (dv_hi + dv_lo) on the FP32 pipe.  Writes no flag: every CTA decides from the
+// same state (the residual that follows marks the correction as applied).
 __device__ __forceinline__ void ir_apply_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
   IrState* S = m.mx.ir;
   if (S->done || !S->in_done || S->applied) return;
-  if (bid == 0 && threadIdx.x == 0) S->applied = 1;   // read by the next kernels only
   for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i / 3]) continue;
     float hi = m.mx.dv_hi[i], lo = m.mx.dv_lo[i];

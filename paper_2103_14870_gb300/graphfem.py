@@ -65,6 +65,10 @@ class Tuning(ctypes.Structure):
 ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
 class MeshInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_nodes", "n_tets", "n_edges", "n_blocks", "n_colours",
                                               "n_nbr_pairs", "device_bytes")]
@@ -111,6 +115,14 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_bsr_pcg_solve_static": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_double,
                                                    ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32),
                                                    ctypes.POINTER(ctypes.c_double)]),
+        "gf_batch_create": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P)]),
+        "gf_batch_destroy": (None, [P]),
+        "gf_batch_step": (ctypes.c_int, [P, ctypes.c_double, P, P, P, P, ctypes.c_int32, P]),
+        "gf_batch_tuning_set": (ctypes.c_int, [P, ctypes.POINTER(BatchTuning)]),
+        "gf_batch_tuning_get": (ctypes.c_int, [P, ctypes.POINTER(BatchTuning)]),
+        "gf_batch_autotune": (ctypes.c_int, [P, ctypes.c_double, P, P, P, P, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_double)]),
+        "gf_batch_launch_count": (ctypes.c_int64, [P]),
         "gf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "gf_last_error": (ctypes.c_char_p, []),
     }
@@ -286,6 +298,83 @@ class Mesh:
 
     def launch_count(self) -> int:
         return int(load_library().gf_launch_count(self._h))
+
+
+class Batch:
+    """gf_batch: step many meshes (same device and precision) with one launch
+    per kernel kind; by default each step replays one CUDA graph whose solve
+    loop runs on the device."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        self.n = len(self.meshes)
+        arr = (P * self.n)(*[m._h for m in self.meshes])
+        h = P()
+        _check(load_library().gf_batch_create(arr, self.n, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().gf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, arrays, dtype, counts, name):
+        if arrays is None:
+            return None, None, []
+        ptrs = (P * self.n)()
+        kinds, keep = [], []
+        for k, a in enumerate(arrays):
+            if a is None:
+                continue
+            p, kd, kp = _arg(a, dtype, counts[k], f"{name}[{k}]")
+            ptrs[k] = p
+            kinds.append(kd)
+            keep.append(kp)
+        return ptrs, (kinds[0] if kinds else None), keep + [ptrs]
+
+    def _inputs(self, f_ext, pinned, pinned_vel):
+        n_pin = [0] * self.n
+        if pinned is not None:
+            n_pin = [0 if a is None else (a.numel() if hasattr(a, "numel") else len(a)) for a in pinned]
+        fp, fk, k1 = self._ptrs(f_ext, np.float64, [3 * m.n_nodes for m in self.meshes], "f_ext")
+        pp, pk, k2 = self._ptrs(pinned, np.int32, n_pin, "pinned")
+        vp, vk, k3 = self._ptrs(pinned_vel, np.float64, [3 * c for c in n_pin], "pinned_vel")
+        npin = (ctypes.c_int64 * self.n)(*n_pin)
+        mem = _one_kind(fk, pk, vk)
+        return fp, pp, npin, vp, mem, k1 + k2 + k3 + [npin]
+
+    def step(self, dt: float, f_ext=None, pinned=None, pinned_vel=None) -> list:
+        fp, pp, npin, vp, mem, keep = self._inputs(f_ext, pinned, pinned_vel)
+        stats = (StepStats * self.n)()
+        _check(load_library().gf_batch_step(self._h, float(dt), fp, pp, npin, vp, mem, stats))
+        return [st.as_dict() for st in stats]
+
+    def tuning_set(self, graph: int = 1, chunk: int = 8):
+        t = BatchTuning()
+        t.graph, t.chunk = graph, chunk
+        _check(load_library().gf_batch_tuning_set(self._h, ctypes.byref(t)))
+
+    def tuning_get(self) -> dict:
+        t = BatchTuning()
+        _check(load_library().gf_batch_tuning_get(self._h, ctypes.byref(t)))
+        return {"graph": t.graph, "chunk": t.chunk}
+
+    def autotune(self, dt: float, f_ext=None, pinned=None, pinned_vel=None, trial_steps: int = 3):
+        fp, pp, npin, vp, mem, keep = self._inputs(f_ext, pinned, pinned_vel)
+        best = BatchTuning()
+        ms = ctypes.c_double(0.0)
+        _check(load_library().gf_batch_autotune(self._h, float(dt), fp, pp, npin, vp, mem, int(trial_steps),
+                                                ctypes.byref(best), ctypes.byref(ms)))
+        return {"graph": best.graph, "chunk": best.chunk}, ms.value
+
+    def launch_count(self) -> int:
+        return int(load_library().gf_batch_launch_count(self._h))
 
 
 def mesh_plan(nodes, tets, mat: Material) -> dict:
