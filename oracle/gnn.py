@@ -191,3 +191,61 @@ def to_bf16(x):
     a = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
     r = ((a + 0x7FFF + ((a >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def build_inputs(A, mass, X, edges, pinned_mask, b):
+    """Network inputs from an assembled system A (scipy sparse, 3n x 3n), the
+    lumped mass, rest positions X, mesh edges (sorted (i, j) pairs), the
+    pinned-node mask and the right-hand side b (n, 3).
+
+    Node inputs f_i (16): [log(t_i / mean t), entries xx yy zz xy xz yz of
+    A_ii / t_i - I, log(m_i / mean m), pinned flag, degree / 16,
+    y_i / s (3), 0 0 0] with t_i = trace(A_ii) / 3, y_i = A_ii^-1 b_i on free
+    nodes (0 on pinned ones) and s = sqrt(mean over free nodes of |y_i|^2).
+    Edge inputs e_ij for the message j -> i (16): [(X_j - X_i) / mean rest edge
+    length (3), A_ij / sqrt(t_i t_j) row-major (9), 0 0 0 0].
+    Returns (Graph, f, C, s, free, Dinv)."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    n = X.shape[0]
+    dd = np.zeros((n, 3, 3))
+    idx = np.arange(n)
+    for a in range(3):
+        for c in range(3):
+            dd[:, a, c] = np.asarray(A[3 * idx + a, 3 * idx + c]).ravel()
+    t = np.trace(dd, axis1=1, axis2=2) / 3.0
+    adj = [[] for _ in range(n)]
+    for i, j in np.asarray(edges, np.int64):
+        adj[i].append(j)
+        adj[j].append(i)
+    row_ptr = [0]
+    col = []
+    for i in range(n):
+        col += sorted(adj[i])
+        row_ptr.append(len(col))
+    col = np.asarray(col, np.int64)
+    dst = np.repeat(np.arange(n), np.diff(row_ptr))
+    hbar = np.mean(np.linalg.norm(X[np.asarray(edges)[:, 1]] - X[np.asarray(edges)[:, 0]], axis=1))
+    ef = np.zeros((len(col), EIN))
+    ef[:, 0:3] = (X[col] - X[dst]) / hbar
+    for a in range(3):
+        for c in range(3):
+            ef[:, 3 + 3 * a + c] = np.asarray(A[3 * dst + a, 3 * col + c]).ravel() / np.sqrt(t[dst] * t[col])
+    free = ~np.asarray(pinned_mask, bool)
+    Dinv = np.linalg.inv(dd)
+    y = np.einsum("nab,nb->na", Dinv, b) * free[:, None]
+    s = float(np.sqrt((y[free] ** 2).sum(1).mean())) if free.any() else 1.0
+    if not s > 0:
+        s = 1.0
+    f = np.zeros((n, NIN))
+    f[:, 0] = np.log(t / t.mean())
+    rel = dd / t[:, None, None] - np.eye(3)
+    for q, (a, c) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+        f[:, 1 + q] = rel[:, a, c]
+    f[:, 7] = np.log(mass / mass.mean())
+    f[:, 8] = (~free).astype(np.float64)
+    f[:, 9] = np.diff(row_ptr) / 16.0
+    f[:, 10:13] = y / s
+    g = Graph(row_ptr, col, ef)
+    C = block_inverse_cholesky(Dinv)
+    return g, f, C, s, free, Dinv

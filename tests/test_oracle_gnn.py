@@ -80,3 +80,48 @@ def test_bf16_rounding():
     # bf16 keeps 8 significand bits: 1 + 2^-8 is a tie -> even (1.0); 1 + 3*2^-8 -> 1 + 2^-6
     np.testing.assert_array_equal(gnn.to_bf16(vals)[[0, 1, 2, 3, 5]], [1.0, 1.0, 1.0 + 2 ** -6, -2.5, 1.0 + 2 ** -7])
     assert gnn.n_params() == sum(int(np.prod(s)) for s in gnn.param_shapes().values())
+
+
+def test_build_inputs_hand_worked_three_nodes():
+    """Network inputs of a 3-node path graph 0-1-2 worked by hand: node 2
+    pinned, rest edge lengths 1 and 2 (mean 1.5), diagonal blocks with traces
+    2, 4, 8 and known inverses."""
+    import scipy.sparse as sp
+    X = np.array([[0.0, 0, 0], [1, 0, 0], [1, 2, 0]])
+    D = [2 * np.eye(3), np.array([[4.0, 1, 0], [1, 4, 0], [0, 0, 4]]), 8 * np.eye(3)]
+    A01 = -0.5 * np.eye(3)
+    A12 = np.zeros((3, 3))
+    A12[0, 1] = 1.0
+    A = np.zeros((9, 9))
+    for i in range(3):
+        A[3 * i:3 * i + 3, 3 * i:3 * i + 3] = D[i]
+    A[0:3, 3:6], A[3:6, 0:3] = A01, A01.T
+    A[3:6, 6:9], A[6:9, 3:6] = A12, A12.T
+    b = np.array([[2.0, 0, 0], [5, 5, 0], [9, 9, 9]])
+    mass = np.array([1.0, 2.0, 3.0])
+    pinned = np.array([False, False, True])
+    g, f, C, s, free, Dinv = gnn.build_inputs(sp.csr_matrix(A), mass, X, np.array([[0, 1], [1, 2]]), pinned, b)
+    # y0 = [1, 0, 0], y1 = [1, 1, 0] (D1 [1, 1, 0] = [5, 5, 0]), y2 = 0 (pinned): s = sqrt(3 / 2)
+    assert s == pytest.approx(np.sqrt(1.5), rel=1e-15)
+    want = np.zeros((3, 16))
+    want[:, 0] = np.log(np.array([2.0, 4.0, 8.0]) / (14.0 / 3.0))
+    want[1, 4] = 0.25                                  # xy of D1 / 4 - I
+    want[:, 7] = np.log(mass / 2.0)
+    want[:, 8] = [0, 0, 1]
+    want[:, 9] = np.array([1, 2, 1]) / 16.0
+    want[0, 10:13] = np.array([1, 0, 0]) / np.sqrt(1.5)
+    want[1, 10:13] = np.array([1, 1, 0]) / np.sqrt(1.5)
+    np.testing.assert_allclose(f, want, rtol=1e-14, atol=1e-15)
+    # rows: 0 <- 1 | 1 <- 0, 1 <- 2 | 2 <- 1
+    assert list(g.row_ptr) == [0, 1, 3, 4] and list(g.col) == [1, 0, 2, 1]
+    ew = np.zeros((4, 16))
+    ew[0, 0:3], ew[0, 3:12] = [2 / 3, 0, 0], (A01 / np.sqrt(8)).ravel()
+    ew[1, 0:3], ew[1, 3:12] = [-2 / 3, 0, 0], (A01.T / np.sqrt(8)).ravel()
+    ew[2, 0:3], ew[2, 3:12] = [0, 4 / 3, 0], (A12 / np.sqrt(32)).ravel()
+    ew[3, 0:3], ew[3, 3:12] = [0, -4 / 3, 0], (A12.T / np.sqrt(32)).ravel()
+    np.testing.assert_allclose(g.efeat, ew, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(C[0], np.sqrt(0.5) * np.eye(3), rtol=1e-14)
+    for i in range(3):
+        np.testing.assert_allclose(C[i] @ C[i].T, np.linalg.inv(D[i]), rtol=1e-13, atol=1e-15)
+        assert np.allclose(np.triu(C[i], 1), 0)
+    assert list(free) == [True, True, False]
