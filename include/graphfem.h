@@ -285,6 +285,77 @@ gf_status gf_batch_autotune(gf_batch* batch, double dt, const double* const* f_e
 /* Kernel launches issued by the batch (graph replays count the kernels run). */
 int64_t gf_batch_launch_count(const gf_batch* batch);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start and block preconditioner for the linear solve of each
+ * step (the system of Eq. 2 after the backward-Euler linearisation).  The
+ * paper solves it with a plain Krylov method; this is an optional extension:
+ * a message-passing network over the mesh graph (3 layers, hidden width 64,
+ * bfloat16 weights, FP32 activations) reads the assembled system and the
+ * right-hand side and outputs, per node i, a 3x3 SPD block
+ *   P_i = C_i (L_i L_i^T + 1e-3 I) C_i^T,   C_i C_i^T = A_ii^-1,
+ * and a start x0_i = P_i b_i + s delta_i (s = rms of |A_ii^-1 b_i| over free
+ * nodes).  With zero decoder weights it is block Jacobi scaled by 1.001.
+ * Parameters: gf_gnn_n_params() floats in the order W0[16][64], b0[64], then
+ * per layer l = 0..2: Wa[64][64], We[16][64], bm[64], Wu[128][64], bu[64],
+ * then Wd[64][9], bd[9] (row-major [in][out]).
+ * Only FP64 meshes (GF_FP64) are supported; the network lives on the mesh's
+ * device and stream.  Destroy it before its mesh.
+ * ------------------------------------------------------------------------ */
+typedef struct gf_gnn gf_gnn;
+
+int64_t gf_gnn_n_params(void);
+
+/* Allocates the network's buffers for `mesh` (graph = off-diagonal block
+ * pattern, static node/edge inputs from the rest positions and masses).
+ * Weights start at zero: set them with gf_gnn_params_set.  One network per
+ * mesh; GF_UNSUPPORTED for a GF_MIXED mesh.  While it exists, every gf_step
+ * keeps the previous step's solution for it (3 n_nodes doubles, device copy). */
+gf_status gf_gnn_create(gf_mesh* mesh, gf_gnn** out);
+void gf_gnn_destroy(gf_gnn* gnn);
+
+/* Host float32 arrays of gf_gnn_n_params() entries (n must equal it).  _set
+ * also resets the optimiser state. */
+gf_status gf_gnn_params_set(gf_gnn* gnn, const float* w, int64_t n);
+gf_status gf_gnn_params_get(gf_gnn* gnn, float* w, int64_t n);
+
+/* Forward pass on the system assembled by the mesh's last gf_step (its
+ * matrix and pinned set) with right-hand side b (float64 [3 * n_nodes],
+ * following `mem`).  Host outputs, each may be NULL: out float32 [n_nodes][9]
+ * (delta, ell), P float32 [n_nodes][9], x0 float32 [n_nodes][3], node_in
+ * float32 [n_nodes][16], edge_in float32 [n_graph_edges][16] (graph rows as in
+ * gf_system_get's pattern without the diagonal).  The mesh is not changed. */
+gf_status gf_gnn_forward(gf_gnn* gnn, const double* b, int32_t mem, float* out, float* P, float* x0, float* node_in,
+                         float* edge_in);
+
+/* Energy-norm loss (x0 - target)^T A_ff (x0 - target) / target^T A_ff target
+ * (A_ff: free block of the mesh's last system) for the pair (b, target), and
+ * its gradient (host float32 [n_params], may be NULL).  b, target: float64
+ * [3 * n_nodes] following `mem`; entries on pinned nodes are ignored. */
+gf_status gf_gnn_loss_grad(gf_gnn* gnn, const double* b, const double* target, int32_t mem, double* loss,
+                           float* grad);
+
+/* Online training on the mesh's last solved step.  With x_prev the solution
+ * of the step before it and w = dv on pinned nodes, x_prev on free ones, the
+ * pair is b = b_sys - A w on free rows and target = dv - x_prev on free nodes;
+ * the loss is the energy-norm error (x0 - target)^T A_ff (x0 - target) /
+ * target^T A_ff target.  Runs `iters` (1..1024) Adam steps (beta 0.9 / 0.999,
+ * learning rate lr) and returns the loss before the first and before the last
+ * update (each may be NULL). */
+gf_status gf_gnn_train(gf_gnn* gnn, int32_t iters, float lr, double* loss_first, double* loss_last);
+
+/* The pair gf_gnn_train uses, for the mesh's last solved step: host float64
+ * [3 * n_nodes] each. */
+gf_status gf_gnn_pair_get(gf_gnn* gnn, double* b, double* target);
+
+/* Use of the network in gf_step (flags = 0 turns it off; the default after
+ * gf_gnn_create).  GF_GNN_START: the solve starts from x_prev + x0, where
+ * x_prev is the previous step's solution and x0 the network's answer for the
+ * right-hand side b_free - A_ff x_prev.  GF_GNN_PRECOND: the learned blocks
+ * P_i replace block Jacobi.  Convergence is still
+ * |b_free - A dv| <= rtol |b_free| either way. */
+enum { GF_GNN_START = 1, GF_GNN_PRECOND = 2 };
+gf_status gf_gnn_attach(gf_mesh* mesh, gf_gnn* gnn, int32_t flags);
+
 const char* gf_status_string(gf_status s);
 const char* gf_last_error(void);
 

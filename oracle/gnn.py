@@ -19,7 +19,13 @@ Outputs (per node):
           inverse diagonal block of A): symmetric positive definite, = block
           Jacobi scaled by (1 + eps) when L = I
   x0_i  = P_i b_i + s delta_i,  s = rms_i |D_i^-1 b_i|
-Loss for a pair (b, dv*) with A dv* = b:  |x0 - dv*|^2 / |dv*|^2 over free nodes.
+Loss for a pair (b, x*) with A_ff x* = b on the free nodes f: the relative
+error of x0 in the energy norm of the free block, which is the norm conjugate
+gradients minimises,
+  loss = (x0 - x*)^T A_ff (x0 - x*) / x*^T A_ff x*.
+In a time step the network solves for the correction to the previous step's
+solution x_prev: b = b_free - A_ff x_prev (``training_pair``) and the start
+handed to the solver is x_prev + x0.
 
 Weights are stored row-major as [in][out]; the forward pass uses them as given
 (the GPU rounds them to bfloat16 first; tests pass the rounded values here).
@@ -128,15 +134,22 @@ def apply_outputs(out, C, b, s):
     return P, x0, L, G
 
 
-def loss_and_grad(params, g: Graph, f, C, b, dv, free, s):
-    """Loss of one pair and d(loss)/d(params) by the chain rule (manual backward)."""
+def loss_and_grad(params, g: Graph, f, C, b, dv, free, s, A):
+    """Loss of one pair and d(loss)/d(params) by the chain rule (manual backward).
+    A: the full system (scipy sparse, 3n x 3n); only its free block enters."""
+    import scipy.sparse as sp
     out, cache = forward(params, g, f, keep=True)
     P, x0, L, G = apply_outputs(out, C, b, s)
     w = free.astype(np.float64)[:, None]
-    den = float((w * dv * dv).sum())
-    diff = (x0 - dv) * w
-    loss = float((diff * diff).sum()) / den
-    dx0 = 2.0 * diff / den                                     # (n, 3)
+    A = sp.csr_matrix(A)
+    e = (x0 - dv) * w
+    q = (A @ e.ravel()).reshape(-1, 3) * w                     # A_ff e on free rows
+    t = dv * w
+    den = float(t.ravel() @ (A @ t.ravel()))
+    if not den > 0:
+        den = 1.0
+    loss = float(e.ravel() @ q.ravel()) / den
+    dx0 = 2.0 * q / den                                        # (n, 3)
     dout = np.zeros_like(out)
     dout[:, 0:3] = s * dx0
     dP = np.einsum("na,nb->nab", dx0, b)                       # d/dP of (P b)
@@ -249,3 +262,17 @@ def build_inputs(A, mass, X, edges, pinned_mask, b):
     g = Graph(row_ptr, col, ef)
     C = block_inverse_cholesky(Dinv)
     return g, f, C, s, free, Dinv
+
+
+def training_pair(A, b, dv, x_prev, pinned_mask):
+    """(b_net, target) of one solved step: with w = dv on pinned nodes and
+    x_prev on free ones, b_net = b - A w on free rows (0 on pinned rows) and
+    target = dv - x_prev on free nodes (0 on pinned).  b, dv, x_prev: (n, 3)."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    pin = np.asarray(pinned_mask, bool)
+    wv = np.where(pin[:, None], dv, x_prev)
+    bn = (b.ravel() - A @ wv.ravel()).reshape(-1, 3)
+    bn[pin] = 0.0
+    tg = np.where(pin[:, None], 0.0, dv - x_prev)
+    return bn, tg

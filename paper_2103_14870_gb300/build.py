@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgraphfem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host_mesh.cpp", "kernels_fp64.cu", "kernels_mixed.cu", "capi.cu", "solve_static.cu"]
+SOURCES = ["host_mesh.cpp", "kernels_fp64.cu", "kernels_mixed.cu", "kernels_gnn.cu", "capi.cu", "solve_static.cu"]
 
 
 def _nvcc() -> str:
@@ -43,7 +43,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     """Compile every translation unit (in parallel) and link the shared library."""
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(ROOT, "include", "graphfem.h"))
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "gf_device.h"
+#include "gf_gnn.h"
 
 namespace gf {
 
@@ -76,11 +77,12 @@ namespace {
 
 enum ProfGroup : int {
   kPStress = 0, kPNonlocal, kPEdge, kPChi, kPAssemble, kPPcgInit, kPSpmv, kPPcgUpdate, kPPcgP, kPResidual,
-  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPCount
+  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPGnn, kPCount
 };
 const char* kProfNames[kPCount] = {"tet_stress",  "nonlocal_avg", "edge_driver", "tet_chi",     "assemble",
                                    "pcg_init",    "pcg_spmv",     "pcg_update",  "pcg_p",       "true_residual",
-                                   "integrate",   "ir_residual",  "ir_inner_init", "ir_apply"};
+                                   "integrate",   "ir_residual",  "ir_inner_init", "ir_apply",
+                                   "gnn"};
 
 __global__ void k_fill(double* p, int64_t n, double v) {
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -130,6 +132,10 @@ struct gf_mesh {
   gf::Material mt{};
   uint64_t lut = 0;
   HostMesh hm;          // host copies kept for getters (pattern, edges, perm, colours)
+  std::vector<double> X0;     // rest positions [N][3]
+  gf_gnn* gnn = nullptr;      // learned start / preconditioner created for this mesh
+  int gnn_flags = 0;          // GF_GNN_START | GF_GNN_PRECOND while attached
+  bool assembled = false;     // a step has assembled the system
   DevMesh dm;
   int32_t* perm_dev = nullptr;
   int last_iters = 4;
@@ -152,6 +158,8 @@ struct gf_mesh {
   std::vector<Rec> recs;
   int ev_next = 0;
 };
+
+void gnn_orphan(gf_gnn* g);
 
 namespace {
 
@@ -371,6 +379,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   }
   std::string err;
   gf_status st = build_host_mesh(nodes, n_nodes, tets, n_tets, M, m->hm, err);
+  if (st == GF_OK) m->X0.assign(nodes, nodes + 3 * n_nodes);
   if (st != GF_OK) {
     set_last_error(err);
     return fail(st);
@@ -561,6 +570,7 @@ void gf_mesh_destroy(gf_mesh* mesh) {
   if (!mesh) return;
   DeviceGuard guard(mesh->device);
   cudaStreamSynchronize(mesh->stream);
+  if (mesh->gnn) gnn_orphan(mesh->gnn);   // the network outlives its mesh: it can only be destroyed now
   release(mesh);
   delete mesh;
 }
@@ -653,7 +663,10 @@ gf_status gf_solver_set(gf_mesh* m, double rtol, int32_t maxit) {
 
 namespace {
 
-// FP64 path: damage, colour-ordered assembly, projected PCG (all FP64).
+int64_t gnn_step_start(gf_gnn* g, const DevMesh& d, int flags, cudaStream_t s);
+cudaError_t gnn_keep_previous(gf_gnn* g, const DevMesh& d, cudaStream_t s);
+
+// FP64 path: damage, two-phase (or colour-ordered) assembly, projected PCG (all FP64).
 gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_pinned, bool has_pvel,
                     int64_t& L) {
   cudaStream_t s = m->stream;
@@ -686,9 +699,16 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
   *m->h_pcg = init;
   GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
   GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
+  if (m->gnn) GF_CK(gnn_keep_previous(m->gnn, d, s));   // the previous solution starts the learned correction
   GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
   L += launch_kind(kB_set_pinned, d, mt, sp, s);
   { Prof p(m, kPPcgInit); L += launch_kind(kB_pcg_init, d, mt, sp, s); }
+  if (m->gnn && m->gnn_flags) {   // learned start and preconditioner
+    { Prof p(m, kPGnn); L += gnn_step_start(m->gnn, d, m->gnn_flags, s); }
+    StepScalars sl = sp;
+    sl.learned = 1;
+    { Prof p(m, kPPcgInit); L += launch_kind(kB_pcg_init, d, mt, sl, s); }
+  }
   int launched_iters = 0;
   int chunk = std::max(1, std::min(m->last_iters + 1, 64));
   for (;;) {
@@ -813,6 +833,7 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
   gf_status st = m->mixed ? step_mixed(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L)
                           : step_fp64(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L);
   if (st != GF_OK) return st;
+  m->assembled = true;
   GF_CK(cudaMemcpyAsync(m->h_cnt, d.counters, sizeof(unsigned long long) * kCntMax, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
   m->launches += L;
@@ -1476,3 +1497,434 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned warm start and block preconditioner
+// ---------------------------------------------------------------------------
+
+struct gf_gnn {
+  gf_mesh* mesh = nullptr;       // NULL once the mesh is destroyed
+  int device = 0;
+  std::vector<void*> blocks;
+  GnnDev g;
+  int adam_t = 0;
+  double* stage_b = nullptr;     // [3N] staged right-hand side
+  double* stage_t = nullptr;     // [3N] staged target
+  double* loss_hist = nullptr;   // [kGnnMaxIters]
+};
+
+namespace {
+
+constexpr int kGnnMaxIters = 1024;
+
+void gnn_free(gf_gnn* g) {
+  for (void* p : g->blocks) cudaFree(p);
+  g->blocks.clear();
+}
+
+template <class T>
+gf_status gnn_alloc(gf_gnn* g, size_t n, T** out) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(256, (n * sizeof(T) + 255) & ~size_t(255));
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("network buffers: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return e == cudaErrorMemoryAllocation ? GF_OOM : GF_CUDA_ERR;
+  }
+  g->blocks.push_back(p);
+  *out = static_cast<T*>(p);
+  return GF_OK;
+}
+
+template <class T>
+gf_status gnn_upload(gf_gnn* g, const std::vector<T>& h, const T** out, cudaStream_t s) {
+  T* p = nullptr;
+  gf_status st = gnn_alloc(g, h.size(), &p);
+  if (st != GF_OK) return st;
+  if (!h.empty()) GF_CK(cudaMemcpyAsync(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+  *out = p;
+  return GF_OK;
+}
+
+int64_t gnn_param_offsets(int64_t (&off)[kGnnTensors]) {
+  int64_t sz[kGnnTensors];
+  sz[kPW0] = kNin * kHid;
+  sz[kPb0] = kHid;
+  for (int l = 0; l < 3; ++l) {
+    sz[kPWa + 5 * l] = kHid * kHid;
+    sz[kPWe + 5 * l] = kEin * kHid;
+    sz[kPbm + 5 * l] = kHid;
+    sz[kPWu + 5 * l] = 2 * kHid * kHid;
+    sz[kPbu + 5 * l] = kHid;
+  }
+  sz[kPWd] = kHid * kNout;
+  sz[kPbd] = kNout;
+  int64_t o = 0;
+  for (int k = 0; k < kGnnTensors; ++k) {
+    off[k] = o;
+    o += sz[k];
+  }
+  return o;
+}
+
+gf_status gnn_check(gf_gnn* g) {
+  if (!g || !g->mesh) {
+    set_last_error(g ? "the network's mesh was destroyed" : "NULL network");
+    return GF_BAD_ARG;
+  }
+  if (!g->mesh->assembled) {
+    set_last_error("the mesh has no assembled system yet: call gf_step first");
+    return GF_BAD_ARG;
+  }
+  return GF_OK;
+}
+
+// b (host or device) -> device pointer
+gf_status gnn_stage(gf_gnn* g, const double* src, int32_t mem, double* stage, const double** out) {
+  if (mem == GF_MEM_DEVICE) {
+    *out = src;
+    return GF_OK;
+  }
+  GF_CK(cudaMemcpyAsync(stage, src, sizeof(double) * 3 * g->g.N, cudaMemcpyHostToDevice, g->mesh->stream));
+  *out = stage;
+  return GF_OK;
+}
+
+// network right-hand side b - A w (w = pinned values, previous solution on free
+// nodes), forward pass, start and blocks into the mesh
+int64_t gnn_step_start(gf_gnn* g, const DevMesh& d, int flags, cudaStream_t s) {
+  int64_t L = gnn_pair(d, g->g.xprev, g->stage_b, nullptr, s);
+  L += gnn_forward(g->g, d, g->stage_b, s);
+  L += gnn_apply_inference(g->g, d, flags, s);
+  return L;
+}
+
+cudaError_t gnn_keep_previous(gf_gnn* g, const DevMesh& d, cudaStream_t s) {
+  return cudaMemcpyAsync(g->g.xprev, d.dv, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gf_gnn_n_params(void) {
+  int64_t off[kGnnTensors];
+  return gnn_param_offsets(off);
+}
+
+gf_status gf_gnn_create(gf_mesh* mesh, gf_gnn** out) {
+  if (!out || !mesh) {
+    set_last_error("mesh and out must not be NULL");
+    return GF_BAD_ARG;
+  }
+  *out = nullptr;
+  if (mesh->mixed) {
+    set_last_error("the learned preconditioner runs with GF_FP64 meshes only");
+    return GF_UNSUPPORTED;
+  }
+  if (mesh->gnn) {
+    set_last_error("the mesh already has a network");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(mesh->device);
+  cudaStream_t s = mesh->stream;
+  const HostMesh& hm = mesh->hm;
+  const int64_t N = hm.n_nodes;
+  // graph: the block pattern without its diagonal (rows sorted)
+  std::vector<int32_t> rp(N + 1, 0), col, dst, amap;
+  col.reserve(hm.col.size());
+  for (int64_t i = 0; i < N; ++i) {
+    for (int32_t p = hm.row_ptr[i]; p < hm.row_ptr[i + 1]; ++p) {
+      if (hm.col[p] == i) continue;
+      col.push_back(hm.col[p]);
+      dst.push_back(int32_t(i));
+      amap.push_back(p);
+    }
+    rp[i + 1] = int32_t(col.size());
+  }
+  const int64_t E = int64_t(col.size());
+  std::vector<int32_t> tpos(E);
+  for (int64_t q = 0; q < E; ++q) {
+    const int32_t i = dst[q], j = col[q];
+    const int32_t* b = col.data() + rp[j];
+    const int32_t* e = col.data() + rp[j + 1];
+    const int32_t* it = std::lower_bound(b, e, i);
+    if (it == e || *it != i) {
+      set_last_error("block pattern is not symmetric");
+      return GF_BAD_ARG;
+    }
+    tpos[q] = int32_t(it - col.data());
+  }
+  // static inputs
+  const std::vector<double>& X = mesh->X0;
+  double hsum = 0.0;
+  for (int64_t k = 0; k < hm.n_edges; ++k) {
+    const int32_t a = hm.edges[2 * k], b = hm.edges[2 * k + 1];
+    double l2 = 0.0;
+    for (int c = 0; c < 3; ++c) l2 += (X[3 * b + c] - X[3 * a + c]) * (X[3 * b + c] - X[3 * a + c]);
+    hsum += std::sqrt(l2);
+  }
+  const double hbar = hm.n_edges > 0 ? hsum / double(hm.n_edges) : 1.0;
+  std::vector<float> relpos(3 * E), nstat(2 * N);
+  for (int64_t q = 0; q < E; ++q)
+    for (int c = 0; c < 3; ++c) relpos[3 * q + c] = float((X[3 * col[q] + c] - X[3 * dst[q] + c]) / hbar);
+  double msum = 0.0;
+  for (int64_t i = 0; i < N; ++i) msum += hm.mass[i];
+  const double mmean = msum / double(N);
+  for (int64_t i = 0; i < N; ++i) {
+    nstat[2 * i] = float(std::log(hm.mass[i] / mmean));
+    nstat[2 * i + 1] = float(rp[i + 1] - rp[i]) / 16.f;
+  }
+
+  gf_gnn* g = new gf_gnn();
+  g->mesh = mesh;
+  g->device = mesh->device;
+  GnnDev& G = g->g;
+  G.N = N;
+  G.E = E;
+  G.P = gnn_param_offsets(G.off);
+  auto fail = [&](gf_status st) {
+    cudaStreamSynchronize(s);
+    gnn_free(g);
+    delete g;
+    return st;
+  };
+  gf_status st = GF_OK;
+#define GNN_TRY(call)            \
+  do {                           \
+    st = (call);                 \
+    if (st != GF_OK) return fail(st); \
+  } while (0)
+  GNN_TRY(gnn_upload(g, rp, &G.row_ptr, s));
+  GNN_TRY(gnn_upload(g, col, &G.col, s));
+  GNN_TRY(gnn_upload(g, dst, &G.dst, s));
+  GNN_TRY(gnn_upload(g, amap, &G.amap, s));
+  GNN_TRY(gnn_upload(g, tpos, &G.tpos, s));
+  GNN_TRY(gnn_upload(g, relpos, &G.relpos, s));
+  GNN_TRY(gnn_upload(g, nstat, &G.nstat, s));
+  const size_t NH = size_t(N) * kHid;
+  GNN_TRY(gnn_alloc(g, size_t(E) * kEin, &G.efeat));
+  GNN_TRY(gnn_alloc(g, size_t(N), &G.T));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 6, &G.C));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &G.Y));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &G.B));
+  GNN_TRY(gnn_alloc(g, size_t(N), &G.freem));
+  GNN_TRY(gnn_alloc(g, size_t(N) * kNin, &G.X0));
+  GNN_TRY(gnn_alloc(g, NH, &G.Z0));
+  GNN_TRY(gnn_alloc(g, 4 * NH, &G.H));
+  GNN_TRY(gnn_alloc(g, 3 * NH, &G.Aa));
+  GNN_TRY(gnn_alloc(g, 3 * NH, &G.M));
+  GNN_TRY(gnn_alloc(g, 3 * NH, &G.ZU));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 16, &G.OUT));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 9, &G.Po));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &G.xo));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &G.xprev));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &G.ebuf));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &G.qbuf));
+  GNN_TRY(gnn_alloc(g, 1, &G.dscal));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 16, &G.dOUT));
+  GNN_TRY(gnn_alloc(g, NH, &G.dH));
+  GNN_TRY(gnn_alloc(g, NH, &G.dZ));
+  GNN_TRY(gnn_alloc(g, NH, &G.dM));
+  GNN_TRY(gnn_alloc(g, NH, &G.dA));
+  G.part_stride = (2 * kHid + 1) * kHid;
+  G.n_gpart = gnn_max_parts();
+  GNN_TRY(gnn_alloc(g, size_t(G.n_gpart) * G.part_stride, &G.gpart));
+  GNN_TRY(gnn_alloc(g, size_t(G.P), &G.grad));
+  GNN_TRY(gnn_alloc(g, size_t(G.P), &G.w32));
+  GNN_TRY(gnn_alloc(g, size_t(G.P), &G.w16));
+  GNN_TRY(gnn_alloc(g, size_t(G.P), &G.m1));
+  GNN_TRY(gnn_alloc(g, size_t(G.P), &G.m2));
+  GNN_TRY(gnn_alloc(g, 4, &G.scal));
+  GNN_TRY(gnn_alloc(g, kGnnMaxIters, &g->loss_hist));
+  G.loss = g->loss_hist;
+  GNN_TRY(gnn_alloc(g, size_t(3) * gnn_reduce_slots(), &G.red));
+  GNN_TRY(gnn_alloc(g, 4, &G.ticket));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &g->stage_b));
+  GNN_TRY(gnn_alloc(g, size_t(N) * 3, &g->stage_t));
+#undef GNN_TRY
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMemsetAsync(G.ticket, 0, 4 * sizeof(unsigned), s);
+  e = e ? e : cudaMemsetAsync(G.xprev, 0, sizeof(double) * 3 * N, s);
+  e = e ? e : cudaMemsetAsync(G.w32, 0, sizeof(float) * G.P, s);
+  e = e ? e : cudaMemsetAsync(G.w16, 0, sizeof(__nv_bfloat16) * G.P, s);
+  e = e ? e : cudaMemsetAsync(G.m1, 0, sizeof(float) * G.P, s);
+  e = e ? e : cudaMemsetAsync(G.m2, 0, sizeof(float) * G.P, s);
+  e = e ? e : cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("network setup: ") + cudaGetErrorString(e));
+    return fail(GF_CUDA_ERR);
+  }
+  mesh->gnn = g;
+  mesh->gnn_flags = 0;
+  *out = g;
+  return GF_OK;
+}
+
+void gf_gnn_destroy(gf_gnn* g) {
+  if (!g) return;
+  DeviceGuard guard(g->device);
+  if (g->mesh) {
+    cudaStreamSynchronize(g->mesh->stream);
+    if (g->mesh->gnn == g) {
+      g->mesh->gnn = nullptr;
+      g->mesh->gnn_flags = 0;
+    }
+  } else {
+    cudaDeviceSynchronize();
+  }
+  gnn_free(g);
+  delete g;
+}
+
+gf_status gf_gnn_params_set(gf_gnn* g, const float* w, int64_t n) {
+  if (!g || !g->mesh || !w || n != g->g.P) {
+    set_last_error("params_set: need the network, a host array and n == gf_gnn_n_params()");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(g->mesh->device);
+  cudaStream_t s = g->mesh->stream;
+  GF_CK(cudaMemcpyAsync(g->g.w32, w, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  GF_CK(cudaMemsetAsync(g->g.m1, 0, sizeof(float) * n, s));
+  GF_CK(cudaMemsetAsync(g->g.m2, 0, sizeof(float) * n, s));
+  g->mesh->launches += gnn_refresh_bf16(g->g, s);
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaStreamSynchronize(s));
+  g->adam_t = 0;
+  return GF_OK;
+}
+
+gf_status gf_gnn_params_get(gf_gnn* g, float* w, int64_t n) {
+  if (!g || !g->mesh || !w || n != g->g.P) {
+    set_last_error("params_get: need the network, a host array and n == gf_gnn_n_params()");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(g->mesh->device);
+  GF_CK(cudaMemcpyAsync(w, g->g.w32, sizeof(float) * n, cudaMemcpyDeviceToHost, g->mesh->stream));
+  GF_CK(cudaStreamSynchronize(g->mesh->stream));
+  return GF_OK;
+}
+
+gf_status gf_gnn_forward(gf_gnn* g, const double* b, int32_t mem, float* out, float* P, float* x0, float* node_in,
+                         float* edge_in) {
+  gf_status st = gnn_check(g);
+  if (st != GF_OK) return st;
+  if (!b || !valid_mem(mem)) {
+    set_last_error("forward: b must not be NULL, mem GF_MEM_HOST or GF_MEM_DEVICE");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(g->mesh->device);
+  cudaStream_t s = g->mesh->stream;
+  const GnnDev& G = g->g;
+  const double* bd = nullptr;
+  if ((st = gnn_stage(g, b, mem, g->stage_b, &bd)) != GF_OK) return st;
+  int64_t L = gnn_forward(G, g->mesh->dm, bd, s);
+  L += gnn_apply_export(G, s);
+  g->mesh->launches += L;
+  GF_CK(cudaGetLastError());
+  std::vector<float> o16;
+  if (out) {
+    o16.resize(size_t(G.N) * 16);
+    GF_CK(cudaMemcpyAsync(o16.data(), G.OUT, sizeof(float) * o16.size(), cudaMemcpyDeviceToHost, s));
+  }
+  if (P) GF_CK(cudaMemcpyAsync(P, G.Po, sizeof(float) * 9 * G.N, cudaMemcpyDeviceToHost, s));
+  if (x0) GF_CK(cudaMemcpyAsync(x0, G.xo, sizeof(float) * 3 * G.N, cudaMemcpyDeviceToHost, s));
+  if (node_in) GF_CK(cudaMemcpyAsync(node_in, G.X0, sizeof(float) * kNin * G.N, cudaMemcpyDeviceToHost, s));
+  if (edge_in && G.E > 0)
+    GF_CK(cudaMemcpyAsync(edge_in, G.efeat, sizeof(float) * kEin * G.E, cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaStreamSynchronize(s));
+  if (out)
+    for (int64_t i = 0; i < G.N; ++i)
+      for (int k = 0; k < kNout; ++k) out[kNout * i + k] = o16[16 * i + k];
+  return GF_OK;
+}
+
+gf_status gf_gnn_loss_grad(gf_gnn* g, const double* b, const double* target, int32_t mem, double* loss,
+                           float* grad) {
+  gf_status st = gnn_check(g);
+  if (st != GF_OK) return st;
+  if (!b || !target || !valid_mem(mem)) {
+    set_last_error("loss_grad: b and target must not be NULL, mem GF_MEM_HOST or GF_MEM_DEVICE");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(g->mesh->device);
+  cudaStream_t s = g->mesh->stream;
+  const GnnDev& G = g->g;
+  const double *bd = nullptr, *td = nullptr;
+  if ((st = gnn_stage(g, b, mem, g->stage_b, &bd)) != GF_OK) return st;
+  if ((st = gnn_stage(g, target, mem, g->stage_t, &td)) != GF_OK) return st;
+  GF_CK(cudaMemsetAsync(G.grad, 0, sizeof(float) * G.P, s));
+  GF_CK(cudaMemsetAsync(G.loss, 0, sizeof(double), s));
+  int64_t L = gnn_forward(G, g->mesh->dm, bd, s);
+  L += gnn_backward_pair(G, g->mesh->dm, td, s);
+  g->mesh->launches += L;
+  GF_CK(cudaGetLastError());
+  double h_loss = 0.0;
+  GF_CK(cudaMemcpyAsync(&h_loss, G.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (grad) GF_CK(cudaMemcpyAsync(grad, G.grad, sizeof(float) * G.P, cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaStreamSynchronize(s));
+  if (loss) *loss = h_loss;
+  return GF_OK;
+}
+
+gf_status gf_gnn_train(gf_gnn* g, int32_t iters, float lr, double* loss_first, double* loss_last) {
+  gf_status st = gnn_check(g);
+  if (st != GF_OK) return st;
+  if (iters < 1 || iters > kGnnMaxIters || !(lr > 0.f) || !std::isfinite(lr)) {
+    set_last_error("train: need 1 <= iters <= 1024 and lr > 0");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(g->mesh->device);
+  cudaStream_t s = g->mesh->stream;
+  const DevMesh& d = g->mesh->dm;
+  int64_t L = gnn_pair(d, g->g.xprev, g->stage_b, g->stage_t, s);
+  GF_CK(cudaMemsetAsync(g->loss_hist, 0, sizeof(double) * iters, s));
+  for (int k = 0; k < iters; ++k) {
+    GnnDev G = g->g;
+    G.loss = g->loss_hist + k;
+    GF_CK(cudaMemsetAsync(G.grad, 0, sizeof(float) * G.P, s));
+    L += gnn_forward(G, d, g->stage_b, s);
+    L += gnn_backward_pair(G, d, g->stage_t, s);
+    L += gnn_adam(G, 1.f, lr, ++g->adam_t, s);
+  }
+  g->mesh->launches += L;
+  GF_CK(cudaGetLastError());
+  double h[2] = {0.0, 0.0};
+  GF_CK(cudaMemcpyAsync(&h[0], g->loss_hist, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaMemcpyAsync(&h[1], g->loss_hist + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaStreamSynchronize(s));
+  if (loss_first) *loss_first = h[0];
+  if (loss_last) *loss_last = h[1];
+  return GF_OK;
+}
+
+gf_status gf_gnn_pair_get(gf_gnn* g, double* b, double* target) {
+  gf_status st = gnn_check(g);
+  if (st != GF_OK) return st;
+  if (!b || !target) {
+    set_last_error("pair_get: b and target must not be NULL");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(g->mesh->device);
+  cudaStream_t s = g->mesh->stream;
+  g->mesh->launches += gnn_pair(g->mesh->dm, g->g.xprev, g->stage_b, g->stage_t, s);
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaMemcpyAsync(b, g->stage_b, sizeof(double) * 3 * g->g.N, cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaMemcpyAsync(target, g->stage_t, sizeof(double) * 3 * g->g.N, cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaStreamSynchronize(s));
+  return GF_OK;
+}
+
+gf_status gf_gnn_attach(gf_mesh* mesh, gf_gnn* g, int32_t flags) {
+  if (!mesh || !g || g->mesh != mesh || (flags & ~(GF_GNN_START | GF_GNN_PRECOND))) {
+    set_last_error("attach: the network must belong to this mesh; flags GF_GNN_START | GF_GNN_PRECOND or 0");
+    return GF_BAD_ARG;
+  }
+  mesh->gnn_flags = flags;
+  return GF_OK;
+}
+
+}  // extern "C"
+
+void gnn_orphan(gf_gnn* g) { g->mesh = nullptr; }

@@ -131,6 +131,7 @@ struct StepScalars {
   double dt;
   float dtf, sKv, cv, alphaf, cmf;   // dt, dt beta + dt^2, beta + dt, alpha, 1 + dt alpha
   int has_fext, has_pvel;
+  int learned;                        // pcg_init keeps the preconditioner, start and |b_free|^2 already set
   int64_t n_pinned;
 };
 

@@ -582,12 +582,23 @@ __global__ void __launch_bounds__(kThreads) kb_set_pinned(const BatchTab* __rest
 }
 
 // r = b - A dv on free nodes, block-Jacobi inverse, z = P r, p = z; rz, rr.
+// With sp.learned the preconditioner blocks and the start dv are the learned
+// ones already in place, and the reference norm |b_free|^2 is kept from the
+// plain initialisation that ran before them.
 __device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
   double v[2] = {0.0, 0.0};
   for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     double r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
-    if (!m.pinned[i]) {
+    if (!m.pinned[i] && sp.learned) {
+      double ad[3];
+      spmv_row(m, i, m.dv, ad);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[c] = m.rhs[3 * i + c] - ad[c];
+      const double* pi = m.pinv + 9 * i;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) z[c] = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
+    } else if (!m.pinned[i]) {
       double ad[3];
       spmv_row(m, i, m.dv, ad);
 #pragma unroll
@@ -618,10 +629,10 @@ __device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& 
     PcgState* s = m.pcg;
     s->rz = out[0];
     s->rr = out[1];
-    s->bb = out[1];
+    if (!sp.learned) s->bb = out[1];
     s->iters = 0;
     s->status = GF_OK;
-    s->done = (out[1] == 0.0 || out[1] <= s->tol2 * out[1]) ? 1 : 0;
+    s->done = (out[1] == 0.0 || out[1] <= s->tol2 * s->bb) ? 1 : 0;
     if (!isfinite(out[1])) {
       s->status = GF_NAN;
       s->done = 1;

@@ -10,6 +10,7 @@ built library or a CUDA device, calls raise.
 from __future__ import annotations
 
 import ctypes
+import weakref
 import math
 import os
 from typing import Optional
@@ -123,6 +124,17 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_batch_autotune": (ctypes.c_int, [P, ctypes.c_double, P, P, P, P, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_double)]),
         "gf_batch_launch_count": (ctypes.c_int64, [P]),
+        "gf_gnn_n_params": (ctypes.c_int64, []),
+        "gf_gnn_create": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+        "gf_gnn_destroy": (None, [P]),
+        "gf_gnn_params_set": (ctypes.c_int, [P, P, ctypes.c_int64]),
+        "gf_gnn_params_get": (ctypes.c_int, [P, P, ctypes.c_int64]),
+        "gf_gnn_forward": (ctypes.c_int, [P, P, ctypes.c_int32, P, P, P, P, P]),
+        "gf_gnn_loss_grad": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), P]),
+        "gf_gnn_train": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+        "gf_gnn_attach": (ctypes.c_int, [P, P, ctypes.c_int32]),
+        "gf_gnn_pair_get": (ctypes.c_int, [P, P, P]),
         "gf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "gf_last_error": (ctypes.c_char_p, []),
     }
@@ -185,6 +197,9 @@ class Mesh:
     # -- lifetime ---------------------------------------------------------
     def close(self):
         if self._h:
+            gnn = getattr(self, "_gnn", None)
+            if gnn is not None and gnn() is not None:
+                gnn().close()
             load_library().gf_mesh_destroy(self._h)
             self._h = None
 
@@ -474,3 +489,92 @@ def mesh_create(nodes, tets, mat: Material, precision: int = FP64, cg_rtol: floa
     inf = MeshInfo()
     _check(lib.gf_mesh_info_get(h, ctypes.byref(inf)))
     return Mesh(h, inf.n_nodes, inf.n_tets, inf.n_edges, keep)
+
+
+GNN_START, GNN_PRECOND = 1, 2
+
+# Parameter tensors of the learned start / preconditioner network, in storage
+# order, each row-major [in][out] (the layout gf_gnn_params_set expects).
+GNN_PARAM_SHAPES = ([("W0", (16, 64)), ("b0", (64,))]
+                    + [t for l in range(3) for t in ((f"Wa{l}", (64, 64)), (f"We{l}", (16, 64)), (f"bm{l}", (64,)),
+                                                     (f"Wu{l}", (128, 64)), (f"bu{l}", (64,)))]
+                    + [("Wd", (64, 9)), ("bd", (9,))])
+
+
+class Gnn:
+    """gf_gnn: learned warm start and block preconditioner for the solve of a
+    GF_FP64 mesh (message passing over the mesh graph, bfloat16 weights)."""
+
+    def __init__(self, mesh: Mesh, params=None):
+        lib = load_library()
+        h = P()
+        _check(lib.gf_gnn_create(mesh._h, ctypes.byref(h)))
+        self._h = h
+        self.mesh = mesh
+        mesh._gnn = weakref.ref(self)
+        self.n_params = int(lib.gf_gnn_n_params())
+        self.n_graph_edges = mesh.info["n_blocks"] - mesh.n_nodes
+        if params is not None:
+            self.params_set(params)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().gf_gnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params_set(self, w):
+        w = np.ascontiguousarray(w, np.float32).ravel()
+        if w.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {w.size}")
+        _check(load_library().gf_gnn_params_set(self._h, w.ctypes.data, w.size))
+
+    def params_get(self) -> np.ndarray:
+        w = np.empty(self.n_params, np.float32)
+        _check(load_library().gf_gnn_params_get(self._h, w.ctypes.data, w.size))
+        return w
+
+    def forward(self, b) -> dict:
+        """Network outputs on the mesh's last assembled system for right-hand side b."""
+        n, e = self.mesh.n_nodes, self.n_graph_edges
+        pb, kb, kb_ = _arg(b, np.float64, 3 * n, "b")
+        out = np.empty((n, 9), np.float32)
+        Pm = np.empty((n, 3, 3), np.float32)
+        x0 = np.empty((n, 3), np.float32)
+        fin = np.empty((n, 16), np.float32)
+        ein = np.empty((max(e, 1), 16), np.float32)
+        _check(load_library().gf_gnn_forward(self._h, pb, kb, out.ctypes.data, Pm.ctypes.data, x0.ctypes.data,
+                                             fin.ctypes.data, ein.ctypes.data))
+        return {"out": out, "P": Pm, "x0": x0, "node_in": fin, "edge_in": ein[:e]}
+
+    def loss_grad(self, b, target):
+        n = self.mesh.n_nodes
+        pb, kb, kb_ = _arg(b, np.float64, 3 * n, "b")
+        pt, kt, kt_ = _arg(target, np.float64, 3 * n, "target")
+        loss = ctypes.c_double()
+        grad = np.empty(self.n_params, np.float32)
+        _check(load_library().gf_gnn_loss_grad(self._h, pb, pt, _one_kind(kb, kt), ctypes.byref(loss),
+                                               grad.ctypes.data))
+        return float(loss.value), grad
+
+    def train(self, iters: int = 1, lr: float = 1e-3):
+        """Adam steps on the mesh's last solved step; returns (first loss, last loss)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(load_library().gf_gnn_train(self._h, int(iters), float(lr), ctypes.byref(a), ctypes.byref(b)))
+        return float(a.value), float(b.value)
+
+    def pair_get(self):
+        """(b, target) of the mesh's last solved step, as gf_gnn_train uses them."""
+        b = np.empty(3 * self.mesh.n_nodes)
+        t = np.empty(3 * self.mesh.n_nodes)
+        _check(load_library().gf_gnn_pair_get(self._h, b.ctypes.data, t.ctypes.data))
+        return b, t
+
+    def attach(self, flags: int = 1):
+        """GNN_START (learned start), GNN_PRECOND (learned blocks), both, or 0 (off)."""
+        _check(load_library().gf_gnn_attach(self.mesh._h, self._h, int(flags)))

@@ -30,17 +30,19 @@ def small_problem(seed=0, n=40):
     dv = rng.normal(size=(n, 3))
     free = rng.uniform(size=n) > 0.1
     s = 0.7
-    return g, f, C, b, dv, free, s, Dinv
+    R = rng.normal(size=(3 * n, 3 * n))
+    Asys = R @ R.T / (3 * n) + np.eye(3 * n)              # SPD system
+    return g, f, C, b, dv, free, s, Dinv, Asys
 
 
 def test_gradients_match_finite_differences():
-    g, f, C, b, dv, free, s, _ = small_problem()
+    g, f, C, b, dv, free, s, _, Asys = small_problem()
     params = gnn.init_params(3)
     rng = np.random.default_rng(4)
     for k in params:                       # make every path active (decoder not zero)
         params[k] = params[k] + 0.05 * rng.normal(size=params[k].shape)
     params["Wd"] = 0.02 * rng.normal(size=params["Wd"].shape)
-    loss, grads = gnn.loss_and_grad(params, g, f, C, b, dv, free, s)
+    loss, grads = gnn.loss_and_grad(params, g, f, C, b, dv, free, s, Asys)
     vec = gnn.flatten(params)
     gvec = gnn.flatten(grads)
     offs = np.cumsum([0] + [int(np.prod(v)) for v in gnn.param_shapes().values()])
@@ -51,14 +53,14 @@ def test_gradients_match_finite_differences():
         vp, vm = vec.copy(), vec.copy()
         vp[i] += h
         vm[i] -= h
-        lp, _ = gnn.loss_and_grad(gnn.unflatten(vp), g, f, C, b, dv, free, s)
-        lm, _ = gnn.loss_and_grad(gnn.unflatten(vm), g, f, C, b, dv, free, s)
+        lp, _ = gnn.loss_and_grad(gnn.unflatten(vp), g, f, C, b, dv, free, s, Asys)
+        lm, _ = gnn.loss_and_grad(gnn.unflatten(vm), g, f, C, b, dv, free, s, Asys)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - gvec[i]) <= 1e-6 * max(abs(fd), 1e-2 * abs(loss)), (i, fd, gvec[i])
 
 
 def test_initial_network_is_scaled_block_jacobi():
-    g, f, C, b, dv, free, s, Dinv = small_problem(seed=1)
+    g, f, C, b, dv, free, s, Dinv, _ = small_problem(seed=1)
     out = gnn.forward(gnn.init_params(5), g, f)
     assert np.abs(out).max() == 0.0
     P, x0, _, _ = gnn.apply_outputs(out, C, b, s)
@@ -67,7 +69,7 @@ def test_initial_network_is_scaled_block_jacobi():
 
 
 def test_preconditioner_blocks_are_spd():
-    g, f, C, b, dv, free, s, _ = small_problem(seed=2)
+    g, f, C, b, dv, free, s, _, _ = small_problem(seed=2)
     params = gnn.init_params(6)
     params["Wd"] = 0.05 * np.random.default_rng(7).normal(size=params["Wd"].shape)
     P, _, _, _ = gnn.apply_outputs(gnn.forward(params, g, f), C, b, s)
@@ -125,3 +127,41 @@ def test_build_inputs_hand_worked_three_nodes():
         np.testing.assert_allclose(C[i] @ C[i].T, np.linalg.inv(D[i]), rtol=1e-13, atol=1e-15)
         assert np.allclose(np.triu(C[i], 1), 0)
     assert list(free) == [True, True, False]
+
+
+def test_energy_loss_of_a_scaled_target():
+    """With target = c x0 the energy-norm loss is (1 - c)^2 / c^2 whatever A is,
+    and the loss and every gradient vanish at target = x0."""
+    g, f, C, b, dv, free, s, _, Asys = small_problem(seed=3)
+    params = gnn.init_params(8)
+    rng = np.random.default_rng(9)
+    params["Wd"] = 0.05 * rng.normal(size=params["Wd"].shape)
+    _, x0, _, _ = gnn.apply_outputs(gnn.forward(params, g, f), C, b, s)
+    for c in (0.5, 2.0, -1.0):
+        loss, _ = gnn.loss_and_grad(params, g, f, C, b, c * x0, free, s, Asys)
+        assert loss == pytest.approx((1 - c) ** 2 / c ** 2, rel=1e-12)
+    loss, grads = gnn.loss_and_grad(params, g, f, C, b, x0, free, s, Asys)
+    assert loss == 0.0
+    assert max(np.abs(v).max() for v in grads.values()) == 0.0
+
+
+def test_training_pair_targets_solve_the_shifted_system():
+    """training_pair: for dv solving the free system (pinned values prescribed),
+    A_ff target = b_net on free rows, and target = 0, b_net = 0 on pinned ones."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    *_, Asys = small_problem(seed=4, n=30)
+    n = 30
+    rng = np.random.default_rng(5)
+    pin = rng.uniform(size=n) < 0.2
+    b = rng.normal(size=(n, 3))
+    dv = np.zeros((n, 3))
+    dv[pin] = rng.normal(size=(pin.sum(), 3))
+    fr = np.repeat(~pin, 3)
+    A = sp.csr_matrix(Asys)
+    rhs = b.ravel()[fr] - A[fr][:, ~fr] @ dv.ravel()[~fr]
+    dv.reshape(-1)[fr] = spl.spsolve(A[fr][:, fr].tocsc(), rhs)
+    x_prev = rng.normal(size=(n, 3))
+    bn, tg = gnn.training_pair(A, b, dv, x_prev, pin)
+    np.testing.assert_allclose((A[fr][:, fr] @ tg.ravel()[fr]), bn.ravel()[fr], rtol=1e-10, atol=1e-12)
+    assert np.abs(tg[pin]).max() == 0.0 and np.abs(bn[pin]).max() == 0.0

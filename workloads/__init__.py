@@ -10,3 +10,4 @@ from .meshes import (  # noqa: F401
     kuhn_box, bcc_ellipsoid, jitter, beam_config, loaf_config, glass_config,
     batch_configs, two_tet_fig4, single_tet, Workload, LOAF_AXES,
 )
+from .weights import he_normal_weights  # noqa: F401
