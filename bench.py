@@ -216,6 +216,66 @@ def run_batch(args, gf, torch, barrier, stream) -> dict:
     return out
 
 
+def run_learned(args, gf, torch, barrier, stream, w, mat, f_dev) -> dict:
+    """Learned warm start on the loaf: one 200-step run; the network trains
+    online on the first 160 steps (one (residual, correction) pair per step,
+    5 Adam iterations each) and the last 40 steps are held out: PCG iterations
+    and ms/step of the learned start vs plain PCG from the same state."""
+    from workloads import he_normal_weights
+    n_steps, n_train = 200, 160
+    m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
+    init = he_normal_weights(gf.GNN_PARAM_SHAPES, seed=1, zero=("Wd",))
+    net = gf.Gnn(m, init)
+    t_train, n_adam, first, last = 0.0, 0, None, None
+    for k in range(n_train):
+        m.step(w.dt, f_dev)
+        if k:
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            l0, l1 = net.train(iters=5, lr=1e-5)
+            t_train += time.perf_counter() - a
+            n_adam += 5
+            first = l0 if first is None else first
+            last = l1
+    x, v = m.positions_get(), m.velocities_get()
+    _, lab = m.damage_get()
+    chi = m.chi_get()
+
+    def held_out(flags):
+        net.attach(flags)
+        m.profile_reset()
+        m.profile_enable(True)
+        iters = []
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps - n_train):
+            s = m.step(w.dt, f_dev)
+            assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
+            iters.append(s["cg_iters"])
+        e1.record(stream)
+        barrier()
+        m.profile_enable(False)
+        prof = m.profile_get()
+        n = n_steps - n_train
+        return {"ms_per_step": e0.elapsed_time(e1) / n, "cg_iters_per_step": statistics.mean(iters),
+                "gnn_ms_per_step": prof["gnn"][0] / n,
+                "pcg_ms_per_step": sum(prof[k][0] for k in ("pcg_init", "pcg_spmv", "pcg_update", "pcg_p")) / n}
+
+    learned = held_out(gf.GNN_START)          # x_prev is the last training step's solution
+    m.state_set(x=x, v=v, labels=lab, chi=chi)
+    plain = held_out(0)
+    net.close()
+    m.close()
+    return {"workload": "loaf_bcc_620k_fp64: 200-step run, online training on steps 2-160 "
+                        "(159 pairs x 5 Adam iterations, lr 1e-5, zero-decoder start), held out: steps 161-200",
+            "train_ms_per_adam_iter": 1e3 * t_train / max(n_adam, 1),
+            "train_loss_first_last": [first, last],
+            "dtype": "bf16 weights, f32 activations; PCG f64 to the same 1e-6 residual",
+            "held_out": {"plain": plain, "learned_start": learned},
+            "cg_iters_saved_per_step": plain["cg_iters_per_step"] - learned["cg_iters_per_step"]}
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -284,6 +344,7 @@ def run_ours(args) -> None:
     mix_ms, mix_launches, mix_prof, mix_it, mix_sw = timed(mm, args.steps)
     mm.close()
     batch = run_batch(args, gf, torch, barrier, stream) if not args.no_batch else None
+    learned = run_learned(args, gf, torch, barrier, stream, w, mat, f_dev) if not args.no_learned else None
     t_all = torch.tensor([ms, e2e_ms, mix_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
@@ -319,6 +380,7 @@ def run_ours(args) -> None:
                   "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mix_prof.items()},
                   "roofline": mix_roof},
         "batch": batch,
+        "learned": learned,
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "kernel_launches": {k: v[1] for k, v in prof.items()},
         "clocks": clocks,
@@ -340,8 +402,17 @@ def run_profile_step(args) -> None:
                                                     radius=w.radius), cg_rtol=w.cg_rtol,
                        precision=gf.MIXED if args.precision == "mixed" else gf.FP64)
     f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
-    for _ in range(args.steps):
+    net = None
+    if args.precision == "learned":      # zero-decoder network: learned start from the second step on
+        from workloads import he_normal_weights
+        net = gf.Gnn(m, he_normal_weights(gf.GNN_PARAM_SHAPES, seed=1, zero=("Wd",)))
+    for k in range(args.steps):
+        if net is not None and k == 1:
+            net.attach(gf.GNN_START)
         s = m.step(w.dt, f_dev)
+    if net is not None:
+        net.attach(0)
+        net.train(iters=1, lr=1e-5)
     torch.cuda.synchronize()
     print(json.dumps({"profile_step": True, "steps": args.steps, "last": s, "launches": m.launch_count()}))
 
@@ -354,9 +425,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched form")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start form")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="form run by --profile-step")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "learned"], default="fp64",
+                    help="form run by --profile-step (learned: FP64 with the network's start, then one Adam step)")
     args = ap.parse_args()
     if args.cpu_sample_child:
         cpu_sample_child(args.cpu_sample_child)

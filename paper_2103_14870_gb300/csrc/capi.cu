@@ -49,7 +49,8 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_edge_driver: case kB_edge_driver32: return {cdiv(NE, 256), 256};
     case kB_node_init: return {cdiv(N, 256), 256};
     case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
-    case kB_gather64: case kB_gather32: return {cdiv(32 * N, 256), 256};
+    case kB_gather64: return {cdiv(9 * m.NB + 12 * N, 256), 256};
+    case kB_gather32: return {cdiv(32 * N, 256), 256};
     case kB_set_pinned: return {cdiv(sp.n_pinned, 256), 256};
     case kB_pcg_init: case kB_pcg_spmv: case kB_pcg_update: case kB_true_residual: return {red_grid(N), 256};
     case kB_pcg_p: return {red_grid(3 * N), 256};

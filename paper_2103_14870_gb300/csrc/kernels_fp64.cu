@@ -375,9 +375,9 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
 // Two-phase FP64 assembly (no colours, no atomics, one launch per phase).
 // k_elem64 (thread per tet) writes the tet's ten upper-triangle blocks of
 // (dt beta + dt^2) chi k_e and its four rhs shares dt chi (f_a - (beta+dt)(k_e v)_a)
-// to its row of the element buffer; k_gather64 (warp per node row, lane per
-// block entry) sums them in a fixed precomputed order and adds mass, external
-// force and mass damping.
+// to its row of the element buffer; k_gather64 (thread per matrix entry or
+// rhs component) sums them in a fixed precomputed order and adds mass,
+// external force and mass damping.
 constexpr int kElemW64 = 104;
 
 __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
@@ -497,35 +497,54 @@ __global__ void __launch_bounds__(128) kb_elem64(const BatchTab* __restrict__ ta
   elem64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
+// Phase 2 of the assembly: each matrix entry and rhs component is the sum, in
+// a fixed order, of its element contributions (plus the lumped-mass term on
+// the diagonal, Eq. 2).  Threads [0, 9 NB) take one entry of an off-diagonal
+// block each (the 4-6 tets around an edge); threads [9 NB, 9 NB + 12 N) take
+// a node's nine diagonal entries and three rhs components (the ~24 tets around
+// the node).  Neighbouring threads sum lists of similar length, so the FP64
+// adds issue in full warps.
 __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const double dt = sp.dt, alpha = mt.alpha;
-  const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
-
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  if (i >= m.N) return;                               // whole warp leaves together
-  const int rb = m.row_ptr[i], rl = m.row_ptr[i + 1] - rb;
-  const int dslot = m.diag_blk[i];
-  const double mi = m.mass[i];
-  for (int o = lane; o < 9 * rl; o += 32) {
-    const int p = o / 9, e = o - 9 * p;
-    const int slot = rb + p;
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t n_off = 9 * m.NB;
+  if (t < n_off) {
+    const int64_t slot = t / 9;
+    const int e = int(t - 9 * slot);
+    if (m.diag_blk[m.col[slot]] == slot) return;       // (j, j): done by the node threads
     const int et = 3 * (e % 3) + e / 3;
     double acc = 0.0;
     for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
       const int ent = m.sc_ent[c];
       acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
     }
-    if (slot == dslot && (e == 0 || e == 4 || e == 8)) acc += (1.0 + dt * alpha) * mi;
-    m.val[9 * int64_t(slot) + e] = acc;
+    m.val[9 * slot + e] = acc;
+    return;
   }
-  if (lane < 3) {
+  const int64_t u = t - n_off;
+  if (u >= 12 * m.N) return;
+  const int64_t i = u / 12;
+  const int q = int(u - 12 * i);
+  const double mi = m.mass[i];
+  if (q < 9) {
+    const int slot = m.diag_blk[i];
+    const int et = 3 * (q % 3) + q / 3;
+    double acc = 0.0;
+    for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
+      const int ent = m.sc_ent[c];
+      acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : q)];
+    }
+    if (q == 0 || q == 4 || q == 8) acc += (1.0 + dt * alpha) * mi;
+    m.val[9 * int64_t(slot) + q] = acc;
+  } else {
+    const int c3 = q - 9;
+    const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
     double acc = 0.0;
     for (int k = m.np_ptr[i]; k < m.np_ptr[i + 1]; ++k) {
       const int pr = m.np_pair[k];
-      acc += m.ebuf[kElemW64 * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
+      acc += m.ebuf[kElemW64 * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + c3];
     }
-    m.rhs[3 * i + lane] = acc + dt * ((f_ext ? f_ext[3 * i + lane] : 0.0) - alpha * mi * m.v[3 * i + lane]);
+    m.rhs[3 * i + c3] = acc + dt * ((f_ext ? f_ext[3 * i + c3] : 0.0) - alpha * mi * m.v[3 * i + c3]);
   }
 }
 __global__ void __launch_bounds__(256) k_gather64(DevMesh m, Material mt, StepScalars sp) {

@@ -134,36 +134,89 @@ __global__ void __launch_bounds__(kT) k_gnn_edgefeat(GnnDev g, DevMesh m) {
   for (int q = 0; q < kEin / 4; ++q) dst[q] = make_float4(e[4 * q], e[4 * q + 1], e[4 * q + 2], e[4 * q + 3]);
 }
 
-// Z = [X1 | X2] W + b (K1 + K2 <= 128 inputs, NO <= 64 outputs), one thread per
-// node; mode 0: Z only, 1: also Hout = relu(Z), 2: also Hout = Hres + relu(Z).
-__global__ void __launch_bounds__(128) k_dense(int64_t N, const float* X1, int K1, const float* X2, int K2,
-                                               const __nv_bfloat16* W, const __nv_bfloat16* bias, int NO, float* Z,
-                                               int ldz, const float* Hres, float* Hout, int mode) {
-  __shared__ float w[128 * 64];
-  __shared__ float bs[64];
+// Z = [X1 | X2] W' (+ bias) over 64-node x 64-output tiles, 256 threads, 4 x 4
+// (X1, X2 row strides ld1, ld2)
+// outputs per thread, K staged in chunks of 32 through shared memory.
+// X rows are read as float4: ld1, ld2 multiples of 4 and K1 a multiple of 4
+// (entries past K inside a row are read and dropped).
+// W' (k, o) = W[k * ldw + o], or W[(k0 + o) * ldw + k] when trans (the
+// backward pass dX = dZ W[k0 : k0 + 64, :]^T).  K1 is a multiple of 32 when
+// K2 > 0.  Epilogue: mode 0 Z = acc (+ Z when accumulate), 1 also
+// Hout = relu(Z), 2 also Hout = Hres + relu(Z).
+constexpr int kDT = 64, kDK = 32;
+__global__ void __launch_bounds__(256, 3) k_dense(int64_t N, const float* X1, int K1, int ld1, const float* X2, int K2,
+                                               int ld2, const __nv_bfloat16* W, int ldw, int k0, int trans,
+                                               const __nv_bfloat16* bias, int NO, float* Z, int ldz,
+                                               const float* Hres, float* Hout, int mode, int accumulate) {
+  __shared__ float xs[kDT][kDK + 1];
+  __shared__ __align__(16) float ws[kDK][kDT];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t r0 = int64_t(blockIdx.x) * kDT;
   const int K = K1 + K2;
-  for (int q = threadIdx.x; q < K * NO; q += blockDim.x) w[q] = bf(W[q]);
-  for (int q = threadIdx.x; q < NO; q += blockDim.x) bs[q] = bias ? bf(bias[q]) : 0.f;
-  __syncthreads();
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= N) return;
-  float acc[64];
+  float acc[4][4];
 #pragma unroll
-  for (int o = 0; o < 64; ++o) acc[o] = 0.f;
-  for (int k = 0; k < K; ++k) {
-    const float xv = k < K1 ? X1[int64_t(K1) * i + k] : X2[int64_t(K2) * i + (k - K1)];
-    const float* wr = w + k * NO;
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int o = 0; o < 64; ++o)
-      if (o < NO) acc[o] += xv * wr[o];
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int kc = 0; kc < K; kc += kDK) {
+    __syncthreads();
+#pragma unroll
+    for (int q0 = 0; q0 < kDT * kDK / 4; q0 += 256) {   // float4 per thread: rows are 16-byte aligned
+      const int q = q0 + tid, r = q / (kDK / 4), kk = 4 * (q % (kDK / 4)), k = kc + kk;
+      const int64_t row = r0 + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < N && k < K)
+        v = k < K1 ? *reinterpret_cast<const float4*>(X1 + int64_t(ld1) * row + k)
+                   : *reinterpret_cast<const float4*>(X2 + int64_t(ld2) * row + (k - K1));
+      xs[r][kk] = k < K ? v.x : 0.f;
+      xs[r][kk + 1] = k + 1 < K ? v.y : 0.f;
+      xs[r][kk + 2] = k + 2 < K ? v.z : 0.f;
+      xs[r][kk + 3] = k + 3 < K ? v.w : 0.f;
+    }
+#pragma unroll
+    for (int q0 = 0; q0 < kDK * kDT; q0 += 256) {
+      const int q = q0 + tid, kk = q / kDT, o = q % kDT, k = kc + kk;
+      float v = 0.f;
+      if (o < NO && k < K) v = __bfloat162float(trans ? W[int64_t(k0 + o) * ldw + k] : W[int64_t(k) * ldw + o]);
+      ws[kk][o] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kDK; ++kk) {
+      const float4 b = *reinterpret_cast<const float4*>(&ws[kk][4 * tx]);
+      float a[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = xs[4 * ty + i][kk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] += a[i] * b.x;
+        acc[i][1] += a[i] * b.y;
+        acc[i][2] += a[i] * b.z;
+        acc[i][3] += a[i] * b.w;
+      }
+    }
+  }
+  float bs[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = 4 * tx + j;
+    bs[j] = (bias && o < NO) ? __bfloat162float(bias[o]) : 0.f;
   }
 #pragma unroll
-  for (int o = 0; o < 64; ++o) {
-    if (o >= NO) break;
-    const float z = acc[o] + bs[o];
-    Z[int64_t(ldz) * i + o] = z;
-    if (mode == 1) Hout[64 * i + o] = fmaxf(z, 0.f);
-    else if (mode == 2) Hout[64 * i + o] = Hres[64 * i + o] + fmaxf(z, 0.f);
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = r0 + 4 * ty + i;
+    if (row >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = 4 * tx + j;
+      if (o >= NO) continue;
+      float z = acc[i][j] + bs[j];
+      float* zp = Z + int64_t(ldz) * row + o;
+      if (accumulate) z += *zp;
+      *zp = z;
+      if (mode == 1) Hout[64 * row + o] = fmaxf(z, 0.f);
+      else if (mode == 2) Hout[64 * row + o] = Hres[64 * row + o] + fmaxf(z, 0.f);
+    }
   }
 }
 
@@ -191,7 +244,28 @@ __global__ void __launch_bounds__(kT) k_gnn_edge_fwd(GnnDev g, const float* a, c
   const float b0 = bf(bm[2 * lane]), b1 = bf(bm[2 * lane + 1]);
   float s0 = 0.f, s1 = 0.f;
   const int p0 = g.row_ptr[i], p1 = g.row_ptr[i + 1];
-  for (int p = p0; p < p1; ++p) {
+  int p = p0;
+  for (; p + 1 < p1; p += 2) {   // two messages per pass: their loads overlap
+    const int64_t ja = g.col[p], jb = g.col[p + 1];
+    float ea[kEin], eb[kEin];
+    load_efeat(g.efeat, p, ea);
+    load_efeat(g.efeat, p + 1, eb);
+    const float2 aa = reinterpret_cast<const float2*>(a + 64 * ja)[lane];
+    const float2 ab = reinterpret_cast<const float2*>(a + 64 * jb)[lane];
+    float za0 = aa.x + b0, za1 = aa.y + b1, zb0 = ab.x + b0, zb1 = ab.y + b1;
+#pragma unroll
+    for (int k = 0; k < kEin; ++k) {
+      za0 += ea[k] * we0[k];
+      za1 += ea[k] * we1[k];
+      zb0 += eb[k] * we0[k];
+      zb1 += eb[k] * we1[k];
+    }
+    s0 += fmaxf(za0, 0.f);
+    s1 += fmaxf(za1, 0.f);
+    s0 += fmaxf(zb0, 0.f);
+    s1 += fmaxf(zb1, 0.f);
+  }
+  if (p < p1) {
     const int64_t j = g.col[p];
     float e[kEin];
     load_efeat(g.efeat, p, e);
@@ -386,38 +460,6 @@ __global__ void __launch_bounds__(kT) k_gnn_train_bwd(GnnDev g) {
 __global__ void __launch_bounds__(kT) k_relu_mask(int64_t n, const float* Z, const float* dY, float* dZ) {
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (q < n) dZ[q] = Z[q] > 0.f ? dY[q] : 0.f;
-}
-
-// dX[:, k] (+)= sum_o dZ[:, o] W[k0 + k][o] for k < 64 (thread per node)
-__global__ void __launch_bounds__(128) k_dense_bwd_x(int64_t N, const float* dZ, int ldz, int NO,
-                                                     const __nv_bfloat16* W, int k0, float* dX, int accumulate) {
-  __shared__ float w[64 * 64];
-  for (int q = threadIdx.x; q < 64 * NO; q += blockDim.x) {
-    const int k = q / NO, o = q - k * NO;
-    w[o * 64 + k] = bf(W[(k0 + k) * NO + o]);
-  }
-  __syncthreads();
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= N) return;
-  float acc[64];
-#pragma unroll
-  for (int k = 0; k < 64; ++k) acc[k] = 0.f;
-  for (int o = 0; o < NO; ++o) {
-    const float d = dZ[int64_t(ldz) * i + o];
-    const float* wr = w + o * 64;
-#pragma unroll
-    for (int k = 0; k < 64; ++k) acc[k] += d * wr[k];
-  }
-  float4* dst = reinterpret_cast<float4*>(dX + 64 * i);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    float4 v = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-    if (accumulate) {
-      const float4 u = dst[q];
-      v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
-    }
-    dst[q] = v;
-  }
 }
 
 // Per-CTA partial weight gradients over a grid-stride set of 32-node tiles:
@@ -616,22 +658,23 @@ int gnn_forward(const GnnDev& g, const DevMesh& m, const double* b, cudaStream_t
     k_gnn_edgefeat<<<cdiv(g.E, kT), kT, 0, s>>>(g, m);
     ++L;
   }
-  const unsigned nb = cdiv(N, 128);
-  k_dense<<<nb, 128, 0, s>>>(N, g.X0, kNin, nullptr, 0, W + g.off[kPW0], W + g.off[kPb0], 64, g.Z0, 64, nullptr, g.H,
-                             1);
+  const unsigned nb = cdiv(N, 64);
+  k_dense<<<nb, 256, 0, s>>>(N, g.X0, kNin, kNin, nullptr, 0, 0, W + g.off[kPW0], 64, 0, 0, W + g.off[kPb0], 64, g.Z0,
+                             64, nullptr, g.H, 1, 0);
   ++L;
   for (int l = 0; l < 3; ++l) {
     const float* h = g.H + int64_t(l) * N * 64;
     float* a = g.Aa + int64_t(l) * N * 64;
     float* M = g.M + int64_t(l) * N * 64;
-    k_dense<<<nb, 128, 0, s>>>(N, h, 64, nullptr, 0, W + g.off[kPWa + 5 * l], nullptr, 64, a, 64, nullptr, nullptr, 0);
+    k_dense<<<nb, 256, 0, s>>>(N, h, 64, 64, nullptr, 0, 0, W + g.off[kPWa + 5 * l], 64, 0, 0, nullptr, 64, a, 64,
+                               nullptr, nullptr, 0, 0);
     k_gnn_edge_fwd<<<cdiv(32 * N, kT), kT, 0, s>>>(g, a, W + g.off[kPWe + 5 * l], W + g.off[kPbm + 5 * l], M);
-    k_dense<<<nb, 128, 0, s>>>(N, h, 64, M, 64, W + g.off[kPWu + 5 * l], W + g.off[kPbu + 5 * l], 64,
-                               g.ZU + int64_t(l) * N * 64, 64, h, g.H + int64_t(l + 1) * N * 64, 2);
+    k_dense<<<nb, 256, 0, s>>>(N, h, 64, 64, M, 64, 64, W + g.off[kPWu + 5 * l], 64, 0, 0, W + g.off[kPbu + 5 * l], 64,
+                               g.ZU + int64_t(l) * N * 64, 64, h, g.H + int64_t(l + 1) * N * 64, 2, 0);
     L += 3;
   }
-  k_dense<<<nb, 128, 0, s>>>(N, g.H + 3 * N * 64, 64, nullptr, 0, W + g.off[kPWd], W + g.off[kPbd], kNout, g.OUT, 16,
-                             nullptr, nullptr, 0);
+  k_dense<<<nb, 256, 0, s>>>(N, g.H + 3 * N * 64, 64, 64, nullptr, 0, 0, W + g.off[kPWd], kNout, 0, 0, W + g.off[kPbd],
+                             kNout, g.OUT, 16, nullptr, nullptr, 0, 0);
   return L + 1;
 }
 
@@ -649,7 +692,7 @@ int gnn_backward_pair(const GnnDev& g, const DevMesh& m, const double* target, c
   const __nv_bfloat16* W = g.w16;
   const int64_t N = g.N;
   const int64_t st = g.part_stride;
-  const unsigned nb = cdiv(N, 128);
+  const unsigned nb = cdiv(N, 64);
   const unsigned wg = pgrid(cdiv(N, kWgRows)), eg = pgrid(cdiv(32 * N, kT));
   int L = 0;
   k_gnn_err<<<cdiv(N, kT), kT, 0, s>>>(g, target);
@@ -659,7 +702,8 @@ int gnn_backward_pair(const GnnDev& g, const DevMesh& m, const double* target, c
   // decoder
   k_dense_wgrad<<<wg, kT, 0, s>>>(N, g.H + 3 * N * 64, 64, nullptr, 0, g.dOUT, 16, kNout, g.gpart, st);
   k_reduce_parts<<<cdiv(65 * kNout, kT), kT, 0, s>>>(g.gpart, st, int(wg), 65 * kNout, g.grad + g.off[kPWd]);
-  k_dense_bwd_x<<<nb, 128, 0, s>>>(N, g.dOUT, 16, kNout, W + g.off[kPWd], 0, g.dH, 0);
+  k_dense<<<nb, 256, 0, s>>>(N, g.dOUT, kNout, 16, nullptr, 0, 0, W + g.off[kPWd], kNout, 0, 1, nullptr, 64, g.dH, 64,
+                             nullptr, nullptr, 0, 0);
   L += 5;
   for (int l = 2; l >= 0; --l) {
     const float* h = g.H + int64_t(l) * N * 64;
@@ -669,13 +713,16 @@ int gnn_backward_pair(const GnnDev& g, const DevMesh& m, const double* target, c
     k_dense_wgrad<<<wg, kT, 0, s>>>(N, h, 64, M, 64, g.dZ, 64, 64, g.gpart, st);
     k_reduce_parts<<<cdiv(129 * 64, kT), kT, 0, s>>>(g.gpart, st, int(wg), 129 * 64, g.grad + g.off[kPWu + 5 * l]);
     // dM = dZU Wu[64:128]^T (the 1/deg factor is applied per edge); the residual keeps dH
-    k_dense_bwd_x<<<nb, 128, 0, s>>>(N, g.dZ, 64, 64, W + g.off[kPWu + 5 * l], 64, g.dM, 0);
-    k_dense_bwd_x<<<nb, 128, 0, s>>>(N, g.dZ, 64, 64, W + g.off[kPWu + 5 * l], 0, g.dH, 1);
+    k_dense<<<nb, 256, 0, s>>>(N, g.dZ, 64, 64, nullptr, 0, 0, W + g.off[kPWu + 5 * l], 64, 64, 1, nullptr, 64, g.dM,
+                               64, nullptr, nullptr, 0, 0);
+    k_dense<<<nb, 256, 0, s>>>(N, g.dZ, 64, 64, nullptr, 0, 0, W + g.off[kPWu + 5 * l], 64, 0, 1, nullptr, 64, g.dH, 64,
+                               nullptr, nullptr, 0, 1);
     k_gnn_edge_bwd<<<eg, kT, 0, s>>>(g, a, W + g.off[kPWe + 5 * l], W + g.off[kPbm + 5 * l], g.dM, g.dA, g.gpart, st);
     k_reduce_parts<<<cdiv((kEin + 1) * 64, kT), kT, 0, s>>>(g.gpart, st, int(eg), (kEin + 1) * 64, g.grad + g.off[kPWe + 5 * l]);
     k_dense_wgrad<<<wg, kT, 0, s>>>(N, h, 64, nullptr, 0, g.dA, 64, 64, g.gpart, st);
     k_reduce_parts<<<cdiv(64 * 64, kT), kT, 0, s>>>(g.gpart, st, int(wg), 64 * 64, g.grad + g.off[kPWa + 5 * l]);
-    k_dense_bwd_x<<<nb, 128, 0, s>>>(N, g.dA, 64, 64, W + g.off[kPWa + 5 * l], 0, g.dH, 1);
+    k_dense<<<nb, 256, 0, s>>>(N, g.dA, 64, 64, nullptr, 0, 0, W + g.off[kPWa + 5 * l], 64, 0, 1, nullptr, 64, g.dH, 64,
+                               nullptr, nullptr, 0, 1);
     L += 10;
   }
   k_relu_mask<<<cdiv(N * 64, kT), kT, 0, s>>>(N * 64, g.Z0, g.dH, g.dZ);
