@@ -79,9 +79,26 @@ MIXED_BYTES = {
     "m:tet_stress": lambda i: i["n_tets"] * (16 + 72 + 4 + 24 + 24) + 12 * i["n_nodes"],
     "m:nonlocal_avg": lambda i: 8.0 * i["n_nbr_pairs"] + i["n_tets"] * (24 + 24),
     "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
-    "m:assemble": lambda i: i["n_tets"] * (16 + 120 + 4 + 16 + 32) + i["n_blocks"] * 36 + i["n_nodes"] * (24 + 36 + 24 + 8),
+    # phase 1: tet, rest row (128 B), chi in; ten 3x3 blocks + four rhs shares out (416 B); u, v per node
+    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 416) + i["n_nodes"] * 24,
+    # phase 2: every element entry once (16 blocks + 4 rhs shares per tet) and its list index, out A, b, D^-1
+    "m:assemble_gather": lambda i: i["n_tets"] * (16 * 9 * 4 + 4 * 3 * 4 + 16 * 4 + 4 * 4)
+                                   + i["n_blocks"] * (36 + 4) + i["n_nodes"] * (12 + 36 + 24),
     "m:pcg_spmv": lambda i: i["n_blocks"] * 40 + i["n_nodes"] * (4 + 12 + 12 + 12),
 }
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# loaf kernels, from one ncu --set full capture of the current kernels each
+# (``bench.py --profile-step --precision fp64|mixed --steps 2``).
+NCU_TRAFFIC = {
+    "nonlocal_avg": 1.291858e9 + 28.97152e6,
+    "assemble": 0.284699e9 + 582.927872e6,
+    "m:nonlocal_avg": 814.254848e6 + 21.138688e6,
+    "m:assemble_gather": 318.089216e6 + 54.717696e6,
+}
+# Executed FP64 flops per tet of the element-block kernel (ncu: 2 DFMA + DADD +
+# DMUL thread instructions per launch / tets): the tangent has no short closed count.
+ELEM64_FLOPS_PER_TET = 1405.0
 
 
 def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, traffic=None):
@@ -95,8 +112,14 @@ def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, tra
                 "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
                 "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
     if group == "assemble":
-        # per launch = all colours of one assembly; FP64 operations counted in the kernel source per tet
-        flops = 2.0 * 1000.0 * T
+        # phase 1: element blocks and rhs shares, executed FP64 flops per tet
+        flops = ELEM64_FLOPS_PER_TET * T
+        return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
+                "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
+    if group == "assemble_gather":
+        # phase 2: one FP64 add per element contribution (16 blocks x 9 + 4 rhs shares x 3 per tet)
+        flops = 156.0 * T
         return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
                 "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
@@ -354,10 +377,11 @@ def run_ours(args) -> None:
         return
     dom = max(prof, key=lambda k: prof[k][0])
     pk = peaks()
-    traffic = None
-    roof = roofline_for(dom, prof[dom][0], prof[dom][1], info, pk, traffic)
-    mdom = max(("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "pcg_spmv"), key=lambda k: mix_prof[k][0])
-    mix_roof = roofline_for("m:" + mdom, mix_prof[mdom][0], mix_prof[mdom][1], info, pk, None)
+    roof = roofline_for(dom, prof[dom][0], prof[dom][1], info, pk, NCU_TRAFFIC.get(dom))
+    mdom = max(("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "assemble_gather", "pcg_spmv"),
+               key=lambda k: mix_prof[k][0])
+    mix_roof = roofline_for("m:" + mdom, mix_prof[mdom][0], mix_prof[mdom][1], info, pk,
+                            NCU_TRAFFIC.get("m:" + mdom))
     cpu = None if args.no_cpu_baseline else cpu_baseline_entry(3, w.n_tets)
     out = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

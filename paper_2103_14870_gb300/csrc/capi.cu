@@ -78,12 +78,12 @@ namespace {
 
 enum ProfGroup : int {
   kPStress = 0, kPNonlocal, kPEdge, kPChi, kPAssemble, kPPcgInit, kPSpmv, kPPcgUpdate, kPPcgP, kPResidual,
-  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPGnn, kPCount
+  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPGnn, kPGather, kPCount
 };
 const char* kProfNames[kPCount] = {"tet_stress",  "nonlocal_avg", "edge_driver", "tet_chi",     "assemble",
                                    "pcg_init",    "pcg_spmv",     "pcg_update",  "pcg_p",       "true_residual",
                                    "integrate",   "ir_residual",  "ir_inner_init", "ir_apply",
-                                   "gnn"};
+                                   "gnn",         "assemble_gather"};
 
 __global__ void k_fill(double* p, int64_t n, double v) {
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -691,8 +691,11 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
       for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble_colour(d, mt, dt, cp[c], cp[c + 1], s);
     } else {
       L += launch_kind(kB_elem64, d, mt, sp, s);
-      L += launch_kind(kB_gather64, d, mt, sp, s);
     }
+  }
+  if (m->tune.assembly != GF_ASSEMBLY_COLOUR) {
+    Prof p(m, kPGather);
+    L += launch_kind(kB_gather64, d, mt, sp, s);
   }
   PcgState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
@@ -750,8 +753,8 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
     Prof p(m, kPAssemble);
     L += launch_kind(kB_elem32, d, mt, sp, s);
     L += launch_kind(kB_fext32, d, mt, sp, s);
-    L += launch_kind(kB_gather32, d, mt, sp, s);
   }
+  { Prof p(m, kPGather); L += launch_kind(kB_gather32, d, mt, sp, s); }
   IrState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
   init.in_tol2 = m->in_rtol * m->in_rtol;
