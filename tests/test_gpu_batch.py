@@ -128,3 +128,40 @@ def test_autotune_keeps_state_and_picks_a_schedule():
         r.step(1e-3, w.f_ext.ravel(), w.pinned)
         np.testing.assert_array_equal(m.positions_get(), r.positions_get())
     batch.close()
+
+
+def test_bench_batch_configuration_members_match_singles_and_oracle():
+    """The batch bench.py times (64 boxes of 2k-80k tets, mixed, CUDA graph):
+    after two steps every member is bit-identical to the same mesh stepped
+    alone, and the two smallest members match the FP64 oracle at the FP32
+    tolerance (1e-5 norm-wise)."""
+    from workloads import batch_configs
+    ws = batch_configs()
+
+    def mesh(w):
+        mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius)
+        return gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=1e-6)
+
+    ms = [mesh(w) for w in ws]
+    batch = gf.Batch(ms)
+    assert batch.tuning_get()["graph"] == 1
+    for _ in range(2):
+        stats = batch.step(ws[0].dt, [w.f_ext.ravel() for w in ws], [w.pinned for w in ws])
+        assert all(s["status"] == 0 and s["rel_res"] <= 1e-6 for s in stats)
+    for k, w in enumerate(ws):
+        single = mesh(w)
+        for _ in range(2):
+            single.step(w.dt, w.f_ext.ravel(), w.pinned)
+        np.testing.assert_array_equal(ms[k].positions_get(), single.positions_get())
+        np.testing.assert_array_equal(ms[k].velocities_get(), single.velocities_get())
+        np.testing.assert_array_equal(ms[k].damage_get()[1], single.damage_get()[1])
+        single.close()
+    for k in np.argsort([w.n_tets for w in ws])[:2]:
+        w = ws[k]
+        model = oracle_model(w)
+        st = model.rest_state()
+        for _ in range(2):
+            st, info = model.step(st, w.dt, w.f_ext, w.pinned)
+        np.testing.assert_array_equal(ms[k].damage_get()[1], info["labels"])
+        assert_norm_close(ms[k].velocities_get(), st.v, rtol=1e-5, what=f"batch member {k} v (mixed)")
+    batch.close()

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from helpers import LABEL_BAND, assert_close
+from helpers import LABEL_BAND, assert_close, assert_norm_close
 from oracle import damage, elastic, mesh as omesh
 from workloads import loaf_config
 
@@ -74,7 +74,20 @@ def oracle_region_state(w, x, labels, edges, tet_edges, centres, lam, mu, radius
     return dict(T_s=T_s, E_s=E_s, driver=drv, need=need, pos=pos, sigf=sigf)
 
 
-def test_loaf_fullsize_sampled_parity(loaf):
+# per precision: element-wise rtol, floor (of the sampled array's scale), label band
+TOL = {"fp64": dict(rtol=1e-9, floor_drv=0.0, abs_drv=1e-13, floor_chi=1e-12, floor_A=1e-12, floor_b=1e-9,
+                    band=LABEL_BAND),
+       "mixed": dict(rtol=1e-5, floor_drv=1e-6, abs_drv=0.0, floor_chi=1e-6, band=1e-5)}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_loaf_fullsize_sampled_parity(loaf, precision):
+    """Both forms bench.py times, on the full loaf.  FP64: element-wise 1e-9.
+    Mixed: the FP32 tolerance 1e-5 (label band 1e-5), norm-wise for the sampled
+    matrix rows and rhs: FP32 strains from displacement differences carry ~1e-6
+    relative error, and the edge-space sums forming a nodal force amplify it
+    about tenfold on single entries."""
+    tol = TOL[precision]
     w, x, v, edges, tet_edges, labels0 = loaf
     lam, mu = elastic.lame(w.young, w.poisson)
     rng = np.random.default_rng(7)
@@ -83,17 +96,20 @@ def test_loaf_fullsize_sampled_parity(loaf):
     E_s, T_s = reg["E_s"], reg["T_s"]
     theta = float(np.quantile(reg["driver"][E_s], 0.9))
     m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=theta,
-                                                    radius=w.radius), cg_rtol=1e-6)
+                                                    radius=w.radius), cg_rtol=1e-6,
+                       precision=gf.MIXED if precision == "mixed" else gf.FP64)
     np.testing.assert_array_equal(m.edges_get(), edges)
     m.state_set(x=x.ravel(), v=v.ravel(), labels=labels0)
     f = w.f_ext
     stats = m.step(w.dt, f.ravel())
+    assert stats["status"] == 0
     drv, lab = m.damage_get()
     # (1) drivers and labels of the sampled edges
-    assert_close(drv[E_s], reg["driver"][E_s], floor=0.0, abs_floor=1e-13, what="driver")
+    assert_close(drv[E_s], reg["driver"][E_s], rtol=tol["rtol"], floor=tol["floor_drv"], abs_floor=tol["abs_drv"],
+                 what="driver")
     want_lab = labels0 | (reg["driver"] >= theta)
     diff = E_s[lab[E_s] != want_lab[E_s]]
-    assert np.all(np.abs(reg["driver"][diff] - theta) <= LABEL_BAND * theta)
+    assert np.all(np.abs(reg["driver"][diff] - theta) <= tol["band"] * theta)
     assert lab[E_s].sum() > 0
     # labels never heal anywhere
     assert np.all(lab >= labels0)
@@ -103,7 +119,10 @@ def test_loaf_fullsize_sampled_parity(loaf):
     sigf_s = reg["sigf"][[reg["pos"][t] for t in T_s]]
     chi_s = damage.chi(new_lab, tet_edges[T_s], sigf_s, w.young)
     chi_gpu = m.chi_get()
-    assert_close(chi_gpu[T_s], chi_s, floor=1e-12, what="chi")
+    # labels inside the band may differ; chi and the system then differ too, so
+    # those checks need identical labels on the sample (they are, at these seeds)
+    assert np.array_equal(lab[E_s], new_lab[E_s])
+    assert_close(chi_gpu[T_s], chi_s, rtol=tol["rtol"], floor=tol["floor_chi"], what="chi")
     assert (chi_s < 1).any()
     # (3) matrix rows and rhs of nodes whose incident tets all lie in T_s
     tets = w.tets.astype(np.int64)
@@ -119,6 +138,7 @@ def test_loaf_fullsize_sampled_parity(loaf):
     mass = omesh.lumped_mass(w.nodes, tets, w.density, omesh.rest_geometry(w.nodes, tets)[0])
     dt = w.dt
     rp, col, val, rhs = m.system_get()
+    got_b, want_bs = [], []
     for n in N_s:
         want_row = {}
         want_b = dt * (f[n] - 0.0 * v[n])
@@ -138,8 +158,16 @@ def test_loaf_fullsize_sampled_parity(loaf):
         assert sorted(want_row) == list(cols)
         got = val[rp[n]:rp[n + 1]]
         want = np.stack([want_row[c] for c in cols])
-        assert_close(got, want, floor=1e-12, what=f"A row {n}")
-        assert_close(rhs[3 * n:3 * n + 3], want_b, floor=1e-9, what=f"rhs row {n}")
+        if precision == "fp64":
+            assert_close(got, want, rtol=tol["rtol"], floor=tol["floor_A"], what=f"A row {n}")
+        else:
+            assert_norm_close(got, want, rtol=tol["rtol"], what=f"A row {n} (mixed)")
+        got_b.append(rhs[3 * n:3 * n + 3])
+        want_bs.append(want_b)
+    if precision == "fp64":
+        assert_close(np.array(got_b), np.array(want_bs), rtol=tol["rtol"], floor=tol["floor_b"], what="rhs rows")
+    else:
+        assert_norm_close(np.array(got_b), np.array(want_bs), rtol=tol["rtol"], what="rhs rows (mixed)")
     # (4) the solve: residual recomputed on the host from the GPU's own system
     rows = np.repeat(np.arange(w.n_nodes), np.diff(rp))
     r3 = (3 * rows[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
