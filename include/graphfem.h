@@ -356,6 +356,17 @@ gf_status gf_gnn_pair_get(gf_gnn* gnn, double* b, double* target);
 enum { GF_GNN_START = 1, GF_GNN_PRECOND = 2 };
 gf_status gf_gnn_attach(gf_mesh* mesh, gf_gnn* gnn, int32_t flags);
 
+/* Kernels of the network's dense contractions (the eight node-wise dense
+ * layers, the per-edge message layer We e_ij of each message-passing layer and
+ * the input gradients of the backward pass).  GF_GNN_TENSOR_CORES (default):
+ * tcgen05 MMAs with the FP32 activations split into three bf16 parts (exact
+ * products, FP32 accumulation, so FP32-accurate); GF_GNN_FP32_FMA: FP32 FMA
+ * kernels.  Both give the same results up to FP32 rounding order.  A device
+ * wait of the tensor-core kernels that gives up (after one second) makes the
+ * call (or gf_step) return GF_TIMEOUT. */
+enum { GF_GNN_TENSOR_CORES = 0, GF_GNN_FP32_FMA = 1 };
+gf_status gf_gnn_kernels_set(gf_gnn* gnn, int32_t kernels);
+
 const char* gf_status_string(gf_status s);
 const char* gf_last_error(void);
 

@@ -861,7 +861,11 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
     rel = ps.bb > 0 ? std::sqrt(ps.true_rr / ps.bb) : 0.0;
   }
   if (status == GF_OK && !std::isfinite(rel)) status = GF_NAN;
-  if (m->h_cnt[3] != 0) {
+  if (status == GF_OK && m->h_cnt[kCntTcTimeout] != 0) {
+    set_last_error("a tensor-core wait of the network gave up (device timeout)");
+    status = GF_TIMEOUT;
+  }
+  if (m->h_cnt[kCntBadPin] != 0) {
     set_last_error("pinned node id out of range (skipped)");
     status = GF_BAD_ARG;
   }
@@ -1608,6 +1612,19 @@ cudaError_t gnn_keep_previous(gf_gnn* g, const DevMesh& d, cudaStream_t s) {
   return cudaMemcpyAsync(g->g.xprev, d.dv, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, s);
 }
 
+// the mesh counter of tensor-core waits that gave up: cleared before a network
+// call, read after it (the stream is synchronised by the caller)
+cudaError_t gnn_tc_clear(gf_gnn* g) { return cudaMemsetAsync(g->g.err, 0, sizeof(unsigned long long), g->mesh->stream); }
+gf_status gnn_tc_status(gf_gnn* g) {
+  unsigned long long n = 0;
+  GF_CK(cudaMemcpy(&n, g->g.err, sizeof(n), cudaMemcpyDeviceToHost));
+  if (n != 0) {
+    set_last_error("a tensor-core wait of the network gave up (device timeout)");
+    return GF_TIMEOUT;
+  }
+  return GF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1681,12 +1698,30 @@ gf_status gf_gnn_create(gf_mesh* mesh, gf_gnn** out) {
     nstat[2 * i + 1] = float(rp[i + 1] - rp[i]) / 16.f;
   }
 
+  // edge-message tiles of the tensor-core kernel: runs of whole destination
+  // nodes with at most kEdgeTileRows messages and nodes each (none when a node
+  // alone has more messages: the FP32 kernel then serves every layer)
+  // (each tile: first node, node count, first message, message count)
+  std::vector<int32_t> etile;
+  for (int64_t i = 0; i < N;) {
+    int64_t j = i;
+    while (j < N && j - i < kEdgeTileRows && rp[j + 1] - rp[i] <= kEdgeTileRows) ++j;
+    if (j == i) {
+      etile.clear();
+      break;
+    }
+    etile.insert(etile.end(), {int32_t(i), int32_t(j - i), rp[i], rp[j] - rp[i]});
+    i = j;
+  }
+
   gf_gnn* g = new gf_gnn();
   g->mesh = mesh;
   g->device = mesh->device;
   GnnDev& G = g->g;
   G.N = N;
   G.E = E;
+  G.n_etiles = int64_t(etile.size()) / 4;
+  G.err = mesh->dm.counters + kCntTcTimeout;
   G.P = gnn_param_offsets(G.off);
   auto fail = [&](gf_status st) {
     cudaStreamSynchronize(s);
@@ -1707,6 +1742,7 @@ gf_status gf_gnn_create(gf_mesh* mesh, gf_gnn** out) {
   GNN_TRY(gnn_upload(g, tpos, &G.tpos, s));
   GNN_TRY(gnn_upload(g, relpos, &G.relpos, s));
   GNN_TRY(gnn_upload(g, nstat, &G.nstat, s));
+  GNN_TRY(gnn_upload(g, etile, reinterpret_cast<const int32_t**>(&G.etile), s));
   const size_t NH = size_t(N) * kHid;
   GNN_TRY(gnn_alloc(g, size_t(E) * kEin, &G.efeat));
   GNN_TRY(gnn_alloc(g, size_t(N), &G.T));
@@ -1823,6 +1859,7 @@ gf_status gf_gnn_forward(gf_gnn* g, const double* b, int32_t mem, float* out, fl
   const GnnDev& G = g->g;
   const double* bd = nullptr;
   if ((st = gnn_stage(g, b, mem, g->stage_b, &bd)) != GF_OK) return st;
+  GF_CK(gnn_tc_clear(g));
   int64_t L = gnn_forward(G, g->mesh->dm, bd, s);
   L += gnn_apply_export(G, s);
   g->mesh->launches += L;
@@ -1838,6 +1875,7 @@ gf_status gf_gnn_forward(gf_gnn* g, const double* b, int32_t mem, float* out, fl
   if (edge_in && G.E > 0)
     GF_CK(cudaMemcpyAsync(edge_in, G.efeat, sizeof(float) * kEin * G.E, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
+  if ((st = gnn_tc_status(g)) != GF_OK) return st;
   if (out)
     for (int64_t i = 0; i < G.N; ++i)
       for (int k = 0; k < kNout; ++k) out[kNout * i + k] = o16[16 * i + k];
@@ -1860,6 +1898,7 @@ gf_status gf_gnn_loss_grad(gf_gnn* g, const double* b, const double* target, int
   if ((st = gnn_stage(g, target, mem, g->stage_t, &td)) != GF_OK) return st;
   GF_CK(cudaMemsetAsync(G.grad, 0, sizeof(float) * G.P, s));
   GF_CK(cudaMemsetAsync(G.loss, 0, sizeof(double), s));
+  GF_CK(gnn_tc_clear(g));
   int64_t L = gnn_forward(G, g->mesh->dm, bd, s);
   L += gnn_backward_pair(G, g->mesh->dm, td, s);
   g->mesh->launches += L;
@@ -1868,6 +1907,7 @@ gf_status gf_gnn_loss_grad(gf_gnn* g, const double* b, const double* target, int
   GF_CK(cudaMemcpyAsync(&h_loss, G.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (grad) GF_CK(cudaMemcpyAsync(grad, G.grad, sizeof(float) * G.P, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
+  if ((st = gnn_tc_status(g)) != GF_OK) return st;
   if (loss) *loss = h_loss;
   return GF_OK;
 }
@@ -1884,6 +1924,7 @@ gf_status gf_gnn_train(gf_gnn* g, int32_t iters, float lr, double* loss_first, d
   const DevMesh& d = g->mesh->dm;
   int64_t L = gnn_pair(d, g->g.xprev, g->stage_b, g->stage_t, s);
   GF_CK(cudaMemsetAsync(g->loss_hist, 0, sizeof(double) * iters, s));
+  GF_CK(gnn_tc_clear(g));
   for (int k = 0; k < iters; ++k) {
     GnnDev G = g->g;
     G.loss = g->loss_hist + k;
@@ -1898,6 +1939,7 @@ gf_status gf_gnn_train(gf_gnn* g, int32_t iters, float lr, double* loss_first, d
   GF_CK(cudaMemcpyAsync(&h[0], g->loss_hist, sizeof(double), cudaMemcpyDeviceToHost, s));
   GF_CK(cudaMemcpyAsync(&h[1], g->loss_hist + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
+  if ((st = gnn_tc_status(g)) != GF_OK) return st;
   if (loss_first) *loss_first = h[0];
   if (loss_last) *loss_last = h[1];
   return GF_OK;
@@ -1917,6 +1959,15 @@ gf_status gf_gnn_pair_get(gf_gnn* g, double* b, double* target) {
   GF_CK(cudaMemcpyAsync(b, g->stage_b, sizeof(double) * 3 * g->g.N, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaMemcpyAsync(target, g->stage_t, sizeof(double) * 3 * g->g.N, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
+  return GF_OK;
+}
+
+gf_status gf_gnn_kernels_set(gf_gnn* g, int32_t kernels) {
+  if (!g || (kernels != GF_GNN_TENSOR_CORES && kernels != GF_GNN_FP32_FMA)) {
+    set_last_error("kernels_set: need the network and GF_GNN_TENSOR_CORES or GF_GNN_FP32_FMA");
+    return GF_BAD_ARG;
+  }
+  g->g.use_tc = kernels == GF_GNN_TENSOR_CORES ? 1 : 0;
   return GF_OK;
 }
 

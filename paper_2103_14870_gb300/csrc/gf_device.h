@@ -19,7 +19,8 @@ struct PcgState {
   int32_t iters, maxit, done, status;
 };
 
-enum Counter : int { kCntBroken = 0, kCntNewBroken = 1, kCntChiZero = 2, kCntMax = 4 };
+// counters[3] flags an out-of-range pinned id, counters[4] a tensor-core wait that gave up
+enum Counter : int { kCntBroken = 0, kCntNewBroken = 1, kCntChiZero = 2, kCntBadPin = 3, kCntTcTimeout = 4, kCntMax = 8 };
 
 // Scalars of the mixed-precision solve: FP64 iterative refinement (outer)
 // around an FP32 PCG (inner) whose dot products accumulate in FP64.

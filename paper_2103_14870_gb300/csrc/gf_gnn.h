@@ -65,7 +65,21 @@ struct GnnDev {
   double* loss = nullptr;               // [1]
   double* red = nullptr;                // reduction partials
   unsigned* ticket = nullptr;           // [4]
+  // tensor-core path
+  int use_tc = 1;                       // 1: tcgen05 dense layers and edge messages, 0: FP32 FMA kernels
+  int64_t n_etiles = 0;                 // edge-message tiles: whole destination nodes, <= 128 messages and nodes
+  const int4* etile = nullptr;          // [n_etiles] (first node, nodes, first message, messages)
+  unsigned long long* err = nullptr;    // the mesh's counter of tensor-core waits that gave up
 };
+
+// tcgen05 kernels (kernels_tc.cu); each returns the launches issued, or -1 when
+// the shape has no tensor-core form
+int dense_tc(int64_t N, const float* X1, int K1, int ld1, const float* X2, int K2, int ld2, const __nv_bfloat16* W,
+             int ldw, int k0, int trans, const __nv_bfloat16* bias, int NO, float* Z, int ldz, const float* Hres,
+             float* Hout, int mode, int accumulate, unsigned long long* err, cudaStream_t s);
+int gnn_edge_fwd_tc(const GnnDev& g, const float* a, const __nv_bfloat16* We, const __nv_bfloat16* bm, float* M,
+                    cudaStream_t s);
+constexpr int kEdgeTileRows = 128;
 
 // forward pass on system A (m.val), right-hand side b (FP64, device); returns launches
 int gnn_forward(const GnnDev& g, const DevMesh& m, const double* b, cudaStream_t s);

@@ -643,6 +643,32 @@ inline unsigned rgrid(int64_t n) {
 }
 inline unsigned pgrid(int64_t units) { return unsigned(units < 1 ? 1 : (units > kMaxParts ? kMaxParts : units)); }
 
+// Dense layer: the tcgen05 kernel when the network uses tensor cores and the
+// shape has a tensor-core form, else the FP32 FMA kernel (same arguments).
+int dense(const GnnDev& g, int64_t N, const float* X1, int K1, int ld1, const float* X2, int K2, int ld2,
+          const __nv_bfloat16* W, int ldw, int k0, int trans, const __nv_bfloat16* bias, int NO, float* Z, int ldz,
+          const float* Hres, float* Hout, int mode, int accumulate, cudaStream_t s) {
+  if (g.use_tc) {
+    const int L = dense_tc(N, X1, K1, ld1, X2, K2, ld2, W, ldw, k0, trans, bias, NO, Z, ldz, Hres, Hout, mode,
+                           accumulate, g.err, s);
+    if (L >= 0) return L;
+  }
+  if (N <= 0) return 0;
+  k_dense<<<cdiv(N, kDT), 256, 0, s>>>(N, X1, K1, ld1, X2, K2, ld2, W, ldw, k0, trans, bias, NO, Z, ldz, Hres, Hout,
+                                      mode, accumulate);
+  return 1;
+}
+
+int edge_fwd(const GnnDev& g, const float* a, const __nv_bfloat16* We, const __nv_bfloat16* bm, float* M,
+             cudaStream_t s) {
+  if (g.use_tc) {
+    const int L = gnn_edge_fwd_tc(g, a, We, bm, M, s);
+    if (L >= 0) return L;
+  }
+  k_gnn_edge_fwd<<<cdiv(32 * g.N, kT), kT, 0, s>>>(g, a, We, bm, M);
+  return 1;
+}
+
 }  // namespace
 
 int gnn_max_parts() { return kMaxParts; }
@@ -658,24 +684,21 @@ int gnn_forward(const GnnDev& g, const DevMesh& m, const double* b, cudaStream_t
     k_gnn_edgefeat<<<cdiv(g.E, kT), kT, 0, s>>>(g, m);
     ++L;
   }
-  const unsigned nb = cdiv(N, 64);
-  k_dense<<<nb, 256, 0, s>>>(N, g.X0, kNin, kNin, nullptr, 0, 0, W + g.off[kPW0], 64, 0, 0, W + g.off[kPb0], 64, g.Z0,
-                             64, nullptr, g.H, 1, 0);
-  ++L;
+  L += dense(g, N, g.X0, kNin, kNin, nullptr, 0, 0, W + g.off[kPW0], 64, 0, 0, W + g.off[kPb0], 64, g.Z0, 64, nullptr,
+             g.H, 1, 0, s);
   for (int l = 0; l < 3; ++l) {
     const float* h = g.H + int64_t(l) * N * 64;
     float* a = g.Aa + int64_t(l) * N * 64;
     float* M = g.M + int64_t(l) * N * 64;
-    k_dense<<<nb, 256, 0, s>>>(N, h, 64, 64, nullptr, 0, 0, W + g.off[kPWa + 5 * l], 64, 0, 0, nullptr, 64, a, 64,
-                               nullptr, nullptr, 0, 0);
-    k_gnn_edge_fwd<<<cdiv(32 * N, kT), kT, 0, s>>>(g, a, W + g.off[kPWe + 5 * l], W + g.off[kPbm + 5 * l], M);
-    k_dense<<<nb, 256, 0, s>>>(N, h, 64, 64, M, 64, 64, W + g.off[kPWu + 5 * l], 64, 0, 0, W + g.off[kPbu + 5 * l], 64,
-                               g.ZU + int64_t(l) * N * 64, 64, h, g.H + int64_t(l + 1) * N * 64, 2, 0);
-    L += 3;
+    L += dense(g, N, h, 64, 64, nullptr, 0, 0, W + g.off[kPWa + 5 * l], 64, 0, 0, nullptr, 64, a, 64, nullptr, nullptr,
+               0, 0, s);
+    L += edge_fwd(g, a, W + g.off[kPWe + 5 * l], W + g.off[kPbm + 5 * l], M, s);
+    L += dense(g, N, h, 64, 64, M, 64, 64, W + g.off[kPWu + 5 * l], 64, 0, 0, W + g.off[kPbu + 5 * l], 64,
+               g.ZU + int64_t(l) * N * 64, 64, h, g.H + int64_t(l + 1) * N * 64, 2, 0, s);
   }
-  k_dense<<<nb, 256, 0, s>>>(N, g.H + 3 * N * 64, 64, 64, nullptr, 0, 0, W + g.off[kPWd], kNout, 0, 0, W + g.off[kPbd],
-                             kNout, g.OUT, 16, nullptr, nullptr, 0, 0);
-  return L + 1;
+  L += dense(g, N, g.H + 3 * N * 64, 64, 64, nullptr, 0, 0, W + g.off[kPWd], kNout, 0, 0, W + g.off[kPbd], kNout,
+             g.OUT, 16, nullptr, nullptr, 0, 0, s);
+  return L;
 }
 
 int gnn_apply_inference(const GnnDev& g, const DevMesh& m, int flags, cudaStream_t s) {
@@ -692,7 +715,6 @@ int gnn_backward_pair(const GnnDev& g, const DevMesh& m, const double* target, c
   const __nv_bfloat16* W = g.w16;
   const int64_t N = g.N;
   const int64_t st = g.part_stride;
-  const unsigned nb = cdiv(N, 64);
   const unsigned wg = pgrid(cdiv(N, kWgRows)), eg = pgrid(cdiv(32 * N, kT));
   int L = 0;
   k_gnn_err<<<cdiv(N, kT), kT, 0, s>>>(g, target);
@@ -702,9 +724,8 @@ int gnn_backward_pair(const GnnDev& g, const DevMesh& m, const double* target, c
   // decoder
   k_dense_wgrad<<<wg, kT, 0, s>>>(N, g.H + 3 * N * 64, 64, nullptr, 0, g.dOUT, 16, kNout, g.gpart, st);
   k_reduce_parts<<<cdiv(65 * kNout, kT), kT, 0, s>>>(g.gpart, st, int(wg), 65 * kNout, g.grad + g.off[kPWd]);
-  k_dense<<<nb, 256, 0, s>>>(N, g.dOUT, kNout, 16, nullptr, 0, 0, W + g.off[kPWd], kNout, 0, 1, nullptr, 64, g.dH, 64,
-                             nullptr, nullptr, 0, 0);
-  L += 5;
+  L += 4 + dense(g, N, g.dOUT, kNout, 16, nullptr, 0, 0, W + g.off[kPWd], kNout, 0, 1, nullptr, 64, g.dH, 64, nullptr,
+                 nullptr, 0, 0, s);
   for (int l = 2; l >= 0; --l) {
     const float* h = g.H + int64_t(l) * N * 64;
     const float* a = g.Aa + int64_t(l) * N * 64;
@@ -713,17 +734,17 @@ int gnn_backward_pair(const GnnDev& g, const DevMesh& m, const double* target, c
     k_dense_wgrad<<<wg, kT, 0, s>>>(N, h, 64, M, 64, g.dZ, 64, 64, g.gpart, st);
     k_reduce_parts<<<cdiv(129 * 64, kT), kT, 0, s>>>(g.gpart, st, int(wg), 129 * 64, g.grad + g.off[kPWu + 5 * l]);
     // dM = dZU Wu[64:128]^T (the 1/deg factor is applied per edge); the residual keeps dH
-    k_dense<<<nb, 256, 0, s>>>(N, g.dZ, 64, 64, nullptr, 0, 0, W + g.off[kPWu + 5 * l], 64, 64, 1, nullptr, 64, g.dM,
-                               64, nullptr, nullptr, 0, 0);
-    k_dense<<<nb, 256, 0, s>>>(N, g.dZ, 64, 64, nullptr, 0, 0, W + g.off[kPWu + 5 * l], 64, 0, 1, nullptr, 64, g.dH, 64,
-                               nullptr, nullptr, 0, 1);
+    L += dense(g, N, g.dZ, 64, 64, nullptr, 0, 0, W + g.off[kPWu + 5 * l], 64, 64, 1, nullptr, 64, g.dM, 64, nullptr,
+               nullptr, 0, 0, s);
+    L += dense(g, N, g.dZ, 64, 64, nullptr, 0, 0, W + g.off[kPWu + 5 * l], 64, 0, 1, nullptr, 64, g.dH, 64, nullptr,
+               nullptr, 0, 1, s);
     k_gnn_edge_bwd<<<eg, kT, 0, s>>>(g, a, W + g.off[kPWe + 5 * l], W + g.off[kPbm + 5 * l], g.dM, g.dA, g.gpart, st);
     k_reduce_parts<<<cdiv((kEin + 1) * 64, kT), kT, 0, s>>>(g.gpart, st, int(eg), (kEin + 1) * 64, g.grad + g.off[kPWe + 5 * l]);
     k_dense_wgrad<<<wg, kT, 0, s>>>(N, h, 64, nullptr, 0, g.dA, 64, 64, g.gpart, st);
     k_reduce_parts<<<cdiv(64 * 64, kT), kT, 0, s>>>(g.gpart, st, int(wg), 64 * 64, g.grad + g.off[kPWa + 5 * l]);
-    k_dense<<<nb, 256, 0, s>>>(N, g.dA, 64, 64, nullptr, 0, 0, W + g.off[kPWa + 5 * l], 64, 0, 1, nullptr, 64, g.dH, 64,
-                               nullptr, nullptr, 0, 1);
-    L += 10;
+    L += dense(g, N, g.dA, 64, 64, nullptr, 0, 0, W + g.off[kPWa + 5 * l], 64, 0, 1, nullptr, 64, g.dH, 64, nullptr,
+               nullptr, 0, 1, s);
+    L += 7;
   }
   k_relu_mask<<<cdiv(N * 64, kT), kT, 0, s>>>(N * 64, g.Z0, g.dH, g.dZ);
   k_dense_wgrad<<<wg, kT, 0, s>>>(N, g.X0, kNin, nullptr, 0, g.dZ, 64, 64, g.gpart, st);

@@ -134,6 +134,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_gnn_train": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
         "gf_gnn_attach": (ctypes.c_int, [P, P, ctypes.c_int32]),
+        "gf_gnn_kernels_set": (ctypes.c_int, [P, ctypes.c_int32]),
         "gf_gnn_pair_get": (ctypes.c_int, [P, P, P]),
         "gf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "gf_last_error": (ctypes.c_char_p, []),
@@ -492,6 +493,7 @@ def mesh_create(nodes, tets, mat: Material, precision: int = FP64, cg_rtol: floa
 
 
 GNN_START, GNN_PRECOND = 1, 2
+GNN_TENSOR_CORES, GNN_FP32_FMA = 0, 1
 
 # Parameter tensors of the learned start / preconditioner network, in storage
 # order, each row-major [in][out] (the layout gf_gnn_params_set expects).
@@ -574,6 +576,10 @@ class Gnn:
         t = np.empty(3 * self.mesh.n_nodes)
         _check(load_library().gf_gnn_pair_get(self._h, b.ctypes.data, t.ctypes.data))
         return b, t
+
+    def kernels_set(self, kernels: int):
+        """GNN_TENSOR_CORES (tcgen05 dense contractions, default) or GNN_FP32_FMA."""
+        _check(load_library().gf_gnn_kernels_set(self._h, int(kernels)))
 
     def attach(self, flags: int = 1):
         """GNN_START (learned start), GNN_PRECOND (learned blocks), both, or 0 (off)."""

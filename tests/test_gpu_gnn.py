@@ -61,11 +61,13 @@ def two_beam_steps():
     return w, model, m, st1, info1
 
 
-def test_network_forward_loss_gradients_and_adam_match_oracle():
+@pytest.mark.parametrize("kernels", [gf.GNN_TENSOR_CORES, gf.GNN_FP32_FMA], ids=["tcgen05", "fp32_fma"])
+def test_network_forward_loss_gradients_and_adam_match_oracle(kernels):
     w, model, m, st1, info1 = two_beam_steps()
     wts = active_weights(5)
     params = og.unflatten(og.to_bf16(wts))
     net = gf.Gnn(m, wts)
+    net.kernels_set(kernels)
     m.step(w.dt, w.f_ext.ravel(), w.pinned)
     _, info2 = model.step(st1, w.dt, w.f_ext, w.pinned)
     A = info2["A"]
@@ -109,6 +111,35 @@ def test_network_forward_loss_gradients_and_adam_match_oracle():
     want = -lr * grad_g / (np.abs(grad_g) + 1e-8)
     big = np.abs(grad_g) > 1e-4 * np.abs(grad_g).max()
     np.testing.assert_allclose(moved[big], want[big], rtol=1e-3, atol=1e-9)
+
+
+def test_tensor_core_and_fp32_kernels_agree_on_a_loaf():
+    """The tcgen05 dense layers and edge messages against the FP32 FMA kernels
+    on a half-size loaf (13,892 nodes: 109 node tiles with a ragged last one,
+    about 1,600 edge tiles): the same FP32-accurate results up to rounding
+    order (1e-5 norm-wise per output and per gradient tensor), and not
+    bit-identical, which shows that the tensor-core path ran."""
+    w = loaf_config(axes=tuple(0.5 * a for a in LOAF_AXES))
+    m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=w.threshold,
+                                                    radius=w.radius), cg_rtol=1e-6)
+    m.step(w.dt, w.f_ext.ravel())
+    m.step(w.dt, w.f_ext.ravel())
+    net = gf.Gnn(m, active_weights(7))
+    b, t = net.pair_get()
+    res = {}
+    for k in (gf.GNN_TENSOR_CORES, gf.GNN_FP32_FMA):
+        net.kernels_set(k)
+        fw = net.forward(b)
+        res[k] = (fw, *net.loss_grad(b, t))
+    (fa, la, ga), (fb, lb, gb) = res[gf.GNN_TENSOR_CORES], res[gf.GNN_FP32_FMA]
+    for key in ("out", "P", "x0"):
+        assert np.linalg.norm(fa[key] - fb[key]) <= RTOL_NET * np.linalg.norm(fb[key]), key
+    assert not np.array_equal(fa["out"], fb["out"])
+    assert abs(la - lb) <= RTOL_NET * abs(lb)
+    offs = np.cumsum([0] + [int(np.prod(v)) for _, v in SHAPES])
+    for i, (name, _) in enumerate(SHAPES):
+        a_, b_ = ga[offs[i]:offs[i + 1]], gb[offs[i]:offs[i + 1]]
+        assert np.linalg.norm(a_ - b_) <= RTOL_NET * np.linalg.norm(b_), name
 
 
 def test_zero_decoder_gives_scaled_block_jacobi():
