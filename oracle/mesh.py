@@ -50,6 +50,38 @@ def lumped_mass(X: np.ndarray, tets: np.ndarray, rho: float, V: np.ndarray):
     return m
 
 
+# Keast's 4-point rule on the reference tet (degree 2, so exact for the
+# products N_a N_b of linear shape functions): barycentric points (a, b, b, b)
+# and permutations, equal weights 1/4 of the volume.
+_QA = 0.5854101966249685
+_QB = 0.1381966011250105
+
+
+def consistent_mass_blocks(tets: np.ndarray, rho: float, V: np.ndarray) -> np.ndarray:
+    """Element mass of Eq. 5, m_e = int rho N_e^T N_e over the tet, as its
+    scalar 4x4 node-pair table (the 12x12 matrix is this (x) I_3, Eq. 8):
+    m_e[a, b] = rho V_e sum_q w_q N_a(p_q) N_b(p_q) by the 4-point rule.
+    Returns (t, 4, 4)."""
+    pts = np.full((4, 4), _QB)
+    np.fill_diagonal(pts, _QA)                  # row q = barycentric point q = (N_0..N_3)(p_q)
+    w = np.full(4, 0.25)
+    ref = np.einsum("q,qa,qb->ab", w, pts, pts)   # int N_a N_b / V over the tet
+    return rho * V[:, None, None] * ref[None]
+
+
+def consistent_mass_matrix(X: np.ndarray, tets: np.ndarray, rho: float, V: np.ndarray):
+    """Global mass of Eq. 4-5 with the consistent element masses, as a scipy
+    CSR (3n x 3n) matrix m (x) I_3."""
+    import scipy.sparse as sp
+    tets = np.asarray(tets, np.int64)
+    me = consistent_mass_blocks(tets, rho, V)
+    n = X.shape[0]
+    rows = np.repeat(tets, 4, axis=1).ravel()
+    cols = np.tile(tets, (1, 4)).ravel()
+    m = sp.coo_matrix((me.ravel(), (rows, cols)), shape=(n, n)).tocsr()
+    return sp.kron(m, sp.identity(3), format="csr")
+
+
 def centroids(X: np.ndarray, tets: np.ndarray) -> np.ndarray:
     """Rest centroid r of every tet (the r, r_0 of Eq. 20)."""
     return X[np.asarray(tets, np.int64)].mean(1)

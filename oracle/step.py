@@ -5,7 +5,8 @@ collision response, which are not part of the computational step:
   1. stresses along the edges at the start-of-step positions, non-local
      average, fracture check and relabel (Eq. 14-21), then chi (Eq. 22-25);
   2. build the system with f* = chi f and K* = sum chi k (Eq. 32-34), mass
-     (Eq. 5, lumped) and damping b* = alpha m + beta k* (Sec. 3.6);
+     (Eq. 5, row-sum lumped by default) and damping b* = alpha m + beta k*
+     (Sec. 3.6);
   3. solve for the velocity (implicit backward Euler + CG, Sec. 4.3);
   4. x += dt v.
 
@@ -15,6 +16,16 @@ The backward-Euler update is linearised once about the start of the step
       = dt [ f_ext + f*(x_n) - alpha M v_n - (beta + dt) K* v_n ]
 which is Eq. 2 with f_int(x_{n+1}) ~ f_int(x_n) + K* dt v_{n+1}.
 Pinned nodes have all three velocity components prescribed (zero by default).
+
+More Newton iterations (``newton_iters`` > 1) solve the backward-Euler
+residual itself,
+  r(v) = M (v - v_n) + dt (B v - f_ext - f*(x_n + dt v)),
+  B = alpha M + beta K*(x),
+from the guess v^0 = 0 (so that x^0 = x_n and the first iterate is the
+linearised step above): J_k = M + dt B_k + dt^2 K*(x^k), J_k d = -r(v^k),
+v^{k+1} = v^k + d, with the damping matrix taken at the current iterate and
+chi frozen for the step.  ``mass="consistent"`` uses the element masses of
+Eq. 5 as they stand instead of their row sums.
 """
 from __future__ import annotations
 
@@ -38,6 +49,7 @@ class Material:
     driver_mode: str = "strain"       # "strain" (sigma*/E) or "stress"
     shear_coef: float = 2.0           # 2: tensor n.S.n; 1: Eq. 16 as printed
     average_degraded: bool = True     # Eq. 20 averages chi_j S_j (True) or S_j
+    mass: str = "lumped"              # "lumped" (row sums of Eq. 5) or "consistent" (Eq. 5)
 
 
 @dataclasses.dataclass
@@ -59,6 +71,12 @@ class Model:
         self.edges, self.tet_edges = mesh.edges_of(self.tets)
         self.V, self.D2, self.q = mesh.rest_geometry(self.X, self.tets)
         self.mass = mesh.lumped_mass(self.X, self.tets, mat.density, self.V)
+        if mat.mass == "consistent":
+            self.M = mesh.consistent_mass_matrix(self.X, self.tets, mat.density, self.V)
+        elif mat.mass == "lumped":
+            self.M = sp.diags(np.repeat(self.mass, 3)).tocsr()
+        else:
+            raise ValueError(f"unknown mass matrix {mat.mass!r}")
         self.centroids = mesh.centroids(self.X, self.tets)
         self.nbrs = self.weights = None
         if nonlocal_lists:
@@ -117,16 +135,30 @@ class Model:
         """A dv = b of the linearised backward-Euler step (module docstring)."""
         mt = self.mat
         K, f = self.assemble(x, chi)
-        M = sp.diags(np.repeat(self.mass, 3))
+        M = self.M
         A = ((1.0 + dt * mt.alpha) * M + (dt * mt.beta + dt * dt) * K).tocsr()
         vv = v.ravel()
         b = dt * (np.asarray(f_ext, np.float64).ravel() + f - mt.alpha * (M @ vv)
                   - (mt.beta + dt) * (K @ vv))
         return A, b, K, f
 
+    def newton_residual(self, x_n, v_n, v, chi, dt, f_ext):
+        """r(v) of the backward-Euler step (module docstring) with B at x = x_n + dt v,
+        and its Jacobian J = M + dt B + dt^2 K*(x)."""
+        mt = self.mat
+        x = x_n + dt * v.reshape(-1, 3)
+        K, f = self.assemble(x, chi)
+        B = mt.alpha * self.M + mt.beta * K
+        vv, vn = v.ravel(), v_n.ravel()
+        r = self.M @ (vv - vn) + dt * (B @ vv - np.asarray(f_ext, np.float64).ravel() - f)
+        J = (self.M + dt * B + dt * dt * K).tocsr()
+        return r, J
+
     def step(self, state: State, dt: float, f_ext, pinned=None, pinned_vel=None,
-             solver: str = "direct", rtol: float = 1e-13, maxit: int = 100000):
+             solver: str = "direct", rtol: float = 1e-13, maxit: int = 100000, newton_iters: int = 1):
         """One step; returns (new State, info dict)."""
+        if newton_iters > 1:
+            return self.step_newton(state, dt, f_ext, pinned, pinned_vel, newton_iters, solver, rtol, maxit)
         drv, labels, chi, sig_star = self.damage_update(state)
         A, b, K, f = self.linear_system(state.x, state.v, chi, dt, f_ext)
         n = self.n_nodes
@@ -154,4 +186,42 @@ class Model:
         v_new = state.v + dv.reshape(-1, 3)
         x_new = state.x + dt * v_new
         info["dv"] = dv.reshape(-1, 3)
+        return State(x_new, v_new, labels, chi), info
+
+    def step_newton(self, state: State, dt: float, f_ext, pinned, pinned_vel, iters: int,
+                    solver: str = "direct", rtol: float = 1e-13, maxit: int = 100000):
+        """Backward Euler by Newton's method on r(v) (module docstring): the damage
+        update once at x_n, then `iters` Newton iterations from v^0 = 0 with
+        the pinned velocities imposed from the first iteration on."""
+        drv, labels, chi, sig_star = self.damage_update(state)
+        n = self.n_nodes
+        fixed = np.zeros(n, bool)
+        vp = np.zeros((0, 3))
+        if pinned is not None and len(pinned):
+            pinned = np.asarray(pinned, np.int64)
+            fixed[pinned] = True
+            vp = np.zeros((len(pinned), 3)) if pinned_vel is None else np.asarray(pinned_vel).reshape(-1, 3)
+        free = np.repeat(~fixed, 3)
+        v = np.zeros(3 * n)
+        res, iters_cg = [], 0
+        for k in range(iters):
+            r, J = self.newton_residual(state.x, state.v, v, chi, dt, f_ext)
+            d = np.zeros(3 * n)
+            if fixed.any():
+                d.reshape(-1, 3)[fixed] = vp - v.reshape(-1, 3)[fixed]
+            rhs = -r[free] - J[free][:, ~free] @ d[~free]
+            res.append(float(np.linalg.norm(rhs)))
+            Jff = J[free][:, free].tocsr()
+            if solver == "direct":
+                d[free] = solve.direct(Jff, rhs) if rhs.size else rhs
+            else:
+                sol, it, _, _ = solve.pcg(Jff, rhs, rtol=rtol, maxit=maxit)
+                d[free] = sol
+                iters_cg += it
+            v = v + d
+        r, _ = self.newton_residual(state.x, state.v, v, chi, dt, f_ext)
+        v_new = v.reshape(-1, 3)
+        x_new = state.x + dt * v_new
+        info = {"driver": drv, "labels": labels, "chi": chi, "sig_star": sig_star, "dv": v_new - state.v,
+                "newton_res": res, "final_res": float(np.linalg.norm(r[free])), "iters": iters_cg}
         return State(x_new, v_new, labels, chi), info
