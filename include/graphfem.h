@@ -60,12 +60,13 @@ enum { GF_DRIVER_STRAIN = 0, GF_DRIVER_STRESS = 1 };
 enum { GF_FP64 = 0, GF_MIXED = 1 };
 enum { GF_PRECOND_BJACOBI = 0 };
 enum { GF_ASSEMBLY_GATHER = 0, GF_ASSEMBLY_COLOUR = 1 };
+enum { GF_MASS_LUMPED = 0, GF_MASS_CONSISTENT = 1 };
 
 /* Material and damage parameters (Sec. 3.1, 3.3, 5.2). */
 typedef struct gf_material {
   double young;          /* Young's modulus E (Pa) */
   double poisson;        /* Poisson ratio nu, in (-1, 0.5) */
-  double density;        /* rho (kg/m^3); lumped mass rho V_e / 4 per node and tet (Eq. 5, lumped) */
+  double density;        /* rho (kg/m^3); element mass of Eq. 5, see mass_matrix */
   double alpha;          /* Rayleigh mass damping (b_e = alpha m_e + beta k_e*, Sec. 3.6) */
   double beta;           /* Rayleigh stiffness damping */
   double threshold;      /* sigma_thres of Eq. 21 in driver units; +inf disables fracture */
@@ -73,7 +74,9 @@ typedef struct gf_material {
   int32_t driver_mode;   /* GF_DRIVER_STRAIN: driver = sigma_star divided by E (dimensionless); GF_DRIVER_STRESS: sigma_star */
   int32_t shear_coef;    /* 2: normal stress n.S.n (default); 1: Eq. 16 as printed */
   int32_t average_degraded; /* 1: Eq. 20 averages chi_j S_j (default); 0: raw S_j */
-  int32_t reserved;      /* set to 0 */
+  int32_t mass_matrix;   /* GF_MASS_LUMPED (0, default): row sums of Eq. 5, rho V_e / 4 per node and
+                            tet; GF_MASS_CONSISTENT: Eq. 5 as it stands, rho V_e (1 + delta_ab) / 20
+                            between the nodes a, b of a tet (same block pattern as K) */
 } gf_material;
 
 typedef void* (*gf_alloc_fn)(size_t bytes, void* ctx);
@@ -101,7 +104,7 @@ typedef struct gf_step_stats {
   int64_t n_new_broken;  /* edges that broke in this step */
   int64_t n_chi_zero;    /* tets split into disjoint pieces (chi = 0) */
   int32_t refine_sweeps; /* GF_MIXED: FP64 refinement sweeps; 0 in GF_FP64 */
-  int32_t reserved;
+  int32_t newton_iters;  /* Newton iterations the step ran (gf_newton_set) */
 } gf_step_stats;
 
 typedef struct gf_mesh_info {
@@ -175,6 +178,18 @@ gf_status gf_refine_set(gf_mesh* mesh, double inner_rtol);
 
 /* Change the solver tolerance and iteration cap between steps (rtol > 0). */
 gf_status gf_solver_set(gf_mesh* mesh, double cg_rtol, int32_t cg_maxit);
+
+/* Newton iterations per step (default 1: the backward-Euler update of Eq. 2
+ * linearised at x_n).  With max_iters > 1 the step solves the backward-Euler
+ * residual r(v) = M (v - v_n) + dt (B v - f_ext - f*(x_n + dt v)),
+ * B = alpha M + beta K*(x_n + dt v), by Newton's method from v = 0, with chi
+ * frozen for the step.  Each iteration re-assembles the system at
+ * x^k = x_n + dt v^k and solves it to cg_rtol (PCG warm-started from the
+ * previous iterate).  It stops after max_iters (1..64) or once
+ * |r(v^k)| <= rtol |b^0| on free DOFs (b^0 the first right-hand side; rtol 0
+ * runs all iterations).  GF_FP64 meshes only (GF_UNSUPPORTED for GF_MIXED and
+ * for batches). */
+gf_status gf_newton_set(gf_mesh* mesh, int32_t max_iters, double rtol);
 
 /* Current positions / velocities, float64 [3*n_nodes]. */
 gf_status gf_positions_get(gf_mesh* mesh, double* x, int32_t mem);

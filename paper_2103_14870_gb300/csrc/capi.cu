@@ -144,6 +144,11 @@ struct gf_mesh {
   bool mixed = false;
   int last_inner = 3;
   double in_rtol = 1e-4;
+  int newton_iters = 1;       // Newton iterations per step (FP64 path)
+  double newton_rtol = 0.0;   // stop early when |r(v^k)| <= newton_rtol |b^0| on free DOFs
+  int newton_done = 1;        // iterations of the last step
+  double newton_res = 0.0;    // |r(v^k)| / |b^0| at the start of the last iteration (0 after one)
+  int newton_cg_total = 0;    // CG iterations of the last step over its Newton iterations
   int64_t launches = 0;
   int64_t nbr_pairs = 0;
 
@@ -272,8 +277,10 @@ void prof_collect(gf_mesh* m, int cg_iters, bool converged) {
 bool material_ok(const gf_material& M) {
   if (!(M.young > 0) || !(M.poisson > -1.0 && M.poisson < 0.5) || !(M.density > 0) || !(M.radius >= 0) ||
       std::isnan(M.threshold) || !(M.alpha >= 0) || !(M.beta >= 0) || (M.shear_coef != 1 && M.shear_coef != 2) ||
-      (M.driver_mode != GF_DRIVER_STRAIN && M.driver_mode != GF_DRIVER_STRESS)) {
-    set_last_error("invalid material (need E > 0, -1 < nu < 0.5, rho > 0, R_d >= 0, alpha, beta >= 0, shear_coef 1|2)");
+      (M.driver_mode != GF_DRIVER_STRAIN && M.driver_mode != GF_DRIVER_STRESS) ||
+      (M.mass_matrix != GF_MASS_LUMPED && M.mass_matrix != GF_MASS_CONSISTENT)) {
+    set_last_error("invalid material (need E > 0, -1 < nu < 0.5, rho > 0, R_d >= 0, alpha, beta >= 0, shear_coef 1|2, "
+                   "mass_matrix lumped|consistent)");
     return false;
   }
   return true;
@@ -434,6 +441,17 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   UP(d.sc_ent, hm.sc_ent, int32_t);
   UP(d.np_ptr, hm.np_ptr, int32_t);
   UP(d.np_pair, hm.np_pair, int32_t);
+  std::vector<double> mass_blk;
+  if (M.mass_matrix == GF_MASS_CONSISTENT) {
+    // Eq. 5 for a linear tet: m_ab = rho V (1 + delta_ab) / 20, summed into the block slots
+    mass_blk.assign(hm.n_blocks, 0.0);
+    for (int64_t t = 0; t < hm.n_tets; ++t) {
+      const double mv = M.density * hm.rest[size_t(kRestV) * hm.n_tets + t] / 20.0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) mass_blk[hm.slot[16 * t + 4 * a + b]] += (a == b ? 2.0 : 1.0) * mv;
+    }
+    UP(d.mass_blk, mass_blk, double);
+  }
   if (!mixed) {
     UP(d.nb_off, hm.nbr.group_off, int64_t);
     UP(d.nb_len, hm.nbr.group_len, int32_t);
@@ -450,6 +468,10 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.nb_wc, mxh.nb_wc, float);
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());
     UP(d.mx.mass32, m32, float);
+    if (!mass_blk.empty()) {
+      std::vector<float> mb32(mass_blk.begin(), mass_blk.end());
+      UP(d.mx.mass_blk32, mb32, float);
+    }
     std::vector<double> Xv(nodes, nodes + 3 * n_nodes);
     UP(d.mx.X, Xv, double);
   }
@@ -464,7 +486,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
       (st = scratch(m, T, &d.chi)) || (st = scratch(m, NE, &d.driver)) || (st = scratch(m, 3 * N, &d.rhs)) ||
       (st = scratch(m, 3 * N, &d.dv)) || (st = scratch(m, N, &d.pinned)) || (st = scratch(m, 3 * N, &d.f_ext)) ||
       (st = scratch(m, N, &d.pin_ids)) || (st = scratch(m, 3 * N, &d.pin_vel)) || (st = scratch(m, 1, &d.pcg)) ||
-      (st = scratch(m, 2 * kMaxPartials, &d.partials)) || (st = scratch(m, kTickets, &d.tickets)) ||
+      (st = scratch(m, 4 * kMaxPartials, &d.partials)) || (st = scratch(m, kTickets, &d.tickets)) ||
       (st = scratch(m, kCntMax, &d.counters)) || (st = scratch(m, 6 * T, &d.sigf)))
     return fail(st);
   if (!mixed) {
@@ -519,7 +541,6 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   hm.et_tet = {};
   hm.tets = {};
   hm.tet_edges = {};
-  hm.mass = {};
   *out = m;
   return GF_OK;
 }
@@ -650,6 +671,20 @@ gf_status gf_refine_set(gf_mesh* m, double inner_rtol) {
   return GF_OK;
 }
 
+gf_status gf_newton_set(gf_mesh* m, int32_t max_iters, double rtol) {
+  if (!m || max_iters < 1 || max_iters > 64 || !(rtol >= 0) || !std::isfinite(rtol)) {
+    set_last_error("need 1 <= max_iters <= 64 and rtol >= 0");
+    return GF_BAD_ARG;
+  }
+  if (m->mixed && max_iters > 1) {
+    set_last_error("more than one Newton iteration per step is built for GF_FP64 meshes only");
+    return GF_UNSUPPORTED;
+  }
+  m->newton_iters = max_iters;
+  m->newton_rtol = rtol;
+  return GF_OK;
+}
+
 gf_status gf_solver_set(gf_mesh* m, double rtol, int32_t maxit) {
   if (!m || !(rtol > 0) || maxit <= 0) {
     set_last_error("need rtol > 0 and maxit > 0");
@@ -668,6 +703,8 @@ int64_t gnn_step_start(gf_gnn* g, const DevMesh& d, int flags, cudaStream_t s);
 cudaError_t gnn_keep_previous(gf_gnn* g, const DevMesh& d, cudaStream_t s);
 
 // FP64 path: damage, two-phase (or colour-ordered) assembly, projected PCG (all FP64).
+// Newton iterations after the first re-assemble at x^k = x + dt v^k with the
+// same kernels (see k_newton_prep) and warm-start the PCG from the previous dv.
 gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_pinned, bool has_pvel,
                     int64_t& L) {
   cudaStream_t s = m->stream;
@@ -682,21 +719,45 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
   }
   { Prof p(m, kPEdge); L += launch_kind(kB_edge_driver, d, mt, sp, s); }
   { Prof p(m, kPChi); L += launch_kind(kB_tet_chi, d, mt, sp, s); }
-  {
-    Prof p(m, kPAssemble);
-    if (m->tune.assembly == GF_ASSEMBLY_COLOUR) {
-      GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
-      L += launch_kind(kB_node_init, d, mt, sp, s);
-      const auto& cp = m->hm.colour_ptr;
-      for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble_colour(d, mt, dt, cp[c], cp[c + 1], s);
-    } else {
-      L += launch_kind(kB_elem64, d, mt, sp, s);
+  // system at positions/velocities of the view de (element kernels) and d (mass terms)
+  auto assemble = [&](const DevMesh& de) -> gf_status {
+    {
+      Prof p(m, kPAssemble);
+      if (m->tune.assembly == GF_ASSEMBLY_COLOUR) {
+        GF_CK(cudaMemsetAsync(d.val, 0, sizeof(double) * 9 * d.NB, s));
+        L += launch_kind(kB_node_init, d, mt, sp, s);
+        const auto& cp = m->hm.colour_ptr;
+        for (size_t c = 0; c + 1 < cp.size(); ++c) L += launch_assemble_colour(de, mt, dt, cp[c], cp[c + 1], s);
+      } else {
+        L += launch_kind(kB_elem64, de, mt, sp, s);
+      }
     }
-  }
-  if (m->tune.assembly != GF_ASSEMBLY_COLOUR) {
-    Prof p(m, kPGather);
-    L += launch_kind(kB_gather64, d, mt, sp, s);
-  }
+    if (m->tune.assembly != GF_ASSEMBLY_COLOUR) {
+      Prof p(m, kPGather);
+      L += launch_kind(kB_gather64, d, mt, sp, s);
+    }
+    return GF_OK;
+  };
+  // PCG on the assembled system from the dv in place; returns after convergence or maxit
+  auto run_pcg = [&]() -> gf_status {
+    int launched_iters = 0;
+    int chunk = std::max(1, std::min(m->last_iters + 1, 64));
+    for (;;) {
+      for (int j = 0; j < chunk; ++j, ++launched_iters) {
+        { Prof p(m, kPSpmv, launched_iters); L += launch_kind(kB_pcg_spmv, d, mt, sp, s); }
+        { Prof p(m, kPPcgUpdate, launched_iters); L += launch_kind(kB_pcg_update, d, mt, sp, s); }
+        { Prof p(m, kPPcgP, launched_iters); L += launch_kind(kB_pcg_p, d, mt, sp, s); }
+      }
+      GF_CK(cudaGetLastError());
+      GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      GF_CK(cudaStreamSynchronize(s));
+      if (m->h_pcg->done || launched_iters >= m->opt.cg_maxit) break;
+      chunk = 8;
+    }
+    return GF_OK;
+  };
+  gf_status st = assemble(d);
+  if (st != GF_OK) return st;
   PcgState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
   init.maxit = m->opt.cg_maxit;
@@ -713,24 +774,35 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
     sl.learned = 1;
     { Prof p(m, kPPcgInit); L += launch_kind(kB_pcg_init, d, mt, sl, s); }
   }
-  int launched_iters = 0;
-  int chunk = std::max(1, std::min(m->last_iters + 1, 64));
-  for (;;) {
-    for (int j = 0; j < chunk; ++j, ++launched_iters) {
-      { Prof p(m, kPSpmv, launched_iters); L += launch_kind(kB_pcg_spmv, d, mt, sp, s); }
-      { Prof p(m, kPPcgUpdate, launched_iters); L += launch_kind(kB_pcg_update, d, mt, sp, s); }
-      { Prof p(m, kPPcgP, launched_iters); L += launch_kind(kB_pcg_p, d, mt, sp, s); }
-    }
-    GF_CK(cudaGetLastError());
-    GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-    GF_CK(cudaStreamSynchronize(s));
-    if (m->h_pcg->done || launched_iters >= m->opt.cg_maxit) break;
-    chunk = 8;
+  if ((st = run_pcg()) != GF_OK) return st;
+  m->newton_done = 1;
+  m->newton_res = 0.0;
+  int cg_total = m->h_pcg->iters;
+  const double bb0 = m->h_pcg->bb;
+  for (int k = 1; k < m->newton_iters && m->h_pcg->status == GF_OK; ++k) {
+    // iterate k: assemble at x^k (element view: positions d.q, K v velocity d.z; PCG vectors are free here)
+    L += launch_newton_prep(d, mt, dt, d.q, d.z, s);
+    DevMesh de = d;
+    de.x = d.q;
+    de.v = d.z;
+    if ((st = assemble(de)) != GF_OK) return st;
+    PcgState again = init;
+    *m->h_pcg = again;
+    GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    StepScalars sw = sp;
+    sw.warm = 1;
+    { Prof p(m, kPPcgInit); L += launch_kind(kB_pcg_init, d, mt, sw, s); }
+    if ((st = run_pcg()) != GF_OK) return st;
+    cg_total += m->h_pcg->iters;
+    m->newton_done = k + 1;
+    m->newton_res = bb0 > 0 ? std::sqrt(m->h_pcg->rr0 / bb0) : 0.0;   // |r(v^k)| / |b^0| on free DOFs
+    if (m->newton_res <= m->newton_rtol) break;
   }
   { Prof p(m, kPResidual); L += launch_kind(kB_true_residual, d, mt, sp, s); }
   { Prof p(m, kPIntegrate); L += launch_kind(kB_integrate, d, mt, sp, s); }
   GF_CK(cudaGetLastError());
   GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  m->newton_cg_total = cg_total;
   return GF_OK;
 }
 
@@ -857,7 +929,7 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
     m->last_iters = ps.iters;
     prof_collect(m, ps.iters, ps.status == GF_OK);
     status = gf_status(ps.status);
-    iters = ps.iters;
+    iters = m->newton_cg_total;
     rel = ps.bb > 0 ? std::sqrt(ps.true_rr / ps.bb) : 0.0;
   }
   if (status == GF_OK && !std::isfinite(rel)) status = GF_NAN;
@@ -877,7 +949,7 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
     stats->n_new_broken = int64_t(m->h_cnt[kCntNewBroken]);
     stats->n_chi_zero = int64_t(m->h_cnt[kCntChiZero]);
     stats->refine_sweeps = sweeps;
-    stats->reserved = 0;
+    stats->newton_iters = m->mixed ? 1 : m->newton_done;
   }
   if (status != GF_OK && status != GF_BAD_ARG)
     set_last_error(std::string("step: ") + gf_status_string(status));
@@ -1303,6 +1375,7 @@ gf_status batch_run(gf_batch* b, gf_step_stats* stats) {
     st.n_broken = int64_t(o.cnt[kCntBroken]);
     st.n_new_broken = int64_t(o.cnt[kCntNewBroken]);
     st.n_chi_zero = int64_t(o.cnt[kCntChiZero]);
+    st.newton_iters = 1;
     if (stats) stats[k] = st;
     if (st.status != GF_OK && first_bad == GF_OK) first_bad = gf_status(st.status);
   }
@@ -1395,6 +1468,11 @@ gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, cons
     set_last_error("batch step: need a batch, dt > 0 and a memory kind");
     return GF_BAD_ARG;
   }
+  for (gf_mesh* mm : b->ms)
+    if (mm->newton_iters > 1) {
+      set_last_error("batch step: members run one Newton iteration per step (gf_newton_set 1)");
+      return GF_UNSUPPORTED;
+    }
   DeviceGuard guard(b->device);
   gf_status st = batch_prepare(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem);
   if (st != GF_OK) return st;

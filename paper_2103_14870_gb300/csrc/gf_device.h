@@ -16,6 +16,7 @@ struct PcgState {
   double alpha, beta;
   double tol2;    // rtol^2
   double true_rr; // ||b - A dv||^2 after the solve
+  double rr0;     // ||b - A dv||^2 at the start (a Newton iterate's residual when warm-started)
   int32_t iters, maxit, done, status;
 };
 
@@ -46,6 +47,7 @@ struct MixDev {
   const int32_t* nb_csr = nullptr;
   const float* nb_wc = nullptr;
   const float* mass32 = nullptr;      // [N]
+  const float* mass_blk32 = nullptr;  // [NB] consistent mass per block slot (NULL: lumped)
   const double* X = nullptr;          // [3N] rest positions
   float* u32 = nullptr;               // [3N] displacement x - X
   float* v32 = nullptr;               // [3N] velocity
@@ -71,7 +73,8 @@ struct DevMesh {
   const int32_t* tet_edges = nullptr;  // [T][6]
   const int32_t* slot = nullptr;       // [T][16]
   const double* rest = nullptr;        // [kRestFields][T]
-  const double* mass = nullptr;        // [N]
+  const double* mass = nullptr;        // [N] lumped (row sums of Eq. 5)
+  const double* mass_blk = nullptr;    // [NB] consistent mass m_ij of Eq. 5 per block slot (NULL: lumped)
   const int32_t* row_ptr = nullptr;    // [N+1]
   const int32_t* col = nullptr;        // [NB]
   const int32_t* diag_blk = nullptr;   // [N]
@@ -133,6 +136,7 @@ struct StepScalars {
   float dtf, sKv, cv, alphaf, cmf;   // dt, dt beta + dt^2, beta + dt, alpha, 1 + dt alpha
   int has_fext, has_pvel;
   int learned;                        // pcg_init keeps the preconditioner, start and |b_free|^2 already set
+  int warm;                           // pcg_init starts from the dv in place (Newton iterations after the first)
   int64_t n_pinned;
 };
 
@@ -196,5 +200,7 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
 // single-mesh launches (return the number of kernels launched)
 int launch_kind(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first = 0);
 int launch_assemble_colour(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s);
+// Newton iterate k >= 1 of the FP64 step: xk = x + dt (v + dv), w = v - dt (v + dv) / (beta + dt)
+int launch_newton_prep(const DevMesh& m, const Material& mt, double dt, double* xk, double* w, cudaStream_t s);
 
 }  // namespace gf

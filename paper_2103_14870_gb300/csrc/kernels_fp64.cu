@@ -232,6 +232,23 @@ __device__ __forceinline__ void node_init_body(const DevMesh& m, const Material&
 
   const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
   if (i >= m.N) return;
+  if (m.mass_blk) {   // consistent mass: every block of the row, and M v over the row
+    double mv[3] = {0.0, 0.0, 0.0};
+    for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) {
+      const double mb = m.mass_blk[b];
+      const int64_t j = m.col[b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mv[c] += mb * m.v[3 * j + c];
+      double* d = m.val + 9 * int64_t(b);
+      const double cm = (1.0 + dt * alpha) * mb;
+      d[0] += cm;
+      d[4] += cm;
+      d[8] += cm;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.rhs[3 * i + c] = dt * ((f_ext ? f_ext[3 * i + c] : 0.0) - alpha * mv[c]);
+    return;
+  }
   const double mi = m.mass[i];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
@@ -498,8 +515,8 @@ __global__ void __launch_bounds__(128) kb_elem64(const BatchTab* __restrict__ ta
 }
 
 // Phase 2 of the assembly: each matrix entry and rhs component is the sum, in
-// a fixed order, of its element contributions (plus the lumped-mass term on
-// the diagonal, Eq. 2).  Threads [0, 9 NB) take one entry of an off-diagonal
+// a fixed order, of its element contributions (plus the mass term of Eq. 2:
+// lumped on the diagonal, or the consistent m_ij of Eq. 5 on every block).  Threads [0, 9 NB) take one entry of an off-diagonal
 // block each (the 4-6 tets around an edge); threads [9 NB, 9 NB + 12 N) take
 // a node's nine diagonal entries and three rhs components (the ~24 tets around
 // the node).  Neighbouring threads sum lists of similar length, so the FP64
@@ -518,6 +535,7 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
       const int ent = m.sc_ent[c];
       acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
     }
+    if (m.mass_blk && (e == 0 || e == 4 || e == 8)) acc += (1.0 + dt * alpha) * m.mass_blk[slot];
     m.val[9 * slot + e] = acc;
     return;
   }
@@ -534,7 +552,7 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
       const int ent = m.sc_ent[c];
       acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : q)];
     }
-    if (q == 0 || q == 4 || q == 8) acc += (1.0 + dt * alpha) * mi;
+    if (q == 0 || q == 4 || q == 8) acc += (1.0 + dt * alpha) * (m.mass_blk ? m.mass_blk[slot] : mi);
     m.val[9 * int64_t(slot) + q] = acc;
   } else {
     const int c3 = q - 9;
@@ -544,7 +562,12 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
       const int pr = m.np_pair[k];
       acc += m.ebuf[kElemW64 * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + c3];
     }
-    m.rhs[3 * i + c3] = acc + dt * ((f_ext ? f_ext[3 * i + c3] : 0.0) - alpha * mi * m.v[3 * i + c3]);
+    double mv = mi * m.v[3 * i + c3];
+    if (m.mass_blk) {   // consistent mass: (M v)_i over the row
+      mv = 0.0;
+      for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) mv += m.mass_blk[b] * m.v[3 * int64_t(m.col[b]) + c3];
+    }
+    m.rhs[3 * i + c3] = acc + dt * ((f_ext ? f_ext[3 * i + c3] : 0.0) - alpha * mv);
   }
 }
 __global__ void __launch_bounds__(256) k_gather64(DevMesh m, Material mt, StepScalars sp) {
@@ -554,6 +577,21 @@ __global__ void __launch_bounds__(256) kb_gather64(const BatchTab* __restrict__ 
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_gather64, blockIdx.x, bid, nb);
   gather64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
+
+// Newton iterate k >= 1 (v^k = v + dv, the previous solve's total velocity
+// change dv): positions xk = x + dt v^k for the element kernel, and the
+// velocity w = v - dt v^k / (beta + dt) of its K v term, so that the assembled
+// right-hand side is b(x^k, v) + dt^2 K(x^k) v^k and the unknown stays
+// dv = v^{k+1} - v.
+__global__ void __launch_bounds__(kThreads) k_newton_prep(int64_t n, const double* __restrict__ x,
+                                                         const double* __restrict__ v, const double* __restrict__ dv,
+                                                         double dt, double cw, double* xk, double* w) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const double vk = v[i] + dv[i];
+  xk[i] = x[i] + dt * vk;
+  w[i] = v[i] - cw * vk;
 }
 
 // ---------------------------------------------------------------------------
@@ -606,9 +644,23 @@ __global__ void __launch_bounds__(kThreads) kb_set_pinned(const BatchTab* __rest
 // plain initialisation that ran before them.
 __device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
-  double v[2] = {0.0, 0.0};
+  double v[3] = {0.0, 0.0, 0.0};
   for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     double r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
+    if (!m.pinned[i] && sp.warm) {   // |b - A_fp dv_p|^2: the reference of a warm-started solve
+      double bf[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) bf[c] = m.rhs[3 * i + c];
+      for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) {
+        const int64_t j = m.col[b];
+        if (!m.pinned[j]) continue;
+        const double* a = m.val + 9 * int64_t(b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          bf[c] -= a[3 * c] * m.dv[3 * j] + a[3 * c + 1] * m.dv[3 * j + 1] + a[3 * c + 2] * m.dv[3 * j + 2];
+      }
+      v[2] += bf[0] * bf[0] + bf[1] * bf[1] + bf[2] * bf[2];
+    }
     if (!m.pinned[i] && sp.learned) {
       double ad[3];
       spmv_row(m, i, m.dv, ad);
@@ -643,12 +695,14 @@ __device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& 
       v[1] += r[c] * r[c];
     }
   }
-  double out[2];
-  if (grid_reduce<2>(v, m.partials, m.tickets + 0, out, bid, nb) && threadIdx.x == 0) {
+  double out[3];
+  if (grid_reduce<3>(v, m.partials, m.tickets + 0, out, bid, nb) && threadIdx.x == 0) {
     PcgState* s = m.pcg;
     s->rz = out[0];
     s->rr = out[1];
-    if (!sp.learned) s->bb = out[1];
+    s->rr0 = out[1];
+    if (sp.warm) s->bb = out[2];
+    else if (!sp.learned) s->bb = out[1];
     s->iters = 0;
     s->status = GF_OK;
     s->done = (out[1] == 0.0 || out[1] <= s->tol2 * s->bb) ? 1 : 0;
@@ -814,6 +868,13 @@ __global__ void __launch_bounds__(kThreads) kb_integrate(const BatchTab* __restr
 }
 
 }  // namespace
+
+int launch_newton_prep(const DevMesh& m, const Material& mt, double dt, double* xk, double* w, cudaStream_t s) {
+  const int64_t n = 3 * m.N;
+  const double cw = dt / (mt.beta + dt);
+  k_newton_prep<<<unsigned((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(n, m.x, m.v, m.dv, dt, cw, xk, w);
+  return 1;
+}
 
 int launch_assemble_colour(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s) {
   if (t1 <= t0) return 0;

@@ -425,7 +425,10 @@ __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& 
       const int ent = m.sc_ent[c];
       acc += x.ebuf[kElemW * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
     }
-    if (slot == dslot) {
+    if (x.mass_blk32) {
+      if (e == 0 || e == 4 || e == 8) acc += cmf * x.mass_blk32[slot];   // consistent mass (Eq. 5)
+      if (slot == dslot) dg[wib][e] = acc;
+    } else if (slot == dslot) {
       if (e == 0 || e == 4 || e == 8) acc += cmf * mi;
       dg[wib][e] = acc;
     }
@@ -438,7 +441,12 @@ __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& 
       acc += x.ebuf[kElemW * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
     }
     const float fe = sp.has_fext ? x.fext32[3 * i + lane] : 0.f;
-    x.rhs32[3 * i + lane] = acc + dtf * (fe - alphaf * mi * x.v32[3 * i + lane]);
+    float mv = mi * x.v32[3 * i + lane];
+    if (x.mass_blk32) {
+      mv = 0.f;
+      for (int b = rb; b < rb + rl; ++b) mv += x.mass_blk32[b] * x.v32[3 * int64_t(m.col[b]) + lane];
+    }
+    x.rhs32[3 * i + lane] = acc + dtf * (fe - alphaf * mv);
   }
   __syncwarp();
   if (lane == 0) {

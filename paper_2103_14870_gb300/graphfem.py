@@ -37,7 +37,7 @@ class Material(ctypes.Structure):
     _fields_ = [("young", ctypes.c_double), ("poisson", ctypes.c_double), ("density", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("threshold", ctypes.c_double),
                 ("radius", ctypes.c_double), ("driver_mode", ctypes.c_int32), ("shear_coef", ctypes.c_int32),
-                ("average_degraded", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("average_degraded", ctypes.c_int32), ("mass_matrix", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -53,10 +53,10 @@ class Options(ctypes.Structure):
 class StepStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("cg_iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
                 ("n_broken", ctypes.c_int64), ("n_new_broken", ctypes.c_int64), ("n_chi_zero", ctypes.c_int64),
-                ("refine_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("refine_sweeps", ctypes.c_int32), ("newton_iters", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Tuning(ctypes.Structure):
@@ -100,6 +100,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
                                    ctypes.POINTER(StepStats)]),
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
+        "gf_newton_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
         "gf_tuning_set": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
         "gf_tuning_get": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
         "gf_positions_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
@@ -182,9 +183,10 @@ def _one_kind(*kinds) -> int:
 
 
 def material(young, poisson, density, threshold=math.inf, radius=0.0, alpha=0.0, beta=0.0,
-             driver_mode=DRIVER_STRAIN, shear_coef=2, average_degraded=True) -> Material:
+             driver_mode=DRIVER_STRAIN, shear_coef=2, average_degraded=True, mass_matrix=0) -> Material:
+    """gf_material; mass_matrix MASS_LUMPED (0) or MASS_CONSISTENT (1)."""
     return Material(young, poisson, density, alpha, beta, threshold, radius, driver_mode, shear_coef,
-                    1 if average_degraded else 0, 0)
+                    1 if average_degraded else 0, int(mass_matrix))
 
 
 class Mesh:
@@ -256,6 +258,10 @@ class Mesh:
 
     def solver_set(self, rtol: float, maxit: int = 10000):
         _check(load_library().gf_solver_set(self._h, float(rtol), int(maxit)))
+
+    def newton_set(self, max_iters: int, rtol: float = 0.0):
+        """Newton iterations per step on the backward-Euler residual (FP64 meshes)."""
+        _check(load_library().gf_newton_set(self._h, int(max_iters), float(rtol)))
 
     # -- getters ----------------------------------------------------------
     def _get(self, fn, n, dtype, out):
@@ -493,6 +499,7 @@ def mesh_create(nodes, tets, mat: Material, precision: int = FP64, cg_rtol: floa
 
 
 GNN_START, GNN_PRECOND = 1, 2
+MASS_LUMPED, MASS_CONSISTENT = 0, 1
 GNN_TENSOR_CORES, GNN_FP32_FMA = 0, 1
 
 # Parameter tensors of the learned start / preconditioner network, in storage
