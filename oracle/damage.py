@@ -32,10 +32,17 @@ from .mesh import LOCAL_EDGES
 VOIGT = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
 
 
-def stress_voigt(C: np.ndarray, lam: float, mu: float) -> np.ndarray:
-    """S = 2 dPsi/dC for Eq. 37 = lam/2 (I_C - 3) Id + mu (C - Id), in Eq. 14 order."""
+def stress_voigt(C: np.ndarray, lam: float, mu: float, energy: str = "stvk", J=None) -> np.ndarray:
+    """S = 2 dPsi/dC in Eq. 14 order.  Eq. 37: lam/2 (I_C - 3) Id + mu (C - Id).
+    Eq. 35 (squared reading, signed J): mu (1 - 1/(I_C + 1)) Id + lam (J - a) J C^-1,
+    from dJ/dC = J/2 C^-1."""
     I = np.trace(C, axis1=-2, axis2=-1)
-    S = lam / 2.0 * (I - 3.0)[..., None, None] * np.eye(3) + mu * (C - np.eye(3))
+    if energy == "stvk":
+        S = lam / 2.0 * (I - 3.0)[..., None, None] * np.eye(3) + mu * (C - np.eye(3))
+    else:
+        a = 1.0 + mu / lam - mu / (4.0 * lam)
+        S = (mu * (1.0 - 1.0 / (I + 1.0)))[..., None, None] * np.eye(3) \
+            + (lam * (J - a) * J)[..., None, None] * np.linalg.inv(C)
     return np.stack([S[..., i, j] for i, j in VOIGT], -1)
 
 

@@ -7,6 +7,12 @@ Paper passages followed:
   C = Lambda . [Q (x) Q]^+ . Q  (^+ = pseudo-inverse).  Reading used: q_mn is the
   REST unit edge, so that C . Q_mn = lambda_mn^2 holds exactly for C = F^T F.
 * Eq. 37: Saint-Venant-Kirchhoff  Psi = lam/8 (I_C-3)^2 + mu/4 (II_C - 2 I_C + 3).
+* Eq. 35: stable Neo-Hookean  Psi = mu/2 (I_C - 3) + lam/2 (J - a)^2 - mu/2 log(I_C + 1),
+  a = 1 + mu/lam - mu/(4 lam).  Reading used: the (J - a) term is squared (as
+  in the energy the paper cites for it; printed without the square, the rest
+  state would carry a stress lam/2), and J is the signed det F: its magnitude
+  sqrt(det C) is a function of the edge lengths, its sign the orientation of
+  the current tet relative to the rest tet.
 * Eq. 12: f_i = -V dPsi/dr_i = 2V sum_j dPsi/d(d_ij^2) d_ij dhat_ij, with dhat_ij
   the unit vector from node i to node j (the restoring sign).
 * Eq. 10/11 and Eq. 33: the tangent k_e is the Hessian of the element energy;
@@ -83,17 +89,61 @@ def stvk_d2psi_dC2(A: np.ndarray, B: np.ndarray, lam: float, mu: float) -> np.nd
     return lam / 4.0 * trA * trB + mu / 2.0 * np.einsum("...ij,...ij->...", A, B)
 
 
+def snh_alpha(lam: float, mu: float) -> float:
+    """a of Eq. 35 (the rest state F = I is stress-free with the squared term)."""
+    return 1.0 + mu / lam - mu / (4.0 * lam)
+
+
+def orientation(x: np.ndarray, tets: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Sign of det F per tet: sign(det Ds) sign(det Dm), with the rest sign read
+    from the rest unit edges q of local edges (0,1) (0,2) (0,3)."""
+    P = x[np.asarray(tets, np.int64)]
+    Ds = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], 2)
+    Qm = np.stack([q[:, 0], q[:, 1], q[:, 2]], 2)
+    return np.sign(np.linalg.det(Ds)) * np.sign(np.linalg.det(Qm))
+
+
+def snh_density(IC, J, lam: float, mu: float):
+    """Eq. 35 (squared reading) from I_C = tr C and the signed J."""
+    a = snh_alpha(lam, mu)
+    return mu / 2.0 * (IC - 3.0) + lam / 2.0 * (J - a) ** 2 - mu / 2.0 * np.log(IC + 1.0)
+
+
 def edge_derivatives(x: np.ndarray, tets: np.ndarray, D2: np.ndarray, q: np.ndarray,
-                     lam: float, mu: float):
+                     lam: float, mu: float, energy: str = "stvk"):
     """g_k = dPsi/ds_k (t, 6) and H_kl = d2Psi/ds_k ds_l (t, 6, 6) by the chain
-    rule through the linear map s -> C of Eq. 31.  Also returns Psi and C."""
+    rule through the linear map s -> C = sum_k s_k M_k of Eq. 31.  Also returns
+    Psi and C.
+
+    energy "stvk" (Eq. 37): g = dPsi/dC : M_k, H = d2Psi/dC2 [M_k, M_l].
+    energy "snh" (Eq. 35): with I_C = sum_k s_k tr M_k, J = sgn sqrt(det C),
+    dJ/ds_k = J/2 tr(C^-1 M_k) and d2J/ds_k ds_l = J/4 t_k t_l - J/2 tr(C^-1 M_l C^-1 M_k)
+    (t_k = tr(C^-1 M_k)), from d det C = det C tr(C^-1 dC)."""
     s = squared_edge_lengths(x, tets)
     M = lsq_operator(D2, q)
     C = np.einsum("tk,tkij->tij", s, M)
-    dPdC = stvk_dpsi_dC(C, lam, mu)
-    g = np.einsum("tij,tkij->tk", dPdC, M)
-    H = stvk_d2psi_dC2(M[:, :, None], M[:, None, :], lam, mu)
-    return stvk_density(C, lam, mu), g, H, C
+    if energy == "stvk":
+        dPdC = stvk_dpsi_dC(C, lam, mu)
+        g = np.einsum("tij,tkij->tk", dPdC, M)
+        H = stvk_d2psi_dC2(M[:, :, None], M[:, None, :], lam, mu)
+        return stvk_density(C, lam, mu), g, H, C
+    if energy != "snh":
+        raise ValueError(f"unknown energy {energy!r}")
+    a = snh_alpha(lam, mu)
+    IC = np.trace(C, axis1=-2, axis2=-1)
+    J = orientation(x, tets, q) * np.sqrt(np.linalg.det(C))
+    trM = np.trace(M, axis1=-2, axis2=-1)                       # (t, 6)
+    Ci = np.linalg.inv(C)
+    CiM = np.einsum("tij,tkjl->tkil", Ci, M)                    # C^-1 M_k
+    t = np.trace(CiM, axis1=-2, axis2=-1)
+    Jk = 0.5 * J[:, None] * t
+    Jkl = 0.25 * J[:, None, None] * t[:, :, None] * t[:, None, :] \
+        - 0.5 * J[:, None, None] * np.einsum("tkij,tlji->tkl", CiM, CiM)
+    w = 1.0 / (IC + 1.0)
+    g = mu / 2.0 * trM * (1.0 - w)[:, None] + lam * (J - a)[:, None] * Jk
+    H = mu / 2.0 * (w * w)[:, None, None] * trM[:, :, None] * trM[:, None, :] \
+        + lam * (Jk[:, :, None] * Jk[:, None, :] + (J - a)[:, None, None] * Jkl)
+    return snh_density(IC, J, lam, mu), g, H, C
 
 
 def grad_s(x: np.ndarray, tets: np.ndarray) -> np.ndarray:
@@ -119,18 +169,21 @@ def hess_s() -> np.ndarray:
     return out
 
 
-def element_energy(x, tets, V, D2, q, lam, mu, chi=None) -> np.ndarray:
-    """chi_e V_e Psi_e (Eq. 25 with Eq. 37), per tet."""
-    s = squared_edge_lengths(x, tets)
-    C = cauchy_green_lsq(s, D2, q)
-    psi = V * stvk_density(C, lam, mu)
+def element_energy(x, tets, V, D2, q, lam, mu, chi=None, energy: str = "stvk") -> np.ndarray:
+    """chi_e V_e Psi_e (Eq. 25 with Eq. 37 or Eq. 35), per tet."""
+    if energy == "stvk":
+        s = squared_edge_lengths(x, tets)
+        C = cauchy_green_lsq(s, D2, q)
+        psi = V * stvk_density(C, lam, mu)
+    else:
+        psi = V * edge_derivatives(x, tets, D2, q, lam, mu, energy)[0]
     return psi if chi is None else chi * psi
 
 
-def element_forces(x, tets, V, D2, q, lam, mu, chi=None) -> np.ndarray:
+def element_forces(x, tets, V, D2, q, lam, mu, chi=None, energy: str = "stvk") -> np.ndarray:
     """Restoring nodal forces of every tet (t, 4, 3) by Eq. 12, times chi (Eq. 32):
     f_i = 2 V chi sum_{j != i} g_ij (x_j - x_i)."""
-    _, g, _, _ = edge_derivatives(x, tets, D2, q, lam, mu)
+    _, g, _, _ = edge_derivatives(x, tets, D2, q, lam, mu, energy)
     P = x[np.asarray(tets, np.int64)]
     f = np.zeros_like(P)
     for k, (a, b) in enumerate(LOCAL_EDGES):
@@ -142,10 +195,10 @@ def element_forces(x, tets, V, D2, q, lam, mu, chi=None) -> np.ndarray:
     return f
 
 
-def element_tangent(x, tets, V, D2, q, lam, mu, chi=None) -> np.ndarray:
+def element_tangent(x, tets, V, D2, q, lam, mu, chi=None, energy: str = "stvk") -> np.ndarray:
     """12x12 element tangent (Eq. 10 / Eq. 33), i.e. the Hessian of V Psi in the
     node positions: V [ sum_kl H_kl ds_k ds_l^T + sum_k g_k d2 s_k ], times chi."""
-    _, g, H, _ = edge_derivatives(x, tets, D2, q, lam, mu)
+    _, g, H, _ = edge_derivatives(x, tets, D2, q, lam, mu, energy)
     Gs = grad_s(x, tets)
     K = np.einsum("tkl,tka,tlb->tab", H, Gs, Gs) + np.einsum("tk,kab->tab", g, hess_s())
     K *= V[:, None, None]

@@ -50,6 +50,7 @@ class Material:
     shear_coef: float = 2.0           # 2: tensor n.S.n; 1: Eq. 16 as printed
     average_degraded: bool = True     # Eq. 20 averages chi_j S_j (True) or S_j
     mass: str = "lumped"              # "lumped" (row sums of Eq. 5) or "consistent" (Eq. 5)
+    energy: str = "stvk"              # "stvk" (Eq. 37) or "snh" (Eq. 35, squared reading)
 
 
 @dataclasses.dataclass
@@ -96,7 +97,10 @@ class Model:
         """Per-tet S (Voigt, Eq. 14) and local edge-normal stress sigma_f = T S (Eq. 18)."""
         s = elastic.squared_edge_lengths(x, self.tets)
         C = elastic.cauchy_green_lsq(s, self.D2, self.q)
-        S = damage.stress_voigt(C, self.lam, self.mu)
+        J = None
+        if self.mat.energy == "snh":
+            J = elastic.orientation(x, self.tets, self.q) * np.sqrt(np.linalg.det(C))
+        S = damage.stress_voigt(C, self.lam, self.mu, self.mat.energy, J)
         T = damage.projection_T(x, self.tets, self.mat.shear_coef)
         return S, T, np.einsum("tkc,tc->tk", T, S)
 
@@ -120,8 +124,8 @@ class Model:
     # ---- system (Eq. 2, 32-34) ---------------------------------------------
     def assemble(self, x, chi):
         """Global K* = sum chi k_e (Eq. 34, CSR) and f* = sum chi f_e (Eq. 32)."""
-        Ke = elastic.element_tangent(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi)
-        fe = elastic.element_forces(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi)
+        Ke = elastic.element_tangent(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi, self.mat.energy)
+        fe = elastic.element_forces(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi, self.mat.energy)
         dof = (3 * self.tets[:, :, None] + np.arange(3)).reshape(-1, 12)
         rows = np.repeat(dof, 12, axis=1).ravel()
         cols = np.tile(dof, (1, 12)).ravel()
