@@ -61,6 +61,7 @@ enum { GF_FP64 = 0, GF_MIXED = 1 };
 enum { GF_PRECOND_BJACOBI = 0 };
 enum { GF_ASSEMBLY_GATHER = 0, GF_ASSEMBLY_COLOUR = 1 };
 enum { GF_MASS_LUMPED = 0, GF_MASS_CONSISTENT = 1 };
+enum { GF_ENERGY_STVK = 0, GF_ENERGY_SNH = 1 };
 
 /* Material and damage parameters (Sec. 3.1, 3.3, 5.2). */
 typedef struct gf_material {
@@ -77,6 +78,11 @@ typedef struct gf_material {
   int32_t mass_matrix;   /* GF_MASS_LUMPED (0, default): row sums of Eq. 5, rho V_e / 4 per node and
                             tet; GF_MASS_CONSISTENT: Eq. 5 as it stands, rho V_e (1 + delta_ab) / 20
                             between the nodes a, b of a tet (same block pattern as K) */
+  int32_t energy;        /* GF_ENERGY_STVK (0, default): Eq. 37; GF_ENERGY_SNH: the stable
+                            Neo-Hookean energy of Eq. 35 with (J - a)^2, a = 1 + mu/lam - mu/(4 lam),
+                            J the signed det F; needs 0 < nu < 0.5, GF_FP64, two-phase assembly.
+                            The damage criterion then uses its S = 2 dPsi/dC (Eq. 14). */
+  int32_t reserved;      /* set to 0 */
 } gf_material;
 
 typedef void* (*gf_alloc_fn)(size_t bytes, void* ctx);

@@ -278,9 +278,10 @@ bool material_ok(const gf_material& M) {
   if (!(M.young > 0) || !(M.poisson > -1.0 && M.poisson < 0.5) || !(M.density > 0) || !(M.radius >= 0) ||
       std::isnan(M.threshold) || !(M.alpha >= 0) || !(M.beta >= 0) || (M.shear_coef != 1 && M.shear_coef != 2) ||
       (M.driver_mode != GF_DRIVER_STRAIN && M.driver_mode != GF_DRIVER_STRESS) ||
-      (M.mass_matrix != GF_MASS_LUMPED && M.mass_matrix != GF_MASS_CONSISTENT)) {
+      (M.mass_matrix != GF_MASS_LUMPED && M.mass_matrix != GF_MASS_CONSISTENT) ||
+      (M.energy != GF_ENERGY_STVK && M.energy != GF_ENERGY_SNH) || (M.energy == GF_ENERGY_SNH && !(M.poisson > 0.0))) {
     set_last_error("invalid material (need E > 0, -1 < nu < 0.5, rho > 0, R_d >= 0, alpha, beta >= 0, shear_coef 1|2, "
-                   "mass_matrix lumped|consistent)");
+                   "mass_matrix lumped|consistent, energy StVK|SNH (SNH: nu > 0))");
     return false;
   }
   return true;
@@ -355,6 +356,10 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   }
   const gf_material& M = *mat;
   if (!material_ok(M)) return GF_BAD_ARG;
+  if (M.energy == GF_ENERGY_SNH && opt.precision == GF_MIXED) {
+    set_last_error("the stable Neo-Hookean energy is built for GF_FP64 meshes only");
+    return GF_UNSUPPORTED;
+  }
   int dev = opt.device;
   if (dev < 0) {
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -403,6 +408,8 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   m->mt.kappa32 = float(m->mt.kappa);
   m->mt.young32 = float(m->mt.young);
   m->mt.inv_young32 = float(1.0 / m->mt.young);
+  m->mt.energy = M.energy;
+  m->mt.snh_a = 1.0 + mu / lam - mu / (4.0 * lam);
 
   HostMesh& hm = m->hm;
   DevMesh& d = m->dm;
@@ -711,6 +718,10 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
   const gf::Material& mt = m->mt;
   const StepScalars sp = step_scalars(mt, dt, has_fext, n_pinned, has_pvel);
   const int64_t N = d.N;
+  if (mt.energy == GF_ENERGY_SNH && m->tune.assembly == GF_ASSEMBLY_COLOUR) {
+    set_last_error("the colour-ordered assembly is built for the StVK energy only");
+    return GF_UNSUPPORTED;
+  }
   if (!(mt.radius > 0.0)) d.sig_bar = d.sig_in;   // R_d = 0: the tet alone (local criterion)
   { Prof p(m, kPStress); L += launch_kind(kB_tet_stress, d, mt, sp, s); }
   if (mt.radius > 0.0) {
@@ -1397,6 +1408,11 @@ gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out) {
     if (!meshes[k] || meshes[k]->device != meshes[0]->device || meshes[k]->mixed != meshes[0]->mixed) {
       set_last_error("batch: meshes must be non-NULL, on one device, with one precision");
       return GF_BAD_ARG;
+    }
+  for (int k = 0; k < n; ++k)
+    if (meshes[k]->mt.energy != GF_ENERGY_STVK) {
+      set_last_error("batches run the StVK energy (Eq. 37) only");
+      return GF_UNSUPPORTED;
     }
   DeviceGuard guard(meshes[0]->device);
   gf_batch* b = new gf_batch();

@@ -127,6 +127,8 @@ struct Material {
   int average_degraded;
   uint64_t lut;       // disconnection table of Eq. 25
   float lam32, mu32, kappa32, young32, inv_young32;
+  int energy;         // GF_ENERGY_STVK (Eq. 37) or GF_ENERGY_SNH (Eq. 35)
+  double snh_a;       // a = 1 + mu/lam - mu/(4 lam) of Eq. 35
 };
 
 // Per-step scalars of one mesh, formed on the host (no FP64 scalar work per

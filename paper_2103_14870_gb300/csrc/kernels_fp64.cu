@@ -59,6 +59,7 @@ __device__ __forceinline__ double normal_stress(const double e[3], double s, con
 // Damage: stress, non-local average, edge driver + relabel, chi
 // ---------------------------------------------------------------------------
 
+template <bool kSNH>
 __device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
@@ -80,10 +81,34 @@ __device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material
   for (int f = 0; f < 9; ++f) B[f] = m.rest[(kRestB + f) * m.T + t];
   double C[6];
   cauchy_green(s, B, C);
-  // second Piola-Kirchhoff stress of Eq. 37: lam/2 (tr C - 3) I + mu (C - I)
-  const double h = 0.5 * mt.lam * (C[0] + C[1] + C[2] - 3.0);
-  double S[6] = {h + mt.mu * (C[0] - 1.0), h + mt.mu * (C[1] - 1.0), h + mt.mu * (C[2] - 1.0),
-                 mt.mu * C[3], mt.mu * C[4], mt.mu * C[5]};
+  double S[6];
+  if constexpr (kSNH) {
+    // Eq. 35: S = mu (1 - 1/(I_C + 1)) I + lam (J - a) J C^-1 = ... + lam (J - a) / J adj(C),
+    // J = det F = det(Ds) det(B) (signed)
+    const double ds = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                      e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                      e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    const double db = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                      B[2] * (B[3] * B[7] - B[4] * B[6]);
+    const double J = ds * db, IC = C[0] + C[1] + C[2];
+    const double d0 = mt.mu * (1.0 - 1.0 / (IC + 1.0)), d1 = mt.lam * (J - mt.snh_a) / J;
+    // adjugate of the symmetric C (Voigt xx yy zz xy xz yz)
+    S[0] = d0 + d1 * (C[1] * C[2] - C[5] * C[5]);
+    S[1] = d0 + d1 * (C[0] * C[2] - C[4] * C[4]);
+    S[2] = d0 + d1 * (C[0] * C[1] - C[3] * C[3]);
+    S[3] = d1 * (C[4] * C[5] - C[3] * C[2]);
+    S[4] = d1 * (C[3] * C[5] - C[4] * C[1]);
+    S[5] = d1 * (C[3] * C[4] - C[0] * C[5]);
+  } else {
+    // second Piola-Kirchhoff stress of Eq. 37: lam/2 (tr C - 3) I + mu (C - I)
+    const double h = 0.5 * mt.lam * (C[0] + C[1] + C[2] - 3.0);
+    S[0] = h + mt.mu * (C[0] - 1.0);
+    S[1] = h + mt.mu * (C[1] - 1.0);
+    S[2] = h + mt.mu * (C[2] - 1.0);
+    S[3] = mt.mu * C[3];
+    S[4] = mt.mu * C[4];
+    S[5] = mt.mu * C[5];
+  }
   const double w = mt.average_degraded ? m.chi[t] : 1.0;
   double2* si = reinterpret_cast<double2*>(m.sig_in + 6 * t);
   si[0] = make_double2(w * S[0], w * S[1]);
@@ -98,12 +123,15 @@ __device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material
   so[2] = make_double2(sf[4], sf[5]);
 }
 __global__ void __launch_bounds__(kThreads) k_tet_stress(DevMesh m, Material mt, StepScalars sp) {
-  tet_stress_body(m, mt, sp, blockIdx.x, gridDim.x);
+  tet_stress_body<false>(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) k_tet_stress_snh(DevMesh m, Material mt, StepScalars sp) {
+  tet_stress_body<true>(m, mt, sp, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kThreads) kb_tet_stress(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_tet_stress, blockIdx.x, bid, nb);
-  tet_stress_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+  tet_stress_body<false>(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);   // batches run the StVK energy
 }
 
 // Eq. 20 sum: thread per tet, neighbour lists in SELL-32 layout (coalesced
@@ -397,6 +425,122 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
 // external force and mass damping.
 constexpr int kElemW64 = 104;
 
+// Stable Neo-Hookean element (Eq. 35, squared reading) from the deformation
+// gradient F = Ds B (B = Dm^-1), with the gradient operator G_0 = -(B_0 + B_1 +
+// B_2), G_{m+1} = B_m (rows of B), dF_ij / dx_{a,c} = delta_ic G_aj:
+//   P = c1 F + c2 cof F,  c1 = mu (1 - w), c2 = lam (J - a), w = 1 / (I_C + 1);
+//   f_a = -V P G_a = -V (c1 u_a + c2 z_a),  u_a = F G_a, z_a = cof(F) G_a;
+//   K_ab = V [c1 (G_a . G_b) I + 2 mu w^2 u_a u_b^T + lam z_a z_b^T + c2 [t]_x],
+//   t_m = det[G_a; G_b; F_m] (F_m row m of F), [t]_x (c, d) = eps_cdm t_m:
+// the contraction of d2Psi/dF2 with G_a, G_b in closed form.  Output as the
+// StVK body: ten upper blocks of (dt beta + dt^2) chi K and the rhs shares
+// dt chi (f_a - (beta + dt) (K v)_a).
+__device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt, const StepScalars& sp, int64_t t,
+                                           double* out, double chi) {
+  const double dt = sp.dt, beta = mt.beta, mu = mt.mu, lam = mt.lam;
+  const int4 n = m.tets[t];
+  const int nid[4] = {n.x, n.y, n.z, n.w};
+  double Px[4][3], U[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ld3(m.x, nid[a], Px[a]);
+    ld3(m.v, nid[a], U[a]);
+  }
+  double B[9];
+#pragma unroll
+  for (int f = 0; f < 9; ++f) B[f] = m.rest[(kRestB + f) * m.T + t];
+  const double V = m.rest[size_t(kRestV) * m.T + t];
+  double G[4][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    G[1][j] = B[j];
+    G[2][j] = B[3 + j];
+    G[3][j] = B[6 + j];
+    G[0][j] = -(B[j] + B[3 + j] + B[6 + j]);
+  }
+  double F[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      F[i][j] = (Px[1][i] - Px[0][i]) * B[j] + (Px[2][i] - Px[0][i]) * B[3 + j] + (Px[3][i] - Px[0][i]) * B[6 + j];
+  double cof[3][3];
+  cof[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+  cof[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+  cof[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+  cof[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+  cof[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+  cof[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+  cof[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+  cof[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+  cof[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  const double J = F[0][0] * cof[0][0] + F[0][1] * cof[0][1] + F[0][2] * cof[0][2];
+  double IC = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) IC += F[i][j] * F[i][j];
+  const double w = 1.0 / (IC + 1.0);
+  const double c1 = mu * (1.0 - w), c2 = lam * (J - mt.snh_a), c3 = 2.0 * mu * w * w;
+  double u[4][3], z[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      u[a][c] = F[c][0] * G[a][0] + F[c][1] * G[a][1] + F[c][2] * G[a][2];
+      z[a][c] = cof[c][0] * G[a][0] + cof[c][1] * G[a][1] + cof[c][2] * G[a][2];
+    }
+  const double sK = (dt * beta + dt * dt) * chi, cv = beta + dt;
+  double Kv[4][3] = {};
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int a = 0; a <= b; ++a) {
+      const double gg = G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2];
+      double tm[3] = {0.0, 0.0, 0.0};
+      if (a != b) {
+        const double x0 = G[a][1] * G[b][2] - G[a][2] * G[b][1];
+        const double x1 = G[a][2] * G[b][0] - G[a][0] * G[b][2];
+        const double x2 = G[a][0] * G[b][1] - G[a][1] * G[b][0];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) tm[mm] = x0 * F[mm][0] + x1 * F[mm][1] + x2 * F[mm][2];
+      }
+      double blk[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) blk[r][c] = V * (c3 * u[a][r] * u[b][c] + lam * z[a][r] * z[b][c]);
+      const double dg = V * c1 * gg;
+      blk[0][0] += dg;
+      blk[1][1] += dg;
+      blk[2][2] += dg;
+      const double s2 = V * c2;
+      blk[0][1] += s2 * tm[2];
+      blk[1][0] -= s2 * tm[2];
+      blk[0][2] -= s2 * tm[1];
+      blk[2][0] += s2 * tm[1];
+      blk[1][2] += s2 * tm[0];
+      blk[2][1] -= s2 * tm[0];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        Kv[a][r] += blk[r][0] * U[b][0] + blk[r][1] * U[b][1] + blk[r][2] * U[b][2];
+        if (a != b) Kv[b][r] += blk[0][r] * U[a][0] + blk[1][r] * U[a][1] + blk[2][r] * U[a][2];
+      }
+      double* dst = out + 9 * blk_q(a, b);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[3 * r + c] = sK * blk[r][c];
+    }
+  const double sf = dt * chi;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[90 + 3 * a + c] = sf * (-V * (c1 * u[a][c] + c2 * z[a][c]) - cv * Kv[a][c]);
+  out[102] = 0.0;
+  out[103] = 0.0;
+}
+
 __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const double dt = sp.dt, beta = mt.beta;
 
@@ -505,13 +649,28 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
   out[102] = 0.0;
   out[103] = 0.0;
 }
+__device__ __forceinline__ void elem_snh64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid,
+                                                unsigned nb) {
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
+  double* out = m.ebuf + kElemW64 * t;
+  const double chi = m.chi[t];
+  if (chi == 0.0) {
+    for (int q = 0; q < kElemW64; ++q) out[q] = 0.0;
+    return;
+  }
+  elem_snh64(m, mt, sp, t, out, chi);
+}
 __global__ void __launch_bounds__(128) k_elem64(DevMesh m, Material mt, StepScalars sp) {
   elem64_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(128) k_elem_snh64(DevMesh m, Material mt, StepScalars sp) {
+  elem_snh64_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(128) kb_elem64(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_elem64, blockIdx.x, bid, nb);
-  elem64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+  elem64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);   // batches run the StVK energy
 }
 
 // Phase 2 of the assembly: each matrix entry and rhs component is the sum, in
@@ -887,12 +1046,18 @@ int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepS
   const LaunchDims d = launch_dims(kind, m, mt, sp);
   if (d.blocks == 0) return 0;
   switch (kind) {
-    case kB_tet_stress: k_tet_stress<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_tet_stress:
+      if (mt.energy == GF_ENERGY_SNH) k_tet_stress_snh<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
+      else k_tet_stress<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
+      break;
     case kB_nonlocal: k_nonlocal<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_edge_driver: k_edge_driver<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_tet_chi: k_tet_chi<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_node_init: k_node_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_elem64: k_elem64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_elem64:
+      if (mt.energy == GF_ENERGY_SNH) k_elem_snh64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
+      else k_elem64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
+      break;
     case kB_gather64: k_gather64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_set_pinned: k_set_pinned<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_pcg_init: k_pcg_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;

@@ -37,7 +37,8 @@ class Material(ctypes.Structure):
     _fields_ = [("young", ctypes.c_double), ("poisson", ctypes.c_double), ("density", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("threshold", ctypes.c_double),
                 ("radius", ctypes.c_double), ("driver_mode", ctypes.c_int32), ("shear_coef", ctypes.c_int32),
-                ("average_degraded", ctypes.c_int32), ("mass_matrix", ctypes.c_int32)]
+                ("average_degraded", ctypes.c_int32), ("mass_matrix", ctypes.c_int32), ("energy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -183,10 +184,10 @@ def _one_kind(*kinds) -> int:
 
 
 def material(young, poisson, density, threshold=math.inf, radius=0.0, alpha=0.0, beta=0.0,
-             driver_mode=DRIVER_STRAIN, shear_coef=2, average_degraded=True, mass_matrix=0) -> Material:
-    """gf_material; mass_matrix MASS_LUMPED (0) or MASS_CONSISTENT (1)."""
+             driver_mode=DRIVER_STRAIN, shear_coef=2, average_degraded=True, mass_matrix=0, energy=0) -> Material:
+    """gf_material; mass_matrix MASS_LUMPED (0) or MASS_CONSISTENT (1); energy ENERGY_STVK (0) or ENERGY_SNH (1)."""
     return Material(young, poisson, density, alpha, beta, threshold, radius, driver_mode, shear_coef,
-                    1 if average_degraded else 0, int(mass_matrix))
+                    1 if average_degraded else 0, int(mass_matrix), int(energy), 0)
 
 
 class Mesh:
@@ -500,6 +501,7 @@ def mesh_create(nodes, tets, mat: Material, precision: int = FP64, cg_rtol: floa
 
 GNN_START, GNN_PRECOND = 1, 2
 MASS_LUMPED, MASS_CONSISTENT = 0, 1
+ENERGY_STVK, ENERGY_SNH = 0, 1
 GNN_TENSOR_CORES, GNN_FP32_FMA = 0, 1
 
 # Parameter tensors of the learned start / preconditioner network, in storage
