@@ -26,6 +26,13 @@ linearised step above): J_k = M + dt B_k + dt^2 K*(x^k), J_k d = -r(v^k),
 v^{k+1} = v^k + d, with the damping matrix taken at the current iterate and
 chi frozen for the step.  ``mass="consistent"`` uses the element masses of
 Eq. 5 as they stand instead of their row sums.
+
+``quasistatic_step`` is the paper's quasi-static solve (Eq. 36, Sec. 4.3): no
+mass or damping, the equilibrium f*(x) + f_ext = 0 on free DOFs found by
+Newton's method with a backtracking line search on the total energy
+E(x) = sum_e chi_e V_e Psi_e(x) - f_ext . x.  The damage update comes first, at
+the start-of-step positions (the order of Algorithm 1), then the pinned nodes
+move to their prescribed positions and chi stays frozen for the solve.
 """
 from __future__ import annotations
 
@@ -229,3 +236,58 @@ class Model:
         info = {"driver": drv, "labels": labels, "chi": chi, "sig_star": sig_star, "dv": v_new - state.v,
                 "newton_res": res, "final_res": float(np.linalg.norm(r[free])), "iters": iters_cg}
         return State(x_new, v_new, labels, chi), info
+
+    def total_energy(self, x, chi, f_ext, with_scale=False):
+        """E(x) = sum_e chi_e V_e Psi_e(x) - f_ext . x (the quasi-static objective);
+        with_scale also returns sum |chi V Psi| + sum |f_i x_i|, the magnitude that
+        sets the rounding of E."""
+        psi = elastic.element_energy(x, self.tets, self.V, self.D2, self.q, self.lam, self.mu, chi, self.mat.energy)
+        fx = np.asarray(f_ext, np.float64).ravel() * x.ravel()
+        e = float(psi.sum() - fx.sum())
+        return (e, float(np.abs(psi).sum() + np.abs(fx).sum())) if with_scale else e
+
+    def quasistatic_step(self, state: State, f_ext, pinned=None, pinned_pos=None, max_newton: int = 50,
+                         rtol: float = 1e-10, c_armijo: float = 1e-4):
+        """Quasi-static load step (module docstring).  Newton direction K*_ff d = r_f
+        with r = f_ext + f*(x); step length by halving from 1 until
+        E(x + a d) <= E(x) - c a r.d.  Stops when |r_f| <= rtol |r_f at the start|.
+        Returns (new State with v = 0, info)."""
+        drv, labels, chi, sig_star = self.damage_update(state)
+        n = self.n_nodes
+        x = state.x.copy()
+        fixed = np.zeros(n, bool)
+        if pinned is not None and len(pinned):
+            pinned = np.asarray(pinned, np.int64)
+            fixed[pinned] = True
+            if pinned_pos is not None:
+                x[pinned] = np.asarray(pinned_pos, np.float64).reshape(-1, 3)
+        free = np.repeat(~fixed, 3)
+        fe = np.asarray(f_ext, np.float64).ravel()
+        res, alphas, energies = [], [], []
+        r0 = None
+        for k in range(max_newton):
+            K, f = self.assemble(x, chi)
+            r = (fe + f)[free]
+            rn = float(np.linalg.norm(r))
+            res.append(rn)
+            if r0 is None:
+                r0 = rn
+            if rn <= rtol * r0 or rn == 0.0:
+                break
+            d = np.zeros(3 * n)
+            d[free] = solve.direct(K[free][:, free].tocsr(), r)
+            slope = float(r @ d[free])
+            e0, scale = self.total_energy(x, chi, fe, with_scale=True)
+            energies.append(e0)
+            a = 1.0
+            while a > 2.0 ** -30:
+                if c_armijo * a * slope <= 1e-12 * scale:
+                    break
+                if self.total_energy(x + a * d.reshape(-1, 3), chi, fe) <= e0 - c_armijo * a * slope:
+                    break
+                a *= 0.5
+            alphas.append(a)
+            x = x + a * d.reshape(-1, 3)
+        info = {"driver": drv, "labels": labels, "chi": chi, "sig_star": sig_star, "newton_res": res,
+                "alphas": alphas, "energies": energies}
+        return State(x, np.zeros_like(state.v), labels, chi), info
