@@ -197,6 +197,25 @@ gf_status gf_solver_set(gf_mesh* mesh, double cg_rtol, int32_t cg_maxit);
  * for batches). */
 gf_status gf_newton_set(gf_mesh* mesh, int32_t max_iters, double rtol);
 
+/* Quasi-static load step (Eq. 36; the paper's quasi-static runs solve it by
+ * Newton's method with a line search, Sec. 4.3).  No mass or damping.  Order:
+ * the damage update at the current positions (stress, Eq. 20 average,
+ * relabel, chi, as in gf_step), then the pinned nodes move to pinned_pos
+ * (host or device float64 [3 * n_pinned] following `mem`; NULL keeps them
+ * where they are), then Newton iterations on f*(x) + f_ext = 0 over the free
+ * DOFs with chi frozen: K* d = f_ext + f* solved by the PCG to cg_rtol, step
+ * length halved from 1 until the total energy
+ * E = sum_e chi_e V_e Psi_e - f_ext . x meets the Armijo condition with
+ * c = 1e-4 (or the decrease asked for is below 1e-12 of the magnitude of E's
+ * terms, where E cannot resolve it).  Stops when |f_ext + f*| on free DOFs is
+ * <= rtol times its value at the first iteration, or after max_newton
+ * (1..1000) iterations (GF_CG_MAXITER).  Velocities are zero afterwards.
+ * stats (nullable): newton_iters, cg_iters summed, rel_res = the last
+ * residual ratio, damage counts.  GF_FP64 meshes only. */
+gf_status gf_quasistatic_step(gf_mesh* mesh, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
+                              const double* pinned_pos, int32_t mem, int32_t max_newton, double rtol,
+                              gf_step_stats* stats);
+
 /* Current positions / velocities, float64 [3*n_nodes]. */
 gf_status gf_positions_get(gf_mesh* mesh, double* x, int32_t mem);
 gf_status gf_velocities_get(gf_mesh* mesh, double* v, int32_t mem);

@@ -24,6 +24,7 @@ StepScalars step_scalars(const Material& mt, double dt, bool has_fext, int64_t n
   sp.has_fext = has_fext ? 1 : 0;
   sp.has_pvel = has_pvel ? 1 : 0;
   sp.n_pinned = n_pinned;
+  sp.mscale = 1.0;
   return sp;
 }
 
@@ -149,6 +150,9 @@ struct gf_mesh {
   int newton_done = 1;        // iterations of the last step
   double newton_res = 0.0;    // |r(v^k)| / |b^0| at the start of the last iteration (0 after one)
   int newton_cg_total = 0;    // CG iterations of the last step over its Newton iterations
+  double* qs_x = nullptr;     // quasi-static: trial positions [3N]
+  double* qs_zero = nullptr;  // quasi-static: zero velocities [3N]
+  double* qs_out = nullptr;   // quasi-static: E, |E| scale, slope [4]
   int64_t launches = 0;
   int64_t nbr_pairs = 0;
 
@@ -965,6 +969,164 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
   if (status != GF_OK && status != GF_BAD_ARG)
     set_last_error(std::string("step: ") + gf_status_string(status));
   return status;
+}
+
+gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
+                              const double* pinned_pos, int32_t mem, int32_t max_newton, double rtol,
+                              gf_step_stats* stats) {
+  if (!m || !valid_mem(mem) || n_pinned < 0 || n_pinned > m->dm.N || (n_pinned > 0 && !pinned) ||
+      max_newton < 1 || max_newton > 1000 || !(rtol >= 0) || !std::isfinite(rtol) || (pinned_pos && n_pinned == 0)) {
+    set_last_error("bad quasi-static step arguments (need 1 <= max_newton <= 1000, rtol >= 0, pinned when "
+                   "n_pinned > 0, pinned_pos only with pinned nodes)");
+    return GF_BAD_ARG;
+  }
+  if (m->mixed) {
+    set_last_error("the quasi-static step is built for GF_FP64 meshes only");
+    return GF_UNSUPPORTED;
+  }
+  if (mem == GF_MEM_HOST)
+    for (int64_t i = 0; i < n_pinned; ++i)
+      if (pinned[i] < 0 || pinned[i] >= m->dm.N) {
+        set_last_error("pinned node id out of range");
+        return GF_BAD_ARG;
+      }
+  DeviceGuard guard(m->device);
+  cudaStream_t s = m->stream;
+  DevMesh d = m->dm;
+  const int64_t N = d.N;
+  gf_status st = GF_OK;
+  if (!m->qs_x) {
+    if ((st = scratch(m, 3 * N, &m->qs_x)) || (st = scratch(m, 3 * N, &m->qs_zero)) || (st = scratch(m, 4, &m->qs_out)))
+      return st;
+    GF_CK(cudaMemsetAsync(m->qs_zero, 0, sizeof(double) * 3 * N, s));
+  }
+  GF_CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long) * kCntMax, s));
+  if (f_ext && mem == GF_MEM_HOST) GF_CK(cudaMemcpyAsync(d.f_ext, f_ext, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+  else if (f_ext) d.f_ext = const_cast<double*>(f_ext);
+  const double* pos = nullptr;
+  if (n_pinned > 0) {
+    if (mem == GF_MEM_HOST) {
+      GF_CK(cudaMemcpyAsync(d.pin_ids, pinned, sizeof(int32_t) * n_pinned, cudaMemcpyHostToDevice, s));
+      if (pinned_pos) {
+        GF_CK(cudaMemcpyAsync(d.pin_vel, pinned_pos, sizeof(double) * 3 * n_pinned, cudaMemcpyHostToDevice, s));
+        pos = d.pin_vel;
+      }
+    } else {
+      d.pin_ids = const_cast<int32_t*>(pinned);
+      pos = pinned_pos;
+    }
+  }
+  int64_t L = 0;
+  // 1. damage at the start-of-step positions (Algorithm 1 order), chi frozen afterwards
+  const gf::Material& mt = m->mt;
+  const StepScalars sp0 = step_scalars(mt, 1.0, false, 0, false);
+  if (!(mt.radius > 0.0)) d.sig_bar = d.sig_in;
+  { Prof p(m, kPStress); L += launch_kind(kB_tet_stress, d, mt, sp0, s); }
+  if (mt.radius > 0.0) {
+    Prof p(m, kPNonlocal);
+    L += launch_kind(kB_nonlocal, d, mt, sp0, s);
+  }
+  { Prof p(m, kPEdge); L += launch_kind(kB_edge_driver, d, mt, sp0, s); }
+  { Prof p(m, kPChi); L += launch_kind(kB_tet_chi, d, mt, sp0, s); }
+  // 2. the pinned nodes move to their prescribed positions
+  if (pos) L += launch_qs_set_pins(d, d.pin_ids, pos, n_pinned, s);
+  // 3. Newton on f* + f_ext = 0 (free DOFs): the dynamic system with no mass, no damping, dt = 1, v = 0
+  gf::Material mq = mt;
+  mq.alpha = 0.0;
+  mq.beta = 0.0;
+  StepScalars sq = step_scalars(mq, 1.0, f_ext != nullptr, n_pinned, false);
+  sq.mscale = 0.0;
+  DevMesh dq = d;
+  dq.v = m->qs_zero;
+  GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
+  double r0 = -1.0, rel = 0.0, h_out[4];
+  int cg_total = 0, k = 0, status = GF_OK;
+  const double c_armijo = 1e-4;
+  for (k = 0; k < max_newton; ++k) {
+    { Prof p(m, kPAssemble); L += launch_kind(kB_elem64, dq, mq, sq, s); }
+    { Prof p(m, kPGather); L += launch_kind(kB_gather64, dq, mq, sq, s); }
+    PcgState init{};
+    init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+    init.maxit = m->opt.cg_maxit;
+    *m->h_pcg = init;
+    GF_CK(cudaMemcpyAsync(d.pcg, m->h_pcg, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * N, s));
+    L += launch_kind(kB_set_pinned, dq, mq, sq, s);
+    { Prof p(m, kPPcgInit); L += launch_kind(kB_pcg_init, dq, mq, sq, s); }
+    GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaStreamSynchronize(s));
+    const double rn = std::sqrt(m->h_pcg->bb);   // |f_ext + f*| on free DOFs
+    if (r0 < 0) r0 = rn;
+    rel = r0 > 0 ? rn / r0 : 0.0;
+    if (!std::isfinite(rn)) {
+      status = GF_NAN;
+      break;
+    }
+    if (rn == 0.0 || rn <= rtol * r0) break;
+    int launched = 0;
+    int chunk = std::max(1, std::min(m->last_iters + 1, 64));
+    for (;;) {
+      for (int j = 0; j < chunk; ++j, ++launched) {
+        { Prof p(m, kPSpmv, launched); L += launch_kind(kB_pcg_spmv, dq, mq, sq, s); }
+        { Prof p(m, kPPcgUpdate, launched); L += launch_kind(kB_pcg_update, dq, mq, sq, s); }
+        { Prof p(m, kPPcgP, launched); L += launch_kind(kB_pcg_p, dq, mq, sq, s); }
+      }
+      GF_CK(cudaGetLastError());
+      GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      GF_CK(cudaStreamSynchronize(s));
+      if (m->h_pcg->done || launched >= m->opt.cg_maxit) break;
+      chunk = 8;
+    }
+    cg_total += m->h_pcg->iters;
+    m->last_iters = m->h_pcg->iters;
+    if (m->h_pcg->status != GF_OK) {
+      status = m->h_pcg->status;
+      break;
+    }
+    // line search on E(x) = sum chi V Psi - f_ext . x
+    L += launch_qs_slope(dq, m->qs_out, s);
+    L += launch_qs_energy(dq, mq, d.x, f_ext ? d.f_ext : nullptr, m->qs_out, s);
+    GF_CK(cudaMemcpyAsync(h_out, m->qs_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaStreamSynchronize(s));
+    const double e0 = h_out[0], scale = h_out[1], slope = h_out[2];
+    double a = 1.0;
+    while (a > std::ldexp(1.0, -30)) {
+      if (c_armijo * a * slope <= 1e-12 * scale) break;   // below what E resolves: take the step
+      L += launch_qs_trial(3 * N, d.x, d.dv, a, m->qs_x, s);
+      L += launch_qs_energy(dq, mq, m->qs_x, f_ext ? d.f_ext : nullptr, m->qs_out, s);
+      GF_CK(cudaMemcpyAsync(h_out, m->qs_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+      GF_CK(cudaStreamSynchronize(s));
+      if (h_out[0] <= e0 - c_armijo * a * slope) break;
+      a *= 0.5;
+    }
+    L += launch_qs_trial(3 * N, d.x, d.dv, a, m->qs_x, s);
+    GF_CK(cudaMemcpyAsync(d.x, m->qs_x, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  }
+  GF_CK(cudaMemsetAsync(d.v, 0, sizeof(double) * 3 * N, s));   // quasi-static: at rest after the step
+  GF_CK(cudaGetLastError());
+  GF_CK(cudaMemcpyAsync(m->h_cnt, d.counters, sizeof(unsigned long long) * kCntMax, cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaStreamSynchronize(s));
+  m->assembled = true;
+  m->launches += L;
+  prof_collect(m, 1 << 30, false);
+  if (status == GF_OK && k >= max_newton && rel > rtol) status = GF_CG_MAXITER;
+  if (m->h_cnt[kCntBadPin] != 0) {
+    set_last_error("pinned node id out of range (skipped)");
+    status = GF_BAD_ARG;
+  }
+  if (stats) {
+    stats->status = status;
+    stats->cg_iters = cg_total;
+    stats->rel_res = rel;
+    stats->n_broken = int64_t(m->h_cnt[kCntBroken]);
+    stats->n_new_broken = int64_t(m->h_cnt[kCntNewBroken]);
+    stats->n_chi_zero = int64_t(m->h_cnt[kCntChiZero]);
+    stats->refine_sweeps = 0;
+    stats->newton_iters = k;
+  }
+  if (status != GF_OK && status != GF_BAD_ARG)
+    set_last_error(std::string("quasi-static step: ") + gf_status_string(gf_status(status)));
+  return gf_status(status);
 }
 
 gf_status gf_positions_get(gf_mesh* m, double* x, int32_t mem) {

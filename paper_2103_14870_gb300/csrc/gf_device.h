@@ -139,6 +139,7 @@ struct StepScalars {
   int has_fext, has_pvel;
   int learned;                        // pcg_init keeps the preconditioner, start and |b_free|^2 already set
   int warm;                           // pcg_init starts from the dv in place (Newton iterations after the first)
+  double mscale;                      // factor on the mass in the matrix (1; 0 for the quasi-static system)
   int64_t n_pinned;
 };
 
@@ -204,5 +205,12 @@ int launch_kind(int kind, const DevMesh& m, const Material& mt, const StepScalar
 int launch_assemble_colour(const DevMesh& m, const Material& mt, double dt, int t0, int t1, cudaStream_t s);
 // Newton iterate k >= 1 of the FP64 step: xk = x + dt (v + dv), w = v - dt (v + dv) / (beta + dt)
 int launch_newton_prep(const DevMesh& m, const Material& mt, double dt, double* xk, double* w, cudaStream_t s);
+// Quasi-static step pieces (FP64): total energy and its magnitude at positions x into out[0..1];
+// r . d over free DOFs (r = m.rhs, d = m.dv) into out[2]; xt = x + a d; pinned positions
+int launch_qs_energy(const DevMesh& m, const Material& mt, const double* x, const double* f_ext, double* out,
+                     cudaStream_t s);
+int launch_qs_slope(const DevMesh& m, double* out, cudaStream_t s);
+int launch_qs_trial(int64_t n, const double* x, const double* d, double a, double* xt, cudaStream_t s);
+int launch_qs_set_pins(const DevMesh& m, const int32_t* ids, const double* pos, int64_t n_pinned, cudaStream_t s);
 
 }  // namespace gf

@@ -16,6 +16,8 @@
 #include "gf_device.h"
 #include "gf_reduce.cuh"
 
+#include <algorithm>
+
 namespace gf {
 namespace {
 
@@ -694,7 +696,7 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
       const int ent = m.sc_ent[c];
       acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
     }
-    if (m.mass_blk && (e == 0 || e == 4 || e == 8)) acc += (1.0 + dt * alpha) * m.mass_blk[slot];
+    if (m.mass_blk && (e == 0 || e == 4 || e == 8)) acc += (1.0 + dt * alpha) * m.mass_blk[slot] * sp.mscale;
     m.val[9 * slot + e] = acc;
     return;
   }
@@ -711,7 +713,7 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
       const int ent = m.sc_ent[c];
       acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : q)];
     }
-    if (q == 0 || q == 4 || q == 8) acc += (1.0 + dt * alpha) * (m.mass_blk ? m.mass_blk[slot] : mi);
+    if (q == 0 || q == 4 || q == 8) acc += (1.0 + dt * alpha) * (m.mass_blk ? m.mass_blk[slot] : mi) * sp.mscale;
     m.val[9 * int64_t(slot) + q] = acc;
   } else {
     const int c3 = q - 9;
@@ -751,6 +753,112 @@ __global__ void __launch_bounds__(kThreads) k_newton_prep(int64_t n, const doubl
   const double vk = v[i] + dv[i];
   xk[i] = x[i] + dt * vk;
   w[i] = v[i] - cw * vk;
+}
+
+// ---------------------------------------------------------------------------
+// Quasi-static load step (Eq. 36; Newton with a line search, Sec. 4.3)
+// ---------------------------------------------------------------------------
+
+// E(x) = sum_e chi_e V_e Psi_e(x) - f_ext . x and sum |chi V Psi| + sum |f_i x_i|
+// (the magnitude that sets E's rounding).  StVK: V Psi = 1/2 (s - s0)^T Hs (s - s0)
+// exactly (Eq. 37 is quadratic in s, Hs includes V); SNH: V Psi(F) of Eq. 35.
+__global__ void __launch_bounds__(kThreads) k_qs_energy(DevMesh m, Material mt, const double* __restrict__ x,
+                                                       const double* __restrict__ f_ext, double* out) {
+  double v[2] = {0.0, 0.0};
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < m.T; t += stride) {
+    const double chi = m.chi[t];
+    if (chi == 0.0) continue;
+    const int4 n = m.tets[t];
+    const int nid[4] = {n.x, n.y, n.z, n.w};
+    double P[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ld3(x, nid[a], P[a]);
+    double psi;
+    if (mt.energy == GF_ENERGY_SNH) {
+      double B[9];
+#pragma unroll
+      for (int f = 0; f < 9; ++f) B[f] = m.rest[(kRestB + f) * m.T + t];
+      double F[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          F[i][j] = (P[1][i] - P[0][i]) * B[j] + (P[2][i] - P[0][i]) * B[3 + j] + (P[3][i] - P[0][i]) * B[6 + j];
+      const double J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                       F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                       F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+      double IC = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) IC += F[i][j] * F[i][j];
+      const double V = m.rest[size_t(kRestV) * m.T + t];
+      psi = V * (0.5 * mt.mu * (IC - 3.0) + 0.5 * mt.lam * (J - mt.snh_a) * (J - mt.snh_a) -
+                 0.5 * mt.mu * log(IC + 1.0));
+    } else {
+      double ds[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        double e2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double e = P[edge_b(k)][c] - P[edge_a(k)][c];
+          e2 += e * e;
+        }
+        ds[k] = e2 - m.rest[(kRestS0 + k) * m.T + t];
+      }
+      psi = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        double hk = 0.0;
+#pragma unroll
+        for (int l = 0; l < 6; ++l)
+          hk += m.rest[(kRestH + (k <= l ? tri6(k, l) : tri6(l, k))) * m.T + t] * ds[l];
+        psi += 0.5 * ds[k] * hk;
+      }
+    }
+    v[0] += chi * psi;
+    v[1] += fabs(chi * psi);
+  }
+  if (f_ext)
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 3 * m.N; i += stride) {
+      const double fx = f_ext[i] * x[i];
+      v[0] -= fx;
+      v[1] += fabs(fx);
+    }
+  double o[2];
+  if (grid_reduce<2>(v, m.partials, m.tickets + 8, o, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
+    out[0] = o[0];
+    out[1] = o[1];
+  }
+}
+
+// r . d on free DOFs (the slope of E along the Newton direction d, r = -grad E)
+__global__ void __launch_bounds__(kThreads) k_qs_slope(DevMesh m, double* out) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x)
+    if (!m.pinned[i])
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[0] += m.rhs[3 * i + c] * m.dv[3 * i + c];
+  double o[1];
+  if (grid_reduce<1>(v, m.partials, m.tickets + 9, o, blockIdx.x, gridDim.x) && threadIdx.x == 0) out[2] = o[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_qs_trial(int64_t n, const double* __restrict__ x,
+                                                      const double* __restrict__ d, double a, double* xt) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) xt[i] = x[i] + a * d[i];
+}
+
+__global__ void __launch_bounds__(kThreads) k_qs_set_pins(DevMesh m, const int32_t* __restrict__ ids,
+                                                         const double* __restrict__ pos, int64_t n_pinned) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p >= n_pinned) return;
+  const int64_t id = ids[p];
+  if (id < 0 || id >= m.N) return;   // reported by k_set_pinned
+#pragma unroll
+  for (int c = 0; c < 3; ++c) m.x[3 * id + c] = pos[3 * p + c];
 }
 
 // ---------------------------------------------------------------------------
@@ -1027,6 +1135,29 @@ __global__ void __launch_bounds__(kThreads) kb_integrate(const BatchTab* __restr
 }
 
 }  // namespace
+
+inline unsigned qs_grid(int64_t n) {
+  const int64_t b = (n + kThreads - 1) / kThreads;
+  return unsigned(b < 1 ? 1 : (b > 4 * 152 ? 4 * 152 : b));
+}
+int launch_qs_energy(const DevMesh& m, const Material& mt, const double* x, const double* f_ext, double* out,
+                     cudaStream_t s) {
+  k_qs_energy<<<qs_grid(std::max(m.T, 3 * m.N)), kThreads, 0, s>>>(m, mt, x, f_ext, out);
+  return 1;
+}
+int launch_qs_slope(const DevMesh& m, double* out, cudaStream_t s) {
+  k_qs_slope<<<qs_grid(m.N), kThreads, 0, s>>>(m, out);
+  return 1;
+}
+int launch_qs_trial(int64_t n, const double* x, const double* d, double a, double* xt, cudaStream_t s) {
+  k_qs_trial<<<unsigned((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(n, x, d, a, xt);
+  return 1;
+}
+int launch_qs_set_pins(const DevMesh& m, const int32_t* ids, const double* pos, int64_t n_pinned, cudaStream_t s) {
+  if (n_pinned <= 0) return 0;
+  k_qs_set_pins<<<unsigned((n_pinned + kThreads - 1) / kThreads), kThreads, 0, s>>>(m, ids, pos, n_pinned);
+  return 1;
+}
 
 int launch_newton_prep(const DevMesh& m, const Material& mt, double dt, double* xk, double* w, cudaStream_t s) {
   const int64_t n = 3 * m.N;

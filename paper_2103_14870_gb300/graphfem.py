@@ -102,6 +102,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_newton_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
+        "gf_quasistatic_step": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_double, ctypes.POINTER(StepStats)]),
         "gf_tuning_set": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
         "gf_tuning_get": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
         "gf_positions_get": (ctypes.c_int, [P, P, ctypes.c_int32]),
@@ -241,6 +243,19 @@ class Mesh:
         st = StepStats()
         status = load_library().gf_step(self._h, float(dt), pf, pp, n_pin, pq, _one_kind(kf, kp, kq),
                                          ctypes.byref(st))
+        _check(status)
+        return st.as_dict()
+
+    def quasistatic_step(self, f_ext=None, pinned=None, pinned_pos=None, max_newton: int = 50,
+                         rtol: float = 1e-10) -> dict:
+        """gf_quasistatic_step: damage update, pinned nodes to pinned_pos, Newton with an energy line search."""
+        pf, kf, kf_ = _arg(f_ext, np.float64, 3 * self.n_nodes, "f_ext")
+        n_pin = 0 if pinned is None else int(np.prod(pinned.shape)) if hasattr(pinned, "shape") else len(pinned)
+        pp, kp, kp_ = _arg(pinned, np.int32, n_pin, "pinned") if n_pin else (None, None, None)
+        pq, kq, kq_ = _arg(pinned_pos, np.float64, 3 * n_pin, "pinned_pos") if n_pin else (None, None, None)
+        st = StepStats()
+        status = load_library().gf_quasistatic_step(self._h, pf, pp, n_pin, pq, _one_kind(kf, kp, kq),
+                                                    int(max_newton), float(rtol), ctypes.byref(st))
         _check(status)
         return st.as_dict()
 
