@@ -216,6 +216,30 @@ gf_status gf_quasistatic_step(gf_mesh* mesh, const double* f_ext, const int32_t*
                               const double* pinned_pos, int32_t mem, int32_t max_newton, double rtol,
                               gf_step_stats* stats);
 
+/* Split visualisation mesh for output (Sec. 4.1, Fig. 6; nothing of it feeds
+ * the dynamics).  Every tet is cut into four node-associated pieces; a broken
+ * edge (Eq. 21 labels) splits into two child nodes at its midpoint, a face
+ * into three at its centroid, a tet into four at its centroid, one child per
+ * parent node.  A child sits at its entity's rest centroid plus the mean
+ * displacement x - X of the parents still joined to it through unbroken
+ * edges of that entity (with no broken edge: the current centroid).
+ * Vertices (float64 [n_vertices][3]): [0, N) the current positions, then
+ * N + 2 e + s (edge e, child of its node edges[e][s], gf_edges_get order),
+ * N + 2 NE + 3 f + c (face f, child of its c-th node; faces are the sorted
+ * node triples in lexicographic order), N + 2 NE + 3 NF + 4 t + a (tet t,
+ * child of local node a).  Quads (int32 [n_quads][4], vertex ids): for each
+ * tet t and each of its broken local edges k = (a, b), c < d the other local
+ * nodes, [E(a), F(abc, a), T(a), F(abd, a)] then [E(b), F(abd, b), T(b),
+ * F(abc, b)]: the crack surface between the pieces of a and b; in order of
+ * tet, local edge (Eq. 15 order), a-side first.
+ * gf_surface_sizes gives the counts for the current labels; gf_surface_get
+ * fills caller buffers (host or device per `mem`) and fails with GF_BAD_ARG,
+ * n_quads set, when max_quads is too small.  The first call builds the face
+ * tables on the host (kept with the mesh). */
+gf_status gf_surface_sizes(gf_mesh* mesh, int64_t* n_vertices, int64_t* n_faces, int64_t* n_quads);
+gf_status gf_surface_get(gf_mesh* mesh, double* vertices, int32_t* quads, int64_t max_quads, int32_t mem,
+                         int64_t* n_quads);
+
 /* Current positions / velocities, float64 [3*n_nodes]. */
 gf_status gf_positions_get(gf_mesh* mesh, double* x, int32_t mem);
 gf_status gf_velocities_get(gf_mesh* mesh, double* v, int32_t mem);

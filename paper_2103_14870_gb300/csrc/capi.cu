@@ -7,6 +7,7 @@
 
 #include "gf_device.h"
 #include "gf_gnn.h"
+#include "gf_surface.h"
 
 namespace gf {
 
@@ -153,6 +154,10 @@ struct gf_mesh {
   double* qs_x = nullptr;     // quasi-static: trial positions [3N]
   double* qs_zero = nullptr;  // quasi-static: zero velocities [3N]
   double* qs_out = nullptr;   // quasi-static: E, |E| scale, slope [4]
+  SurfDev surf{};             // split visualisation mesh tables (built on first use)
+  bool surf_ready = false;
+  void* surf_stage = nullptr; // host-output staging of the surface buffers (cudaMalloc, grown on demand)
+  size_t surf_stage_bytes = 0;
   int64_t launches = 0;
   int64_t nbr_pairs = 0;
 
@@ -235,6 +240,7 @@ void release(gf_mesh* m) {
   if (m->h_pcg) cudaFreeHost(m->h_pcg);
   if (m->h_ir) cudaFreeHost(m->h_ir);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
+  if (m->surf_stage) cudaFree(m->surf_stage);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
 }
 
@@ -1127,6 +1133,143 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
   if (status != GF_OK && status != GF_BAD_ARG)
     set_last_error(std::string("quasi-static step: ") + gf_status_string(gf_status(status)));
   return gf_status(status);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Faces (sorted node triples, lexicographic), the face opposite each local node
+// of every tet and each face's edge ids; rest positions; the scan buffer.
+gf_status surface_setup(gf_mesh* m) {
+  if (m->surf_ready) return GF_OK;
+  DevMesh& d = m->dm;
+  const int64_t T = d.T;
+  std::vector<int32_t> tets(4 * T);
+  GF_CK(cudaMemcpyAsync(tets.data(), d.tets, sizeof(int32_t) * 4 * T, cudaMemcpyDeviceToHost, m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  struct Tri { int32_t a, b, c; int64_t slot; };
+  std::vector<Tri> tri(4 * T);
+  const int opp[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  for (int64_t t = 0; t < T; ++t)
+    for (int i = 0; i < 4; ++i) {
+      int32_t v[3] = {tets[4 * t + opp[i][0]], tets[4 * t + opp[i][1]], tets[4 * t + opp[i][2]]};
+      std::sort(v, v + 3);
+      tri[4 * t + i] = {v[0], v[1], v[2], 4 * t + i};
+    }
+  std::sort(tri.begin(), tri.end(), [](const Tri& x, const Tri& y) {
+    return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : (x.c != y.c ? x.c < y.c : x.slot < y.slot));
+  });
+  std::vector<int32_t> faces, tet_faces(4 * T), face_edges;
+  const std::vector<int32_t>& E = m->hm.edges;
+  const int64_t NE = m->hm.n_edges;
+  auto edge_id = [&](int32_t u, int32_t v) -> int32_t {
+    int64_t lo = 0, hi = NE;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (E[2 * mid] < u || (E[2 * mid] == u && E[2 * mid + 1] < v)) lo = mid + 1;
+      else hi = mid;
+    }
+    return int32_t(lo);
+  };
+  for (size_t i = 0; i < tri.size(); ++i) {
+    if (i == 0 || tri[i].a != tri[i - 1].a || tri[i].b != tri[i - 1].b || tri[i].c != tri[i - 1].c) {
+      faces.insert(faces.end(), {tri[i].a, tri[i].b, tri[i].c});
+      face_edges.insert(face_edges.end(), {edge_id(tri[i].a, tri[i].b), edge_id(tri[i].a, tri[i].c),
+                                           edge_id(tri[i].b, tri[i].c)});
+    }
+    tet_faces[tri[i].slot] = int32_t(faces.size() / 3 - 1);
+  }
+  SurfDev& sd = m->surf;
+  sd.NF = int64_t(faces.size() / 3);
+  gf_status st = GF_OK;
+  const double* X = nullptr;
+  const int32_t *pf = nullptr, *pfe = nullptr, *ptf = nullptr;
+  if ((st = upload(m, m->X0, &X)) || (st = upload(m, faces, &pf)) || (st = upload(m, face_edges, &pfe)) ||
+      (st = upload(m, tet_faces, &ptf)) || (st = scratch(m, size_t(surf_blocks(d) + 1), &sd.bsum)))
+    return st;
+  sd.X = X;
+  sd.faces = reinterpret_cast<const int3*>(pf);
+  sd.face_edges = reinterpret_cast<const int3*>(pfe);
+  sd.tet_faces = reinterpret_cast<const int4*>(ptf);
+  m->surf_ready = true;
+  return GF_OK;
+}
+
+gf_status surface_count(gf_mesh* m, int64_t* n_quads) {
+  gf_status st = surface_setup(m);
+  if (st != GF_OK) return st;
+  m->launches += launch_surface_count(m->dm, m->surf, m->stream);
+  GF_CK(cudaGetLastError());
+  unsigned total = 0;
+  GF_CK(cudaMemcpyAsync(&total, m->surf.bsum + surf_blocks(m->dm), sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  *n_quads = int64_t(total);
+  return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gf_status gf_surface_sizes(gf_mesh* m, int64_t* n_vertices, int64_t* n_faces, int64_t* n_quads) {
+  if (!m || !n_vertices || !n_faces || !n_quads) {
+    set_last_error("surface_sizes: need the mesh and three outputs");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  gf_status st = surface_count(m, n_quads);
+  if (st != GF_OK) return st;
+  *n_faces = m->surf.NF;
+  *n_vertices = m->dm.N + 2 * m->dm.NE + 3 * m->surf.NF + 4 * m->dm.T;
+  return GF_OK;
+}
+
+gf_status gf_surface_get(gf_mesh* m, double* vertices, int32_t* quads, int64_t max_quads, int32_t mem,
+                         int64_t* n_quads) {
+  if (!m || !vertices || !n_quads || max_quads < 0 || (max_quads > 0 && !quads) || !valid_mem(mem)) {
+    set_last_error("surface_get: need the mesh, vertices, n_quads, quads when max_quads > 0, a memory kind");
+    return GF_BAD_ARG;
+  }
+  DeviceGuard guard(m->device);
+  int64_t nq = 0;
+  gf_status st = surface_count(m, &nq);
+  if (st != GF_OK) return st;
+  *n_quads = nq;
+  if (nq > max_quads) {
+    set_last_error("surface_get: max_quads is below the quad count (returned in n_quads)");
+    return GF_BAD_ARG;
+  }
+  const DevMesh& d = m->dm;
+  const int64_t nv = d.N + 2 * d.NE + 3 * m->surf.NF + 4 * d.T;
+  double* V = vertices;
+  int32_t* Q = quads;
+  if (mem == GF_MEM_HOST) {
+    const size_t need = sizeof(double) * 3 * nv + sizeof(int32_t) * 4 * size_t(nq) + 256;
+    if (need > m->surf_stage_bytes) {
+      if (m->surf_stage) cudaFree(m->surf_stage);
+      m->surf_stage = nullptr;
+      m->surf_stage_bytes = 0;
+      if (cudaMalloc(&m->surf_stage, need) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error("surface_get: staging allocation failed");
+        return GF_OOM;
+      }
+      m->surf_stage_bytes = need;
+    }
+    V = static_cast<double*>(m->surf_stage);
+    Q = reinterpret_cast<int32_t*>(static_cast<char*>(m->surf_stage) + ((sizeof(double) * 3 * nv + 255) & ~size_t(255)));
+  }
+  m->launches += launch_surface_vertices(d, m->surf, V, m->stream);
+  if (nq > 0) m->launches += launch_surface_quads(d, m->surf, Q, nq, m->stream);
+  GF_CK(cudaGetLastError());
+  if (mem == GF_MEM_HOST) {
+    GF_CK(cudaMemcpyAsync(vertices, V, sizeof(double) * 3 * nv, cudaMemcpyDeviceToHost, m->stream));
+    if (nq > 0) GF_CK(cudaMemcpyAsync(quads, Q, sizeof(int32_t) * 4 * nq, cudaMemcpyDeviceToHost, m->stream));
+  }
+  GF_CK(cudaStreamSynchronize(m->stream));
+  return GF_OK;
 }
 
 gf_status gf_positions_get(gf_mesh* m, double* x, int32_t mem) {

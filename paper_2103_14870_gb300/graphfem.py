@@ -102,6 +102,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_newton_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
+        "gf_surface_sizes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]),
+        "gf_surface_get": (ctypes.c_int, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
         "gf_quasistatic_step": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_double, ctypes.POINTER(StepStats)]),
         "gf_tuning_set": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
@@ -258,6 +261,21 @@ class Mesh:
                                                     int(max_newton), float(rtol), ctypes.byref(st))
         _check(status)
         return st.as_dict()
+
+    def surface_sizes(self) -> dict:
+        nv, nf, nq = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().gf_surface_sizes(self._h, ctypes.byref(nv), ctypes.byref(nf), ctypes.byref(nq)))
+        return {"n_vertices": nv.value, "n_faces": nf.value, "n_quads": nq.value}
+
+    def surface_get(self):
+        """Split visualisation mesh (Sec. 4.1): vertices float64 (n, 3), crack quads int32 (q, 4)."""
+        sz = self.surface_sizes()
+        V = np.empty((sz["n_vertices"], 3), np.float64)
+        Q = np.empty((max(sz["n_quads"], 1), 4), np.int32)
+        nq = ctypes.c_int64()
+        _check(load_library().gf_surface_get(self._h, V.ctypes.data, Q.ctypes.data, Q.shape[0], MEM_HOST,
+                                             ctypes.byref(nq)))
+        return {"vertices": V, "quads": Q[:nq.value], "n_faces": sz["n_faces"]}
 
     def tuning_set(self, assembly: int):
         t = Tuning()
