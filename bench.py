@@ -299,6 +299,94 @@ def run_learned(args, gf, torch, barrier, stream, w, mat, f_dev) -> dict:
             "cg_iters_saved_per_step": plain["cg_iters_per_step"] - learned["cg_iters_per_step"]}
 
 
+def run_extensions(args, gf, torch, barrier, stream, w, f_dev, m_main) -> dict:
+    """The widening rows on the loaf (each timed with CUDA events after warm-up):
+    stable Neo-Hookean FP64 step, consistent mass with one and two Newton
+    iterations, a quasi-static pull of the end caps (Newton + energy line
+    search, inner PCG to 1e-6) on the main mesh, and the split visualisation
+    mesh of its state."""
+    import numpy as np
+
+    def timed(m, steps, pinned=None):
+        for _ in range(3):
+            m.step(w.dt, f_dev, pinned)
+        m.profile_reset()
+        m.profile_enable(True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, newton = [], []
+        for _ in range(steps):
+            s = m.step(w.dt, f_dev, pinned)
+            assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
+            its.append(s["cg_iters"])
+            newton.append(s["newton_iters"])
+        e1.record(stream)
+        barrier()
+        m.profile_enable(False)
+        prof = m.profile_get()
+        ms = e0.elapsed_time(e1) / steps
+        return {"ms_per_step": ms, "element_updates_per_s": w.n_tets / (ms * 1e-3),
+                "cg_iters_per_step": statistics.mean(its), "newton_iters_per_step": statistics.mean(newton),
+                "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[0] > 0}}
+
+    out = {}
+    steps = 20
+    mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius, energy=gf.ENERGY_SNH)
+    ms = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
+    out["snh_fp64"] = timed(ms, steps)
+    ms.close()
+    mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius,
+                      mass_matrix=gf.MASS_CONSISTENT)
+    mc = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
+    out["consistent_mass_fp64"] = timed(mc, steps)
+    mc.newton_set(2)
+    out["consistent_mass_newton2_fp64"] = timed(mc, steps)
+    mc.close()
+    # quasi-static pull: end caps pinned and moved apart by 0.02% of the length per load step (the
+    # loaf's break threshold is 1e-3 strain)
+    X = w.nodes
+    L = X[:, 0].max() - X[:, 0].min()
+    lo = np.nonzero(X[:, 0] <= X[:, 0].min() + 0.1 * L)[0].astype(np.int32)
+    hi = np.nonzero(X[:, 0] >= X[:, 0].max() - 0.1 * L)[0].astype(np.int32)
+    pins = np.concatenate([lo, hi])
+    m_main.state_set(x=X.ravel(), v=np.zeros(X.size), labels=np.zeros(m_main.n_edges, np.uint8))
+    qs = []
+    for k in range(1, 4):
+        target = X[pins].copy()
+        target[:len(lo), 0] -= 1e-4 * L * k
+        target[len(lo):, 0] += 1e-4 * L * k
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = m_main.quasistatic_step(None, pins, target, max_newton=20, rtol=1e-6)
+        qs.append({"ms": 1e3 * (time.perf_counter() - t0), "newton_iters": s["newton_iters"],
+                   "cg_iters": s["cg_iters"], "rel_res": s["rel_res"], "n_broken": s["n_broken"]})
+    out["quasistatic_pull_fp64"] = {"load_steps": qs, "inner_cg_rtol": w.cg_rtol,
+                                    "ms_per_load_step": statistics.mean(q["ms"] for q in qs)}
+    # split visualisation mesh of the pulled state (device output)
+    sz = m_main.surface_sizes()
+    V = torch.empty((sz["n_vertices"], 3), dtype=torch.float64, device="cuda")
+    Q = torch.empty((max(sz["n_quads"], 1), 4), dtype=torch.int32, device="cuda")
+    lib = gf.load_library()
+    import ctypes
+    nq = ctypes.c_int64()
+    for _ in range(3):
+        lib.gf_surface_get(m_main._h, V.data_ptr(), Q.data_ptr(), Q.shape[0], gf.MEM_DEVICE, ctypes.byref(nq))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 10
+    for _ in range(reps):
+        st = lib.gf_surface_get(m_main._h, V.data_ptr(), Q.data_ptr(), Q.shape[0], gf.MEM_DEVICE, ctypes.byref(nq))
+        assert st == 0
+    e1.record(stream)
+    barrier()
+    out["surface_extraction"] = {"ms_per_call": e0.elapsed_time(e1) / reps, "n_vertices": sz["n_vertices"],
+                                 "n_quads": sz["n_quads"], "bytes_written": 24 * sz["n_vertices"] + 16 * sz["n_quads"],
+                                 "note": "includes the quad count readback (one host sync per call)"}
+    return out
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -361,6 +449,7 @@ def run_ours(args) -> None:
         m.positions_get(out=x_host)
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    ext = run_extensions(args, gf, torch, barrier, stream, w, f_dev, m) if not args.no_extensions else None
     m.close()
     # mixed-precision form on the same workload and tolerance
     mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
@@ -405,6 +494,7 @@ def run_ours(args) -> None:
                   "roofline": mix_roof},
         "batch": batch,
         "learned": learned,
+        "extensions": ext,
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "kernel_launches": {k: v[1] for k, v in prof.items()},
         "clocks": clocks,
@@ -450,6 +540,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched form")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start form")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the SNH / consistent-mass / Newton / quasi-static / surface lines")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
     ap.add_argument("--precision", choices=["fp64", "mixed", "learned"], default="fp64",

@@ -211,7 +211,10 @@ gf_status gf_newton_set(gf_mesh* mesh, int32_t max_iters, double rtol);
  * <= rtol times its value at the first iteration, or after max_newton
  * (1..1000) iterations (GF_CG_MAXITER).  Velocities are zero afterwards.
  * stats (nullable): newton_iters, cg_iters summed, rel_res = the last
- * residual ratio, damage counts.  GF_FP64 meshes only. */
+ * residual ratio, damage counts.  GF_FP64 meshes only.  With no mass, a
+ * node whose tets all have chi = 0 has no stiffness: it keeps its position
+ * (its block-Jacobi block is zero).  A separated fragment of several tets is a
+ * free rigid body; the PCG finds the solution without rigid motion of it. */
 gf_status gf_quasistatic_step(gf_mesh* mesh, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
                               const double* pinned_pos, int32_t mem, int32_t max_newton, double rtol,
                               gf_step_stats* stats);

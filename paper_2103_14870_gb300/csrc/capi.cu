@@ -1115,7 +1115,11 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
   m->assembled = true;
   m->launches += L;
   prof_collect(m, 1 << 30, false);
-  if (status == GF_OK && k >= max_newton && rel > rtol) status = GF_CG_MAXITER;
+  bool newton_short = false;
+  if (status == GF_OK && k >= max_newton && rel > rtol) {
+    status = GF_CG_MAXITER;
+    newton_short = true;
+  }
   if (m->h_cnt[kCntBadPin] != 0) {
     set_last_error("pinned node id out of range (skipped)");
     status = GF_BAD_ARG;
@@ -1130,7 +1134,9 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
     stats->refine_sweeps = 0;
     stats->newton_iters = k;
   }
-  if (status != GF_OK && status != GF_BAD_ARG)
+  if (newton_short)
+    set_last_error("quasi-static step: Newton did not reach rtol within max_newton iterations");
+  else if (status != GF_OK && status != GF_BAD_ARG)
     set_last_error(std::string("quasi-static step: ") + gf_status_string(gf_status(status)));
   return gf_status(status);
 }

@@ -945,7 +945,10 @@ __device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& 
       const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[2] * a[7] - a[1] * a[8], c02 = a[1] * a[5] - a[2] * a[4];
       const double c10 = a[5] * a[6] - a[3] * a[8], c11 = a[0] * a[8] - a[2] * a[6], c12 = a[2] * a[3] - a[0] * a[5];
       const double c20 = a[3] * a[7] - a[4] * a[6], c21 = a[1] * a[6] - a[0] * a[7], c22 = a[0] * a[4] - a[1] * a[3];
-      const double id = 1.0 / (a[0] * c00 + a[1] * c10 + a[2] * c20);
+      // a node with no stiffness and no mass (every tet around it at chi = 0 in a
+      // quasi-static solve) has a zero block: a zero inverse keeps it in place
+      const double det = a[0] * c00 + a[1] * c10 + a[2] * c20;
+      const double id = det != 0.0 ? 1.0 / det : 0.0;
       double* pi = m.pinv + 9 * i;
       const double inv[9] = {c00 * id, c01 * id, c02 * id, c10 * id, c11 * id, c12 * id, c20 * id, c21 * id, c22 * id};
 #pragma unroll

@@ -93,3 +93,21 @@ def test_quasistatic_step_is_refused_on_mixed_meshes():
     m = gf.mesh_create(X, T, gf.material(E, NU, RHO), precision=gf.MIXED)
     with pytest.raises(gf.GraphFEMError):
         m.quasistatic_step(None, lo.astype(np.int32), None)
+
+
+def test_fragmenting_pull_stays_finite():
+    """A pull far past the break threshold separates pieces: nodes left without
+    stiffness keep their positions and the step returns finite positions
+    (no mass regularises the quasi-static system)."""
+    X, T, lo, hi = bar(nz=8)
+    model, m = meshes(X, T, "stvk", 1e-3)
+    pins = np.concatenate([lo, hi]).astype(np.int32)
+    for k in range(1, 4):
+        target = X[pins].copy()
+        target[len(lo):, 2] += 0.4 * k
+        s = m.quasistatic_step(None, pins, target, max_newton=30, rtol=1e-8)
+        assert s["status"] == 0
+    x = m.positions_get().reshape(-1, 3)
+    assert np.isfinite(x).all()
+    assert (m.chi_get() == 0).sum() > 0
+    np.testing.assert_allclose(x[pins], target, rtol=0, atol=1e-12)

@@ -199,8 +199,8 @@ def loaf_config(seed: int = 1, axes=LOAF_AXES) -> Workload:
 
 
 # Driver threshold of the loaf case (dimensionless strain).  The configuration
-# gives none, so it is set to the value that breaks about 0.1% of the edges of
-# the loaded loaf; ``tests/golden/make_thresholds.py`` documents the rule.
+# gives none; 1e-3 strain is the value used for it (the cost of a step does not
+# depend on it).
 LOAF_THRESHOLD = 1.0e-3
 
 
