@@ -506,20 +506,26 @@ def run_ours(args) -> None:
 
 
 def run_profile_step(args) -> None:
-    """Minimal command for ncu captures: build the loaf mesh, run `--steps` steps, no timing."""
+    """Minimal command for ncu captures: build the loaf mesh, run `--steps` steps, no timing.
+    --precision: fp64 | mixed | learned (FP64 with the network's start, then one Adam step) |
+    snh (stable Neo-Hookean FP64) | qs (one quasi-static pull load step after the steps) |
+    surface (split visualisation mesh after the steps)."""
+    import numpy as np
     import torch
     import paper_2103_14870_gb300 as gf
     from workloads import loaf_config
     torch.cuda.set_device(0)
     w = loaf_config()
-    m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=w.threshold,
-                                                    radius=w.radius), cg_rtol=w.cg_rtol,
+    mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius,
+                      energy=gf.ENERGY_SNH if args.precision == "snh" else gf.ENERGY_STVK)
+    m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol,
                        precision=gf.MIXED if args.precision == "mixed" else gf.FP64)
     f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
     net = None
     if args.precision == "learned":      # zero-decoder network: learned start from the second step on
         from workloads import he_normal_weights
         net = gf.Gnn(m, he_normal_weights(gf.GNN_PARAM_SHAPES, seed=1, zero=("Wd",)))
+    s = None
     for k in range(args.steps):
         if net is not None and k == 1:
             net.attach(gf.GNN_START)
@@ -527,6 +533,20 @@ def run_profile_step(args) -> None:
     if net is not None:
         net.attach(0)
         net.train(iters=1, lr=1e-5)
+    if args.precision == "qs":
+        X = w.nodes
+        L = X[:, 0].max() - X[:, 0].min()
+        lo = np.nonzero(X[:, 0] <= X[:, 0].min() + 0.1 * L)[0].astype(np.int32)
+        hi = np.nonzero(X[:, 0] >= X[:, 0].max() - 0.1 * L)[0].astype(np.int32)
+        pins = np.concatenate([lo, hi])
+        m.state_set(x=X.ravel(), v=np.zeros(X.size), labels=np.zeros(m.n_edges, np.uint8))
+        target = X[pins].copy()
+        target[:len(lo), 0] -= 1e-4 * L
+        target[len(lo):, 0] += 1e-4 * L
+        s = m.quasistatic_step(None, pins, target, max_newton=20, rtol=1e-6)
+    if args.precision == "surface":
+        s = m.surface_get()
+        s = {"n_vertices": int(s["vertices"].shape[0]), "n_quads": int(s["quads"].shape[0])}
     torch.cuda.synchronize()
     print(json.dumps({"profile_step": True, "steps": args.steps, "last": s, "launches": m.launch_count()}))
 
@@ -544,8 +564,8 @@ def main():
                     help="skip the SNH / consistent-mass / Newton / quasi-static / surface lines")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "learned"], default="fp64",
-                    help="form run by --profile-step (learned: FP64 with the network's start, then one Adam step)")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "learned", "snh", "qs", "surface"], default="fp64",
+                    help="form run by --profile-step (see run_profile_step)")
     args = ap.parse_args()
     if args.cpu_sample_child:
         cpu_sample_child(args.cpu_sample_child)

@@ -484,15 +484,19 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
     for (int j = 0; j < 3; ++j) IC += F[i][j] * F[i][j];
   const double w = 1.0 / (IC + 1.0);
   const double c1 = mu * (1.0 - w), c2 = lam * (J - mt.snh_a), c3 = 2.0 * mu * w * w;
-  double u[4][3], z[4][3];
+  // the block scale (dt beta + dt^2) chi V is folded into the factors: blocks come out scaled
+  const double sK = (dt * beta + dt * dt) * chi, sV = sK * V;
+  const double k1 = sV * c1, k2 = sV * c2, k3 = sV * c3, k4 = sV * lam;
+  double u[4][3], z[4][3], us[4][3], zs[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       u[a][c] = F[c][0] * G[a][0] + F[c][1] * G[a][1] + F[c][2] * G[a][2];
       z[a][c] = cof[c][0] * G[a][0] + cof[c][1] * G[a][1] + cof[c][2] * G[a][2];
+      us[a][c] = k3 * u[a][c];
+      zs[a][c] = k4 * z[a][c];
     }
-  const double sK = (dt * beta + dt * dt) * chi, cv = beta + dt;
   double Kv[4][3] = {};
 #pragma unroll
   for (int b = 0; b < 4; ++b)
@@ -505,24 +509,23 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
         const double x1 = G[a][2] * G[b][0] - G[a][0] * G[b][2];
         const double x2 = G[a][0] * G[b][1] - G[a][1] * G[b][0];
 #pragma unroll
-        for (int mm = 0; mm < 3; ++mm) tm[mm] = x0 * F[mm][0] + x1 * F[mm][1] + x2 * F[mm][2];
+        for (int mm = 0; mm < 3; ++mm) tm[mm] = k2 * (x0 * F[mm][0] + x1 * F[mm][1] + x2 * F[mm][2]);
       }
       double blk[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) blk[r][c] = V * (c3 * u[a][r] * u[b][c] + lam * z[a][r] * z[b][c]);
-      const double dg = V * c1 * gg;
+        for (int c = 0; c < 3; ++c) blk[r][c] = us[a][r] * u[b][c] + zs[a][r] * z[b][c];
+      const double dg = k1 * gg;
       blk[0][0] += dg;
       blk[1][1] += dg;
       blk[2][2] += dg;
-      const double s2 = V * c2;
-      blk[0][1] += s2 * tm[2];
-      blk[1][0] -= s2 * tm[2];
-      blk[0][2] -= s2 * tm[1];
-      blk[2][0] += s2 * tm[1];
-      blk[1][2] += s2 * tm[0];
-      blk[2][1] -= s2 * tm[0];
+      blk[0][1] += tm[2];
+      blk[1][0] -= tm[2];
+      blk[0][2] -= tm[1];
+      blk[2][0] += tm[1];
+      blk[1][2] += tm[0];
+      blk[2][1] -= tm[0];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         Kv[a][r] += blk[r][0] * U[b][0] + blk[r][1] * U[b][1] + blk[r][2] * U[b][2];
@@ -532,13 +535,15 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[3 * r + c] = sK * blk[r][c];
+        for (int c = 0; c < 3; ++c) dst[3 * r + c] = blk[r][c];
     }
-  const double sf = dt * chi;
+  // rhs shares dt chi (f_a - (beta + dt) (K v)_a): the blocks carry (dt beta + dt^2) chi = dt chi (beta + dt),
+  // so the damping/velocity term is the scaled blocks' K v itself
+  const double sf = dt * chi * V;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[90 + 3 * a + c] = sf * (-V * (c1 * u[a][c] + c2 * z[a][c]) - cv * Kv[a][c]);
+    for (int c = 0; c < 3; ++c) out[90 + 3 * a + c] = -sf * (c1 * u[a][c] + c2 * z[a][c]) - Kv[a][c];
   out[102] = 0.0;
   out[103] = 0.0;
 }

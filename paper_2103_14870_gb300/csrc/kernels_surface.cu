@@ -41,6 +41,9 @@ __device__ __forceinline__ void components(const bool (&brk)[n][n], int (&comp)[
   }
 }
 
+// 1 / k for the member counts of an entity (multiplications instead of FP64 divides; within an ulp)
+__device__ __forceinline__ double inv_count(int k) { return k == 1 ? 1.0 : (k == 2 ? 0.5 : (k == 3 ? 1.0 / 3.0 : 0.25)); }
+
 // children of one entity with nodes nid[0..n): rest centroid + mean displacement of each component
 template <int n>
 __device__ __forceinline__ void follow(const double* __restrict__ X, const double* __restrict__ x, const int (&nid)[n],
@@ -57,7 +60,7 @@ __device__ __forceinline__ void follow(const double* __restrict__ X, const doubl
       d[i][c] = x[3 * int64_t(nid[i]) + c] - Xi;
     }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) Xc[c] /= double(n);
+  for (int c = 0; c < 3; ++c) Xc[c] *= inv_count(n);
 #pragma unroll
   for (int i = 0; i < n; ++i) {
     double s[3] = {0.0, 0.0, 0.0};
@@ -69,8 +72,9 @@ __device__ __forceinline__ void follow(const double* __restrict__ X, const doubl
 #pragma unroll
         for (int c = 0; c < 3; ++c) s[c] += d[j][c];
       }
+    const double ic = inv_count(cnt);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[3 * i + c] = Xc[c] + s[c] / double(cnt);
+    for (int c = 0; c < 3; ++c) out[3 * i + c] = Xc[c] + s[c] * ic;
   }
 }
 
