@@ -278,18 +278,19 @@ __global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restr
 // ---------------------------------------------------------------------------
 
 constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad (16-byte rows)
+// Each thread's row is built in shared memory (stride 105 floats: conflict-free
+// for 32 consecutive threads) and the CTA then writes its 128 contiguous rows
+// with coalesced 16-byte stores.
+constexpr int kElemThreads = 128, kElemSS = kElemW + 1;
+constexpr unsigned kElemSmem = kElemThreads * kElemSS * 4;
 
-__device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+// one tet's row: ten upper 3x3 blocks (scaled), four rhs shares, two zeros
+__device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& sp, int64_t t, float* o) {
   const float sKv = sp.sKv, cv = sp.cv, dtf = sp.dtf;
-
-  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= m.T) return;
   const MixDev& x = m.mx;
-  float4* out = reinterpret_cast<float4*>(x.ebuf + kElemW * t);
   const float chi = x.chi32[t];
   if (chi == 0.f) {
-#pragma unroll
-    for (int q = 0; q < kElemW / 4; ++q) out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < kElemW; ++q) o[q] = 0.f;
     return;
   }
   const int4 n = m.tets[t];
@@ -316,7 +317,6 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
     g[k] = s;
   }
   // Y_b[k][c] = sum_{l in b} H_kl sgn_lb e_l[c]  (sgn = -1 if b is the first node of l)
-  float o[kElemW];
   float Kv[4][3] = {};
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -390,9 +390,24 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
     }
   o[102] = 0.f;
   o[103] = 0.f;
-#pragma unroll
-  for (int q = 0; q < kElemW / 4; ++q) out[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
+__device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  extern __shared__ float sh_rows[];
+  const int64_t t0 = bid * int64_t(blockDim.x), t = t0 + threadIdx.x;
+  const MixDev& x = m.mx;
+  float* o = sh_rows + threadIdx.x * kElemSS;
+  if (t < m.T) elem32_row(m, sp, t, o);
+  __syncthreads();
+  // coalesced write-out of the CTA's rows [t0, t0 + rows)
+  const int rows = int(m.T - t0 < int64_t(blockDim.x) ? m.T - t0 : int64_t(blockDim.x));
+  float4* dst = reinterpret_cast<float4*>(x.ebuf + kElemW * t0);
+  for (int q = threadIdx.x; q < rows * (kElemW / 4); q += blockDim.x) {
+    const int r = q / (kElemW / 4), c = 4 * (q - r * (kElemW / 4));
+    const float* src = sh_rows + r * kElemSS + c;
+    dst[q] = make_float4(src[0], src[1], src[2], src[3]);
+  }
+}
+
 __global__ void __launch_bounds__(128) k_elem32(DevMesh m, Material mt, StepScalars sp) {
   elem32_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
@@ -927,6 +942,16 @@ __global__ void kb_chi_to32(const BatchTab* __restrict__ tab) {
 
 }  // namespace
 
+// the element kernels stage 53.8 KB of rows in shared memory: raise the limit once per device
+void elem32_smem_attr() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_elem32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kElemSmem));
+  cudaFuncSetAttribute(kb_elem32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kElemSmem));
+  done[dev] = true;
+}
+
 int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first) {
   const LaunchDims d = launch_dims(kind, m, mt, sp);
   if (d.blocks == 0) return 0;
@@ -935,7 +960,10 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
     case kB_nonlocal32: k_nonlocal32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_edge_driver32: k_edge_driver32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_tet_chi32: k_tet_chi32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_elem32: k_elem32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_elem32:
+      elem32_smem_attr();
+      k_elem32<<<d.blocks, d.threads, kElemSmem, s>>>(m, mt, sp);
+      break;
     case kB_gather32: k_gather32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_fext32: k_fext32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_residual: k_ir_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp, first); break;
@@ -959,7 +987,10 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
     case kB_nonlocal32: kb_nonlocal32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_edge_driver32: kb_edge_driver32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_tet_chi32: kb_tet_chi32<<<blocks, threads, 0, s>>>(tab); break;
-    case kB_elem32: kb_elem32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_elem32:
+      elem32_smem_attr();
+      kb_elem32<<<blocks, threads, kElemSmem, s>>>(tab);
+      break;
     case kB_gather32: kb_gather32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_fext32: kb_fext32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_residual: kb_ir_residual<<<blocks, threads, 0, s>>>(tab, first); break;
