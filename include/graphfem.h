@@ -96,7 +96,8 @@ typedef struct gf_options {
   int32_t precond;       /* GF_PRECOND_BJACOBI */
   int32_t device;        /* CUDA device ordinal; -1 -> the current device */
   void* stream;          /* cudaStream_t for all work; NULL -> a stream the library creates */
-  gf_alloc_fn alloc;     /* optional device allocator (e.g. a caching allocator); NULL -> cudaMalloc */
+  gf_alloc_fn alloc;     /* optional device allocator (e.g. a caching allocator); NULL -> cudaMalloc.
+                            It must return 16-byte-aligned device memory (else GF_BAD_ARG) */
   gf_free_fn free;       /* matching free; required when alloc is set */
   void* alloc_ctx;       /* passed to alloc/free */
 } gf_options;

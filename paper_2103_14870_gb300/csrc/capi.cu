@@ -51,8 +51,9 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_edge_driver: case kB_edge_driver32: return {cdiv(NE, 256), 256};
     case kB_node_init: return {cdiv(N, 256), 256};
     case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
-    case kB_gather64: return {cdiv(9 * m.NB + 12 * N, 256), 256};
-    case kB_gather32: return {cdiv(32 * N, 256), 256};
+    case kB_gather64: return {cdiv(9 * m.NE + 12 * N, 256), 256};
+    case kB_gather32: return {cdiv(9 * m.NE + 12 * N, 256), 256};
+    case kB_pinv32: return {cdiv(N, 256), 256};
     case kB_set_pinned: return {cdiv(sp.n_pinned, 256), 256};
     case kB_pcg_init: case kB_pcg_spmv: case kB_pcg_update: case kB_true_residual: return {red_grid(N), 256};
     case kB_pcg_p: return {red_grid(3 * N), 256};
@@ -196,6 +197,11 @@ gf_status dev_alloc(gf_mesh* m, size_t bytes, void** out) {
     if (!p) {
       set_last_error("device allocator returned NULL for " + std::to_string(bytes) + " bytes");
       return GF_OOM;
+    }
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0) {   // the kernels use 16-byte vector accesses
+      m->free_fn(p, m->alloc_ctx);
+      set_last_error("device allocator returned a pointer that is not 16-byte aligned");
+      return GF_BAD_ARG;
     }
   } else {
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -454,10 +460,10 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   UP(d.et_ptr, hm.et_ptr, int32_t);
   UP(d.et_tet, hm.et_tet, int32_t);
   UP(d.colour_tets, hm.colour_tets, int32_t);
-  UP(d.sc_ptr, hm.sc_ptr, int32_t);
-  UP(d.sc_ent, hm.sc_ent, int32_t);
   UP(d.np_ptr, hm.np_ptr, int32_t);
-  UP(d.np_pair, hm.np_pair, int32_t);
+  UP(d.nrow, hm.nrow, int32_t);
+  UP(d.erow, hm.erow, int32_t);
+  UP(d.edge_slot, hm.edge_slot, int32_t);
   std::vector<double> mass_blk;
   if (M.mass_matrix == GF_MASS_CONSISTENT) {
     // Eq. 5 for a linear tet: m_ab = rho V (1 + delta_ab) / 20, summed into the block slots
@@ -847,7 +853,11 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
     L += launch_kind(kB_elem32, d, mt, sp, s);
     L += launch_kind(kB_fext32, d, mt, sp, s);
   }
-  { Prof p(m, kPGather); L += launch_kind(kB_gather32, d, mt, sp, s); }
+  {
+    Prof p(m, kPGather);
+    L += launch_kind(kB_gather32, d, mt, sp, s);
+    L += launch_kind(kB_pinv32, d, mt, sp, s);
+  }
   IrState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
   init.in_tol2 = m->in_rtol * m->in_rtol;
@@ -1503,7 +1513,7 @@ const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_ch
 const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
 const int kSuffixFp64[] = {kB_true_residual, kB_integrate};
 const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32,
-                            kB_gather32, kB_set_pinned, kB_refresh32};
+                            kB_gather32, kB_pinv32, kB_set_pinned, kB_refresh32};
 const int kBodyMixed[] = {kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_ir_residual};
 const int kSuffixMixed[] = {kB_integrate32};
 

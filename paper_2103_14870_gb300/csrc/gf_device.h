@@ -56,7 +56,7 @@ struct MixDev {
   float* sig_bar32 = nullptr;         // [T][8]
   float* sigf32 = nullptr;            // [T][6]
   float* val32 = nullptr;             // [NB][9]
-  float* ebuf = nullptr;              // [T][104] element blocks + rhs shares (two-phase assembly)
+  float* ebuf = nullptr;              // [4T][12] node rows, then [6T][9] edge rows (two-phase assembly)
   float* rhs32 = nullptr;             // [3N]
   float* rres = nullptr;              // [3N] leading float of the refinement residual
   float* fext32 = nullptr;            // [3N]
@@ -82,10 +82,12 @@ struct DevMesh {
   const int32_t* et_ptr = nullptr;     // [NE+1]
   const int32_t* et_tet = nullptr;
   const int32_t* colour_tets = nullptr;  // [T] tets grouped by colour
-  const int32_t* sc_ptr = nullptr;     // [NB+1] block slot -> element-block contributions
-  const int32_t* sc_ent = nullptr;     // [16T] (tet << 5) | q | 16 * transposed
-  const int32_t* np_ptr = nullptr;     // [N+1] node -> (tet << 2) | local node
-  const int32_t* np_pair = nullptr;    // [4T]
+  // assembly rows: node i owns rows [np_ptr[i], np_ptr[i+1]) and edge e rows
+  // [et_ptr[e], et_ptr[e+1]), one per incident tet in ascending tet order
+  const int32_t* np_ptr = nullptr;     // [N+1]
+  const int32_t* nrow = nullptr;       // [T][4] node row of (tet, local node)
+  const int32_t* erow = nullptr;       // [T][6] edge row of (tet, local edge)
+  const int2* edge_slot = nullptr;     // [NE] block slots of (i, j) and (j, i), i < j
   const int64_t* nb_off = nullptr;     // [G]
   const int32_t* nb_len = nullptr;     // [G]
   const int32_t* nb_idx = nullptr;
@@ -101,7 +103,7 @@ struct DevMesh {
   double* sig_bar = nullptr;           // [T][6] Eq. 20 averages
   double* sigf = nullptr;              // [T][6] local edge-normal stresses
   double* val = nullptr;               // [NB][9] system matrix A
-  double* ebuf = nullptr;              // [T][104] element blocks + rhs shares (two-phase assembly)
+  double* ebuf = nullptr;              // [4T][12] node rows, then [6T][9] edge rows (two-phase assembly)
   double* rhs = nullptr;               // [3N] b
   double* dv = nullptr;                // [3N] unknown
   double* r = nullptr;
@@ -159,7 +161,7 @@ enum BatchKind : int {
   kB_pcg_init, kB_pcg_spmv, kB_pcg_update, kB_pcg_p, kB_true_residual, kB_integrate,
   kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_fext32,
   kB_ir_residual, kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_integrate32, kB_refresh32,
-  kB_chi_to32, kB_step_begin, kBKinds
+  kB_chi_to32, kB_pinv32, kB_step_begin, kBKinds
 };
 constexpr int kMaxBatch = 256;
 

@@ -77,18 +77,19 @@ struct HostMesh {
   std::vector<int32_t> perm;       // internal tet -> caller tet (identity)
   std::vector<int32_t> colour_ptr; // [C+1] ranges of colour_tets
   std::vector<int32_t> colour_tets;// [T] tets grouped by colour (no two share a node within a colour)
-  // two-phase assembly: block slot -> (tet << 5) | q | 16*transposed, node -> (tet << 2) | local node
-  std::vector<int32_t> sc_ptr;     // [NB+1]
-  std::vector<int32_t> sc_ent;     // [16T]
+  // two-phase assembly: node i's rows [np_ptr[i], np_ptr[i+1]) and edge e's
+  // rows [et_ptr[e], et_ptr[e+1]), one per incident tet in ascending order
   std::vector<int32_t> np_ptr;     // [N+1]
-  std::vector<int32_t> np_pair;    // [4T]
+  std::vector<int32_t> nrow;       // [T][4] node row of (tet, local node)
+  std::vector<int32_t> erow;       // [T][6] edge row of (tet, local edge)
+  std::vector<int32_t> edge_slot;  // [NE][2] block slots of (i, j) and (j, i), i < j
   std::vector<int32_t> edges;      // [NE][2]
   std::vector<int32_t> tet_edges;  // [T][6] internal order
   std::vector<int32_t> row_ptr;    // [N+1] block-CSR pattern
   std::vector<int32_t> col;        // [NB]
   std::vector<int32_t> diag_blk;   // [N] block index of (i, i)
   std::vector<int32_t> slot;       // [T][16] block index of local (a, b), internal order
-  std::vector<int32_t> et_ptr;     // [NE+1] edge -> incident tets
+  std::vector<int32_t> et_ptr;     // [NE+1] edge -> incident tets (and edge rows)
   std::vector<int32_t> et_tet;     // internal tet ids
   std::vector<double> rest;        // [kRestFields][T]
   std::vector<double> mass;        // [N] lumped

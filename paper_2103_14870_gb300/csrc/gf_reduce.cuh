@@ -6,6 +6,24 @@
 
 namespace gf {
 
+// Sum of src[stride r] over the rows r in [r0, r1), in ascending r.  The
+// values are loaded B at a time before any add, so each thread keeps B
+// independent loads in flight; the adds still run one by one in row order.
+// `src` must not be written during the kernel.
+template <int B, typename T>
+__device__ __forceinline__ T row_sum(const T* __restrict__ src, int stride, int r0, int r1) {
+  T acc = T(0);
+  for (int r = r0; r < r1; r += B) {
+    T v[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) v[k] = r + k < r1 ? __ldg(src + int64_t(stride) * (r + k)) : T(0);
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (r + k < r1) acc += v[k];
+  }
+  return acc;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -202,30 +202,26 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
     }
   });
 
-  // ---- two-phase assembly lists ----
+  // ---- two-phase assembly rows ----
+  // Node rows: node i owns rows [np_ptr[i], np_ptr[i+1]), one per incident tet
+  // in ascending tet order; nrow[4t+a] is the row of (tet t, local node a).
   hm.np_ptr.assign(N + 1, 0);
   for (int64_t i = 0; i < 4 * T; ++i) hm.np_ptr[hm.tets[i] + 1]++;
   for (int64_t i = 0; i < N; ++i) hm.np_ptr[i + 1] += hm.np_ptr[i];
-  hm.np_pair.resize(4 * T);
+  hm.nrow.resize(4 * T);
   {
     std::vector<int32_t> pos(hm.np_ptr.begin(), hm.np_ptr.end() - 1);
     for (int64_t t = 0; t < T; ++t)
-      for (int a = 0; a < 4; ++a) hm.np_pair[pos[hm.tets[4 * t + a]]++] = int32_t((t << 2) | a);
+      for (int a = 0; a < 4; ++a) hm.nrow[4 * t + a] = pos[hm.tets[4 * t + a]]++;
   }
-  hm.sc_ptr.assign(hm.n_blocks + 1, 0);
-  for (int64_t t = 0; t < T; ++t)
-    for (int q = 0; q < 16; ++q) hm.sc_ptr[hm.slot[16 * t + q] + 1]++;
-  for (int64_t b = 0; b < hm.n_blocks; ++b) hm.sc_ptr[b + 1] += hm.sc_ptr[b];
-  hm.sc_ent.resize(16 * T);
-  {
-    std::vector<int32_t> pos(hm.sc_ptr.begin(), hm.sc_ptr.end() - 1);
-    for (int64_t t = 0; t < T; ++t)
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-          const int q = a <= b ? blk_q(a, b) : blk_q(b, a);
-          const int code = a <= b ? q : q + 16;
-          hm.sc_ent[pos[hm.slot[16 * t + 4 * a + b]]++] = int32_t((t << 5) | code);
-        }
+  // block slots of (i, j) and (j, i) for every edge i < j
+  hm.edge_slot.resize(2 * hm.n_edges);
+  for (int64_t e = 0; e < hm.n_edges; ++e) {
+    const int32_t i = hm.edges[2 * e], j = hm.edges[2 * e + 1];
+    hm.edge_slot[2 * e] =
+        int32_t(std::lower_bound(hm.col.begin() + hm.row_ptr[i], hm.col.begin() + hm.row_ptr[i + 1], j) - hm.col.begin());
+    hm.edge_slot[2 * e + 1] =
+        int32_t(std::lower_bound(hm.col.begin() + hm.row_ptr[j], hm.col.begin() + hm.row_ptr[j + 1], i) - hm.col.begin());
   }
   if (T >= (int64_t(1) << 26)) {
     err = "at most 2^26 tets per mesh";
@@ -321,8 +317,13 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
   hm.et_tet.resize(6 * T);
   {
     std::vector<int32_t> pos(hm.et_ptr.begin(), hm.et_ptr.end() - 1);
+    hm.erow.resize(6 * T);
     for (int64_t i = 0; i < T; ++i)
-      for (int k = 0; k < 6; ++k) hm.et_tet[pos[hm.tet_edges[6 * i + k]]++] = int32_t(i);
+      for (int k = 0; k < 6; ++k) {
+        const int32_t r = pos[hm.tet_edges[6 * i + k]]++;
+        hm.et_tet[r] = int32_t(i);
+        hm.erow[6 * i + k] = r;   // edge rows follow the edge -> tet lists
+      }
   }
 
   // ---- Eq. 20 neighbour lists on rest centroids, w = V_j (1 - r^2/R^2)^2 normalised ----

@@ -420,12 +420,67 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
 }
 
 // Two-phase FP64 assembly (no colours, no atomics, one launch per phase).
-// k_elem64 (thread per tet) writes the tet's ten upper-triangle blocks of
+// k_elem64 (thread per tet) computes the tet's ten upper-triangle blocks of
 // (dt beta + dt^2) chi k_e and its four rhs shares dt chi (f_a - (beta+dt)(k_e v)_a)
-// to its row of the element buffer; k_gather64 (thread per matrix entry or
-// rhs component) sums them in a fixed precomputed order and adds mass,
-// external force and mass damping.
-constexpr int kElemW64 = 104;
+// and writes each straight into the assembly row it belongs to: local node a's
+// diagonal block and rhs share to node row nrow[4t+a] (12 values), local edge
+// k's block to edge row erow[6t+k] (9 values, oriented for the global edge
+// (i, j), i < j).  A node's or an edge's rows are contiguous, so k_gather64
+// (thread per matrix entry or rhs component) streams through them in a fixed
+// order and adds mass, external force and mass damping.
+constexpr int kNodeRow = 12, kEdgeRow = 9;
+
+// where a tet's contributions go (the writes scatter; the gather reads stream)
+struct ElemRows64 {
+  double* nb;        // node rows [4T][12]
+  double* eb;        // edge rows [6T][9]
+  const int32_t* nr; // nrow + 4t
+  const int32_t* er; // erow + 6t
+  unsigned flip;     // bit k: the tet lists local edge k against the global (i < j) order
+  __device__ __forceinline__ ElemRows64(const DevMesh& m, int64_t t, const int (&nid)[4])
+      : nb(m.ebuf), eb(m.ebuf + int64_t(kNodeRow) * 4 * m.T), nr(m.nrow + 4 * t), er(m.erow + 6 * t), flip(0u) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) flip |= nid[edge_a(k)] > nid[edge_b(k)] ? (1u << k) : 0u;
+  }
+  // block (a, b), a <= b, of the tet's matrix
+  __device__ __forceinline__ void block(int a, int b, const double (&blk)[3][3]) const {
+    if (a == b) {
+      double* d = nb + int64_t(kNodeRow) * __ldg(nr + a);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[3 * r + c] = blk[r][c];
+    } else {
+      const int k = a == 0 ? b - 1 : a + b;   // local edge of (a, b)
+      double* d = eb + int64_t(kEdgeRow) * __ldg(er + k);
+      const bool tr = (flip >> k) & 1u;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[tr ? 3 * c + r : 3 * r + c] = blk[r][c];
+    }
+  }
+  __device__ __forceinline__ void rhs(int a, const double (&f)[3]) const {
+    double* d = nb + int64_t(kNodeRow) * __ldg(nr + a) + 9;
+    d[0] = f[0];
+    d[1] = f[1];
+    d[2] = f[2];
+  }
+  __device__ __forceinline__ void zero() const {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      double* d = nb + int64_t(kNodeRow) * __ldg(nr + a);
+#pragma unroll
+      for (int q = 0; q < kNodeRow; ++q) d[q] = 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double* d = eb + int64_t(kEdgeRow) * __ldg(er + k);
+#pragma unroll
+      for (int q = 0; q < kEdgeRow; ++q) d[q] = 0.0;
+    }
+  }
+};
 
 // Stable Neo-Hookean element (Eq. 35, squared reading) from the deformation
 // gradient F = Ds B (B = Dm^-1), with the gradient operator G_0 = -(B_0 + B_1 +
@@ -438,10 +493,9 @@ constexpr int kElemW64 = 104;
 // StVK body: ten upper blocks of (dt beta + dt^2) chi K and the rhs shares
 // dt chi (f_a - (beta + dt) (K v)_a).
 __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt, const StepScalars& sp, int64_t t,
-                                           double* out, double chi) {
+                                           const int (&nid)[4], double chi) {
   const double dt = sp.dt, beta = mt.beta, mu = mt.mu, lam = mt.lam;
-  const int4 n = m.tets[t];
-  const int nid[4] = {n.x, n.y, n.z, n.w};
+  const ElemRows64 out(m, t, nid);
   double Px[4][3], U[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -531,21 +585,18 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
         Kv[a][r] += blk[r][0] * U[b][0] + blk[r][1] * U[b][1] + blk[r][2] * U[b][2];
         if (a != b) Kv[b][r] += blk[0][r] * U[a][0] + blk[1][r] * U[a][1] + blk[2][r] * U[a][2];
       }
-      double* dst = out + 9 * blk_q(a, b);
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dst[3 * r + c] = blk[r][c];
+      out.block(a, b, blk);
     }
   // rhs shares dt chi (f_a - (beta + dt) (K v)_a): the blocks carry (dt beta + dt^2) chi = dt chi (beta + dt),
   // so the damping/velocity term is the scaled blocks' K v itself
   const double sf = dt * chi * V;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a) {
+    double f[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[90 + 3 * a + c] = -sf * (c1 * u[a][c] + c2 * z[a][c]) - Kv[a][c];
-  out[102] = 0.0;
-  out[103] = 0.0;
+    for (int c = 0; c < 3; ++c) f[c] = -sf * (c1 * u[a][c] + c2 * z[a][c]) - Kv[a][c];
+    out.rhs(a, f);
+  }
 }
 
 __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
@@ -553,14 +604,14 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
 
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
-  double* out = m.ebuf + kElemW64 * t;
-  const double chi = m.chi[t];
-  if (chi == 0.0) {
-    for (int q = 0; q < kElemW64; ++q) out[q] = 0.0;
-    return;
-  }
   const int4 n = m.tets[t];
   const int nid[4] = {n.x, n.y, n.z, n.w};
+  const ElemRows64 out(m, t, nid);
+  const double chi = m.chi[t];
+  if (chi == 0.0) {
+    out.zero();
+    return;
+  }
   const int inc[4][3] = {{0, 1, 2}, {0, 3, 4}, {1, 3, 5}, {2, 4, 5}};
   const double sgn[4][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {1, 1, 1}};
   const int kab[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
@@ -612,9 +663,7 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
       }
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) out[90 + 3 * a + c] = f[a][c];
+    for (int a = 0; a < 4; ++a) out.rhs(a, f[a]);
   }
   const double sK = (dt * beta + dt * dt) * chi;
 #pragma unroll
@@ -646,27 +695,22 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
       blk[0][0] += geo;
       blk[1][1] += geo;
       blk[2][2] += geo;
-      double* dst = out + 9 * blk_q(a, b);
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dst[3 * r + c] = blk[r][c];
+      out.block(a, b, blk);
     }
   }
-  out[102] = 0.0;
-  out[103] = 0.0;
 }
 __device__ __forceinline__ void elem_snh64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid,
                                                 unsigned nb) {
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= m.T) return;
-  double* out = m.ebuf + kElemW64 * t;
+  const int4 n = m.tets[t];
+  const int nid[4] = {n.x, n.y, n.z, n.w};
   const double chi = m.chi[t];
   if (chi == 0.0) {
-    for (int q = 0; q < kElemW64; ++q) out[q] = 0.0;
+    ElemRows64(m, t, nid).zero();
     return;
   }
-  elem_snh64(m, mt, sp, t, out, chi);
+  elem_snh64(m, mt, sp, t, nid, chi);
 }
 __global__ void __launch_bounds__(128) k_elem64(DevMesh m, Material mt, StepScalars sp) {
   elem64_body(m, mt, sp, blockIdx.x, gridDim.x);
@@ -681,53 +725,40 @@ __global__ void __launch_bounds__(128) kb_elem64(const BatchTab* __restrict__ ta
 }
 
 // Phase 2 of the assembly: each matrix entry and rhs component is the sum, in
-// a fixed order, of its element contributions (plus the mass term of Eq. 2:
-// lumped on the diagonal, or the consistent m_ij of Eq. 5 on every block).  Threads [0, 9 NB) take one entry of an off-diagonal
-// block each (the 4-6 tets around an edge); threads [9 NB, 9 NB + 12 N) take
-// a node's nine diagonal entries and three rhs components (the ~24 tets around
-// the node).  Neighbouring threads sum lists of similar length, so the FP64
-// adds issue in full warps.
+// ascending tet order, of its element contributions (plus the mass term of
+// Eq. 2: lumped on the diagonal, or the consistent m_ij of Eq. 5 on every
+// block).  Threads [0, 9 NE) take one entry of an edge's block (the 4-6 tets
+// around the edge, rows contiguous) and write it to both (i, j) and, transposed,
+// (j, i); threads [9 NE, 9 NE + 12 N) take a node's nine diagonal entries and
+// three rhs components (the ~24 tets around the node).  Neighbouring threads
+// read neighbouring values, and sum lists of similar length.
 __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const double dt = sp.dt, alpha = mt.alpha;
+  const double cm = (1.0 + dt * alpha) * sp.mscale;
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t n_off = 9 * m.NB;
-  if (t < n_off) {
-    const int64_t slot = t / 9;
-    const int e = int(t - 9 * slot);
-    if (m.diag_blk[m.col[slot]] == slot) return;       // (j, j): done by the node threads
-    const int et = 3 * (e % 3) + e / 3;
-    double acc = 0.0;
-    for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
-      const int ent = m.sc_ent[c];
-      acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
-    }
-    if (m.mass_blk && (e == 0 || e == 4 || e == 8)) acc += (1.0 + dt * alpha) * m.mass_blk[slot] * sp.mscale;
-    m.val[9 * slot + e] = acc;
+  const int64_t n_edge = 9 * m.NE;
+  if (t < n_edge) {
+    const int64_t e = t / 9;
+    const int q = int(t - 9 * e);
+    const double acc = row_sum<8>(m.ebuf + int64_t(kNodeRow) * 4 * m.T + q, kEdgeRow, m.et_ptr[e], m.et_ptr[e + 1]);
+    const int2 sl = m.edge_slot[e];
+    const bool dg = q == 0 || q == 4 || q == 8;
+    m.val[9 * int64_t(sl.x) + q] = (m.mass_blk && dg) ? acc + cm * m.mass_blk[sl.x] : acc;
+    m.val[9 * int64_t(sl.y) + 3 * (q % 3) + q / 3] = (m.mass_blk && dg) ? acc + cm * m.mass_blk[sl.y] : acc;
     return;
   }
-  const int64_t u = t - n_off;
+  const int64_t u = t - n_edge;
   if (u >= 12 * m.N) return;
   const int64_t i = u / 12;
   const int q = int(u - 12 * i);
+  const double acc = row_sum<8>(m.ebuf + q, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
   const double mi = m.mass[i];
   if (q < 9) {
     const int slot = m.diag_blk[i];
-    const int et = 3 * (q % 3) + q / 3;
-    double acc = 0.0;
-    for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
-      const int ent = m.sc_ent[c];
-      acc += m.ebuf[kElemW64 * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : q)];
-    }
-    if (q == 0 || q == 4 || q == 8) acc += (1.0 + dt * alpha) * (m.mass_blk ? m.mass_blk[slot] : mi) * sp.mscale;
-    m.val[9 * int64_t(slot) + q] = acc;
+    m.val[9 * int64_t(slot) + q] = (q == 0 || q == 4 || q == 8) ? acc + cm * (m.mass_blk ? m.mass_blk[slot] : mi) : acc;
   } else {
     const int c3 = q - 9;
     const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
-    double acc = 0.0;
-    for (int k = m.np_ptr[i]; k < m.np_ptr[i + 1]; ++k) {
-      const int pr = m.np_pair[k];
-      acc += m.ebuf[kElemW64 * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + c3];
-    }
     double mv = mi * m.v[3 * i + c3];
     if (m.mass_blk) {   // consistent mass: (M v)_i over the row
       mv = 0.0;

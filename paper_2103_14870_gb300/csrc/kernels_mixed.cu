@@ -270,17 +270,23 @@ __global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restr
 // Two-phase assembly, no colours and no atomics.
 // Phase 1 (k_elem32, one thread per tet): the tet's ten upper-triangle 3x3
 // blocks (a <= b) of (dt beta + dt^2) chi k_e and its four nodal rhs shares
-// dt chi (f_a - (beta + dt) (k_e v)_a), written to a per-tet row of kElemW floats.
-// Phase 2 (k_gather32, one warp per node row): lane p sums the contributions of
-// block slot p in a fixed, precomputed order (transposing lower blocks), adds
-// the lumped mass, and lane 0 inverts the diagonal block (block Jacobi); lanes
-// 0..2 sum the node's rhs shares and add the external and damping terms.
+// dt chi (f_a - (beta + dt) (k_e v)_a), built in a shared-memory row of
+// kElemW floats, then written by the CTA into the assembly rows they belong
+// to: local node a's diagonal block and rhs share to node row nrow[4t+a] (12
+// floats), local edge k's block to edge row erow[6t+k] (9 floats, oriented for
+// the global edge (i, j), i < j).
+// Phase 2 (k_gather32): a thread per matrix entry or rhs component streams
+// through the contiguous rows of its edge or node in ascending tet order and
+// adds the mass, external and damping terms; k_pinv32 then inverts the
+// diagonal blocks (block Jacobi).
 // ---------------------------------------------------------------------------
 
-constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad (16-byte rows)
+constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad
+constexpr int kNodeRow = 12, kEdgeRow = 9;
 // Each thread's row is built in shared memory (stride 105 floats: conflict-free
-// for 32 consecutive threads) and the CTA then writes its 128 contiguous rows
-// with coalesced 16-byte stores.
+// for 32 consecutive threads); each warp then writes its 32 rows out, the node
+// rows as 16-byte stores and the edge rows as runs of 9 consecutive floats,
+// with the destination rows passed between lanes by shuffles.
 constexpr int kElemThreads = 128, kElemSS = kElemW + 1;
 constexpr unsigned kElemSmem = kElemThreads * kElemSS * 4;
 
@@ -394,17 +400,61 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
 __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   extern __shared__ float sh_rows[];
   const int64_t t0 = bid * int64_t(blockDim.x), t = t0 + threadIdx.x;
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   const MixDev& x = m.mx;
-  float* o = sh_rows + threadIdx.x * kElemSS;
-  if (t < m.T) elem32_row(m, sp, t, o);
-  __syncthreads();
-  // coalesced write-out of the CTA's rows [t0, t0 + rows)
-  const int rows = int(m.T - t0 < int64_t(blockDim.x) ? m.T - t0 : int64_t(blockDim.x));
-  float4* dst = reinterpret_cast<float4*>(x.ebuf + kElemW * t0);
-  for (int q = threadIdx.x; q < rows * (kElemW / 4); q += blockDim.x) {
-    const int r = q / (kElemW / 4), c = 4 * (q - r * (kElemW / 4));
-    const float* src = sh_rows + r * kElemSS + c;
-    dst[q] = make_float4(src[0], src[1], src[2], src[3]);
+  int32_t nr[4] = {0, 0, 0, 0}, er[6] = {0, 0, 0, 0, 0, 0};
+  unsigned fl = 0u;
+  if (t < m.T) {
+    elem32_row(m, sp, t, sh_rows + threadIdx.x * kElemSS);
+    const int4 n = m.tets[t];
+    const int nid[4] = {n.x, n.y, n.z, n.w};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      fl |= nid[edge_a(k)] > nid[edge_b(k)] ? (1u << k) : 0u;
+      er[k] = m.erow[6 * t + k];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) nr[a] = m.nrow[4 * t + a];
+  }
+  __syncwarp();
+  // each warp writes out its own 32 rows; the row indices come from the owning lane
+  const int64_t rem = m.T - (t0 + wbase);
+  const int nw = rem < 32 ? int(rem) : 32;   // live rows of this warp (the whole warp agrees)
+  if (nw <= 0) return;
+  const float* wrows = sh_rows + wbase * kElemSS;
+  // node rows: 3 float4 each (diagonal block of node a, then its rhs share)
+  float4* nbuf = reinterpret_cast<float4*>(x.ebuf);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int db = 9 * blk_q(a, a);
+#pragma unroll
+    for (int j = lane; j < 96; j += 32) {
+      const int r = j / 3, part = j - 3 * r;
+      const int32_t row = __shfl_sync(0xffffffffu, nr[a], r);
+      if (r < nw) {
+        const float* src = wrows + r * kElemSS;
+        float v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int q = 4 * part + c;
+          v[c] = q < 9 ? src[db + q] : src[90 + 3 * a + q - 9];
+        }
+        nbuf[3 * int64_t(row) + part] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+  }
+  // edge rows: 9 consecutive floats each, transposed where the global order flips the edge
+  float* ebuf = x.ebuf + int64_t(kNodeRow) * 4 * m.T;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int bq = 9 * blk_q(edge_a(k), edge_b(k));
+#pragma unroll
+    for (int j = lane; j < 288; j += 32) {
+      const int r = j / 9, q = j - 9 * r;
+      const int32_t row = __shfl_sync(0xffffffffu, er[k], r);
+      const unsigned f = __shfl_sync(0xffffffffu, fl, r);
+      if (r < nw) ebuf[int64_t(kEdgeRow) * row + q] = wrows[r * kElemSS + bq + (((f >> k) & 1u) ? 3 * (q % 3) + q / 3 : q)];
+    }
   }
 }
 
@@ -417,64 +467,69 @@ __global__ void __launch_bounds__(128) kb_elem32(const BatchTab* __restrict__ ta
   elem32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
+// Phase 2 in the layout of the FP64 gather: threads [0, 9 NE) take one entry
+// of an edge's block (the 4-6 tets around the edge, rows contiguous) and write
+// it to (i, j) and, transposed, (j, i); threads [9 NE, 9 NE + 12 N) take a
+// node's nine diagonal entries (with the mass) and three rhs components (the
+// ~24 tets around the node).  Sums run in ascending tet order (deterministic).
 __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const float dtf = sp.dtf, alphaf = sp.alphaf, cmf = sp.cmf;
-
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  if (i >= m.N) return;                               // whole warp leaves together
-  __shared__ float dg[8][9];
-  const int wib = threadIdx.x >> 5;
   const MixDev& x = m.mx;
-  const int rb = m.row_ptr[i], rl = m.row_ptr[i + 1] - rb;
-  const int dslot = m.diag_blk[i];
-  const float mi = x.mass32[i];
-  // lane o takes entry (r, c) = o % 9 of block slot rb + o / 9: the lanes of one
-  // pass read 3-4 whole element blocks per request
-  for (int o = lane; o < 9 * rl; o += 32) {
-    const int p = o / 9, e = o - 9 * p;
-    const int slot = rb + p;
-    const int et = 3 * (e % 3) + e / 3;          // entry of the transposed block
-    float acc = 0.f;
-    for (int c = m.sc_ptr[slot]; c < m.sc_ptr[slot + 1]; ++c) {
-      const int ent = m.sc_ent[c];
-      acc += x.ebuf[kElemW * int64_t(ent >> 5) + 9 * (ent & 15) + ((ent & 16) ? et : e)];
-    }
-    if (x.mass_blk32) {
-      if (e == 0 || e == 4 || e == 8) acc += cmf * x.mass_blk32[slot];   // consistent mass (Eq. 5)
-      if (slot == dslot) dg[wib][e] = acc;
-    } else if (slot == dslot) {
-      if (e == 0 || e == 4 || e == 8) acc += cmf * mi;
-      dg[wib][e] = acc;
-    }
-    x.val32[9 * int64_t(slot) + e] = acc;
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t n_edge = 9 * m.NE;
+  if (t < n_edge) {
+    const int64_t e = t / 9;
+    const int q = int(t - 9 * e);
+    const float acc = row_sum<8>(x.ebuf + int64_t(kNodeRow) * 4 * m.T + q, kEdgeRow, m.et_ptr[e], m.et_ptr[e + 1]);
+    const int2 sl = m.edge_slot[e];
+    const bool dg = q == 0 || q == 4 || q == 8;
+    x.val32[9 * int64_t(sl.x) + q] = (x.mass_blk32 && dg) ? acc + cmf * x.mass_blk32[sl.x] : acc;   // Eq. 5
+    x.val32[9 * int64_t(sl.y) + 3 * (q % 3) + q / 3] = (x.mass_blk32 && dg) ? acc + cmf * x.mass_blk32[sl.y] : acc;
+    return;
   }
-  if (lane < 3) {
-    float acc = 0.f;
-    for (int k = m.np_ptr[i]; k < m.np_ptr[i + 1]; ++k) {
-      const int pr = m.np_pair[k];
-      acc += x.ebuf[kElemW * int64_t(pr >> 2) + 90 + 3 * (pr & 3) + lane];
-    }
-    const float fe = sp.has_fext ? x.fext32[3 * i + lane] : 0.f;
-    float mv = mi * x.v32[3 * i + lane];
+  const int64_t u = t - n_edge;
+  if (u >= 12 * m.N) return;
+  const int64_t i = u / 12;
+  const int q = int(u - 12 * i);
+  const float acc = row_sum<8>(x.ebuf + q, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
+  const float mi = x.mass32[i];
+  if (q < 9) {
+    const int slot = m.diag_blk[i];
+    x.val32[9 * int64_t(slot) + q] =
+        (q == 0 || q == 4 || q == 8) ? acc + cmf * (x.mass_blk32 ? x.mass_blk32[slot] : mi) : acc;
+  } else {
+    const int c3 = q - 9;
+    const float fe = sp.has_fext ? x.fext32[3 * i + c3] : 0.f;
+    float mv = mi * x.v32[3 * i + c3];
     if (x.mass_blk32) {
       mv = 0.f;
-      for (int b = rb; b < rb + rl; ++b) mv += x.mass_blk32[b] * x.v32[3 * int64_t(m.col[b]) + lane];
+      for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) mv += x.mass_blk32[b] * x.v32[3 * int64_t(m.col[b]) + c3];
     }
-    x.rhs32[3 * i + lane] = acc + dtf * (fe - alphaf * mv);
+    x.rhs32[3 * i + c3] = acc + dtf * (fe - alphaf * mv);
   }
-  __syncwarp();
-  if (lane == 0) {
-    const float* d = dg[wib];
-    const float c00 = d[4] * d[8] - d[5] * d[7], c01 = d[2] * d[7] - d[1] * d[8], c02 = d[1] * d[5] - d[2] * d[4];
-    const float c10 = d[5] * d[6] - d[3] * d[8], c11 = d[0] * d[8] - d[2] * d[6], c12 = d[2] * d[3] - d[0] * d[5];
-    const float c20 = d[3] * d[7] - d[4] * d[6], c21 = d[1] * d[6] - d[0] * d[7], c22 = d[0] * d[4] - d[1] * d[3];
-    const float id = 1.f / (d[0] * c00 + d[1] * c10 + d[2] * c20);
-    float* pi = x.pinv32 + 9 * i;
-    pi[0] = c00 * id; pi[1] = c01 * id; pi[2] = c02 * id;
-    pi[3] = c10 * id; pi[4] = c11 * id; pi[5] = c12 * id;
-    pi[6] = c20 * id; pi[7] = c21 * id; pi[8] = c22 * id;
-  }
+}
+
+// block-Jacobi inverse of every node's assembled diagonal block (FP32)
+__device__ __forceinline__ void pinv32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= m.N) return;
+  const float* d = m.mx.val32 + 9 * int64_t(m.diag_blk[i]);
+  const float c00 = d[4] * d[8] - d[5] * d[7], c01 = d[2] * d[7] - d[1] * d[8], c02 = d[1] * d[5] - d[2] * d[4];
+  const float c10 = d[5] * d[6] - d[3] * d[8], c11 = d[0] * d[8] - d[2] * d[6], c12 = d[2] * d[3] - d[0] * d[5];
+  const float c20 = d[3] * d[7] - d[4] * d[6], c21 = d[1] * d[6] - d[0] * d[7], c22 = d[0] * d[4] - d[1] * d[3];
+  const float id = 1.f / (d[0] * c00 + d[1] * c10 + d[2] * c20);
+  float* pi = m.mx.pinv32 + 9 * i;
+  pi[0] = c00 * id; pi[1] = c01 * id; pi[2] = c02 * id;
+  pi[3] = c10 * id; pi[4] = c11 * id; pi[5] = c12 * id;
+  pi[6] = c20 * id; pi[7] = c21 * id; pi[8] = c22 * id;
+}
+__global__ void __launch_bounds__(256) k_pinv32(DevMesh m, Material mt, StepScalars sp) {
+  pinv32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256) kb_pinv32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_pinv32, blockIdx.x, bid, nb);
+  pinv32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 __global__ void __launch_bounds__(256) k_gather32(DevMesh m, Material mt, StepScalars sp) {
   gather32_body(m, mt, sp, blockIdx.x, gridDim.x);
@@ -965,6 +1020,7 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
       k_elem32<<<d.blocks, d.threads, kElemSmem, s>>>(m, mt, sp);
       break;
     case kB_gather32: k_gather32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_pinv32: k_pinv32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_fext32: k_fext32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_residual: k_ir_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp, first); break;
     case kB_ir_inner_init: k_ir_inner_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
@@ -992,6 +1048,7 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
       kb_elem32<<<blocks, threads, kElemSmem, s>>>(tab);
       break;
     case kB_gather32: kb_gather32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_pinv32: kb_pinv32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_fext32: kb_fext32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_residual: kb_ir_residual<<<blocks, threads, 0, s>>>(tab, first); break;
     case kB_ir_inner_init: kb_ir_inner_init<<<blocks, threads, 0, s>>>(tab); break;
