@@ -35,9 +35,9 @@ inline unsigned red_grid(int64_t n) {   // FP64 reducing kernels: one thread per
   const int64_t b = (n + 255) / 256;
   return unsigned(b < 1 ? 1 : (b > kMaxPartials ? kMaxPartials : b));
 }
-inline unsigned ir_grid(int64_t n) {    // refinement kernels: <= 4 CTAs per SM, grid-stride
+inline unsigned ir_grid(int64_t n, int per_sm = 4) {    // refinement kernels: <= per_sm CTAs per SM, grid-stride
   const int64_t b = (n + 255) / 256;
-  return unsigned(b < 1 ? 1 : (b > 4 * 152 ? 4 * 152 : b));
+  return unsigned(b < 1 ? 1 : (b > per_sm * 152 ? per_sm * 152 : b));
 }
 }  // namespace
 
@@ -59,7 +59,8 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_pcg_p: return {red_grid(3 * N), 256};
     case kB_integrate: case kB_integrate32: case kB_refresh32: return {cdiv(3 * N, 256), 256};
     case kB_fext32: return {sp.has_fext ? cdiv(3 * N, 256) : 0u, 256};
-    case kB_ir_residual: case kB_ir_spmv: return {ir_grid(16 * N), 256};
+    case kB_ir_residual: return {ir_grid(8 * N, 5), 256};
+    case kB_ir_spmv: return {ir_grid(16 * N), 256};
     case kB_ir_inner_init: case kB_ir_update: return {ir_grid(N), 256};
     case kB_ir_p: case kB_ir_apply: return {ir_grid(3 * N), 256};
     case kB_step_begin: return {cdiv(3 * N, 256), 256};

@@ -654,10 +654,23 @@ __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float
 }
 
 // r = b - A32 dv on free rows, with A32 dv formed in double-float (dv = dv_hi +
-// dv_lo) and b - A dv in double-float; half a warp per block row (lane j takes
-// blocks j, j+16, ...), then a 16-lane double-float reduction.  The inner
+// dv_lo) and b - A dv in double-float; eight lanes per block row (lane j takes
+// blocks j, j+8, ..., two at a time so that both blocks' loads are in flight
+// before the arithmetic), then an 8-lane double-float reduction.  The inner
 // solve's right-hand side is the leading float of r; ||r||^2 accumulates in
 // double-float.
+__device__ __forceinline__ void df_block_acc(float (&hi)[3], float (&lo)[3], const float (&a)[9], const float (&xh)[3],
+                                             const float (&xl)[3]) {
+#pragma unroll
+  for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float p, pe;
+      two_prod(a[3 * rr + c], xh[c], p, pe);
+      pe = fmaf(a[3 * rr + c], xl[c], pe);
+      df_add(hi[rr], lo[rr], p, pe);
+    }
+}
 __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb, int first) {
 
   IrState* S = m.mx.ir;
@@ -665,45 +678,49 @@ __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Materia
   // finished, residual not yet formed); flags are written by the last CTA only
   if (!first && (S->done || !S->in_done || S->applied)) return;
   const MixDev& x = m.mx;
-  const int j16 = threadIdx.x & 15;
-  const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+  const int j8 = threadIdx.x & 7;
+  const unsigned gmask = 0xffu << (threadIdx.x & 24);
   float nh_[1] = {0.f}, nl_[1] = {0.f};
-  const int64_t nh = (int64_t(nb) * blockDim.x) >> 4;
-  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
+  const int64_t ng = (int64_t(nb) * blockDim.x) >> 3;
+  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 3; i < m.N; i += ng) {
     float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
+    // independent loads first; pinned rows run the loop too and are zeroed at the end
     const bool fixed = m.pinned[i];
-    if (!fixed) {
-      for (int b = m.row_ptr[i] + j16; b < m.row_ptr[i + 1]; b += 16) {
-        const int64_t j = m.col[b];
-        const float* a = x.val32 + 9 * int64_t(b);
-        float xh[3], xl[3];
-        ld3f(x.dv_hi, j, xh);
-        ld3f(x.dv_lo, j, xl);
+    const int b1 = m.row_ptr[i + 1];
+    float bh[3] = {0.f, 0.f, 0.f};
+    if (j8 == 0) ld3f(x.rhs32, i, bh);
+    {
+      for (int b = m.row_ptr[i] + j8; b < b1; b += 16) {
+        const bool two = b + 8 < b1;
+        const int64_t j0 = m.col[b], j1 = two ? m.col[b + 8] : j0;
+        float a0[9], a1[9], xh0[3], xl0[3], xh1[3], xl1[3];
 #pragma unroll
-        for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float p, pe;
-            two_prod(a[3 * rr + c], xh[c], p, pe);
-            pe = fmaf(a[3 * rr + c], xl[c], pe);
-            df_add(hi[rr], lo[rr], p, pe);
-          }
+        for (int q = 0; q < 9; ++q) {
+          a0[q] = x.val32[9 * int64_t(b) + q];
+          a1[q] = two ? x.val32[9 * int64_t(b + 8) + q] : 0.f;
+        }
+        ld3f(x.dv_hi, j0, xh0);
+        ld3f(x.dv_lo, j0, xl0);
+        ld3f(x.dv_hi, j1, xh1);
+        ld3f(x.dv_lo, j1, xl1);
+        df_block_acc(hi, lo, a0, xh0, xl0);
+        if (two) df_block_acc(hi, lo, a1, xh1, xl1);
       }
     }
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
+    for (int o = 4; o > 0; o >>= 1)
 #pragma unroll
       for (int rr = 0; rr < 3; ++rr) {
-        const float oh = __shfl_xor_sync(hmask, hi[rr], o);
-        const float ol = __shfl_xor_sync(hmask, lo[rr], o);
+        const float oh = __shfl_xor_sync(gmask, hi[rr], o);
+        const float ol = __shfl_xor_sync(gmask, lo[rr], o);
         df_add(hi[rr], lo[rr], oh, ol);
       }
-    if (j16 == 0) {
+    if (j8 == 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         float rh = 0.f, rl = 0.f;
         if (!fixed) {
-          rh = x.rhs32[3 * i + c];
+          rh = bh[c];
           df_add(rh, rl, -hi[c], -lo[c]);
         }
         x.rres[3 * i + c] = rh;
@@ -734,10 +751,10 @@ __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Materia
     }
   }
 }
-__global__ void __launch_bounds__(kThreads) k_ir_residual(DevMesh m, Material mt, StepScalars sp, int first) {
+__global__ void __launch_bounds__(kThreads, 5) k_ir_residual(DevMesh m, Material mt, StepScalars sp, int first) {
   ir_residual_body(m, mt, sp, blockIdx.x, gridDim.x, first);
 }
-__global__ void __launch_bounds__(kThreads) kb_ir_residual(const BatchTab* __restrict__ tab, int first) {
+__global__ void __launch_bounds__(kThreads, 5) kb_ir_residual(const BatchTab* __restrict__ tab, int first) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_ir_residual, blockIdx.x, bid, nb);
   ir_residual_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb, first);
