@@ -47,7 +47,7 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_tet_stress: case kB_tet_chi: case kB_tet_stress32: case kB_tet_chi32: case kB_chi_to32:
       return {cdiv(T, 256), 256};
     case kB_nonlocal: return {mt.radius > 0.0 ? cdiv(T, 256) : 0u, 256};
-    case kB_nonlocal32: return {mt.radius > 0.0 ? cdiv(32 * T, 256) : 0u, 256};
+    case kB_nonlocal32: return {mt.radius > 0.0 ? cdiv(T, kNlTile) : 0u, 256};
     case kB_edge_driver: case kB_edge_driver32: return {cdiv(NE, 256), 256};
     case kB_node_init: return {cdiv(N, 256), 256};
     case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
@@ -488,8 +488,10 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.restB, mxh.restB, float);
     UP(d.mx.edge_e0, mxh.edge_e0, float);
     UP(d.mx.nb_ptr, mxh.nb_ptr, int64_t);
-    UP(d.mx.nb_csr, mxh.nb_csr, int32_t);
+    UP(d.mx.nb_loc, mxh.nb_loc, uint16_t);
     UP(d.mx.nb_wc, mxh.nb_wc, float);
+    UP(d.mx.nl_uptr, mxh.nl_uptr, int64_t);
+    UP(d.mx.nl_uidx, mxh.nl_uidx, int32_t);
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());
     UP(d.mx.mass32, m32, float);
     if (!mass_blk.empty()) {

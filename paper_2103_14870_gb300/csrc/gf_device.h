@@ -44,8 +44,10 @@ struct MixDev {
   const float* restB = nullptr;       // [T][kRBStride]
   const float* edge_e0 = nullptr;     // [NE][3]
   const int64_t* nb_ptr = nullptr;    // [T+1] CSR Eq. 20 lists
-  const int32_t* nb_csr = nullptr;
-  const float* nb_wc = nullptr;
+  const uint16_t* nb_loc = nullptr;   // per pair: the neighbour's position in its tile's union
+  const float* nb_wc = nullptr;       // per pair: FP32 weight
+  const int64_t* nl_uptr = nullptr;   // [ceil(T / kNlTile) + 1] tile unions
+  const int32_t* nl_uidx = nullptr;   // union members (global tet ids, ascending per tile)
   const float* mass32 = nullptr;      // [N]
   const float* mass_blk32 = nullptr;  // [NB] consistent mass per block slot (NULL: lumped)
   const double* X = nullptr;          // [3N] rest positions

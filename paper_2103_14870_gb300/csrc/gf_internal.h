@@ -48,15 +48,26 @@ struct NeighbourSell {            // Eq. 20 neighbour lists, 32 tets per group, 
 //   restB [T][12]: B = Dm^-1 row-major (9), pad
 enum Rest32Field : int { kRAE0 = 0, kRAH = 9, kRAV = 30, kRAStride = 32, kRBStride = 12 };
 
+// Tiles of the mixed Eq. 20 kernel: kNlTile consecutive tets share one CTA,
+// which stages the union of their neighbour sets (at most kNlCap rows) in
+// shared memory; each pair names its neighbour by its position in that union.
+constexpr int kNlTile = 128;
+constexpr int kNlCap = 1792;
+constexpr int64_t kNlMaxUnion = 65536;   // 16-bit positions
+
 // Extra host data of the mixed-precision path (two-phase assembly).
 struct MixedHost {
   std::vector<float> restA;         // [T][kRAStride]
   std::vector<float> restB;         // [T][kRBStride]
   std::vector<float> edge_e0;       // [NE][3] rest edge vectors (b - a)
-  // CSR neighbour lists (one warp per tet): nb_ptr [T+1], nb_csr (neighbour << 0), nb_wc FP32 weights
+  // CSR neighbour lists: nb_ptr [T+1]; per pair the neighbour's position in its
+  // tile's union (nb_loc) and the FP32 weight (nb_wc); per tile the union's
+  // global tet ids nl_uidx[nl_uptr[g], nl_uptr[g+1]), ascending
   std::vector<int64_t> nb_ptr;
-  std::vector<int32_t> nb_csr;
+  std::vector<uint16_t> nb_loc;
   std::vector<float> nb_wc;
+  std::vector<int64_t> nl_uptr;
+  std::vector<int32_t> nl_uidx;
 };
 
 

@@ -436,6 +436,48 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
   return GF_OK;
 }
 
+// Order of one tet's pairs for the shared-memory reads of the mixed Eq. 20
+// kernel: lane l of chunk c takes pair beg + 32 c + l, and reads the six
+// floats of union row loc as three 8-byte words at bank pair (3 loc + h) mod
+// 16.  The pairs are dealt to the chunks round-robin in (loc mod 16, loc)
+// order, so each chunk holds about two of every residue, and within a chunk
+// the first copy of each residue goes to lanes 0-15 and the second to 16-31:
+// the half-warps then read 16 distinct bank pairs (no conflicts).  Only the
+// order of the terms changes.
+void deal_pairs(MixedHost& mx, int64_t i) {
+  const int64_t b = mx.nb_ptr[i], n = mx.nb_ptr[i + 1] - b;
+  if (n <= 1) return;
+  std::vector<std::pair<uint16_t, float>> pr(n), out(n);
+  for (int64_t k = 0; k < n; ++k) pr[k] = {mx.nb_loc[b + k], mx.nb_wc[b + k]};
+  auto key = [](const std::pair<uint16_t, float>& a) { return std::make_pair(a.first % 16, a.first); };
+  std::sort(pr.begin(), pr.end(), [&](const auto& a, const auto& c) { return key(a) < key(c); });
+  const int64_t nc = (n + 31) / 32;
+  // chunk c holds min(32, n - 32 c) pairs: all but the last are full
+  std::vector<std::vector<std::pair<uint16_t, float>>> chunk(nc);
+  for (int64_t k = 0, c = 0; k < n; ++k, c = (c + 1) % nc) {
+    while (int64_t(chunk[c].size()) == std::min<int64_t>(32, n - 32 * c)) c = (c + 1) % nc;
+    chunk[c].push_back(pr[k]);
+  }
+  int64_t o = 0;
+  for (auto& c : chunk) {
+    std::sort(c.begin(), c.end(), [&](const auto& a, const auto& d) { return key(a) < key(d); });
+    // first copies of the residues to the low half, the rest after them
+    std::vector<std::pair<uint16_t, float>> lo, hi;
+    for (size_t k = 0; k < c.size(); ++k)
+      ((k == 0 || c[k].first % 16 != c[k - 1].first % 16) && lo.size() < 16 ? lo : hi).push_back(c[k]);
+    while (lo.size() < 16 && !hi.empty()) {
+      lo.push_back(hi.back());
+      hi.pop_back();
+    }
+    for (auto& e : lo) out[o++] = e;
+    for (auto& e : hi) out[o++] = e;
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    mx.nb_loc[b + k] = out[k].first;
+    mx.nb_wc[b + k] = out[k].second;
+  }
+}
+
 gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, std::string& err) {
   const int64_t N = hm.n_nodes, T = hm.n_tets, NE = hm.n_edges;
   mx.restA.assign(size_t(kRAStride) * T, 0.f);
@@ -467,19 +509,49 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
       }
       mx.nb_ptr[i + 1] = mx.nb_ptr[i] + cnt;
     }
-    mx.nb_csr.resize(mx.nb_ptr[T]);
+    std::vector<int32_t> nb_csr(mx.nb_ptr[T]);
     mx.nb_wc.resize(mx.nb_ptr[T]);
     for (int64_t i = 0; i < T; ++i) {
       int64_t g = i / 32, l = i % 32, p = mx.nb_ptr[i];
       for (int32_t k = 0; k < S.group_len[g]; ++k) {
         int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
         if (S.w[o] > 0.0) {
-          mx.nb_csr[p] = S.idx[o];
+          nb_csr[p] = S.idx[o];
           mx.nb_wc[p] = float(S.w[o]);
           ++p;
         }
       }
     }
+    // tile unions and 16-bit positions in them
+    const int64_t NT = (T + kNlTile - 1) / kNlTile;
+    std::vector<std::vector<int32_t>> U(NT);
+    mx.nb_loc.resize(nb_csr.size());
+    std::atomic<int64_t> too_big{-1};
+    parallel_for(NT, [&](int64_t b, int64_t e) {
+      for (int64_t g = b; g < e; ++g) {
+        const int64_t p0 = mx.nb_ptr[kNlTile * g], p1 = mx.nb_ptr[std::min(T, kNlTile * (g + 1))];
+        std::vector<int32_t>& u = U[g];
+        u.assign(nb_csr.begin() + p0, nb_csr.begin() + p1);
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        if (int64_t(u.size()) > kNlMaxUnion) {
+          too_big = g;
+          continue;
+        }
+        for (int64_t p = p0; p < p1; ++p)
+          mx.nb_loc[p] = uint16_t(std::lower_bound(u.begin(), u.end(), nb_csr[p]) - u.begin());
+        for (int64_t i = kNlTile * g; i < std::min(T, kNlTile * (g + 1)); ++i) deal_pairs(mx, i);
+      }
+    });
+    if (too_big >= 0) {
+      err = "Eq. 20 neighbour sets too large for the mixed-precision path (a tile of " + std::to_string(kNlTile) +
+            " tets reaches more than " + std::to_string(kNlMaxUnion) + " tets; reduce the radius)";
+      return GF_UNSUPPORTED;
+    }
+    mx.nl_uptr.assign(NT + 1, 0);
+    for (int64_t g = 0; g < NT; ++g) mx.nl_uptr[g + 1] = mx.nl_uptr[g] + int64_t(U[g].size());
+    mx.nl_uidx.resize(mx.nl_uptr[NT]);
+    for (int64_t g = 0; g < NT; ++g) std::copy(U[g].begin(), U[g].end(), mx.nl_uidx.begin() + mx.nl_uptr[g]);
   }
   return GF_OK;
 }

@@ -146,40 +146,145 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
   tet_stress32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-// Eq. 20 sum in FP32: one warp per tet over its CSR neighbour list (coalesced
-// index and weight loads; the gathered 32-byte stress rows of a tet's
-// neighbours come from short runs of consecutive tets), then a fixed-order
-// warp reduction (deterministic).
-__device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+// Eq. 20 sum in FP32, tiled.  A CTA takes kNlTile consecutive tets and first
+// stages the union of their neighbour sets (ascending tet ids, six floats a
+// row) in shared memory; a tile whose union exceeds kNlCap rows reads the rows
+// from global memory instead.  Then one warp per tet (16 per warp) streams the
+// tet's pairs (16-bit union position, FP32 weight) with coalesced loads, four
+// per lane in flight; a tet's neighbours are short runs of consecutive tets,
+// so the lanes read neighbouring shared-memory rows.  The six sums are reduced
+// across the warp in a fixed order by a transposing butterfly (each step keeps
+// half of the values per lane), and eight lanes write the 32-byte output row.
+// A lane loads all of a tet's pairs it takes (up to six) at once, and the next
+// tet's while the current one is summed.
+constexpr int kNlThreads = 256, kNlWarpTets = kNlTile / (kNlThreads / 32);
+constexpr unsigned kNlSmem = kNlCap * 24;
 
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t(nb) * blockDim.x) >> 5;
-  for (int64_t t = (bid * int64_t(blockDim.x) + threadIdx.x) >> 5; t < m.T; t += nw) {
-    const int64_t beg = m.mx.nb_ptr[t], end = m.mx.nb_ptr[t + 1];
-    float acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t p = beg + lane; p < end; p += 32) {
-      const int j = __ldg(m.mx.nb_csr + p);
-      const float w = __ldg(m.mx.nb_wc + p);
-      float sj[8];
-      ld8f(m.mx.sig_in32 + 8 * int64_t(j), sj);
+// all-reduce of v[0..7] over the warp: afterwards lane L holds the total of
+// value 4 b4 + 2 b3 + b2 (b_k bit k of L)
+__device__ __forceinline__ float warp_transpose_sum8(const float (&v)[8], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+  float u[4], w2[2];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) acc[q] += w * sj[q];
-    }
+  for (int k = 0; k < 4; ++k) {
+    const float snd = h4 ? v[k] : v[4 + k];
+    u[k] = (h4 ? v[4 + k] : v[k]) + __shfl_xor_sync(0xffffffffu, snd, 16);
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+  for (int k = 0; k < 2; ++k) {
+    const float snd = h3 ? u[k] : u[2 + k];
+    w2[k] = (h3 ? u[2 + k] : u[k]) + __shfl_xor_sync(0xffffffffu, snd, 8);
+  }
+  float r = (h2 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? w2[0] : w2[1], 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+// one tet's pair chunk of a lane: up to kNlChunks pairs (p, p + 32, ...)
+constexpr int kNlChunks = 6;
+struct NlPairs {
+  int loc[kNlChunks];
+  float wt[kNlChunks];
+};
+__device__ __forceinline__ void nl_load(const MixDev& x, int64_t p, int64_t end, NlPairs& q) {
 #pragma unroll
-      for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (lane == 0) {
-      float4* o = reinterpret_cast<float4*>(m.mx.sig_bar32 + 8 * t);
-      o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-      o[1] = make_float4(acc[4], acc[5], 0.f, 0.f);
-    }
+  for (int c = 0; c < kNlChunks; ++c) {
+    const int64_t pc = p + 32 * c;
+    q.loc[c] = pc < end ? int(__ldg(x.nb_loc + pc)) : -1;
+    q.wt[c] = pc < end ? __ldg(x.nb_wc + pc) : 0.f;
   }
 }
-__global__ void __launch_bounds__(kThreads) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
+__device__ __forceinline__ void nl_row(const MixDev& x, const float2* su, bool staged, int64_t u0, int loc, float2& r0,
+                                       float2& r1, float2& r2) {
+  if (staged) {
+    r0 = su[3 * loc];
+    r1 = su[3 * loc + 1];
+    r2 = su[3 * loc + 2];
+  } else {
+    float sj[8];
+    ld8f(x.sig_in32 + 8 * int64_t(__ldg(x.nl_uidx + u0 + loc)), sj);
+    r0 = make_float2(sj[0], sj[1]);
+    r1 = make_float2(sj[2], sj[3]);
+    r2 = make_float2(sj[4], sj[5]);
+  }
+}
+__device__ __forceinline__ void nl_accumulate(const MixDev& x, const float2* su, bool staged, int64_t u0, const NlPairs& q,
+                                              float (&acc)[8]) {
+#pragma unroll
+  for (int c = 0; c < kNlChunks; ++c) {
+    if (q.loc[c] < 0) continue;
+    float2 r0, r1, r2;
+    nl_row(x, su, staged, u0, q.loc[c], r0, r1, r2);
+    acc[0] += q.wt[c] * r0.x;
+    acc[1] += q.wt[c] * r0.y;
+    acc[2] += q.wt[c] * r1.x;
+    acc[3] += q.wt[c] * r1.y;
+    acc[4] += q.wt[c] * r2.x;
+    acc[5] += q.wt[c] * r2.y;
+  }
+}
+
+__device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  extern __shared__ float2 su[];   // [kNlCap][3]: stress rows of the tile's union
+  constexpr int kStage = (kNlCap + kNlThreads - 1) / kNlThreads;
+  const MixDev& x = m.mx;
+  const int64_t t0 = int64_t(bid) * kNlTile;
+  const int64_t u0 = x.nl_uptr[bid], un = x.nl_uptr[bid + 1] - u0;
+  const bool staged = un <= kNlCap;
+  if (staged) {   // all of a thread's union ids, then all of its rows, in flight together
+    int64_t j[kStage];
+#pragma unroll
+    for (int c = 0; c < kStage; ++c) {
+      const int64_t r = threadIdx.x + int64_t(c) * kNlThreads;
+      j[c] = r < un ? __ldg(x.nl_uidx + u0 + r) : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < kStage; ++c) {
+      if (j[c] < 0) continue;
+      const int64_t r = threadIdx.x + int64_t(c) * kNlThreads;
+      float sj[8];
+      ld8f(x.sig_in32 + 8 * j[c], sj);
+      su[3 * r] = make_float2(sj[0], sj[1]);
+      su[3 * r + 1] = make_float2(sj[2], sj[3]);
+      su[3 * r + 2] = make_float2(sj[4], sj[5]);
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t tw = t0 + int64_t(kNlWarpTets) * (threadIdx.x >> 5);
+  if (tw >= m.T) return;
+  const int nt = int(m.T - tw < kNlWarpTets ? m.T - tw : kNlWarpTets);
+  // nb_ptr[tw .. tw + nt] in lanes 0..nt
+  const int64_t myptr = lane <= nt ? x.nb_ptr[tw + lane] : 0;
+  NlPairs cur, nxt;
+#pragma unroll
+  for (int c = 0; c < kNlChunks; ++c) nxt.loc[c] = -1, nxt.wt[c] = 0.f;
+  int64_t beg = __shfl_sync(0xffffffffu, myptr, 0), end = __shfl_sync(0xffffffffu, myptr, 1);
+  nl_load(x, beg + lane, end, cur);
+  for (int k = 0; k < nt; ++k) {
+    // the next tet's first chunk is in flight while this one is summed
+    const int64_t nbeg = end, nend = __shfl_sync(0xffffffffu, myptr, k + 2 <= nt ? k + 2 : nt);
+    if (k + 1 < nt) nl_load(x, nbeg + lane, nend, nxt);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    nl_accumulate(x, su, staged, u0, cur, acc);
+    for (int64_t p = beg + lane + 32 * kNlChunks; p < end; p += 32 * kNlChunks) {   // lists longer than 192
+      NlPairs more;
+      nl_load(x, p, end, more);
+      nl_accumulate(x, su, staged, u0, more, acc);
+    }
+    const float tot = warp_transpose_sum8(acc, lane);
+    if ((lane & 3) == 0)   // value 4 b4 + 2 b3 + b2 of lane L is column L / 4 of the row (6, 7 are zero)
+      x.sig_bar32[8 * (tw + k) + (lane >> 2)] = tot;
+    cur = nxt;
+    beg = nbeg;
+    end = nend;
+  }
+}
+__global__ void __launch_bounds__(kNlThreads, 4) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
   nonlocal32_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
-__global__ void __launch_bounds__(kThreads) kb_nonlocal32(const BatchTab* __restrict__ tab) {
+__global__ void __launch_bounds__(kNlThreads, 4) kb_nonlocal32(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_nonlocal32, blockIdx.x, bid, nb);
   nonlocal32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
@@ -1029,7 +1134,7 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
   if (d.blocks == 0) return 0;
   switch (kind) {
     case kB_tet_stress32: k_tet_stress32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_nonlocal32: k_nonlocal32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_nonlocal32: k_nonlocal32<<<d.blocks, d.threads, kNlSmem, s>>>(m, mt, sp); break;
     case kB_edge_driver32: k_edge_driver32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_tet_chi32: k_tet_chi32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_elem32:
@@ -1057,7 +1162,7 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
   if (blocks == 0) return 0;
   switch (kind) {
     case kB_tet_stress32: kb_tet_stress32<<<blocks, threads, 0, s>>>(tab); break;
-    case kB_nonlocal32: kb_nonlocal32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_nonlocal32: kb_nonlocal32<<<blocks, threads, kNlSmem, s>>>(tab); break;
     case kB_edge_driver32: kb_edge_driver32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_tet_chi32: kb_tet_chi32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_elem32:
