@@ -77,24 +77,33 @@ class ClockSampler:
 # written once; gathers of node data counted once per node).
 MIXED_BYTES = {
     "m:tet_stress": lambda i: i["n_tets"] * (16 + 72 + 4 + 24 + 24) + 12 * i["n_nodes"],
-    "m:nonlocal_avg": lambda i: 8.0 * i["n_nbr_pairs"] + i["n_tets"] * (24 + 24),
+    # per pair a 16-bit union position and an FP32 weight; per tet its list
+    # pointer, its stress row read once and its average row written
+    "m:nonlocal_avg": lambda i: 6.0 * i["n_nbr_pairs"] + i["n_tets"] * (8 + 32 + 32),
     "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
-    # phase 1: tet, rest row (128 B), chi in; ten 3x3 blocks + four rhs shares out (416 B); u, v per node
-    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 416) + i["n_nodes"] * 24,
-    # phase 2: every element entry once (16 blocks + 4 rhs shares per tet) and its list index, out A, b, D^-1
-    "m:assemble_gather": lambda i: i["n_tets"] * (16 * 9 * 4 + 4 * 3 * 4 + 16 * 4 + 4 * 4)
-                                   + i["n_blocks"] * (36 + 4) + i["n_nodes"] * (12 + 36 + 24),
+    # phase 1: tet, rest row (128 B), chi, its ten row indices in; 6 edge rows
+    # (36 B) + 4 node rows (48 B) out; u, v and the external force per node
+    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 40 + 408) + i["n_nodes"] * (24 + 24),
+    # phase 2: every row once (408 B per tet); per edge its row pointer and two
+    # slots; per node pointers, mass, v, f_ext, rhs; A once; the block-Jacobi
+    # inverse reads the diagonal blocks and writes D^-1
+    "m:assemble_gather": lambda i: i["n_tets"] * 408 + i["n_edges"] * (4 + 8) + i["n_blocks"] * 36
+                                   + i["n_nodes"] * (4 + 4 + 4 + 12 + 12 + 12 + 36 + 36),
     "m:pcg_spmv": lambda i: i["n_blocks"] * 40 + i["n_nodes"] * (4 + 12 + 12 + 12),
 }
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# loaf kernels, from one ncu --set full capture of the current kernels each
-# (``bench.py --profile-step --precision fp64|mixed --steps 2``).
+# loaf kernels, from ncu captures of the current kernels
+# (``bench.py --profile-step --precision fp64|mixed --steps 2``); the two
+# assembly groups list their main kernel (k_elem64 / k_gather64, k_elem32 /
+# k_gather32).
 NCU_TRAFFIC = {
     "nonlocal_avg": 1.291858e9 + 28.97152e6,
-    "assemble": 0.284699e9 + 582.927872e6,
-    "m:nonlocal_avg": 814.254848e6 + 21.138688e6,
-    "m:assemble_gather": 318.089216e6 + 54.717696e6,
+    "assemble": 234.703360e6 + 499.401728e6,
+    "assemble_gather": 530.260736e6 + 118.412544e6,
+    "m:nonlocal_avg": 649.088512e6 + 20.163328e6,
+    "m:assemble": 122.624256e6 + 195.889408e6,
+    "m:assemble_gather": 274.354944e6 + 59.933696e6,
 }
 # Executed FP64 flops per tet of the element-block kernel (ncu: 2 DFMA + DADD +
 # DMUL thread instructions per launch / tets): the tangent has no short closed count.
@@ -118,11 +127,13 @@ def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, tra
                 "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
                 "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
     if group == "assemble_gather":
-        # phase 2: one FP64 add per element contribution (16 blocks x 9 + 4 rhs shares x 3 per tet)
-        flops = 156.0 * T
-        return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
-                "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
+        # phase 2: every FP64 row once (102 values per tet), per edge its row
+        # pointer and two slots, per node pointers, mass, v, f_ext and rhs, A once
+        bytes_per = T * 816 + info["n_edges"] * (4 + 8) + NB * 72 + N * (4 + 4 + 8 + 24 + 24 + 24)
+        gbs = bytes_per / t / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                "traffic": traffic, "kernel": group, "work_per_launch": {"bytes": bytes_per, "fp64_flop": 102.0 * T},
+                "peak_kind": "measured HBM copy bandwidth"}
     if group == "pcg_spmv":
         flops = 18.0 * NB
         return {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -18,8 +18,10 @@ __device__ __forceinline__ T row_sum(const T* __restrict__ src, int stride, int 
 #pragma unroll
     for (int k = 0; k < B; ++k) v[k] = r + k < r1 ? __ldg(src + int64_t(stride) * (r + k)) : T(0);
 #pragma unroll
-    for (int k = 0; k < B; ++k)
-      if (r + k < r1) acc += v[k];
+    for (int k = 0; k < B; ++k) {   // stop at the row count: no add issues once every lane is done
+      if (r + k >= r1) break;
+      acc += v[k];
+    }
   }
   return acc;
 }
