@@ -50,11 +50,12 @@ __device__ __forceinline__ void cauchy_green(const double s[6], const double B[9
 }
 
 // Normal stress along e (Eq. 16 with the current direction, Eq. 17): (e.S.e)/|e|^2,
-// shear terms weighted by kappa.
-__device__ __forceinline__ double normal_stress(const double e[3], double s, const double S[6], double kappa) {
-  double q = e[0] * e[0] * S[0] + e[1] * e[1] * S[1] + e[2] * e[2] * S[2] +
-             kappa * (e[0] * e[1] * S[3] + e[0] * e[2] * S[4] + e[1] * e[2] * S[5]);
-  return q / s;
+// shear terms weighted by kappa.  edge_traction is the numerator e.S.e; callers
+// divide by |e|^2 (an FP64 division is a multi-instruction sequence, so they
+// share divisions where they can).
+__device__ __forceinline__ double edge_traction(const double e[3], const double S[6], double kappa) {
+  return e[0] * e[0] * S[0] + e[1] * e[1] * S[1] + e[2] * e[2] * S[2] +
+         kappa * (e[0] * e[1] * S[3] + e[0] * e[2] * S[4] + e[1] * e[2] * S[5]);
 }
 
 // ---------------------------------------------------------------------------
@@ -116,9 +117,22 @@ __device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material
   si[0] = make_double2(w * S[0], w * S[1]);
   si[1] = make_double2(w * S[2], w * S[3]);
   si[2] = make_double2(w * S[4], w * S[5]);
+  // 1 / s_k of the six edges with one division (batch inversion: prefix
+  // products, one reciprocal, then back-substitution)
+  double pre[6], rs[6];
+  pre[0] = s[0];
+#pragma unroll
+  for (int k = 1; k < 6; ++k) pre[k] = pre[k - 1] * s[k];
+  double inv = 1.0 / pre[5];
+#pragma unroll
+  for (int k = 5; k > 0; --k) {
+    rs[k] = inv * pre[k - 1];
+    inv *= s[k];
+  }
+  rs[0] = inv;
   double sf[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) sf[k] = normal_stress(e[k], s[k], S, mt.kappa);
+  for (int k = 0; k < 6; ++k) sf[k] = edge_traction(e[k], S, mt.kappa) * rs[k];
   double2* so = reinterpret_cast<double2*>(m.sigf + 6 * t);
   so[0] = make_double2(sf[0], sf[1]);
   so[1] = make_double2(sf[2], sf[3]);
@@ -186,13 +200,16 @@ __device__ __forceinline__ void edge_driver_body(const DevMesh& m, const Materia
     ld3(m.x, ab.y, pb);
     const double e[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
     const double s = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-    double mx = -INFINITY;
+    // max over the incident tets of (e.S.e) / s: s > 0 and rounded division is
+    // monotone, so dividing the largest numerator once gives the same value
+    double mq = -INFINITY;
     for (int p = m.et_ptr[i]; p < m.et_ptr[i + 1]; ++p) {
       const double2* sb = reinterpret_cast<const double2*>(m.sig_bar + 6 * int64_t(m.et_tet[p]));
       const double2 a = sb[0], b = sb[1], c = sb[2];
       const double S[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
-      mx = fmax(mx, normal_stress(e, s, S, mt.kappa));
+      mq = fmax(mq, edge_traction(e, S, mt.kappa));
     }
+    const double mx = mq / s;
     const double d = mt.driver_stress ? mx : mx / mt.young;
     m.driver[i] = d;
     const uint8_t old = m.labels[i];

@@ -305,12 +305,14 @@ __device__ __forceinline__ void edge_driver32_body(const DevMesh& m, const Mater
     ld3f(m.mx.edge_e0, i, e0);
     const float e[3] = {e0[0] + (ub[0] - ua[0]), e0[1] + (ub[1] - ua[1]), e0[2] + (ub[2] - ua[2])};
     const float s = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-    float mx = -INFINITY;
+    // max of (e.S.e) / s over the incident tets: one division of the largest numerator
+    float mq = -INFINITY;
     for (int p = m.et_ptr[i]; p < m.et_ptr[i + 1]; ++p) {
       float S[8];
       ld8f(m.mx.sig_bar32 + 8 * int64_t(m.et_tet[p]), S);
-      mx = fmaxf(mx, normal_stress32(e, s, S, kappa));
+      mq = fmaxf(mq, normal_stress32(e, 1.f, S, kappa));
     }
+    const float mx = mq / s;
     const double d = double(stress_mode ? mx : mx * inv_young);
     m.driver[i] = d;
     const uint8_t old = m.labels[i];
