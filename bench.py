@@ -171,8 +171,9 @@ def cpu_sample_child(steps: int) -> None:
     print(json.dumps({"sec_per_step": dt, "tets": w.n_tets, "steps": steps, "cg_iters": info["iters"]}))
 
 
-def cpu_sample(steps: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+def cpu_sample(steps: int, threads: int = 1) -> dict:
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-child", str(steps)],
                          capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
@@ -181,10 +182,15 @@ def cpu_sample(steps: int) -> dict:
 def cpu_baseline_entry(steps: int, full_tets: int) -> dict:
     s = cpu_sample(steps)
     ms = s["sec_per_step"] * 1e3 * full_tets / s["tets"]
+    nproc = os.cpu_count() or 1
+    a = cpu_sample(steps, nproc)
     return {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{s['steps']} oracle steps on the loaf generator with axes x{SAMPLE_SCALE} ({s['tets']} tets), "
                       f"same material/dt/R_d/loads, PCG rtol 1e-6 ({s['cg_iters']} iterations), "
-                      f"{s['sec_per_step']:.2f} s/step scaled per tet to {full_tets} tets; numpy/scipy, 1 thread"}
+                      f"{s['sec_per_step']:.2f} s/step scaled per tet to {full_tets} tets; numpy/scipy, 1 thread",
+            "all_cores": {"value": a["sec_per_step"] * 1e3 * full_tets / a["tets"], "unit": UNIT, "cores": nproc,
+                          "sample": f"the same sample with OMP/BLAS threads = {nproc} (the oracle's sparse "
+                                    f"products and Python loops stay single-threaded)"}}
 
 
 def run_reference(args) -> None:
@@ -319,10 +325,10 @@ def run_extensions(args, gf, torch, barrier, stream, w, f_dev, m_main) -> dict:
     import numpy as np
 
     def timed(m, steps, pinned=None):
+        """Unprofiled timed steps (as a user runs them), then 3 profiled steps for
+        the per-kernel breakdown."""
         for _ in range(3):
             m.step(w.dt, f_dev, pinned)
-        m.profile_reset()
-        m.profile_enable(True)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -334,12 +340,16 @@ def run_extensions(args, gf, torch, barrier, stream, w, f_dev, m_main) -> dict:
             newton.append(s["newton_iters"])
         e1.record(stream)
         barrier()
+        ms = e0.elapsed_time(e1) / steps
+        m.profile_reset()
+        m.profile_enable(True)
+        for _ in range(3):
+            m.step(w.dt, f_dev, pinned)
         m.profile_enable(False)
         prof = m.profile_get()
-        ms = e0.elapsed_time(e1) / steps
         return {"ms_per_step": ms, "element_updates_per_s": w.n_tets / (ms * 1e-3),
                 "cg_iters_per_step": statistics.mean(its), "newton_iters_per_step": statistics.mean(newton),
-                "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[0] > 0}}
+                "kernels_ms_per_step": {k: v[0] / 3 for k, v in prof.items() if v[0] > 0}}
 
     out = {}
     steps = 20
@@ -424,11 +434,12 @@ def run_ours(args) -> None:
     stream = torch.cuda.current_stream()
 
     def timed(m, steps):
+        """Time `steps` steps as a user runs them (no per-launch profiling, so the
+        step is one graph replay), then profile a few more steps separately for
+        the per-kernel breakdown (profiling puts events between launches)."""
         iters, sweeps = [], []
         for _ in range(args.warmup):
             m.step(w.dt, f_dev)
-        m.profile_reset()
-        m.profile_enable(True)
         l0 = m.launch_count()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,9 +451,20 @@ def run_ours(args) -> None:
             assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
         e1.record(stream)
         barrier()
+        ms, launches = e0.elapsed_time(e1) / steps, m.launch_count() - l0
+        return ms, launches, profiled(m, min(steps, 5)), statistics.mean(iters), statistics.mean(sweeps)
+
+    def profiled(m, steps, pinned=None):
+        """Per-kernel-group times of `steps` further steps, scaled to the same
+        number of steps as the timed region (the caller divides by it)."""
+        m.profile_reset()
+        m.profile_enable(True)
+        for _ in range(steps):
+            m.step(w.dt, f_dev, pinned)
         m.profile_enable(False)
-        return (e0.elapsed_time(e1) / steps, m.launch_count() - l0, m.profile_get(), statistics.mean(iters),
-                statistics.mean(sweeps))
+        prof = m.profile_get()
+        scale = args.steps / steps
+        return {k: (v[0] * scale, int(round(v[1] * scale))) for k, v in prof.items()}
 
     # plain FP64 form (the headline)
     m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)

@@ -170,10 +170,20 @@ gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* 
  * assembly: GF_ASSEMBLY_GATHER (default) computes every tet's blocks once into
  * an element buffer and gathers each matrix row in a fixed order (one launch
  * per phase); GF_ASSEMBLY_COLOUR scatters tet by tet in colour order (no two
- * tets of a colour share a node), one launch per colour (GF_FP64 only). */
+ * tets of a colour share a node), one launch per colour (GF_FP64 only).
+ * step_launch: GF_STEP_GRAPH (default) runs a plain step (one Newton
+ * iteration, gather assembly, no network attached, profiling off) as one CUDA
+ * graph replay: its launches are captured on the first such step and again
+ * whenever dt, the presence of f_ext / pinned velocities, the pinned count,
+ * the device input pointers or the iteration limit change; the solver loop is
+ * a device-side WHILE node, so the host waits once per step.  The results are
+ * the same bits as GF_STEP_STREAM, which launches kernel by kernel with a host
+ * check per chunk of solver iterations (and is what the other steps use). */
+enum { GF_STEP_GRAPH = 0, GF_STEP_STREAM = 1 };
 typedef struct gf_tuning {
   int32_t assembly;
-  int32_t reserved[7];   /* set to 0 */
+  int32_t step_launch;   /* GF_STEP_GRAPH (0, default) or GF_STEP_STREAM */
+  int32_t reserved[6];   /* set to 0 */
 } gf_tuning;
 gf_status gf_tuning_set(gf_mesh* mesh, const gf_tuning* tuning);
 gf_status gf_tuning_get(const gf_mesh* mesh, gf_tuning* tuning);

@@ -39,6 +39,17 @@ inline unsigned ir_grid(int64_t n, int per_sm = 4) {    // refinement kernels: <
   const int64_t b = (n + 255) / 256;
   return unsigned(b < 1 ? 1 : (b > per_sm * 152 ? per_sm * 152 : b));
 }
+
+// Solver-loop condition of the single-mesh step graph: continue while the
+// solve is not done (and below the cap on WHILE iterations).
+__global__ void k_step_cond(const PcgState* pcg, const IrState* ir, int* loops, int cap,
+                            cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const int it = ++*loops;
+  const bool go = ir ? !ir->done : !pcg->done;
+  cudaGraphSetConditional(h, (go && it < cap) ? 1u : 0u);
+}
+
 }  // namespace
 
 LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp) {
@@ -167,6 +178,26 @@ struct gf_mesh {
   IrState* h_ir = nullptr;                 // pinned host mirror (mixed)
   unsigned long long* h_cnt = nullptr;     // pinned host mirror of counters
 
+  // graph form of the plain step (see step_graph)
+  struct GraphKey {
+    double dt = 0.0;
+    int64_t n_pinned = -1;
+    int has_fext = -1, has_pvel = -1, maxit = -1, loop = -1;
+    const void *f_ext = nullptr, *pin_ids = nullptr, *pin_vel = nullptr;
+    bool operator==(const GraphKey& o) const {
+      return dt == o.dt && n_pinned == o.n_pinned && has_fext == o.has_fext && has_pvel == o.has_pvel &&
+             maxit == o.maxit && loop == o.loop && f_ext == o.f_ext && pin_ids == o.pin_ids && pin_vel == o.pin_vel;
+    }
+  };
+  GraphKey gkey;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t body_stream = nullptr;      // capture stream of the WHILE body
+  int* d_loops = nullptr;                  // WHILE iterations of the last replay
+  int* h_loops = nullptr;                  // pinned mirror
+  void* h_init = nullptr;                  // pinned solver-state initialiser read by the graph
+  int64_t g_prefix = 0, g_body = 0, g_suffix = 0;
+
   bool prof = false;
   double prof_ms[kPCount] = {};
   int64_t prof_n[kPCount] = {};
@@ -247,6 +278,11 @@ void release(gf_mesh* m) {
   if (m->h_pcg) cudaFreeHost(m->h_pcg);
   if (m->h_ir) cudaFreeHost(m->h_ir);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
+  if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+  if (m->graph) cudaGraphDestroy(m->graph);
+  if (m->body_stream) cudaStreamDestroy(m->body_stream);
+  if (m->h_loops) cudaFreeHost(m->h_loops);
+  if (m->h_init) cudaFreeHost(m->h_init);
   if (m->surf_stage) cudaFree(m->surf_stage);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
 }
@@ -678,7 +714,12 @@ gf_status gf_tuning_set(gf_mesh* m, const gf_tuning* t) {
     set_last_error("GF_MIXED assembles by gather only");
     return GF_UNSUPPORTED;
   }
+  if (t->step_launch != GF_STEP_GRAPH && t->step_launch != GF_STEP_STREAM) {
+    set_last_error("bad tuning (step_launch must be GF_STEP_GRAPH or GF_STEP_STREAM)");
+    return GF_BAD_ARG;
+  }
   m->tune = *t;
+  m->gkey = gf_mesh::GraphKey{};   // capture again on the next step
   return GF_OK;
 }
 
@@ -902,6 +943,163 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   return GF_OK;
 }
 
+// Whether a step can run as the captured graph: the plain step (one Newton
+// iteration, two-phase assembly, no network, no per-launch profiling).
+bool graph_step_ok(const gf_mesh* m) {
+  return m->tune.step_launch == GF_STEP_GRAPH && !m->prof && !m->gnn &&
+         (m->mixed || (m->newton_iters == 1 && m->tune.assembly == GF_ASSEMBLY_GATHER));
+}
+
+// Capture the plain step: the launches of step_fp64 / step_mixed in the same
+// order (so the results are the same bits), with the solver loop as a WHILE
+// node whose body is `loop` PCG iterations (FP64) or one round of two
+// refinement sweeps with `loop` inner iterations each (mixed).
+gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loop) {
+  cudaStream_t s = m->stream;
+  const gf::Material& mt = m->mt;
+  if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+  if (m->graph) cudaGraphDestroy(m->graph);
+  m->graph_exec = nullptr;
+  m->graph = nullptr;
+  if (!m->body_stream) GF_CK(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  GF_CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  GF_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  GF_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int64_t L = 0;
+  GF_CK(cudaMemsetAsync(m->d_loops, 0, sizeof(int), s));
+  if (m->mixed) {
+    if (!(mt.radius > 0.0)) d.mx.sig_bar32 = d.mx.sig_in32;
+    L += launch_kind(kB_tet_stress32, d, mt, sp, s);
+    if (mt.radius > 0.0) L += launch_kind(kB_nonlocal32, d, mt, sp, s);
+    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32, kB_gather32, kB_pinv32})
+      L += launch_kind(kind, d, mt, sp, s);
+    GF_CK(cudaMemcpyAsync(d.mx.ir, m->h_init, sizeof(IrState), cudaMemcpyHostToDevice, s));
+  } else {
+    if (!(mt.radius > 0.0)) d.sig_bar = d.sig_in;
+    L += launch_kind(kB_tet_stress, d, mt, sp, s);
+    if (mt.radius > 0.0) L += launch_kind(kB_nonlocal, d, mt, sp, s);
+    for (int kind : {kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64}) L += launch_kind(kind, d, mt, sp, s);
+    GF_CK(cudaMemcpyAsync(d.pcg, m->h_init, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+  }
+  GF_CK(cudaMemsetAsync(d.pinned, 0, d.N, s));
+  GF_CK(cudaMemsetAsync(d.dv, 0, sizeof(double) * 3 * d.N, s));
+  L += launch_kind(kB_set_pinned, d, mt, sp, s);
+  if (m->mixed) {
+    L += launch_kind(kB_refresh32, d, mt, sp, s);
+    L += launch_kind(kB_ir_residual, d, mt, sp, s, 1);
+  } else {
+    L += launch_kind(kB_pcg_init, d, mt, sp, s);
+  }
+  m->g_prefix = L;
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  GF_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, &ed, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t wn;
+  GF_CK(cudaGraphAddNode(&wn, g, deps, ed, nd, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaStream_t bs = m->body_stream;
+  GF_CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  L = 0;
+  int cap;
+  if (m->mixed) {
+    for (int sw = 0; sw < 2; ++sw) {
+      L += launch_kind(kB_ir_inner_init, d, mt, sp, bs);
+      for (int j = 0; j < loop; ++j)
+        for (int kind : {kB_ir_spmv, kB_ir_update, kB_ir_p}) L += launch_kind(kind, d, mt, sp, bs);
+      L += launch_kind(kB_ir_apply, d, mt, sp, bs);
+      L += launch_kind(kB_ir_residual, d, mt, sp, bs, 0);
+    }
+    cap = 4096;
+    k_step_cond<<<1, 32, 0, bs>>>(nullptr, d.mx.ir, m->d_loops, cap, h);
+  } else {
+    for (int j = 0; j < loop; ++j)
+      for (int kind : {kB_pcg_spmv, kB_pcg_update, kB_pcg_p}) L += launch_kind(kind, d, mt, sp, bs);
+    cap = m->opt.cg_maxit / loop + 2;
+    k_step_cond<<<1, 32, 0, bs>>>(d.pcg, nullptr, m->d_loops, cap, h);
+  }
+  m->g_body = L + 1;
+  GF_CK(cudaStreamEndCapture(bs, &body));
+  GF_CK(cudaStreamUpdateCaptureDependencies(s, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  L = 0;
+  if (m->mixed) {
+    L += launch_kind(kB_integrate32, d, mt, sp, s);
+  } else {
+    L += launch_kind(kB_true_residual, d, mt, sp, s);
+    L += launch_kind(kB_integrate, d, mt, sp, s);
+  }
+  m->g_suffix = L;
+  GF_CK(cudaStreamEndCapture(s, &g));
+  m->graph = g;
+  GF_CK(cudaGraphInstantiate(&m->graph_exec, g, 0));
+  return GF_OK;
+}
+
+// The plain step as one graph replay: stage the solver initialiser, capture
+// the graph when the key changed, launch it and queue the state read-back.
+gf_status step_graph(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_pinned, bool has_pvel) {
+  cudaStream_t s = m->stream;
+  const StepScalars sp = step_scalars(m->mt, dt, has_fext, n_pinned, has_pvel);
+  if (!m->h_loops) GF_CK(cudaMallocHost(&m->h_loops, sizeof(int)));
+  if (!m->h_init) GF_CK(cudaMallocHost(&m->h_init, std::max(sizeof(IrState), sizeof(PcgState))));
+  if (!m->d_loops) {
+    gf_status st = scratch(m, 1, &m->d_loops);
+    if (st != GF_OK) return st;
+  }
+  gf_mesh::GraphKey key;
+  key.dt = dt;
+  key.n_pinned = n_pinned;
+  key.has_fext = has_fext ? 1 : 0;
+  key.has_pvel = has_pvel ? 1 : 0;
+  key.maxit = m->opt.cg_maxit;
+  key.f_ext = d.f_ext;
+  key.pin_ids = d.pin_ids;
+  key.pin_vel = d.pin_vel;
+  // the loop body: 2 PCG iterations (FP64); inner iterations of a sweep as the
+  // stream form picks them from the previous step (mixed)
+  key.loop = m->mixed ? std::max(2, std::min(m->last_inner + 1, 32)) : 2;
+  if (m->mixed) {
+    IrState init{};
+    init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+    init.in_tol2 = m->in_rtol * m->in_rtol;
+    init.maxit = m->opt.cg_maxit;
+    init.in_maxit = 32;
+    init.applied = 1;
+    init.in_done = 1;
+    std::memcpy(m->h_init, &init, sizeof(IrState));
+  } else {
+    PcgState init{};
+    init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+    init.maxit = m->opt.cg_maxit;
+    std::memcpy(m->h_init, &init, sizeof(PcgState));
+  }
+  // a key that differs from the captured one only in the mixed loop length keeps the graph
+  gf_mesh::GraphKey cmp = key;
+  if (m->mixed && m->graph_exec) cmp.loop = m->gkey.loop;
+  if (!m->graph_exec || !(cmp == m->gkey)) {
+    gf_status st = build_step_graph(m, d, sp, key.loop);
+    if (st != GF_OK) {
+      m->gkey = gf_mesh::GraphKey{};
+      return st;
+    }
+    m->gkey = key;
+  }
+  GF_CK(cudaGraphLaunch(m->graph_exec, s));
+  GF_CK(cudaGetLastError());
+  if (m->mixed) GF_CK(cudaMemcpyAsync(m->h_ir, d.mx.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+  else GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  GF_CK(cudaMemcpyAsync(m->h_loops, m->d_loops, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return GF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -940,12 +1138,24 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
     }
   }
   int64_t L = 0;
-  gf_status st = m->mixed ? step_mixed(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L)
-                          : step_fp64(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L);
+  const bool graph = graph_step_ok(m);
+  gf_status st = graph ? step_graph(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr)
+                 : m->mixed ? step_mixed(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L)
+                            : step_fp64(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L);
   if (st != GF_OK) return st;
   m->assembled = true;
   GF_CK(cudaMemcpyAsync(m->h_cnt, d.counters, sizeof(unsigned long long) * kCntMax, cudaMemcpyDeviceToHost, s));
   GF_CK(cudaStreamSynchronize(s));
+  if (graph) {
+    L = m->g_prefix + m->g_suffix + int64_t(*m->h_loops) * m->g_body;
+    if (m->mixed) {
+      m->last_inner = std::max(1, std::min(m->h_ir->in_iters, 32));
+    } else {
+      m->newton_done = 1;
+      m->newton_res = 0.0;
+      m->newton_cg_total = m->h_pcg->iters;
+    }
+  }
   m->launches += L;
   gf_status status;
   int iters, sweeps = 0;

@@ -61,10 +61,11 @@ class StepStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("assembly", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("assembly", ctypes.c_int32), ("step_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
+STEP_GRAPH, STEP_STREAM = 0, 1
 
 
 class BatchTuning(ctypes.Structure):
@@ -277,15 +278,16 @@ class Mesh:
                                              ctypes.byref(nq)))
         return {"vertices": V, "quads": Q[:nq.value], "n_faces": sz["n_faces"]}
 
-    def tuning_set(self, assembly: int):
+    def tuning_set(self, assembly: int = ASSEMBLY_GATHER, step_launch: int = STEP_GRAPH):
         t = Tuning()
         t.assembly = assembly
+        t.step_launch = step_launch
         _check(load_library().gf_tuning_set(self._h, ctypes.byref(t)))
 
     def tuning_get(self) -> dict:
         t = Tuning()
         _check(load_library().gf_tuning_get(self._h, ctypes.byref(t)))
-        return {"assembly": t.assembly}
+        return {"assembly": t.assembly, "step_launch": t.step_launch}
 
     def refine_set(self, inner_rtol: float):
         _check(load_library().gf_refine_set(self._h, float(inner_rtol)))
