@@ -123,3 +123,42 @@ def test_mixed_resume_bit_identical_and_rest():
     for _ in range(2):
         d.step(w.dt, w.f_ext.ravel(), w.pinned)
     np.testing.assert_array_equal(b.positions_get(), d.positions_get())
+
+
+@pytest.mark.parametrize("dims,radius", [((3, 3, 7), 1.5), ((6, 6, 12), 3.0)], ids=["ragged-tile", "large-unions"])
+def test_mixed_nonlocal_tiles(dims, radius):
+    """The tiled Eq. 20 kernel (128 tets per CTA, neighbour union staged in
+    shared memory up to 1,792 rows, read from global memory beyond) on a mesh
+    whose last tile is partial (378 tets) and on one whose tile unions exceed
+    the staged capacity (R_d = 3 on 2,592 tets), against the oracle."""
+    from oracle import mesh as omesh
+    from workloads import Workload
+    from workloads.meshes import jitter, kuhn_box
+    nodes, tets, grid = kuhn_box(*dims)
+    nodes = jitter(nodes, 0.01, 1.0, 5)
+    top = np.nonzero(grid[:, 2] == dims[2])[0]
+    f = np.zeros_like(nodes)
+    f[top, 0] = 50.0 / len(top)
+    pinned = np.nonzero(grid[:, 2] == 0)[0].astype(np.int32)
+    w = Workload("box_tiles", nodes, tets, 1e6, 0.3, 1000.0, 1e-3, 3, math.inf, radius, f, pinned)
+    T = len(tets)
+    nb = omesh.nonlocal_neighbours(nodes, tets, radius)
+    unions = [len(set().union(*[set(x) for x in nb[g:g + 128]])) for g in range(0, T, 128)]
+    if radius == 1.5:
+        assert T % 128 != 0
+    else:
+        assert max(unions) > 1792   # these tiles take the global-memory path
+    model0 = oracle_model(w, threshold=math.inf, radius=radius)
+    st = deformed_state(w, seed=31)
+    d0, _, _, _ = model0.damage_update(st)
+    theta = float(np.quantile(d0, 0.95))
+    model = oracle_model(w, threshold=theta, radius=radius)
+    m = mixed_mesh(w, gpu_material(gf, w, threshold=theta, radius=radius))
+    m.state_set(x=st.x.ravel(), v=st.v.ravel(), labels=st.labels, chi=st.chi)
+    s = m.step(w.dt, w.f_ext.ravel(), w.pinned)
+    assert s["status"] == 0
+    new, info = model.step(st, w.dt, w.f_ext, w.pinned)
+    drv, lab = m.damage_get()
+    assert_close(drv, info["driver"], rtol=RTOL32, floor=FLOOR32, what="driver (mixed, tiles)")
+    assert_labels(lab, info["labels"], info["driver"], theta, band=BAND32)
+    assert lab.sum() > 0

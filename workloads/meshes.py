@@ -27,7 +27,7 @@ import numpy as np
 
 @dataclasses.dataclass
 class Workload:
-    """A mesh plus its material, loads and constraints (one BASELINE-style case)."""
+    """A mesh plus its material, loads and constraints (one benchmark case)."""
     name: str
     nodes: np.ndarray          # (n, 3) float64 rest positions
     tets: np.ndarray           # (t, 4) int32
