@@ -553,6 +553,9 @@ def run_profile_step(args) -> None:
                       energy=gf.ENERGY_SNH if args.precision == "snh" else gf.ENERGY_STVK)
     m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol,
                        precision=gf.MIXED if args.precision == "mixed" else gf.FP64)
+    # kernel-by-kernel launches (the same kernels as the graph replay), so that
+    # ncu lists every kernel of the step
+    m.tuning_set(step_launch=gf.STEP_STREAM)
     f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
     net = None
     if args.precision == "learned":      # zero-decoder network: learned start from the second step on

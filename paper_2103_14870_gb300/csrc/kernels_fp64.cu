@@ -446,6 +446,7 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
 // (thread per matrix entry or rhs component) streams through them in a fixed
 // order and adds mass, external force and mass damping.
 constexpr int kNodeRow = 12, kEdgeRow = 9;
+constexpr int kElemThreads64 = 128;   // threads per CTA of the element kernels (shared-memory sums)
 
 // where a tet's contributions go (the writes scatter; the gather reads stream)
 struct ElemRows64 {
@@ -629,6 +630,13 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
     out.zero();
     return;
   }
+  // The energy depends on node differences only, so every block row of the
+  // tet's tangent sums to zero: K_aa = -sum_{b != a} K_ab.  Only the six
+  // off-diagonal blocks are formed (Y for b = 1..3); the diagonal blocks are
+  // summed from them in shared memory (entry-major: consecutive threads,
+  // consecutive doubles), which saves Y_0 and four block products.
+  __shared__ double s_diag[36][kElemThreads64];
+  double* sd = &s_diag[0][threadIdx.x];
   const int inc[4][3] = {{0, 1, 2}, {0, 3, 4}, {1, 3, 5}, {2, 4, 5}};
   const double sgn[4][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {1, 1, 1}};
   const int kab[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
@@ -684,8 +692,8 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
   }
   const double sK = (dt * beta + dt * dt) * chi;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    double Y[6][3];
+  for (int b = 1; b < 4; ++b) {
+    double Y[6][3];   // Y[k][c] = 4 sK sum_j H(k, l_j) sgn_bj e_{l_j}[c]
 #pragma unroll
     for (int k = 0; k < 6; ++k)
 #pragma unroll
@@ -696,7 +704,7 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
         Y[k][c] = 4.0 * sK * y;
       }
 #pragma unroll
-    for (int a = 0; a <= b; ++a) {
+    for (int a = 0; a < b; ++a) {
       double blk[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -707,13 +715,31 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
           for (int i = 0; i < 3; ++i) v += sgn[a][i] * e[inc[a][i]][r] * Y[inc[a][i]][c];
           blk[r][c] = v;
         }
-      const double geo = (a == b) ? 2.0 * sK * (g[inc[a][0]] + g[inc[a][1]] + g[inc[a][2]])
-                                  : -2.0 * sK * g[kab[a][b]];
+      const double geo = -2.0 * sK * g[kab[a][b]];
       blk[0][0] += geo;
       blk[1][1] += geo;
       blk[2][2] += geo;
       out.block(a, b, blk);
+      // -K_aa collects K_ab (first: K_01), -K_bb collects K_ab^T (first: K_0b)
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double* pa = sd + kElemThreads64 * (9 * a + 3 * r + c);
+          double* pb = sd + kElemThreads64 * (9 * b + 3 * c + r);
+          *pa = (a == 0 && b == 1) ? blk[r][c] : *pa + blk[r][c];
+          *pb = (a == 0) ? blk[r][c] : *pb + blk[r][c];
+        }
     }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double blk[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) blk[r][c] = -sd[kElemThreads64 * (9 * a + 3 * r + c)];
+    out.block(a, a, blk);
   }
 }
 __device__ __forceinline__ void elem_snh64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid,
@@ -729,13 +755,13 @@ __device__ __forceinline__ void elem_snh64_body(const DevMesh& m, const Material
   }
   elem_snh64(m, mt, sp, t, nid, chi);
 }
-__global__ void __launch_bounds__(128) k_elem64(DevMesh m, Material mt, StepScalars sp) {
+__global__ void __launch_bounds__(kElemThreads64) k_elem64(DevMesh m, Material mt, StepScalars sp) {
   elem64_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(128) k_elem_snh64(DevMesh m, Material mt, StepScalars sp) {
   elem_snh64_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
-__global__ void __launch_bounds__(128) kb_elem64(const BatchTab* __restrict__ tab) {
+__global__ void __launch_bounds__(kElemThreads64) kb_elem64(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_elem64, blockIdx.x, bid, nb);
   elem64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);   // batches run the StVK energy
