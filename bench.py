@@ -77,9 +77,11 @@ class ClockSampler:
 # written once; gathers of node data counted once per node).
 MIXED_BYTES = {
     "m:tet_stress": lambda i: i["n_tets"] * (16 + 72 + 4 + 24 + 24) + 12 * i["n_nodes"],
-    # per pair a 16-bit union position and an FP32 weight; per tet its list
-    # pointer, its stress row read once and its average row written
-    "m:nonlocal_avg": lambda i: 6.0 * i["n_nbr_pairs"] + i["n_tets"] * (8 + 32 + 32),
+    # joint lists of tet pairs: per entry a 16-bit union position and two FP32
+    # weights, 0.61 entries per (tet, neighbour) pair on the loaf (6.1 B per
+    # pair); per tet half a list pointer, its stress row read once and its
+    # average row written
+    "m:nonlocal_avg": lambda i: 6.1 * i["n_nbr_pairs"] + i["n_tets"] * (4 + 32 + 32),
     "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
     # phase 1: tet, rest row (128 B), chi, its ten row indices in; 6 edge rows
     # (36 B) + 4 node rows (48 B) out; u, v and the external force per node
@@ -101,7 +103,7 @@ NCU_TRAFFIC = {
     "nonlocal_avg": 1.291858e9 + 28.97152e6,
     "assemble": 234.703360e6 + 499.401728e6,
     "assemble_gather": 530.260736e6 + 118.412544e6,
-    "m:nonlocal_avg": 649.088512e6 + 20.163328e6,
+    "m:nonlocal_avg": 662.371328e6 + 20.333568e6,
     "m:assemble": 122.624256e6 + 195.889408e6,
     "m:assemble_gather": 274.354944e6 + 59.933696e6,
 }

@@ -525,7 +525,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.edge_e0, mxh.edge_e0, float);
     UP(d.mx.nb_ptr, mxh.nb_ptr, int64_t);
     UP(d.mx.nb_loc, mxh.nb_loc, uint16_t);
-    UP(d.mx.nb_wc, mxh.nb_wc, float);
+    UP(d.mx.nb_w2, mxh.nb_w2, float);
     UP(d.mx.nl_uptr, mxh.nl_uptr, int64_t);
     UP(d.mx.nl_uidx, mxh.nl_uidx, int32_t);
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());

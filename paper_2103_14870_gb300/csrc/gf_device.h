@@ -43,9 +43,9 @@ struct MixDev {
   const float* restA = nullptr;       // [T][kRAStride] (128-byte aligned rows)
   const float* restB = nullptr;       // [T][kRBStride]
   const float* edge_e0 = nullptr;     // [NE][3]
-  const int64_t* nb_ptr = nullptr;    // [T+1] CSR Eq. 20 lists
-  const uint16_t* nb_loc = nullptr;   // per pair: the neighbour's position in its tile's union
-  const float* nb_wc = nullptr;       // per pair: FP32 weight
+  const int64_t* nb_ptr = nullptr;    // [ceil(T/2)+1] Eq. 20 joint lists of tet pairs (2q, 2q+1)
+  const uint16_t* nb_loc = nullptr;   // per entry: the neighbour's position in its tile's union
+  const float2* nb_w2 = nullptr;      // per entry: the FP32 weights of tets 2q and 2q+1 (0 if not a neighbour)
   const int64_t* nl_uptr = nullptr;   // [ceil(T / kNlTile) + 1] tile unions
   const int32_t* nl_uidx = nullptr;   // union members (global tet ids, ascending per tile)
   const float* mass32 = nullptr;      // [N]

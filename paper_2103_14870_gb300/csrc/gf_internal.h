@@ -60,12 +60,14 @@ struct MixedHost {
   std::vector<float> restA;         // [T][kRAStride]
   std::vector<float> restB;         // [T][kRBStride]
   std::vector<float> edge_e0;       // [NE][3] rest edge vectors (b - a)
-  // CSR neighbour lists: nb_ptr [T+1]; per pair the neighbour's position in its
-  // tile's union (nb_loc) and the FP32 weight (nb_wc); per tile the union's
-  // global tet ids nl_uidx[nl_uptr[g], nl_uptr[g+1]), ascending
-  std::vector<int64_t> nb_ptr;
+  // Eq. 20 lists of the mixed kernel, per pair of consecutive tets (2q, 2q+1):
+  // the union of the two neighbour sets, entries [nb_ptr[q], nb_ptr[q+1]),
+  // each with the neighbour's position in its tile's union (nb_loc) and the
+  // two FP32 weights (nb_w2, zero where a tet lacks that neighbour); per tile
+  // the union's global tet ids nl_uidx[nl_uptr[g], nl_uptr[g+1]), ascending
+  std::vector<int64_t> nb_ptr;      // [ceil(T/2) + 1]
   std::vector<uint16_t> nb_loc;
-  std::vector<float> nb_wc;
+  std::vector<float> nb_w2;         // [entries][2]
   std::vector<int64_t> nl_uptr;
   std::vector<int32_t> nl_uidx;
 };

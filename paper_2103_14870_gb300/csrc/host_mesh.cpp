@@ -436,45 +436,42 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
   return GF_OK;
 }
 
-// Order of one tet's pairs for the shared-memory reads of the mixed Eq. 20
-// kernel: lane l of chunk c takes pair beg + 32 c + l, and reads the six
-// floats of union row loc as three 8-byte words at bank pair (3 loc + h) mod
-// 16.  The pairs are dealt to the chunks round-robin in (loc mod 16, loc)
+// Order of one joint list's entries for the shared-memory reads of the mixed
+// Eq. 20 kernel: lane l of chunk c takes entry beg + 32 c + l, and reads the
+// six floats of union row loc as three 8-byte words at bank pair (3 loc + h)
+// mod 16.  The entries are dealt to the chunks round-robin in (loc mod 16, loc)
 // order, so each chunk holds about two of every residue, and within a chunk
 // the first copy of each residue goes to lanes 0-15 and the second to 16-31:
-// the half-warps then read 16 distinct bank pairs (no conflicts).  Only the
-// order of the terms changes.
-void deal_pairs(MixedHost& mx, int64_t i) {
-  const int64_t b = mx.nb_ptr[i], n = mx.nb_ptr[i + 1] - b;
+// the half-warps then read distinct bank pairs where the residues allow it.
+// Only the order of the terms changes.
+struct JointEntry {
+  uint16_t loc;
+  float w[2];
+};
+void deal_entries(std::vector<JointEntry>& e) {
+  const int64_t n = int64_t(e.size());
   if (n <= 1) return;
-  std::vector<std::pair<uint16_t, float>> pr(n), out(n);
-  for (int64_t k = 0; k < n; ++k) pr[k] = {mx.nb_loc[b + k], mx.nb_wc[b + k]};
-  auto key = [](const std::pair<uint16_t, float>& a) { return std::make_pair(a.first % 16, a.first); };
-  std::sort(pr.begin(), pr.end(), [&](const auto& a, const auto& c) { return key(a) < key(c); });
+  auto key = [](const JointEntry& a) { return std::make_pair(a.loc % 16, a.loc); };
+  std::sort(e.begin(), e.end(), [&](const JointEntry& a, const JointEntry& c) { return key(a) < key(c); });
   const int64_t nc = (n + 31) / 32;
-  // chunk c holds min(32, n - 32 c) pairs: all but the last are full
-  std::vector<std::vector<std::pair<uint16_t, float>>> chunk(nc);
+  // chunk c holds min(32, n - 32 c) entries: all but the last are full
+  std::vector<std::vector<JointEntry>> chunk(nc);
   for (int64_t k = 0, c = 0; k < n; ++k, c = (c + 1) % nc) {
     while (int64_t(chunk[c].size()) == std::min<int64_t>(32, n - 32 * c)) c = (c + 1) % nc;
-    chunk[c].push_back(pr[k]);
+    chunk[c].push_back(e[k]);
   }
   int64_t o = 0;
   for (auto& c : chunk) {
-    std::sort(c.begin(), c.end(), [&](const auto& a, const auto& d) { return key(a) < key(d); });
-    // first copies of the residues to the low half, the rest after them
-    std::vector<std::pair<uint16_t, float>> lo, hi;
+    std::sort(c.begin(), c.end(), [&](const JointEntry& a, const JointEntry& d) { return key(a) < key(d); });
+    std::vector<JointEntry> lo, hi;
     for (size_t k = 0; k < c.size(); ++k)
-      ((k == 0 || c[k].first % 16 != c[k - 1].first % 16) && lo.size() < 16 ? lo : hi).push_back(c[k]);
+      ((k == 0 || c[k].loc % 16 != c[k - 1].loc % 16) && lo.size() < 16 ? lo : hi).push_back(c[k]);
     while (lo.size() < 16 && !hi.empty()) {
       lo.push_back(hi.back());
       hi.pop_back();
     }
-    for (auto& e : lo) out[o++] = e;
-    for (auto& e : hi) out[o++] = e;
-  }
-  for (int64_t k = 0; k < n; ++k) {
-    mx.nb_loc[b + k] = out[k].first;
-    mx.nb_wc[b + k] = out[k].second;
+    for (auto& x : lo) e[o++] = x;
+    for (auto& x : hi) e[o++] = x;
   }
 }
 
@@ -495,52 +492,67 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
   for (int64_t e = 0; e < NE; ++e)
     for (int c = 0; c < 3; ++c)
       mx.edge_e0[3 * e + c] = float(X[3 * hm.edges[2 * e + 1] + c] - X[3 * hm.edges[2 * e] + c]);
-  // CSR copy of the neighbour lists (from the SELL-32 layout: real entries have w > 0
-  // or are the tet itself)
+  // Neighbour lists per tet (from the SELL-32 layout: real entries have w > 0),
+  // then the tile unions and the joint lists of tet pairs (2q, 2q+1)
   {
     const NeighbourSell& S = hm.nbr;
-    mx.nb_ptr.assign(T + 1, 0);
+    std::vector<int64_t> tp(T + 1, 0);
     for (int64_t i = 0; i < T; ++i) {
       int64_t g = i / 32, l = i % 32;
       int32_t cnt = 0;
-      for (int32_t k = 0; k < S.group_len[g]; ++k) {
-        int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
-        if (S.w[o] > 0.0) cnt++;
-      }
-      mx.nb_ptr[i + 1] = mx.nb_ptr[i] + cnt;
+      for (int32_t k = 0; k < S.group_len[g]; ++k)
+        if (S.w[S.group_off[g] + 32 * int64_t(k) + l] > 0.0) cnt++;
+      tp[i + 1] = tp[i] + cnt;
     }
-    std::vector<int32_t> nb_csr(mx.nb_ptr[T]);
-    mx.nb_wc.resize(mx.nb_ptr[T]);
+    std::vector<int32_t> nb_id(tp[T]);
+    std::vector<float> nb_w(tp[T]);
     for (int64_t i = 0; i < T; ++i) {
-      int64_t g = i / 32, l = i % 32, p = mx.nb_ptr[i];
+      int64_t g = i / 32, l = i % 32, p = tp[i];
       for (int32_t k = 0; k < S.group_len[g]; ++k) {
         int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
         if (S.w[o] > 0.0) {
-          nb_csr[p] = S.idx[o];
-          mx.nb_wc[p] = float(S.w[o]);
+          nb_id[p] = S.idx[o];
+          nb_w[p] = float(S.w[o]);
           ++p;
         }
       }
     }
-    // tile unions and 16-bit positions in them
-    const int64_t NT = (T + kNlTile - 1) / kNlTile;
+    const int64_t NT = (T + kNlTile - 1) / kNlTile, NQ = (T + 1) / 2;
     std::vector<std::vector<int32_t>> U(NT);
-    mx.nb_loc.resize(nb_csr.size());
+    std::vector<std::vector<JointEntry>> J(NQ);
     std::atomic<int64_t> too_big{-1};
     parallel_for(NT, [&](int64_t b, int64_t e) {
       for (int64_t g = b; g < e; ++g) {
-        const int64_t p0 = mx.nb_ptr[kNlTile * g], p1 = mx.nb_ptr[std::min(T, kNlTile * (g + 1))];
+        const int64_t t0 = kNlTile * g, t1 = std::min(T, kNlTile * (g + 1));
         std::vector<int32_t>& u = U[g];
-        u.assign(nb_csr.begin() + p0, nb_csr.begin() + p1);
+        u.assign(nb_id.begin() + tp[t0], nb_id.begin() + tp[t1]);
         std::sort(u.begin(), u.end());
         u.erase(std::unique(u.begin(), u.end()), u.end());
         if (int64_t(u.size()) > kNlMaxUnion) {
           too_big = g;
           continue;
         }
-        for (int64_t p = p0; p < p1; ++p)
-          mx.nb_loc[p] = uint16_t(std::lower_bound(u.begin(), u.end(), nb_csr[p]) - u.begin());
-        for (int64_t i = kNlTile * g; i < std::min(T, kNlTile * (g + 1)); ++i) deal_pairs(mx, i);
+        auto pos = [&](int32_t j) { return uint16_t(std::lower_bound(u.begin(), u.end(), j) - u.begin()); };
+        for (int64_t a = t0; a < t1; a += 2) {   // merge the two sorted lists
+          std::vector<JointEntry>& jq = J[a / 2];
+          int64_t p = tp[a], pe = tp[a + 1], r = a + 1 < T ? tp[a + 1] : 0, re = a + 1 < T ? tp[a + 2] : 0;
+          while (p < pe || r < re) {
+            JointEntry x{};
+            if (r >= re || (p < pe && nb_id[p] < nb_id[r])) {
+              x = {pos(nb_id[p]), {nb_w[p], 0.f}};
+              ++p;
+            } else if (p >= pe || nb_id[r] < nb_id[p]) {
+              x = {pos(nb_id[r]), {0.f, nb_w[r]}};
+              ++r;
+            } else {
+              x = {pos(nb_id[p]), {nb_w[p], nb_w[r]}};
+              ++p;
+              ++r;
+            }
+            jq.push_back(x);
+          }
+          deal_entries(jq);
+        }
       }
     });
     if (too_big >= 0) {
@@ -552,6 +564,19 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
     for (int64_t g = 0; g < NT; ++g) mx.nl_uptr[g + 1] = mx.nl_uptr[g] + int64_t(U[g].size());
     mx.nl_uidx.resize(mx.nl_uptr[NT]);
     for (int64_t g = 0; g < NT; ++g) std::copy(U[g].begin(), U[g].end(), mx.nl_uidx.begin() + mx.nl_uptr[g]);
+    mx.nb_ptr.assign(NQ + 1, 0);
+    for (int64_t q = 0; q < NQ; ++q) mx.nb_ptr[q + 1] = mx.nb_ptr[q] + int64_t(J[q].size());
+    mx.nb_loc.resize(mx.nb_ptr[NQ]);
+    mx.nb_w2.resize(2 * mx.nb_ptr[NQ]);
+    parallel_for(NQ, [&](int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q)
+        for (size_t k = 0; k < J[q].size(); ++k) {
+          const int64_t o = mx.nb_ptr[q] + int64_t(k);
+          mx.nb_loc[o] = J[q][k].loc;
+          mx.nb_w2[2 * o] = J[q][k].w[0];
+          mx.nb_w2[2 * o + 1] = J[q][k].w[1];
+        }
+    });
   }
   return GF_OK;
 }
