@@ -1016,8 +1016,11 @@ __device__ __forceinline__ void pcg_init_body(const DevMesh& m, const Material& 
 #pragma unroll
       for (int c = 0; c < 3; ++c) z[c] = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
     } else if (!m.pinned[i]) {
-      double ad[3];
-      spmv_row(m, i, m.dv, ad);
+      // every caller zeroes dv before k_set_pinned, so without pinned nodes and
+      // without a warm start dv is exactly zero: A dv = 0 and b - 0 = b, and the
+      // product is skipped (same bits)
+      double ad[3] = {0.0, 0.0, 0.0};
+      if (sp.n_pinned > 0 || sp.warm) spmv_row(m, i, m.dv, ad);
 #pragma unroll
       for (int c = 0; c < 3; ++c) r[c] = m.rhs[3 * i + c] - ad[c];
       const double* a = m.val + 9 * int64_t(m.diag_blk[i]);

@@ -816,7 +816,9 @@ __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Materia
     const int b1 = m.row_ptr[i + 1];
     float bh[3] = {0.f, 0.f, 0.f};
     if (j8 == 0) ld3f(x.rhs32, i, bh);
-    {
+    // the first residual of a step without pinned nodes has dv = 0 exactly:
+    // A dv = 0 and b - 0 = b, so the product is skipped (same bits)
+    if (!(first && sp.n_pinned == 0)) {
       for (int b = m.row_ptr[i] + j8; b < b1; b += 16) {
         const bool two = b + 8 < b1;
         const int64_t j0 = m.col[b], j1 = two ? m.col[b + 8] : j0;
