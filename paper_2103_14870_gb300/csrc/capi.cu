@@ -516,6 +516,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.nb_off, hm.nbr.group_off, int64_t);
     UP(d.nb_len, hm.nbr.group_len, int32_t);
     UP(d.nb_idx, hm.nbr.idx, int32_t);
+    UP(d.nb_perm, hm.nbr.perm, int32_t);
     UP(d.slot, hm.slot, int32_t);
     UP(d.rest, hm.rest, double);
     UP(d.nb_w, hm.nbr.w, double);
@@ -632,7 +633,7 @@ gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets
   info->device_bytes = int64_t(hm.tets.size() * 4 + hm.tet_edges.size() * 4 + hm.slot.size() * 4 +
                                hm.rest.size() * 8 + hm.row_ptr.size() * 4 + hm.col.size() * 4 +
                                hm.edges.size() * 4 + hm.et_ptr.size() * 4 + hm.et_tet.size() * 4 +
-                               hm.nbr.idx.size() * 12 + hm.nbr.group_off.size() * 12) +
+                               hm.nbr.idx.size() * 12 + hm.nbr.group_off.size() * 12 + hm.nbr.perm.size() * 4) +
                        N * (8 + 8 * 3 * 12 + 9 * 8 + 8) + T * (8 + 18 * 8 + 4) + hm.n_edges * 9 + hm.n_blocks * 72;
   if (edges) std::memcpy(edges, hm.edges.data(), sizeof(int32_t) * hm.edges.size());
   if (colour)
@@ -641,7 +642,7 @@ gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets
   if (nbr_count) {
     const NeighbourSell& S = hm.nbr;
     for (int64_t i = 0; i < T; ++i) {
-      int64_t g = i / 32, l = i % 32;
+      int64_t g = S.slot[i] / 32, l = S.slot[i] % 32;
       int32_t cnt = 0;
       for (int32_t k = 0; k < S.group_len[g]; ++k) cnt += S.w[S.group_off[g] + 32 * k + l] > 0.0 ? 1 : 0;
       nbr_count[hm.perm[i]] = cnt;

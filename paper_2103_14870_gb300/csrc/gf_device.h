@@ -93,6 +93,7 @@ struct DevMesh {
   const int64_t* nb_off = nullptr;     // [G]
   const int32_t* nb_len = nullptr;     // [G]
   const int32_t* nb_idx = nullptr;
+  const int32_t* nb_perm = nullptr;    // [T] lane slot -> tet (the SELL order)
   const double* nb_w = nullptr;
   // state
   double* x = nullptr;                 // [3N]

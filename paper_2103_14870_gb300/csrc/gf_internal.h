@@ -37,6 +37,8 @@ GF_HD constexpr int tri6(int k, int l) { return k * 6 - k * (k - 1) / 2 + (l - k
 struct NeighbourSell {            // Eq. 20 neighbour lists, 32 tets per group, entry-major in a group
   std::vector<int64_t> group_off; // [G] first entry of the group
   std::vector<int32_t> group_len; // [G] entries per lane (max count in the group)
+  std::vector<int32_t> perm;      // [T] lane slot 32 g + l -> tet (tets sorted by list length within windows)
+  std::vector<int32_t> slot;      // [T] tet -> lane slot
   std::vector<int32_t> idx;       // [sum 32*len] neighbour tet (internal order); padding -> own tet
   std::vector<double> w;          // normalised weights; padding -> 0
   int64_t pairs = 0;              // real (unpadded) pairs

@@ -402,15 +402,27 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
       }
     });
   }
-  // SELL-32 layout: 32 consecutive tets per group, entry k of lane l at off + 32 k + l
+  // SELL-32 layout: 32 tets per group, entry k of lane l at off + 32 k + l.
+  // Within each window of 1024 consecutive tets the tets are ordered by list
+  // length (longest first), so that the 32 lanes of a group have nearly equal
+  // lists and the group's padding (to its longest list) is small; the window
+  // keeps a group's tets close together on the mesh.
   NeighbourSell& S = hm.nbr;
   int64_t G = (T + 31) / 32;
+  S.perm.resize(T);
+  S.slot.resize(T);
+  for (int64_t i = 0; i < T; ++i) S.perm[i] = int32_t(i);
+  constexpr int64_t kWin = 1024;
+  for (int64_t w0 = 0; w0 < T; w0 += kWin)
+    std::stable_sort(S.perm.begin() + w0, S.perm.begin() + std::min(T, w0 + kWin),
+                     [&](int32_t x, int32_t y) { return nb_list[x].size() > nb_list[y].size(); });
+  for (int64_t q = 0; q < T; ++q) S.slot[S.perm[q]] = int32_t(q);
   S.group_off.resize(G);
   S.group_len.resize(G);
   int64_t total = 0;
   for (int64_t g = 0; g < G; ++g) {
     size_t mx = 0;
-    for (int64_t i = 32 * g; i < std::min(T, 32 * g + 32); ++i) mx = std::max(mx, nb_list[i].size());
+    for (int64_t q = 32 * g; q < std::min(T, 32 * g + 32); ++q) mx = std::max(mx, nb_list[S.perm[q]].size());
     S.group_off[g] = total;
     S.group_len[g] = int32_t(mx);
     total += 32 * int64_t(mx);
@@ -420,15 +432,16 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
   S.pairs = 0;
   for (int64_t g = 0; g < G; ++g)
     for (int l = 0; l < 32; ++l) {
-      int64_t i = 32 * g + l;
+      const int64_t q = 32 * g + l;
+      const int64_t i = q < T ? S.perm[q] : 0;
       for (int32_t k = 0; k < S.group_len[g]; ++k) {
         int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
-        if (i < T && size_t(k) < nb_list[i].size()) {
+        if (q < T && size_t(k) < nb_list[i].size()) {
           S.idx[o] = nb_list[i][k];
           S.w[o] = nb_wt[i][k];
           S.pairs++;
         } else {
-          S.idx[o] = int32_t(i < T ? i : 0);
+          S.idx[o] = int32_t(i);
           S.w[o] = 0.0;
         }
       }
@@ -498,7 +511,7 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
     const NeighbourSell& S = hm.nbr;
     std::vector<int64_t> tp(T + 1, 0);
     for (int64_t i = 0; i < T; ++i) {
-      int64_t g = i / 32, l = i % 32;
+      int64_t g = S.slot[i] / 32, l = S.slot[i] % 32;
       int32_t cnt = 0;
       for (int32_t k = 0; k < S.group_len[g]; ++k)
         if (S.w[S.group_off[g] + 32 * int64_t(k) + l] > 0.0) cnt++;
@@ -507,7 +520,7 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
     std::vector<int32_t> nb_id(tp[T]);
     std::vector<float> nb_w(tp[T]);
     for (int64_t i = 0; i < T; ++i) {
-      int64_t g = i / 32, l = i % 32, p = tp[i];
+      int64_t g = S.slot[i] / 32, l = S.slot[i] % 32, p = tp[i];
       for (int32_t k = 0; k < S.group_len[g]; ++k) {
         int64_t o = S.group_off[g] + 32 * int64_t(k) + l;
         if (S.w[o] > 0.0) {

@@ -150,14 +150,16 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress(const BatchTab* __rest
   tet_stress_body<false>(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);   // batches run the StVK energy
 }
 
-// Eq. 20 sum: thread per tet, neighbour lists in SELL-32 layout (coalesced
-// index/weight loads; the neighbour stresses are gathered from L2).
+// Eq. 20 sum: thread per SELL-32 lane slot (coalesced index/weight loads; the
+// neighbour stresses are gathered from L2).  Slot q holds tet nb_perm[q]: the
+// tets of a window are ordered by list length, so a group pads little.
 __device__ __forceinline__ void nonlocal_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
-  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= m.T) return;
-  const int64_t g = t >> 5;
-  const int lane = int(t & 31);
+  const int64_t q = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= m.T) return;
+  const int64_t g = q >> 5;
+  const int lane = int(q & 31);
+  const int64_t t = m.nb_perm[q];
   const int64_t off = m.nb_off[g] + lane;
   const int len = m.nb_len[g];
   double acc[6] = {0, 0, 0, 0, 0, 0};
