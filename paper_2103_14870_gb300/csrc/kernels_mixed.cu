@@ -780,22 +780,31 @@ __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float
   df_add(hi, lo, p, pe);
 }
 
-// r = b - A32 dv on free rows, with A32 dv formed in double-float (dv = dv_hi +
-// dv_lo) and b - A dv in double-float; eight lanes per block row (lane j takes
-// blocks j, j+8, ..., two at a time so that both blocks' loads are in flight
-// before the arithmetic), then an 8-lane double-float reduction.  The inner
-// solve's right-hand side is the leading float of r; ||r||^2 accumulates in
-// double-float.
-__device__ __forceinline__ void df_block_acc(float (&hi)[3], float (&lo)[3], const float (&a)[9], const float (&xh)[3],
-                                             const float (&xl)[3]) {
+// r = b - A32 dv on free rows, with A32 dv formed to double-float accuracy
+// (dv = dv_hi + dv_lo) and b - A dv in double-float; eight lanes per block row
+// (lane j takes blocks j, j+8, ..., two at a time so that both blocks' loads
+// are in flight before the arithmetic).  Each lane accumulates in the manner of
+// Dot2 (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): s collects
+// the rounded products, c the exact error of each product (an FMA) and of each
+// addition (TwoSum), and s + c is as accurate as a sum in twice the precision;
+// the pair is renormalised once per lane.  A transposing double-float butterfly
+// then leaves component c of row i in lanes 2c and 2c + 1, and lane 2c forms
+// r_c.  The inner solve's right-hand side is the leading float of r; ||r||^2
+// accumulates in double-float.
+__device__ __forceinline__ void dot2_block(float (&s)[4], float (&c)[4], const float (&a)[9], const float (&xh)[3],
+                                           const float (&xl)[3]) {
 #pragma unroll
   for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float p, pe;
-      two_prod(a[3 * rr + c], xh[c], p, pe);
-      pe = fmaf(a[3 * rr + c], xl[c], pe);
-      df_add(hi[rr], lo[rr], p, pe);
+    for (int k = 0; k < 3; ++k) {
+      const float av = a[3 * rr + k];
+      const float p = av * xh[k];
+      const float pe = fmaf(av, xl[k], fmaf(av, xh[k], -p));   // product error + the dv_lo term
+      const float t = s[rr] + p;
+      const float bp = t - s[rr];
+      const float e = (s[rr] - (t - bp)) + (p - bp);              // TwoSum error
+      s[rr] = t;
+      c[rr] += e + pe;
     }
 }
 __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb, int first) {
@@ -810,15 +819,16 @@ __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Materia
   float nh_[1] = {0.f}, nl_[1] = {0.f};
   const int64_t ng = (int64_t(nb) * blockDim.x) >> 3;
   for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 3; i < m.N; i += ng) {
-    float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
+    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
     // independent loads first; pinned rows run the loop too and are zeroed at the end
     const bool fixed = m.pinned[i];
     const int b1 = m.row_ptr[i + 1];
-    float bh[3] = {0.f, 0.f, 0.f};
-    if (j8 == 0) ld3f(x.rhs32, i, bh);
+    const int cw = j8 >> 1;   // the component this lane ends with (3: none)
+    const float bh = ((j8 & 1) == 0 && cw < 3) ? x.rhs32[3 * i + cw] : 0.f;
     // the first residual of a step without pinned nodes has dv = 0 exactly:
     // A dv = 0 and b - 0 = b, so the product is skipped (same bits)
     if (!(first && sp.n_pinned == 0)) {
+      float sacc[4] = {0, 0, 0, 0}, cacc[4] = {0, 0, 0, 0};
       for (int b = m.row_ptr[i] + j8; b < b1; b += 16) {
         const bool two = b + 8 < b1;
         const int64_t j0 = m.col[b], j1 = two ? m.col[b + 8] : j0;
@@ -832,30 +842,38 @@ __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Materia
         ld3f(x.dv_lo, j0, xl0);
         ld3f(x.dv_hi, j1, xh1);
         ld3f(x.dv_lo, j1, xl1);
-        df_block_acc(hi, lo, a0, xh0, xl0);
-        if (two) df_block_acc(hi, lo, a1, xh1, xl1);
+        dot2_block(sacc, cacc, a0, xh0, xl0);
+        if (two) dot2_block(sacc, cacc, a1, xh1, xl1);
       }
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr) two_sum(sacc[rr], cacc[rr], hi[rr], lo[rr]);
     }
+    // transposing butterfly over the 8 lanes: keep 2 of 4 values, then 1 of 2, then pair up
+    {
+      const bool h2 = j8 & 4, h1 = j8 & 2;
+      float uh[2], ul[2];
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-      for (int rr = 0; rr < 3; ++rr) {
-        const float oh = __shfl_xor_sync(gmask, hi[rr], o);
-        const float ol = __shfl_xor_sync(gmask, lo[rr], o);
-        df_add(hi[rr], lo[rr], oh, ol);
+      for (int k = 0; k < 2; ++k) {
+        const float sh = h2 ? hi[k] : hi[2 + k], sl = h2 ? lo[k] : lo[2 + k];
+        uh[k] = h2 ? hi[2 + k] : hi[k];
+        ul[k] = h2 ? lo[2 + k] : lo[k];
+        df_add(uh[k], ul[k], __shfl_xor_sync(gmask, sh, 4), __shfl_xor_sync(gmask, sl, 4));
       }
-    if (j8 == 0) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float rh = 0.f, rl = 0.f;
-        if (!fixed) {
-          rh = bh[c];
-          df_add(rh, rl, -hi[c], -lo[c]);
-        }
-        x.rres[3 * i + c] = rh;
-        df_acc_prod(nh_[0], nl_[0], rh, rh);
-        df_add(nh_[0], nl_[0], 2.f * rh * rl, 0.f);
+      float vh = h1 ? uh[1] : uh[0], vl = h1 ? ul[1] : ul[0];
+      df_add(vh, vl, __shfl_xor_sync(gmask, h1 ? uh[0] : uh[1], 2), __shfl_xor_sync(gmask, h1 ? ul[0] : ul[1], 2));
+      df_add(vh, vl, __shfl_xor_sync(gmask, vh, 1), __shfl_xor_sync(gmask, vl, 1));
+      hi[0] = vh;
+      lo[0] = vl;
+    }
+    if ((j8 & 1) == 0 && cw < 3) {
+      float rh = 0.f, rl = 0.f;
+      if (!fixed) {
+        rh = bh;
+        df_add(rh, rl, -hi[0], -lo[0]);
       }
+      x.rres[3 * i + cw] = rh;
+      df_acc_prod(nh_[0], nl_[0], rh, rh);
+      df_add(nh_[0], nl_[0], 2.f * rh * rl, 0.f);
     }
   }
   double out[1];
