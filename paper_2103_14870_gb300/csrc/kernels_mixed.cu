@@ -216,27 +216,31 @@ __device__ __forceinline__ void nl_row(const MixDev& x, const float2* su, bool s
     r2 = make_float2(sj[4], sj[5]);
   }
 }
-// acc[0..5]: first tet of the pair, acc[8..13]: second (6, 7, 14, 15 stay 0)
+// Packed FP32 FMA (two lanes of fma.rn.f32x2, sm_100 and later): c.x += a.x b.x,
+// c.y += a.y b.y, each rounded once like a scalar FMA.
+__device__ __forceinline__ void fma2(float2& c, float2 a, float2 b) {
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%0, %1};\n\t"
+      "fma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+      : "+f"(c.x), "+f"(c.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+}
+// acc[0..2]: the first tet of the pair (columns 0-5 as pairs), acc[4..6]: the second
+// (acc[3], acc[7] stay 0: columns 6, 7 of the output rows)
 __device__ __forceinline__ void nl_accumulate(const MixDev& x, const float2* su, bool staged, int64_t u0, const NlPairs& q,
-                                              float (&acc)[16]) {
+                                              float2 (&acc)[8]) {
 #pragma unroll
   for (int c = 0; c < kNlChunks; ++c) {
     if (q.loc[c] < 0) continue;
     float2 r0, r1, r2;
     nl_row(x, su, staged, u0, q.loc[c], r0, r1, r2);
-    const float wa = q.wt[c].x, wb = q.wt[c].y;
-    acc[0] += wa * r0.x;
-    acc[1] += wa * r0.y;
-    acc[2] += wa * r1.x;
-    acc[3] += wa * r1.y;
-    acc[4] += wa * r2.x;
-    acc[5] += wa * r2.y;
-    acc[8] += wb * r0.x;
-    acc[9] += wb * r0.y;
-    acc[10] += wb * r1.x;
-    acc[11] += wb * r1.y;
-    acc[12] += wb * r2.x;
-    acc[13] += wb * r2.y;
+    const float2 wa = make_float2(q.wt[c].x, q.wt[c].x), wb = make_float2(q.wt[c].y, q.wt[c].y);
+    fma2(acc[0], wa, r0);
+    fma2(acc[1], wa, r1);
+    fma2(acc[2], wa, r2);
+    fma2(acc[4], wb, r0);
+    fma2(acc[5], wb, r1);
+    fma2(acc[6], wb, r2);
   }
 }
 
@@ -283,14 +287,20 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
     // the next pair's first chunks are in flight while this one is summed
     const int64_t nbeg = end, nend = __shfl_sync(0xffffffffu, myptr, k + 2 <= np ? k + 2 : np);
     if (k + 1 < np) nl_load(x, nbeg + lane, nend, nxt);
-    float acc[16];
+    float2 acc2[8];
 #pragma unroll
-    for (int v = 0; v < 16; ++v) acc[v] = 0.f;
-    nl_accumulate(x, su, staged, u0, cur, acc);
+    for (int v = 0; v < 8; ++v) acc2[v] = make_float2(0.f, 0.f);
+    nl_accumulate(x, su, staged, u0, cur, acc2);
     for (int64_t p = beg + lane + 32 * kNlChunks; p < end; p += 32 * kNlChunks) {   // lists longer than 224
       NlPairs more;
       nl_load(x, p, end, more);
-      nl_accumulate(x, su, staged, u0, more, acc);
+      nl_accumulate(x, su, staged, u0, more, acc2);
+    }
+    float acc[16];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      acc[2 * v] = acc2[v].x;
+      acc[2 * v + 1] = acc2[v].y;
     }
     const float tot = warp_transpose_sum16(acc, lane);
     // lane L (even) holds value L / 2: tet (L / 16) of the pair, column (L / 2) % 8 (6, 7 are zero)
