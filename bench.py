@@ -231,7 +231,7 @@ def run_batch(args, gf, torch, barrier, stream) -> dict:
            "cg_rtol": 1e-6, "tuning": tuned, "autotune_ms_per_step": tuned_ms}
     per_mode = {}
     for graph in (1, 0):
-        b.tuning_set(graph=graph, chunk=tuned["chunk"] if tuned["graph"] == 0 else 8)
+        b.tuning_set(graph=graph, chunk=tuned["chunk"] if tuned["graph"] == 0 else 8, grid_budget=tuned["grid_budget"])
         for _ in range(args.warmup):
             b.step(dt, f, pins)
         l0 = b.launch_count()
@@ -248,7 +248,7 @@ def run_batch(args, gf, torch, barrier, stream) -> dict:
         ms_b = e0.elapsed_time(e1) / args.steps
         per_mode["graph" if graph else "stream"] = {"ms_per_step": ms_b, "gpu_launches": b.launch_count() - l0,
                                                     "cg_iters_mean": statistics.mean(iters)}
-    b.tuning_set(graph=tuned["graph"], chunk=tuned["chunk"])
+    b.tuning_set(graph=tuned["graph"], chunk=tuned["chunk"], grid_budget=tuned["grid_budget"])
     best = per_mode["graph" if tuned["graph"] else "stream"]
     out.update(ms_per_step=best["ms_per_step"], element_updates_per_s=out["n_tets_total"] / (best["ms_per_step"] * 1e-3),
                modes=per_mode)
@@ -543,6 +543,7 @@ def run_ours(args) -> None:
 def run_profile_step(args) -> None:
     """Minimal command for ncu captures: build the loaf mesh, run `--steps` steps, no timing.
     --precision: fp64 | mixed | learned (FP64 with the network's start, then one Adam step) |
+    batch (the 64-box mixed batch, stream launches) |
     snh (stable Neo-Hookean FP64) | qs (one quasi-static pull load step after the steps) |
     surface (split visualisation mesh after the steps)."""
     import numpy as np
@@ -550,6 +551,23 @@ def run_profile_step(args) -> None:
     import paper_2103_14870_gb300 as gf
     from workloads import loaf_config
     torch.cuda.set_device(0)
+    if args.precision == "batch":        # the 64-box batch, stream launches so that ncu lists the kernels
+        from workloads import batch_configs
+        ws = batch_configs()
+        meshes = [gf.mesh_create(v.nodes, v.tets, gf.material(v.young, v.poisson, v.density, threshold=v.threshold,
+                                                              radius=v.radius), precision=gf.MIXED, cg_rtol=1e-6)
+                  for v in ws]
+        b = gf.Batch(meshes)
+        b.tuning_set(graph=0, chunk=8, grid_budget=4 * 152 * 2)
+        f = [torch.tensor(v.f_ext.ravel(), dtype=torch.float64, device="cuda") for v in ws]
+        pins = [torch.tensor(v.pinned, dtype=torch.int32, device="cuda") for v in ws]
+        st = None
+        for _ in range(args.steps):
+            st = b.step(ws[0].dt, f, pins)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "steps": args.steps, "batch": len(ws),
+                          "max_cg_iters": max(x["cg_iters"] for x in st), "launches": b.launch_count()}))
+        return
     w = loaf_config()
     mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius,
                       energy=gf.ENERGY_SNH if args.precision == "snh" else gf.ENERGY_STVK)
@@ -602,7 +620,7 @@ def main():
                     help="skip the SNH / consistent-mass / Newton / quasi-static / surface lines")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "learned", "snh", "qs", "surface"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "mixed", "learned", "snh", "qs", "surface", "batch"], default="fp64",
                     help="form run by --profile-step (see run_profile_step)")
     args = ap.parse_args()
     if args.cpu_sample_child:

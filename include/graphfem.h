@@ -174,8 +174,9 @@ gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* 
  * step_launch: GF_STEP_GRAPH (default) runs a plain step (one Newton
  * iteration, gather assembly, no network attached, profiling off) as one CUDA
  * graph replay: its launches are captured on the first such step and again
- * whenever dt, the presence of f_ext / pinned velocities, the pinned count,
- * the device input pointers or the iteration limit change; the solver loop is
+ * whenever dt, the presence of f_ext / pinned velocities, the pinned count or
+ * the iteration limit change (device inputs are copied into the mesh's own
+ * buffers first, so a new caller buffer per step costs no capture); the solver loop is
  * a device-side WHILE node, so the host waits once per step.  The results are
  * the same bits as GF_STEP_STREAM, which launches kernel by kernel with a host
  * check per chunk of solver iterations (and is what the other steps use). */
@@ -331,7 +332,13 @@ typedef struct gf_batch_tuning {
   int32_t graph;        /* 1: whole step as one CUDA graph with a device-side solve loop (default)
                            0: stream launches, host checks convergence every `chunk` iterations */
   int32_t chunk;        /* iterations between host checks when graph = 0 (0 -> 8) */
-  int32_t reserved[6];  /* set to 0 */
+  int32_t grid_budget;  /* CTAs of one launch of a solver-loop kernel, summed over the meshes.
+                           0 (default): every mesh keeps its single-mesh grid, and members step
+                           bit-identically to single-mesh steps.  > 0: the budget is split over the
+                           meshes by node count (at least 1 CTA each, at most the single-mesh grid);
+                           converged meshes then cost few early-exit CTAs per iteration, and the
+                           per-mesh reductions sum in a different (still fixed) order. */
+  int32_t reserved[5];  /* set to 0 */
 } gf_batch_tuning;
 
 /* meshes: n handles (1 <= n <= 256), same device and precision.  The batch
@@ -352,7 +359,8 @@ gf_status gf_batch_tuning_set(gf_batch* batch, const gf_batch_tuning* tuning);
 gf_status gf_batch_tuning_get(const gf_batch* batch, gf_batch_tuning* tuning);
 
 /* Autotuner: times `trial_steps` batch steps under each candidate schedule
- * (graph replay vs stream launches with several host-check intervals) on a
+ * (graph replay vs stream launches with several host-check intervals, with
+ * the single-mesh grids and with grid budgets of 1, 2 and 4 waves) on a
  * copy of the current state, restores the state, keeps the fastest schedule
  * and returns it in *best (may be NULL) and its time per step in *ms (may be
  * NULL).  Inputs as in gf_batch_step. */

@@ -1122,24 +1122,28 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
   cudaStream_t s = m->stream;
   DevMesh d = m->dm;   // per-step view (input pointers may be overridden)
   const int64_t N = d.N;
+  const bool graph = graph_step_ok(m);
   GF_CK(cudaMemsetAsync(d.counters, 0, sizeof(unsigned long long) * kCntMax, s));
-  if (f_ext && mem == GF_MEM_HOST) {
-    GF_CK(cudaMemcpyAsync(d.f_ext, f_ext, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+  // inputs: host arrays are copied into the library's buffers; device arrays are
+  // read in place, except by the graph form, which copies them too (a few us) so
+  // that a new caller buffer per step does not force a new capture
+  const cudaMemcpyKind in_kind = mem == GF_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const bool copy_in = mem == GF_MEM_HOST || graph;
+  if (f_ext && copy_in) {
+    GF_CK(cudaMemcpyAsync(d.f_ext, f_ext, sizeof(double) * 3 * N, in_kind, s));
   } else if (f_ext) {
     d.f_ext = const_cast<double*>(f_ext);
   }
   if (n_pinned > 0) {
-    if (mem == GF_MEM_HOST) {
-      GF_CK(cudaMemcpyAsync(d.pin_ids, pinned, sizeof(int32_t) * n_pinned, cudaMemcpyHostToDevice, s));
-      if (pinned_vel)
-        GF_CK(cudaMemcpyAsync(d.pin_vel, pinned_vel, sizeof(double) * 3 * n_pinned, cudaMemcpyHostToDevice, s));
+    if (copy_in) {
+      GF_CK(cudaMemcpyAsync(d.pin_ids, pinned, sizeof(int32_t) * n_pinned, in_kind, s));
+      if (pinned_vel) GF_CK(cudaMemcpyAsync(d.pin_vel, pinned_vel, sizeof(double) * 3 * n_pinned, in_kind, s));
     } else {
       d.pin_ids = const_cast<int32_t*>(pinned);
       if (pinned_vel) d.pin_vel = const_cast<double*>(pinned_vel);
     }
   }
   int64_t L = 0;
-  const bool graph = graph_step_ok(m);
   gf_status st = graph ? step_graph(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr)
                  : m->mixed ? step_mixed(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L)
                             : step_fp64(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L);
@@ -1842,11 +1846,21 @@ gf_status batch_prepare(gf_batch* b, double dt, const double* const* f_ext, cons
   }
   std::vector<int32_t> shape;
   shape.reserve(size_t(kBKinds) * (b->n + 1));
+  int64_t n_sum = 0;
+  for (int k = 0; k < b->n; ++k) n_sum += b->htab->mesh[k].N;
+  const int64_t budget = b->tune.grid_budget;
   for (int kind = 0; kind < kBKinds; ++kind) {
+    // the solver-loop kernels are grid-stride: any per-mesh grid covers the mesh
+    const bool loop_kind = kind == kB_ir_inner_init || kind == kB_ir_spmv || kind == kB_ir_update || kind == kB_ir_p ||
+                           kind == kB_ir_apply || kind == kB_ir_residual || kind == kB_pcg_spmv ||
+                           kind == kB_pcg_update || kind == kB_pcg_p;
     int32_t acc = 0;
     b->htab->off[kind][0] = 0;
     for (int k = 0; k < b->n; ++k) {
-      acc += int32_t(launch_dims(kind, b->htab->mesh[k], b->htab->mt[k], b->htab->sp[k]).blocks);
+      int64_t blocks = launch_dims(kind, b->htab->mesh[k], b->htab->mt[k], b->htab->sp[k]).blocks;
+      if (loop_kind && budget > 0 && blocks > 0)
+        blocks = std::min(blocks, std::max<int64_t>(1, (budget * b->htab->mesh[k].N + n_sum - 1) / n_sum));
+      acc += int32_t(blocks);
       b->htab->off[kind][k + 1] = acc;
     }
     b->blocks[kind] = unsigned(acc);
@@ -2031,8 +2045,8 @@ gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, cons
 }
 
 gf_status gf_batch_tuning_set(gf_batch* b, const gf_batch_tuning* t) {
-  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0) {
-    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0");
+  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0 || t->grid_budget < 0) {
+    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0, grid_budget >= 0");
     return GF_BAD_ARG;
   }
   b->tune = *t;
@@ -2090,14 +2104,19 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
   const gf_batch_tuning orig = b->tune;
   std::vector<gf_batch_tuning> cands;
   {
-    gf_batch_tuning t{};
-    t.graph = 1;
-    t.chunk = 8;
-    cands.push_back(t);
-    for (int c : {2, 4, 8, 16}) {
-      t.graph = 0;
-      t.chunk = c;
+    const int wave = 4 * 152;   // one wave of a loop kernel at 4 CTAs per SM
+    for (int budget : {0, wave, 2 * wave, 4 * wave}) {
+      gf_batch_tuning t{};
+      t.graph = 1;
+      t.chunk = 8;
+      t.grid_budget = budget;
       cands.push_back(t);
+      if (budget > 2 * wave) continue;
+      for (int c : {2, 8}) {
+        t.graph = 0;
+        t.chunk = c;
+        cands.push_back(t);
+      }
     }
   }
   double best_t = 1e300;

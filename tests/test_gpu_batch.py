@@ -83,6 +83,33 @@ def test_batch_equals_single_meshes(precision, graph):
     batch.close()
 
 
+@pytest.mark.parametrize("precision", [gf.FP64, gf.MIXED])
+def test_batch_grid_budget(precision):
+    """A grid budget (the loop kernels' CTAs split over the meshes by size)
+    changes only the reductions' summation order: members agree with their
+    single-mesh steps to rounding and converge to the same tolerance."""
+    ws = box_workloads()
+    states, thetas = start_states(ws)
+    singles = make(ws, precision, thetas)
+    members = make(ws, precision, thetas)
+    for m1, m2, st in zip(singles, members, states):
+        for m in (m1, m2):
+            m.state_set(x=st.x.ravel(), v=st.v.ravel())
+    batch = gf.Batch(members)
+    batch.tuning_set(graph=1, chunk=8, grid_budget=48)
+    assert batch.tuning_get()["grid_budget"] == 48
+    f = [w.f_ext.ravel() for w in ws]
+    pins = [w.pinned for w in ws]
+    bstats = batch.step(1e-3, f, pins)
+    sstats = [m.step(1e-3, w.f_ext.ravel(), w.pinned) for m, w in zip(singles, ws)]
+    for a, b in zip(bstats, sstats):
+        assert a["status"] == 0 and a["rel_res"] <= 1e-10 and b["rel_res"] <= 1e-10
+    for m1, m2 in zip(singles, members):
+        x1, x2 = m1.positions_get(), m2.positions_get()
+        assert np.abs(x1 - x2).max() <= 1e-9 * np.abs(x1).max()
+    batch.close()
+
+
 def test_batch_meshes_converge_independently():
     ws = box_workloads(seed=5)
     ms = make(ws, gf.FP64, [math.inf] * len(ws))

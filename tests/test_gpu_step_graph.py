@@ -66,7 +66,8 @@ def test_graph_step_matches_stream_step(precision):
 
 
 def test_graph_step_device_inputs_and_pointer_change():
-    """Device input buffers are part of the capture: a new buffer re-captures."""
+    """A new device input buffer every step (copied into the mesh's buffers by
+    the graph form, read in place by the stream form) gives the same bits."""
     w = beam_config()
     st, mat = _fracturing_material(w)
     g, s = _pair(w, mat, st, gf.FP64)
