@@ -100,7 +100,7 @@ MIXED_BYTES = {
 # assembly groups list their main kernel (k_elem64 / k_gather64, k_elem32 /
 # k_gather32).
 NCU_TRAFFIC = {
-    "nonlocal_avg": 1.291858e9 + 28.97152e6,
+    "nonlocal_avg": 1.236900864e9 + 30.863872e6,
     "assemble": 234.703360e6 + 499.401728e6,
     "assemble_gather": 530.260736e6 + 118.412544e6,
     "m:nonlocal_avg": 662.371328e6 + 20.333568e6,
