@@ -213,11 +213,16 @@ def run_reference(args) -> None:
                       "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def run_batch(args, gf, torch, barrier, stream) -> dict:
+def run_batch(args, gf, torch, barrier, stream, world=1, rank=0, dist=None) -> dict:
     """64 Kuhn boxes of uneven size (2k-80k tets, log-uniform, seed 2), mixed
-    precision, stepped together: autotuned schedule, then timed."""
+    precision, stepped together: autotuned schedule, then timed.  With N ranks
+    the meshes are split by the greedy largest-first rule (no collective on the
+    data path) and the time per step is the max over ranks."""
+    from paper_2103_14870_gb300.sharding import assign_meshes
     from workloads import batch_configs
-    ws = batch_configs()
+    ws_all = batch_configs()
+    mine = assign_meshes([w.n_tets for w in ws_all], world)[rank]
+    ws = [ws_all[k] for k in mine]
     meshes = [gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=w.threshold,
                                                           radius=w.radius), precision=gf.MIXED, cg_rtol=1e-6)
               for w in ws]
@@ -227,8 +232,10 @@ def run_batch(args, gf, torch, barrier, stream) -> dict:
     dt = ws[0].dt
     tuned, tuned_ms = b.autotune(dt, f, pins, trial_steps=3)
     out = {"workload": "64 Kuhn boxes, 2k-80k tets (log-uniform, seed 2), E in [1e4, 1e8]",
-           "n_meshes": len(ws), "n_tets_total": int(sum(w.n_tets for w in ws)), "precision": "mixed",
-           "cg_rtol": 1e-6, "tuning": tuned, "autotune_ms_per_step": tuned_ms}
+           "n_meshes": len(ws_all), "n_tets_total": int(sum(w.n_tets for w in ws_all)), "precision": "mixed",
+           "cg_rtol": 1e-6, "tuning": tuned, "autotune_ms_per_step": tuned_ms,
+           "sharding": {"ranks": world, "rule": "greedy largest-first by tets, no data-path collective",
+                        "meshes_rank0": len(ws) if rank == 0 else None}}
     per_mode = {}
     for graph in (1, 0):
         b.tuning_set(graph=graph, chunk=tuned["chunk"] if tuned["graph"] == 0 else 8, grid_budget=tuned["grid_budget"])
@@ -249,9 +256,13 @@ def run_batch(args, gf, torch, barrier, stream) -> dict:
         per_mode["graph" if graph else "stream"] = {"ms_per_step": ms_b, "gpu_launches": b.launch_count() - l0,
                                                     "cg_iters_mean": statistics.mean(iters)}
     b.tuning_set(graph=tuned["graph"], chunk=tuned["chunk"], grid_budget=tuned["grid_budget"])
-    best = per_mode["graph" if tuned["graph"] else "stream"]
-    out.update(ms_per_step=best["ms_per_step"], element_updates_per_s=out["n_tets_total"] / (best["ms_per_step"] * 1e-3),
-               modes=per_mode)
+    best_ms = per_mode["graph" if tuned["graph"] else "stream"]["ms_per_step"]
+    if dist is not None:   # the slowest rank's share sets the batch's step time
+        t = torch.tensor([best_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        best_ms = float(t[0])
+    out.update(ms_per_step=best_ms, element_updates_per_s=out["n_tets_total"] / (best_ms * 1e-3),
+               scaling="strong" if world > 1 else None, modes=per_mode)
     b.close()
     for m in meshes:
         m.close()
@@ -490,7 +501,7 @@ def run_ours(args) -> None:
     mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
     mix_ms, mix_launches, mix_prof, mix_it, mix_sw = timed(mm, args.steps)
     mm.close()
-    batch = run_batch(args, gf, torch, barrier, stream) if not args.no_batch else None
+    batch = run_batch(args, gf, torch, barrier, stream, world, rank, dist) if not args.no_batch else None
     learned = run_learned(args, gf, torch, barrier, stream, w, mat, f_dev) if not args.no_learned else None
     t_all = torch.tensor([ms, e2e_ms, mix_ms], dtype=torch.float64, device="cuda")
     if dist is not None:
