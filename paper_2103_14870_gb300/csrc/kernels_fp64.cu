@@ -62,17 +62,16 @@ __device__ __forceinline__ double edge_traction(const double e[3], const double 
 // Damage: stress, non-local average, edge driver + relabel, chi
 // ---------------------------------------------------------------------------
 
+// The tet's current edge vectors e_k, squared lengths s_k and second
+// Piola-Kirchhoff stress S (Voigt xx yy zz xy xz yz) from the positions x.
 template <bool kSNH>
-__device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-
-  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= m.T) return;
+__device__ __forceinline__ void tet_current_stress(const DevMesh& m, const Material& mt, int64_t t, double (&e)[6][3],
+                                                   double (&s)[6], double (&S)[6]) {
   const int4 n = m.tets[t];
   const int nid[4] = {n.x, n.y, n.z, n.w};
   double P[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a) ld3(m.x, nid[a], P[a]);
-  double e[6][3], s[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
 #pragma unroll
@@ -84,7 +83,6 @@ __device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material
   for (int f = 0; f < 9; ++f) B[f] = m.rest[(kRestB + f) * m.T + t];
   double C[6];
   cauchy_green(s, B, C);
-  double S[6];
   if constexpr (kSNH) {
     // Eq. 35: S = mu (1 - 1/(I_C + 1)) I + lam (J - a) J C^-1 = ... + lam (J - a) / J adj(C),
     // J = det F = det(Ds) det(B) (signed)
@@ -112,31 +110,23 @@ __device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material
     S[4] = mt.mu * C[4];
     S[5] = mt.mu * C[5];
   }
+}
+
+// Eq. 14 per tet: the stress fed to the Eq. 20 average (chi S, or S).  The
+// tet's own edge-normal stresses of Eq. 22-25 are formed in k_tet_chi, only for
+// the tets that have a broken edge (chi = 1 needs none of them).
+template <bool kSNH>
+__device__ __forceinline__ void tet_stress_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
+  double e[6][3], s[6], S[6];
+  tet_current_stress<kSNH>(m, mt, t, e, s, S);
   const double w = mt.average_degraded ? m.chi[t] : 1.0;
   double2* si = reinterpret_cast<double2*>(m.sig_in + 6 * t);
   si[0] = make_double2(w * S[0], w * S[1]);
   si[1] = make_double2(w * S[2], w * S[3]);
   si[2] = make_double2(w * S[4], w * S[5]);
-  // 1 / s_k of the six edges with one division (batch inversion: prefix
-  // products, one reciprocal, then back-substitution)
-  double pre[6], rs[6];
-  pre[0] = s[0];
-#pragma unroll
-  for (int k = 1; k < 6; ++k) pre[k] = pre[k - 1] * s[k];
-  double inv = 1.0 / pre[5];
-#pragma unroll
-  for (int k = 5; k > 0; --k) {
-    rs[k] = inv * pre[k - 1];
-    inv *= s[k];
-  }
-  rs[0] = inv;
-  double sf[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) sf[k] = edge_traction(e[k], S, mt.kappa) * rs[k];
-  double2* so = reinterpret_cast<double2*>(m.sigf + 6 * t);
-  so[0] = make_double2(sf[0], sf[1]);
-  so[1] = make_double2(sf[2], sf[3]);
-  so[2] = make_double2(sf[4], sf[5]);
 }
 __global__ void __launch_bounds__(kThreads) k_tet_stress(DevMesh m, Material mt, StepScalars sp) {
   tet_stress_body<false>(m, mt, sp, blockIdx.x, gridDim.x);
@@ -233,6 +223,10 @@ __global__ void __launch_bounds__(kThreads) kb_edge_driver(const BatchTab* __res
 }
 
 // Eq. 22-25: chi from the tet's broken-edge mask and its local edge stresses.
+// Eq. 22-25: chi from the tet's broken-edge mask and its local edge-normal
+// stresses sigma_f = (e.S.e)/|e|^2 of its own (un-averaged) stress, formed
+// here for the tets that have a broken edge and are not split apart.
+template <bool kSNH>
 __device__ __forceinline__ void tet_chi_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const uint64_t lut = mt.lut;
 
@@ -247,10 +241,12 @@ __device__ __forceinline__ void tet_chi_body(const DevMesh& m, const Material& m
       if ((lut >> mask) & 1ull) {
         c = 0.0;
       } else {
+        double e[6][3], s[6], S[6];
+        tet_current_stress<kSNH>(m, mt, t, e, s, S);
         double num = 0.0, den = 0.0;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const double a = fabs(m.sigf[6 * t + k]);
+          const double a = fabs(edge_traction(e[k], S, mt.kappa) / s[k]);
           den += a;
           if (!((mask >> k) & 1)) num += a;
         }
@@ -263,12 +259,15 @@ __device__ __forceinline__ void tet_chi_body(const DevMesh& m, const Material& m
   warp_count(zero, m.counters + kCntChiZero);
 }
 __global__ void __launch_bounds__(kThreads) k_tet_chi(DevMesh m, Material mt, StepScalars sp) {
-  tet_chi_body(m, mt, sp, blockIdx.x, gridDim.x);
+  tet_chi_body<false>(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) k_tet_chi_snh(DevMesh m, Material mt, StepScalars sp) {
+  tet_chi_body<true>(m, mt, sp, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kThreads) kb_tet_chi(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_tet_chi, blockIdx.x, bid, nb);
-  tet_chi_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+  tet_chi_body<false>(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);   // batches run the StVK energy
 }
 
 // ---------------------------------------------------------------------------
@@ -1270,7 +1269,10 @@ int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepS
       break;
     case kB_nonlocal: k_nonlocal<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_edge_driver: k_edge_driver<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_tet_chi: k_tet_chi<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_tet_chi:
+      if (mt.energy == GF_ENERGY_SNH) k_tet_chi_snh<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
+      else k_tet_chi<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
+      break;
     case kB_node_init: k_node_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_elem64:
       if (mt.energy == GF_ENERGY_SNH) k_elem_snh64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
