@@ -562,7 +562,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     MixDev& x = d.mx;
     if ((st = scratch(m, 3 * N, &x.u32)) || (st = scratch(m, 3 * N, &x.v32)) || (st = scratch(m, T, &x.chi32)) ||
         (st = scratch(m, 8 * T, &x.sig_in32)) || (st = scratch(m, 8 * T, &x.sig_bar32)) ||
-        (st = scratch(m, 6 * T, &x.sigf32)) || (st = scratch(m, 9 * NB, &x.val32)) ||
+        (st = scratch(m, 9 * NB, &x.val32)) ||
         (st = scratch(m, 104 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
         (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||

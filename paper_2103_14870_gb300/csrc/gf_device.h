@@ -56,7 +56,6 @@ struct MixDev {
   float* chi32 = nullptr;             // [T]
   float* sig_in32 = nullptr;          // [T][8] (6 used; 32-byte rows for single-sector gathers)
   float* sig_bar32 = nullptr;         // [T][8]
-  float* sigf32 = nullptr;            // [T][6]
   float* val32 = nullptr;             // [NB][9]
   float* ebuf = nullptr;              // [4T][12] node rows, then [6T][9] edge rows (two-phase assembly)
   float* rhs32 = nullptr;             // [3N]

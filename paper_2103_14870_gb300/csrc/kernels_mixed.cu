@@ -82,12 +82,11 @@ __device__ __forceinline__ float normal_stress32(const float e[3], float s, cons
 // damage (Eq. 14-25) in FP32, threshold test in FP64
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void tet_stress32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-  const float lam = mt.lam32, mu = mt.mu32, kappa = mt.kappa32;
-  const int avg = mt.average_degraded;
-
-  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= m.T) return;
+// The tet's current edge vectors e_k (from displacements) and its second
+// Piola-Kirchhoff stress S (Voigt xx yy zz xy xz yz), in FP32.
+__device__ __forceinline__ void tet_current_stress32(const DevMesh& m, const Material& mt, int64_t t, float (&e)[6][3],
+                                                     float (&S)[6]) {
+  const float lam = mt.lam32, mu = mt.mu32;
   const MixDev& x = m.mx;
   const int4 n = m.tets[t];
   const int nid[4] = {n.x, n.y, n.z, n.w};
@@ -96,7 +95,7 @@ __device__ __forceinline__ void tet_stress32_body(const DevMesh& m, const Materi
   for (int a = 0; a < 4; ++a) ld3f(x.u32, nid[a], du[a]);
   float A[32];
   load_restA(x.restA, t, A);
-  float E0[6][3], e[6][3], ds[6];
+  float E0[6][3], ds[6];
   rest_edges(A, E0);
   edge_state(E0, du, e, ds);
   float B[9];
@@ -126,16 +125,27 @@ __device__ __forceinline__ void tet_stress32_body(const DevMesh& m, const Materi
   for (int v = 0; v < 6; ++v)
     Eg[v] = 0.5f * (B[I[v]] * Y[0][J[v]] + B[3 + I[v]] * Y[1][J[v]] + B[6 + I[v]] * Y[2][J[v]]);
   const float tr = lam * (Eg[0] + Eg[1] + Eg[2]);
-  const float S[6] = {tr + 2.f * mu * Eg[0], tr + 2.f * mu * Eg[1], tr + 2.f * mu * Eg[2],
-                      2.f * mu * Eg[3], 2.f * mu * Eg[4], 2.f * mu * Eg[5]};
-  const float w = avg ? x.chi32[t] : 1.f;
+  S[0] = tr + 2.f * mu * Eg[0];
+  S[1] = tr + 2.f * mu * Eg[1];
+  S[2] = tr + 2.f * mu * Eg[2];
+  S[3] = 2.f * mu * Eg[3];
+  S[4] = 2.f * mu * Eg[4];
+  S[5] = 2.f * mu * Eg[5];
+}
+
+// Eq. 14 per tet: the stress fed to the Eq. 20 average (chi S, or S); the
+// edge-normal stresses of Eq. 22-25 are formed in k_tet_chi32, only for the
+// tets that have a broken edge.
+__device__ __forceinline__ void tet_stress32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m.T) return;
+  const MixDev& x = m.mx;
+  float e[6][3], S[6];
+  tet_current_stress32(m, mt, t, e, S);
+  const float w = mt.average_degraded ? x.chi32[t] : 1.f;
   float4* si = reinterpret_cast<float4*>(x.sig_in32 + 8 * t);
   si[0] = make_float4(w * S[0], w * S[1], w * S[2], w * S[3]);
   si[1] = make_float4(w * S[4], w * S[5], 0.f, 0.f);
-  float* sf = x.sigf32 + 6 * t;
-#pragma unroll
-  for (int k = 0; k < 6; ++k)
-    sf[k] = normal_stress32(e[k], e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2], S, kappa);
 }
 __global__ void __launch_bounds__(kThreads) k_tet_stress32(DevMesh m, Material mt, StepScalars sp) {
   tet_stress32_body(m, mt, sp, blockIdx.x, gridDim.x);
@@ -378,10 +388,13 @@ __device__ __forceinline__ void tet_chi32_body(const DevMesh& m, const Material&
       if ((lut >> mask) & 1ull) {
         c = 0.f;
       } else {
+        float e[6][3], S[6];
+        tet_current_stress32(m, mt, t, e, S);
         float num = 0.f, den = 0.f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const float a = fabsf(m.mx.sigf32[6 * t + k]);
+          const float a =
+              fabsf(normal_stress32(e[k], e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2], S, mt.kappa32));
           den += a;
           if (!((mask >> k) & 1)) num += a;
         }
