@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -1985,7 +1986,7 @@ gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out) {
       cudaMalloc(&b->dout, sizeof(BatchOut) * n) != cudaSuccess || cudaMalloc(&b->d_iter, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&b->h_iter, sizeof(int)) != cudaSuccess)
     return fail("allocation");
-  std::memset(b->htab, 0, sizeof(BatchTab));
+  new (b->htab) BatchTab();   // pinned host memory from cudaMallocHost: construct the table in place
   b->htab->n = n;
   std::vector<BatchInit> init(n);
   int maxit = 1;
