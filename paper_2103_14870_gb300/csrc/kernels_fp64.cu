@@ -570,14 +570,20 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
       us[a][c] = k3 * u[a][c];
       zs[a][c] = k4 * z[a][c];
     }
+  // Zero block-row sums (the energy depends on node differences only):
+  // K_aa = -sum_{b != a} K_ab, and (K v)_a = sum_{b != a} K_ab (v_b - v_a).  The
+  // six off-diagonal blocks are formed; the diagonal ones are summed from them
+  // in shared memory (entry-major, as in the StVK element).
+  __shared__ double s_diag[36][kElemThreads64];
+  double* sd = &s_diag[0][threadIdx.x];
   double Kv[4][3] = {};
 #pragma unroll
-  for (int b = 0; b < 4; ++b)
+  for (int b = 1; b < 4; ++b)
 #pragma unroll
-    for (int a = 0; a <= b; ++a) {
+    for (int a = 0; a < b; ++a) {
       const double gg = G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2];
-      double tm[3] = {0.0, 0.0, 0.0};
-      if (a != b) {
+      double tm[3];
+      {
         const double x0 = G[a][1] * G[b][2] - G[a][2] * G[b][1];
         const double x1 = G[a][2] * G[b][0] - G[a][0] * G[b][2];
         const double x2 = G[a][0] * G[b][1] - G[a][1] * G[b][0];
@@ -599,13 +605,32 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
       blk[2][0] += tm[1];
       blk[1][2] += tm[0];
       blk[2][1] -= tm[0];
+      const double du[3] = {U[b][0] - U[a][0], U[b][1] - U[a][1], U[b][2] - U[a][2]};
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        Kv[a][r] += blk[r][0] * U[b][0] + blk[r][1] * U[b][1] + blk[r][2] * U[b][2];
-        if (a != b) Kv[b][r] += blk[0][r] * U[a][0] + blk[1][r] * U[a][1] + blk[2][r] * U[a][2];
+        Kv[a][r] += blk[r][0] * du[0] + blk[r][1] * du[1] + blk[r][2] * du[2];
+        Kv[b][r] -= blk[0][r] * du[0] + blk[1][r] * du[1] + blk[2][r] * du[2];
       }
       out.block(a, b, blk);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double* pa = sd + kElemThreads64 * (9 * a + 3 * r + c);
+          double* pb = sd + kElemThreads64 * (9 * b + 3 * c + r);
+          *pa = (a == 0 && b == 1) ? blk[r][c] : *pa + blk[r][c];
+          *pb = (a == 0) ? blk[r][c] : *pb + blk[r][c];
+        }
     }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double blk[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) blk[r][c] = -sd[kElemThreads64 * (9 * a + 3 * r + c)];
+    out.block(a, a, blk);
+  }
   // rhs shares dt chi (f_a - (beta + dt) (K v)_a): the blocks carry (dt beta + dt^2) chi = dt chi (beta + dt),
   // so the damping/velocity term is the scaled blocks' K v itself
   const double sf = dt * chi * V;
