@@ -63,7 +63,8 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_edge_driver: case kB_edge_driver32: return {cdiv(NE, 256), 256};
     case kB_node_init: return {cdiv(N, 256), 256};
     case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
-    case kB_gather64: return {cdiv(9 * m.NE + 12 * N, 256), 256};
+    case kB_gather64: return {cdiv(9 * m.NE + 3 * N, 256), 256};
+    case kB_diag64: return {cdiv(9 * N, 256), 256};
     case kB_gather32: return {cdiv(9 * m.NE + 12 * N, 256), 256};
     case kB_pinv32: return {cdiv(N, 256), 256};
     case kB_set_pinned: return {cdiv(sp.n_pinned, 256), 256};
@@ -555,7 +556,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     return fail(st);
   if (!mixed) {
     if ((st = scratch(m, 6 * T, &d.sig_in)) || (st = scratch(m, 6 * T, &d.sig_bar)) ||
-        (st = scratch(m, 9 * NB, &d.val)) || (st = scratch(m, 104 * T, &d.ebuf)) ||
+        (st = scratch(m, 9 * NB, &d.val)) || (st = scratch(m, 70 * T, &d.ebuf)) ||
         (st = scratch(m, 3 * N, &d.r)) || (st = scratch(m, 3 * N, &d.z)) ||
         (st = scratch(m, 3 * N, &d.p)) || (st = scratch(m, 3 * N, &d.q)) || (st = scratch(m, 9 * N, &d.pinv)))
       return fail(st);
@@ -808,6 +809,7 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
     if (m->tune.assembly != GF_ASSEMBLY_COLOUR) {
       Prof p(m, kPGather);
       L += launch_kind(kB_gather64, d, mt, sp, s);
+      L += launch_kind(kB_diag64, d, mt, sp, s);
     }
     return GF_OK;
   };
@@ -982,7 +984,7 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
     if (!(mt.radius > 0.0)) d.sig_bar = d.sig_in;
     L += launch_kind(kB_tet_stress, d, mt, sp, s);
     if (mt.radius > 0.0) L += launch_kind(kB_nonlocal, d, mt, sp, s);
-    for (int kind : {kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64}) L += launch_kind(kind, d, mt, sp, s);
+    for (int kind : {kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64, kB_diag64}) L += launch_kind(kind, d, mt, sp, s);
     GF_CK(cudaMemcpyAsync(d.pcg, m->h_init, sizeof(PcgState), cudaMemcpyHostToDevice, s));
   }
   GF_CK(cudaMemsetAsync(d.pinned, 0, d.N, s));
@@ -1279,7 +1281,11 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
   const double c_armijo = 1e-4;
   for (k = 0; k < max_newton; ++k) {
     { Prof p(m, kPAssemble); L += launch_kind(kB_elem64, dq, mq, sq, s); }
-    { Prof p(m, kPGather); L += launch_kind(kB_gather64, dq, mq, sq, s); }
+    {
+      Prof p(m, kPGather);
+      L += launch_kind(kB_gather64, dq, mq, sq, s);
+      L += launch_kind(kB_diag64, dq, mq, sq, s);
+    }
     PcgState init{};
     init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
     init.maxit = m->opt.cg_maxit;
@@ -1727,7 +1733,7 @@ void batch_free(gf_batch* b) {
   if (b->body_stream) cudaStreamDestroy(b->body_stream);
 }
 
-const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64,
+const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64, kB_diag64,
                            kB_set_pinned, kB_pcg_init};
 const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
 const int kSuffixFp64[] = {kB_true_residual, kB_integrate};

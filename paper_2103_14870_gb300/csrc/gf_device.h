@@ -105,7 +105,7 @@ struct DevMesh {
   double* sig_bar = nullptr;           // [T][6] Eq. 20 averages
   double* sigf = nullptr;              // [T][6] local edge-normal stresses
   double* val = nullptr;               // [NB][9] system matrix A
-  double* ebuf = nullptr;              // [4T][12] node rows, then [6T][9] edge rows (two-phase assembly)
+  double* ebuf = nullptr;              // [4T][4] node rows (rhs), then [6T][9] edge rows (two-phase assembly)
   double* rhs = nullptr;               // [3N] b
   double* dv = nullptr;                // [3N] unknown
   double* r = nullptr;
@@ -158,8 +158,10 @@ constexpr int kTickets = 16;
 // off[kind][k+1]; inside, the kernel body sees that mesh's data and its local
 // block index and count (reductions and grid-stride loops stay per mesh).
 // ---------------------------------------------------------------------------
+// The FP64 kinds come first: every kind below kB_tet_stress32 is launched by
+// the FP64 dispatcher, every kind from it on by the mixed one.
 enum BatchKind : int {
-  kB_tet_stress = 0, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_node_init, kB_elem64, kB_gather64, kB_set_pinned,
+  kB_tet_stress = 0, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_node_init, kB_elem64, kB_gather64, kB_diag64, kB_set_pinned,
   kB_pcg_init, kB_pcg_spmv, kB_pcg_update, kB_pcg_p, kB_true_residual, kB_integrate,
   kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_fext32,
   kB_ir_residual, kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_integrate32, kB_refresh32,

@@ -437,21 +437,24 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
   }
 }
 
-// Two-phase FP64 assembly (no colours, no atomics, one launch per phase).
-// k_elem64 (thread per tet) computes the tet's ten upper-triangle blocks of
-// (dt beta + dt^2) chi k_e and its four rhs shares dt chi (f_a - (beta+dt)(k_e v)_a)
-// and writes each straight into the assembly row it belongs to: local node a's
-// diagonal block and rhs share to node row nrow[4t+a] (12 values), local edge
+// Two-phase FP64 assembly (no colours, no atomics).
+// k_elem64 (thread per tet) computes the six off-diagonal blocks of
+// (dt beta + dt^2) chi k_e and the four rhs shares dt chi (f_a - (beta+dt)(k_e v)_a)
+// and writes each straight into the assembly row it belongs to: local edge
 // k's block to edge row erow[6t+k] (9 values, oriented for the global edge
-// (i, j), i < j).  A node's or an edge's rows are contiguous, so k_gather64
+// (i, j), i < j), local node a's rhs share to node row nrow[4t+a] (3 values
+// and a pad).  A node's or an edge's rows are contiguous, so k_gather64
 // (thread per matrix entry or rhs component) streams through them in a fixed
-// order and adds mass, external force and mass damping.
-constexpr int kNodeRow = 12, kEdgeRow = 9;
-constexpr int kElemThreads64 = 128;   // threads per CTA of the element kernels (shared-memory sums)
+// order.  The element energy depends on node differences only, so every
+// block row of k_e sums to zero, and so does every block row of the assembled
+// stiffness: k_diag64 forms the diagonal blocks as minus the sum of their
+// row's off-diagonal blocks and adds the mass terms.
+constexpr int kNodeRow = 4, kEdgeRow = 9;
+constexpr int kElemThreads64 = 128;   // threads per CTA of the element kernels
 
 // where a tet's contributions go (the writes scatter; the gather reads stream)
 struct ElemRows64 {
-  double* nb;        // node rows [4T][12]
+  double* nb;        // node rows [4T][4]: rhs share, pad
   double* eb;        // edge rows [6T][9]
   const int32_t* nr; // nrow + 4t
   const int32_t* er; // erow + 6t
@@ -461,36 +464,27 @@ struct ElemRows64 {
 #pragma unroll
     for (int k = 0; k < 6; ++k) flip |= nid[edge_a(k)] > nid[edge_b(k)] ? (1u << k) : 0u;
   }
-  // block (a, b), a <= b, of the tet's matrix
+  // off-diagonal block (a, b), a < b, of the tet's matrix
   __device__ __forceinline__ void block(int a, int b, const double (&blk)[3][3]) const {
-    if (a == b) {
-      double* d = nb + int64_t(kNodeRow) * __ldg(nr + a);
+    const int k = a == 0 ? b - 1 : a + b;   // local edge of (a, b)
+    double* d = eb + int64_t(kEdgeRow) * __ldg(er + k);
+    const bool tr = (flip >> k) & 1u;
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) d[3 * r + c] = blk[r][c];
-    } else {
-      const int k = a == 0 ? b - 1 : a + b;   // local edge of (a, b)
-      double* d = eb + int64_t(kEdgeRow) * __ldg(er + k);
-      const bool tr = (flip >> k) & 1u;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) d[tr ? 3 * c + r : 3 * r + c] = blk[r][c];
-    }
+      for (int c = 0; c < 3; ++c) d[tr ? 3 * c + r : 3 * r + c] = blk[r][c];
   }
   __device__ __forceinline__ void rhs(int a, const double (&f)[3]) const {
-    double* d = nb + int64_t(kNodeRow) * __ldg(nr + a) + 9;
-    d[0] = f[0];
-    d[1] = f[1];
-    d[2] = f[2];
+    double2* d = reinterpret_cast<double2*>(nb + int64_t(kNodeRow) * __ldg(nr + a));
+    d[0] = make_double2(f[0], f[1]);
+    d[1] = make_double2(f[2], 0.0);
   }
   __device__ __forceinline__ void zero() const {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      double* d = nb + int64_t(kNodeRow) * __ldg(nr + a);
-#pragma unroll
-      for (int q = 0; q < kNodeRow; ++q) d[q] = 0.0;
+      double2* d = reinterpret_cast<double2*>(nb + int64_t(kNodeRow) * __ldg(nr + a));
+      d[0] = make_double2(0.0, 0.0);
+      d[1] = make_double2(0.0, 0.0);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -571,11 +565,8 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
       zs[a][c] = k4 * z[a][c];
     }
   // Zero block-row sums (the energy depends on node differences only):
-  // K_aa = -sum_{b != a} K_ab, and (K v)_a = sum_{b != a} K_ab (v_b - v_a).  The
-  // six off-diagonal blocks are formed; the diagonal ones are summed from them
-  // in shared memory (entry-major, as in the StVK element).
-  __shared__ double s_diag[36][kElemThreads64];
-  double* sd = &s_diag[0][threadIdx.x];
+  // (K v)_a = sum_{b != a} K_ab (v_b - v_a); only the six off-diagonal blocks
+  // are formed (k_diag64 forms the assembled diagonal blocks).
   double Kv[4][3] = {};
 #pragma unroll
   for (int b = 1; b < 4; ++b)
@@ -612,25 +603,7 @@ __device__ __forceinline__ void elem_snh64(const DevMesh& m, const Material& mt,
         Kv[b][r] -= blk[0][r] * du[0] + blk[1][r] * du[1] + blk[2][r] * du[2];
       }
       out.block(a, b, blk);
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          double* pa = sd + kElemThreads64 * (9 * a + 3 * r + c);
-          double* pb = sd + kElemThreads64 * (9 * b + 3 * c + r);
-          *pa = (a == 0 && b == 1) ? blk[r][c] : *pa + blk[r][c];
-          *pb = (a == 0) ? blk[r][c] : *pb + blk[r][c];
-        }
     }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    double blk[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) blk[r][c] = -sd[kElemThreads64 * (9 * a + 3 * r + c)];
-    out.block(a, a, blk);
-  }
   // rhs shares dt chi (f_a - (beta + dt) (K v)_a): the blocks carry (dt beta + dt^2) chi = dt chi (beta + dt),
   // so the damping/velocity term is the scaled blocks' K v itself
   const double sf = dt * chi * V;
@@ -657,12 +630,8 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
     return;
   }
   // The energy depends on node differences only, so every block row of the
-  // tet's tangent sums to zero: K_aa = -sum_{b != a} K_ab.  Only the six
-  // off-diagonal blocks are formed (Y for b = 1..3); the diagonal blocks are
-  // summed from them in shared memory (entry-major: consecutive threads,
-  // consecutive doubles), which saves Y_0 and four block products.
-  __shared__ double s_diag[36][kElemThreads64];
-  double* sd = &s_diag[0][threadIdx.x];
+  // tet's tangent sums to zero: only the six off-diagonal blocks are formed
+  // (Y for b = 1..3), and k_diag64 forms the assembled diagonal blocks.
   const int inc[4][3] = {{0, 1, 2}, {0, 3, 4}, {1, 3, 5}, {2, 4, 5}};
   const double sgn[4][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {1, 1, 1}};
   const int kab[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
@@ -746,26 +715,7 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
       blk[1][1] += geo;
       blk[2][2] += geo;
       out.block(a, b, blk);
-      // -K_aa collects K_ab (first: K_01), -K_bb collects K_ab^T (first: K_0b)
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          double* pa = sd + kElemThreads64 * (9 * a + 3 * r + c);
-          double* pb = sd + kElemThreads64 * (9 * b + 3 * c + r);
-          *pa = (a == 0 && b == 1) ? blk[r][c] : *pa + blk[r][c];
-          *pb = (a == 0) ? blk[r][c] : *pb + blk[r][c];
-        }
     }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    double blk[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) blk[r][c] = -sd[kElemThreads64 * (9 * a + 3 * r + c)];
-    out.block(a, a, blk);
   }
 }
 __device__ __forceinline__ void elem_snh64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid,
@@ -793,17 +743,15 @@ __global__ void __launch_bounds__(kElemThreads64) kb_elem64(const BatchTab* __re
   elem64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);   // batches run the StVK energy
 }
 
-// Phase 2 of the assembly: each matrix entry and rhs component is the sum, in
-// ascending tet order, of its element contributions (plus the mass term of
-// Eq. 2: lumped on the diagonal, or the consistent m_ij of Eq. 5 on every
-// block).  Threads [0, 9 NE) take one entry of an edge's block (the 4-6 tets
-// around the edge, rows contiguous) and write it to both (i, j) and, transposed,
-// (j, i); threads [9 NE, 9 NE + 12 N) take a node's nine diagonal entries and
-// three rhs components (the ~24 tets around the node).  Neighbouring threads
-// read neighbouring values, and sum lists of similar length.
+// Phase 2 of the assembly: each off-diagonal matrix entry and rhs component is
+// the sum, in ascending tet order, of its element contributions.  Threads
+// [0, 9 NE) take one entry of an edge's block (the 4-6 tets around the edge,
+// rows contiguous) and write it to both (i, j) and, transposed, (j, i);
+// threads [9 NE, 9 NE + 3 N) take a node's rhs components (the ~24 tets around
+// the node) and add the external force and mass damping of Eq. 2.
+// Neighbouring threads read neighbouring values and sum lists of similar length.
 __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const double dt = sp.dt, alpha = mt.alpha;
-  const double cm = (1.0 + dt * alpha) * sp.mscale;
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   const int64_t n_edge = 9 * m.NE;
   if (t < n_edge) {
@@ -811,30 +759,57 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
     const int q = int(t - 9 * e);
     const double acc = row_sum<8>(m.ebuf + int64_t(kNodeRow) * 4 * m.T + q, kEdgeRow, m.et_ptr[e], m.et_ptr[e + 1]);
     const int2 sl = m.edge_slot[e];
-    const bool dg = q == 0 || q == 4 || q == 8;
-    m.val[9 * int64_t(sl.x) + q] = (m.mass_blk && dg) ? acc + cm * m.mass_blk[sl.x] : acc;
-    m.val[9 * int64_t(sl.y) + 3 * (q % 3) + q / 3] = (m.mass_blk && dg) ? acc + cm * m.mass_blk[sl.y] : acc;
+    m.val[9 * int64_t(sl.x) + q] = acc;
+    m.val[9 * int64_t(sl.y) + 3 * (q % 3) + q / 3] = acc;
     return;
   }
   const int64_t u = t - n_edge;
-  if (u >= 12 * m.N) return;
-  const int64_t i = u / 12;
-  const int q = int(u - 12 * i);
-  const double acc = row_sum<8>(m.ebuf + q, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
-  const double mi = m.mass[i];
-  if (q < 9) {
-    const int slot = m.diag_blk[i];
-    m.val[9 * int64_t(slot) + q] = (q == 0 || q == 4 || q == 8) ? acc + cm * (m.mass_blk ? m.mass_blk[slot] : mi) : acc;
-  } else {
-    const int c3 = q - 9;
-    const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
-    double mv = mi * m.v[3 * i + c3];
-    if (m.mass_blk) {   // consistent mass: (M v)_i over the row
-      mv = 0.0;
-      for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) mv += m.mass_blk[b] * m.v[3 * int64_t(m.col[b]) + c3];
-    }
-    m.rhs[3 * i + c3] = acc + dt * ((f_ext ? f_ext[3 * i + c3] : 0.0) - alpha * mv);
+  if (u >= 3 * m.N) return;
+  const int64_t i = u / 3;
+  const int c3 = int(u - 3 * i);
+  const double acc = row_sum<8>(m.ebuf + c3, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
+  const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
+  double mv = m.mass[i] * m.v[3 * i + c3];
+  if (m.mass_blk) {   // consistent mass: (M v)_i over the row
+    mv = 0.0;
+    for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) mv += m.mass_blk[b] * m.v[3 * int64_t(m.col[b]) + c3];
   }
+  m.rhs[3 * i + c3] = acc + dt * ((f_ext ? f_ext[3 * i + c3] : 0.0) - alpha * mv);
+}
+
+// Phase 3: the diagonal blocks.  Every block row of the assembled stiffness
+// sums to zero (each element's does: its energy depends on node differences
+// only), so A_ii = -sum_{j != i} A_ij + the mass terms of Eq. 2 (lumped on the
+// diagonal, or the consistent m_ij of Eq. 5 on every block of the row, added
+// here after the sum).  Thread per (node, entry); a row's blocks are read in
+// order (deterministic) and only its own thread writes them.
+__device__ __forceinline__ void diag64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= 9 * m.N) return;
+  const int64_t i = t / 9;
+  const int q = int(t - 9 * i);
+  const int d = m.diag_blk[i], b0 = m.row_ptr[i], b1 = m.row_ptr[i + 1];
+  double acc = 0.0;
+  for (int b = b0; b < b1; ++b)
+    if (b != d) acc += m.val[9 * int64_t(b) + q];
+  double diag = -acc;
+  const bool dg = q == 0 || q == 4 || q == 8;
+  if (dg) {
+    const double cm = (1.0 + sp.dt * mt.alpha) * sp.mscale;
+    diag += cm * (m.mass_blk ? m.mass_blk[d] : m.mass[i]);
+    if (m.mass_blk)
+      for (int b = b0; b < b1; ++b)
+        if (b != d) m.val[9 * int64_t(b) + q] += cm * m.mass_blk[b];
+  }
+  m.val[9 * int64_t(d) + q] = diag;
+}
+__global__ void __launch_bounds__(256) k_diag64(DevMesh m, Material mt, StepScalars sp) {
+  diag64_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256) kb_diag64(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_diag64, blockIdx.x, bid, nb);
+  diag64_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 __global__ void __launch_bounds__(256) k_gather64(DevMesh m, Material mt, StepScalars sp) {
   gather64_body(m, mt, sp, blockIdx.x, gridDim.x);
@@ -1304,6 +1279,7 @@ int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepS
       else k_elem64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp);
       break;
     case kB_gather64: k_gather64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_diag64: k_diag64<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_set_pinned: k_set_pinned<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_pcg_init: k_pcg_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_pcg_spmv: k_pcg_spmv<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
@@ -1326,6 +1302,7 @@ int launch_batch_fp64(int kind, const BatchTab* tab, unsigned blocks, unsigned t
     case kB_node_init: kb_node_init<<<blocks, threads, 0, s>>>(tab); break;
     case kB_elem64: kb_elem64<<<blocks, threads, 0, s>>>(tab); break;
     case kB_gather64: kb_gather64<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_diag64: kb_diag64<<<blocks, threads, 0, s>>>(tab); break;
     case kB_set_pinned: kb_set_pinned<<<blocks, threads, 0, s>>>(tab); break;
     case kB_pcg_init: kb_pcg_init<<<blocks, threads, 0, s>>>(tab); break;
     case kB_pcg_spmv: kb_pcg_spmv<<<blocks, threads, 0, s>>>(tab); break;
