@@ -65,7 +65,8 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
     case kB_gather64: return {cdiv(9 * m.NE + 3 * N, 256), 256};
     case kB_diag64: return {cdiv(9 * N, 256), 256};
-    case kB_gather32: return {cdiv(9 * m.NE + 12 * N, 256), 256};
+    case kB_gather32: return {cdiv(9 * m.NE + 3 * N, 256), 256};
+    case kB_diag32: return {cdiv(9 * N, 256), 256};
     case kB_pinv32: return {cdiv(N, 256), 256};
     case kB_set_pinned: return {cdiv(sp.n_pinned, 256), 256};
     case kB_pcg_init: case kB_pcg_spmv: case kB_pcg_update: case kB_true_residual: return {red_grid(N), 256};
@@ -565,7 +566,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     if ((st = scratch(m, 3 * N, &x.u32)) || (st = scratch(m, 3 * N, &x.v32)) || (st = scratch(m, T, &x.chi32)) ||
         (st = scratch(m, 8 * T, &x.sig_in32)) || (st = scratch(m, 8 * T, &x.sig_bar32)) ||
         (st = scratch(m, 9 * NB, &x.val32)) ||
-        (st = scratch(m, 104 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
+        (st = scratch(m, 70 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
         (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
         (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
@@ -904,6 +905,7 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   {
     Prof p(m, kPGather);
     L += launch_kind(kB_gather32, d, mt, sp, s);
+    L += launch_kind(kB_diag32, d, mt, sp, s);
     L += launch_kind(kB_pinv32, d, mt, sp, s);
   }
   IrState init{};
@@ -977,7 +979,7 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
     if (!(mt.radius > 0.0)) d.mx.sig_bar32 = d.mx.sig_in32;
     L += launch_kind(kB_tet_stress32, d, mt, sp, s);
     if (mt.radius > 0.0) L += launch_kind(kB_nonlocal32, d, mt, sp, s);
-    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32, kB_gather32, kB_pinv32})
+    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32, kB_gather32, kB_diag32, kB_pinv32})
       L += launch_kind(kind, d, mt, sp, s);
     GF_CK(cudaMemcpyAsync(d.mx.ir, m->h_init, sizeof(IrState), cudaMemcpyHostToDevice, s));
   } else {
@@ -1738,7 +1740,7 @@ const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_ch
 const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
 const int kSuffixFp64[] = {kB_true_residual, kB_integrate};
 const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32,
-                            kB_gather32, kB_pinv32, kB_set_pinned, kB_refresh32};
+                            kB_gather32, kB_diag32, kB_pinv32, kB_set_pinned, kB_refresh32};
 const int kBodyMixed[] = {kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_ir_residual};
 const int kSuffixMixed[] = {kB_integrate32};
 

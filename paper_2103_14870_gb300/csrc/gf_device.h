@@ -57,7 +57,7 @@ struct MixDev {
   float* sig_in32 = nullptr;          // [T][8] (6 used; 32-byte rows for single-sector gathers)
   float* sig_bar32 = nullptr;         // [T][8]
   float* val32 = nullptr;             // [NB][9]
-  float* ebuf = nullptr;              // [4T][12] node rows, then [6T][9] edge rows (two-phase assembly)
+  float* ebuf = nullptr;              // [4T][4] node rows (rhs), then [6T][9] edge rows (two-phase assembly)
   float* rhs32 = nullptr;             // [3N]
   float* rres = nullptr;              // [3N] leading float of the refinement residual
   float* fext32 = nullptr;            // [3N]
@@ -165,7 +165,7 @@ enum BatchKind : int {
   kB_pcg_init, kB_pcg_spmv, kB_pcg_update, kB_pcg_p, kB_true_residual, kB_integrate,
   kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_fext32,
   kB_ir_residual, kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_integrate32, kB_refresh32,
-  kB_chi_to32, kB_pinv32, kB_step_begin, kBKinds
+  kB_chi_to32, kB_pinv32, kB_diag32, kB_step_begin, kBKinds
 };
 constexpr int kMaxBatch = 256;
 

@@ -418,25 +418,28 @@ __global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restr
 
 // ---------------------------------------------------------------------------
 // Two-phase assembly, no colours and no atomics.
-// Phase 1 (k_elem32, one thread per tet): the tet's ten upper-triangle 3x3
-// blocks (a <= b) of (dt beta + dt^2) chi k_e and its four nodal rhs shares
+// Phase 1 (k_elem32, one thread per tet): the tet's six off-diagonal 3x3
+// blocks (a < b) of (dt beta + dt^2) chi k_e and its four nodal rhs shares
 // dt chi (f_a - (beta + dt) (k_e v)_a), built in a shared-memory row of
 // kElemW floats, then written by the CTA into the assembly rows they belong
-// to: local node a's diagonal block and rhs share to node row nrow[4t+a] (12
-// floats), local edge k's block to edge row erow[6t+k] (9 floats, oriented for
-// the global edge (i, j), i < j).
-// Phase 2 (k_gather32): a thread per matrix entry or rhs component streams
-// through the contiguous rows of its edge or node in ascending tet order and
-// adds the mass, external and damping terms; k_pinv32 then inverts the
-// diagonal blocks (block Jacobi).
+// to: local node a's rhs share to node row nrow[4t+a] (3 floats and a pad),
+// local edge k's block to edge row erow[6t+k] (9 floats, oriented for the
+// global edge (i, j), i < j).
+// Phase 2 (k_gather32): a thread per off-diagonal matrix entry or rhs
+// component streams through the contiguous rows of its edge or node in
+// ascending tet order and adds the external and damping terms.
+// Phase 3 (k_diag32): the diagonal blocks as minus the sum of their row's
+// off-diagonal blocks (every block row of the stiffness sums to zero) plus
+// the mass; k_pinv32 then inverts them (block Jacobi).
 // ---------------------------------------------------------------------------
 
 constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad
-constexpr int kNodeRow = 12, kEdgeRow = 9;
+constexpr int kNodeRow = 4, kEdgeRow = 9;
 // Each thread's row is built in shared memory (stride 105 floats: conflict-free
-// for 32 consecutive threads); each warp then writes its 32 rows out, the node
-// rows as 16-byte stores and the edge rows as runs of 9 consecutive floats,
-// with the destination rows passed between lanes by shuffles.
+// for 32 consecutive threads; the four diagonal block slots stay unused); each
+// warp then writes its 32 rows out, the node rows as one 16-byte store each and
+// the edge rows as runs of 9 consecutive floats, with the destination rows
+// passed between lanes by shuffles.
 constexpr int kElemThreads = 128, kElemSS = kElemW + 1;
 constexpr unsigned kElemSmem = kElemThreads * kElemSS * 4;
 
@@ -473,9 +476,11 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
     g[k] = s;
   }
   // Y_b[k][c] = sum_{l in b} H_kl sgn_lb e_l[c]  (sgn = -1 if b is the first node of l)
+  // only the off-diagonal blocks (a < b): the block rows sum to zero, and
+  // k_diag32 forms the assembled diagonal blocks
   float Kv[4][3] = {};
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
+  for (int b = 1; b < 4; ++b) {
     float Y[6][3];
 #pragma unroll
     for (int k = 0; k < 6; ++k)
@@ -490,7 +495,7 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
         Y[k][c] = y;
       }
 #pragma unroll
-    for (int a = 0; a <= b; ++a) {
+    for (int a = 0; a < b; ++a) {
       float blk[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -572,26 +577,14 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
   const int nw = rem < 32 ? int(rem) : 32;   // live rows of this warp (the whole warp agrees)
   if (nw <= 0) return;
   const float* wrows = sh_rows + wbase * kElemSS;
-  // node rows: 3 float4 each (diagonal block of node a, then its rhs share)
+  // node rows: one float4 each (the rhs share of node a and a pad); lane r
+  // writes its own row's four node rows
   float4* nbuf = reinterpret_cast<float4*>(x.ebuf);
+  if (lane < nw) {
+    const float* src = wrows + lane * kElemSS;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int db = 9 * blk_q(a, a);
-#pragma unroll
-    for (int j = lane; j < 96; j += 32) {
-      const int r = j / 3, part = j - 3 * r;
-      const int32_t row = __shfl_sync(0xffffffffu, nr[a], r);
-      if (r < nw) {
-        const float* src = wrows + r * kElemSS;
-        float v[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int q = 4 * part + c;
-          v[c] = q < 9 ? src[db + q] : src[90 + 3 * a + q - 9];
-        }
-        nbuf[3 * int64_t(row) + part] = make_float4(v[0], v[1], v[2], v[3]);
-      }
-    }
+    for (int a = 0; a < 4; ++a)
+      nbuf[nr[a]] = make_float4(src[90 + 3 * a], src[90 + 3 * a + 1], src[90 + 3 * a + 2], 0.f);
   }
   // edge rows: 9 consecutive floats each, transposed where the global order flips the edge
   float* ebuf = x.ebuf + int64_t(kNodeRow) * 4 * m.T;
@@ -619,11 +612,11 @@ __global__ void __launch_bounds__(128) kb_elem32(const BatchTab* __restrict__ ta
 
 // Phase 2 in the layout of the FP64 gather: threads [0, 9 NE) take one entry
 // of an edge's block (the 4-6 tets around the edge, rows contiguous) and write
-// it to (i, j) and, transposed, (j, i); threads [9 NE, 9 NE + 12 N) take a
-// node's nine diagonal entries (with the mass) and three rhs components (the
-// ~24 tets around the node).  Sums run in ascending tet order (deterministic).
+// it to (i, j) and, transposed, (j, i); threads [9 NE, 9 NE + 3 N) take a
+// node's rhs components (the ~24 tets around the node).  Sums run in
+// ascending tet order (deterministic).
 __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-  const float dtf = sp.dtf, alphaf = sp.alphaf, cmf = sp.cmf;
+  const float dtf = sp.dtf, alphaf = sp.alphaf;
   const MixDev& x = m.mx;
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   const int64_t n_edge = 9 * m.NE;
@@ -632,31 +625,54 @@ __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& 
     const int q = int(t - 9 * e);
     const float acc = row_sum<8>(x.ebuf + int64_t(kNodeRow) * 4 * m.T + q, kEdgeRow, m.et_ptr[e], m.et_ptr[e + 1]);
     const int2 sl = m.edge_slot[e];
-    const bool dg = q == 0 || q == 4 || q == 8;
-    x.val32[9 * int64_t(sl.x) + q] = (x.mass_blk32 && dg) ? acc + cmf * x.mass_blk32[sl.x] : acc;   // Eq. 5
-    x.val32[9 * int64_t(sl.y) + 3 * (q % 3) + q / 3] = (x.mass_blk32 && dg) ? acc + cmf * x.mass_blk32[sl.y] : acc;
+    x.val32[9 * int64_t(sl.x) + q] = acc;
+    x.val32[9 * int64_t(sl.y) + 3 * (q % 3) + q / 3] = acc;
     return;
   }
   const int64_t u = t - n_edge;
-  if (u >= 12 * m.N) return;
-  const int64_t i = u / 12;
-  const int q = int(u - 12 * i);
-  const float acc = row_sum<8>(x.ebuf + q, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
-  const float mi = x.mass32[i];
-  if (q < 9) {
-    const int slot = m.diag_blk[i];
-    x.val32[9 * int64_t(slot) + q] =
-        (q == 0 || q == 4 || q == 8) ? acc + cmf * (x.mass_blk32 ? x.mass_blk32[slot] : mi) : acc;
-  } else {
-    const int c3 = q - 9;
-    const float fe = sp.has_fext ? x.fext32[3 * i + c3] : 0.f;
-    float mv = mi * x.v32[3 * i + c3];
-    if (x.mass_blk32) {
-      mv = 0.f;
-      for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) mv += x.mass_blk32[b] * x.v32[3 * int64_t(m.col[b]) + c3];
-    }
-    x.rhs32[3 * i + c3] = acc + dtf * (fe - alphaf * mv);
+  if (u >= 3 * m.N) return;
+  const int64_t i = u / 3;
+  const int c3 = int(u - 3 * i);
+  const float acc = row_sum<8>(x.ebuf + c3, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
+  const float fe = sp.has_fext ? x.fext32[3 * i + c3] : 0.f;
+  float mv = x.mass32[i] * x.v32[3 * i + c3];
+  if (x.mass_blk32) {
+    mv = 0.f;
+    for (int b = m.row_ptr[i]; b < m.row_ptr[i + 1]; ++b) mv += x.mass_blk32[b] * x.v32[3 * int64_t(m.col[b]) + c3];
   }
+  x.rhs32[3 * i + c3] = acc + dtf * (fe - alphaf * mv);
+}
+
+// Phase 3: A_ii = -sum_{j != i} A_ij (zero block-row sums of the stiffness)
+// plus the mass (lumped on the diagonal, or the consistent m_ij of Eq. 5 on
+// every block of the row, added after the sum).  Thread per (node, entry).
+__device__ __forceinline__ void diag32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  const MixDev& x = m.mx;
+  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= 9 * m.N) return;
+  const int64_t i = t / 9;
+  const int q = int(t - 9 * i);
+  const int d = m.diag_blk[i], b0 = m.row_ptr[i], b1 = m.row_ptr[i + 1];
+  float acc = 0.f;
+  for (int b = b0; b < b1; ++b)
+    if (b != d) acc += x.val32[9 * int64_t(b) + q];
+  float diag = -acc;
+  if (q == 0 || q == 4 || q == 8) {
+    const float cmf = sp.cmf;
+    diag += cmf * (x.mass_blk32 ? x.mass_blk32[d] : x.mass32[i]);
+    if (x.mass_blk32)
+      for (int b = b0; b < b1; ++b)
+        if (b != d) x.val32[9 * int64_t(b) + q] += cmf * x.mass_blk32[b];   // Eq. 5
+  }
+  x.val32[9 * int64_t(d) + q] = diag;
+}
+__global__ void __launch_bounds__(256) k_diag32(DevMesh m, Material mt, StepScalars sp) {
+  diag32_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256) kb_diag32(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_diag32, blockIdx.x, bid, nb);
+  diag32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // block-Jacobi inverse of every node's assembled diagonal block (FP32)
@@ -1207,6 +1223,7 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
       k_elem32<<<d.blocks, d.threads, kElemSmem, s>>>(m, mt, sp);
       break;
     case kB_gather32: k_gather32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_diag32: k_diag32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_pinv32: k_pinv32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_fext32: k_fext32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_residual: k_ir_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp, first); break;
@@ -1235,6 +1252,7 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
       kb_elem32<<<blocks, threads, kElemSmem, s>>>(tab);
       break;
     case kB_gather32: kb_gather32<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_diag32: kb_diag32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_pinv32: kb_pinv32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_fext32: kb_fext32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_residual: kb_ir_residual<<<blocks, threads, 0, s>>>(tab, first); break;
