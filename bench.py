@@ -84,28 +84,28 @@ MIXED_BYTES = {
     "m:nonlocal_avg": lambda i: 6.1 * i["n_nbr_pairs"] + i["n_tets"] * (4 + 32 + 32),
     "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
     # phase 1: tet, rest row (128 B), chi, its ten row indices in; 6 edge rows
-    # (36 B) + 4 node rows (48 B) out; u, v and the external force per node
-    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 40 + 408) + i["n_nodes"] * (24 + 24),
-    # phase 2: every row once (408 B per tet); per edge its row pointer and two
-    # slots; per node pointers, mass, v, f_ext, rhs; A once; the block-Jacobi
-    # inverse reads the diagonal blocks and writes D^-1
-    "m:assemble_gather": lambda i: i["n_tets"] * 408 + i["n_edges"] * (4 + 8) + i["n_blocks"] * 36
-                                   + i["n_nodes"] * (4 + 4 + 4 + 12 + 12 + 12 + 36 + 36),
+    # (36 B) + 4 node rows (16 B) out; u, v and the external force per node
+    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 40 + 280) + i["n_nodes"] * (24 + 24),
+    # phases 2 and 3: every row once (280 B per tet); per edge its row pointer
+    # and two slots; the off-diagonal blocks written, then read back for the
+    # diagonal sums; per node pointers, mass, v, f_ext, rhs and the diagonal
+    # block; the block-Jacobi inverse reads the diagonal blocks and writes D^-1
+    "m:assemble_gather": lambda i: i["n_tets"] * 280 + i["n_edges"] * (4 + 8) + i["n_blocks"] * (36 + 36)
+                                   + i["n_nodes"] * (4 + 4 + 4 + 12 + 12 + 12 + 36 + 36 + 36),
     "m:pcg_spmv": lambda i: i["n_blocks"] * 40 + i["n_nodes"] * (4 + 12 + 12 + 12),
 }
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # loaf kernels, from ncu captures of the current kernels
-# (``bench.py --profile-step --precision fp64|mixed --steps 2``); the two
-# assembly groups list their main kernel (k_elem64 / k_gather64, k_elem32 /
-# k_gather32).
+# (``bench.py --profile-step --precision fp64|mixed --steps 2``); the gather
+# groups add their diagonal kernel (k_gather64 + k_diag64, k_gather32 + k_diag32).
 NCU_TRAFFIC = {
     "nonlocal_avg": 1.236900864e9 + 30.863872e6,
-    "assemble": 234.703360e6 + 499.401728e6,
-    "assemble_gather": 530.260736e6 + 118.412544e6,
+    "assemble": 180.427008e6 + 287.742976e6,
+    "assemble_gather": (367.732224e6 + 107.057152e6) + (117.284608e6 + 1.588224e6),
     "m:nonlocal_avg": 662.371328e6 + 20.333568e6,
-    "m:assemble": 122.624256e6 + 195.889408e6,
-    "m:assemble_gather": 274.354944e6 + 59.933696e6,
+    "m:assemble": 123.677184e6 + 116.235264e6,
+    "m:assemble_gather": (191.055360e6 + 42.795520e6) + (59.088640e6 + 1.280e3),
 }
 # Executed FP64 flops per tet of the element-block kernel (ncu: 2 DFMA + DADD +
 # DMUL thread instructions per launch / tets): the tangent has no short closed count.
@@ -129,12 +129,15 @@ def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, tra
                 "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": group,
                 "work_per_launch": {"fp64_flop": flops}, "peak_kind": "FP64 derived: 152 SM x 4 flop/clk x 2.07 GHz"}
     if group == "assemble_gather":
-        # phase 2: every FP64 row once (102 values per tet), per edge its row
-        # pointer and two slots, per node pointers, mass, v, f_ext and rhs, A once
-        bytes_per = T * 816 + info["n_edges"] * (4 + 8) + NB * 72 + N * (4 + 4 + 8 + 24 + 24 + 24)
+        # phases 2 and 3: every FP64 row once (70 values per tet), per edge its
+        # row pointer and two slots, the off-diagonal blocks written and read
+        # back for the diagonal sums, per node pointers, mass, v, f_ext, rhs and
+        # the diagonal block
+        bytes_per = T * 560 + info["n_edges"] * (4 + 8) + NB * (72 + 72) + N * (4 + 4 + 8 + 24 + 24 + 24 + 72)
         gbs = bytes_per / t / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
-                "traffic": traffic, "kernel": group, "work_per_launch": {"bytes": bytes_per, "fp64_flop": 102.0 * T},
+                "traffic": traffic, "kernel": group,
+                "work_per_launch": {"bytes": bytes_per, "fp64_flop": 66.0 * T + 126.0 * N},
                 "peak_kind": "measured HBM copy bandwidth"}
     if group == "pcg_spmv":
         flops = 18.0 * NB
