@@ -107,9 +107,11 @@ NCU_TRAFFIC = {
     "m:assemble": 123.677184e6 + 116.235264e6,
     "m:assemble_gather": (191.055360e6 + 42.795520e6) + (59.088640e6 + 1.280e3),
 }
-# Executed FP64 flops per tet of the element-block kernel (ncu: 2 DFMA + DADD +
-# DMUL thread instructions per launch / tets): the tangent has no short closed count.
-ELEM64_FLOPS_PER_TET = 1405.0
+# Executed FP64 flops per tet of the element-block kernel, off-diagonal blocks
+# and rhs shares only (ncu: 2 DFMA + DADD + DMUL thread instructions per launch /
+# tets = (2 x 264.4 M + 53.3 M + 55.7 M) / 619,300): the tangent has no short
+# closed count.
+ELEM64_FLOPS_PER_TET = 1030.0
 
 
 def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, traffic=None):
