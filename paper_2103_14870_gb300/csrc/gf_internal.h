@@ -78,13 +78,6 @@ struct MixedHost {
 
 gf_status build_mixed_host(const double* X, const struct HostMesh& hm, MixedHost& mx, std::string& err);
 
-// Upper-triangle block order of a tet's 4x4 node blocks: q -> (a, b), a <= b.
-GF_HD constexpr int blk_a(int q) { return q < 4 ? 0 : (q < 7 ? 1 : (q < 9 ? 2 : 3)); }
-GF_HD constexpr int blk_b(int q) { return q < 4 ? q : (q < 7 ? q - 3 : (q < 9 ? q - 5 : 3)); }
-GF_HD constexpr int blk_q(int a, int b) {   // a <= b
-  return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
-}
-
 // Everything mesh_create computes on the host before upload.
 struct HostMesh {
   int64_t n_nodes = 0, n_tets = 0, n_edges = 0, n_blocks = 0;

@@ -433,17 +433,17 @@ __global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restr
 // the mass; k_pinv32 then inverts them (block Jacobi).
 // ---------------------------------------------------------------------------
 
-constexpr int kElemW = 104;   // 90 block floats + 12 rhs floats + 2 pad
+constexpr int kElemW = 68;   // 54 block floats + 12 rhs floats + 2 pad
 constexpr int kNodeRow = 4, kEdgeRow = 9;
-// Each thread's row is built in shared memory (stride 105 floats: conflict-free
-// for 32 consecutive threads; the four diagonal block slots stay unused); each
-// warp then writes its 32 rows out, the node rows as one 16-byte store each and
+// Each thread's row is built in shared memory (stride 69 floats: conflict-free
+// for 32 consecutive threads); each warp then writes its 32 rows out, the node rows as one 16-byte store each and
 // the edge rows as runs of 9 consecutive floats, with the destination rows
 // passed between lanes by shuffles.
 constexpr int kElemThreads = 128, kElemSS = kElemW + 1;
 constexpr unsigned kElemSmem = kElemThreads * kElemSS * 4;
 
-// one tet's row: ten upper 3x3 blocks (scaled), four rhs shares, two zeros
+// one tet's row: the six off-diagonal 3x3 blocks (scaled; local edge k's block
+// at 9 k), four rhs shares, two zeros
 __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& sp, int64_t t, float* o) {
   const float sKv = sp.sKv, cv = sp.cv, dtf = sp.dtf;
   const MixDev& x = m.mx;
@@ -528,7 +528,7 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
           Kv[b][r] += blk[0][r] * (vv[a][0] - vv[b][0]) + blk[1][r] * (vv[a][1] - vv[b][1]) +
                       blk[2][r] * (vv[a][2] - vv[b][2]);
       }
-      const int q = blk_q(a, b);
+      const int q = a == 0 ? b - 1 : a + b;   // local edge of (a, b)
       const float sk = sKv * chi;
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -547,10 +547,10 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
         if (edge_a(k) == a) f += 2.f * g[k] * e[k][r];
         if (edge_b(k) == a) f -= 2.f * g[k] * e[k][r];
       }
-      o[90 + 3 * a + r] = dtf * chi * (f - cv * Kv[a][r]);
+      o[54 + 3 * a + r] = dtf * chi * (f - cv * Kv[a][r]);
     }
-  o[102] = 0.f;
-  o[103] = 0.f;
+  o[66] = 0.f;
+  o[67] = 0.f;
 }
 __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   extern __shared__ float sh_rows[];
@@ -584,13 +584,13 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
     const float* src = wrows + lane * kElemSS;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
-      nbuf[nr[a]] = make_float4(src[90 + 3 * a], src[90 + 3 * a + 1], src[90 + 3 * a + 2], 0.f);
+      nbuf[nr[a]] = make_float4(src[54 + 3 * a], src[54 + 3 * a + 1], src[54 + 3 * a + 2], 0.f);
   }
   // edge rows: 9 consecutive floats each, transposed where the global order flips the edge
   float* ebuf = x.ebuf + int64_t(kNodeRow) * 4 * m.T;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const int bq = 9 * blk_q(edge_a(k), edge_b(k));
+    const int bq = 9 * k;
 #pragma unroll
     for (int j = lane; j < 288; j += 32) {
       const int r = j / 9, q = j - 9 * r;
@@ -601,10 +601,10 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
   }
 }
 
-__global__ void __launch_bounds__(128) k_elem32(DevMesh m, Material mt, StepScalars sp) {
+__global__ void __launch_bounds__(128, 6) k_elem32(DevMesh m, Material mt, StepScalars sp) {
   elem32_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
-__global__ void __launch_bounds__(128) kb_elem32(const BatchTab* __restrict__ tab) {
+__global__ void __launch_bounds__(128, 6) kb_elem32(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_elem32, blockIdx.x, bid, nb);
   elem32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
