@@ -12,8 +12,22 @@ namespace gf {
 // `src` must not be written during the kernel.
 template <int B, typename T>
 __device__ __forceinline__ T row_sum(const T* __restrict__ src, int stride, int r0, int r1) {
-  T acc = T(0);
-  for (int r = r0; r < r1; r += B) {
+  if (r0 >= r1) return T(0);
+  // the sum starts from the first row (0 + x would cost an add on a pipe that
+  // binds the FP64 gathers); later batches add in row order as before
+  T acc;
+  {
+    T v[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) v[k] = r0 + k < r1 ? __ldg(src + int64_t(stride) * (r0 + k)) : T(0);
+    acc = v[0];
+#pragma unroll
+    for (int k = 1; k < B; ++k) {
+      if (r0 + k >= r1) break;
+      acc += v[k];
+    }
+  }
+  for (int r = r0 + B; r < r1; r += B) {
     T v[B];
 #pragma unroll
     for (int k = 0; k < B; ++k) v[k] = r + k < r1 ? __ldg(src + int64_t(stride) * (r + k)) : T(0);

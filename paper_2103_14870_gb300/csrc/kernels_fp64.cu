@@ -192,14 +192,18 @@ __device__ __forceinline__ void edge_driver_body(const DevMesh& m, const Materia
     ld3(m.x, ab.y, pb);
     const double e[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
     const double s = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    // e.S.e = sum_v w_v S_v with the edge's weights w (the shear ones carry
+    // kappa), formed once per edge: one DMUL and five DFMA per incident tet
+    const double w[6] = {e[0] * e[0], e[1] * e[1], e[2] * e[2], mt.kappa * (e[0] * e[1]), mt.kappa * (e[0] * e[2]),
+                         mt.kappa * (e[1] * e[2])};
     // max over the incident tets of (e.S.e) / s: s > 0 and rounded division is
     // monotone, so dividing the largest numerator once gives the same value
     double mq = -INFINITY;
     for (int p = m.et_ptr[i]; p < m.et_ptr[i + 1]; ++p) {
       const double2* sb = reinterpret_cast<const double2*>(m.sig_bar + 6 * int64_t(m.et_tet[p]));
       const double2 a = sb[0], b = sb[1], c = sb[2];
-      const double S[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
-      mq = fmax(mq, edge_traction(e, S, mt.kappa));
+      const double q = fma(w[5], c.y, fma(w[4], c.x, fma(w[3], b.y, fma(w[2], b.x, fma(w[1], a.y, w[0] * a.x)))));
+      mq = fmax(mq, q);
     }
     const double mx = mq / s;
     const double d = mt.driver_stress ? mx : mx / mt.young;
@@ -222,7 +226,6 @@ __global__ void __launch_bounds__(kThreads) kb_edge_driver(const BatchTab* __res
   edge_driver_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-// Eq. 22-25: chi from the tet's broken-edge mask and its local edge stresses.
 // Eq. 22-25: chi from the tet's broken-edge mask and its local edge-normal
 // stresses sigma_f = (e.S.e)/|e|^2 of its own (un-averaged) stress, formed
 // here for the tets that have a broken edge and are not split apart.
@@ -794,8 +797,11 @@ __device__ __forceinline__ void diag64_body(const DevMesh& m, const Material& mt
   const int64_t i = t / 9;
   const int q = int(t - 9 * i);
   const int d = m.diag_blk[i], b0 = m.row_ptr[i], b1 = m.row_ptr[i + 1];
-  double acc = 0.0;
-  for (int b = b0; b < b1; ++b)
+  // the sum starts from the row's first off-diagonal block (none for a node
+  // outside every tet)
+  const int bf = b0 == d ? b0 + 1 : b0;
+  double acc = bf < b1 ? m.val[9 * int64_t(bf) + q] : 0.0;
+  for (int b = bf + 1; b < b1; ++b)
     if (b != d) acc += m.val[9 * int64_t(b) + q];
   double diag = -acc;
   const bool dg = q == 0 || q == 4 || q == 8;
