@@ -170,6 +170,7 @@ struct gf_mesh {
   double* qs_x = nullptr;     // quasi-static: trial positions [3N]
   double* qs_zero = nullptr;  // quasi-static: zero velocities [3N]
   double* qs_out = nullptr;   // quasi-static: E, |E| scale, slope [4]
+  double* qs_w = nullptr;     // quasi-static: A z of the Chronopoulos-Gear PCG [3N]
   SurfDev surf{};             // split visualisation mesh tables (built on first use)
   bool surf_ready = false;
   void* surf_stage = nullptr; // host-output staging of the surface buffers (cudaMalloc, grown on demand)
@@ -1235,7 +1236,8 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
   const int64_t N = d.N;
   gf_status st = GF_OK;
   if (!m->qs_x) {
-    if ((st = scratch(m, 3 * N, &m->qs_x)) || (st = scratch(m, 3 * N, &m->qs_zero)) || (st = scratch(m, 4, &m->qs_out)))
+    if ((st = scratch(m, 3 * N, &m->qs_x)) || (st = scratch(m, 3 * N, &m->qs_zero)) || (st = scratch(m, 4, &m->qs_out)) ||
+        (st = scratch(m, 3 * N, &m->qs_w)))
       return st;
     GF_CK(cudaMemsetAsync(m->qs_zero, 0, sizeof(double) * 3 * N, s));
   }
@@ -1277,6 +1279,7 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
   sq.mscale = 0.0;
   DevMesh dq = d;
   dq.v = m->qs_zero;
+  dq.w = m->qs_w;
   GF_CK(cudaMemsetAsync(d.pinned, 0, N, s));
   double r0 = -1.0, rel = 0.0, h_out[4];
   int cg_total = 0, k = 0, status = GF_OK;
@@ -1306,13 +1309,15 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
       break;
     }
     if (rn == 0.0 || rn <= rtol * r0) break;
+    // PCG in the Chronopoulos-Gear form: w = A z and the coefficients, then
+    // per iteration the vector updates and the next w = A z
     int launched = 0;
     int chunk = std::max(1, std::min(m->last_iters + 1, 64));
+    { Prof p(m, kPSpmv, launched); L += launch_qs_cg_spmv(dq, s); }
     for (;;) {
       for (int j = 0; j < chunk; ++j, ++launched) {
-        { Prof p(m, kPSpmv, launched); L += launch_kind(kB_pcg_spmv, dq, mq, sq, s); }
-        { Prof p(m, kPPcgUpdate, launched); L += launch_kind(kB_pcg_update, dq, mq, sq, s); }
-        { Prof p(m, kPPcgP, launched); L += launch_kind(kB_pcg_p, dq, mq, sq, s); }
+        { Prof p(m, kPPcgUpdate, launched); L += launch_qs_cg_update(dq, s); }
+        { Prof p(m, kPSpmv, launched); L += launch_qs_cg_spmv(dq, s); }
       }
       GF_CK(cudaGetLastError());
       GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));

@@ -18,6 +18,7 @@ struct PcgState {
   double true_rr; // ||b - A dv||^2 after the solve
   double rr0;     // ||b - A dv||^2 at the start (a Newton iterate's residual when warm-started)
   int32_t iters, maxit, done, status;
+  int32_t cg_k;   // Chronopoulos-Gear form (quasi-static solve): reductions taken so far
 };
 
 // counters[3] flags an out-of-range pinned id, counters[4] a tensor-core wait that gave up
@@ -112,6 +113,7 @@ struct DevMesh {
   double* z = nullptr;
   double* p = nullptr;
   double* q = nullptr;
+  double* w = nullptr;                 // [3N] A z of the quasi-static Chronopoulos-Gear PCG
   double* pinv = nullptr;              // [N][9] block-Jacobi inverses
   uint8_t* pinned = nullptr;           // [N] 1 = velocity prescribed
   double* f_ext = nullptr;             // [3N] staging
@@ -216,6 +218,8 @@ int launch_newton_prep(const DevMesh& m, const Material& mt, double dt, double* 
 int launch_qs_energy(const DevMesh& m, const Material& mt, const double* x, const double* f_ext, double* out,
                      cudaStream_t s);
 int launch_qs_slope(const DevMesh& m, double* out, cudaStream_t s);
+int launch_qs_cg_spmv(const DevMesh& m, cudaStream_t s);     // Chronopoulos-Gear PCG: w = A z, dots, coefficients
+int launch_qs_cg_update(const DevMesh& m, cudaStream_t s);   // Chronopoulos-Gear PCG: vector updates
 int launch_qs_trial(int64_t n, const double* x, const double* d, double a, double* xt, cudaStream_t s);
 int launch_qs_set_pins(const DevMesh& m, const int32_t* ids, const double* pos, int64_t n_pinned, cudaStream_t s);
 

@@ -1189,6 +1189,91 @@ __global__ void __launch_bounds__(kThreads) kb_pcg_p(const BatchTab* __restrict_
   pcg_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
+// Quasi-static inner solve: the same projected block-Jacobi PCG in the
+// Chronopoulos-Gear form (Chronopoulos & Gear, J. Comput. Appl. Math. 25, 1989),
+// whose Krylov iterates equal the three-kernel form's in exact arithmetic but
+// which needs one grid reduction per iteration instead of two.  With w = A z,
+// gamma = r.z and delta = z.w: beta = gamma / gamma_old, p.A.p = delta -
+// beta gamma / alpha_old, alpha = gamma / p.A.p, and q = A p follows the
+// recurrence q = w + beta q.  k_qs_cg_spmv forms w and the three dots and sets
+// the coefficients in its last CTA; k_qs_cg_update streams the vector updates
+// with no reduction.  The mass-free quasi-static system takes hundreds of
+// iterations per Newton iteration, so a reduction and a launch saved per
+// iteration add up.
+__global__ void __launch_bounds__(kThreads) k_qs_cg_spmv(DevMesh m) {
+  PcgState* S = m.pcg;
+  if (S->done) return;   // set only by a last CTA, after every CTA has passed here
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double y[3];
+    spmv_row(m, i, m.z, y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double z = m.z[3 * i + c], r = m.r[3 * i + c];
+      m.w[3 * i + c] = y[c];
+      v[0] += r * z;      // z and r are zero on pinned rows
+      v[1] += z * y[c];
+      v[2] += r * r;
+    }
+  }
+  double out[3];
+  if (grid_reduce<3>(v, m.partials, m.tickets + 10, out, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
+    const int k = S->cg_k;   // updates applied so far
+    S->cg_k = k + 1;
+    S->iters = k;
+    S->rr = out[2];
+    const double gamma = out[0], delta = out[1];
+    const double beta = k > 0 ? gamma / S->rz : 0.0;
+    const double den = k > 0 ? delta - beta * gamma / S->alpha : delta;   // p.A.p
+    if (!isfinite(out[2]) || !isfinite(delta)) {
+      S->status = GF_NAN;
+      S->done = 1;
+    } else if (out[2] <= S->tol2 * S->bb) {
+      S->done = 1;
+    } else if (k >= S->maxit) {
+      S->status = GF_CG_MAXITER;
+      S->done = 1;
+    } else if (!(den > 0.0)) {
+      S->status = GF_CG_BREAKDOWN;
+      S->done = 1;
+    } else {
+      S->beta = beta;
+      S->alpha = gamma / den;
+      S->rz = gamma;
+      S->pq = den;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_qs_cg_update(DevMesh m) {
+  const PcgState* S = m.pcg;
+  if (S->done) return;
+  const double alpha = S->alpha, beta = S->beta;
+  const bool first = S->cg_k == 1;   // p = z, q = w
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double p[3], q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double z = m.z[3 * i + c], w = m.w[3 * i + c];
+      p[c] = first ? z : z + beta * m.p[3 * i + c];
+      q[c] = first ? w : w + beta * m.q[3 * i + c];
+      m.p[3 * i + c] = p[c];
+      m.q[3 * i + c] = q[c];
+    }
+    if (m.pinned[i]) continue;
+    double r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.dv[3 * i + c] += alpha * p[c];
+      r[c] = m.r[3 * i + c] - alpha * q[c];
+      m.r[3 * i + c] = r[c];
+    }
+    const double* pi = m.pinv + 9 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.z[3 * i + c] = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
+  }
+}
+
 // ||b - A dv||^2 over free nodes, recomputed from scratch after the solve.
 __device__ __forceinline__ void true_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
@@ -1246,6 +1331,14 @@ int launch_qs_energy(const DevMesh& m, const Material& mt, const double* x, cons
 }
 int launch_qs_slope(const DevMesh& m, double* out, cudaStream_t s) {
   k_qs_slope<<<qs_grid(m.N), kThreads, 0, s>>>(m, out);
+  return 1;
+}
+int launch_qs_cg_spmv(const DevMesh& m, cudaStream_t s) {
+  k_qs_cg_spmv<<<qs_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_qs_cg_update(const DevMesh& m, cudaStream_t s) {
+  k_qs_cg_update<<<qs_grid(m.N), kThreads, 0, s>>>(m);
   return 1;
 }
 int launch_qs_trial(int64_t n, const double* x, const double* d, double a, double* xt, cudaStream_t s) {
