@@ -205,8 +205,9 @@ __device__ __forceinline__ void edge_driver_body(const DevMesh& m, const Materia
       const double q = fma(w[5], c.y, fma(w[4], c.x, fma(w[3], b.y, fma(w[2], b.x, fma(w[1], a.y, w[0] * a.x)))));
       mq = fmax(mq, q);
     }
-    const double mx = mq / s;
-    const double d = mt.driver_stress ? mx : mx / mt.young;
+    // one FP64 division per edge (a multi-instruction sequence on the FP64
+    // pipe): the strain driver divides by s E at once
+    const double d = mq / (mt.driver_stress ? s : s * mt.young);
     m.driver[i] = d;
     const uint8_t old = m.labels[i];
     const uint8_t now = (old || d >= mt.threshold) ? 1 : 0;
