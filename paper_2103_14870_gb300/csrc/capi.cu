@@ -505,6 +505,8 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   UP(d.nrow, hm.nrow, int32_t);
   UP(d.erow, hm.erow, int32_t);
   UP(d.edge_slot, hm.edge_slot, int32_t);
+  UP(d.edge_order, hm.edge_order, int32_t);
+  UP(d.node_order, hm.node_order, int32_t);
   std::vector<double> mass_blk;
   if (M.mass_matrix == GF_MASS_CONSISTENT) {
     // Eq. 5 for a linear tet: m_ab = rho V (1 + delta_ab) / 20, summed into the block slots
@@ -637,6 +639,7 @@ gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets
   info->device_bytes = int64_t(hm.tets.size() * 4 + hm.tet_edges.size() * 4 + hm.slot.size() * 4 +
                                hm.rest.size() * 8 + hm.row_ptr.size() * 4 + hm.col.size() * 4 +
                                hm.edges.size() * 4 + hm.et_ptr.size() * 4 + hm.et_tet.size() * 4 +
+                               hm.edge_order.size() * 4 + hm.node_order.size() * 4 +
                                hm.nbr.idx.size() * 12 + hm.nbr.group_off.size() * 12 + hm.nbr.perm.size() * 4) +
                        N * (8 + 8 * 3 * 12 + 9 * 8 + 8) + T * (8 + 18 * 8 + 4) + hm.n_edges * 9 + hm.n_blocks * 72;
   if (edges) std::memcpy(edges, hm.edges.data(), sizeof(int32_t) * hm.edges.size());

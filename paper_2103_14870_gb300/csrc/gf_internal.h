@@ -99,6 +99,8 @@ struct HostMesh {
   std::vector<int32_t> slot;       // [T][16] block index of local (a, b), internal order
   std::vector<int32_t> et_ptr;     // [NE+1] edge -> incident tets (and edge rows)
   std::vector<int32_t> et_tet;     // internal tet ids
+  std::vector<int32_t> edge_order; // [NE] gather order of the edges (row counts grouped)
+  std::vector<int32_t> node_order; // [N] gather order of the nodes (row counts grouped)
   std::vector<double> rest;        // [kRestFields][T]
   std::vector<double> mass;        // [N] lumped
   NeighbourSell nbr;

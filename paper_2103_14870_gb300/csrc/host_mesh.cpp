@@ -325,6 +325,22 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
         hm.erow[6 * i + k] = r;   // edge rows follow the edge -> tet lists
       }
   }
+  // Order in which the gather visits edges and nodes: within windows of 1,024,
+  // by descending row count (stable), so the lanes of a warp sum rows of equal
+  // count and few of them idle in the FP64 adds; the windows keep the rows read
+  // by neighbouring warps close in memory.
+  auto count_order = [](const std::vector<int32_t>& ptr, std::vector<int32_t>& order) {
+    const int64_t n = int64_t(ptr.size()) - 1;
+    order.resize(n);
+    std::iota(order.begin(), order.end(), 0);
+    constexpr int64_t kWin = 1024;
+    for (int64_t w0 = 0; w0 < n; w0 += kWin)
+      std::stable_sort(order.begin() + w0, order.begin() + std::min(n, w0 + kWin), [&](int32_t x, int32_t y) {
+        return ptr[x + 1] - ptr[x] > ptr[y + 1] - ptr[y];
+      });
+  };
+  count_order(hm.et_ptr, hm.edge_order);
+  count_order(hm.np_ptr, hm.node_order);
 
   // ---- Eq. 20 neighbour lists on rest centroids, w = V_j (1 - r^2/R^2)^2 normalised ----
   const double R = mat.radius;

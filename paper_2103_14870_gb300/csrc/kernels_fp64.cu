@@ -764,8 +764,9 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   const int64_t n_edge = 9 * m.NE;
   if (t < n_edge) {
-    const int64_t e = t / 9;
-    const int q = int(t - 9 * e);
+    const int64_t g = t / 9;
+    const int q = int(t - 9 * g);
+    const int64_t e = m.edge_order[g];   // edges of equal row count side by side
     const double acc = row_sum<8>(m.ebuf + int64_t(kNodeRow) * 4 * m.T + q, kEdgeRow, m.et_ptr[e], m.et_ptr[e + 1]);
     const int2 sl = m.edge_slot[e];
     m.val[9 * int64_t(sl.x) + q] = acc;
@@ -774,8 +775,9 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
   }
   const int64_t u = t - n_edge;
   if (u >= 3 * m.N) return;
-  const int64_t i = u / 3;
-  const int c3 = int(u - 3 * i);
+  const int64_t g = u / 3;
+  const int c3 = int(u - 3 * g);
+  const int64_t i = m.node_order[g];
   const double acc = row_sum<8>(m.ebuf + c3, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
   const double* f_ext = sp.has_fext ? m.f_ext : nullptr;
   double mv = m.mass[i] * m.v[3 * i + c3];
