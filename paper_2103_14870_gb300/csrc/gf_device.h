@@ -90,8 +90,8 @@ struct DevMesh {
   const int32_t* nrow = nullptr;       // [T][4] node row of (tet, local node)
   const int32_t* erow = nullptr;       // [T][6] edge row of (tet, local edge)
   const int2* edge_slot = nullptr;     // [NE] block slots of (i, j) and (j, i), i < j
-  const int32_t* edge_order = nullptr; // [NE] FP64 gather: slot -> edge, row counts grouped
-  const int32_t* node_order = nullptr; // [N] FP64 gather: slot -> node, row counts grouped
+  const int32_t* edge_order = nullptr; // [NE] FP64 gather and edge driver: slot -> edge, row counts grouped
+  const int32_t* node_order = nullptr; // [N] FP64 gather and diagonal: slot -> node, row counts grouped
   const int64_t* nb_off = nullptr;     // [G]
   const int32_t* nb_len = nullptr;     // [G]
   const int32_t* nb_idx = nullptr;

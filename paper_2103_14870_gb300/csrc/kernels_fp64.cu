@@ -183,9 +183,10 @@ __global__ void __launch_bounds__(kThreads) kb_nonlocal(const BatchTab* __restri
 // driver = sigma*/E (or sigma*), then zeta |= (driver >= threshold) (Eq. 21).
 __device__ __forceinline__ void edge_driver_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
-  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t g = bid * int64_t(blockDim.x) + threadIdx.x;
   unsigned long long n_brk = 0, n_new = 0;
-  if (i < m.NE) {
+  if (g < m.NE) {
+    const int64_t i = m.edge_order[g];   // edges of equal incident-tet count side by side
     const int2 ab = m.edges[i];
     double pa[3], pb[3];
     ld3(m.x, ab.x, pa);
@@ -797,8 +798,9 @@ __device__ __forceinline__ void gather64_body(const DevMesh& m, const Material& 
 __device__ __forceinline__ void diag64_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
   const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
   if (t >= 9 * m.N) return;
-  const int64_t i = t / 9;
-  const int q = int(t - 9 * i);
+  const int64_t g = t / 9;
+  const int q = int(t - 9 * g);
+  const int64_t i = m.node_order[g];   // nodes of similar degree side by side
   const int d = m.diag_blk[i], b0 = m.row_ptr[i], b1 = m.row_ptr[i + 1];
   // the sum starts from the row's first off-diagonal block (none for a node
   // outside every tet)
