@@ -646,17 +646,16 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
     ld3(m.x, nid[a], P[a]);
     ld3(m.v, nid[a], U[a]);
   }
-  double e[6][3], ds[6], Dv[6];
+  double e[6][3], du[6][3], ds[6], Dv[6];   // edge vectors and edge velocity differences
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    double du[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       e[k][c] = P[edge_b(k)][c] - P[edge_a(k)][c];
-      du[c] = U[edge_b(k)][c] - U[edge_a(k)][c];
+      du[k][c] = U[edge_b(k)][c] - U[edge_a(k)][c];
     }
     ds[k] = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2] - m.rest[(kRestS0 + k) * m.T + t];
-    Dv[k] = 2.0 * (e[k][0] * du[0] + e[k][1] * du[1] + e[k][2] * du[2]);
+    Dv[k] = 2.0 * (e[k][0] * du[k][0] + e[k][1] * du[k][1] + e[k][2] * du[k][2]);
   }
   double H[21];
 #pragma unroll
@@ -682,7 +681,7 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
       const double a1 = sc * (g[k] + cv * w[k]), a2 = sc * cv * g[k];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double tk = a1 * e[k][c] + a2 * (U[edge_b(k)][c] - U[edge_a(k)][c]);
+        const double tk = a1 * e[k][c] + a2 * du[k][c];
         f[edge_a(k)][c] += tk;
         f[edge_b(k)][c] -= tk;
       }
