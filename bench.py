@@ -32,6 +32,8 @@ UNIT = "ms/step"
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 SAMPLE_SCALE = 0.4          # oracle sample: loaf axes x 0.4 (~40k tets)
+MIXED_DTYPE = ("f32 tangents/stresses/SpMV/inner PCG; double-float (float pairs, ~48-bit significand) "
+               "refinement residual, correction and dot products; f64 state and threshold compare")
 
 
 def peaks():
@@ -77,11 +79,10 @@ class ClockSampler:
 # written once; gathers of node data counted once per node).
 MIXED_BYTES = {
     "m:tet_stress": lambda i: i["n_tets"] * (16 + 72 + 4 + 24 + 24) + 12 * i["n_nodes"],
-    # joint lists of tet pairs: per entry a 16-bit union position and two FP32
-    # weights, 0.61 entries per (tet, neighbour) pair on the loaf (6.1 B per
-    # pair); per tet half a list pointer, its stress row read once and its
-    # average row written
-    "m:nonlocal_avg": lambda i: 6.1 * i["n_nbr_pairs"] + i["n_tets"] * (4 + 32 + 32),
+    # joint lists of tet pairs: per entry a 16-bit union position and the two
+    # FP32 weights; per tile its union ids; per tet half a list pointer, its
+    # stress row read once and its average row written
+    "m:nonlocal_avg": lambda i: 10 * i["n_joint_entries"] + 4 * i["n_union_rows"] + i["n_tets"] * (4 + 32 + 32),
     "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
     # phase 1: tet, rest row (128 B), chi, its ten row indices in; 6 edge rows
     # (36 B) + 4 node rows (16 B) out; u, v and the external force per node
@@ -115,6 +116,13 @@ NCU_TRAFFIC = {
 # tets = (2 x 264.4 M + 53.3 M + 40.9 M) / 619,300): the tangent has no short
 # closed count.
 ELEM64_FLOPS_PER_TET = 1006.0
+
+
+def broken_summary(broken: list) -> dict:
+    """Broken edges (labels = 1) after each timed step: first, last, and the
+    steps in which the count grew (relabelling did work)."""
+    grew = sum(1 for a, b in zip(broken, broken[1:]) if b > a)
+    return {"first": broken[0], "last": broken[-1], "steps_with_new_breaks": grew, "steps": len(broken)}
 
 
 def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, traffic=None):
@@ -165,7 +173,7 @@ def roofline_for(group: str, ms: float, launches: int, info: dict, pk: dict, tra
             "traffic": traffic, "kernel": group, "work_per_launch": {"bytes": bytes_per}}
 
 
-def cpu_sample_child(steps: int) -> None:
+def cpu_sample_child(steps: int, warmup: int = 1) -> None:
     """Run in a subprocess with one BLAS/OpenMP thread: oracle steps on the sample."""
     import numpy as np
     from oracle.step import Material, Model
@@ -173,19 +181,21 @@ def cpu_sample_child(steps: int) -> None:
     w = loaf_config(axes=tuple(a * SAMPLE_SCALE for a in LOAF_AXES))
     m = Model(w.nodes, w.tets, Material(w.young, w.poisson, w.density, w.threshold, w.radius))
     st = m.rest_state()
-    st, _ = m.step(st, w.dt, w.f_ext, None, solver="pcg", rtol=w.cg_rtol)   # warm-up
+    for _ in range(warmup):
+        st, _ = m.step(st, w.dt, w.f_ext, None, solver="pcg", rtol=w.cg_rtol)
     t0 = time.perf_counter()
     for _ in range(steps):
         st, info = m.step(st, w.dt, w.f_ext, None, solver="pcg", rtol=w.cg_rtol)
     dt = (time.perf_counter() - t0) / steps
-    print(json.dumps({"sec_per_step": dt, "tets": w.n_tets, "steps": steps, "cg_iters": info["iters"]}))
+    print(json.dumps({"sec_per_step": dt, "tets": w.n_tets, "steps": steps, "warmup": warmup,
+                      "cg_iters": info["iters"]}))
 
 
-def cpu_sample(steps: int, threads: int = 1) -> dict:
+def cpu_sample(steps: int, threads: int = 1, warmup: int = 1) -> dict:
     t = str(threads)
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-child", str(steps)],
-                         capture_output=True, text=True, env=env, check=True)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-child", str(steps),
+                          "--cpu-sample-warmup", str(warmup)], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
@@ -195,28 +205,35 @@ def cpu_baseline_entry(steps: int, full_tets: int) -> dict:
     nproc = os.cpu_count() or 1
     a = cpu_sample(steps, nproc)
     return {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{s['steps']} oracle steps on the loaf generator with axes x{SAMPLE_SCALE} ({s['tets']} tets), "
-                      f"same material/dt/R_d/loads, PCG rtol 1e-6 ({s['cg_iters']} iterations), "
-                      f"{s['sec_per_step']:.2f} s/step scaled per tet to {full_tets} tets; numpy/scipy, 1 thread",
+            "sample": f"{s['steps']} oracle steps (after {s['warmup']} warm-up) on the loaf generator with axes "
+                      f"x{SAMPLE_SCALE} ({s['tets']} tets), same material/dt/R_d/loads, PCG rtol 1e-6 "
+                      f"({s['cg_iters']} iterations), {s['sec_per_step']:.2f} s/step scaled per tet to {full_tets} "
+                      f"tets; numpy/scipy, 1 thread",
             "all_cores": {"value": a["sec_per_step"] * 1e3 * full_tets / a["tets"], "unit": UNIT, "cores": nproc,
                           "sample": f"the same sample with OMP/BLAS threads = {nproc} (the oracle's sparse "
                                     f"products and Python loops stay single-threaded)"}}
 
 
 def run_reference(args) -> None:
+    """The oracle as the reference arm: W warm-up and K timed steps, each one
+    oracle step on the bounded sample of the loaf (axes x0.4), scaled per tet
+    to the full mesh.  The line says what ran: the sample's tets and steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from workloads import loaf_config
     w_tets = 619300
-    s = cpu_sample(args.steps + args.warmup)
+    s = cpu_sample(args.steps, warmup=args.warmup)
     ms = s["sec_per_step"] * 1e3 * w_tets / s["tets"]
     cb = {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": f"{s['steps']} oracle steps on a {s['tets']}-tet sample (loaf axes x{SAMPLE_SCALE}), scaled per tet"}
+          "sample": f"{s['steps']} timed oracle steps after {s['warmup']} warm-up, each on a {s['tets']}-tet sample "
+                    f"of the loaf (axes x{SAMPLE_SCALE}), {s['sec_per_step']:.3f} s/step scaled per tet to "
+                    f"{w_tets} tets; numpy/scipy, 1 thread"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+                      "steps": s["steps"], "warmup": s["warmup"], "ms_per_step": ms, "higher_is_better": False,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "loaf_bcc_620k_fp64", "n_tets": w_tets, "cg_rtol": 1e-6},
+                      "config": {"workload": "loaf_bcc_620k_fp64", "n_tets": w_tets, "cg_rtol": 1e-6,
+                                 "sample_tets": s["tets"], "sample_steps_timed": s["steps"],
+                                 "sample_warmup": s["warmup"], "scaled_per_tet_to": w_tets},
                       "cpu_baseline": cb,
                       "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -335,6 +352,158 @@ def run_learned(args, gf, torch, barrier, stream, w, mat, f_dev) -> dict:
             "dtype": "bf16 weights, f32 activations; PCG f64 to the same 1e-6 residual",
             "held_out": {"plain": plain, "learned_start": learned},
             "cg_iters_saved_per_step": plain["cg_iters_per_step"] - learned["cg_iters_per_step"]}
+
+
+def calibrate_threshold(m, w, f_dev, pins, np):
+    """Threshold rule for configurations that give none: the (1 - 1e-3)
+    quantile of the FP64 edge drivers of step 10 from rest, unbroken
+    (threshold +inf), rounded to 3 significant figures.  Leaves the mesh at
+    rest with that threshold set."""
+    m.threshold_set(math.inf)
+    for _ in range(10):
+        s = m.step(w.dt, f_dev, pins)
+        assert s["status"] == 0, s
+    drv, _ = m.damage_get()
+    theta = float(f"{float(np.quantile(drv[np.isfinite(drv)], 1.0 - 1e-3)):.3g}")
+    m.state_set(x=w.nodes.ravel(), v=np.zeros(w.nodes.size), labels=np.zeros(m.n_edges, np.uint8),
+                chi=np.ones(m.n_tets))
+    m.threshold_set(theta)
+    return theta
+
+
+def timed_from_rest(args, m, w, f_dev, pins, barrier, stream, torch, steps):
+    """`steps` timed steps after the warm-up, from the rest state, unprofiled
+    (one graph replay per step), then 3 profiled steps for the breakdown."""
+    import numpy as np
+    m.state_set(x=w.nodes.ravel(), v=np.zeros(w.nodes.size), labels=np.zeros(m.n_edges, np.uint8),
+                chi=np.ones(m.n_tets))
+    for _ in range(args.warmup):
+        m.step(w.dt, f_dev, pins)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its, sweeps, broken = [], [], []
+    for _ in range(steps):
+        s = m.step(w.dt, f_dev, pins)
+        assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
+        its.append(s["cg_iters"])
+        sweeps.append(s["refine_sweeps"])
+        broken.append(s["n_broken"])
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / steps
+    m.profile_reset()
+    m.profile_enable(True)
+    for _ in range(3):
+        m.step(w.dt, f_dev, pins)
+    m.profile_enable(False)
+    prof = m.profile_get()
+    return {"ms_per_step": ms, "element_updates_per_s": w.n_tets / (ms * 1e-3),
+            "cg_iters_per_step": statistics.mean(its), "refine_sweeps_per_step": statistics.mean(sweeps),
+            "n_broken_timed": broken_summary(broken),
+            "kernels_ms_per_step": {k: v[0] / 3 for k, v in prof.items() if v[0] > 0},
+            "_prof": prof}
+
+
+def run_glass(args, gf, torch, barrier, stream) -> dict:
+    """Brittle glass point impact on the loaf mesh (E = 7e10, nu = 0.22,
+    rho = 2500, 1e4 N at the top apex, lowest 5% of nodes pinned, R_d = 1.5 h)
+    in mixed precision, with the FP64 step timed beside it on the same
+    configuration and threshold.  Per-step error of the mixed step: both forms
+    step from the same state (the FP64 form's), and the mixed velocity update
+    is compared with the FP64 one (the FP64 path matches the FP64 oracle to
+    1e-9 in the parity tests)."""
+    import numpy as np
+    from workloads import glass_config
+    w = glass_config()
+    f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
+    pins = torch.tensor(w.pinned, dtype=torch.int32, device="cuda")
+    mat = gf.material(w.young, w.poisson, w.density, threshold=math.inf, radius=w.radius)
+    m64 = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
+    theta = calibrate_threshold(m64, w, f_dev, pins, np)
+    mat = gf.material(w.young, w.poisson, w.density, threshold=theta, radius=w.radius)
+    mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
+    steps = min(args.steps, 100)
+    fp64 = timed_from_rest(args, m64, w, f_dev, pins, barrier, stream, torch, steps)
+    mixed = timed_from_rest(args, mm, w, f_dev, pins, barrier, stream, torch, steps)
+    pk = peaks()
+    for form, r, pre, mesh in (("fp64", fp64, "", m64), ("mixed", mixed, "m:", mm)):
+        prof = r.pop("_prof")
+        cands = ("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "assemble_gather", "pcg_spmv")
+        dom = max(cands, key=lambda k: prof[k][0])
+        r["roofline"] = roofline_for(pre + dom, prof[dom][0], prof[dom][1], mesh.info, pk, None)
+    # per-step error of the mixed step from the FP64 form's state
+    zeros = np.zeros(w.nodes.size)
+    m64.state_set(x=w.nodes.ravel(), v=zeros, labels=np.zeros(m64.n_edges, np.uint8), chi=np.ones(m64.n_tets))
+    err_dv, err_drv, lab_diff, broken = [], [], [], []
+    n_err = min(args.steps, 20)
+    for _ in range(n_err):
+        x0, v0 = m64.positions_get(), m64.velocities_get()
+        _, l0 = m64.damage_get()
+        mm.state_set(x=x0, v=v0, labels=l0, chi=m64.chi_get())
+        s64 = m64.step(w.dt, f_dev, pins)
+        s32 = mm.step(w.dt, f_dev, pins)
+        assert s64["status"] == 0 and s32["status"] == 0
+        dv64 = m64.velocities_get() - v0
+        dv32 = mm.velocities_get() - v0
+        d64, l64 = m64.damage_get()
+        d32, l32 = mm.damage_get()
+        fin = np.isfinite(d64)
+        err_dv.append(float(np.linalg.norm(dv32 - dv64) / max(np.linalg.norm(dv64), 1e-300)))
+        err_drv.append(float(np.abs(d32[fin] - d64[fin]).max() / max(np.abs(d64[fin]).max(), 1e-300)))
+        lab_diff.append(int((l32 != l64).sum()))
+        broken.append(s64["n_broken"])
+    m64.close()
+    mm.close()
+    return {"workload": "loaf_bcc_620k_glass: the loaf mesh, E=7e10, nu=0.22, rho=2500, 1e4 N point impact at the "
+                        "top apex, lowest 5% of nodes pinned, dt=5e-4, R_d=1.5, CG rtol 1e-6",
+            "threshold": theta,
+            "threshold_rule": "(1 - 1e-3) quantile of the FP64 step-10 drivers from rest, 3 significant figures",
+            "steps_timed": steps, "fp64": fp64, "mixed": mixed,
+            "speedup_mixed_vs_fp64": fp64["ms_per_step"] / mixed["ms_per_step"],
+            "mixed_dtype": MIXED_DTYPE,
+            "per_step_error_vs_fp64": {
+                "steps": n_err, "from": "the FP64 form's state at every step, starting at rest",
+                "rel_err_dv": err_dv, "rel_err_dv_max": max(err_dv),
+                "rel_err_driver_max_norm": err_drv, "label_mismatches": lab_diff, "n_broken_fp64": broken,
+                "note": "the FP64 path is parity-tested against the FP64 oracle to 1e-9; the oracle does not run "
+                        "inside the timed bench"}}
+
+
+def run_survey_c2(args, gf, torch, barrier, stream) -> dict:
+    """The loaf at R_d = 2 h (the radius the survey proposes for this
+    configuration) with the threshold by the quantile rule, FP64 and mixed,
+    each with its roofline figure and the broken-edge counts of the timed
+    steps."""
+    import numpy as np
+    from workloads import loaf_config
+    w = loaf_config()
+    radius = 2.0
+    f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
+    mat = gf.material(w.young, w.poisson, w.density, threshold=math.inf, radius=radius)
+    m64 = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
+    theta = calibrate_threshold(m64, w, f_dev, None, np)
+    info = m64.info
+    pk = peaks()
+    out = {"workload": "loaf_bcc_620k at R_d = 2 h, threshold by the quantile rule", "radius": radius,
+           "threshold": theta,
+           "threshold_rule": "(1 - 1e-3) quantile of the FP64 step-10 drivers from rest, 3 significant figures",
+           "n_nbr_pairs": info["n_nbr_pairs"]}
+    steps = min(args.steps, 100)
+    out["fp64"] = timed_from_rest(args, m64, w, f_dev, None, barrier, stream, torch, steps)
+    m64.close()
+    mat = gf.material(w.young, w.poisson, w.density, threshold=theta, radius=radius)
+    mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
+    mix_info = mm.info
+    out["mixed"] = timed_from_rest(args, mm, w, f_dev, None, barrier, stream, torch, steps)
+    mm.close()
+    for form, pre, inf in (("fp64", "", info), ("mixed", "m:", mix_info)):
+        prof = out[form].pop("_prof")
+        cands = ("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "assemble_gather", "pcg_spmv")
+        dom = max(cands, key=lambda k: prof[k][0])
+        out[form]["roofline"] = roofline_for(pre + dom, prof[dom][0], prof[dom][1], inf, pk, None)
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
 
 
 def run_extensions(args, gf, torch, barrier, stream, w, f_dev, m_main) -> dict:
@@ -458,7 +627,7 @@ def run_ours(args) -> None:
         """Time `steps` steps as a user runs them (no per-launch profiling, so the
         step is one graph replay), then profile a few more steps separately for
         the per-kernel breakdown (profiling puts events between launches)."""
-        iters, sweeps = [], []
+        iters, sweeps, broken = [], [], []
         for _ in range(args.warmup):
             m.step(w.dt, f_dev)
         l0 = m.launch_count()
@@ -469,11 +638,13 @@ def run_ours(args) -> None:
             s = m.step(w.dt, f_dev)
             iters.append(s["cg_iters"])
             sweeps.append(s["refine_sweeps"])
+            broken.append(s["n_broken"])
             assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
         e1.record(stream)
         barrier()
         ms, launches = e0.elapsed_time(e1) / steps, m.launch_count() - l0
-        return ms, launches, profiled(m, min(steps, 5)), statistics.mean(iters), statistics.mean(sweeps)
+        return (ms, launches, profiled(m, min(steps, 5)), statistics.mean(iters), statistics.mean(sweeps),
+                broken_summary(broken))
 
     def profiled(m, steps, pinned=None):
         """Per-kernel-group times of `steps` further steps, scaled to the same
@@ -491,7 +662,7 @@ def run_ours(args) -> None:
     m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol)
     info = m.info
     clk = ClockSampler(local)
-    ms, launches, prof, it_mean, _ = timed(m, args.steps)
+    ms, launches, prof, it_mean, _, broken = timed(m, args.steps)
     clocks = clk.stop()
     # end to end through the public API with host buffers: pinned f_ext in, positions out, every step
     f_host = torch.tensor(w.f_ext.ravel(), dtype=torch.float64).pin_memory()
@@ -507,8 +678,11 @@ def run_ours(args) -> None:
     m.close()
     # mixed-precision form on the same workload and tolerance
     mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
-    mix_ms, mix_launches, mix_prof, mix_it, mix_sw = timed(mm, args.steps)
+    mix_info = mm.info
+    mix_ms, mix_launches, mix_prof, mix_it, mix_sw, mix_broken = timed(mm, args.steps)
     mm.close()
+    glass = run_glass(args, gf, torch, barrier, stream) if not args.no_glass else None
+    survey_c2 = run_survey_c2(args, gf, torch, barrier, stream) if not args.no_c2 else None
     batch = run_batch(args, gf, torch, barrier, stream, world, rank, dist) if not args.no_batch else None
     learned = run_learned(args, gf, torch, barrier, stream, w, mat, f_dev) if not args.no_learned else None
     t_all = torch.tensor([ms, e2e_ms, mix_ms], dtype=torch.float64, device="cuda")
@@ -523,7 +697,7 @@ def run_ours(args) -> None:
     roof = roofline_for(dom, prof[dom][0], prof[dom][1], info, pk, NCU_TRAFFIC.get(dom))
     mdom = max(("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "assemble_gather", "pcg_spmv"),
                key=lambda k: mix_prof[k][0])
-    mix_roof = roofline_for("m:" + mdom, mix_prof[mdom][0], mix_prof[mdom][1], info, pk,
+    mix_roof = roofline_for("m:" + mdom, mix_prof[mdom][0], mix_prof[mdom][1], mix_info, pk,
                             NCU_TRAFFIC.get("m:" + mdom))
     cpu = None if args.no_cpu_baseline else cpu_baseline_entry(3, w.n_tets)
     out = {
@@ -537,15 +711,18 @@ def run_ours(args) -> None:
                    "parallelism": "replicas" if world > 1 else "single"},
         "element_updates_per_s": info["n_tets"] / (ms * 1e-3),
         "cg_iters_per_step": it_mean,
+        "n_broken_timed": broken,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * w.n_nodes,
                 "d2h_bytes_per_step": 8 * 3 * w.n_nodes + 48},
         "gpu_launches": launches,
         "roofline": roof,
         "mixed": {"ms_per_step": mix_ms, "speedup_vs_fp64": ms / mix_ms, "cg_iters_per_step": mix_it,
-                  "refine_sweeps_per_step": mix_sw, "element_updates_per_s": info["n_tets"] / (mix_ms * 1e-3),
-                  "gpu_launches": mix_launches, "dtype": "f32 tangents/SpMV/PCG, f64 state/residual/dots/threshold",
+                  "refine_sweeps_per_step": mix_sw, "n_broken_timed": mix_broken, "element_updates_per_s": info["n_tets"] / (mix_ms * 1e-3),
+                  "gpu_launches": mix_launches, "dtype": MIXED_DTYPE,
                   "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mix_prof.items()},
                   "roofline": mix_roof},
+        "mixed_glass": glass,
+        "survey_c2": survey_c2,
         "batch": batch,
         "learned": learned,
         "extensions": ext,
@@ -635,15 +812,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched form")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start form")
+    ap.add_argument("--no-glass", action="store_true", help="skip the glass point-impact lines (mixed and FP64)")
+    ap.add_argument("--no-c2", action="store_true", help="skip the loaf at R_d = 2 h with the quantile threshold")
     ap.add_argument("--no-extensions", action="store_true",
                     help="skip the SNH / consistent-mass / Newton / quasi-static / surface lines")
     ap.add_argument("--cpu-sample-child", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sample-warmup", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
     ap.add_argument("--precision", choices=["fp64", "mixed", "learned", "snh", "qs", "surface", "batch"], default="fp64",
                     help="form run by --profile-step (see run_profile_step)")
     args = ap.parse_args()
     if args.cpu_sample_child:
-        cpu_sample_child(args.cpu_sample_child)
+        cpu_sample_child(args.cpu_sample_child, args.cpu_sample_warmup)
         return
     if args.profile_step:
         run_profile_step(args)

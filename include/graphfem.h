@@ -122,6 +122,8 @@ typedef struct gf_mesh_info {
   int64_t n_colours;     /* tet colours of the conflict-free assembly scatter */
   int64_t n_nbr_pairs;   /* (tet, neighbour) pairs of Eq. 20 within R_d */
   int64_t device_bytes;  /* device memory held by the mesh */
+  int64_t n_joint_entries; /* GF_MIXED: entries of the Eq. 20 joint lists of tet pairs (0 otherwise) */
+  int64_t n_union_rows;  /* GF_MIXED: tet ids in the per-tile neighbour unions of Eq. 20 (0 otherwise) */
 } gf_mesh_info;
 
 typedef struct gf_mesh gf_mesh;
@@ -193,6 +195,13 @@ gf_status gf_tuning_get(const gf_mesh* mesh, gf_tuning* tuning);
  * iterative refinement (default 1e-4; 0 < inner_rtol < 1).  The outer FP64
  * tolerance stays cg_rtol. */
 gf_status gf_refine_set(gf_mesh* mesh, double inner_rtol);
+
+/* Change the break threshold sigma_thres of Eq. 21 between steps (same units
+ * as gf_material.threshold; +inf breaks nothing).  For a threshold calibrated
+ * on the mesh's own run (e.g. a quantile of its drivers).  Labels already
+ * broken stay broken.  A batch copies its meshes' materials when it is
+ * created, so set the threshold before gf_batch_create.  NaN -> GF_BAD_ARG. */
+gf_status gf_threshold_set(gf_mesh* mesh, double threshold);
 
 /* Change the solver tolerance and iteration cap between steps (rtol > 0). */
 gf_status gf_solver_set(gf_mesh* mesh, double cg_rtol, int32_t cg_maxit);
@@ -300,16 +309,20 @@ int64_t gf_launch_count(const gf_mesh* mesh);
  * row_ptr int32 [n_rows+1], col int32 [row_ptr[n_rows]] (each in [0, n_rows),
  * else GF_BAD_ARG), values float64 [9 * row_ptr[n_rows]] row-major 3x3 blocks of
  * a symmetric positive definite matrix, b float64 [3 * n_rows], x float64
- * [3 * n_rows] (in: prescribed values on fixed rows, free rows ignored and
- * started from 0; out: the solution), fixed uint8 [n_rows] (1 = row held at
- * x, NULL = none).  Stops when ||b - A x|| <= rtol ||b - A x_fixed|| on free
- * rows.  stream: cudaStream_t (NULL = legacy default); returns after the
- * solve completes.  iters and rel_res (host, may be NULL) receive the CG
- * iterations and the final relative residual.  The scratch array is shared by
- * all calls on a device and keeps the last call's contents (each call clears
- * what must start at zero); calls whose work overlaps on the GPU race on it.
- * The first call on a device looks up the array's device address, so that call
- * should come before any stream capture. */
+ * [3 * n_rows] (in: prescribed values on fixed rows; free rows are never read,
+ * so they may hold anything, and the solve starts from 0 there; out: the
+ * solution), fixed uint8 [n_rows] (1 = row held at x, NULL = none).  Every
+ * free row needs an invertible diagonal block (block-Jacobi preconditioner);
+ * a missing or singular one returns GF_BAD_ARG before any iteration.  Stops
+ * when ||b - A x|| <= rtol ||b - A x_fixed|| on free rows.  stream:
+ * cudaStream_t (NULL = legacy default); returns after the solve completes.
+ * iters and rel_res (host, may be NULL) receive the CG iterations and the final
+ * relative residual.  The scratch array is shared by all calls on a device and
+ * keeps the last call's contents (each call clears what must start at zero);
+ * calls whose work overlaps on the GPU race on it.  The first call on a device
+ * looks up the array's device address and keeps it for the life of the
+ * process, so that call should come before any stream capture, and this entry
+ * point must not be used after a cudaDeviceReset of that device. */
 gf_status gf_bsr_pcg_solve_static(const int32_t* row_ptr, const int32_t* col, const double* values, int64_t n_rows,
                                   const double* b, double* x, const uint8_t* fixed, double rtol, int32_t maxit,
                                   void* stream, int32_t* iters, double* rel_res);

@@ -177,6 +177,8 @@ struct gf_mesh {
   size_t surf_stage_bytes = 0;
   int64_t launches = 0;
   int64_t nbr_pairs = 0;
+  int64_t joint_entries = 0;  // GF_MIXED: entries of the Eq. 20 joint lists of tet pairs
+  int64_t union_rows = 0;     // GF_MIXED: tet ids of the per-tile neighbour unions
 
   PcgState* h_pcg = nullptr;               // pinned host mirror
   IrState* h_ir = nullptr;                 // pinned host mirror (mixed)
@@ -535,6 +537,8 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.nb_w2, mxh.nb_w2, float);
     UP(d.mx.nl_uptr, mxh.nl_uptr, int64_t);
     UP(d.mx.nl_uidx, mxh.nl_uidx, int32_t);
+    m->joint_entries = int64_t(mxh.nb_loc.size());
+    m->union_rows = int64_t(mxh.nl_uidx.size());
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());
     UP(d.mx.mass32, m32, float);
     if (!mass_blk.empty()) {
@@ -635,6 +639,8 @@ gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets
   info->n_blocks = hm.n_blocks;
   info->n_colours = int64_t(hm.colour_ptr.size()) - 1;
   info->n_nbr_pairs = hm.nbr.pairs;
+  info->n_joint_entries = 0;
+  info->n_union_rows = 0;
   const int64_t N = hm.n_nodes, T = hm.n_tets;
   info->device_bytes = int64_t(hm.tets.size() * 4 + hm.tet_edges.size() * 4 + hm.slot.size() * 4 +
                                hm.rest.size() * 8 + hm.row_ptr.size() * 4 + hm.col.size() * 4 +
@@ -679,6 +685,8 @@ gf_status gf_mesh_info_get(const gf_mesh* m, gf_mesh_info* info) {
   info->n_colours = int64_t(m->hm.colour_ptr.size()) - 1;
   info->n_nbr_pairs = m->nbr_pairs;
   info->device_bytes = m->bytes;
+  info->n_joint_entries = m->joint_entries;
+  info->n_union_rows = m->union_rows;
   return GF_OK;
 }
 
@@ -757,6 +765,17 @@ gf_status gf_newton_set(gf_mesh* m, int32_t max_iters, double rtol) {
   }
   m->newton_iters = max_iters;
   m->newton_rtol = rtol;
+  return GF_OK;
+}
+
+gf_status gf_threshold_set(gf_mesh* m, double threshold) {
+  if (!m || std::isnan(threshold)) {
+    set_last_error("need a mesh and a threshold that is not NaN");
+    return GF_BAD_ARG;
+  }
+  m->mat.threshold = threshold;
+  m->mt.threshold = threshold;
+  m->gkey = gf_mesh::GraphKey{};   // the captured step holds the material by value: capture again
   return GF_OK;
 }
 

@@ -1324,9 +1324,17 @@ __global__ void __launch_bounds__(kThreads) kb_integrate(const BatchTab* __restr
 
 }  // namespace
 
+// Quasi-static kernels: grid-stride over at most four CTAs per SM of the
+// current device (and never more CTAs than the reduction partials hold).
 inline unsigned qs_grid(int64_t n) {
+  static int sm_count[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& sms = sm_count[dev & 63];
+  if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+  const int64_t cap = std::min<int64_t>(4 * int64_t(sms), kMaxPartials);
   const int64_t b = (n + kThreads - 1) / kThreads;
-  return unsigned(b < 1 ? 1 : (b > 4 * 152 ? 4 * 152 : b));
+  return unsigned(b < 1 ? 1 : (b > cap ? cap : b));
 }
 int launch_qs_energy(const DevMesh& m, const Material& mt, const double* x, const double* f_ext, double* out,
                      cudaStream_t s) {

@@ -32,19 +32,20 @@ constexpr int kMaxDevices = 64;
 
 struct StaticState {
   double bb, rz, pq, rr, alpha, beta, tol2, true_rr;
+  double bad_cols, bad_diag;   // column ids out of range; free rows without an invertible diagonal block
   int32_t iters, maxit, done, status;
   unsigned tickets[4];
 };
 
 // scratch layout in doubles: r, z, p, q [3 * rows each], block-Jacobi [9 * rows],
-// reduction partials [4 * grid] (at most 4 values per CTA), solver state
+// reduction partials [5 * grid] (at most 5 values per CTA), solver state
 constexpr int64_t kOffR = 0;
 constexpr int64_t kOffZ = kOffR + 3 * kStaticMaxRows;
 constexpr int64_t kOffP = kOffZ + 3 * kStaticMaxRows;
 constexpr int64_t kOffQ = kOffP + 3 * kStaticMaxRows;
 constexpr int64_t kOffPinv = kOffQ + 3 * kStaticMaxRows;
 constexpr int64_t kOffPart = kOffPinv + 9 * kStaticMaxRows;
-constexpr int64_t kOffState = kOffPart + 4 * kSMaxGrid;
+constexpr int64_t kOffState = kOffPart + 5 * kSMaxGrid;
 constexpr int64_t kScratchDoubles = kOffState + (sizeof(StaticState) + 7) / 8;
 
 static __device__ __align__(256) double g_pcg_scratch[kScratchDoubles];
@@ -112,15 +113,16 @@ __device__ bool sreduce(double (&v)[NV], double* part, unsigned* ticket, double 
 
 __device__ __forceinline__ bool is_fixed(const SView& v, int64_t i) { return v.fixed && v.fixed[i]; }
 
-// r = b - A x on free rows; reference t = b - A x_fixed (free part of x taken as 0);
-// block-Jacobi inverses; z = P r; p = z
+// Free rows of x are not read: the solve starts from x = 0 there (written
+// below), so the caller may pass uninitialised values.  r = t = b - A x_fixed
+// on free rows; block-Jacobi inverses; z = P r; p = z.  Counts column ids out
+// of range and free rows whose diagonal block is missing or not invertible.
 __global__ void __launch_bounds__(kSThreads) ks_init(SView v) {
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};   // r.z, r.r, t.t, column ids out of range
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // r.z, r.r, t.t, bad columns, bad diagonals
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < v.n; i += int64_t(gridDim.x) * blockDim.x) {
     double r[3] = {0, 0, 0}, z[3] = {0, 0, 0};
     if (!is_fixed(v, i)) {
       double t[3] = {v.b[3 * i], v.b[3 * i + 1], v.b[3 * i + 2]};
-      double ax[3] = {0, 0, 0};
       const double* d = nullptr;
       for (int k = v.row_ptr[i]; k < v.row_ptr[i + 1]; ++k) {
         const int64_t j = v.col[k];
@@ -130,38 +132,39 @@ __global__ void __launch_bounds__(kSThreads) ks_init(SView v) {
         }
         const double* a = v.val + 9 * int64_t(k);
         if (j == i) d = a;
+        if (!is_fixed(v, j)) continue;   // free columns multiply the zero start
         const double x0 = v.x[3 * j], x1 = v.x[3 * j + 1], x2 = v.x[3 * j + 2];
-        const double y0 = a[0] * x0 + a[1] * x1 + a[2] * x2;
-        const double y1 = a[3] * x0 + a[4] * x1 + a[5] * x2;
-        const double y2 = a[6] * x0 + a[7] * x1 + a[8] * x2;
-        if (is_fixed(v, j)) {
-          t[0] -= y0;
-          t[1] -= y1;
-          t[2] -= y2;
-        } else {
-          ax[0] += y0;
-          ax[1] += y1;
-          ax[2] += y2;
-        }
+        t[0] -= a[0] * x0 + a[1] * x1 + a[2] * x2;
+        t[1] -= a[3] * x0 + a[4] * x1 + a[5] * x2;
+        t[2] -= a[6] * x0 + a[7] * x1 + a[8] * x2;
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r[c] = t[c] - ax[c];
+      for (int c = 0; c < 3; ++c) r[c] = t[c];
       double inv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      bool ok = false;
       if (d) {
         const double c00 = d[4] * d[8] - d[5] * d[7], c01 = d[2] * d[7] - d[1] * d[8], c02 = d[1] * d[5] - d[2] * d[4];
         const double c10 = d[5] * d[6] - d[3] * d[8], c11 = d[0] * d[8] - d[2] * d[6], c12 = d[2] * d[3] - d[0] * d[5];
         const double c20 = d[3] * d[7] - d[4] * d[6], c21 = d[1] * d[6] - d[0] * d[7], c22 = d[0] * d[4] - d[1] * d[3];
-        const double id = 1.0 / (d[0] * c00 + d[1] * c10 + d[2] * c20);
-        const double w[9] = {c00 * id, c01 * id, c02 * id, c10 * id, c11 * id, c12 * id, c20 * id, c21 * id, c22 * id};
+        const double det = d[0] * c00 + d[1] * c10 + d[2] * c20;
+        const double id = 1.0 / det;
+        ok = det != 0.0 && isfinite(id);
+        if (ok) {
+          const double w[9] = {c00 * id, c01 * id, c02 * id, c10 * id, c11 * id, c12 * id, c20 * id, c21 * id, c22 * id};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) inv[k] = w[k];
+          for (int k = 0; k < 9; ++k) inv[k] = w[k];
+        }
       }
+      if (!ok) acc[4] += 1.0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) v.pinv[9 * i + k] = inv[k];
 #pragma unroll
       for (int c = 0; c < 3; ++c) z[c] = inv[3 * c] * r[0] + inv[3 * c + 1] * r[1] + inv[3 * c + 2] * r[2];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[2] += t[c] * t[c];
+      for (int c = 0; c < 3; ++c) {
+        acc[2] += t[c] * t[c];
+        v.x[3 * i + c] = 0.0;
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -172,12 +175,14 @@ __global__ void __launch_bounds__(kSThreads) ks_init(SView v) {
       acc[1] += r[c] * r[c];
     }
   }
-  double out[4];
-  if (sreduce<4>(acc, v.part, &v.st->tickets[0], out) && threadIdx.x == 0) {
+  double out[5];
+  if (sreduce<5>(acc, v.part, &v.st->tickets[0], out) && threadIdx.x == 0) {
     StaticState* s = v.st;
     s->rz = out[0];
     s->rr = out[1];
     s->bb = out[2];
+    s->bad_cols = out[3];
+    s->bad_diag = out[4];
     s->iters = 0;
     s->status = GF_OK;
     s->done = (out[1] == 0.0 || out[1] <= s->tol2 * out[2]) ? 1 : 0;
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(kSThreads) ks_init(SView v) {
       s->status = GF_NAN;
       s->done = 1;
     }
-    if (out[3] > 0.0) {
+    if (out[3] > 0.0 || out[4] > 0.0) {
       s->status = GF_BAD_ARG;
       s->done = 1;
     }
@@ -392,7 +397,15 @@ extern "C" gf_status gf_bsr_pcg_solve_static(const int32_t* row_ptr, const int32
   if (rel_res) *rel_res = host.bb > 0 ? std::sqrt(host.true_rr / host.bb) : 0.0;
   gf_status status = gf_status(host.status);
   if (status == GF_OK && !host.done) status = GF_CG_MAXITER;
-  if (status == GF_BAD_ARG) set_last_error("static solve: a column index lies outside [0, n_rows)");
+  if (status == GF_BAD_ARG) {
+    std::string msg = "static solve:";
+    if (host.bad_cols > 0) msg += " " + std::to_string(int64_t(host.bad_cols)) + " column ids lie outside [0, n_rows);";
+    if (host.bad_diag > 0)
+      msg += " " + std::to_string(int64_t(host.bad_diag)) +
+             " free rows have no diagonal block or a singular one (block Jacobi needs its inverse);";
+    msg.pop_back();
+    set_last_error(msg);
+  }
   else if (status != GF_OK) set_last_error(std::string("static solve: ") + gf_status_string(status));
   return status;
 }

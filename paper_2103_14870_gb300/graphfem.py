@@ -75,7 +75,7 @@ class BatchTuning(ctypes.Structure):
 
 class MeshInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_nodes", "n_tets", "n_edges", "n_blocks", "n_colours",
-                                              "n_nbr_pairs", "device_bytes")]
+                                              "n_nbr_pairs", "device_bytes", "n_joint_entries", "n_union_rows")]
 
 
 _LIB = None
@@ -102,6 +102,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_step": (ctypes.c_int, [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int32,
                                    ctypes.POINTER(StepStats)]),
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
+        "gf_threshold_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_newton_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
         "gf_surface_sizes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -293,6 +294,10 @@ class Mesh:
     def refine_set(self, inner_rtol: float):
         _check(load_library().gf_refine_set(self._h, float(inner_rtol)))
 
+    def threshold_set(self, threshold: float):
+        """gf_threshold_set: the break threshold of Eq. 21 between steps."""
+        _check(load_library().gf_threshold_set(self._h, float(threshold)))
+
     def solver_set(self, rtol: float, maxit: int = 10000):
         _check(load_library().gf_solver_set(self._h, float(rtol), int(maxit)))
 
@@ -454,24 +459,41 @@ def mesh_plan(nodes, tets, mat: Material) -> dict:
     return out
 
 
+def _static_solve_args(row_ptr, col, values, b, x, fixed, device: int, stream_device):
+    """Argument checks of bsr_pcg_solve_static (plain attribute access, so the
+    CPU suite can run them with stand-in objects).  The C entry point launches
+    on the current device with that device's scratch array, so every tensor and
+    the stream must live there."""
+    import torch
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col", col, torch.int32), ("values", values, torch.float64),
+                        ("b", b, torch.float64), ("x", x, torch.float64), ("fixed", fixed, torch.uint8)):
+        if t is None and name == "fixed":
+            continue
+        if not (_is_torch_cuda(t) and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"{name}: expected a contiguous CUDA tensor of {dt}")
+        if t.device.index != device:
+            raise ValueError(f"{name} lives on cuda:{t.device.index}, but the current device is cuda:{device}")
+    if stream_device is not None and stream_device != device:
+        raise ValueError(f"the stream belongs to cuda:{stream_device}, but the current device is cuda:{device}")
+    n_rows = row_ptr.numel() - 1
+    if b.numel() != 3 * n_rows or x.numel() != 3 * n_rows or (fixed is not None and fixed.numel() != n_rows):
+        raise ValueError("b and x need 3 * n_rows entries, fixed n_rows")
+    return n_rows
+
+
 def bsr_pcg_solve_static(row_ptr, col, values, b, x, fixed=None, rtol: float = 1e-6, maxit: int = 10000,
                          stream=None):
     """gf_bsr_pcg_solve_static: solve a block-CSR system without any device
     allocation (for callers that must not allocate while solving).  All arrays
-    are CUDA tensors on the current device; x is overwritten with the solution.
-    Returns (iterations, relative residual)."""
+    are contiguous CUDA tensors on the current device; x holds the prescribed
+    values on fixed rows (free rows are not read) and is overwritten with the
+    solution.  Returns (iterations, relative residual)."""
     import torch
-    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col", col, torch.int32), ("values", values, torch.float64),
-                        ("b", b, torch.float64), ("x", x, torch.float64)):
-        if not (_is_torch_cuda(t) and t.dtype == dt and t.is_contiguous()):
-            raise TypeError(f"{name}: expected a contiguous CUDA tensor of {dt}")
-    if fixed is not None and not (_is_torch_cuda(fixed) and fixed.dtype == torch.uint8):
-        raise TypeError("fixed: expected a CUDA uint8 tensor")
-    n_rows = row_ptr.numel() - 1
-    if b.numel() != 3 * n_rows or x.numel() != 3 * n_rows or (fixed is not None and fixed.numel() != n_rows):
-        raise ValueError("b and x need 3 * n_rows entries, fixed n_rows")
+    device = torch.cuda.current_device()
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(device)
+    stream_device = stream.device.index if hasattr(stream, "device") else None
+    n_rows = _static_solve_args(row_ptr, col, values, b, x, fixed, device, stream_device)
     sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     it = ctypes.c_int32(0)
     rel = ctypes.c_double(0.0)

@@ -1,9 +1,10 @@
-"""Full-size parity on the 620k-tet loaf, in the configuration bench.py times
-(FP64, CG to 1e-6).  The oracle cannot step the whole mesh in seconds, so it
-recomputes sampled outputs one by one: four compact regions of tets, whose
-edge drivers and labels (Eq. 20-21), chi (Eq. 25), and the matrix rows and
-right-hand sides of their interior nodes (Eq. 2, 12, 32-34) it evaluates from
-the same start state.  Properties that hold at any size are checked on the
+"""Full-size parity on the 620k-tet loaf mesh, in the configurations bench.py
+times: the ductile loaf in FP64 and mixed precision, and the brittle glass
+point impact in mixed precision, CG to 1e-6.  The oracle cannot step the whole
+mesh in seconds, so it recomputes sampled outputs one by one: four compact
+regions of tets, whose edge drivers and labels (Eq. 20-21), chi (Eq. 25), and
+the matrix rows and right-hand sides of their interior nodes (Eq. 2, 12,
+32-34) it evaluates from the same start state.  Properties that hold at any size are checked on the
 whole mesh: the solver residual recomputed on the host from the GPU's own
 system, the position update, and monotone labels."""
 import numpy as np
@@ -12,7 +13,7 @@ import scipy.sparse as sp
 
 from helpers import LABEL_BAND, assert_close, assert_norm_close
 from oracle import damage, elastic, mesh as omesh
-from workloads import loaf_config
+from workloads import glass_config, loaf_config
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -22,22 +23,37 @@ if not torch.cuda.is_available():
 import paper_2103_14870_gb300 as gf  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def loaf():
-    w = loaf_config()
-    rng = np.random.default_rng(21)
+def seeded_state(w, seed, strain, speed, broken):
+    """A smooth seeded displacement field of the given strain scale, random
+    velocities and a random 0.3% (``broken``) of edges already broken."""
+    rng = np.random.default_rng(seed)
     X = w.nodes
     L = X.max(0) - X.min(0)
     u = np.zeros_like(X)
     ph = rng.uniform(0, 2 * np.pi, size=(3, 3))
     for c in range(3):
         for d in range(3):
-            u[:, c] += 0.004 * L[d] / 6 * np.sin(2 * np.pi * X[:, d] / L[d] + ph[c, d])
-    x = X + u + 1e-4 * rng.normal(size=X.shape)
-    v = 0.01 * rng.normal(size=X.shape)
+            u[:, c] += strain * L[d] / 6 * np.sin(2 * np.pi * X[:, d] / L[d] + ph[c, d])
+    x = X + u + 0.025 * strain * rng.normal(size=X.shape)
+    v = speed * rng.normal(size=X.shape)
     edges, tet_edges = omesh.edges_of(w.tets)
-    labels0 = (rng.uniform(size=len(edges)) < 0.003).astype(np.uint8)
-    return w, x, v, edges, tet_edges, labels0
+    labels0 = (rng.uniform(size=len(edges)) < broken).astype(np.uint8)
+    return x, v, edges, tet_edges, labels0
+
+
+@pytest.fixture(scope="module")
+def loaf():
+    w = loaf_config()
+    return (w,) + seeded_state(w, 21, 0.004, 0.01, 0.003)
+
+
+@pytest.fixture(scope="module")
+def glass():
+    """The brittle glass configuration: the loaf mesh, E = 7e10, nu = 0.22,
+    rho = 2500, the lowest 5% of nodes pinned and a 1e4 N point impact at the
+    top apex; a state at glass-like strains (1e-5)."""
+    w = glass_config()
+    return (w,) + seeded_state(w, 23, 1e-5, 1e-4, 0.003)
 
 
 def oracle_region_state(w, x, labels, edges, tet_edges, centres, lam, mu, radius):
@@ -87,21 +103,48 @@ def test_loaf_fullsize_sampled_parity(loaf, precision):
     matrix rows and rhs: FP32 strains from displacement differences carry ~1e-6
     relative error, and the edge-space sums forming a nodal force amplify it
     about tenfold on single entries."""
+    sampled_parity(loaf, precision)
+
+
+def test_glass_fullsize_sampled_parity(glass):
+    """The glass point impact in mixed precision on the full mesh, at the 1e-5
+    bar of reduced precision: sampled drivers, labels, chi, matrix rows and
+    rhs against the oracle, and the FP64-accurate solve residual over the free
+    DOFs with the bottom nodes pinned."""
+    w = glass[0]
+    stats = sampled_parity(glass, "mixed", pinned=w.pinned)
+    assert stats["cg_iters"] > 2 * stats["refine_sweeps"]     # the stiff case: many inner iterations
+
+
+def threshold_in_gap(drv, q):
+    """A threshold near the q-quantile of the sampled drivers, at the middle of
+    the widest relative gap among the 41 sorted drivers around it, so that no
+    sampled driver lies within the label band of it and the labels, chi and
+    system of the sampled tets must agree exactly."""
+    d = np.sort(drv[np.isfinite(drv)])
+    k = int(q * (len(d) - 1))
+    lo, hi = max(k - 20, 0), min(k + 20, len(d) - 1)
+    gaps = (d[lo + 1:hi + 1] - d[lo:hi]) / np.abs(d[lo + 1:hi + 1])
+    i = lo + int(np.argmax(gaps))
+    return float(0.5 * (d[i] + d[i + 1]))
+
+
+def sampled_parity(case, precision, pinned=None):
     tol = TOL[precision]
-    w, x, v, edges, tet_edges, labels0 = loaf
+    w, x, v, edges, tet_edges, labels0 = case
     lam, mu = elastic.lame(w.young, w.poisson)
     rng = np.random.default_rng(7)
     centres = w.nodes[rng.choice(w.n_nodes, 4, replace=False)]
     reg = oracle_region_state(w, x, labels0, edges, tet_edges, centres, lam, mu, w.radius)
     E_s, T_s = reg["E_s"], reg["T_s"]
-    theta = float(np.quantile(reg["driver"][E_s], 0.9))
+    theta = threshold_in_gap(reg["driver"][E_s], 0.9)
     m = gf.mesh_create(w.nodes, w.tets, gf.material(w.young, w.poisson, w.density, threshold=theta,
                                                     radius=w.radius), cg_rtol=1e-6,
                        precision=gf.MIXED if precision == "mixed" else gf.FP64)
     np.testing.assert_array_equal(m.edges_get(), edges)
     m.state_set(x=x.ravel(), v=v.ravel(), labels=labels0)
     f = w.f_ext
-    stats = m.step(w.dt, f.ravel())
+    stats = m.step(w.dt, f.ravel(), pinned)
     assert stats["status"] == 0
     drv, lab = m.damage_get()
     # (1) drivers and labels of the sampled edges
@@ -130,7 +173,10 @@ def test_loaf_fullsize_sampled_parity(loaf, precision):
     in_s[T_s] = True
     node_all_in = np.ones(w.n_nodes, bool)
     np.logical_and.at(node_all_in, tets.ravel(), np.repeat(in_s, 4))
-    N_s = np.nonzero(node_all_in & np.isin(np.arange(w.n_nodes), tets[T_s].ravel()))[0]
+    free = np.ones(w.n_nodes, bool)
+    if pinned is not None:
+        free[pinned] = False
+    N_s = np.nonzero(node_all_in & free & np.isin(np.arange(w.n_nodes), tets[T_s].ravel()))[0]
     assert len(N_s) >= 4
     V, D2, q = omesh.rest_geometry(w.nodes, tets[T_s])
     Ke = elastic.element_tangent(x, tets[T_s], V, D2, q, lam, mu, chi_s)
@@ -168,15 +214,21 @@ def test_loaf_fullsize_sampled_parity(loaf, precision):
         assert_close(np.array(got_b), np.array(want_bs), rtol=tol["rtol"], floor=tol["floor_b"], what="rhs rows")
     else:
         assert_norm_close(np.array(got_b), np.array(want_bs), rtol=tol["rtol"], what="rhs rows (mixed)")
-    # (4) the solve: residual recomputed on the host from the GPU's own system
+    # (4) the solve: residual over the free DOFs recomputed on the host from the
+    # GPU's own system, relative to b_free = b - A_fp dv_p (prescribed rows)
     rows = np.repeat(np.arange(w.n_nodes), np.diff(rp))
     r3 = (3 * rows[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
     c3 = (3 * col[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
     A = sp.csr_matrix((val.ravel(), (r3.ravel(), c3.ravel())), shape=(3 * w.n_nodes, 3 * w.n_nodes))
     v_new = m.velocities_get()
     dv = v_new - v.ravel()
-    res = np.linalg.norm(rhs - A @ dv) / np.linalg.norm(rhs)
+    fr = np.repeat(free, 3)
+    np.testing.assert_array_equal(v_new.reshape(-1, 3)[~free], 0.0)      # prescribed: at rest
+    dvp = np.where(fr, 0.0, dv)
+    res = np.linalg.norm((rhs - A @ dv)[fr]) / np.linalg.norm((rhs - A @ dvp)[fr])
     assert res <= 1e-6
     assert abs(res - stats["rel_res"]) <= 1e-3 * res + 1e-15
     # (5) position update x_new = x + dt v_new
     np.testing.assert_allclose(m.positions_get(), x.ravel() + dt * v_new, rtol=1e-15, atol=1e-15)
+    m.close()
+    return stats

@@ -90,7 +90,8 @@ def test_mixed_residual_is_fp64_accurate():
 
 def test_mixed_stiff_glass_material():
     """Glass-like stiffness (E = 7e10, rho = 2500) on the beam: many CG
-    iterations; the refinement still reaches 1e-8 and tracks the FP64 oracle."""
+    iterations.  Each step starts from the oracle's state, and the mixed step
+    matches the oracle's step at the reduced-precision bar of 1e-5."""
     from workloads import Workload
     b = beam_config()
     w = Workload("beam_glass", b.nodes, b.tets, 7e10, 0.22, 2500.0, 5e-4, 3, math.inf, 1.5,
@@ -99,10 +100,13 @@ def test_mixed_stiff_glass_material():
     m = mixed_mesh(w, gpu_material(gf, w), rtol=1e-8)
     st = model.rest_state()
     for k in range(3):
+        m.state_set(x=st.x.ravel(), v=st.v.ravel(), labels=st.labels, chi=st.chi)
         s = m.step(w.dt, w.f_ext.ravel(), w.pinned)
-        st, info = model.step(st, w.dt, w.f_ext, w.pinned)
+        new, info = model.step(st, w.dt, w.f_ext, w.pinned)
         assert s["status"] == 0 and s["rel_res"] <= 1e-8 and s["cg_iters"] > 10
-    assert_norm_close(m.velocities_get(), st.v, rtol=1e-4, what="v (glass, mixed, 3 steps)")
+        assert_norm_close(m.velocities_get(), new.v, rtol=RTOL32, what=f"v (glass, mixed, step {k})")
+        assert_positions_close(m.positions_get(), new.x, st.x, rtol=RTOL32, noise=1e-7, what=f"x (glass, step {k})")
+        st = new
 
 
 def test_mixed_resume_bit_identical_and_rest():
