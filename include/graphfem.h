@@ -183,10 +183,30 @@ gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* 
  * the same bits as GF_STEP_STREAM, which launches kernel by kernel with a host
  * check per chunk of solver iterations (and is what the other steps use). */
 enum { GF_STEP_GRAPH = 0, GF_STEP_STREAM = 1 };
+/* solve_loop: the form of the solver loop.
+ * GF_SOLVE_KERNELS (0, default): kernel by kernel, three per PCG iteration
+ * (GF_FP64) or the refinement's phase kernels (GF_MIXED), as a WHILE node of
+ * the step graph or with host checks in the stream form.
+ * GF_SOLVE_CG (GF_FP64 only): the PCG in the Chronopoulos-Gear form (Chronopoulos
+ * and Gear, 1989): w = A z and the three dot products in one kernel, the vector
+ * updates in another, one grid reduction per iteration; the iterates equal the
+ * three-kernel form's in exact arithmetic.
+ * GF_SOLVE_PERSISTENT (GF_MIXED only): the whole refinement loop as one
+ * cooperative launch (one CTA set resident on every SM), with grid barriers
+ * between its phases and the direction update fused into the SpMV.  Each barrier
+ * wait gives up after 1 s and the step then returns GF_TIMEOUT (the mesh state
+ * is then unspecified: set it again with gf_state_set).
+ * Another form than the precision supports -> GF_UNSUPPORTED.
+ * wait_test: a test hook; 1 makes one CTA of the next persistent solve skip its
+ * first barrier arrival, so that every wait of that barrier runs out (the
+ * step returns GF_TIMEOUT after about 1 s).  Leave it 0. */
+enum { GF_SOLVE_KERNELS = 0, GF_SOLVE_PERSISTENT = 1, GF_SOLVE_CG = 2 };
 typedef struct gf_tuning {
   int32_t assembly;
   int32_t step_launch;   /* GF_STEP_GRAPH (0, default) or GF_STEP_STREAM */
-  int32_t reserved[6];   /* set to 0 */
+  int32_t solve_loop;    /* GF_SOLVE_KERNELS (default), GF_SOLVE_CG or GF_SOLVE_PERSISTENT */
+  int32_t wait_test;     /* test hook, 0 */
+  int32_t reserved[4];   /* set to 0 */
 } gf_tuning;
 gf_status gf_tuning_set(gf_mesh* mesh, const gf_tuning* tuning);
 gf_status gf_tuning_get(const gf_mesh* mesh, gf_tuning* tuning);
@@ -351,7 +371,12 @@ typedef struct gf_batch_tuning {
                            meshes by node count (at least 1 CTA each, at most the single-mesh grid);
                            converged meshes then cost few early-exit CTAs per iteration, and the
                            per-mesh reductions sum in a different (still fixed) order. */
-  int32_t reserved[5];  /* set to 0 */
+  int32_t solve_loop;   /* GF_SOLVE_KERNELS (0, default): per-kind launches (graph WHILE node or
+                           stream, as `graph` says).  GF_SOLVE_PERSISTENT (GF_MIXED batches): the
+                           whole solve of every member as one cooperative launch whose phases take
+                           only the blocks of the meshes still iterating (members step bit-identically
+                           to single-mesh persistent steps).  GF_FP64 batches use the kernels. */
+  int32_t reserved[4];  /* set to 0 */
 } gf_batch_tuning;
 
 /* meshes: n handles (1 <= n <= 256), same device and precision.  The batch

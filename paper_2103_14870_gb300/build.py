@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgraphfem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["host_mesh.cpp", "kernels_fp64.cu", "kernels_mixed.cu", "kernels_gnn.cu", "kernels_tc.cu", "kernels_surface.cu",
-           "capi.cu",
+           "capi.cu", "solve_persist.cu",
            "solve_static.cu"]
 
 

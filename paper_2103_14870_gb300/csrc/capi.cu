@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -96,12 +97,12 @@ namespace {
 
 enum ProfGroup : int {
   kPStress = 0, kPNonlocal, kPEdge, kPChi, kPAssemble, kPPcgInit, kPSpmv, kPPcgUpdate, kPPcgP, kPResidual,
-  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPGnn, kPGather, kPCount
+  kPIntegrate, kPIrResidual, kPIrInit, kPIrApply, kPGnn, kPGather, kPSolve, kPCount
 };
 const char* kProfNames[kPCount] = {"tet_stress",  "nonlocal_avg", "edge_driver", "tet_chi",     "assemble",
                                    "pcg_init",    "pcg_spmv",     "pcg_update",  "pcg_p",       "true_residual",
                                    "integrate",   "ir_residual",  "ir_inner_init", "ir_apply",
-                                   "gnn",         "assemble_gather"};
+                                   "gnn",         "assemble_gather", "solve_persistent"};
 
 __global__ void k_fill(double* p, int64_t n, double v) {
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -203,6 +204,11 @@ struct gf_mesh {
   int* h_loops = nullptr;                  // pinned mirror
   void* h_init = nullptr;                  // pinned solver-state initialiser read by the graph
   int64_t g_prefix = 0, g_body = 0, g_suffix = 0;
+
+  // persistent solve (GF_MIXED, GF_SOLVE_PERSISTENT): a one-mesh table and its control block
+  BatchTab* ptab = nullptr;
+  PersistCtl* pctl = nullptr;
+  PersistCtl* h_pctl = nullptr;            // pinned host mirror of the control block's head
 
   bool prof = false;
   double prof_ms[kPCount] = {};
@@ -576,7 +582,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
         (st = scratch(m, 70 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
         (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
-        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
+        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.p32b)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
         (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) ||
         (st = scratch(m, 1, &x.ir)))
       return fail(st);
@@ -734,6 +740,15 @@ gf_status gf_tuning_set(gf_mesh* m, const gf_tuning* t) {
     set_last_error("bad tuning (step_launch must be GF_STEP_GRAPH or GF_STEP_STREAM)");
     return GF_BAD_ARG;
   }
+  if ((t->solve_loop != GF_SOLVE_KERNELS && t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_CG) ||
+      (t->wait_test != 0 && t->wait_test != 1)) {
+    set_last_error("bad tuning (solve_loop must be GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT or GF_SOLVE_CG, wait_test 0 or 1)");
+    return GF_BAD_ARG;
+  }
+  if ((t->solve_loop == GF_SOLVE_PERSISTENT && !m->mixed) || (t->solve_loop == GF_SOLVE_CG && m->mixed)) {
+    set_last_error("GF_SOLVE_PERSISTENT is built for GF_MIXED meshes, GF_SOLVE_CG for GF_FP64 meshes");
+    return GF_UNSUPPORTED;
+  }
   m->tune = *t;
   m->gkey = gf_mesh::GraphKey{};   // capture again on the next step
   return GF_OK;
@@ -796,6 +811,57 @@ namespace {
 int64_t gnn_step_start(gf_gnn* g, const DevMesh& d, int flags, cudaStream_t s);
 cudaError_t gnn_keep_previous(gf_gnn* g, const DevMesh& d, cudaStream_t s);
 
+// The one-mesh table and control block of the persistent solve (allocated and
+// uploaded on first use, outside any stream capture: the table's pointers and
+// block counts do not change for the life of the mesh).
+// Blocks of a mesh in one phase of the persistent solve: the kernel form's
+// grid, at most one CTA set of the persistent launch (so a lone mesh's phase
+// is one balanced wave).  The same for a mesh alone and in a batch.
+unsigned persist_blocks(int kind, unsigned blocks) {
+  const bool solve_kind = kind == kB_ir_inner_init || kind == kB_ir_spmv || kind == kB_ir_update ||
+                          kind == kB_ir_apply || kind == kB_ir_residual;
+  const unsigned g = persist_grid();
+  return (solve_kind && g > 0 && blocks > g) ? g : blocks;
+}
+
+gf_status persist_setup(gf_mesh* m) {
+  if (m->ptab) return GF_OK;
+  gf_status st = GF_OK;
+  void* p = nullptr;
+  if ((st = dev_alloc(m, sizeof(BatchTab), &p)) != GF_OK) return st;
+  BatchTab* dt = static_cast<BatchTab*>(p);
+  if ((st = dev_alloc(m, sizeof(PersistCtl), &p)) != GF_OK) return st;
+  PersistCtl* ctl = static_cast<PersistCtl*>(p);
+  if (!m->h_pctl) GF_CK(cudaMallocHost(&m->h_pctl, sizeof(PersistCtl)));
+  std::unique_ptr<BatchTab> h(new BatchTab());
+  h->n = 1;
+  h->mesh[0] = m->dm;
+  h->mt[0] = m->mt;
+  h->sp[0] = step_scalars(m->mt, 1.0, false, 0, false);
+  for (int kind = 0; kind < kBKinds; ++kind) {
+    h->off[kind][0] = 0;
+    h->off[kind][1] = int32_t(persist_blocks(kind, launch_dims(kind, h->mesh[0], h->mt[0], h->sp[0]).blocks));
+  }
+  GF_CK(cudaMemcpyAsync(dt, h.get(), sizeof(BatchTab), cudaMemcpyHostToDevice, m->stream));
+  GF_CK(cudaStreamSynchronize(m->stream));
+  m->ptab = dt;
+  m->pctl = ctl;
+  return GF_OK;
+}
+
+bool persist_on(const gf_mesh* m) { return m->mixed && m->tune.solve_loop == GF_SOLVE_PERSISTENT; }
+
+// GF_SOLVE_CG (GF_FP64): the Chronopoulos-Gear PCG needs the vector w = A z
+bool cg_form_on(const gf_mesh* m) { return !m->mixed && m->tune.solve_loop == GF_SOLVE_CG; }
+gf_status cg_form_setup(gf_mesh* m, DevMesh& d) {
+  if (!m->qs_w) {
+    gf_status st = scratch(m, 3 * size_t(d.N), &m->qs_w);
+    if (st != GF_OK) return st;
+  }
+  d.w = m->qs_w;
+  return GF_OK;
+}
+
 // FP64 path: damage, two-phase (or colour-ordered) assembly, projected PCG (all FP64).
 // Newton iterations after the first re-assemble at x^k = x + dt v^k with the
 // same kernels (see k_newton_prep) and warm-start the PCG from the previous dv.
@@ -838,11 +904,22 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
     return GF_OK;
   };
   // PCG on the assembled system from the dv in place; returns after convergence or maxit
+  const bool cg_form = cg_form_on(m);
+  if (cg_form) {
+    gf_status st = cg_form_setup(m, d);
+    if (st != GF_OK) return st;
+  }
   auto run_pcg = [&]() -> gf_status {
     int launched_iters = 0;
     int chunk = std::max(1, std::min(m->last_iters + 1, 64));
+    if (cg_form) { Prof p(m, kPSpmv, 0); L += launch_qs_cg_spmv(d, s); }   // w = A z, coefficients
     for (;;) {
       for (int j = 0; j < chunk; ++j, ++launched_iters) {
+        if (cg_form) {   // Chronopoulos-Gear: updates, then the next w = A z with the coefficients
+          { Prof p(m, kPPcgUpdate, launched_iters); L += launch_qs_cg_update(d, s); }
+          { Prof p(m, kPSpmv, launched_iters + 1); L += launch_qs_cg_spmv(d, s); }
+          continue;
+        }
         { Prof p(m, kPSpmv, launched_iters); L += launch_kind(kB_pcg_spmv, d, mt, sp, s); }
         { Prof p(m, kPPcgUpdate, launched_iters); L += launch_kind(kB_pcg_update, d, mt, sp, s); }
         { Prof p(m, kPPcgP, launched_iters); L += launch_kind(kB_pcg_p, d, mt, sp, s); }
@@ -947,6 +1024,23 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   L += launch_kind(kB_set_pinned, d, mt, sp, s);
   L += launch_kind(kB_refresh32, d, mt, sp, s);
   { Prof p(m, kPIrResidual); L += launch_kind(kB_ir_residual, d, mt, sp, s, 1); }
+  if (persist_on(m)) {
+    int n;
+    {
+      Prof p(m, kPSolve);
+      n = launch_ir_persist(m->ptab, 1, m->pctl, 2 * m->opt.cg_maxit + 64, m->tune.wait_test, s);
+    }
+    if (n < 0) {
+      set_last_error("the cooperative launch of the persistent solve was refused");
+      return GF_CUDA_ERR;
+    }
+    L += n;
+    GF_CK(cudaMemcpyAsync(m->h_pctl, m->pctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    { Prof p(m, kPIntegrate); L += launch_kind(kB_integrate32, d, mt, sp, s); }
+    GF_CK(cudaGetLastError());
+    GF_CK(cudaMemcpyAsync(m->h_ir, d.mx.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+    return GF_OK;
+  }
   int max_inner = 0;
   for (int round = 0;; ++round) {
     for (int sw = 0; sw < 2; ++sw) {
@@ -993,8 +1087,10 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
   if (!m->body_stream) GF_CK(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
   cudaGraph_t g;
   GF_CK(cudaGraphCreate(&g, 0));
-  cudaGraphConditionalHandle h;
-  GF_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  // the persistent solve needs no WHILE node, and a graph may hold no unused conditional handle
+  const bool persist = m->mixed && persist_on(m);
+  cudaGraphConditionalHandle h{};
+  if (!persist) GF_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
   GF_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   int64_t L = 0;
   GF_CK(cudaMemsetAsync(m->d_loops, 0, sizeof(int), s));
@@ -1020,6 +1116,28 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
     L += launch_kind(kB_ir_residual, d, mt, sp, s, 1);
   } else {
     L += launch_kind(kB_pcg_init, d, mt, sp, s);
+    if (cg_form_on(m)) L += launch_qs_cg_spmv(d, s);   // w = A z and the first coefficients
+  }
+  if (persist) {   // the whole solve as one cooperative launch: no WHILE node
+    const int n = launch_ir_persist(m->ptab, 1, m->pctl, 2 * m->opt.cg_maxit + 64, m->tune.wait_test, s);
+    if (n < 0) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(s, &dead);
+      if (dead) cudaGraphDestroy(dead);
+      cudaGraphDestroy(g);
+      set_last_error("the cooperative launch of the persistent solve could not be captured");
+      return GF_CUDA_ERR;
+    }
+    L += n;
+    GF_CK(cudaMemcpyAsync(m->h_pctl, m->pctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    L += launch_kind(kB_integrate32, d, mt, sp, s);
+    m->g_prefix = L;
+    m->g_body = 0;
+    m->g_suffix = 0;
+    GF_CK(cudaStreamEndCapture(s, &g));
+    m->graph = g;
+    GF_CK(cudaGraphInstantiate(&m->graph_exec, g, 0));
+    return GF_OK;
   }
   m->g_prefix = L;
   cudaStreamCaptureStatus cs;
@@ -1049,6 +1167,13 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
     }
     cap = 4096;
     k_step_cond<<<1, 32, 0, bs>>>(nullptr, d.mx.ir, m->d_loops, cap, h);
+  } else if (cg_form_on(m)) {
+    for (int j = 0; j < loop; ++j) {
+      L += launch_qs_cg_update(d, bs);
+      L += launch_qs_cg_spmv(d, bs);
+    }
+    cap = m->opt.cg_maxit / loop + 2;
+    k_step_cond<<<1, 32, 0, bs>>>(d.pcg, nullptr, m->d_loops, cap, h);
   } else {
     for (int j = 0; j < loop; ++j)
       for (int kind : {kB_pcg_spmv, kB_pcg_update, kB_pcg_p}) L += launch_kind(kind, d, mt, sp, bs);
@@ -1113,6 +1238,14 @@ gf_status step_graph(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   // a key that differs from the captured one only in the mixed loop length keeps the graph
   gf_mesh::GraphKey cmp = key;
   if (m->mixed && m->graph_exec) cmp.loop = m->gkey.loop;
+  if (persist_on(m)) {
+    gf_status st = persist_setup(m);
+    if (st != GF_OK) return st;
+  }
+  if (cg_form_on(m)) {
+    gf_status st = cg_form_setup(m, d);
+    if (st != GF_OK) return st;
+  }
   if (!m->graph_exec || !(cmp == m->gkey)) {
     gf_status st = build_step_graph(m, d, sp, key.loop);
     if (st != GF_OK) {
@@ -1172,6 +1305,11 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
     }
   }
   int64_t L = 0;
+  const bool persist = persist_on(m);
+  if (persist && !graph) {
+    gf_status ps = persist_setup(m);
+    if (ps != GF_OK) return ps;
+  }
   gf_status st = graph ? step_graph(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr)
                  : m->mixed ? step_mixed(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L)
                             : step_fp64(m, d, dt, f_ext != nullptr, n_pinned, pinned_vel != nullptr, L);
@@ -1210,6 +1348,12 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
     rel = ps.bb > 0 ? std::sqrt(ps.true_rr / ps.bb) : 0.0;
   }
   if (status == GF_OK && !std::isfinite(rel)) status = GF_NAN;
+  if (persist && m->h_pctl->error != 0) {
+    // a phase cut short may leave reduction tickets counted: clear them for the next step
+    GF_CK(cudaMemsetAsync(d.tickets, 0, sizeof(unsigned) * kTickets, s));
+    GF_CK(cudaStreamSynchronize(s));
+    status = GF_TIMEOUT;
+  }
   if (status == GF_OK && m->h_cnt[kCntTcTimeout] != 0) {
     set_last_error("a tensor-core wait of the network gave up (device timeout)");
     status = GF_TIMEOUT;
@@ -1742,6 +1886,8 @@ struct gf_batch {
   cudaGraphExec_t exec = nullptr;
   gf_batch_tuning tune{};
   int cap = 0;
+  PersistCtl* pctl = nullptr;        // control block of the persistent solve
+  PersistCtl* h_pctl = nullptr;      // pinned mirror of its head
   int64_t launches = 0;
   int64_t prefix_kernels = 0, body_kernels = 0, suffix_kernels = 0;
 };
@@ -1760,6 +1906,8 @@ void batch_free(gf_batch* b) {
   if (b->hout) cudaFreeHost(b->hout);
   if (b->h_iter) cudaFreeHost(b->h_iter);
   if (b->body_stream) cudaStreamDestroy(b->body_stream);
+  if (b->pctl) cudaFree(b->pctl);
+  if (b->h_pctl) cudaFreeHost(b->h_pctl);
 }
 
 const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64, kB_diag64,
@@ -1800,6 +1948,16 @@ int64_t enqueue_body(gf_batch* b, cudaStream_t s) {
   return enqueue_kinds(b, kBodyFp64, s);
 }
 
+bool batch_persist(const gf_batch* b) { return b->mixed && b->tune.solve_loop == GF_SOLVE_PERSISTENT; }
+
+// the whole solve of every member as one cooperative launch (after the prefix)
+int64_t enqueue_persist(gf_batch* b, cudaStream_t s) {
+  const int n = launch_ir_persist(b->dtab, b->n, b->pctl, b->cap, 0, s);
+  if (n < 0) return -1;
+  if (cudaMemcpyAsync(b->h_pctl, b->pctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+  return n;
+}
+
 int64_t enqueue_suffix(gf_batch* b, cudaStream_t s) {
   int64_t L = b->mixed ? enqueue_kinds(b, kSuffixMixed, s) : enqueue_kinds(b, kSuffixFp64, s);
   kb_collect<<<unsigned((b->n + 127) / 128), 128, 0, s>>>(b->dtab, b->mixed ? 1 : 0, b->dout);
@@ -1823,10 +1981,30 @@ gf_status build_graph(gf_batch* b) {
   b->graph = nullptr;
   cudaGraph_t g;
   GB_CK(cudaGraphCreate(&g, 0));
-  cudaGraphConditionalHandle h;
-  GB_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphConditionalHandle h{};
+  if (!batch_persist(b)) GB_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
   GB_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   b->prefix_kernels = enqueue_prefix(b, s);
+  if (batch_persist(b)) {   // no WHILE node: the solve loop runs inside one cooperative launch
+    const int64_t np = enqueue_persist(b, s);
+    if (np < 0) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(s, &dead);
+      if (dead) cudaGraphDestroy(dead);
+      cudaGraphDestroy(g);
+      set_last_error("the cooperative launch of the persistent solve could not be captured");
+      return GF_CUDA_ERR;
+    }
+    b->prefix_kernels += np;
+    b->body_kernels = 0;
+    GB_CK(cudaMemsetAsync(b->d_iter, 0, sizeof(int), s));
+    b->suffix_kernels = enqueue_suffix(b, s);
+    GB_CK(cudaMemcpyAsync(b->h_iter, b->d_iter, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamEndCapture(s, &g));
+    GB_CK(cudaGraphInstantiate(&b->exec, g, 0));
+    b->graph = g;
+    return GF_OK;
+  }
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
   const cudaGraphEdgeData* ed = nullptr;
@@ -1894,6 +2072,7 @@ gf_status batch_prepare(gf_batch* b, double dt, const double* const* f_ext, cons
     b->htab->off[kind][0] = 0;
     for (int k = 0; k < b->n; ++k) {
       int64_t blocks = launch_dims(kind, b->htab->mesh[k], b->htab->mt[k], b->htab->sp[k]).blocks;
+      if (batch_persist(b)) blocks = persist_blocks(kind, unsigned(blocks));
       if (loop_kind && budget > 0 && blocks > 0)
         blocks = std::min(blocks, std::max<int64_t>(1, (budget * b->htab->mesh[k].N + n_sum - 1) / n_sum));
       acc += int32_t(blocks);
@@ -1929,6 +2108,18 @@ gf_status batch_run(gf_batch* b, gf_step_stats* stats) {
     GB_CK(cudaMemcpyAsync(b->hout, b->dout, sizeof(BatchOut) * b->n, cudaMemcpyDeviceToHost, s));
     GB_CK(cudaStreamSynchronize(s));
     L = b->prefix_kernels + b->suffix_kernels + int64_t(*b->h_iter) * b->body_kernels;
+  } else if (batch_persist(b)) {
+    L += enqueue_prefix(b, s);
+    const int64_t np = enqueue_persist(b, s);
+    if (np < 0) {
+      set_last_error("the cooperative launch of the persistent solve was refused");
+      return GF_CUDA_ERR;
+    }
+    L += np;
+    L += enqueue_suffix(b, s);
+    GB_CK(cudaGetLastError());
+    GB_CK(cudaMemcpyAsync(b->hout, b->dout, sizeof(BatchOut) * b->n, cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));
   } else {
     L += enqueue_prefix(b, s);
     const int chunk = b->tune.chunk > 0 ? b->tune.chunk : 8;
@@ -1950,6 +2141,11 @@ gf_status batch_run(gf_batch* b, gf_step_stats* stats) {
     GB_CK(cudaStreamSynchronize(s));
   }
   b->launches += L;
+  const bool timed_out = batch_persist(b) && b->h_pctl->error != 0;
+  if (timed_out) {   // a phase cut short may leave reduction tickets counted: clear them
+    for (int k = 0; k < b->n; ++k) GB_CK(cudaMemsetAsync(b->ms[k]->dm.tickets, 0, sizeof(unsigned) * kTickets, s));
+    GB_CK(cudaStreamSynchronize(s));
+  }
   gf_status first_bad = GF_OK;
   for (int k = 0; k < b->n; ++k) {
     const BatchOut& o = b->hout[k];
@@ -1967,6 +2163,7 @@ gf_status batch_run(gf_batch* b, gf_step_stats* stats) {
       st.rel_res = o.pcg.bb > 0 ? std::sqrt(o.pcg.true_rr / o.pcg.bb) : 0.0;
     }
     if (st.status == GF_OK && !std::isfinite(st.rel_res)) st.status = GF_NAN;
+    if (timed_out) st.status = GF_TIMEOUT;
     if (o.cnt[3] != 0) st.status = GF_BAD_ARG;
     st.n_broken = int64_t(o.cnt[kCntBroken]);
     st.n_new_broken = int64_t(o.cnt[kCntNewBroken]);
@@ -2019,8 +2216,10 @@ gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out) {
       cudaMalloc(&b->dinit, sizeof(BatchInit) * n) != cudaSuccess ||
       cudaMallocHost(&b->hout, sizeof(BatchOut) * n) != cudaSuccess ||
       cudaMalloc(&b->dout, sizeof(BatchOut) * n) != cudaSuccess || cudaMalloc(&b->d_iter, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&b->h_iter, sizeof(int)) != cudaSuccess)
+      cudaMallocHost(&b->h_iter, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->pctl, sizeof(PersistCtl)) != cudaSuccess || cudaMallocHost(&b->h_pctl, sizeof(PersistCtl)) != cudaSuccess)
     return fail("allocation");
+  std::memset(b->h_pctl, 0, sizeof(PersistCtl));
   new (b->htab) BatchTab();   // pinned host memory from cudaMallocHost: construct the table in place
   b->htab->n = n;
   std::vector<BatchInit> init(n);
@@ -2081,11 +2280,18 @@ gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, cons
 }
 
 gf_status gf_batch_tuning_set(gf_batch* b, const gf_batch_tuning* t) {
-  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0 || t->grid_budget < 0) {
-    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0, grid_budget >= 0");
+  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0 || t->grid_budget < 0 ||
+      (t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_KERNELS)) {
+    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0, grid_budget >= 0, solve_loop "
+                   "GF_SOLVE_KERNELS or GF_SOLVE_PERSISTENT");
     return GF_BAD_ARG;
   }
+  const bool rebuild = t->solve_loop != b->tune.solve_loop;
   b->tune = *t;
+  if (rebuild && b->exec) {   // the captured graph holds the other solve form
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
   return GF_OK;
 }
 
@@ -2146,6 +2352,7 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
       t.graph = 1;
       t.chunk = 8;
       t.grid_budget = budget;
+      t.solve_loop = GF_SOLVE_KERNELS;
       cands.push_back(t);
       if (budget > 2 * wave) continue;
       for (int c : {2, 8}) {
@@ -2154,6 +2361,15 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
         cands.push_back(t);
       }
     }
+    if (b->mixed)   // the persistent solve: every member's own blocks, or a budget of one or two waves
+      for (int budget : {0, wave, 2 * wave}) {
+        gf_batch_tuning t{};
+        t.graph = 1;
+        t.chunk = 8;
+        t.grid_budget = budget;
+        t.solve_loop = GF_SOLVE_PERSISTENT;
+        cands.push_back(t);
+      }
   }
   double best_t = 1e300;
   gf_batch_tuning best_c = orig;

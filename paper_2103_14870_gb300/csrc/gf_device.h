@@ -64,6 +64,7 @@ struct MixDev {
   float* fext32 = nullptr;            // [3N]
   float* pinv32 = nullptr;            // [N][9]
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;   // [3N]
+  float* p32b = nullptr;              // [3N] second search-direction buffer of the persistent solve
   float *dv_hi = nullptr, *dv_lo = nullptr;   // [3N] double-float split of dv
   IrState* ir = nullptr;
 };
@@ -209,6 +210,33 @@ int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepS
 int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first);
 int launch_batch_fp64(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s);
 int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s, int first);
+
+// Persistent refinement solve (GF_MIXED): one cooperative launch runs the whole
+// solver loop of every mesh in `tab` (inner FP32 PCG and double-float
+// refinement), with grid barriers between its phases instead of kernel
+// boundaries.  Each phase processes the blocks of the meshes that need it, so
+// converged meshes take no CTAs.  Every barrier wait is bounded.
+// Phases decide which meshes take part from per-mesh flags (done, in_done,
+// applied).  A phase's last block may change them while a CTA without work in
+// that phase is still reading them, so the flags live in two slots: during the
+// phase after barrier g every CTA reads slot g & 1, and the phase writes slot
+// (g + 1) & 1 (the last block of a mesh its new flags, block 0 the unchanged
+// flags of the meshes that sit the phase out).
+struct PersistCtl {
+  unsigned arrive;   // grid-barrier arrivals of the running launch (reset before each launch)
+  int error;         // 1: a barrier wait ran out and the launch stopped early
+  int rounds;        // rounds the launch ran
+  int test_skip;     // test hook: block 0 skips its first arrival, so every wait of that barrier runs out
+  int flags[2][kMaxBatch][3];   // [slot][mesh]: done, in_done, applied
+};
+constexpr unsigned long long kPersistWaitNs = 1000000000ull;   // limit of one barrier wait (1 s)
+// Grid of the persistent launch on the current device (resident CTAs x SMs).
+unsigned persist_grid();
+// Enqueue the persistent solve (a small kernel that resets `ctl` and takes the
+// meshes' flags, then the cooperative launch); `cap` bounds its rounds,
+// test_skip arms the test hook.  Returns the kernels launched (2), or -1 if the
+// cooperative launch was refused.
+int launch_ir_persist(const BatchTab* tab, int n, PersistCtl* ctl, int cap, int test_skip, cudaStream_t s);
 
 // single-mesh launches (return the number of kernels launched)
 int launch_kind(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first = 0);

@@ -465,43 +465,51 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
   return GF_OK;
 }
 
-// Order of one joint list's entries for the shared-memory reads of the mixed
-// Eq. 20 kernel: lane l of chunk c takes entry beg + 32 c + l, and reads the
-// six floats of union row loc as three 8-byte words at bank pair (3 loc + h)
-// mod 16.  The entries are dealt to the chunks round-robin in (loc mod 16, loc)
-// order, so each chunk holds about two of every residue, and within a chunk
-// the first copy of each residue goes to lanes 0-15 and the second to 16-31:
-// the half-warps then read distinct bank pairs where the residues allow it.
-// Only the order of the terms changes.
+// Order of the joint list of pair q for the shared-memory reads of the mixed
+// Eq. 20 kernel.  Eight lanes read a pair's list, lane s the entries 8c + s
+// (chunk c), and a lane reads the six floats of union row loc as three 8-byte
+// words at bank pair (3 loc + h) mod 16; a half-warp (two pairs, q even and
+// q + 1) is one shared-memory wavefront per word.  So each chunk of eight
+// entries takes distinct residues loc mod 16 from one half of the residues,
+// the low half when q + c is even and the high half otherwise (the two pairs
+// of a half-warp take opposite halves), the residues with the most entries
+// left first; what a half cannot supply comes from the other half.  Only the
+// order of the terms changes.
 struct JointEntry {
   uint16_t loc;
   float w[2];
 };
-void deal_entries(std::vector<JointEntry>& e) {
+void deal_entries(std::vector<JointEntry>& e, int64_t q) {
   const int64_t n = int64_t(e.size());
   if (n <= 1) return;
-  auto key = [](const JointEntry& a) { return std::make_pair(a.loc % 16, a.loc); };
-  std::sort(e.begin(), e.end(), [&](const JointEntry& a, const JointEntry& c) { return key(a) < key(c); });
-  const int64_t nc = (n + 31) / 32;
-  // chunk c holds min(32, n - 32 c) entries: all but the last are full
-  std::vector<std::vector<JointEntry>> chunk(nc);
-  for (int64_t k = 0, c = 0; k < n; ++k, c = (c + 1) % nc) {
-    while (int64_t(chunk[c].size()) == std::min<int64_t>(32, n - 32 * c)) c = (c + 1) % nc;
-    chunk[c].push_back(e[k]);
+  std::vector<JointEntry> bucket[16];
+  for (const auto& x : e) bucket[x.loc % 16].push_back(x);
+  size_t next[16] = {};
+  auto left = [&](int r) { return bucket[r].size() - next[r]; };
+  std::vector<JointEntry> out;
+  out.reserve(size_t(n));
+  for (int64_t c = 0; int64_t(out.size()) < n; ++c) {
+    const int64_t want = std::min<int64_t>(8, n - int64_t(out.size()));
+    const int half = ((q + c) & 1) ? 8 : 0;
+    bool used[16] = {};
+    int64_t got = 0;
+    auto take_from = [&](int lo, bool distinct) {
+      while (got < want) {
+        int best = -1;
+        for (int r = lo; r < lo + 8; ++r)
+          if (left(r) > 0 && !(distinct && used[r]) && (best < 0 || left(r) > left(best))) best = r;
+        if (best < 0) return;
+        out.push_back(bucket[best][next[best]++]);
+        used[best] = true;
+        ++got;
+      }
+    };
+    take_from(half, true);
+    take_from(8 - half, true);
+    take_from(half, false);
+    take_from(8 - half, false);
   }
-  int64_t o = 0;
-  for (auto& c : chunk) {
-    std::sort(c.begin(), c.end(), [&](const JointEntry& a, const JointEntry& d) { return key(a) < key(d); });
-    std::vector<JointEntry> lo, hi;
-    for (size_t k = 0; k < c.size(); ++k)
-      ((k == 0 || c[k].loc % 16 != c[k - 1].loc % 16) && lo.size() < 16 ? lo : hi).push_back(c[k]);
-    while (lo.size() < 16 && !hi.empty()) {
-      lo.push_back(hi.back());
-      hi.pop_back();
-    }
-    for (auto& x : lo) e[o++] = x;
-    for (auto& x : hi) e[o++] = x;
-  }
+  e.swap(out);
 }
 
 gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, std::string& err) {
@@ -580,7 +588,7 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
             }
             jq.push_back(x);
           }
-          deal_entries(jq);
+          deal_entries(jq, a / 2);
         }
       }
     });

@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "gf_device.h"
+#include "gf_df.cuh"
 #include "gf_reduce.cuh"
 
 namespace gf {
@@ -159,55 +160,32 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
 // Eq. 20 sum in FP32, tiled.  A CTA takes kNlTile consecutive tets and first
 // stages the union of their neighbour sets (ascending tet ids, six floats a
 // row) in shared memory; a tile whose union exceeds kNlCap rows reads the rows
-// from global memory instead.  A warp then takes a pair of tets (2q, 2q+1) at
-// a time and streams the pair's joint list (the union of the two neighbour
-// lists: a 16-bit union position and the two FP32 weights per entry, zero
-// where a tet lacks that neighbour) with coalesced loads, all of a lane's
-// entries at once and the next pair's while the current one is summed.  One
-// staged row read thus serves both tets (0.61 row reads per pair on the loaf
-// instead of 1), and a pair's neighbours are short runs of consecutive tets,
-// so the lanes read neighbouring shared-memory rows.  The twelve sums are
-// reduced across the warp in a fixed order by a transposing butterfly (each
-// step keeps half of the values per lane), and sixteen lanes write the two
-// 32-byte output rows.
+// from global memory instead.  Each pair of tets (2q, 2q+1) has a joint list:
+// the union of the two neighbour lists, per entry a 16-bit union position and
+// the two FP32 weights (zero where a tet lacks that neighbour), so one staged
+// row read serves both tets (0.61 row reads per (tet, neighbour) pair on the
+// loaf instead of 1).  A warp works on four pairs at once, eight lanes per
+// pair: lane s of a pair takes the entries s, s + 8, s + 16, ... of its list,
+// a batch of kNlBatch of them loaded while the previous batch is summed.  The
+// twelve sums of a pair are then reduced over its eight lanes by a transposing
+// butterfly (three steps, each lane keeping half of its values), which leaves
+// two output columns in each lane: one 8-byte store per lane writes the two
+// 32-byte output rows.  The host orders each list so that the eight entries a
+// pair reads at once fall on distinct shared-memory bank pairs, and the two
+// pairs of a half-warp on opposite halves of the banks.
 constexpr int kNlThreads = 256, kNlWarpPairs = kNlTile / 2 / (kNlThreads / 32);
 constexpr unsigned kNlSmem = kNlCap * 24;
+constexpr int kNlBatch = 6;   // entries of a lane in flight per load batch
 
-// all-reduce of v[0..15] over the warp: afterwards lane L holds the total of
-// value L / 2 (= 8 b4 + 4 b3 + 2 b2 + b1, b_k bit k of L)
-__device__ __forceinline__ float warp_transpose_sum16(const float (&v)[16], int lane) {
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
-  float u[8], x[4], y[2];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const float snd = h4 ? v[k] : v[8 + k];
-    u[k] = (h4 ? v[8 + k] : v[k]) + __shfl_xor_sync(0xffffffffu, snd, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float snd = h3 ? u[k] : u[4 + k];
-    x[k] = (h3 ? u[4 + k] : u[k]) + __shfl_xor_sync(0xffffffffu, snd, 8);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float snd = h2 ? x[k] : x[2 + k];
-    y[k] = (h2 ? x[2 + k] : x[k]) + __shfl_xor_sync(0xffffffffu, snd, 4);
-  }
-  float r = (h1 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, h1 ? y[0] : y[1], 2);
-  r += __shfl_xor_sync(0xffffffffu, r, 1);
-  return r;
-}
-
-// one pair's joint-list entries of a lane: up to kNlChunks (p, p + 32, ...)
-constexpr int kNlChunks = 7;
-struct NlPairs {
-  int loc[kNlChunks];
-  float2 wt[kNlChunks];
+struct NlBatch {
+  int loc[kNlBatch];
+  float2 wt[kNlBatch];
 };
-__device__ __forceinline__ void nl_load(const MixDev& x, int64_t p, int64_t end, NlPairs& q) {
+// lane entries p, p + 8, ..., p + 8 (kNlBatch - 1); loc -1 past the list end
+__device__ __forceinline__ void nl_load(const MixDev& x, int64_t p, int64_t end, NlBatch& q) {
 #pragma unroll
-  for (int c = 0; c < kNlChunks; ++c) {
-    const int64_t pc = p + 32 * c;
+  for (int c = 0; c < kNlBatch; ++c) {
+    const int64_t pc = p + 8 * c;
     q.loc[c] = pc < end ? int(__ldg(x.nb_loc + pc)) : -1;
     q.wt[c] = pc < end ? __ldg(x.nb_w2 + pc) : make_float2(0.f, 0.f);
   }
@@ -235,12 +213,11 @@ __device__ __forceinline__ void fma2(float2& c, float2 a, float2 b) {
       : "+f"(c.x), "+f"(c.y)
       : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
 }
-// acc[0..2]: the first tet of the pair (columns 0-5 as pairs), acc[4..6]: the second
-// (acc[3], acc[7] stay 0: columns 6, 7 of the output rows)
-__device__ __forceinline__ void nl_accumulate(const MixDev& x, const float2* su, bool staged, int64_t u0, const NlPairs& q,
-                                              float2 (&acc)[8]) {
+// acc[0..2]: the first tet of the pair (columns 0-5 as pairs), acc[3..5]: the second
+__device__ __forceinline__ void nl_accumulate(const MixDev& x, const float2* su, bool staged, int64_t u0, const NlBatch& q,
+                                              float2 (&acc)[6]) {
 #pragma unroll
-  for (int c = 0; c < kNlChunks; ++c) {
+  for (int c = 0; c < kNlBatch; ++c) {
     if (q.loc[c] < 0) continue;
     float2 r0, r1, r2;
     nl_row(x, su, staged, u0, q.loc[c], r0, r1, r2);
@@ -248,10 +225,31 @@ __device__ __forceinline__ void nl_accumulate(const MixDev& x, const float2* su,
     fma2(acc[0], wa, r0);
     fma2(acc[1], wa, r1);
     fma2(acc[2], wa, r2);
-    fma2(acc[4], wb, r0);
-    fma2(acc[5], wb, r1);
-    fma2(acc[6], wb, r2);
+    fma2(acc[3], wb, r0);
+    fma2(acc[4], wb, r1);
+    fma2(acc[5], wb, r2);
   }
+}
+// Reduce v[0..15] (columns 0-7 of the first tet, then of the second) over the
+// eight lanes of a group: afterwards lane s holds columns 2 (s & 3) and
+// 2 (s & 3) + 1 of tet s >> 2 (each step keeps the half named by a bit of s).
+__device__ __forceinline__ float2 group_transpose_sum(const float (&v)[16], int s, unsigned gmask) {
+  const bool b2 = s & 4, b1 = s & 2, b0 = s & 1;
+  float u[8], w[4];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float snd = b2 ? v[k] : v[8 + k];
+    u[k] = (b2 ? v[8 + k] : v[k]) + __shfl_xor_sync(gmask, snd, 4);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float snd = b1 ? u[k] : u[4 + k];
+    w[k] = (b1 ? u[4 + k] : u[k]) + __shfl_xor_sync(gmask, snd, 2);
+  }
+  const float s0 = b0 ? w[0] : w[2], s1 = b0 ? w[1] : w[3];
+  const float k0 = (b0 ? w[2] : w[0]) + __shfl_xor_sync(gmask, s0, 1);
+  const float k1 = (b0 ? w[3] : w[1]) + __shfl_xor_sync(gmask, s1, 1);
+  return make_float2(k0, k1);
 }
 
 __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
@@ -280,45 +278,42 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  // this warp's pairs: q in [qw, qw + np) (pair q = tets 2q, 2q+1)
+  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+  const unsigned gmask = 0xffu << (lane & 24);
+  // this warp's pairs: q in [qw, qw + np) (pair q = tets 2q, 2q+1), four at a time
   const int64_t NQ = (m.T + 1) / 2;
   const int64_t qw = t0 / 2 + int64_t(kNlWarpPairs) * (threadIdx.x >> 5);
   if (qw >= NQ) return;
   const int np = int(NQ - qw < kNlWarpPairs ? NQ - qw : kNlWarpPairs);
-  // nb_ptr[qw .. qw + np] in lanes 0..np
-  const int64_t myptr = lane <= np ? x.nb_ptr[qw + lane] : 0;
-  NlPairs cur, nxt;
+  for (int r0 = 0; r0 < np; r0 += 4) {
+    const int64_t q = qw + r0 + g;
+    const bool live = r0 + g < np;
+    const int64_t beg = live ? x.nb_ptr[q] : 0, end = live ? x.nb_ptr[q + 1] : 0;
+    // batches of this lane's entries; every lane of the warp runs the longest group's count
+    const int mine = end - beg > sl ? int((end - beg - sl + 7) / 8) : 0;
+    const int rounds = __reduce_max_sync(0xffffffffu, (mine + kNlBatch - 1) / kNlBatch);
+    float2 acc2[6];
 #pragma unroll
-  for (int c = 0; c < kNlChunks; ++c) nxt.loc[c] = -1, nxt.wt[c] = make_float2(0.f, 0.f);
-  int64_t beg = __shfl_sync(0xffffffffu, myptr, 0), end = __shfl_sync(0xffffffffu, myptr, 1);
-  nl_load(x, beg + lane, end, cur);
-  for (int k = 0; k < np; ++k) {
-    // the next pair's first chunks are in flight while this one is summed
-    const int64_t nbeg = end, nend = __shfl_sync(0xffffffffu, myptr, k + 2 <= np ? k + 2 : np);
-    if (k + 1 < np) nl_load(x, nbeg + lane, nend, nxt);
-    float2 acc2[8];
-#pragma unroll
-    for (int v = 0; v < 8; ++v) acc2[v] = make_float2(0.f, 0.f);
-    nl_accumulate(x, su, staged, u0, cur, acc2);
-    for (int64_t p = beg + lane + 32 * kNlChunks; p < end; p += 32 * kNlChunks) {   // lists longer than 224
-      NlPairs more;
-      nl_load(x, p, end, more);
-      nl_accumulate(x, su, staged, u0, more, acc2);
+    for (int v = 0; v < 6; ++v) acc2[v] = make_float2(0.f, 0.f);
+    NlBatch cur, nxt;
+    nl_load(x, beg + sl, end, cur);
+    for (int b = 0; b < rounds; ++b) {
+      if (b + 1 < rounds) nl_load(x, beg + sl + 8 * kNlBatch * (b + 1), end, nxt);
+      nl_accumulate(x, su, staged, u0, cur, acc2);
+      cur = nxt;
     }
     float acc[16];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 3; ++v) {
       acc[2 * v] = acc2[v].x;
       acc[2 * v + 1] = acc2[v].y;
+      acc[8 + 2 * v] = acc2[3 + v].x;
+      acc[8 + 2 * v + 1] = acc2[3 + v].y;
     }
-    const float tot = warp_transpose_sum16(acc, lane);
-    // lane L (even) holds value L / 2: tet (L / 16) of the pair, column (L / 2) % 8 (6, 7 are zero)
-    const int64_t t = 2 * (qw + k) + (lane >> 4);
-    if ((lane & 1) == 0 && t < m.T) x.sig_bar32[8 * t + ((lane >> 1) & 7)] = tot;
-    cur = nxt;
-    beg = nbeg;
-    end = nend;
+    acc[6] = acc[7] = acc[14] = acc[15] = 0.f;
+    const float2 tot = group_transpose_sum(acc, sl, gmask);
+    const int64_t t = 2 * q + (sl >> 2);
+    if (live && t < m.T) reinterpret_cast<float2*>(x.sig_bar32 + 8 * t)[sl & 3] = tot;
   }
 }
 __global__ void __launch_bounds__(kNlThreads, 3) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
@@ -726,99 +721,6 @@ __global__ void __launch_bounds__(kThreads) kb_fext32(const BatchTab* __restrict
 // FP64 iterative refinement around an FP32 PCG
 // ---------------------------------------------------------------------------
 
-// error-free product and sum (Dekker / Knuth) for double-float accumulation
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = a * b;
-  e = fmaf(a, b, -p);
-}
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void df_add(float& hi, float& lo, float p, float pe) {
-  float s, e;
-  two_sum(hi, p, s, e);
-  e += lo + pe;
-  hi = s + e;
-  lo = e - (hi - s);
-}
-
-// Double-float (float pair) warp and grid reductions: ~48-bit sums on the FP32
-// pipe.  The FP64 pipe of GB300 costs a full 64-cycle slot per warp
-// instruction even with one active lane, so the refinement keeps FP64-level
-// accuracy with float pairs and converts to double only for the final scalars.
-__device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_down_sync(0xffffffffu, hi, o);
-    const float ol = __shfl_down_sync(0xffffffffu, lo, o);
-    df_add(hi, lo, oh, ol);
-  }
-}
-
-template <int NV>
-__device__ __forceinline__ bool grid_reduce_df(float (&hi)[NV], float (&lo)[NV], double* partials, unsigned* ticket,
-                                               double (&out)[NV], unsigned bid, unsigned nb) {
-  __shared__ float sh[NV][2][32];
-  __shared__ bool last;
-  float2* part = reinterpret_cast<float2*>(partials);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    df_warp_sum(hi[i], lo[i]);
-    if (lane == 0) {
-      sh[i][0][wid] = hi[i];
-      sh[i][1][wid] = lo[i];
-    }
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      float h = lane < nw ? sh[i][0][lane] : 0.f, l = lane < nw ? sh[i][1][lane] : 0.f;
-      df_warp_sum(h, l);
-      if (lane == 0) part[bid * NV + i] = make_float2(h, l);
-    }
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = (atomicAdd(ticket, 1u) == nb - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    float h = 0.f, l = 0.f;
-    for (unsigned j = threadIdx.x; j < nb; j += blockDim.x) {
-      const float2 v = __ldcg(&part[j * NV + i]);
-      df_add(h, l, v.x, v.y);
-    }
-    df_warp_sum(h, l);
-    __syncthreads();
-    if (lane == 0) {
-      sh[i][0][wid] = h;
-      sh[i][1][wid] = l;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      h = lane < nw ? sh[i][0][lane] : 0.f;
-      l = lane < nw ? sh[i][1][lane] : 0.f;
-      df_warp_sum(h, l);
-      if (lane == 0) out[i] = double(h) + double(l);
-    }
-  }
-  if (threadIdx.x == 0) *ticket = 0u;
-  return true;
-}
-
-__device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float b) {
-  float p, pe;
-  two_prod(a, b, p, pe);
-  df_add(hi, lo, p, pe);
-}
-
 // r = b - A32 dv on free rows, with A32 dv formed to double-float accuracy
 // (dv = dv_hi + dv_lo) and b - A dv in double-float; eight lanes per block row
 // (lane j takes blocks j, j+8, ..., two at a time so that both blocks' loads
@@ -830,22 +732,6 @@ __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float
 // then leaves component c of row i in lanes 2c and 2c + 1, and lane 2c forms
 // r_c.  The inner solve's right-hand side is the leading float of r; ||r||^2
 // accumulates in double-float.
-__device__ __forceinline__ void dot2_block(float (&s)[4], float (&c)[4], const float (&a)[9], const float (&xh)[3],
-                                           const float (&xl)[3]) {
-#pragma unroll
-  for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float av = a[3 * rr + k];
-      const float p = av * xh[k];
-      const float pe = fmaf(av, xl[k], fmaf(av, xh[k], -p));   // product error + the dv_lo term
-      const float t = s[rr] + p;
-      const float bp = t - s[rr];
-      const float e = (s[rr] - (t - bp)) + (p - bp);              // TwoSum error
-      s[rr] = t;
-      c[rr] += e + pe;
-    }
-}
 __device__ __forceinline__ void ir_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb, int first) {
 
   IrState* S = m.mx.ir;

@@ -61,16 +61,18 @@ class StepStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("assembly", ctypes.c_int32), ("step_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("assembly", ctypes.c_int32), ("step_launch", ctypes.c_int32), ("solve_loop", ctypes.c_int32),
+                ("wait_test", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
 STEP_GRAPH, STEP_STREAM = 0, 1
+SOLVE_KERNELS, SOLVE_PERSISTENT, SOLVE_CG = 0, 1, 2
 
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_int32), ("chunk", ctypes.c_int32), ("grid_budget", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("solve_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -280,16 +282,20 @@ class Mesh:
                                              ctypes.byref(nq)))
         return {"vertices": V, "quads": Q[:nq.value], "n_faces": sz["n_faces"]}
 
-    def tuning_set(self, assembly: int = ASSEMBLY_GATHER, step_launch: int = STEP_GRAPH):
+    def tuning_set(self, assembly: int = ASSEMBLY_GATHER, step_launch: int = STEP_GRAPH,
+                   solve_loop: int = SOLVE_KERNELS, wait_test: int = 0):
         t = Tuning()
         t.assembly = assembly
         t.step_launch = step_launch
+        t.solve_loop = solve_loop
+        t.wait_test = wait_test
         _check(load_library().gf_tuning_set(self._h, ctypes.byref(t)))
 
     def tuning_get(self) -> dict:
         t = Tuning()
         _check(load_library().gf_tuning_get(self._h, ctypes.byref(t)))
-        return {"assembly": t.assembly, "step_launch": t.step_launch}
+        return {"assembly": t.assembly, "step_launch": t.step_launch, "solve_loop": t.solve_loop,
+                "wait_test": t.wait_test}
 
     def refine_set(self, inner_rtol: float):
         _check(load_library().gf_refine_set(self._h, float(inner_rtol)))
@@ -419,15 +425,15 @@ class Batch:
         _check(load_library().gf_batch_step(self._h, float(dt), fp, pp, npin, vp, mem, stats))
         return [st.as_dict() for st in stats]
 
-    def tuning_set(self, graph: int = 1, chunk: int = 8, grid_budget: int = 0):
+    def tuning_set(self, graph: int = 1, chunk: int = 8, grid_budget: int = 0, solve_loop: int = SOLVE_KERNELS):
         t = BatchTuning()
-        t.graph, t.chunk, t.grid_budget = graph, chunk, grid_budget
+        t.graph, t.chunk, t.grid_budget, t.solve_loop = graph, chunk, grid_budget, solve_loop
         _check(load_library().gf_batch_tuning_set(self._h, ctypes.byref(t)))
 
     def tuning_get(self) -> dict:
         t = BatchTuning()
         _check(load_library().gf_batch_tuning_get(self._h, ctypes.byref(t)))
-        return {"graph": t.graph, "chunk": t.chunk, "grid_budget": t.grid_budget}
+        return {"graph": t.graph, "chunk": t.chunk, "grid_budget": t.grid_budget, "solve_loop": t.solve_loop}
 
     def autotune(self, dt: float, f_ext=None, pinned=None, pinned_vel=None, trial_steps: int = 3):
         fp, pp, npin, vp, mem, keep = self._inputs(f_ext, pinned, pinned_vel)
