@@ -102,14 +102,13 @@ MIXED_BYTES = {
 # groups add their diagonal kernel (k_gather64 + k_diag64, k_gather32 + k_diag32).
 NCU_TRAFFIC = {
     "nonlocal_avg": 1.236900864e9 + 30.863872e6,
-    # k_elem64, k_gather64 and k_diag64 changed (edge velocity differences kept,
-    # count-ordered visits) since their last capture
-    "assemble": None,
-    "assemble_gather": None,
-    "m:nonlocal_avg": 662.371328e6 + 20.333568e6,
-    "m:assemble": 127.123712e6 + 121.151232e6,
-    # k_gather32 changed (row sums start from the first row) since its capture
-    "m:assemble_gather": None,
+    # k_elem64; k_gather64 + k_diag64
+    "assemble": 184.756992e6 + 293.543424e6,
+    "assemble_gather": (371.265536e6 + 107.799296e6) + (117.729792e6 + 1.789440e6),
+    # k_nonlocal32 (eight lanes per tet pair); k_elem32; k_gather32 + k_diag32
+    "m:nonlocal_avg": 662.230528e6 + 19.512576e6,
+    "m:assemble": 127.145472e6 + 118.654464e6,
+    "m:assemble_gather": (191.035136e6 + 42.632448e6) + (59.089408e6 + 0.0),
 }
 # Executed FP64 flops per tet of the element-block kernel, off-diagonal blocks
 # and rhs shares only (ncu: 2 DFMA + DADD + DMUL thread instructions per launch /

@@ -196,11 +196,12 @@ enum { GF_STEP_GRAPH = 0, GF_STEP_STREAM = 1 };
  * between its phases and the direction update fused into the SpMV.  Each barrier
  * wait gives up after 1 s and the step then returns GF_TIMEOUT (the mesh state
  * is then unspecified: set it again with gf_state_set).
+ * GF_SOLVE_DISTRIBUTED is a batch form (gf_batch_tuning).
  * Another form than the precision supports -> GF_UNSUPPORTED.
  * wait_test: a test hook; 1 makes one CTA of the next persistent solve skip its
  * first barrier arrival, so that every wait of that barrier runs out (the
  * step returns GF_TIMEOUT after about 1 s).  Leave it 0. */
-enum { GF_SOLVE_KERNELS = 0, GF_SOLVE_PERSISTENT = 1, GF_SOLVE_CG = 2 };
+enum { GF_SOLVE_KERNELS = 0, GF_SOLVE_PERSISTENT = 1, GF_SOLVE_CG = 2, GF_SOLVE_DISTRIBUTED = 3 };
 typedef struct gf_tuning {
   int32_t assembly;
   int32_t step_launch;   /* GF_STEP_GRAPH (0, default) or GF_STEP_STREAM */
@@ -371,11 +372,20 @@ typedef struct gf_batch_tuning {
                            meshes by node count (at least 1 CTA each, at most the single-mesh grid);
                            converged meshes then cost few early-exit CTAs per iteration, and the
                            per-mesh reductions sum in a different (still fixed) order. */
-  int32_t solve_loop;   /* GF_SOLVE_KERNELS (0, default): per-kind launches (graph WHILE node or
-                           stream, as `graph` says).  GF_SOLVE_PERSISTENT (GF_MIXED batches): the
-                           whole solve of every member as one cooperative launch whose phases take
-                           only the blocks of the meshes still iterating (members step bit-identically
-                           to single-mesh persistent steps).  GF_FP64 batches use the kernels. */
+  int32_t solve_loop;   /* GF_SOLVE_KERNELS (0, default): per-kind launches of the solver loop
+                           (graph WHILE node or stream, as `graph` says), each mesh with its
+                           single-mesh grid or its share of grid_budget.
+                           GF_SOLVE_DISTRIBUTED: per-kind launches of grid_budget CTAs (0: four per
+                           SM) over a work table the device rebuilds after every loop iteration:
+                           the grid is split over the meshes not yet converged by node count (at
+                           least one block each, at most the single-mesh grid), so a converged
+                           mesh costs nothing and the last ones to converge get the whole grid.
+                           The reductions then group rows by the current split (a fixed order for
+                           a given batch and state). 
+                           GF_SOLVE_PERSISTENT (GF_MIXED batches): the whole solve of every member
+                           as one cooperative launch whose phases take only the blocks of the
+                           meshes still iterating (members step bit-identically to single-mesh
+                           persistent steps). */
   int32_t reserved[4];  /* set to 0 */
 } gf_batch_tuning;
 

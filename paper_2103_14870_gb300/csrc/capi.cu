@@ -1840,13 +1840,97 @@ __global__ void __launch_bounds__(256) kb_step_begin(const BatchTab* __restrict_
   }
 }
 
-// Solve-loop condition: continue while any mesh is unconverged (and below the cap).
+// Exclusive block-wide prefix sum (blockDim.x = 256 >= the batch size);
+// s[t] receives thread t's offset and the function returns the total.
+__device__ int block_scan256(int v, int* s, int* sw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  __syncthreads();   // s and sw may still be read from the previous call
+  if (lane == 31) sw[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < 8 ? sw[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    if (lane < 8) sw[lane] = w;
+  }
+  __syncthreads();
+  const int base = wid ? sw[wid - 1] : 0;
+  s[threadIdx.x] = base + incl - v;
+  __syncthreads();
+  return sw[7];
+}
+
+// The work table of the distributed loop: the unconverged meshes and, per
+// solver-loop kind, the offsets of their blocks.  The launch grid `grid` is
+// split over the active meshes by node count (at least one block each, at most
+// its single-mesh grid), so as meshes converge the others get more of it.
+// Returns whether any mesh is left.
+__device__ bool build_act(const BatchTab* __restrict__ tab, BatchAct* act, int mixed, int grid) {
+  __shared__ int s_pos[256], s_off[256], s_w[8];
+  __shared__ unsigned long long s_nodes;
+  const int k = threadIdx.x, n = tab->n;
+  const int active = k < n && (mixed ? !tab->mesh[k].mx.ir->done : !tab->mesh[k].pcg->done);
+  if (k == 0) s_nodes = 0ull;
+  __syncthreads();
+  if (active) atomicAdd(&s_nodes, (unsigned long long)tab->mesh[k].N);
+  const int n_act = block_scan256(active, s_pos, s_w);
+  const unsigned long long nodes = s_nodes;
+  if (active) act->mesh[s_pos[k]] = k;
+  const int nk = mixed ? 6 : 3;
+  for (int j = 0; j < nk; ++j) {
+    int kind;
+    if (mixed) {
+      switch (j) {
+        case 0: kind = kB_ir_inner_init; break;
+        case 1: kind = kB_ir_spmv; break;
+        case 2: kind = kB_ir_update; break;
+        case 3: kind = kB_ir_p; break;
+        case 4: kind = kB_ir_apply; break;
+        default: kind = kB_ir_residual; break;
+      }
+    } else {
+      kind = j == 0 ? kB_pcg_spmv : (j == 1 ? kB_pcg_update : kB_pcg_p);
+    }
+    int cnt = 0;
+    if (active) {
+      const long long natural = tab->off[kind][k + 1] - tab->off[kind][k];
+      const long long share = (static_cast<long long>(grid) * tab->mesh[k].N + (long long)nodes - 1) / (long long)nodes;
+      cnt = int(share < 1 ? 1 : (share > natural ? natural : share));
+    }
+    const int total = block_scan256(cnt, s_off, s_w);
+    if (active) act->off[kind][s_pos[k]] = s_off[k];
+    if (k == 0) act->off[kind][n_act] = total;
+  }
+  if (k == 0) act->n = n_act;
+  return n_act > 0;
+}
+
+__global__ void __launch_bounds__(256) kb_activate(const BatchTab* __restrict__ tab, BatchAct* act, int mixed,
+                                                    int grid) {
+  build_act(tab, act, mixed, grid);
+}
+
+// Solve-loop condition: continue while any mesh is unconverged (and below the
+// cap); with a work table, rebuild it for the next iteration.
 __global__ void __launch_bounds__(256) kb_any_active(const BatchTab* __restrict__ tab, int mixed, int* iter, int cap,
-                                                      cudaGraphConditionalHandle h) {
+                                                      cudaGraphConditionalHandle h, BatchAct* act, int grid) {
   int active = 0;
-  for (int k = threadIdx.x; k < tab->n; k += blockDim.x)
-    active |= mixed ? !tab->mesh[k].mx.ir->done : !tab->mesh[k].pcg->done;
-  active = __syncthreads_or(active);
+  if (act) {
+    active = build_act(tab, act, mixed, grid);
+  } else {
+    for (int k = threadIdx.x; k < tab->n; k += blockDim.x)
+      active |= mixed ? !tab->mesh[k].mx.ir->done : !tab->mesh[k].pcg->done;
+    active = __syncthreads_or(active);
+  }
   if (threadIdx.x == 0) {
     const int it = ++(*iter);
     cudaGraphSetConditional(h, (active && it < cap) ? 1u : 0u);
@@ -1886,6 +1970,7 @@ struct gf_batch {
   cudaGraphExec_t exec = nullptr;
   gf_batch_tuning tune{};
   int cap = 0;
+  BatchAct* dact = nullptr;          // work table of the distributed solve loop
   PersistCtl* pctl = nullptr;        // control block of the persistent solve
   PersistCtl* h_pctl = nullptr;      // pinned mirror of its head
   int64_t launches = 0;
@@ -1907,7 +1992,17 @@ void batch_free(gf_batch* b) {
   if (b->h_iter) cudaFreeHost(b->h_iter);
   if (b->body_stream) cudaStreamDestroy(b->body_stream);
   if (b->pctl) cudaFree(b->pctl);
+  if (b->dact) cudaFree(b->dact);
   if (b->h_pctl) cudaFreeHost(b->h_pctl);
+}
+
+bool batch_dist(const gf_batch* b) { return b->tune.solve_loop == GF_SOLVE_DISTRIBUTED; }
+// grid of a distributed loop launch: the tuning's budget, else four CTAs per SM
+unsigned dist_grid(const gf_batch* b) {
+  if (b->tune.grid_budget > 0) return unsigned(b->tune.grid_budget);
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return unsigned(4 * sms);
 }
 
 const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_elem64, kB_gather64, kB_diag64,
@@ -1936,10 +2031,23 @@ int64_t enqueue_prefix(gf_batch* b, cudaStream_t s) {
   } else {
     L += enqueue_kinds(b, kPrefixFp64, s);
   }
+  if (batch_dist(b)) {   // the first work table: the meshes the first residual left unconverged
+    kb_activate<<<1, 256, 0, s>>>(b->dtab, b->dact, b->mixed ? 1 : 0, int(dist_grid(b)));
+    ++L;
+  }
   return L;
 }
 
 int64_t enqueue_body(gf_batch* b, cudaStream_t s) {
+  if (batch_dist(b)) {
+    int64_t L = 0;
+    const unsigned g = dist_grid(b);
+    if (b->mixed)
+      for (int kind : kBodyMixed) L += launch_dist_mixed(kind, b->dtab, b->dact, g, s);
+    else
+      for (int kind : kBodyFp64) L += launch_dist_fp64(kind, b->dtab, b->dact, g, s);
+    return L;
+  }
   if (b->mixed) {
     int64_t L = 0;
     for (int kind : kBodyMixed) L += launch_batch(kind, b->dtab, b->blocks[kind], s, 0);
@@ -2020,7 +2128,8 @@ gf_status build_graph(gf_batch* b) {
   cudaGraph_t body = p.conditional.phGraph_out[0];
   GB_CK(cudaStreamBeginCaptureToGraph(b->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   b->body_kernels = enqueue_body(b, b->body_stream);
-  kb_any_active<<<1, 256, 0, b->body_stream>>>(b->dtab, b->mixed ? 1 : 0, b->d_iter, b->cap, h);
+  kb_any_active<<<1, 256, 0, b->body_stream>>>(b->dtab, b->mixed ? 1 : 0, b->d_iter, b->cap, h,
+                                                 batch_dist(b) ? b->dact : nullptr, int(dist_grid(b)));
   ++b->body_kernels;
   GB_CK(cudaStreamEndCapture(b->body_stream, &body));
   GB_CK(cudaStreamUpdateCaptureDependencies(s, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
@@ -2073,7 +2182,7 @@ gf_status batch_prepare(gf_batch* b, double dt, const double* const* f_ext, cons
     for (int k = 0; k < b->n; ++k) {
       int64_t blocks = launch_dims(kind, b->htab->mesh[k], b->htab->mt[k], b->htab->sp[k]).blocks;
       if (batch_persist(b)) blocks = persist_blocks(kind, unsigned(blocks));
-      if (loop_kind && budget > 0 && blocks > 0)
+      if (loop_kind && budget > 0 && blocks > 0 && !batch_dist(b))
         blocks = std::min(blocks, std::max<int64_t>(1, (budget * b->htab->mesh[k].N + n_sum - 1) / n_sum));
       acc += int32_t(blocks);
       b->htab->off[kind][k + 1] = acc;
@@ -2125,7 +2234,13 @@ gf_status batch_run(gf_batch* b, gf_step_stats* stats) {
     const int chunk = b->tune.chunk > 0 ? b->tune.chunk : 8;
     int it = 0;
     for (;;) {
-      for (int j = 0; j < chunk; ++j, ++it) L += enqueue_body(b, s);
+      for (int j = 0; j < chunk; ++j, ++it) {
+        L += enqueue_body(b, s);
+        if (batch_dist(b)) {   // the next iteration's work table
+          kb_activate<<<1, 256, 0, s>>>(b->dtab, b->dact, b->mixed ? 1 : 0, int(dist_grid(b)));
+          ++L;
+        }
+      }
       kb_collect<<<unsigned((b->n + 127) / 128), 128, 0, s>>>(b->dtab, b->mixed ? 1 : 0, b->dout);
       ++L;
       GB_CK(cudaGetLastError());
@@ -2217,7 +2332,8 @@ gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out) {
       cudaMallocHost(&b->hout, sizeof(BatchOut) * n) != cudaSuccess ||
       cudaMalloc(&b->dout, sizeof(BatchOut) * n) != cudaSuccess || cudaMalloc(&b->d_iter, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&b->h_iter, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&b->pctl, sizeof(PersistCtl)) != cudaSuccess || cudaMallocHost(&b->h_pctl, sizeof(PersistCtl)) != cudaSuccess)
+      cudaMalloc(&b->pctl, sizeof(PersistCtl)) != cudaSuccess || cudaMallocHost(&b->h_pctl, sizeof(PersistCtl)) != cudaSuccess ||
+      cudaMalloc(&b->dact, sizeof(BatchAct)) != cudaSuccess)
     return fail("allocation");
   std::memset(b->h_pctl, 0, sizeof(PersistCtl));
   new (b->htab) BatchTab();   // pinned host memory from cudaMallocHost: construct the table in place
@@ -2281,9 +2397,10 @@ gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, cons
 
 gf_status gf_batch_tuning_set(gf_batch* b, const gf_batch_tuning* t) {
   if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0 || t->grid_budget < 0 ||
-      (t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_KERNELS)) {
+      (t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_KERNELS &&
+       t->solve_loop != GF_SOLVE_DISTRIBUTED)) {
     set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0, grid_budget >= 0, solve_loop "
-                   "GF_SOLVE_KERNELS or GF_SOLVE_PERSISTENT");
+                   "GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT or GF_SOLVE_DISTRIBUTED");
     return GF_BAD_ARG;
   }
   const bool rebuild = t->solve_loop != b->tune.solve_loop;
@@ -2370,6 +2487,14 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
         t.solve_loop = GF_SOLVE_PERSISTENT;
         cands.push_back(t);
       }
+    for (int g : {wave / 2, wave, 2 * wave, 4 * wave}) {   // the distributed loop: its launch grid
+      gf_batch_tuning t{};
+      t.graph = 1;
+      t.chunk = 8;
+      t.grid_budget = g;
+      t.solve_loop = GF_SOLVE_DISTRIBUTED;
+      cands.push_back(t);
+    }
   }
   double best_t = 1e300;
   gf_batch_tuning best_c = orig;

@@ -198,6 +198,34 @@ __device__ __forceinline__ int batch_locate(const BatchTab* __restrict__ tab, in
 }
 #endif
 
+// Work table of the distributed solver loop of a batch (GF_SOLVE_DISTRIBUTED):
+// the meshes that have not converged and, per solver-loop kind, the offsets
+// of their blocks (each mesh keeps its own single-mesh grid).  A kernel rebuilds
+// it on the device after every loop iteration; the loop kernels then run with a
+// fixed grid whose CTAs take the listed blocks in turn, so a converged mesh
+// costs nothing and an active one keeps its full grid.
+struct BatchAct {
+  int32_t n;                             // meshes still iterating
+  int32_t mesh[kMaxBatch];               // their ids, ascending
+  int32_t off[kBKinds][kMaxBatch + 1];   // per solver-loop kind: block offsets over them
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int act_locate(const BatchAct* __restrict__ a, int kind, unsigned w, unsigned& bid,
+                                          unsigned& nb) {
+  const int32_t* off = a->off[kind];
+  int lo = 0, hi = a->n;            // off[lo] <= w < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (unsigned(off[mid]) <= w) lo = mid;
+    else hi = mid;
+  }
+  bid = w - unsigned(off[lo]);
+  nb = unsigned(off[lo + 1] - off[lo]);
+  return a->mesh[lo];
+}
+#endif
+
 // Launch geometry of each kind for one mesh: (blocks, threads).
 struct LaunchDims {
   unsigned blocks, threads;
@@ -210,6 +238,10 @@ int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepS
 int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const StepScalars& sp, cudaStream_t s, int first);
 int launch_batch_fp64(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s);
 int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned threads, cudaStream_t s, int first);
+// Distributed solver-loop launches: `grid` CTAs over the blocks listed in `act`
+// (solver-loop kinds only; returns 0 for other kinds).
+int launch_dist_fp64(int kind, const BatchTab* tab, const BatchAct* act, unsigned grid, cudaStream_t s);
+int launch_dist_mixed(int kind, const BatchTab* tab, const BatchAct* act, unsigned grid, cudaStream_t s);
 
 // Persistent refinement solve (GF_MIXED): one cooperative launch runs the whole
 // solver loop of every mesh in `tab` (inner FP32 PCG and double-float

@@ -1322,6 +1322,22 @@ __global__ void __launch_bounds__(kThreads) kb_integrate(const BatchTab* __restr
   integrate_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
+// Distributed solver-loop kernels of a batch (see the mixed ones).
+#define GF_DIST_KERNEL(name, kind, body)                                                               \
+  __global__ void __launch_bounds__(kThreads) name(const BatchTab* __restrict__ tab, const BatchAct* __restrict__ act) { \
+    const int total = act->off[kind][act->n];                                                          \
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {                                              \
+      unsigned bid, nb;                                                                                \
+      const int k = act_locate(act, kind, unsigned(w), bid, nb);                                       \
+      body;                                                                                            \
+      __syncthreads();                                                                                 \
+    }                                                                                                  \
+  }
+GF_DIST_KERNEL(kd_pcg_spmv, kB_pcg_spmv, pcg_spmv_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+GF_DIST_KERNEL(kd_pcg_update, kB_pcg_update, pcg_update_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+GF_DIST_KERNEL(kd_pcg_p, kB_pcg_p, pcg_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+#undef GF_DIST_KERNEL
+
 }  // namespace
 
 // Quasi-static kernels: grid-stride over at most four CTAs per SM of the
@@ -1406,6 +1422,16 @@ int launch_kind_fp64(int kind, const DevMesh& m, const Material& mt, const StepS
     case kB_true_residual: k_true_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_integrate: k_integrate<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     default: return -1;
+  }
+  return 1;
+}
+
+int launch_dist_fp64(int kind, const BatchTab* tab, const BatchAct* act, unsigned grid, cudaStream_t s) {
+  switch (kind) {
+    case kB_pcg_spmv: kd_pcg_spmv<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_pcg_update: kd_pcg_update<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_pcg_p: kd_pcg_p<<<grid, kThreads, 0, s>>>(tab, act); break;
+    default: return 0;
   }
   return 1;
 }

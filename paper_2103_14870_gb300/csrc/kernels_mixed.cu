@@ -316,7 +316,7 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
     if (live && t < m.T) reinterpret_cast<float2*>(x.sig_bar32 + 8 * t)[sl & 3] = tot;
   }
 }
-__global__ void __launch_bounds__(kNlThreads, 3) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
+__global__ void __launch_bounds__(kNlThreads, 4) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
   nonlocal32_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kNlThreads, 3) kb_nonlocal32(const BatchTab* __restrict__ tab) {
@@ -1084,7 +1084,43 @@ __global__ void kb_chi_to32(const BatchTab* __restrict__ tab) {
   chi_to32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
+// Distributed solver-loop kernels of a batch: a fixed grid whose CTAs take the
+// blocks listed in the work table in turn (the same bodies, the same per-mesh
+// block index and count as the per-kind launches).
+#define GF_DIST_KERNEL(name, bounds, kind, body)                                                       \
+  __global__ void __launch_bounds__ bounds name(const BatchTab* __restrict__ tab, const BatchAct* __restrict__ act) { \
+    const int total = act->off[kind][act->n];                                                          \
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {                                              \
+      unsigned bid, nb;                                                                                \
+      const int k = act_locate(act, kind, unsigned(w), bid, nb);                                       \
+      body;                                                                                            \
+      __syncthreads();                                                                                 \
+    }                                                                                                  \
+  }
+GF_DIST_KERNEL(kd_ir_residual, (kThreads, 5), kB_ir_residual,
+               ir_residual_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb, 0))
+GF_DIST_KERNEL(kd_ir_inner_init, (kThreads), kB_ir_inner_init,
+               ir_inner_init_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+GF_DIST_KERNEL(kd_ir_spmv, (kThreads), kB_ir_spmv, ir_spmv_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+GF_DIST_KERNEL(kd_ir_update, (kThreads), kB_ir_update, ir_update_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+GF_DIST_KERNEL(kd_ir_p, (kThreads), kB_ir_p, ir_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+GF_DIST_KERNEL(kd_ir_apply, (kThreads), kB_ir_apply, ir_apply_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb))
+#undef GF_DIST_KERNEL
+
 }  // namespace
+
+int launch_dist_mixed(int kind, const BatchTab* tab, const BatchAct* act, unsigned grid, cudaStream_t s) {
+  switch (kind) {
+    case kB_ir_residual: kd_ir_residual<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_ir_inner_init: kd_ir_inner_init<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_ir_spmv: kd_ir_spmv<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_ir_update: kd_ir_update<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_ir_p: kd_ir_p<<<grid, kThreads, 0, s>>>(tab, act); break;
+    case kB_ir_apply: kd_ir_apply<<<grid, kThreads, 0, s>>>(tab, act); break;
+    default: return 0;
+  }
+  return 1;
+}
 
 // the element kernels stage 53.8 KB of rows in shared memory: raise the limit once per device
 void elem32_smem_attr() {

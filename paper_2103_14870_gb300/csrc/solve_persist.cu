@@ -12,10 +12,16 @@
 //   * every phase serves all meshes of a batch at once and only those that
 //     need it: the CTAs take the phase's blocks of the active meshes in
 //     turn, so a converged mesh costs nothing while the others iterate.
-// Data written during the launch is read with ld.global.cg (L2): the L1 of
-// another SM may hold a stale copy.  Reductions keep the kernels' per-block
-// partials and fixed-order sums (the last block of a mesh sums them), so a
-// mesh's scalars do not depend on how many meshes share the launch.
+// Vectors written by other CTAs are read only after the grid barrier that
+// ends their phase, whose acquire fence (as in a cooperative grid sync) makes
+// those writes visible; the solver scalars, which a phase's last block writes,
+// are read and written through volatile accesses.  Reductions keep the
+// kernels' per-block partials and fixed-order sums (the last block of a mesh
+// sums them), so a mesh's scalars do not depend on how many meshes share the
+// launch.  Measured on GB300 a barrier over 456 CTAs costs about 3.2 us, about
+// a kernel boundary inside a CUDA graph, so the persistent form does not beat
+// the graph of phase kernels on one mesh; its use is the batch, where phases
+// skip the meshes that have converged.
 #include <cmath>
 
 #include "gf_device.h"

@@ -67,7 +67,7 @@ class Tuning(ctypes.Structure):
 
 ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
 STEP_GRAPH, STEP_STREAM = 0, 1
-SOLVE_KERNELS, SOLVE_PERSISTENT, SOLVE_CG = 0, 1, 2
+SOLVE_KERNELS, SOLVE_PERSISTENT, SOLVE_CG, SOLVE_DISTRIBUTED = 0, 1, 2, 3
 
 
 class BatchTuning(ctypes.Structure):

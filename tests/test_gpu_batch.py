@@ -84,10 +84,16 @@ def test_batch_equals_single_meshes(precision, graph):
 
 
 @pytest.mark.parametrize("precision", [gf.FP64, gf.MIXED])
-def test_batch_grid_budget(precision):
-    """A grid budget (the loop kernels' CTAs split over the meshes by size)
-    changes only the reductions' summation order: members agree with their
-    single-mesh steps to rounding and converge to the same tolerance."""
+@pytest.mark.parametrize("form,grid,graph", [(gf.SOLVE_KERNELS, 48, 1), (gf.SOLVE_DISTRIBUTED, 48, 1),
+                                             (gf.SOLVE_DISTRIBUTED, 7, 0), (gf.SOLVE_DISTRIBUTED, 0, 1)],
+                         ids=["budget-48", "distributed-48", "distributed-7-stream", "distributed-default"])
+def test_batch_grid_budget(precision, form, grid, graph):
+    """A grid budget (the loop kernels' CTAs split over the meshes by size), or
+    the distributed loop (a fixed grid split over the meshes still iterating,
+    from a work table rebuilt on the device each iteration; 7 CTAs make each
+    CTA take many blocks), changes only the reductions' summation order:
+    members agree with their single-mesh steps to rounding and converge to the
+    same tolerance."""
     ws = box_workloads()
     states, thetas = start_states(ws)
     singles = make(ws, precision, thetas)
@@ -96,8 +102,8 @@ def test_batch_grid_budget(precision):
         for m in (m1, m2):
             m.state_set(x=st.x.ravel(), v=st.v.ravel())
     batch = gf.Batch(members)
-    batch.tuning_set(graph=1, chunk=8, grid_budget=48)
-    assert batch.tuning_get()["grid_budget"] == 48
+    batch.tuning_set(graph=graph, chunk=8, grid_budget=grid, solve_loop=form)
+    assert batch.tuning_get()["grid_budget"] == grid and batch.tuning_get()["solve_loop"] == form
     f = [w.f_ext.ravel() for w in ws]
     pins = [w.pinned for w in ws]
     bstats = batch.step(1e-3, f, pins)
