@@ -213,8 +213,9 @@ gf_status gf_tuning_set(gf_mesh* mesh, const gf_tuning* tuning);
 gf_status gf_tuning_get(const gf_mesh* mesh, gf_tuning* tuning);
 
 /* GF_MIXED: relative tolerance of each inner FP32 PCG solve of the FP64
- * iterative refinement (default 1e-4; 0 < inner_rtol < 1).  The outer FP64
- * tolerance stays cg_rtol. */
+ * iterative refinement (default 1e-5; 0 < inner_rtol < 1; each inner solve also
+ * stops after 32 iterations).  The outer FP64 tolerance stays cg_rtol.  At the
+ * default, a well-conditioned system at cg_rtol 1e-6 needs one sweep. */
 gf_status gf_refine_set(gf_mesh* mesh, double inner_rtol);
 
 /* Change the break threshold sigma_thres of Eq. 21 between steps (same units

@@ -162,7 +162,7 @@ struct gf_mesh {
   gf_tuning tune{};           // assembly schedule etc. (defaults: two-phase gather)
   bool mixed = false;
   int last_inner = 3;
-  double in_rtol = 1e-4;
+  double in_rtol = 1e-5;
   int newton_iters = 1;       // Newton iterations per step (FP64 path)
   double newton_rtol = 0.0;   // stop early when |r(v^k)| <= newton_rtol |b^0| on free DOFs
   int newton_done = 1;        // iterations of the last step
@@ -543,6 +543,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.nb_w2, mxh.nb_w2, float);
     UP(d.mx.nl_uptr, mxh.nl_uptr, int64_t);
     UP(d.mx.nl_uidx, mxh.nl_uidx, int32_t);
+    d.mx.nl_cap = mxh.nl_cap;
     m->joint_entries = int64_t(mxh.nb_loc.size());
     m->union_rows = int64_t(mxh.nl_uidx.size());
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());

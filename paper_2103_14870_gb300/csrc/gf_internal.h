@@ -54,7 +54,8 @@ enum Rest32Field : int { kRAE0 = 0, kRAH = 9, kRAV = 30, kRAStride = 32, kRBStri
 // which stages the union of their neighbour sets (at most kNlCap rows) in
 // shared memory; each pair names its neighbour by its position in that union.
 constexpr int kNlTile = 128;
-constexpr int kNlCap = 1792;
+constexpr int kNlCap = 1792;      // staged rows of a batched launch (one shared-memory size for all meshes)
+constexpr int kNlCapMax = 9216;   // staged rows of a single-mesh launch at most (216 KB)
 constexpr int64_t kNlMaxUnion = 65536;   // 16-bit positions
 
 // Extra host data of the mixed-precision path (two-phase assembly).
@@ -72,6 +73,7 @@ struct MixedHost {
   std::vector<float> nb_w2;         // [entries][2]
   std::vector<int64_t> nl_uptr;
   std::vector<int32_t> nl_uidx;
+  int32_t nl_cap = 0;               // rows a single-mesh launch stages: the largest union, at most kNlCapMax
 };
 
 

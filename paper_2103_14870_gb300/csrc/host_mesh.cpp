@@ -598,7 +598,12 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
       return GF_UNSUPPORTED;
     }
     mx.nl_uptr.assign(NT + 1, 0);
-    for (int64_t g = 0; g < NT; ++g) mx.nl_uptr[g + 1] = mx.nl_uptr[g] + int64_t(U[g].size());
+    int64_t largest = 0;
+    for (int64_t g = 0; g < NT; ++g) {
+      mx.nl_uptr[g + 1] = mx.nl_uptr[g] + int64_t(U[g].size());
+      largest = std::max<int64_t>(largest, int64_t(U[g].size()));
+    }
+    mx.nl_cap = int32_t(std::min<int64_t>(largest, kNlCapMax));
     mx.nl_uidx.resize(mx.nl_uptr[NT]);
     for (int64_t g = 0; g < NT; ++g) std::copy(U[g].begin(), U[g].end(), mx.nl_uidx.begin() + mx.nl_uptr[g]);
     mx.nb_ptr.assign(NQ + 1, 0);

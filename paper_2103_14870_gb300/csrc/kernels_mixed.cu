@@ -159,8 +159,10 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
 
 // Eq. 20 sum in FP32, tiled.  A CTA takes kNlTile consecutive tets and first
 // stages the union of their neighbour sets (ascending tet ids, six floats a
-// row) in shared memory; a tile whose union exceeds kNlCap rows reads the rows
-// from global memory instead.  Each pair of tets (2q, 2q+1) has a joint list:
+// row) in shared memory; a tile whose union exceeds the staged capacity reads
+// the rows from global memory instead.  A single-mesh launch stages as many
+// rows as the mesh's largest union (at most kNlCapMax), so its occupancy
+// follows the radius; a batched launch stages kNlCap rows for every mesh.  Each pair of tets (2q, 2q+1) has a joint list:
 // the union of the two neighbour lists, per entry a 16-bit union position and
 // the two FP32 weights (zero where a tet lacks that neighbour), so one staged
 // row read serves both tets (0.61 row reads per (tet, neighbour) pair on the
@@ -174,7 +176,8 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
 // pair reads at once fall on distinct shared-memory bank pairs, and the two
 // pairs of a half-warp on opposite halves of the banks.
 constexpr int kNlThreads = 256, kNlWarpPairs = kNlTile / 2 / (kNlThreads / 32);
-constexpr unsigned kNlSmem = kNlCap * 24;
+constexpr unsigned kNlSmem = kNlCap * 24;           // batched launches
+constexpr unsigned kNlSmemMax = kNlCapMax * 24;     // single-mesh launches at most
 constexpr int kNlBatch = 6;   // entries of a lane in flight per load batch
 
 struct NlBatch {
@@ -252,29 +255,33 @@ __device__ __forceinline__ float2 group_transpose_sum(const float (&v)[16], int 
   return make_float2(k0, k1);
 }
 
-__device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-  extern __shared__ float2 su[];   // [kNlCap][3]: stress rows of the tile's union
-  constexpr int kStage = (kNlCap + kNlThreads - 1) / kNlThreads;
+// cap: rows this launch stages (its dynamic shared memory / 24 B)
+__device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb,
+                                                int cap) {
+  extern __shared__ float2 su[];   // [cap][3]: stress rows of the tile's union
+  constexpr int kStage = 8;        // union rows of a thread in flight together
   const MixDev& x = m.mx;
   const int64_t t0 = int64_t(bid) * kNlTile;
   const int64_t u0 = x.nl_uptr[bid], un = x.nl_uptr[bid + 1] - u0;
-  const bool staged = un <= kNlCap;
-  if (staged) {   // all of a thread's union ids, then all of its rows, in flight together
-    int64_t j[kStage];
+  const bool staged = un <= cap;
+  if (staged) {   // a thread's union ids, then their rows, kStage at a time in flight together
+    for (int64_t r0 = 0; r0 < un; r0 += int64_t(kStage) * kNlThreads) {
+      int64_t j[kStage];
 #pragma unroll
-    for (int c = 0; c < kStage; ++c) {
-      const int64_t r = threadIdx.x + int64_t(c) * kNlThreads;
-      j[c] = r < un ? __ldg(x.nl_uidx + u0 + r) : -1;
-    }
+      for (int c = 0; c < kStage; ++c) {
+        const int64_t r = r0 + threadIdx.x + int64_t(c) * kNlThreads;
+        j[c] = r < un ? __ldg(x.nl_uidx + u0 + r) : -1;
+      }
 #pragma unroll
-    for (int c = 0; c < kStage; ++c) {
-      if (j[c] < 0) continue;
-      const int64_t r = threadIdx.x + int64_t(c) * kNlThreads;
-      float sj[8];
-      ld8f(x.sig_in32 + 8 * j[c], sj);
-      su[3 * r] = make_float2(sj[0], sj[1]);
-      su[3 * r + 1] = make_float2(sj[2], sj[3]);
-      su[3 * r + 2] = make_float2(sj[4], sj[5]);
+      for (int c = 0; c < kStage; ++c) {
+        if (j[c] < 0) continue;
+        const int64_t r = r0 + threadIdx.x + int64_t(c) * kNlThreads;
+        float sj[8];
+        ld8f(x.sig_in32 + 8 * j[c], sj);
+        su[3 * r] = make_float2(sj[0], sj[1]);
+        su[3 * r + 1] = make_float2(sj[2], sj[3]);
+        su[3 * r + 2] = make_float2(sj[4], sj[5]);
+      }
     }
   }
   __syncthreads();
@@ -317,12 +324,12 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
   }
 }
 __global__ void __launch_bounds__(kNlThreads, 4) k_nonlocal32(DevMesh m, Material mt, StepScalars sp) {
-  nonlocal32_body(m, mt, sp, blockIdx.x, gridDim.x);
+  nonlocal32_body(m, mt, sp, blockIdx.x, gridDim.x, m.mx.nl_cap);
 }
 __global__ void __launch_bounds__(kNlThreads, 3) kb_nonlocal32(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_nonlocal32, blockIdx.x, bid, nb);
-  nonlocal32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+  nonlocal32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb, kNlCap);
 }
 
 __device__ __forceinline__ void edge_driver32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
@@ -1122,13 +1129,15 @@ int launch_dist_mixed(int kind, const BatchTab* tab, const BatchAct* act, unsign
   return 1;
 }
 
-// the element kernels stage 53.8 KB of rows in shared memory: raise the limit once per device
+// the element kernels stage 53.8 KB of rows in shared memory, a single-mesh
+// Eq. 20 launch up to 216 KB of union rows: raise the limits once per device
 void elem32_smem_attr() {
   static bool done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
   cudaFuncSetAttribute(k_elem32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kElemSmem));
   cudaFuncSetAttribute(kb_elem32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kElemSmem));
+  cudaFuncSetAttribute(k_nonlocal32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kNlSmemMax));
   done[dev] = true;
 }
 
@@ -1137,7 +1146,10 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
   if (d.blocks == 0) return 0;
   switch (kind) {
     case kB_tet_stress32: k_tet_stress32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_nonlocal32: k_nonlocal32<<<d.blocks, d.threads, kNlSmem, s>>>(m, mt, sp); break;
+    case kB_nonlocal32:   // stages nl_cap rows of 24 B
+      elem32_smem_attr();
+      k_nonlocal32<<<d.blocks, d.threads, unsigned(m.mx.nl_cap) * 24u, s>>>(m, mt, sp);
+      break;
     case kB_edge_driver32: k_edge_driver32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_tet_chi32: k_tet_chi32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_elem32:

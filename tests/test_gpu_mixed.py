@@ -132,9 +132,11 @@ def test_mixed_resume_bit_identical_and_rest():
 @pytest.mark.parametrize("dims,radius", [((3, 3, 7), 1.5), ((6, 6, 12), 3.0)], ids=["ragged-tile", "large-unions"])
 def test_mixed_nonlocal_tiles(dims, radius):
     """The tiled Eq. 20 kernel (128 tets per CTA, neighbour union staged in
-    shared memory up to 1,792 rows, read from global memory beyond) on a mesh
-    whose last tile is partial (378 tets) and on one whose tile unions exceed
-    the staged capacity (R_d = 3 on 2,592 tets), against the oracle."""
+    shared memory) on a mesh whose last tile is partial (378 tets) and on one
+    whose tile unions exceed 1,792 rows (R_d = 3 on 2,592 tets), against the
+    oracle.  A single-mesh launch stages the mesh's largest union; a batched
+    launch stages 1,792 rows, so in a batch those tiles read global memory:
+    the batch member must give the single-mesh drivers bit for bit."""
     from oracle import mesh as omesh
     from workloads import Workload
     from workloads.meshes import jitter, kuhn_box
@@ -166,3 +168,10 @@ def test_mixed_nonlocal_tiles(dims, radius):
     assert_close(drv, info["driver"], rtol=RTOL32, floor=FLOOR32, what="driver (mixed, tiles)")
     assert_labels(lab, info["labels"], info["driver"], theta, band=BAND32)
     assert lab.sum() > 0
+    member = mixed_mesh(w, gpu_material(gf, w, threshold=theta, radius=radius))
+    member.state_set(x=st.x.ravel(), v=st.v.ravel(), labels=st.labels, chi=st.chi)
+    b = gf.Batch([member])
+    sb = b.step(w.dt, [w.f_ext.ravel()], [w.pinned])
+    assert sb[0]["status"] == 0
+    np.testing.assert_array_equal(member.damage_get()[0], drv)
+    b.close()
