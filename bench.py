@@ -423,7 +423,9 @@ def run_glass(args, gf, torch, barrier, stream) -> dict:
     mat = gf.material(w.young, w.poisson, w.density, threshold=theta, radius=w.radius)
     mm = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=w.cg_rtol)
     steps = min(args.steps, 100)
+    clk = ClockSampler(torch.cuda.current_device())
     fp64 = timed_from_rest(args, m64, w, f_dev, pins, barrier, stream, torch, steps)
+    fp64["clocks"] = clk.stop()
     m64.tuning_set(solve_loop=gf.SOLVE_CG)
     fp64_cg = timed_from_rest(args, m64, w, f_dev, pins, barrier, stream, torch, min(steps, 30))
     fp64_cg.pop("_prof")
@@ -432,7 +434,9 @@ def run_glass(args, gf, torch, barrier, stream) -> dict:
     mixed_p = timed_from_rest(args, mm, w, f_dev, pins, barrier, stream, torch, min(steps, 30))
     mixed_p.pop("_prof")
     mm.tuning_set(solve_loop=gf.SOLVE_KERNELS)
+    clk = ClockSampler(torch.cuda.current_device())
     mixed = timed_from_rest(args, mm, w, f_dev, pins, barrier, stream, torch, steps)
+    mixed["clocks"] = clk.stop()
     pk = peaks()
     for form, r, pre, mesh in (("fp64", fp64, "", m64), ("mixed", mixed, "m:", mm)):
         prof = r.pop("_prof")

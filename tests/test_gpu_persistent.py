@@ -2,8 +2,9 @@
 
 The whole refinement loop (inner FP32 PCG, double-float residual) runs as one
 cooperative launch with grid barriers between its phases.  Its phases do the
-arithmetic of the kernel-by-kernel form over the same row partition, so the
-two forms must agree to the last bit; the persistent form must match the FP64
+arithmetic of the kernel-by-kernel form (a lone mesh's phases group the rows
+into at most one CTA set), so the two forms must agree to rounding and its
+graph replay and stream launches to the last bit; the persistent form must match the FP64
 oracle at the reduced-precision bar on a fracturing beam and on a stiff
 (glass-like) beam with many inner iterations; a batch's members must step as
 they do alone; and a barrier wait that runs out (a test hook makes one CTA
