@@ -55,7 +55,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(lambda a: _compile(a[0], a[1], verbose), zip(SOURCES, objs)))
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gf_device.h"
 #include "gf_gnn.h"
 #include "gf_surface.h"
@@ -310,10 +312,23 @@ int prof_mark(gf_mesh* m) {
   cudaEventRecord(m->ev_pool[i], m->stream);
   return i;
 }
+// An NVTX range on the host thread (header-only NVTX 3: it costs a pointer
+// test when no tool is attached): tools such as Nsight Systems show the phases
+// of a call and which kernels each phase enqueued.
+struct Nvtx {
+  explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+  Nvtx(const Nvtx&) = delete;
+  Nvtx& operator=(const Nvtx&) = delete;
+};
+
+// A kernel group of a step: an NVTX range named after the group and, when
+// profiling is on, CUDA events on the mesh's stream around its launches.
 struct Prof {
   gf_mesh* m;
   int group, ev0 = -1, iter;
-  Prof(gf_mesh* mm, int g, int it = -1) : m(mm), group(g), iter(it) {
+  Nvtx range;
+  Prof(gf_mesh* mm, int g, int it = -1) : m(mm), group(g), iter(it), range(kProfNames[g]) {
     if (m->prof) ev0 = prof_mark(m);
   }
   ~Prof() {
@@ -1281,6 +1296,7 @@ gf_status gf_step(gf_mesh* m, double dt, const double* f_ext, const int32_t* pin
         return GF_BAD_ARG;
       }
   DeviceGuard guard(m->device);
+  Nvtx range(graph_step_ok(m) ? "gf_step (graph replay)" : "gf_step");
   cudaStream_t s = m->stream;
   DevMesh d = m->dm;   // per-step view (input pointers may be overridden)
   const int64_t N = d.N;
@@ -1398,6 +1414,7 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
         return GF_BAD_ARG;
       }
   DeviceGuard guard(m->device);
+  Nvtx range("gf_quasistatic_step");
   cudaStream_t s = m->stream;
   DevMesh d = m->dm;
   const int64_t N = d.N;
@@ -2391,6 +2408,7 @@ gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, cons
       return GF_UNSUPPORTED;
     }
   DeviceGuard guard(b->device);
+  Nvtx range("gf_batch_step");
   gf_status st = batch_prepare(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem);
   if (st != GF_OK) return st;
   return batch_run(b, stats);

@@ -10,9 +10,11 @@ built library or a CUDA device, calls raise.
 from __future__ import annotations
 
 import ctypes
+import json
 import weakref
 import math
 import os
+import time
 from typing import Optional
 
 import numpy as np
@@ -82,6 +84,13 @@ class MeshInfo(ctypes.Structure):
 
 _LIB = None
 P = ctypes.c_void_p
+
+
+def metrics_line(step: int, dt: float, status: int, stats: dict) -> str:
+    """One JSON line of the per-step metrics log."""
+    rec = {"step": int(step), "time": time.time(), "dt": float(dt), "status": int(status)}
+    rec.update({k: (float(v) if isinstance(v, float) else int(v)) for k, v in stats.items()})
+    return json.dumps(rec, sort_keys=True)
 
 
 def load_library(path: Optional[str] = None) -> ctypes.CDLL:
@@ -207,9 +216,21 @@ class Mesh:
         self._h = handle
         self.n_nodes, self.n_tets, self.n_edges = n_nodes, n_tets, n_edges
         self._keep = keep
+        self._log, self._log_steps = None, 0
+
+    def metrics_log(self, path: Optional[str]):
+        """Append one JSON line per step (step number, wall time, dt and the
+        step's statistics) to `path`; None stops logging."""
+        if self._log is not None:
+            self._log.close()
+        self._log = open(path, "a") if path else None
+        self._log_steps = 0
 
     # -- lifetime ---------------------------------------------------------
     def close(self):
+        if getattr(self, "_log", None) is not None:
+            self._log.close()
+            self._log = None
         if self._h:
             gnn = getattr(self, "_gnn", None)
             if gnn is not None and gnn() is not None:
@@ -251,6 +272,10 @@ class Mesh:
         st = StepStats()
         status = load_library().gf_step(self._h, float(dt), pf, pp, n_pin, pq, _one_kind(kf, kp, kq),
                                          ctypes.byref(st))
+        if self._log is not None:
+            self._log.write(metrics_line(self._log_steps, dt, status, st.as_dict()) + "\n")
+            self._log.flush()
+            self._log_steps += 1
         _check(status)
         return st.as_dict()
 

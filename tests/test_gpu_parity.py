@@ -217,3 +217,20 @@ def test_assembly_schedules_agree():
         out[sched] = (m.system_get()[2], m.velocities_get())
     np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-12, atol=1e-12 * np.abs(out[0][0]).max())
     assert np.linalg.norm(out[0][1] - out[1][1]) <= 1e-12 * np.linalg.norm(out[0][1])
+
+
+def test_metrics_log_one_line_per_step(tmp_path):
+    """The binding's per-step metrics log writes one JSON line per step with the
+    step's statistics."""
+    import json
+    w = beam_config()
+    m = gpu_mesh(w, gpu_material(gf, w), rtol=1e-8)
+    log = tmp_path / "steps.jsonl"
+    m.metrics_log(str(log))
+    stats = [m.step(w.dt, w.f_ext.ravel(), w.pinned) for _ in range(3)]
+    m.metrics_log(None)
+    recs = [json.loads(line) for line in log.read_text().splitlines()]
+    assert [r["step"] for r in recs] == [0, 1, 2]
+    assert [r["cg_iters"] for r in recs] == [s["cg_iters"] for s in stats]
+    assert all(r["status"] == 0 and r["dt"] == w.dt for r in recs)
+    m.close()
