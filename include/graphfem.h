@@ -187,9 +187,10 @@ enum { GF_STEP_GRAPH = 0, GF_STEP_STREAM = 1 };
  * GF_SOLVE_KERNELS (0, default): kernel by kernel, three per PCG iteration
  * (GF_FP64) or the refinement's phase kernels (GF_MIXED), as a WHILE node of
  * the step graph or with host checks in the stream form.
- * GF_SOLVE_CG (GF_FP64 only): the PCG in the Chronopoulos-Gear form (Chronopoulos
- * and Gear, 1989): w = A z and the three dot products in one kernel, the vector
- * updates in another, one grid reduction per iteration; the iterates equal the
+ * GF_SOLVE_CG: the PCG (GF_FP64) or the inner FP32 PCG of the refinement
+ * (GF_MIXED) in the Chronopoulos-Gear form (Chronopoulos and Gear, 1989):
+ * w = A z and the three dot products in one kernel, the vector updates in
+ * another, one grid reduction per iteration; the iterates equal the
  * three-kernel form's in exact arithmetic.
  * GF_SOLVE_PERSISTENT (GF_MIXED only): the whole refinement loop as one
  * cooperative launch (one CTA set resident on every SM), with grid barriers

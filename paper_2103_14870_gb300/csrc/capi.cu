@@ -77,8 +77,8 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_integrate: case kB_integrate32: case kB_refresh32: return {cdiv(3 * N, 256), 256};
     case kB_fext32: return {sp.has_fext ? cdiv(3 * N, 256) : 0u, 256};
     case kB_ir_residual: return {ir_grid(8 * N, 5), 256};
-    case kB_ir_spmv: return {ir_grid(16 * N), 256};
-    case kB_ir_inner_init: case kB_ir_update: return {ir_grid(N), 256};
+    case kB_ir_spmv: case kB_ir_cg_spmv: return {ir_grid(16 * N), 256};
+    case kB_ir_inner_init: case kB_ir_update: case kB_ir_cg_update: return {ir_grid(N), 256};
     case kB_ir_p: case kB_ir_apply: return {ir_grid(3 * N), 256};
     case kB_step_begin: return {cdiv(3 * N, 256), 256};
   }
@@ -598,7 +598,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
         (st = scratch(m, 70 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
         (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
-        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.p32b)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
+        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.p32b)) || (st = scratch(m, 3 * N, &x.w32)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
         (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) ||
         (st = scratch(m, 1, &x.ir)))
       return fail(st);
@@ -761,8 +761,8 @@ gf_status gf_tuning_set(gf_mesh* m, const gf_tuning* t) {
     set_last_error("bad tuning (solve_loop must be GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT or GF_SOLVE_CG, wait_test 0 or 1)");
     return GF_BAD_ARG;
   }
-  if ((t->solve_loop == GF_SOLVE_PERSISTENT && !m->mixed) || (t->solve_loop == GF_SOLVE_CG && m->mixed)) {
-    set_last_error("GF_SOLVE_PERSISTENT is built for GF_MIXED meshes, GF_SOLVE_CG for GF_FP64 meshes");
+  if (t->solve_loop == GF_SOLVE_PERSISTENT && !m->mixed) {
+    set_last_error("GF_SOLVE_PERSISTENT is built for GF_MIXED meshes");
     return GF_UNSUPPORTED;
   }
   m->tune = *t;
@@ -867,8 +867,10 @@ gf_status persist_setup(gf_mesh* m) {
 
 bool persist_on(const gf_mesh* m) { return m->mixed && m->tune.solve_loop == GF_SOLVE_PERSISTENT; }
 
-// GF_SOLVE_CG (GF_FP64): the Chronopoulos-Gear PCG needs the vector w = A z
+// GF_SOLVE_CG: the Chronopoulos-Gear PCG needs the vector w = A z (FP64: allocated
+// on first use; GF_MIXED: its FP32 w32 is allocated with the mesh)
 bool cg_form_on(const gf_mesh* m) { return !m->mixed && m->tune.solve_loop == GF_SOLVE_CG; }
+bool mixed_cg_on(const gf_mesh* m) { return m->mixed && m->tune.solve_loop == GF_SOLVE_CG; }
 gf_status cg_form_setup(gf_mesh* m, DevMesh& d) {
   if (!m->qs_w) {
     gf_status st = scratch(m, 3 * size_t(d.N), &m->qs_w);
@@ -1062,6 +1064,11 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
     for (int sw = 0; sw < 2; ++sw) {
       { Prof p(m, kPIrInit); L += launch_kind(kB_ir_inner_init, d, mt, sp, s); }
       for (int j = 0; j < K; ++j) {
+        if (mixed_cg_on(m)) {
+          { Prof p(m, kPSpmv, -2); L += launch_kind(kB_ir_cg_spmv, d, mt, sp, s); }
+          { Prof p(m, kPPcgUpdate, -2); L += launch_kind(kB_ir_cg_update, d, mt, sp, s); }
+          continue;
+        }
         { Prof p(m, kPSpmv, -2); L += launch_kind(kB_ir_spmv, d, mt, sp, s); }
         { Prof p(m, kPPcgUpdate, -2); L += launch_kind(kB_ir_update, d, mt, sp, s); }
         { Prof p(m, kPPcgP, -2); L += launch_kind(kB_ir_p, d, mt, sp, s); }
@@ -1176,8 +1183,13 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
   if (m->mixed) {
     for (int sw = 0; sw < 2; ++sw) {
       L += launch_kind(kB_ir_inner_init, d, mt, sp, bs);
-      for (int j = 0; j < loop; ++j)
+      for (int j = 0; j < loop; ++j) {
+        if (mixed_cg_on(m)) {
+          for (int kind : {kB_ir_cg_spmv, kB_ir_cg_update}) L += launch_kind(kind, d, mt, sp, bs);
+          continue;
+        }
         for (int kind : {kB_ir_spmv, kB_ir_update, kB_ir_p}) L += launch_kind(kind, d, mt, sp, bs);
+      }
       L += launch_kind(kB_ir_apply, d, mt, sp, bs);
       L += launch_kind(kB_ir_residual, d, mt, sp, bs, 0);
     }

@@ -1008,6 +1008,130 @@ __global__ void __launch_bounds__(kThreads) kb_ir_p(const BatchTab* __restrict__
   ir_p_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
+// Inner PCG in two kernels per iteration (GF_SOLVE_CG), the iterates of the
+// three-kernel form in exact arithmetic.  The search direction's image
+// q = A p follows the recurrence q = w + beta q with w = A z, and p.A.p =
+// z.A.z - beta gamma / alpha_old (the identity of Chronopoulos and Gear, J.
+// Comput. Appl. Math. 25, 1989; gamma = r.z), so the direction update joins the
+// vector update.  k_ir_cg_spmv forms w = A32 z and z.w in double-float; its
+// last CTA takes alpha = gamma / p.A.p.  k_ir_cg_update applies p = z + beta p,
+// q = w + beta q, d += alpha p, r -= alpha q, z = P r and reduces r.z and r.r
+// in double-float; its last CTA counts the iteration, stops the inner solve at
+// in_rtol (or the iteration limits) and takes beta = gamma_new / gamma.  Each
+// kernel keeps the three-kernel form's single dot product per row in its tail.
+__device__ __forceinline__ void ir_cg_spmv_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid,
+                                                unsigned nb) {
+  IrState* S = m.mx.ir;
+  if (S->done || S->in_done) return;
+  const MixDev& x = m.mx;
+  const int j16 = threadIdx.x & 15;
+  const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+  float h[1] = {0.f}, l[1] = {0.f};
+  const int64_t nh = (int64_t(nb) * blockDim.x) >> 4;
+  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+    for (int b = m.row_ptr[i] + j16; b < m.row_ptr[i + 1]; b += 16) {
+      const int64_t j = m.col[b];
+      const float* a = x.val32 + 9 * int64_t(b);
+      const float z0 = x.z32[3 * j], z1 = x.z32[3 * j + 1], z2 = x.z32[3 * j + 2];
+      y0 += a[0] * z0 + a[1] * z1 + a[2] * z2;
+      y1 += a[3] * z0 + a[4] * z1 + a[5] * z2;
+      y2 += a[6] * z0 + a[7] * z1 + a[8] * z2;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      y0 += __shfl_xor_sync(hmask, y0, o);
+      y1 += __shfl_xor_sync(hmask, y1, o);
+      y2 += __shfl_xor_sync(hmask, y2, o);
+    }
+    if (j16 == 0) {
+      const float y[3] = {y0, y1, y2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x.w32[3 * i + c] = y[c];
+        df_acc_prod(h[0], l[0], x.z32[3 * i + c], y[c]);   // z is zero on pinned rows
+      }
+    }
+  }
+  double out[1];
+  if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 11, out, bid, nb) && threadIdx.x == 0) {
+    const double den = S->in_iters > 0 ? out[0] - S->beta * S->rz / S->alpha : out[0];   // p.A.p
+    S->pq = den;
+    if (!(den > 0.0)) {
+      if (!isfinite(den)) {
+        S->status = GF_NAN;
+        S->done = 1;
+      } else if (S->in_iters == 0) {
+        S->status = GF_CG_BREAKDOWN;
+        S->done = 1;
+      }
+      S->in_done = 1;   // lost positive definiteness in FP32: hand back to the refinement
+    } else {
+      S->alpha = S->rz / den;
+      S->alpha32 = float(S->alpha);
+    }
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_ir_cg_spmv(DevMesh m, Material mt, StepScalars sp) {
+  ir_cg_spmv_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void ir_cg_update_body(const DevMesh& m, const Material& mt, const StepScalars& sp,
+                                                  unsigned bid, unsigned nb) {
+  IrState* S = m.mx.ir;
+  if (S->done || S->in_done) return;
+  const MixDev& x = m.mx;
+  const float alpha = S->alpha32, beta = S->beta32;
+  const bool first = S->in_iters == 0;   // p = z, q = w
+  float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
+  for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
+    float p[3], q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float z = x.z32[3 * i + c], w = x.w32[3 * i + c];
+      p[c] = first ? z : z + beta * x.p32[3 * i + c];
+      q[c] = first ? w : w + beta * x.q32[3 * i + c];
+      x.p32[3 * i + c] = p[c];
+      x.q32[3 * i + c] = q[c];
+    }
+    if (m.pinned[i]) continue;
+    float r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x.d32[3 * i + c] += alpha * p[c];
+      r[c] = x.r32[3 * i + c] - alpha * q[c];
+      x.r32[3 * i + c] = r[c];
+    }
+    const float* pi = x.pinv32 + 9 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
+      x.z32[3 * i + c] = z;
+      df_acc_prod(h[0], l[0], r[c], z);
+      df_acc_prod(h[1], l[1], r[c], r[c]);
+    }
+  }
+  double out[2];
+  if (grid_reduce_df<2>(h, l, m.partials, m.tickets + 12, out, bid, nb) && threadIdx.x == 0) {
+    S->in_iters += 1;
+    S->total_iters += 1;
+    S->beta = out[0] / S->rz;
+    S->beta32 = float(S->beta);
+    S->rz = out[0];
+    S->in_rr = out[1];
+    if (!isfinite(out[0]) || !isfinite(out[1])) {
+      S->status = GF_NAN;
+      S->done = 1;
+      S->in_done = 1;
+    } else if (!(out[1] > S->in_tol2 * S->in_rr0) || S->in_iters >= S->in_maxit || S->total_iters >= S->maxit) {
+      S->in_done = 1;
+    }
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_ir_cg_update(DevMesh m, Material mt, StepScalars sp) {
+  ir_cg_update_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+
 // dv += d on free rows once the inner solve has finished, kept as a float pair
 // (dv_hi + dv_lo) on the FP32 pipe.  Writes no flag: every CTA decides from the
 // same state (the residual that follows marks the correction as applied).
@@ -1166,6 +1290,8 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
     case kB_ir_update: k_ir_update<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_p: k_ir_p<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_apply: k_ir_apply<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_cg_spmv: k_ir_cg_spmv<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
+    case kB_ir_cg_update: k_ir_cg_update<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_integrate32: k_integrate32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_refresh32: k_refresh32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_chi_to32: k_chi_to32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
