@@ -578,19 +578,32 @@ def run_extensions(args, gf, torch, barrier, stream, w, f_dev, m_main) -> dict:
     lo = np.nonzero(X[:, 0] <= X[:, 0].min() + 0.1 * L)[0].astype(np.int32)
     hi = np.nonzero(X[:, 0] >= X[:, 0].max() - 0.1 * L)[0].astype(np.int32)
     pins = np.concatenate([lo, hi])
-    m_main.state_set(x=X.ravel(), v=np.zeros(X.size), labels=np.zeros(m_main.n_edges, np.uint8))
-    qs = []
-    for k in range(1, 4):
-        target = X[pins].copy()
-        target[:len(lo), 0] -= 1e-4 * L * k
-        target[len(lo):, 0] += 1e-4 * L * k
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s = m_main.quasistatic_step(None, pins, target, max_newton=20, rtol=1e-6)
-        qs.append({"ms": 1e3 * (time.perf_counter() - t0), "newton_iters": s["newton_iters"],
-                   "cg_iters": s["cg_iters"], "rel_res": s["rel_res"], "n_broken": s["n_broken"]})
+    def pull(solver):
+        m_main.quasistatic_solver_set(solver)
+        m_main.state_set(x=X.ravel(), v=np.zeros(X.size), labels=np.zeros(m_main.n_edges, np.uint8),
+                         chi=np.ones(m_main.n_tets))
+        qs = []
+        for k in range(1, 4):
+            target = X[pins].copy()
+            target[:len(lo), 0] -= 1e-4 * L * k
+            target[len(lo):, 0] += 1e-4 * L * k
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = m_main.quasistatic_step(None, pins, target, max_newton=20, rtol=1e-6)
+            qs.append({"ms": 1e3 * (time.perf_counter() - t0), "newton_iters": s["newton_iters"],
+                       "cg_iters": s["cg_iters"], "rel_res": s["rel_res"], "n_broken": s["n_broken"]})
+        return qs, m_main.positions_get(), m_main.damage_get()[1]
+    qs_n, x_n, lab_n = pull(gf.QS_SOLVE_NESTED)
+    qs, x_64, lab_64 = pull(gf.QS_SOLVE_FP64)
+    dx = np.abs(x_64 - X.ravel()).max()
     out["quasistatic_pull_fp64"] = {"load_steps": qs, "inner_cg_rtol": w.cg_rtol,
                                     "ms_per_load_step": statistics.mean(q["ms"] for q in qs)}
+    out["quasistatic_pull_nested_fp32_inner"] = {
+        "solver": "flexible FP64 PCG, inner FP32 PCG (two kernels per iteration) to 1e-2, one graph per solve",
+        "load_steps": qs_n, "ms_per_load_step": statistics.mean(q["ms"] for q in qs_n),
+        "speedup_vs_fp64": statistics.mean(q["ms"] for q in qs) / statistics.mean(q["ms"] for q in qs_n),
+        "after_3_load_steps_vs_fp64": {"max_abs_dx_over_max_displacement": float(np.abs(x_n - x_64).max() / dx),
+                                       "labels_differing": int((lab_n != lab_64).sum())}}
     # split visualisation mesh of the pulled state (device output)
     sz = m_main.surface_sizes()
     V = torch.empty((sz["n_vertices"], 3), dtype=torch.float64, device="cuda")

@@ -263,6 +263,23 @@ gf_status gf_quasistatic_step(gf_mesh* mesh, const double* f_ext, const int32_t*
                               const double* pinned_pos, int32_t mem, int32_t max_newton, double rtol,
                               gf_step_stats* stats);
 
+/* Linear solver of the quasi-static Newton iterations (GF_FP64 meshes).
+ * GF_QS_SOLVE_FP64 (default): the PCG in FP64 (Chronopoulos-Gear form).
+ * GF_QS_SOLVE_NESTED: flexible PCG in FP64 (Notay, 2000; one previous
+ * direction kept) whose preconditioner is an inner PCG in FP32 on the matrix
+ * and the block-Jacobi inverses rounded to FP32 (two kernels per iteration),
+ * run until its residual falls by inner_rtol (0 < inner_rtol < 1; a value <= 0
+ * keeps the current one, default 1e-2).  The outer residual, iterate and
+ * coefficients are FP64 and the outer test is the FP64 PCG's
+ * (|r| <= cg_rtol |b|), so the Newton iterations solve the same FP64 systems;
+ * the outer Krylov iteration keeps converging where the FP32 matrix's rounding
+ * would stall plain refinement.  cg_maxit bounds the inner iterations summed
+ * over the outer ones, and stats report them as cg_iters.  GF_BAD_ARG for
+ * another solver value, GF_UNSUPPORTED on GF_MIXED meshes.  The FP32 copies
+ * (36 B per block, 108 B per node) are allocated on the first such load step. */
+enum { GF_QS_SOLVE_FP64 = 0, GF_QS_SOLVE_NESTED = 1 };
+gf_status gf_quasistatic_solver_set(gf_mesh* mesh, int32_t solver, double inner_rtol);
+
 /* Split visualisation mesh for output (Sec. 4.1, Fig. 6; nothing of it feeds
  * the dynamics).  Every tet is cut into four node-associated pieces; a broken
  * edge (Eq. 21 labels) splits into two child nodes at its midpoint, a face

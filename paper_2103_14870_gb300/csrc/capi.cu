@@ -174,6 +174,12 @@ struct gf_mesh {
   double* qs_zero = nullptr;  // quasi-static: zero velocities [3N]
   double* qs_out = nullptr;   // quasi-static: E, |E| scale, slope [4]
   double* qs_w = nullptr;     // quasi-static: A z of the Chronopoulos-Gear PCG [3N]
+  int qs_solver = GF_QS_SOLVE_FP64;
+  double qs_in_rtol = 1e-2;   // inner tolerance of the nested quasi-static solve
+  MixDev qsr{};               // its FP32 matrix, inverses, vectors and state (first use)
+  cudaGraph_t qs_graph = nullptr;          // its solver loop as a WHILE node (first use)
+  cudaGraphExec_t qs_graph_exec = nullptr;
+  int* qs_loops = nullptr;                 // the loop's body count
   SurfDev surf{};             // split visualisation mesh tables (built on first use)
   bool surf_ready = false;
   void* surf_stage = nullptr; // host-output staging of the surface buffers (cudaMalloc, grown on demand)
@@ -294,6 +300,8 @@ void release(gf_mesh* m) {
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->graph) cudaGraphDestroy(m->graph);
+  if (m->qs_graph_exec) cudaGraphExecDestroy(m->qs_graph_exec);
+  if (m->qs_graph) cudaGraphDestroy(m->qs_graph);
   if (m->body_stream) cudaStreamDestroy(m->body_stream);
   if (m->h_loops) cudaFreeHost(m->h_loops);
   if (m->h_init) cudaFreeHost(m->h_init);
@@ -782,6 +790,21 @@ gf_status gf_refine_set(gf_mesh* m, double inner_rtol) {
     return GF_BAD_ARG;
   }
   m->in_rtol = inner_rtol;
+  return GF_OK;
+}
+
+gf_status gf_quasistatic_solver_set(gf_mesh* m, int32_t solver, double inner_rtol) {
+  if (!m || (solver != GF_QS_SOLVE_FP64 && solver != GF_QS_SOLVE_NESTED) || !(inner_rtol < 1) ||
+      std::isnan(inner_rtol)) {
+    set_last_error("need solver GF_QS_SOLVE_FP64 or GF_QS_SOLVE_NESTED and inner_rtol < 1");
+    return GF_BAD_ARG;
+  }
+  if (m->mixed) {
+    set_last_error("the quasi-static step is built for GF_FP64 meshes only");
+    return GF_UNSUPPORTED;
+  }
+  m->qs_solver = solver;
+  if (inner_rtol > 0) m->qs_in_rtol = inner_rtol;
   return GF_OK;
 }
 
@@ -1290,6 +1313,110 @@ gf_status step_graph(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   return GF_OK;
 }
 
+// The quasi-static solve of K dv = b with an FP32 inner solve
+// (GF_QS_SOLVE_NESTED), after k_pcg_init has formed the FP64 block-Jacobi
+// inverses, r = b and |b|^2 (bb) with dv = 0: flexible PCG in FP64 whose
+// preconditioner is the mixed step's two-kernel inner PCG on the FP32 copies,
+// until |r|^2 <= cg_rtol^2 bb.  The loop runs as one graph: a WHILE node whose
+// body is kQsPairs inner iterations and the outer pair (which acts only once
+// the inner solve has finished); with per-launch profiling on, the same
+// launches go from the host.  iters: inner iterations; status: the solve's.
+constexpr int kQsPairs = 8;
+
+gf_status qs_nested_graph(gf_mesh* m, const DevMesh& dq, const gf::Material& mq, const StepScalars& sq) {
+  if (m->qs_graph_exec) return GF_OK;
+  if (!m->body_stream) GF_CK(cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  GF_CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h{};
+  GF_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t wn;
+  GF_CK(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaStream_t bs = m->body_stream;
+  GF_CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  for (int j = 0; j < kQsPairs; ++j) {
+    launch_kind(kB_ir_cg_spmv, dq, mq, sq, bs);
+    launch_kind(kB_ir_cg_update, dq, mq, sq, bs);
+  }
+  launch_fcg_spmv(dq, bs);
+  launch_fcg_update(dq, bs);
+  const int cap = m->opt.cg_maxit / kQsPairs + 4096;
+  k_step_cond<<<1, 32, 0, bs>>>(nullptr, dq.mx.ir, m->qs_loops, cap, h);
+  GF_CK(cudaStreamEndCapture(bs, &body));
+  m->qs_graph = g;
+  GF_CK(cudaGraphInstantiate(&m->qs_graph_exec, g, 0));
+  return GF_OK;
+}
+
+gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const StepScalars& sq, double bb,
+                          int64_t& L, int& iters, int& status) {
+  cudaStream_t s = m->stream;
+  const int64_t N = dq.N;
+  MixDev& x = m->qsr;
+  if (!x.ir) {
+    gf_status st;
+    if ((st = scratch(m, 9 * size_t(dq.NB), &x.val32)) || (st = scratch(m, 9 * size_t(N), &x.pinv32)) ||
+        (st = scratch(m, 3 * size_t(N), &x.r32)) || (st = scratch(m, 3 * size_t(N), &x.z32)) ||
+        (st = scratch(m, 3 * size_t(N), &x.p32)) || (st = scratch(m, 3 * size_t(N), &x.q32)) ||
+        (st = scratch(m, 3 * size_t(N), &x.w32)) || (st = scratch(m, 3 * size_t(N), &x.d32)) ||
+        (st = scratch(m, 1, &x.ir)) || (st = scratch(m, 1, &m->qs_loops)))
+      return st;
+  }
+  dq.mx = x;
+  L += launch_qsr_to32(dq, s);
+  IrState init{};
+  init.bb = bb;
+  init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
+  init.in_tol2 = m->qs_in_rtol * m->qs_in_rtol;
+  init.maxit = m->opt.cg_maxit;
+  init.in_maxit = m->opt.cg_maxit;
+  *m->h_ir = init;
+  GF_CK(cudaMemcpyAsync(x.ir, m->h_ir, sizeof(IrState), cudaMemcpyHostToDevice, s));
+  { Prof p(m, kPIrInit); L += launch_qsr_start(dq, s); }
+  if (!m->prof) {
+    if (!m->h_loops) GF_CK(cudaMallocHost(&m->h_loops, sizeof(int)));
+    gf_status st = qs_nested_graph(m, dq, mq, sq);
+    if (st != GF_OK) return st;
+    GF_CK(cudaMemsetAsync(m->qs_loops, 0, sizeof(int), s));
+    GF_CK(cudaGraphLaunch(m->qs_graph_exec, s));
+    int loops = 0;
+    GF_CK(cudaMemcpyAsync(m->h_ir, x.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaMemcpyAsync(m->h_loops, m->qs_loops, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GF_CK(cudaStreamSynchronize(s));
+    loops = *m->h_loops;
+    L += int64_t(loops) * (2 * kQsPairs + 3);
+  } else {
+    int chunk = std::max(2, std::min(m->last_iters + 1, 64));
+    for (int outer = 0; outer < 100000; ++outer) {
+      for (;;) {
+        for (int j = 0; j < chunk; ++j) {
+          { Prof p(m, kPSpmv, -2); L += launch_kind(kB_ir_cg_spmv, dq, mq, sq, s); }
+          { Prof p(m, kPPcgUpdate, -2); L += launch_kind(kB_ir_cg_update, dq, mq, sq, s); }
+        }
+        GF_CK(cudaGetLastError());
+        GF_CK(cudaMemcpyAsync(m->h_ir, x.ir, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+        GF_CK(cudaStreamSynchronize(s));
+        if (m->h_ir->done || m->h_ir->in_done) break;
+        chunk = 8;
+      }
+      if (m->h_ir->done) break;
+      chunk = std::max(2, std::min(m->h_ir->in_iters + 1, 64));
+      { Prof p(m, kPIrResidual); L += launch_fcg_spmv(dq, s); }
+      { Prof p(m, kPIrApply); L += launch_fcg_update(dq, s); }
+    }
+  }
+  GF_CK(cudaGetLastError());
+  iters = m->h_ir->total_iters;
+  status = m->h_ir->done ? m->h_ir->status : GF_CG_MAXITER;
+  return GF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1505,6 +1632,16 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
       break;
     }
     if (rn == 0.0 || rn <= rtol * r0) break;
+    if (m->qs_solver == GF_QS_SOLVE_NESTED) {
+      int its = 0, qst = GF_OK;
+      if ((st = qs_nested_solve(m, dq, mq, sq, m->h_pcg->bb, L, its, qst)) != GF_OK) return st;
+      cg_total += its;
+      m->last_iters = its;
+      if (qst != GF_OK) {
+        status = qst;
+        break;
+      }
+    } else {
     // PCG in the Chronopoulos-Gear form: w = A z and the coefficients, then
     // per iteration the vector updates and the next w = A z
     int launched = 0;
@@ -1526,6 +1663,7 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
     if (m->h_pcg->status != GF_OK) {
       status = m->h_pcg->status;
       break;
+    }
     }
     // line search on E(x) = sum chi V Psi - f_ext . x
     L += launch_qs_slope(dq, m->qs_out, s);

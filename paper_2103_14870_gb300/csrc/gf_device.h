@@ -285,6 +285,14 @@ int launch_qs_slope(const DevMesh& m, double* out, cudaStream_t s);
 int launch_qs_cg_spmv(const DevMesh& m, cudaStream_t s);     // Chronopoulos-Gear PCG: w = A z, dots, coefficients
 int launch_qs_cg_update(const DevMesh& m, cudaStream_t s);   // Chronopoulos-Gear PCG: vector updates
 int launch_qs_trial(int64_t n, const double* x, const double* d, double a, double* xt, cudaStream_t s);
+// Quasi-static solve with an FP32 inner PCG: val32/pinv32 from the FP64 system,
+// the first inner start, and per outer flexible-PCG iteration w = A z with its
+// coefficients, then the FP64 updates and the next inner start (m.mx holds the
+// FP32 buffers and IrState, m.pcg the outer scalars, m.w the vector A z)
+int launch_qsr_to32(const DevMesh& m, cudaStream_t s);
+int launch_qsr_start(const DevMesh& m, cudaStream_t s);
+int launch_fcg_spmv(const DevMesh& m, cudaStream_t s);
+int launch_fcg_update(const DevMesh& m, cudaStream_t s);
 int launch_qs_set_pins(const DevMesh& m, const int32_t* ids, const double* pos, int64_t n_pinned, cudaStream_t s);
 
 }  // namespace gf

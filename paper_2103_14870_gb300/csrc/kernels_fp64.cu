@@ -1278,6 +1278,190 @@ __global__ void __launch_bounds__(kThreads) k_qs_cg_update(DevMesh m) {
   }
 }
 
+// Quasi-static solve with an FP32 inner solve (GF_QS_SOLVE_NESTED; FP64
+// meshes): flexible PCG in FP64 (Notay, SIAM J. Sci. Comput. 22, 2000; one
+// previous direction kept) whose preconditioner is an inner PCG in FP32 on the
+// matrix and block-Jacobi inverses rounded to FP32 (the mixed step's two-kernel
+// inner iterations, on m.mx), run until its residual falls by the inner
+// tolerance.  With z the inner solution for the outer residual r, w = A z and
+// the previous direction p' (q' = A p'):
+//   beta = z.q' / p'.q',  p = z - beta p',  q = w - beta q' (= A p),
+//   p.q = z.w - 2 beta z.q' + beta^2 p'.q' (A symmetric),  alpha = p.r / p.q,
+//   dv += alpha p,  r -= alpha q.
+// The outer residual, iterate and coefficients are FP64, and the iteration
+// stops at |r| <= cg_rtol |b| like the FP64 PCG.  Outer scalars live in m.pcg,
+// the inner ones in m.mx.ir; ir->done ends both.
+
+// val32 = fl(val), pinv32 = fl(pinv): once per Newton iteration, after the FP64
+// assembly and block-Jacobi inverses
+__global__ void __launch_bounds__(kThreads) k_qsr_to32(DevMesh m) {
+  const int64_t nv = 9 * m.NB, stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < nv; k += stride) m.mx.val32[k] = float(m.val[k]);
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < 9 * m.N; k += stride)
+    m.mx.pinv32[k] = float(m.pinv[k]);
+}
+
+// Inner start on row i from the outer residual r (zero on pinned rows), scaled
+// by sc = 1 / |r_prev| so that the FP32 solve and its double-float sums work on
+// values near 1 whatever the outer residual has fallen to (the flexible PCG is
+// invariant to a scaling of the preconditioner's output): r32 = fl(sc r),
+// z32 = P32 r32, p32 = z32, d32 = 0; adds r32 . z32 and r32 . r32 to g and n
+// (exact products of floats, summed in FP64)
+__device__ __forceinline__ void inner_start_row(const DevMesh& m, int64_t i, const double r[3], double sc, double& g,
+                                                double& n) {
+  const MixDev& x = m.mx;
+  float r32[3], z32[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r32[c] = float(sc * r[c]);
+  const float* pi = x.pinv32 + 9 * i;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    z32[c] = pi[3 * c] * r32[0] + pi[3 * c + 1] * r32[1] + pi[3 * c + 2] * r32[2];
+    g += double(r32[c]) * double(z32[c]);
+    n += double(r32[c]) * double(r32[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x.r32[3 * i + c] = r32[c];
+    x.z32[3 * i + c] = z32[c];
+    x.p32[3 * i + c] = z32[c];
+    x.d32[3 * i + c] = 0.f;
+  }
+}
+
+// the last CTA's bookkeeping after a new outer residual: the outer test, then
+// the inner solve's start (reference |r32|^2, gamma, no iterations yet)
+__device__ __forceinline__ void outer_residual_done(IrState* S, double rr, double gamma, double rr32, bool first) {
+  if (first) {
+    S->sweeps = 0;
+    S->total_iters = 0;
+    S->status = GF_OK;
+  } else {
+    S->sweeps += 1;
+  }
+  S->rr = rr;
+  S->done = (rr == 0.0 || rr <= S->tol2 * S->bb) ? 1 : 0;
+  if (!isfinite(rr) || !isfinite(gamma)) {
+    S->status = GF_NAN;
+    S->done = 1;
+  } else if (!S->done && S->total_iters >= S->maxit) {
+    S->status = GF_CG_MAXITER;
+    S->done = 1;
+  }
+  S->in_rr0 = rr32;
+  S->in_iters = 0;
+  S->rz = gamma;
+  S->in_done = (S->done || gamma == 0.0) ? 1 : 0;
+}
+
+// first inner start, from the residual k_pcg_init left in m.r (dv = 0)
+__global__ void __launch_bounds__(kThreads) k_qsr_start(DevMesh m) {
+  const double bb = m.mx.ir->bb;   // r = b on free rows
+  const double sc = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r[c] = m.r[3 * i + c];
+      v[0] += r[c] * r[c];
+    }
+    inner_start_row(m, i, r, sc, v[1], v[2]);
+  }
+  double out[3];
+  if (grid_reduce<3>(v, m.partials, m.tickets + 13, out, blockIdx.x, gridDim.x) && threadIdx.x == 0)
+    outer_residual_done(m.mx.ir, out[0], out[1], out[2], true);
+}
+
+// z = fl64(d32) (the inner solution; zero on pinned rows), w = A z, and z.q',
+// z.w, z.r, p'.r; the last CTA forms beta, p.q and alpha.  Runs only once the
+// inner solve has finished (a graph body launches it after every group of
+// inner iterations); the first outer iteration is the one with no sweep yet.
+__global__ void __launch_bounds__(kThreads) k_fcg_spmv(DevMesh m) {
+  const IrState* S = m.mx.ir;
+  if (S->done || !S->in_done) return;
+  const bool first = S->sweeps == 0;
+  const float* __restrict__ d32 = m.mx.d32;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    const int b1 = m.row_ptr[i + 1];
+    for (int b = m.row_ptr[i]; b < b1; ++b) {
+      const int64_t j = m.col[b];
+      const double* a = m.val + 9 * int64_t(b);
+      const double x0 = d32[3 * j], x1 = d32[3 * j + 1], x2 = d32[3 * j + 2];
+      y0 = fma(a[2], x2, fma(a[1], x1, fma(a[0], x0, y0)));
+      y1 = fma(a[5], x2, fma(a[4], x1, fma(a[3], x0, y1)));
+      y2 = fma(a[8], x2, fma(a[7], x1, fma(a[6], x0, y2)));
+    }
+    const double y[3] = {y0, y1, y2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double z = d32[3 * i + c], r = m.r[3 * i + c];
+      m.z[3 * i + c] = z;
+      m.w[3 * i + c] = y[c];
+      v[1] += z * y[c];
+      v[2] += z * r;
+      if (!first) {
+        v[0] += z * m.q[3 * i + c];
+        v[3] += m.p[3 * i + c] * r;
+      }
+    }
+  }
+  double out[4];
+  if (grid_reduce<4>(v, m.partials, m.tickets + 14, out, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
+    IrState* I = m.mx.ir;
+    PcgState* P = m.pcg;
+    const double beta = first ? 0.0 : out[0] / P->pq;
+    const double pq = first ? out[1] : out[1] - 2.0 * beta * out[0] + beta * beta * P->pq;
+    const double pr = first ? out[2] : out[2] - beta * out[3];
+    if (!isfinite(pq) || !isfinite(pr)) {
+      I->status = GF_NAN;
+      I->done = 1;
+    } else if (!(pq > 0.0)) {
+      I->status = GF_CG_BREAKDOWN;
+      I->done = 1;
+    } else {
+      P->beta = beta;
+      P->pq = pq;
+      P->alpha = pr / pq;
+    }
+  }
+}
+
+// p = z - beta p', q = w - beta q', dv += alpha p, r -= alpha q on free rows,
+// then the next inner start from the new r, |r|^2 and the outer test (which
+// counts the sweep and clears in_done: the flags are read by every CTA first)
+__global__ void __launch_bounds__(kThreads) k_fcg_update(DevMesh m) {
+  if (m.mx.ir->done || !m.mx.ir->in_done) return;
+  const bool first = m.mx.ir->sweeps == 0;
+  const double alpha = m.pcg->alpha, beta = m.pcg->beta;
+  const double rr_prev = m.mx.ir->rr;   // written again only by this launch's last CTA
+  const double sc = rr_prev > 0.0 ? 1.0 / sqrt(rr_prev) : 1.0;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    double r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double p = first ? m.z[3 * i + c] : m.z[3 * i + c] - beta * m.p[3 * i + c];
+      const double q = first ? m.w[3 * i + c] : m.w[3 * i + c] - beta * m.q[3 * i + c];
+      m.p[3 * i + c] = p;
+      m.q[3 * i + c] = q;
+      r[c] = 0.0;
+      if (!m.pinned[i]) {
+        m.dv[3 * i + c] += alpha * p;
+        r[c] = m.r[3 * i + c] - alpha * q;
+      }
+      m.r[3 * i + c] = r[c];
+      v[0] += r[c] * r[c];
+    }
+    inner_start_row(m, i, r, sc, v[1], v[2]);
+  }
+  double out[3];
+  if (grid_reduce<3>(v, m.partials, m.tickets + 15, out, blockIdx.x, gridDim.x) && threadIdx.x == 0)
+    outer_residual_done(m.mx.ir, out[0], out[1], out[2], false);
+}
+
 // ||b - A dv||^2 over free nodes, recomputed from scratch after the solve.
 __device__ __forceinline__ void true_residual_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
@@ -1367,6 +1551,22 @@ int launch_qs_cg_spmv(const DevMesh& m, cudaStream_t s) {
 }
 int launch_qs_cg_update(const DevMesh& m, cudaStream_t s) {
   k_qs_cg_update<<<qs_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_qsr_to32(const DevMesh& m, cudaStream_t s) {
+  k_qsr_to32<<<qs_grid(9 * m.NB), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_qsr_start(const DevMesh& m, cudaStream_t s) {
+  k_qsr_start<<<qs_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_fcg_spmv(const DevMesh& m, cudaStream_t s) {
+  k_fcg_spmv<<<qs_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_fcg_update(const DevMesh& m, cudaStream_t s) {
+  k_fcg_update<<<qs_grid(m.N), kThreads, 0, s>>>(m);
   return 1;
 }
 int launch_qs_trial(int64_t n, const double* x, const double* d, double a, double* xt, cudaStream_t s) {

@@ -70,6 +70,7 @@ class Tuning(ctypes.Structure):
 ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
 STEP_GRAPH, STEP_STREAM = 0, 1
 SOLVE_KERNELS, SOLVE_PERSISTENT, SOLVE_CG, SOLVE_DISTRIBUTED = 0, 1, 2, 3
+QS_SOLVE_FP64, QS_SOLVE_NESTED = 0, 1
 
 
 class BatchTuning(ctypes.Structure):
@@ -115,6 +116,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_solver_set": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int32]),
         "gf_threshold_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
+        "gf_quasistatic_solver_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
         "gf_newton_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
         "gf_surface_sizes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64)]),
@@ -324,6 +326,10 @@ class Mesh:
 
     def refine_set(self, inner_rtol: float):
         _check(load_library().gf_refine_set(self._h, float(inner_rtol)))
+
+    def quasistatic_solver_set(self, solver: int, inner_rtol: float = 0.0):
+        """gf_quasistatic_solver_set: QS_SOLVE_FP64 or QS_SOLVE_NESTED (inner_rtol <= 0 keeps the current one)."""
+        _check(load_library().gf_quasistatic_solver_set(self._h, int(solver), float(inner_rtol)))
 
     def threshold_set(self, threshold: float):
         """gf_threshold_set: the break threshold of Eq. 21 between steps."""
