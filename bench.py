@@ -780,7 +780,8 @@ def run_ours(args) -> None:
 
 
 def run_profile_step(args) -> None:
-    """Minimal command for ncu captures: build the loaf mesh, run `--steps` steps, no timing.
+    """Minimal command for ncu captures: build the loaf mesh (--workload glass: the glass point
+    impact on it), run `--steps` steps with the --solve form, no timing.
     --precision: fp64 | mixed | learned (FP64 with the network's start, then one Adam step) |
     batch (the 64-box mixed batch, stream launches) |
     snh (stable Neo-Hookean FP64) | qs (one quasi-static pull load step after the steps) |
@@ -807,15 +808,23 @@ def run_profile_step(args) -> None:
         print(json.dumps({"profile_step": True, "steps": args.steps, "batch": len(ws),
                           "max_cg_iters": max(x["cg_iters"] for x in st), "launches": b.launch_count()}))
         return
-    w = loaf_config()
+    if args.workload == "glass":
+        from workloads import glass_config
+        w = glass_config()
+    else:
+        w = loaf_config()
     mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius,
                       energy=gf.ENERGY_SNH if args.precision == "snh" else gf.ENERGY_STVK)
     m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol,
                        precision=gf.MIXED if args.precision == "mixed" else gf.FP64)
     # kernel-by-kernel launches (the same kernels as the graph replay), so that
     # ncu lists every kernel of the step
-    m.tuning_set(step_launch=gf.STEP_STREAM)
+    solve = {"kernels": gf.SOLVE_KERNELS, "cg": gf.SOLVE_CG, "persistent": gf.SOLVE_PERSISTENT}[args.solve]
+    m.tuning_set(step_launch=gf.STEP_STREAM, solve_loop=solve)
+    if args.qs_solver == "nested":
+        m.quasistatic_solver_set(gf.QS_SOLVE_NESTED)
     f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
+    pins_dev = torch.tensor(w.pinned, dtype=torch.int32, device="cuda") if len(w.pinned) else None
     net = None
     if args.precision == "learned":      # zero-decoder network: learned start from the second step on
         from workloads import he_normal_weights
@@ -824,7 +833,7 @@ def run_profile_step(args) -> None:
     for k in range(args.steps):
         if net is not None and k == 1:
             net.attach(gf.GNN_START)
-        s = m.step(w.dt, f_dev)
+        s = m.step(w.dt, f_dev, pins_dev)
     if net is not None:
         net.attach(0)
         net.train(iters=1, lr=1e-5)
@@ -864,6 +873,12 @@ def main():
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
     ap.add_argument("--precision", choices=["fp64", "mixed", "learned", "snh", "qs", "surface", "batch"], default="fp64",
                     help="form run by --profile-step (see run_profile_step)")
+    ap.add_argument("--workload", choices=["loaf", "glass"], default="loaf",
+                    help="--profile-step workload: the loaf or the glass point impact on the loaf mesh")
+    ap.add_argument("--solve", choices=["kernels", "cg", "persistent"], default="kernels",
+                    help="--profile-step solver-loop form (gf_tuning.solve_loop)")
+    ap.add_argument("--qs-solver", choices=["fp64", "nested"], default="fp64",
+                    help="--profile-step --precision qs: linear solver of the Newton iterations")
     args = ap.parse_args()
     if args.cpu_sample_child:
         cpu_sample_child(args.cpu_sample_child, args.cpu_sample_warmup)

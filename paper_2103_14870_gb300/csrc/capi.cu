@@ -77,7 +77,7 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_integrate: case kB_integrate32: case kB_refresh32: return {cdiv(3 * N, 256), 256};
     case kB_fext32: return {sp.has_fext ? cdiv(3 * N, 256) : 0u, 256};
     case kB_ir_residual: return {ir_grid(8 * N, 5), 256};
-    case kB_ir_spmv: case kB_ir_cg_spmv: return {ir_grid(16 * N), 256};
+    case kB_ir_spmv: case kB_ir_cg_spmv: return {ir_grid(16 * N, 6), 256};
     case kB_ir_inner_init: case kB_ir_update: case kB_ir_cg_update: return {ir_grid(N), 256};
     case kB_ir_p: case kB_ir_apply: return {ir_grid(3 * N), 256};
     case kB_step_begin: return {cdiv(3 * N, 256), 256};

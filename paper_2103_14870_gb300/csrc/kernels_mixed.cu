@@ -883,41 +883,76 @@ __global__ void __launch_bounds__(kThreads) kb_ir_inner_init(const BatchTab* __r
   ir_inner_init_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-// q = A32 p with half a warp per block row (coalesced block loads), p . q in double-float
-__device__ __forceinline__ void ir_spmv_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-
-  IrState* S = m.mx.ir;
-  if (S->done || S->in_done) return;
-  const MixDev& x = m.mx;
+// y = A32 v over all rows with half a warp per block row (coalesced block
+// loads) and two rows (i0, i0 + nh) in flight per half-warp; lane c < 3 ends
+// with component c of both rows, stores it to y and adds v_i . y_i to (h, l)
+// in double-float (own v loaded up front).  The same bits for y as one row at a
+// time: every lane sums its blocks in the same order.
+__device__ __forceinline__ void spmv32_rows(const DevMesh& m, const float* __restrict__ v, float* __restrict__ y,
+                                            unsigned bid, unsigned nb, float& h, float& l) {
+  const float* __restrict__ val = m.mx.val32;
   const int j16 = threadIdx.x & 15;
   const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
-  float h[1] = {0.f}, l[1] = {0.f};
   const int64_t nh = (int64_t(nb) * blockDim.x) >> 4;
-  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
-    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-    for (int b = m.row_ptr[i] + j16; b < m.row_ptr[i + 1]; b += 16) {
-      const int64_t j = m.col[b];
-      const float* a = x.val32 + 9 * int64_t(b);
-      const float p0 = x.p32[3 * j], p1 = x.p32[3 * j + 1], p2 = x.p32[3 * j + 2];
-      y0 += a[0] * p0 + a[1] * p1 + a[2] * p2;
-      y1 += a[3] * p0 + a[4] * p1 + a[5] * p2;
-      y2 += a[6] * p0 + a[7] * p1 + a[8] * p2;
+  for (int64_t i0 = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i0 < m.N; i0 += 2 * nh) {
+    const int64_t i1 = i0 + nh;
+    const bool two = i1 < m.N;
+    const int s0 = m.row_ptr[i0], e0 = m.row_ptr[i0 + 1];
+    const int s1 = two ? m.row_ptr[i1] : 0, e1 = two ? m.row_ptr[i1 + 1] : 0;
+    const float vi0 = j16 < 3 ? v[3 * i0 + j16] : 0.f;
+    const float vi1 = (two && j16 < 3) ? v[3 * i1 + j16] : 0.f;
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    const int len = max(e0 - s0, e1 - s1);
+    for (int k = j16; k < len; k += 16) {
+      if (s0 + k < e0) {
+        const int b = s0 + k;
+        const int64_t j = m.col[b];
+        const float* a = val + 9 * int64_t(b);
+        const float x0 = v[3 * j], x1 = v[3 * j + 1], x2 = v[3 * j + 2];
+        y0 += a[0] * x0 + a[1] * x1 + a[2] * x2;
+        y1 += a[3] * x0 + a[4] * x1 + a[5] * x2;
+        y2 += a[6] * x0 + a[7] * x1 + a[8] * x2;
+      }
+      if (s1 + k < e1) {
+        const int b = s1 + k;
+        const int64_t j = m.col[b];
+        const float* a = val + 9 * int64_t(b);
+        const float x0 = v[3 * j], x1 = v[3 * j + 1], x2 = v[3 * j + 2];
+        u0 += a[0] * x0 + a[1] * x1 + a[2] * x2;
+        u1 += a[3] * x0 + a[4] * x1 + a[5] * x2;
+        u2 += a[6] * x0 + a[7] * x1 + a[8] * x2;
+      }
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) {
       y0 += __shfl_xor_sync(hmask, y0, o);
       y1 += __shfl_xor_sync(hmask, y1, o);
       y2 += __shfl_xor_sync(hmask, y2, o);
+      u0 += __shfl_xor_sync(hmask, u0, o);
+      u1 += __shfl_xor_sync(hmask, u1, o);
+      u2 += __shfl_xor_sync(hmask, u2, o);
     }
-    if (j16 == 0) {
-      const float y[3] = {y0, y1, y2};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        x.q32[3 * i + c] = y[c];
-        df_acc_prod(h[0], l[0], x.p32[3 * i + c], y[c]);
+    if (j16 < 3) {
+      const float yc = j16 == 0 ? y0 : (j16 == 1 ? y1 : y2);
+      y[3 * i0 + j16] = yc;
+      df_acc_prod(h, l, vi0, yc);
+      if (two) {
+        const float uc = j16 == 0 ? u0 : (j16 == 1 ? u1 : u2);
+        y[3 * i1 + j16] = uc;
+        df_acc_prod(h, l, vi1, uc);
       }
     }
   }
+}
+
+// q = A32 p, p . q in double-float
+__device__ __forceinline__ void ir_spmv_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+
+  IrState* S = m.mx.ir;
+  if (S->done || S->in_done) return;
+  const MixDev& x = m.mx;
+  float h[1] = {0.f}, l[1] = {0.f};
+  spmv32_rows(m, x.p32, x.q32, bid, nb, h[0], l[0]);
   double out[1];
   if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 6, out, bid, nb) && threadIdx.x == 0) {
     S->pq = out[0];
@@ -1024,35 +1059,8 @@ __device__ __forceinline__ void ir_cg_spmv_body(const DevMesh& m, const Material
   IrState* S = m.mx.ir;
   if (S->done || S->in_done) return;
   const MixDev& x = m.mx;
-  const int j16 = threadIdx.x & 15;
-  const unsigned hmask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
   float h[1] = {0.f}, l[1] = {0.f};
-  const int64_t nh = (int64_t(nb) * blockDim.x) >> 4;
-  for (int64_t i = (bid * int64_t(blockDim.x) + threadIdx.x) >> 4; i < m.N; i += nh) {
-    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-    for (int b = m.row_ptr[i] + j16; b < m.row_ptr[i + 1]; b += 16) {
-      const int64_t j = m.col[b];
-      const float* a = x.val32 + 9 * int64_t(b);
-      const float z0 = x.z32[3 * j], z1 = x.z32[3 * j + 1], z2 = x.z32[3 * j + 2];
-      y0 += a[0] * z0 + a[1] * z1 + a[2] * z2;
-      y1 += a[3] * z0 + a[4] * z1 + a[5] * z2;
-      y2 += a[6] * z0 + a[7] * z1 + a[8] * z2;
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      y0 += __shfl_xor_sync(hmask, y0, o);
-      y1 += __shfl_xor_sync(hmask, y1, o);
-      y2 += __shfl_xor_sync(hmask, y2, o);
-    }
-    if (j16 == 0) {
-      const float y[3] = {y0, y1, y2};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        x.w32[3 * i + c] = y[c];
-        df_acc_prod(h[0], l[0], x.z32[3 * i + c], y[c]);   // z is zero on pinned rows
-      }
-    }
-  }
+  spmv32_rows(m, x.z32, x.w32, bid, nb, h[0], l[0]);   // w = A32 z, z . w (z is zero on pinned rows)
   double out[1];
   if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 11, out, bid, nb) && threadIdx.x == 0) {
     const double den = S->in_iters > 0 ? out[0] - S->beta * S->rz / S->alpha : out[0];   // p.A.p
