@@ -262,7 +262,8 @@ def run_batch(args, gf, torch, barrier, stream, world=1, rank=0, dist=None) -> d
                         "meshes_rank0": len(ws) if rank == 0 else None}}
     per_mode = {}
     for graph in (1, 0):
-        b.tuning_set(graph=graph, chunk=tuned["chunk"] if tuned["graph"] == 0 else 8, grid_budget=tuned["grid_budget"])
+        b.tuning_set(graph=graph, chunk=tuned["chunk"] if tuned["graph"] == 0 else 8, grid_budget=tuned["grid_budget"],
+                     solve_loop=tuned["solve_loop"], inner=tuned["inner"])
         for _ in range(args.warmup):
             b.step(dt, f, pins)
         l0 = b.launch_count()
@@ -279,8 +280,28 @@ def run_batch(args, gf, torch, barrier, stream, world=1, rank=0, dist=None) -> d
         ms_b = e0.elapsed_time(e1) / args.steps
         per_mode["graph" if graph else "stream"] = {"ms_per_step": ms_b, "gpu_launches": b.launch_count() - l0,
                                                     "cg_iters_mean": statistics.mean(iters)}
-    b.tuning_set(graph=tuned["graph"], chunk=tuned["chunk"], grid_budget=tuned["grid_budget"])
+    b.tuning_set(graph=tuned["graph"], chunk=tuned["chunk"], grid_budget=tuned["grid_budget"],
+                 solve_loop=tuned["solve_loop"], inner=tuned["inner"])
     best_ms = per_mode["graph" if tuned["graph"] else "stream"]["ms_per_step"]
+    # the same members stepped one at a time as single meshes (graph replay each,
+    # the inner form the autotuner chose where a single mesh has it)
+    for m in meshes:
+        m.tuning_set(solve_loop=tuned["solve_loop"] if tuned["solve_loop"] in (gf.SOLVE_KERNELS, gf.SOLVE_CG,
+                                                                                gf.SOLVE_PERSISTENT)
+                     else gf.SOLVE_KERNELS)
+    for _ in range(2):
+        for m, fk, pk in zip(meshes, f, pins):
+            m.step(dt, fk, pk)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_seq = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(n_seq):
+        for m, fk, pk in zip(meshes, f, pins):
+            m.step(dt, fk, pk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_mode["members_one_at_a_time"] = {"ms_per_step": e0.elapsed_time(e1) / n_seq,
+                                         "what": "every member stepped alone, one after another"}
     if dist is not None:   # the slowest rank's share sets the batch's step time
         t = torch.tensor([best_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -404,8 +404,15 @@ typedef struct gf_batch_tuning {
                            GF_SOLVE_PERSISTENT (GF_MIXED batches): the whole solve of every member
                            as one cooperative launch whose phases take only the blocks of the
                            meshes still iterating (members step bit-identically to single-mesh
-                           persistent steps). */
-  int32_t reserved[4];  /* set to 0 */
+                           persistent steps).
+                           GF_SOLVE_CG (GF_MIXED batches): the per-kind form with the inner FP32
+                           PCG in two kernels per iteration (gf_tuning's GF_SOLVE_CG; members
+                           step bit-identically to single-mesh steps in that form). */
+  int32_t inner;        /* GF_MIXED, per-kind and distributed forms: inner iterations per pass of
+                           the solver loop (a pass is: inner start, `inner` iterations, apply,
+                           residual; a member whose inner solve ends early waits for the pass to
+                           end).  0 -> 8.  Any value gives the same results. */
+  int32_t reserved[3];  /* set to 0 */
 } gf_batch_tuning;
 
 /* meshes: n handles (1 <= n <= 256), same device and precision.  The batch

@@ -2179,7 +2179,6 @@ const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
 const int kSuffixFp64[] = {kB_true_residual, kB_integrate};
 const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32,
                             kB_gather32, kB_diag32, kB_pinv32, kB_set_pinned, kB_refresh32};
-const int kBodyMixed[] = {kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_ir_residual};
 const int kSuffixMixed[] = {kB_integrate32};
 
 template <size_t K>
@@ -2206,22 +2205,40 @@ int64_t enqueue_prefix(gf_batch* b, cudaStream_t s) {
   return L;
 }
 
+// One pass of the solver loop.  GF_MIXED: inner start, `inner` inner iterations
+// (three kernels each, or two in the GF_SOLVE_CG form), apply, residual: a
+// member's kernels act only in the phase its own flags call for, so a member
+// whose inner solve ends early idles to the end of the pass.  FP64: one PCG
+// iteration.
 int64_t enqueue_body(gf_batch* b, cudaStream_t s) {
-  if (batch_dist(b)) {
-    int64_t L = 0;
-    const unsigned g = dist_grid(b);
-    if (b->mixed)
-      for (int kind : kBodyMixed) L += launch_dist_mixed(kind, b->dtab, b->dact, g, s);
-    else
+  const bool dist = batch_dist(b);
+  const unsigned g = dist ? dist_grid(b) : 0u;
+  int64_t L = 0;
+  if (!b->mixed) {
+    if (dist)
       for (int kind : kBodyFp64) L += launch_dist_fp64(kind, b->dtab, b->dact, g, s);
+    else
+      L += enqueue_kinds(b, kBodyFp64, s);
     return L;
   }
-  if (b->mixed) {
-    int64_t L = 0;
-    for (int kind : kBodyMixed) L += launch_batch(kind, b->dtab, b->blocks[kind], s, 0);
-    return L;
+  auto one = [&](int kind) {
+    L += dist ? launch_dist_mixed(kind, b->dtab, b->dact, g, s) : launch_batch(kind, b->dtab, b->blocks[kind], s, 0);
+  };
+  const int inner = b->tune.inner > 0 ? b->tune.inner : 8;
+  one(kB_ir_inner_init);
+  for (int j = 0; j < inner; ++j) {
+    if (b->tune.solve_loop == GF_SOLVE_CG) {
+      one(kB_ir_cg_spmv);
+      one(kB_ir_cg_update);
+    } else {
+      one(kB_ir_spmv);
+      one(kB_ir_update);
+      one(kB_ir_p);
+    }
   }
-  return enqueue_kinds(b, kBodyFp64, s);
+  one(kB_ir_apply);
+  one(kB_ir_residual);
+  return L;
 }
 
 bool batch_persist(const gf_batch* b) { return b->mixed && b->tune.solve_loop == GF_SOLVE_PERSISTENT; }
@@ -2343,8 +2360,8 @@ gf_status batch_prepare(gf_batch* b, double dt, const double* const* f_ext, cons
   for (int kind = 0; kind < kBKinds; ++kind) {
     // the solver-loop kernels are grid-stride: any per-mesh grid covers the mesh
     const bool loop_kind = kind == kB_ir_inner_init || kind == kB_ir_spmv || kind == kB_ir_update || kind == kB_ir_p ||
-                           kind == kB_ir_apply || kind == kB_ir_residual || kind == kB_pcg_spmv ||
-                           kind == kB_pcg_update || kind == kB_pcg_p;
+                           kind == kB_ir_apply || kind == kB_ir_residual || kind == kB_ir_cg_spmv ||
+                           kind == kB_ir_cg_update || kind == kB_pcg_spmv || kind == kB_pcg_update || kind == kB_pcg_p;
     int32_t acc = 0;
     b->htab->off[kind][0] = 0;
     for (int k = 0; k < b->n; ++k) {
@@ -2565,14 +2582,19 @@ gf_status gf_batch_step(gf_batch* b, double dt, const double* const* f_ext, cons
 }
 
 gf_status gf_batch_tuning_set(gf_batch* b, const gf_batch_tuning* t) {
-  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0 || t->grid_budget < 0 ||
+  if (!b || !t || (t->graph != 0 && t->graph != 1) || t->chunk < 0 || t->grid_budget < 0 || t->inner < 0 ||
+      t->inner > 64 ||
       (t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_KERNELS &&
-       t->solve_loop != GF_SOLVE_DISTRIBUTED)) {
-    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0, grid_budget >= 0, solve_loop "
-                   "GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT or GF_SOLVE_DISTRIBUTED");
+       t->solve_loop != GF_SOLVE_DISTRIBUTED && t->solve_loop != GF_SOLVE_CG)) {
+    set_last_error("batch tuning: graph must be 0 or 1, chunk >= 0, grid_budget >= 0, 0 <= inner <= 64, "
+                   "solve_loop GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT, GF_SOLVE_CG or GF_SOLVE_DISTRIBUTED");
     return GF_BAD_ARG;
   }
-  const bool rebuild = t->solve_loop != b->tune.solve_loop;
+  if (t->solve_loop == GF_SOLVE_CG && !b->mixed) {
+    set_last_error("batch tuning: GF_SOLVE_CG is built for GF_MIXED batches");
+    return GF_UNSUPPORTED;
+  }
+  const bool rebuild = t->solve_loop != b->tune.solve_loop || t->inner != b->tune.inner;
   b->tune = *t;
   if (rebuild && b->exec) {   // the captured graph holds the other solve form
     cudaGraphExecDestroy(b->exec);
@@ -2647,7 +2669,7 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
         cands.push_back(t);
       }
     }
-    if (b->mixed)   // the persistent solve: every member's own blocks, or a budget of one or two waves
+    if (b->mixed) {   // the persistent solve: every member's own blocks, or a budget of one or two waves
       for (int budget : {0, wave, 2 * wave}) {
         gf_batch_tuning t{};
         t.graph = 1;
@@ -2656,6 +2678,26 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
         t.solve_loop = GF_SOLVE_PERSISTENT;
         cands.push_back(t);
       }
+      // the two-kernel inner form, and both forms with shorter and longer passes
+      for (int budget : {0, wave, 2 * wave}) {
+        gf_batch_tuning t{};
+        t.graph = 1;
+        t.chunk = 8;
+        t.grid_budget = budget;
+        t.solve_loop = GF_SOLVE_CG;
+        cands.push_back(t);
+      }
+      for (int form : {GF_SOLVE_KERNELS, GF_SOLVE_CG})
+        for (int inner : {2, 4, 16}) {
+          gf_batch_tuning t{};
+          t.graph = 1;
+          t.chunk = 8;
+          t.grid_budget = 2 * wave;
+          t.solve_loop = form;
+          t.inner = inner;
+          cands.push_back(t);
+        }
+    }
     for (int g : {wave / 2, wave, 2 * wave, 4 * wave}) {   // the distributed loop: its launch grid
       gf_batch_tuning t{};
       t.graph = 1;

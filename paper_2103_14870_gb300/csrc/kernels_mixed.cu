@@ -1083,6 +1083,11 @@ __device__ __forceinline__ void ir_cg_spmv_body(const DevMesh& m, const Material
 __global__ void __launch_bounds__(kThreads) k_ir_cg_spmv(DevMesh m, Material mt, StepScalars sp) {
   ir_cg_spmv_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
+__global__ void __launch_bounds__(kThreads) kb_ir_cg_spmv(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_cg_spmv, blockIdx.x, bid, nb);
+  ir_cg_spmv_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+}
 
 __device__ __forceinline__ void ir_cg_update_body(const DevMesh& m, const Material& mt, const StepScalars& sp,
                                                   unsigned bid, unsigned nb) {
@@ -1138,6 +1143,11 @@ __device__ __forceinline__ void ir_cg_update_body(const DevMesh& m, const Materi
 }
 __global__ void __launch_bounds__(kThreads) k_ir_cg_update(DevMesh m, Material mt, StepScalars sp) {
   ir_cg_update_body(m, mt, sp, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kThreads) kb_ir_cg_update(const BatchTab* __restrict__ tab) {
+  unsigned bid, nb;
+  const int k = batch_locate(tab, kB_ir_cg_update, blockIdx.x, bid, nb);
+  ir_cg_update_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // dv += d on free rows once the inner solve has finished, kept as a float pair
@@ -1329,6 +1339,8 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
     case kB_ir_update: kb_ir_update<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_p: kb_ir_p<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_apply: kb_ir_apply<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_cg_spmv: kb_ir_cg_spmv<<<blocks, threads, 0, s>>>(tab); break;
+    case kB_ir_cg_update: kb_ir_cg_update<<<blocks, threads, 0, s>>>(tab); break;
     case kB_integrate32: kb_integrate32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_refresh32: kb_refresh32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_chi_to32: kb_chi_to32<<<blocks, threads, 0, s>>>(tab); break;

@@ -75,7 +75,7 @@ QS_SOLVE_FP64, QS_SOLVE_NESTED = 0, 1
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_int32), ("chunk", ctypes.c_int32), ("grid_budget", ctypes.c_int32),
-                ("solve_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("solve_loop", ctypes.c_int32), ("inner", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -456,15 +456,17 @@ class Batch:
         _check(load_library().gf_batch_step(self._h, float(dt), fp, pp, npin, vp, mem, stats))
         return [st.as_dict() for st in stats]
 
-    def tuning_set(self, graph: int = 1, chunk: int = 8, grid_budget: int = 0, solve_loop: int = SOLVE_KERNELS):
+    def tuning_set(self, graph: int = 1, chunk: int = 8, grid_budget: int = 0, solve_loop: int = SOLVE_KERNELS,
+                   inner: int = 0):
         t = BatchTuning()
-        t.graph, t.chunk, t.grid_budget, t.solve_loop = graph, chunk, grid_budget, solve_loop
+        t.graph, t.chunk, t.grid_budget, t.solve_loop, t.inner = graph, chunk, grid_budget, solve_loop, inner
         _check(load_library().gf_batch_tuning_set(self._h, ctypes.byref(t)))
 
     def tuning_get(self) -> dict:
         t = BatchTuning()
         _check(load_library().gf_batch_tuning_get(self._h, ctypes.byref(t)))
-        return {"graph": t.graph, "chunk": t.chunk, "grid_budget": t.grid_budget, "solve_loop": t.solve_loop}
+        return {"graph": t.graph, "chunk": t.chunk, "grid_budget": t.grid_budget, "solve_loop": t.solve_loop,
+                "inner": t.inner}
 
     def autotune(self, dt: float, f_ext=None, pinned=None, pinned_vel=None, trial_steps: int = 3):
         fp, pp, npin, vp, mem, keep = self._inputs(f_ext, pinned, pinned_vel)
@@ -472,7 +474,8 @@ class Batch:
         ms = ctypes.c_double(0.0)
         _check(load_library().gf_batch_autotune(self._h, float(dt), fp, pp, npin, vp, mem, int(trial_steps),
                                                 ctypes.byref(best), ctypes.byref(ms)))
-        return {"graph": best.graph, "chunk": best.chunk, "grid_budget": best.grid_budget}, ms.value
+        return {"graph": best.graph, "chunk": best.chunk, "grid_budget": best.grid_budget, "solve_loop": best.solve_loop,
+                "inner": best.inner}, ms.value
 
     def launch_count(self) -> int:
         return int(load_library().gf_batch_launch_count(self._h))
