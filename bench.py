@@ -819,7 +819,8 @@ def run_profile_step(args) -> None:
                                                               radius=v.radius), precision=gf.MIXED, cg_rtol=1e-6)
                   for v in ws]
         b = gf.Batch(meshes)
-        b.tuning_set(graph=0, chunk=8, grid_budget=4 * 152 * 2)
+        b.tuning_set(graph=0, chunk=8, grid_budget=4 * 152 * 2,
+                     solve_loop=gf.SOLVE_CG if args.solve == "cg" else gf.SOLVE_KERNELS)
         f = [torch.tensor(v.f_ext.ravel(), dtype=torch.float64, device="cuda") for v in ws]
         pins = [torch.tensor(v.pinned, dtype=torch.int32, device="cuda") for v in ws]
         st = None
