@@ -1134,14 +1134,24 @@ __device__ __forceinline__ void pcg_update_body(const DevMesh& m, const Material
   double v[2] = {0.0, 0.0};
   for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i]) continue;
-    double r[3];
+    // every load before the first store (the vectors may alias as far as the
+    // compiler knows)
+    double dv[3], p[3], r[3], q[3], pi[9];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      m.dv[3 * i + c] += alpha * m.p[3 * i + c];
-      r[c] = m.r[3 * i + c] - alpha * m.q[3 * i + c];
+      dv[c] = m.dv[3 * i + c];
+      p[c] = m.p[3 * i + c];
+      r[c] = m.r[3 * i + c];
+      q[c] = m.q[3 * i + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) pi[k] = m.pinv[9 * i + k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.dv[3 * i + c] = dv[c] + alpha * p[c];
+      r[c] = r[c] - alpha * q[c];
       m.r[3 * i + c] = r[c];
     }
-    const double* pi = m.pinv + 9 * i;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
@@ -1255,24 +1265,37 @@ __global__ void __launch_bounds__(kThreads) k_qs_cg_update(DevMesh m) {
   const double alpha = S->alpha, beta = S->beta;
   const bool first = S->cg_k == 1;   // p = z, q = w
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
+    // every load first (the vectors may alias as far as the compiler knows);
+    // p' and q' are not used on the first iteration, dv, r and the inverse not
+    // on pinned rows
+    const bool fixed = m.pinned[i];
+    double zo[3], w[3], po[3], qo[3], dv[3], r[3], pi[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zo[c] = m.z[3 * i + c];
+      w[c] = m.w[3 * i + c];
+      po[c] = m.p[3 * i + c];
+      qo[c] = m.q[3 * i + c];
+      dv[c] = m.dv[3 * i + c];
+      r[c] = m.r[3 * i + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) pi[k] = m.pinv[9 * i + k];
     double p[3], q[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double z = m.z[3 * i + c], w = m.w[3 * i + c];
-      p[c] = first ? z : z + beta * m.p[3 * i + c];
-      q[c] = first ? w : w + beta * m.q[3 * i + c];
+      p[c] = first ? zo[c] : zo[c] + beta * po[c];
+      q[c] = first ? w[c] : w[c] + beta * qo[c];
       m.p[3 * i + c] = p[c];
       m.q[3 * i + c] = q[c];
     }
-    if (m.pinned[i]) continue;
-    double r[3];
+    if (fixed) continue;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      m.dv[3 * i + c] += alpha * p[c];
-      r[c] = m.r[3 * i + c] - alpha * q[c];
+      m.dv[3 * i + c] = dv[c] + alpha * p[c];
+      r[c] = r[c] - alpha * q[c];
       m.r[3 * i + c] = r[c];
     }
-    const double* pi = m.pinv + 9 * i;
 #pragma unroll
     for (int c = 0; c < 3; ++c) m.z[3 * i + c] = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
   }

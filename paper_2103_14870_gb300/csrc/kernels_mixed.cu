@@ -989,14 +989,24 @@ __device__ __forceinline__ void ir_update_body(const DevMesh& m, const Material&
   float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
   for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
     if (m.pinned[i]) continue;
-    float r[3];
+    // every load before the first store (the vectors may alias as far as the
+    // compiler knows)
+    float d[3], p[3], r[3], q[3], pi[9];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      x.d32[3 * i + c] += alpha * x.p32[3 * i + c];
-      r[c] = x.r32[3 * i + c] - alpha * x.q32[3 * i + c];
+      d[c] = x.d32[3 * i + c];
+      p[c] = x.p32[3 * i + c];
+      r[c] = x.r32[3 * i + c];
+      q[c] = x.q32[3 * i + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) pi[k] = x.pinv32[9 * i + k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x.d32[3 * i + c] = d[c] + alpha * p[c];
+      r[c] = r[c] - alpha * q[c];
       x.r32[3 * i + c] = r[c];
     }
-    const float* pi = x.pinv32 + 9 * i;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
@@ -1098,24 +1108,37 @@ __device__ __forceinline__ void ir_cg_update_body(const DevMesh& m, const Materi
   const bool first = S->in_iters == 0;   // p = z, q = w
   float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
   for (int64_t i = bid * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(nb) * blockDim.x) {
+    // every load first (the vectors may alias as far as the compiler knows, so
+    // loads after a store would wait for it); p' and q' are not used on the
+    // first iteration, and d, r and the inverse not on pinned rows
+    const bool fixed = m.pinned[i];
+    float zo[3], w[3], pq[3], qo[3], d[3], r[3], pi[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zo[c] = x.z32[3 * i + c];
+      w[c] = x.w32[3 * i + c];
+      pq[c] = x.p32[3 * i + c];
+      qo[c] = x.q32[3 * i + c];
+      d[c] = x.d32[3 * i + c];
+      r[c] = x.r32[3 * i + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) pi[k] = x.pinv32[9 * i + k];
     float p[3], q[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float z = x.z32[3 * i + c], w = x.w32[3 * i + c];
-      p[c] = first ? z : z + beta * x.p32[3 * i + c];
-      q[c] = first ? w : w + beta * x.q32[3 * i + c];
+      p[c] = first ? zo[c] : zo[c] + beta * pq[c];
+      q[c] = first ? w[c] : w[c] + beta * qo[c];
       x.p32[3 * i + c] = p[c];
       x.q32[3 * i + c] = q[c];
     }
-    if (m.pinned[i]) continue;
-    float r[3];
+    if (fixed) continue;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      x.d32[3 * i + c] += alpha * p[c];
-      r[c] = x.r32[3 * i + c] - alpha * q[c];
+      x.d32[3 * i + c] = d[c] + alpha * p[c];
+      r[c] = r[c] - alpha * q[c];
       x.r32[3 * i + c] = r[c];
     }
-    const float* pi = x.pinv32 + 9 * i;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
