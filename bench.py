@@ -869,6 +869,8 @@ def run_profile_step(args) -> None:
         target = X[pins].copy()
         target[:len(lo), 0] -= 1e-4 * L
         target[len(lo):, 0] += 1e-4 * L
+        if args.qs_solver == "nested":   # per-kernel profiling: the solve launches from the host, so ncu lists its kernels
+            m.profile_enable(True)
         s = m.quasistatic_step(None, pins, target, max_newton=20, rtol=1e-6)
     if args.precision == "surface":
         s = m.surface_get()
