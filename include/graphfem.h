@@ -183,15 +183,19 @@ gf_status gf_step(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* 
  * the same bits as GF_STEP_STREAM, which launches kernel by kernel with a host
  * check per chunk of solver iterations (and is what the other steps use). */
 enum { GF_STEP_GRAPH = 0, GF_STEP_STREAM = 1 };
-/* solve_loop: the form of the solver loop.
- * GF_SOLVE_KERNELS (0, default): kernel by kernel, three per PCG iteration
- * (GF_FP64) or the refinement's phase kernels (GF_MIXED), as a WHILE node of
- * the step graph or with host checks in the stream form.
- * GF_SOLVE_CG: the PCG (GF_FP64) or the inner FP32 PCG of the refinement
- * (GF_MIXED) in the Chronopoulos-Gear form (Chronopoulos and Gear, 1989):
- * w = A z and the three dot products in one kernel, the vector updates in
- * another, one grid reduction per iteration; the iterates equal the
- * three-kernel form's in exact arithmetic.
+/* solve_loop: the form of the solver loop.  A new mesh starts with
+ * GF_SOLVE_KERNELS (GF_FP64) or GF_SOLVE_CG (GF_MIXED), the faster form of
+ * each on the measured workloads.
+ * GF_SOLVE_KERNELS: kernel by kernel, three per PCG iteration (GF_FP64, or the
+ * inner FP32 PCG of GF_MIXED) with the refinement's phase kernels around the
+ * inner solves, as a WHILE node of the step graph or with host checks in the
+ * stream form.
+ * GF_SOLVE_CG: two kernels per iteration.  GF_FP64: the PCG in the
+ * Chronopoulos-Gear form (Chronopoulos and Gear, 1989): w = A z and the three
+ * dot products in one kernel, the vector updates in another, one grid
+ * reduction per iteration.  GF_MIXED: the inner FP32 PCG with q = A p carried
+ * by recurrence (w = A z and z.w in one kernel; p, q, d, r, z and r.z, r.r in
+ * the other).  The iterates equal the three-kernel form's in exact arithmetic.
  * GF_SOLVE_PERSISTENT (GF_MIXED only): the whole refinement loop as one
  * cooperative launch (one CTA set resident on every SM), with grid barriers
  * between its phases and the direction update fused into the SpMV.  Each barrier
@@ -206,7 +210,7 @@ enum { GF_SOLVE_KERNELS = 0, GF_SOLVE_PERSISTENT = 1, GF_SOLVE_CG = 2, GF_SOLVE_
 typedef struct gf_tuning {
   int32_t assembly;
   int32_t step_launch;   /* GF_STEP_GRAPH (0, default) or GF_STEP_STREAM */
-  int32_t solve_loop;    /* GF_SOLVE_KERNELS (default), GF_SOLVE_CG or GF_SOLVE_PERSISTENT */
+  int32_t solve_loop;    /* GF_SOLVE_KERNELS, GF_SOLVE_CG or GF_SOLVE_PERSISTENT (default: see above) */
   int32_t wait_test;     /* test hook, 0 */
   int32_t reserved[4];   /* set to 0 */
 } gf_tuning;
@@ -391,7 +395,9 @@ typedef struct gf_batch_tuning {
                            meshes by node count (at least 1 CTA each, at most the single-mesh grid);
                            converged meshes then cost few early-exit CTAs per iteration, and the
                            per-mesh reductions sum in a different (still fixed) order. */
-  int32_t solve_loop;   /* GF_SOLVE_KERNELS (0, default): per-kind launches of the solver loop
+  int32_t solve_loop;   /* A new batch starts with its members' default form (GF_SOLVE_KERNELS for
+                           GF_FP64, GF_SOLVE_CG for GF_MIXED).
+                           GF_SOLVE_KERNELS: per-kind launches of the solver loop
                            (graph WHILE node or stream, as `graph` says), each mesh with its
                            single-mesh grid or its share of grid_budget.
                            GF_SOLVE_DISTRIBUTED: per-kind launches of grid_budget CTAs (0: four per

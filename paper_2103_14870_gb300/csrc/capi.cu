@@ -503,6 +503,8 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
   DevMesh& d = m->dm;
   const bool mixed = opt.precision == GF_MIXED;
   m->mixed = mixed;
+  // the mixed step's default solver loop: the inner FP32 PCG in two kernels per iteration
+  m->tune.solve_loop = mixed ? GF_SOLVE_CG : GF_SOLVE_KERNELS;
   MixedHost mxh;
   if (mixed) {
     st = build_mixed_host(nodes, hm, mxh, err);
@@ -2505,6 +2507,7 @@ gf_status gf_batch_create(gf_mesh* const* meshes, int32_t n, gf_batch** out) {
   b->stream = meshes[0]->stream;
   b->tune.graph = 1;
   b->tune.chunk = 8;
+  b->tune.solve_loop = b->mixed ? GF_SOLVE_CG : GF_SOLVE_KERNELS;   // as a member mesh's default
   auto fail = [&](const char* what) {
     set_last_error(std::string("batch create: ") + what);
     batch_free(b);

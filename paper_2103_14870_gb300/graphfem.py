@@ -309,13 +309,15 @@ class Mesh:
                                              ctypes.byref(nq)))
         return {"vertices": V, "quads": Q[:nq.value], "n_faces": sz["n_faces"]}
 
-    def tuning_set(self, assembly: int = ASSEMBLY_GATHER, step_launch: int = STEP_GRAPH,
-                   solve_loop: int = SOLVE_KERNELS, wait_test: int = 0):
+    def tuning_set(self, assembly: int = None, step_launch: int = None, solve_loop: int = None,
+                   wait_test: int = None):
+        """gf_tuning_set; an argument left as None keeps the mesh's current value."""
+        cur = self.tuning_get()
         t = Tuning()
-        t.assembly = assembly
-        t.step_launch = step_launch
-        t.solve_loop = solve_loop
-        t.wait_test = wait_test
+        t.assembly = cur["assembly"] if assembly is None else assembly
+        t.step_launch = cur["step_launch"] if step_launch is None else step_launch
+        t.solve_loop = cur["solve_loop"] if solve_loop is None else solve_loop
+        t.wait_test = cur["wait_test"] if wait_test is None else wait_test
         _check(load_library().gf_tuning_set(self._h, ctypes.byref(t)))
 
     def tuning_get(self) -> dict:
@@ -456,10 +458,16 @@ class Batch:
         _check(load_library().gf_batch_step(self._h, float(dt), fp, pp, npin, vp, mem, stats))
         return [st.as_dict() for st in stats]
 
-    def tuning_set(self, graph: int = 1, chunk: int = 8, grid_budget: int = 0, solve_loop: int = SOLVE_KERNELS,
-                   inner: int = 0):
+    def tuning_set(self, graph: int = None, chunk: int = None, grid_budget: int = None, solve_loop: int = None,
+                   inner: int = None):
+        """gf_batch_tuning_set; an argument left as None keeps the batch's current value."""
+        cur = self.tuning_get()
         t = BatchTuning()
-        t.graph, t.chunk, t.grid_budget, t.solve_loop, t.inner = graph, chunk, grid_budget, solve_loop, inner
+        t.graph = cur["graph"] if graph is None else graph
+        t.chunk = cur["chunk"] if chunk is None else chunk
+        t.grid_budget = cur["grid_budget"] if grid_budget is None else grid_budget
+        t.solve_loop = cur["solve_loop"] if solve_loop is None else solve_loop
+        t.inner = cur["inner"] if inner is None else inner
         _check(load_library().gf_batch_tuning_set(self._h, ctypes.byref(t)))
 
     def tuning_get(self) -> dict:

@@ -117,6 +117,7 @@ def test_persistent_batch_members_step_as_alone():
         for w, th in zip(ws, thetas):
             mat = gf.material(w.young, w.poisson, w.density, threshold=th, radius=w.radius)
             singles.append(gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=1e-10, cg_maxit=5000))
+            singles[-1].tuning_set(solve_loop=gf.SOLVE_KERNELS)   # the three-kernel inner PCG of the phases
             members.append(gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED, cg_rtol=1e-10, cg_maxit=5000))
         for m, st in zip(singles + members, states + states):
             m.state_set(x=st.x.ravel(), v=st.v.ravel())
