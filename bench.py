@@ -254,7 +254,7 @@ def run_batch(args, gf, torch, barrier, stream, world=1, rank=0, dist=None) -> d
     f = [torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda") for w in ws]
     pins = [torch.tensor(w.pinned, dtype=torch.int32, device="cuda") for w in ws]
     dt = ws[0].dt
-    tuned, tuned_ms = b.autotune(dt, f, pins, trial_steps=3)
+    tuned, tuned_ms = b.autotune(dt, f, pins, trial_steps=6)
     out = {"workload": "64 Kuhn boxes, 2k-80k tets (log-uniform, seed 2), E in [1e4, 1e8]",
            "n_meshes": len(ws_all), "n_tets_total": int(sum(w.n_tets for w in ws_all)), "precision": "mixed",
            "cg_rtol": 1e-6, "tuning": tuned, "autotune_ms_per_step": tuned_ms,
