@@ -233,3 +233,37 @@ def sampled_parity(case, precision, pinned=None):
     np.testing.assert_allclose(m.positions_get(), x.ravel() + dt * v_new, rtol=1e-15, atol=1e-15)
     m.close()
     return stats
+
+
+def test_loaf_quasistatic_nested_solve_matches_fp64_solver():
+    """One quasi-static load step of the full loaf (end caps pulled apart by
+    1e-4 of the length, Newton to 1e-6) with each linear solver of the Newton
+    iterations: the nested solve (flexible FP64 PCG, FP32 inner PCG) stops at
+    the FP64 PCG's residual test, so both reach the same equilibrium: the same
+    labels and Newton iteration count, positions within 1e-7 of the largest
+    displacement (each Newton system is solved to cg_rtol 1e-6, so the two
+    iterates differ by the solver error, far below the load step)."""
+    w = loaf_config()
+    X = w.nodes
+    L = X[:, 0].max() - X[:, 0].min()
+    lo = np.nonzero(X[:, 0] <= X[:, 0].min() + 0.1 * L)[0].astype(np.int32)
+    hi = np.nonzero(X[:, 0] >= X[:, 0].max() - 0.1 * L)[0].astype(np.int32)
+    pins = np.concatenate([lo, hi])
+    target = X[pins].copy()
+    target[:len(lo), 0] -= 1e-4 * L
+    target[len(lo):, 0] += 1e-4 * L
+    mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius)
+    out = {}
+    for solver in (gf.QS_SOLVE_FP64, gf.QS_SOLVE_NESTED):
+        m = gf.mesh_create(X, w.tets, mat, cg_rtol=w.cg_rtol)
+        m.quasistatic_solver_set(solver)
+        s = m.quasistatic_step(None, pins, target, max_newton=20, rtol=1e-6)
+        assert s["status"] == 0 and s["rel_res"] <= 1e-6 and s["cg_iters"] > 0
+        out[solver] = (s, m.positions_get(), m.damage_get()[1])
+        m.close()
+    (s64, x64, l64), (sn, xn, ln) = out[gf.QS_SOLVE_FP64], out[gf.QS_SOLVE_NESTED]
+    assert sn["newton_iters"] == s64["newton_iters"]
+    np.testing.assert_array_equal(ln, l64)
+    d = np.abs(x64 - X.ravel()).max()
+    assert d > 0 and np.abs(xn - x64).max() <= 1e-7 * d
+    np.testing.assert_allclose(xn.reshape(-1, 3)[pins], target, rtol=0, atol=1e-12)
