@@ -472,6 +472,9 @@ def run_glass(args, gf, torch, barrier, stream) -> dict:
     m64.tuning_set(solve_loop=gf.SOLVE_CG)
     fp64_cg = timed_from_rest(args, m64, w, f_dev, pins, barrier, stream, torch, min(steps, 30))
     fp64_cg.pop("_prof")
+    m64.tuning_set(solve_loop=gf.SOLVE_NESTED)
+    fp64_nested = timed_from_rest(args, m64, w, f_dev, pins, barrier, stream, torch, min(steps, 30))
+    fp64_nested.pop("_prof")
     m64.tuning_set(solve_loop=gf.SOLVE_KERNELS)
     mm.tuning_set(solve_loop=gf.SOLVE_PERSISTENT)
     mixed_p = timed_from_rest(args, mm, w, f_dev, pins, barrier, stream, torch, min(steps, 30))
@@ -518,6 +521,9 @@ def run_glass(args, gf, torch, barrier, stream) -> dict:
             "threshold_rule": "(1 - 1e-3) quantile of the FP64 step-10 drivers from rest, 3 significant figures",
             "steps_timed": steps, "fp64": fp64, "mixed": mixed,
             "fp64_solve_cg_form": {k: fp64_cg[k] for k in ("ms_per_step", "cg_iters_per_step")},
+            "fp64_solve_nested": dict({k: fp64_nested[k] for k in ("ms_per_step", "cg_iters_per_step")},
+                                      solve="flexible FP64 PCG around an FP32 inner PCG to 1e-2, same FP64 "
+                                            "1e-6 residual test; cg_iters are inner iterations"),
             "mixed_solve_persistent": {k: mixed_p[k] for k in ("ms_per_step", "cg_iters_per_step", "refine_sweeps_per_step")},
             "mixed_three_kernel_inner_pcg": {k: mixed_k3[k] for k in ("ms_per_step", "cg_iters_per_step",
                                                                        "refine_sweeps_per_step")},

@@ -201,16 +201,23 @@ enum { GF_STEP_GRAPH = 0, GF_STEP_STREAM = 1 };
  * between its phases and the direction update fused into the SpMV.  Each barrier
  * wait gives up after 1 s and the step then returns GF_TIMEOUT (the mesh state
  * is then unspecified: set it again with gf_state_set).
+ * GF_SOLVE_NESTED (GF_FP64 only): the step's linear solve as flexible PCG in
+ * FP64 around an inner PCG in FP32 on the matrix and block inverses rounded to
+ * FP32, the quasi-static step's GF_QS_SOLVE_NESTED (inner tolerance: the one
+ * gf_quasistatic_solver_set sets, default 1e-2).  It stops at the FP64 PCG's
+ * residual test, so it solves the same FP64 system; it pays on stiff systems
+ * with many PCG iterations.  Steps in this form launch kernel by kernel (the
+ * solve loop itself is one graph); stats report the inner iterations.
  * GF_SOLVE_DISTRIBUTED is a batch form (gf_batch_tuning).
  * Another form than the precision supports -> GF_UNSUPPORTED.
  * wait_test: a test hook; 1 makes one CTA of the next persistent solve skip its
  * first barrier arrival, so that every wait of that barrier runs out (the
  * step returns GF_TIMEOUT after about 1 s).  Leave it 0. */
-enum { GF_SOLVE_KERNELS = 0, GF_SOLVE_PERSISTENT = 1, GF_SOLVE_CG = 2, GF_SOLVE_DISTRIBUTED = 3 };
+enum { GF_SOLVE_KERNELS = 0, GF_SOLVE_PERSISTENT = 1, GF_SOLVE_CG = 2, GF_SOLVE_DISTRIBUTED = 3, GF_SOLVE_NESTED = 4 };
 typedef struct gf_tuning {
   int32_t assembly;
   int32_t step_launch;   /* GF_STEP_GRAPH (0, default) or GF_STEP_STREAM */
-  int32_t solve_loop;    /* GF_SOLVE_KERNELS, GF_SOLVE_CG or GF_SOLVE_PERSISTENT (default: see above) */
+  int32_t solve_loop;    /* GF_SOLVE_KERNELS, GF_SOLVE_CG, GF_SOLVE_PERSISTENT or GF_SOLVE_NESTED (default: see above) */
   int32_t wait_test;     /* test hook, 0 */
   int32_t reserved[4];   /* set to 0 */
 } gf_tuning;

@@ -175,7 +175,7 @@ struct gf_mesh {
   double* qs_out = nullptr;   // quasi-static: E, |E| scale, slope [4]
   double* qs_w = nullptr;     // quasi-static: A z of the Chronopoulos-Gear PCG [3N]
   int qs_solver = GF_QS_SOLVE_FP64;
-  double qs_in_rtol = 1e-2;   // inner tolerance of the nested quasi-static solve
+  double qs_in_rtol = 1e-2;   // inner tolerance of the nested solve (quasi-static step, GF_SOLVE_NESTED)
   MixDev qsr{};               // its FP32 matrix, inverses, vectors and state (first use)
   cudaGraph_t qs_graph = nullptr;          // its solver loop as a WHILE node (first use)
   cudaGraphExec_t qs_graph_exec = nullptr;
@@ -766,13 +766,19 @@ gf_status gf_tuning_set(gf_mesh* m, const gf_tuning* t) {
     set_last_error("bad tuning (step_launch must be GF_STEP_GRAPH or GF_STEP_STREAM)");
     return GF_BAD_ARG;
   }
-  if ((t->solve_loop != GF_SOLVE_KERNELS && t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_CG) ||
+  if ((t->solve_loop != GF_SOLVE_KERNELS && t->solve_loop != GF_SOLVE_PERSISTENT && t->solve_loop != GF_SOLVE_CG &&
+       t->solve_loop != GF_SOLVE_NESTED) ||
       (t->wait_test != 0 && t->wait_test != 1)) {
-    set_last_error("bad tuning (solve_loop must be GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT or GF_SOLVE_CG, wait_test 0 or 1)");
+    set_last_error("bad tuning (solve_loop must be GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT, GF_SOLVE_CG or "
+                   "GF_SOLVE_NESTED, wait_test 0 or 1)");
     return GF_BAD_ARG;
   }
   if (t->solve_loop == GF_SOLVE_PERSISTENT && !m->mixed) {
     set_last_error("GF_SOLVE_PERSISTENT is built for GF_MIXED meshes");
+    return GF_UNSUPPORTED;
+  }
+  if (t->solve_loop == GF_SOLVE_NESTED && m->mixed) {
+    set_last_error("GF_SOLVE_NESTED is built for GF_FP64 meshes");
     return GF_UNSUPPORTED;
   }
   m->tune = *t;
@@ -896,6 +902,11 @@ bool persist_on(const gf_mesh* m) { return m->mixed && m->tune.solve_loop == GF_
 // on first use; GF_MIXED: its FP32 w32 is allocated with the mesh)
 bool cg_form_on(const gf_mesh* m) { return !m->mixed && m->tune.solve_loop == GF_SOLVE_CG; }
 bool mixed_cg_on(const gf_mesh* m) { return m->mixed && m->tune.solve_loop == GF_SOLVE_CG; }
+// GF_SOLVE_NESTED (GF_FP64): flexible FP64 PCG around an FP32 inner PCG (the
+// quasi-static nested solve), stream form
+bool nested_on(const gf_mesh* m) { return !m->mixed && m->tune.solve_loop == GF_SOLVE_NESTED; }
+gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const StepScalars& sq, int64_t& L,
+                          int& iters, int& status);
 gf_status cg_form_setup(gf_mesh* m, DevMesh& d) {
   if (!m->qs_w) {
     gf_status st = scratch(m, 3 * size_t(d.N), &m->qs_w);
@@ -947,12 +958,20 @@ gf_status step_fp64(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n_
     return GF_OK;
   };
   // PCG on the assembled system from the dv in place; returns after convergence or maxit
-  const bool cg_form = cg_form_on(m);
-  if (cg_form) {
+  const bool cg_form = cg_form_on(m), nested = nested_on(m);
+  if (cg_form || nested) {   // both keep w = A z
     gf_status st = cg_form_setup(m, d);
     if (st != GF_OK) return st;
   }
   auto run_pcg = [&]() -> gf_status {
+    if (nested) {   // its outcome lands in d.pcg like the PCG's
+      int its = 0, nst = GF_OK;
+      gf_status st = qs_nested_solve(m, d, mt, sp, L, its, nst);
+      if (st != GF_OK) return st;
+      GF_CK(cudaMemcpyAsync(m->h_pcg, d.pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      GF_CK(cudaStreamSynchronize(s));
+      return GF_OK;
+    }
     int launched_iters = 0;
     int chunk = std::max(1, std::min(m->last_iters + 1, 64));
     if (cg_form) { Prof p(m, kPSpmv, 0); L += launch_qs_cg_spmv(d, s); }   // w = A z, coefficients
@@ -1117,7 +1136,7 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
 // Whether a step can run as the captured graph: the plain step (one Newton
 // iteration, two-phase assembly, no network, no per-launch profiling).
 bool graph_step_ok(const gf_mesh* m) {
-  return m->tune.step_launch == GF_STEP_GRAPH && !m->prof && !m->gnn &&
+  return m->tune.step_launch == GF_STEP_GRAPH && !m->prof && !m->gnn && !nested_on(m) &&
          (m->mixed || (m->newton_iters == 1 && m->tune.assembly == GF_ASSEMBLY_GATHER));
 }
 
@@ -1356,8 +1375,8 @@ gf_status qs_nested_graph(gf_mesh* m, const DevMesh& dq, const gf::Material& mq,
   return GF_OK;
 }
 
-gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const StepScalars& sq, double bb,
-                          int64_t& L, int& iters, int& status) {
+gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const StepScalars& sq, int64_t& L,
+                          int& iters, int& status) {
   cudaStream_t s = m->stream;
   const int64_t N = dq.N;
   MixDev& x = m->qsr;
@@ -1372,8 +1391,7 @@ gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const 
   }
   dq.mx = x;
   L += launch_qsr_to32(dq, s);
-  IrState init{};
-  init.bb = bb;
+  IrState init{};   // bb: k_qsr_start takes the reference k_pcg_init left in m.pcg
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
   init.in_tol2 = m->qs_in_rtol * m->qs_in_rtol;
   init.maxit = m->opt.cg_maxit;
@@ -1413,6 +1431,7 @@ gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const 
       { Prof p(m, kPIrApply); L += launch_fcg_update(dq, s); }
     }
   }
+  L += launch_nested_finish(dq, s);
   GF_CK(cudaGetLastError());
   iters = m->h_ir->total_iters;
   status = m->h_ir->done ? m->h_ir->status : GF_CG_MAXITER;
@@ -1636,7 +1655,7 @@ gf_status gf_quasistatic_step(gf_mesh* m, const double* f_ext, const int32_t* pi
     if (rn == 0.0 || rn <= rtol * r0) break;
     if (m->qs_solver == GF_QS_SOLVE_NESTED) {
       int its = 0, qst = GF_OK;
-      if ((st = qs_nested_solve(m, dq, mq, sq, m->h_pcg->bb, L, its, qst)) != GF_OK) return st;
+      if ((st = qs_nested_solve(m, dq, mq, sq, L, its, qst)) != GF_OK) return st;
       cg_total += its;
       m->last_iters = its;
       if (qst != GF_OK) {

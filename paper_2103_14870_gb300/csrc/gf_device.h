@@ -291,6 +291,7 @@ int launch_qs_trial(int64_t n, const double* x, const double* d, double a, doubl
 // FP32 buffers and IrState, m.pcg the outer scalars, m.w the vector A z)
 int launch_qsr_to32(const DevMesh& m, cudaStream_t s);
 int launch_qsr_start(const DevMesh& m, cudaStream_t s);
+int launch_nested_finish(const DevMesh& m, cudaStream_t s);   // its outcome into m.pcg
 int launch_fcg_spmv(const DevMesh& m, cudaStream_t s);
 int launch_fcg_update(const DevMesh& m, cudaStream_t s);
 int launch_qs_set_pins(const DevMesh& m, const int32_t* ids, const double* pos, int64_t n_pinned, cudaStream_t s);

@@ -1377,10 +1377,11 @@ __device__ __forceinline__ void outer_residual_done(IrState* S, double rr, doubl
   S->in_done = (S->done || gamma == 0.0) ? 1 : 0;
 }
 
-// first inner start, from the residual k_pcg_init left in m.r (dv = 0)
+// first inner start, from the residual r = b - A dv that k_pcg_init left in m.r
+// (dv = 0, or a warm start), with the reference |b|^2 it left in m.pcg
 __global__ void __launch_bounds__(kThreads) k_qsr_start(DevMesh m) {
-  const double bb = m.mx.ir->bb;   // r = b on free rows
-  const double sc = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
+  const double bb = m.pcg->bb, rr0 = m.pcg->rr;
+  const double sc = rr0 > 0.0 ? 1.0 / sqrt(rr0) : 1.0;
   double v[3] = {0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m.N; i += int64_t(gridDim.x) * blockDim.x) {
     double r[3];
@@ -1392,8 +1393,21 @@ __global__ void __launch_bounds__(kThreads) k_qsr_start(DevMesh m) {
     inner_start_row(m, i, r, sc, v[1], v[2]);
   }
   double out[3];
-  if (grid_reduce<3>(v, m.partials, m.tickets + 13, out, blockIdx.x, gridDim.x) && threadIdx.x == 0)
+  if (grid_reduce<3>(v, m.partials, m.tickets + 13, out, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
+    m.mx.ir->bb = bb;
     outer_residual_done(m.mx.ir, out[0], out[1], out[2], true);
+  }
+}
+
+// the nested solve's outcome in the PCG state the step reads: iterations (inner),
+// status, done
+__global__ void k_nested_finish(DevMesh m) {
+  if (threadIdx.x != 0) return;
+  const IrState* S = m.mx.ir;
+  m.pcg->iters = S->total_iters;
+  m.pcg->status = S->done ? S->status : GF_CG_MAXITER;
+  m.pcg->rr = S->rr;
+  m.pcg->done = 1;
 }
 
 // z = fl64(d32) (the inner solution; zero on pinned rows), w = A z, and z.q',
@@ -1582,6 +1596,10 @@ int launch_qsr_to32(const DevMesh& m, cudaStream_t s) {
 }
 int launch_qsr_start(const DevMesh& m, cudaStream_t s) {
   k_qsr_start<<<qs_grid(m.N), kThreads, 0, s>>>(m);
+  return 1;
+}
+int launch_nested_finish(const DevMesh& m, cudaStream_t s) {
+  k_nested_finish<<<1, 32, 0, s>>>(m);
   return 1;
 }
 int launch_fcg_spmv(const DevMesh& m, cudaStream_t s) {

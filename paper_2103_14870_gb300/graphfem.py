@@ -69,7 +69,7 @@ class Tuning(ctypes.Structure):
 
 ASSEMBLY_GATHER, ASSEMBLY_COLOUR = 0, 1
 STEP_GRAPH, STEP_STREAM = 0, 1
-SOLVE_KERNELS, SOLVE_PERSISTENT, SOLVE_CG, SOLVE_DISTRIBUTED = 0, 1, 2, 3
+SOLVE_KERNELS, SOLVE_PERSISTENT, SOLVE_CG, SOLVE_DISTRIBUTED, SOLVE_NESTED = 0, 1, 2, 3, 4
 QS_SOLVE_FP64, QS_SOLVE_NESTED = 0, 1
 
 

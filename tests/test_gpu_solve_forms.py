@@ -152,6 +152,55 @@ def test_mixed_cg_form_stiff_glass_beam():
         st = new
 
 
+@pytest.mark.parametrize("launch", [gf.STEP_GRAPH, gf.STEP_STREAM])
+def test_fp64_nested_form_fracturing_steps_match_oracle(launch):
+    """FP64 steps whose linear solve is the nested one (flexible FP64 PCG around
+    an FP32 inner PCG): it stops at the FP64 residual test (1e-12 here), so the
+    steps match the oracle at the FP64 bar."""
+    w = beam_config()
+    st = deformed_state(w, seed=31)
+    d0, _, _, _ = oracle_model(w, threshold=math.inf).damage_update(st)
+    theta = float(np.quantile(d0, 0.95))
+    model = oracle_model(w, threshold=theta)
+    m = fp64_mesh(w, gpu_material(gf, w, threshold=theta), launch, solve=gf.SOLVE_NESTED)
+    for k in range(3):
+        m.state_set(x=st.x.ravel(), v=st.v.ravel(), labels=st.labels, chi=st.chi)
+        s = m.step(w.dt, w.f_ext.ravel(), w.pinned)
+        new, info = model.step(st, w.dt, w.f_ext, w.pinned)
+        assert s["status"] == 0 and s["rel_res"] <= 1e-12 and s["cg_iters"] > 0
+        drv, lab = m.damage_get()
+        fin = np.isfinite(info["driver"])
+        assert_close(drv[fin], info["driver"][fin], what="driver", floor=0.0, abs_floor=1e-13)
+        assert_labels(lab, info["labels"], info["driver"], theta)
+        if np.array_equal(lab, info["labels"]):
+            assert_norm_close(m.velocities_get(), new.v, what="v (nested form)")
+            assert_positions_close(m.positions_get(), new.x, st.x, what="x (nested form)")
+        st = new
+
+
+def test_fp64_nested_form_stiff_glass_beam():
+    """Glass stiffness: the nested form reaches the same 1e-12 FP64 residual as
+    the three-kernel PCG and agrees with it and with the oracle's direct solve
+    to the accuracy that residual allows (R36)."""
+    b = beam_config()
+    w = Workload("beam_glass", b.nodes, b.tets, 7e10, 0.22, 2500.0, 5e-4, 3, math.inf, 1.5, b.f_ext * 20.0, b.pinned)
+    model = oracle_model(w)
+    mat = gpu_material(gf, w)
+    n = fp64_mesh(w, mat, gf.STEP_GRAPH, solve=gf.SOLVE_NESTED)
+    k3 = fp64_mesh(w, mat, gf.STEP_GRAPH, solve=gf.SOLVE_KERNELS)
+    st = model.rest_state()
+    for k in range(3):
+        for m in (n, k3):
+            m.state_set(x=st.x.ravel(), v=st.v.ravel())
+        sn = n.step(w.dt, w.f_ext.ravel(), w.pinned)
+        sk = k3.step(w.dt, w.f_ext.ravel(), w.pinned)
+        new, _ = model.step(st, w.dt, w.f_ext, w.pinned)
+        assert sn["status"] == 0 and sn["rel_res"] <= 1e-12 and sn["cg_iters"] > 10
+        assert_norm_close(n.velocities_get(), new.v, rtol=1e-7, what=f"v (glass, nested form, step {k})")
+        assert_norm_close(n.velocities_get(), k3.velocities_get(), rtol=1e-7, what="v, nested vs three kernels")
+        st = new
+
+
 def test_solve_forms_refused_where_not_built():
     w = beam_config()
     mat = gpu_material(gf, w)
@@ -159,4 +208,9 @@ def test_solve_forms_refused_where_not_built():
     with pytest.raises(gf.GraphFEMError) as e:
         m64.tuning_set(solve_loop=gf.SOLVE_PERSISTENT)
     assert e.value.status == 8
+    m32 = gf.mesh_create(w.nodes, w.tets, mat, precision=gf.MIXED)
+    with pytest.raises(gf.GraphFEMError) as e:
+        m32.tuning_set(solve_loop=gf.SOLVE_NESTED)
+    assert e.value.status == 8
     m64.close()
+    m32.close()
