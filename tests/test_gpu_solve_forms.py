@@ -201,6 +201,29 @@ def test_fp64_nested_form_stiff_glass_beam():
         st = new
 
 
+def test_fp64_nested_form_with_newton_iterations():
+    """Two Newton iterations per step: the second solve starts from the first
+    one's dv (a warm start, the reference |b|^2 from k_pcg_init); the nested
+    form matches the three-kernel PCG to its 1e-12 residual on fracturing beam
+    steps."""
+    w = beam_config()
+    st = deformed_state(w, seed=37)
+    d0, _, _, _ = oracle_model(w, threshold=math.inf).damage_update(st)
+    mat = gpu_material(gf, w, threshold=float(np.quantile(d0, 0.95)))
+    n = fp64_mesh(w, mat, gf.STEP_STREAM, solve=gf.SOLVE_NESTED)
+    k3 = fp64_mesh(w, mat, gf.STEP_STREAM, solve=gf.SOLVE_KERNELS)
+    for m in (n, k3):
+        m.newton_set(2)
+        m.state_set(x=st.x.ravel(), v=st.v.ravel())
+    for k in range(3):
+        sn = n.step(w.dt, w.f_ext.ravel(), w.pinned)
+        sk = k3.step(w.dt, w.f_ext.ravel(), w.pinned)
+        assert sn["status"] == 0 and sk["status"] == 0 and sn["newton_iters"] == 2 == sk["newton_iters"]
+        assert sn["rel_res"] <= 1e-12
+        np.testing.assert_array_equal(n.damage_get()[1], k3.damage_get()[1])
+        assert_norm_close(n.velocities_get(), k3.velocities_get(), rtol=1e-9, what=f"v, nested vs kernels, step {k}")
+
+
 def test_solve_forms_refused_where_not_built():
     w = beam_config()
     mat = gpu_material(gf, w)
