@@ -608,7 +608,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
         (st = scratch(m, 70 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
         (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
-        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.p32b)) || (st = scratch(m, 3 * N, &x.w32)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
+        (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.p32b)) || (st = scratch(m, 3 * N, &x.w32)) || (st = scratch(m, N, &x.z4)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
         (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) ||
         (st = scratch(m, 1, &x.ir)))
       return fail(st);
@@ -1386,7 +1386,7 @@ gf_status qs_nested_solve(gf_mesh* m, DevMesh dq, const gf::Material& mq, const 
         (st = scratch(m, 3 * size_t(N), &x.r32)) || (st = scratch(m, 3 * size_t(N), &x.z32)) ||
         (st = scratch(m, 3 * size_t(N), &x.p32)) || (st = scratch(m, 3 * size_t(N), &x.q32)) ||
         (st = scratch(m, 3 * size_t(N), &x.w32)) || (st = scratch(m, 3 * size_t(N), &x.d32)) ||
-        (st = scratch(m, 1, &x.ir)) || (st = scratch(m, 1, &m->qs_loops)))
+        (st = scratch(m, size_t(N), &x.z4)) || (st = scratch(m, 1, &x.ir)) || (st = scratch(m, 1, &m->qs_loops)))
       return st;
   }
   dq.mx = x;

@@ -66,7 +66,8 @@ struct MixDev {
   float* pinv32 = nullptr;            // [N][9]
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;   // [3N]
   float* p32b = nullptr;              // [3N] second search-direction buffer of the persistent solve
-  float* w32 = nullptr;               // [3N] A z of the Chronopoulos-Gear inner PCG
+  float* w32 = nullptr;               // [3N] A z of the two-kernel inner PCG
+  float4* z4 = nullptr;               // [N] z of the two-kernel inner PCG, one 16-byte row per node (w unused)
   float *dv_hi = nullptr, *dv_lo = nullptr;   // [3N] double-float split of dv
   IrState* ir = nullptr;
 };

@@ -1328,8 +1328,8 @@ __global__ void __launch_bounds__(kThreads) k_qsr_to32(DevMesh m) {
 // by sc = 1 / |r_prev| so that the FP32 solve and its double-float sums work on
 // values near 1 whatever the outer residual has fallen to (the flexible PCG is
 // invariant to a scaling of the preconditioner's output): r32 = fl(sc r),
-// z32 = P32 r32, p32 = z32, d32 = 0; adds r32 . z32 and r32 . r32 to g and n
-// (exact products of floats, summed in FP64)
+// z = P32 r32 (into z4, the two-kernel inner form's z), d32 = 0; adds
+// r32 . z and r32 . r32 to g and n (exact products of floats, summed in FP64)
 __device__ __forceinline__ void inner_start_row(const DevMesh& m, int64_t i, const double r[3], double sc, double& g,
                                                 double& n) {
   const MixDev& x = m.mx;
@@ -1346,10 +1346,9 @@ __device__ __forceinline__ void inner_start_row(const DevMesh& m, int64_t i, con
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     x.r32[3 * i + c] = r32[c];
-    x.z32[3 * i + c] = z32[c];
-    x.p32[3 * i + c] = z32[c];
     x.d32[3 * i + c] = 0.f;
   }
+  x.z4[i] = make_float4(z32[0], z32[1], z32[2], 0.f);
 }
 
 // the last CTA's bookkeeping after a new outer residual: the outer test, then

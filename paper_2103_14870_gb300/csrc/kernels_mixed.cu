@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, 5) kb_ir_residual(const BatchTab* __
 }
 
 // inner PCG start (only after a fresh residual; otherwise the current inner
-// solve continues): r32 = r, z = P r, p = z, d = 0
+// solve continues): r32 = r, z = P r (z32 and z4), p = z, d = 0
 __device__ __forceinline__ void ir_inner_init_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
 
   IrState* S = m.mx.ir;
@@ -864,6 +864,7 @@ __device__ __forceinline__ void ir_inner_init_body(const DevMesh& m, const Mater
       x.d32[3 * i + c] = 0.f;
       df_acc_prod(h[0], l[0], r[c], z[c]);
     }
+    x.z4[i] = make_float4(z[0], z[1], z[2], 0.f);   // z of the two-kernel form
   }
   double out[1];
   if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 5, out, bid, nb) && threadIdx.x == 0) {
@@ -888,7 +889,26 @@ __global__ void __launch_bounds__(kThreads) kb_ir_inner_init(const BatchTab* __r
 // with component c of both rows, stores it to y and adds v_i . y_i to (h, l)
 // in double-float (own v loaded up front).  The same bits for y as one row at a
 // time: every lane sums its blocks in the same order.
-__device__ __forceinline__ void spmv32_rows(const DevMesh& m, const float* __restrict__ v, float* __restrict__ y,
+// A node's three components of a vector stored as [N][3] floats or as one
+// 16-byte row per node (float4, w unused: a single load per gather)
+__device__ __forceinline__ void vrow(const float* __restrict__ v, int64_t j, float& a, float& b, float& c) {
+  a = v[3 * j];
+  b = v[3 * j + 1];
+  c = v[3 * j + 2];
+}
+__device__ __forceinline__ void vrow(const float4* __restrict__ v, int64_t j, float& a, float& b, float& c) {
+  const float4 t = v[j];
+  a = t.x;
+  b = t.y;
+  c = t.z;
+}
+__device__ __forceinline__ float vcomp(const float* __restrict__ v, int64_t i, int c) { return v[3 * i + c]; }
+__device__ __forceinline__ float vcomp(const float4* __restrict__ v, int64_t i, int c) {
+  return reinterpret_cast<const float*>(v)[4 * i + c];
+}
+
+template <typename V>
+__device__ __forceinline__ void spmv32_rows(const DevMesh& m, const V* __restrict__ v, float* __restrict__ y,
                                             unsigned bid, unsigned nb, float& h, float& l) {
   const float* __restrict__ val = m.mx.val32;
   const int j16 = threadIdx.x & 15;
@@ -899,8 +919,8 @@ __device__ __forceinline__ void spmv32_rows(const DevMesh& m, const float* __res
     const bool two = i1 < m.N;
     const int s0 = m.row_ptr[i0], e0 = m.row_ptr[i0 + 1];
     const int s1 = two ? m.row_ptr[i1] : 0, e1 = two ? m.row_ptr[i1 + 1] : 0;
-    const float vi0 = j16 < 3 ? v[3 * i0 + j16] : 0.f;
-    const float vi1 = (two && j16 < 3) ? v[3 * i1 + j16] : 0.f;
+    const float vi0 = j16 < 3 ? vcomp(v, i0, j16) : 0.f;
+    const float vi1 = (two && j16 < 3) ? vcomp(v, i1, j16) : 0.f;
     float y0 = 0.f, y1 = 0.f, y2 = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
     const int len = max(e0 - s0, e1 - s1);
     for (int k = j16; k < len; k += 16) {
@@ -908,7 +928,8 @@ __device__ __forceinline__ void spmv32_rows(const DevMesh& m, const float* __res
         const int b = s0 + k;
         const int64_t j = m.col[b];
         const float* a = val + 9 * int64_t(b);
-        const float x0 = v[3 * j], x1 = v[3 * j + 1], x2 = v[3 * j + 2];
+        float x0, x1, x2;
+        vrow(v, j, x0, x1, x2);
         y0 += a[0] * x0 + a[1] * x1 + a[2] * x2;
         y1 += a[3] * x0 + a[4] * x1 + a[5] * x2;
         y2 += a[6] * x0 + a[7] * x1 + a[8] * x2;
@@ -917,7 +938,8 @@ __device__ __forceinline__ void spmv32_rows(const DevMesh& m, const float* __res
         const int b = s1 + k;
         const int64_t j = m.col[b];
         const float* a = val + 9 * int64_t(b);
-        const float x0 = v[3 * j], x1 = v[3 * j + 1], x2 = v[3 * j + 2];
+        float x0, x1, x2;
+        vrow(v, j, x0, x1, x2);
         u0 += a[0] * x0 + a[1] * x1 + a[2] * x2;
         u1 += a[3] * x0 + a[4] * x1 + a[5] * x2;
         u2 += a[6] * x0 + a[7] * x1 + a[8] * x2;
@@ -1070,7 +1092,7 @@ __device__ __forceinline__ void ir_cg_spmv_body(const DevMesh& m, const Material
   if (S->done || S->in_done) return;
   const MixDev& x = m.mx;
   float h[1] = {0.f}, l[1] = {0.f};
-  spmv32_rows(m, x.z32, x.w32, bid, nb, h[0], l[0]);   // w = A32 z, z . w (z is zero on pinned rows)
+  spmv32_rows(m, x.z4, x.w32, bid, nb, h[0], l[0]);   // w = A32 z, z . w (z is zero on pinned rows)
   double out[1];
   if (grid_reduce_df<1>(h, l, m.partials, m.tickets + 11, out, bid, nb) && threadIdx.x == 0) {
     const double den = S->in_iters > 0 ? out[0] - S->beta * S->rz / S->alpha : out[0];   // p.A.p
@@ -1113,9 +1135,14 @@ __device__ __forceinline__ void ir_cg_update_body(const DevMesh& m, const Materi
     // first iteration, and d, r and the inverse not on pinned rows
     const bool fixed = m.pinned[i];
     float zo[3], w[3], pq[3], qo[3], d[3], r[3], pi[9];
+    {
+      const float4 t = x.z4[i];
+      zo[0] = t.x;
+      zo[1] = t.y;
+      zo[2] = t.z;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      zo[c] = x.z32[3 * i + c];
       w[c] = x.w32[3 * i + c];
       pq[c] = x.p32[3 * i + c];
       qo[c] = x.q32[3 * i + c];
@@ -1139,13 +1166,14 @@ __device__ __forceinline__ void ir_cg_update_body(const DevMesh& m, const Materi
       r[c] = r[c] - alpha * q[c];
       x.r32[3 * i + c] = r[c];
     }
+    float zn[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float z = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
-      x.z32[3 * i + c] = z;
-      df_acc_prod(h[0], l[0], r[c], z);
+      zn[c] = pi[3 * c] * r[0] + pi[3 * c + 1] * r[1] + pi[3 * c + 2] * r[2];
+      df_acc_prod(h[0], l[0], r[c], zn[c]);
       df_acc_prod(h[1], l[1], r[c], r[c]);
     }
+    x.z4[i] = make_float4(zn[0], zn[1], zn[2], 0.f);
   }
   double out[2];
   if (grid_reduce_df<2>(h, l, m.partials, m.tickets + 12, out, bid, nb) && threadIdx.x == 0) {
