@@ -850,7 +850,7 @@ def run_profile_step(args) -> None:
                   for v in ws]
         b = gf.Batch(meshes)
         b.tuning_set(graph=0, chunk=8, grid_budget=4 * 152 * 2,
-                     solve_loop=gf.SOLVE_CG if args.solve == "cg" else gf.SOLVE_KERNELS)
+                     solve_loop={"default": None, "cg": gf.SOLVE_CG}.get(args.solve, gf.SOLVE_KERNELS))
         f = [torch.tensor(v.f_ext.ravel(), dtype=torch.float64, device="cuda") for v in ws]
         pins = [torch.tensor(v.pinned, dtype=torch.int32, device="cuda") for v in ws]
         st = None
@@ -871,8 +871,11 @@ def run_profile_step(args) -> None:
                        precision=gf.MIXED if args.precision == "mixed" else gf.FP64)
     # kernel-by-kernel launches (the same kernels as the graph replay), so that
     # ncu lists every kernel of the step
-    solve = {"kernels": gf.SOLVE_KERNELS, "cg": gf.SOLVE_CG, "persistent": gf.SOLVE_PERSISTENT}[args.solve]
+    solve = {"default": None, "kernels": gf.SOLVE_KERNELS, "cg": gf.SOLVE_CG, "persistent": gf.SOLVE_PERSISTENT,
+             "nested": gf.SOLVE_NESTED}[args.solve]
     m.tuning_set(step_launch=gf.STEP_STREAM, solve_loop=solve)
+    if args.solve == "nested":   # per-kernel profiling: the nested solve launches from the host, so ncu lists it
+        m.profile_enable(True)
     if args.qs_solver == "nested":
         m.quasistatic_solver_set(gf.QS_SOLVE_NESTED)
     f_dev = torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda")
@@ -935,8 +938,8 @@ def main():
                     help="form run by --profile-step (see run_profile_step)")
     ap.add_argument("--workload", choices=["loaf", "glass"], default="loaf",
                     help="--profile-step workload: the loaf or the glass point impact on the loaf mesh")
-    ap.add_argument("--solve", choices=["kernels", "cg", "persistent"], default="kernels",
-                    help="--profile-step solver-loop form (gf_tuning.solve_loop)")
+    ap.add_argument("--solve", choices=["default", "kernels", "cg", "persistent", "nested"], default="default",
+                    help="--profile-step solver-loop form (gf_tuning.solve_loop; default: the mesh's own)")
     ap.add_argument("--qs-solver", choices=["fp64", "nested"], default="fp64",
                     help="--profile-step --precision qs: linear solver of the Newton iterations")
     args = ap.parse_args()
