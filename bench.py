@@ -825,9 +825,40 @@ def run_ours(args) -> None:
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    out.update(summary_scalars(out))   # flat copies: a record that keeps only scalars still shows them
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def summary_scalars(out: dict) -> dict:
+    """The main numbers of the nested lines, flat (ms per step unless named)."""
+    def get(*path):
+        d = out
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    return {
+        "fp64_roofline_frac": get("roofline", "frac"),
+        "mixed_ms_per_step": get("mixed", "ms_per_step"),
+        "mixed_roofline_frac": get("mixed", "roofline", "frac"),
+        "mixed_speedup_vs_fp64": get("mixed", "speedup_vs_fp64"),
+        "glass_fp64_ms_per_step": get("mixed_glass", "fp64", "ms_per_step"),
+        "glass_fp64_nested_ms_per_step": get("mixed_glass", "fp64_solve_nested", "ms_per_step"),
+        "glass_mixed_ms_per_step": get("mixed_glass", "mixed", "ms_per_step"),
+        "glass_mixed_rel_err_dv_max": get("mixed_glass", "per_step_error_vs_fp64", "rel_err_dv_max"),
+        "c2_fp64_ms_per_step": get("survey_c2", "fp64", "ms_per_step"),
+        "c2_mixed_ms_per_step": get("survey_c2", "mixed", "ms_per_step"),
+        "batch_ms_per_step": get("batch", "ms_per_step"),
+        "batch_members_one_at_a_time_ms": get("batch", "modes", "members_one_at_a_time", "ms_per_step"),
+        "learned_ms_per_step": get("learned", "held_out", "learned_start", "ms_per_step"),
+        "learned_plain_ms_per_step": get("learned", "held_out", "plain", "ms_per_step"),
+        "quasistatic_fp64_ms_per_load_step": get("extensions", "quasistatic_pull_fp64", "ms_per_load_step"),
+        "quasistatic_nested_ms_per_load_step": get("extensions", "quasistatic_pull_nested_fp32_inner",
+                                                   "ms_per_load_step"),
+    }
 
 
 def run_profile_step(args) -> None:
