@@ -415,36 +415,53 @@ def calibrate_threshold(m, w, f_dev, pins, np):
 
 def timed_from_rest(args, m, w, f_dev, pins, barrier, stream, torch, steps):
     """`steps` timed steps after the warm-up, from the rest state, unprofiled
-    (one graph replay per step), then 3 profiled steps for the breakdown."""
+    (one graph replay per step), then 3 profiled steps for the breakdown.  If
+    the timed loop took more than 1.25x the kernel time per step (+0.2 ms), the
+    GPU sat idle between steps (the host thread stalled on the shared machine):
+    the loop is timed once more from rest, and both timings are reported."""
     import numpy as np
-    m.state_set(x=w.nodes.ravel(), v=np.zeros(w.nodes.size), labels=np.zeros(m.n_edges, np.uint8),
-                chi=np.ones(m.n_tets))
-    for _ in range(args.warmup):
-        m.step(w.dt, f_dev, pins)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    its, sweeps, broken = [], [], []
-    for _ in range(steps):
-        s = m.step(w.dt, f_dev, pins)
-        assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
-        its.append(s["cg_iters"])
-        sweeps.append(s["refine_sweeps"])
-        broken.append(s["n_broken"])
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1) / steps
+
+    def timed_loop():
+        m.state_set(x=w.nodes.ravel(), v=np.zeros(w.nodes.size), labels=np.zeros(m.n_edges, np.uint8),
+                    chi=np.ones(m.n_tets))
+        for _ in range(args.warmup):
+            m.step(w.dt, f_dev, pins)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, sweeps, broken = [], [], []
+        for _ in range(steps):
+            s = m.step(w.dt, f_dev, pins)
+            assert s["status"] == 0 and s["rel_res"] <= w.cg_rtol, s
+            its.append(s["cg_iters"])
+            sweeps.append(s["refine_sweeps"])
+            broken.append(s["n_broken"])
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / steps, its, sweeps, broken
+
+    ms, its, sweeps, broken = timed_loop()
     m.profile_reset()
     m.profile_enable(True)
     for _ in range(3):
         m.step(w.dt, f_dev, pins)
     m.profile_enable(False)
     prof = m.profile_get()
-    return {"ms_per_step": ms, "element_updates_per_s": w.n_tets / (ms * 1e-3),
-            "cg_iters_per_step": statistics.mean(its), "refine_sweeps_per_step": statistics.mean(sweeps),
-            "n_broken_timed": broken_summary(broken),
-            "kernels_ms_per_step": {k: v[0] / 3 for k, v in prof.items() if v[0] > 0},
-            "_prof": prof}
+    kernel_ms = sum(v[0] for v in prof.values()) / 3
+    first = None
+    if ms > 1.25 * kernel_ms + 0.2:
+        first = ms
+        ms, its, sweeps, broken = timed_loop()
+    out = {"ms_per_step": ms, "element_updates_per_s": w.n_tets / (ms * 1e-3),
+           "cg_iters_per_step": statistics.mean(its), "refine_sweeps_per_step": statistics.mean(sweeps),
+           "n_broken_timed": broken_summary(broken), "kernel_ms_per_step_profiled": kernel_ms}
+    if first is not None:
+        out["re_measured"] = {"first_ms_per_step": first,
+                              "why": "the first loop exceeded 1.25x the profiled kernel time per step: the GPU "
+                                     "sat idle between steps (host stalls)"}
+    out["kernels_ms_per_step"] = {k: v[0] / 3 for k, v in prof.items() if v[0] > 0}
+    out["_prof"] = prof
+    return out
 
 
 def run_glass(args, gf, torch, barrier, stream) -> dict:
