@@ -62,7 +62,7 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_tet_stress: case kB_tet_chi: case kB_tet_stress32: case kB_tet_chi32: case kB_chi_to32:
       return {cdiv(T, 256), 256};
     case kB_nonlocal: return {mt.radius > 0.0 ? cdiv(T, 256) : 0u, 256};
-    case kB_nonlocal32: return {mt.radius > 0.0 ? cdiv(T, kNlTile) : 0u, 256};
+    case kB_nonlocal32: return {mt.radius > 0.0 ? cdiv(T, m.mx.nl_tile) : 0u, 256};
     case kB_edge_driver: case kB_edge_driver32: return {cdiv(NE, 256), 256};
     case kB_node_init: return {cdiv(N, 256), 256};
     case kB_elem64: case kB_elem32: return {cdiv(T, 128), 128};
@@ -569,6 +569,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.nl_uptr, mxh.nl_uptr, int64_t);
     UP(d.mx.nl_uidx, mxh.nl_uidx, int32_t);
     d.mx.nl_cap = mxh.nl_cap;
+    d.mx.nl_tile = mxh.nl_tile;
     m->joint_entries = int64_t(mxh.nb_loc.size());
     m->union_rows = int64_t(mxh.nl_uidx.size());
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());

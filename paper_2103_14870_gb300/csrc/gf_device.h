@@ -47,9 +47,10 @@ struct MixDev {
   const int64_t* nb_ptr = nullptr;    // [ceil(T/2)+1] Eq. 20 joint lists of tet pairs (2q, 2q+1)
   const uint16_t* nb_loc = nullptr;   // per entry: the neighbour's position in its tile's union
   const float2* nb_w2 = nullptr;      // per entry: the FP32 weights of tets 2q and 2q+1 (0 if not a neighbour)
-  const int64_t* nl_uptr = nullptr;   // [ceil(T / kNlTile) + 1] tile unions
+  const int64_t* nl_uptr = nullptr;   // [ceil(T / nl_tile) + 1] tile unions
   const int32_t* nl_uidx = nullptr;   // union members (global tet ids, ascending per tile)
   int32_t nl_cap = 0;                 // rows a single-mesh launch stages (its shared memory: 24 B a row)
+  int32_t nl_tile = 128;              // tets per tile (128, or 64 for a wide radius)
   const float* mass32 = nullptr;      // [N]
   const float* mass_blk32 = nullptr;  // [NB] consistent mass per block slot (NULL: lumped)
   const double* X = nullptr;          // [3N] rest positions

@@ -50,10 +50,15 @@ struct NeighbourSell {            // Eq. 20 neighbour lists, 32 tets per group, 
 //   restB [T][12]: B = Dm^-1 row-major (9), pad
 enum Rest32Field : int { kRAE0 = 0, kRAH = 9, kRAV = 30, kRAStride = 32, kRBStride = 12 };
 
-// Tiles of the mixed Eq. 20 kernel: kNlTile consecutive tets share one CTA,
-// which stages the union of their neighbour sets (at most kNlCap rows) in
-// shared memory; each pair names its neighbour by its position in that union.
-constexpr int kNlTile = 128;
+// Tiles of the mixed Eq. 20 kernel: a tile of consecutive tets (kNlTile, or
+// kNlTileSmall for a wide radius, chosen per mesh) shares one CTA, which
+// stages the union of their neighbour sets (at most kNlCap rows in a batched
+// launch) in shared memory; each pair names its neighbour by its position in
+// that union.  The small tile is taken when kNlCtasWanted CTAs per SM with the
+// large tile's largest union would not fit the SM's shared memory.
+constexpr int kNlTile = 128, kNlTileSmall = 64;
+constexpr int kNlCtasWanted = 4;
+constexpr int64_t kNlSmemPerSm = 227 * 1024;
 constexpr int kNlCap = 1792;      // staged rows of a batched launch (one shared-memory size for all meshes)
 constexpr int kNlCapMax = 9216;   // staged rows of a single-mesh launch at most (216 KB)
 constexpr int64_t kNlMaxUnion = 65536;   // 16-bit positions
@@ -74,6 +79,7 @@ struct MixedHost {
   std::vector<int64_t> nl_uptr;
   std::vector<int32_t> nl_uidx;
   int32_t nl_cap = 0;               // rows a single-mesh launch stages: the largest union, at most kNlCapMax
+  int32_t nl_tile = kNlTile;        // tets per tile
 };
 
 

@@ -554,71 +554,81 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
         }
       }
     }
-    const int64_t NT = (T + kNlTile - 1) / kNlTile, NQ = (T + 1) / 2;
-    std::vector<std::vector<int32_t>> U(NT);
-    std::vector<std::vector<JointEntry>> J(NQ);
-    std::atomic<int64_t> too_big{-1};
-    parallel_for(NT, [&](int64_t b, int64_t e) {
-      for (int64_t g = b; g < e; ++g) {
-        const int64_t t0 = kNlTile * g, t1 = std::min(T, kNlTile * (g + 1));
-        std::vector<int32_t>& u = U[g];
-        u.assign(nb_id.begin() + tp[t0], nb_id.begin() + tp[t1]);
-        std::sort(u.begin(), u.end());
-        u.erase(std::unique(u.begin(), u.end()), u.end());
-        if (int64_t(u.size()) > kNlMaxUnion) {
-          too_big = g;
-          continue;
-        }
-        auto pos = [&](int32_t j) { return uint16_t(std::lower_bound(u.begin(), u.end(), j) - u.begin()); };
-        for (int64_t a = t0; a < t1; a += 2) {   // merge the two sorted lists
-          std::vector<JointEntry>& jq = J[a / 2];
-          int64_t p = tp[a], pe = tp[a + 1], r = a + 1 < T ? tp[a + 1] : 0, re = a + 1 < T ? tp[a + 2] : 0;
-          while (p < pe || r < re) {
-            JointEntry x{};
-            if (r >= re || (p < pe && nb_id[p] < nb_id[r])) {
-              x = {pos(nb_id[p]), {nb_w[p], 0.f}};
-              ++p;
-            } else if (p >= pe || nb_id[r] < nb_id[p]) {
-              x = {pos(nb_id[r]), {0.f, nb_w[r]}};
-              ++r;
-            } else {
-              x = {pos(nb_id[p]), {nb_w[p], nb_w[r]}};
-              ++p;
-              ++r;
-            }
-            jq.push_back(x);
+    // Tiles of kNlTile tets, or of kNlTileSmall where the largest union of the
+    // large tile leaves fewer than kNlCtasWanted CTAs per SM room in shared
+    // memory (a wide radius): smaller unions let more CTAs hide the list latency
+    auto build_tiles = [&](int tile) -> gf_status {
+      const int64_t NT = (T + tile - 1) / tile, NQ = (T + 1) / 2;
+      std::vector<std::vector<int32_t>> U(NT);
+      std::vector<std::vector<JointEntry>> J(NQ);
+      std::atomic<int64_t> too_big{-1};
+      parallel_for(NT, [&](int64_t b, int64_t e) {
+        for (int64_t g = b; g < e; ++g) {
+          const int64_t t0 = tile * g, t1 = std::min(T, tile * (g + 1));
+          std::vector<int32_t>& u = U[g];
+          u.assign(nb_id.begin() + tp[t0], nb_id.begin() + tp[t1]);
+          std::sort(u.begin(), u.end());
+          u.erase(std::unique(u.begin(), u.end()), u.end());
+          if (int64_t(u.size()) > kNlMaxUnion) {
+            too_big = g;
+            continue;
           }
-          deal_entries(jq, a / 2);
+          auto pos = [&](int32_t j) { return uint16_t(std::lower_bound(u.begin(), u.end(), j) - u.begin()); };
+          for (int64_t a = t0; a < t1; a += 2) {   // merge the two sorted lists
+            std::vector<JointEntry>& jq = J[a / 2];
+            int64_t p = tp[a], pe = tp[a + 1], r = a + 1 < T ? tp[a + 1] : 0, re = a + 1 < T ? tp[a + 2] : 0;
+            while (p < pe || r < re) {
+              JointEntry x{};
+              if (r >= re || (p < pe && nb_id[p] < nb_id[r])) {
+                x = {pos(nb_id[p]), {nb_w[p], 0.f}};
+                ++p;
+              } else if (p >= pe || nb_id[r] < nb_id[p]) {
+                x = {pos(nb_id[r]), {0.f, nb_w[r]}};
+                ++r;
+              } else {
+                x = {pos(nb_id[p]), {nb_w[p], nb_w[r]}};
+                ++p;
+                ++r;
+              }
+              jq.push_back(x);
+            }
+            deal_entries(jq, a / 2);
+          }
         }
+      });
+      if (too_big >= 0) {
+        err = "Eq. 20 neighbour sets too large for the mixed-precision path (a tile of " + std::to_string(tile) +
+              " tets reaches more than " + std::to_string(kNlMaxUnion) + " tets; reduce the radius)";
+        return GF_UNSUPPORTED;
       }
-    });
-    if (too_big >= 0) {
-      err = "Eq. 20 neighbour sets too large for the mixed-precision path (a tile of " + std::to_string(kNlTile) +
-            " tets reaches more than " + std::to_string(kNlMaxUnion) + " tets; reduce the radius)";
-      return GF_UNSUPPORTED;
-    }
-    mx.nl_uptr.assign(NT + 1, 0);
-    int64_t largest = 0;
-    for (int64_t g = 0; g < NT; ++g) {
-      mx.nl_uptr[g + 1] = mx.nl_uptr[g] + int64_t(U[g].size());
-      largest = std::max<int64_t>(largest, int64_t(U[g].size()));
-    }
-    mx.nl_cap = int32_t(std::min<int64_t>(largest, kNlCapMax));
-    mx.nl_uidx.resize(mx.nl_uptr[NT]);
-    for (int64_t g = 0; g < NT; ++g) std::copy(U[g].begin(), U[g].end(), mx.nl_uidx.begin() + mx.nl_uptr[g]);
-    mx.nb_ptr.assign(NQ + 1, 0);
-    for (int64_t q = 0; q < NQ; ++q) mx.nb_ptr[q + 1] = mx.nb_ptr[q] + int64_t(J[q].size());
-    mx.nb_loc.resize(mx.nb_ptr[NQ]);
-    mx.nb_w2.resize(2 * mx.nb_ptr[NQ]);
-    parallel_for(NQ, [&](int64_t b, int64_t e) {
-      for (int64_t q = b; q < e; ++q)
-        for (size_t k = 0; k < J[q].size(); ++k) {
-          const int64_t o = mx.nb_ptr[q] + int64_t(k);
-          mx.nb_loc[o] = J[q][k].loc;
-          mx.nb_w2[2 * o] = J[q][k].w[0];
-          mx.nb_w2[2 * o + 1] = J[q][k].w[1];
-        }
-    });
+      mx.nl_tile = tile;
+      mx.nl_uptr.assign(NT + 1, 0);
+      int64_t largest = 0;
+      for (int64_t g = 0; g < NT; ++g) {
+        mx.nl_uptr[g + 1] = mx.nl_uptr[g] + int64_t(U[g].size());
+        largest = std::max<int64_t>(largest, int64_t(U[g].size()));
+      }
+      mx.nl_cap = int32_t(std::min<int64_t>(largest, kNlCapMax));
+      mx.nl_uidx.resize(mx.nl_uptr[NT]);
+      for (int64_t g = 0; g < NT; ++g) std::copy(U[g].begin(), U[g].end(), mx.nl_uidx.begin() + mx.nl_uptr[g]);
+      mx.nb_ptr.assign(NQ + 1, 0);
+      for (int64_t q = 0; q < NQ; ++q) mx.nb_ptr[q + 1] = mx.nb_ptr[q] + int64_t(J[q].size());
+      mx.nb_loc.resize(mx.nb_ptr[NQ]);
+      mx.nb_w2.resize(2 * mx.nb_ptr[NQ]);
+      parallel_for(NQ, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q)
+          for (size_t k = 0; k < J[q].size(); ++k) {
+            const int64_t o = mx.nb_ptr[q] + int64_t(k);
+            mx.nb_loc[o] = J[q][k].loc;
+            mx.nb_w2[2 * o] = J[q][k].w[0];
+            mx.nb_w2[2 * o + 1] = J[q][k].w[1];
+          }
+      });
+      return GF_OK;
+    };
+    gf_status st = build_tiles(kNlTile);
+    if (st == GF_OK && int64_t(mx.nl_cap) * 24 * kNlCtasWanted > kNlSmemPerSm) st = build_tiles(kNlTileSmall);
+    if (st != GF_OK) return st;
   }
   return GF_OK;
 }

@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
   tet_stress32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
-// Eq. 20 sum in FP32, tiled.  A CTA takes kNlTile consecutive tets and first
+// Eq. 20 sum in FP32, tiled.  A CTA takes a tile of consecutive tets (128, or
+// 64 where the radius makes the unions wide: the mesh's nl_tile) and first
 // stages the union of their neighbour sets (ascending tet ids, six floats a
 // row) in shared memory; a tile whose union exceeds the staged capacity reads
 // the rows from global memory instead.  A single-mesh launch stages as many
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
 // 32-byte output rows.  The host orders each list so that the eight entries a
 // pair reads at once fall on distinct shared-memory bank pairs, and the two
 // pairs of a half-warp on opposite halves of the banks.
-constexpr int kNlThreads = 256, kNlWarpPairs = kNlTile / 2 / (kNlThreads / 32);
+constexpr int kNlThreads = 256;
 constexpr unsigned kNlSmem = kNlCap * 24;           // batched launches
 constexpr unsigned kNlSmemMax = kNlCapMax * 24;     // single-mesh launches at most
 constexpr int kNlBatch = 6;   // entries of a lane in flight per load batch
@@ -261,7 +262,8 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
   extern __shared__ float2 su[];   // [cap][3]: stress rows of the tile's union
   constexpr int kStage = 8;        // union rows of a thread in flight together
   const MixDev& x = m.mx;
-  const int64_t t0 = int64_t(bid) * kNlTile;
+  const int64_t t0 = int64_t(bid) * x.nl_tile;
+  const int warp_pairs = x.nl_tile / 2 / (kNlThreads / 32);   // tet pairs of a warp: 8 (128-tet tiles) or 4
   const int64_t u0 = x.nl_uptr[bid], un = x.nl_uptr[bid + 1] - u0;
   const bool staged = un <= cap;
   if (staged) {   // a thread's union ids, then their rows, kStage at a time in flight together
@@ -289,9 +291,9 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
   const unsigned gmask = 0xffu << (lane & 24);
   // this warp's pairs: q in [qw, qw + np) (pair q = tets 2q, 2q+1), four at a time
   const int64_t NQ = (m.T + 1) / 2;
-  const int64_t qw = t0 / 2 + int64_t(kNlWarpPairs) * (threadIdx.x >> 5);
+  const int64_t qw = t0 / 2 + int64_t(warp_pairs) * (threadIdx.x >> 5);
   if (qw >= NQ) return;
-  const int np = int(NQ - qw < kNlWarpPairs ? NQ - qw : kNlWarpPairs);
+  const int np = int(NQ - qw < warp_pairs ? NQ - qw : warp_pairs);
   for (int r0 = 0; r0 < np; r0 += 4) {
     const int64_t q = qw + r0 + g;
     const bool live = r0 + g < np;
