@@ -674,6 +674,7 @@ gf_status gf_mesh_plan(const double* nodes, int64_t n_nodes, const int32_t* tets
   info->n_nbr_pairs = hm.nbr.pairs;
   info->n_joint_entries = 0;
   info->n_union_rows = 0;
+  info->eq20_tile = 0;
   const int64_t N = hm.n_nodes, T = hm.n_tets;
   info->device_bytes = int64_t(hm.tets.size() * 4 + hm.tet_edges.size() * 4 + hm.slot.size() * 4 +
                                hm.rest.size() * 8 + hm.row_ptr.size() * 4 + hm.col.size() * 4 +
@@ -720,6 +721,7 @@ gf_status gf_mesh_info_get(const gf_mesh* m, gf_mesh_info* info) {
   info->device_bytes = m->bytes;
   info->n_joint_entries = m->joint_entries;
   info->n_union_rows = m->union_rows;
+  info->eq20_tile = m->mixed && m->mt.radius > 0.0 ? m->dm.mx.nl_tile : 0;
   return GF_OK;
 }
 

@@ -80,7 +80,8 @@ class BatchTuning(ctypes.Structure):
 
 class MeshInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_nodes", "n_tets", "n_edges", "n_blocks", "n_colours",
-                                              "n_nbr_pairs", "device_bytes", "n_joint_entries", "n_union_rows")]
+                                              "n_nbr_pairs", "device_bytes", "n_joint_entries", "n_union_rows",
+                                              "eq20_tile")]
 
 
 _LIB = None

@@ -129,14 +129,17 @@ def test_mixed_resume_bit_identical_and_rest():
     np.testing.assert_array_equal(b.positions_get(), d.positions_get())
 
 
-@pytest.mark.parametrize("dims,radius", [((3, 3, 7), 1.5), ((6, 6, 12), 3.0)], ids=["ragged-tile", "large-unions"])
+@pytest.mark.parametrize("dims,radius", [((3, 3, 7), 1.5), ((6, 6, 12), 3.0), ((8, 8, 12), 3.0)],
+                         ids=["ragged-tile", "large-unions", "wide-radius"])
 def test_mixed_nonlocal_tiles(dims, radius):
-    """The tiled Eq. 20 kernel (128 tets per CTA, neighbour union staged in
-    shared memory) on a mesh whose last tile is partial (378 tets) and on one
-    whose tile unions exceed 1,792 rows (R_d = 3 on 2,592 tets), against the
-    oracle.  A single-mesh launch stages the mesh's largest union; a batched
-    launch stages 1,792 rows, so in a batch those tiles read global memory:
-    the batch member must give the single-mesh drivers bit for bit."""
+    """The tiled Eq. 20 kernel (a tile of tets per CTA, neighbour union staged in
+    shared memory) on a mesh whose last tile is partial (378 tets), on one whose
+    tile unions exceed 1,792 rows (R_d = 3 on 2,592 tets), and on one whose
+    128-tet unions are too wide for four CTAs per SM (R_d = 3 on 4,608 tets), so
+    the mesh takes 64-tet tiles; against the oracle.  A single-mesh launch
+    stages the mesh's largest union; a batched launch stages 1,792 rows, so in a
+    batch the large tiles read global memory: the batch member must give the
+    single-mesh drivers bit for bit."""
     from oracle import mesh as omesh
     from workloads import Workload
     from workloads.meshes import jitter, kuhn_box
@@ -154,12 +157,17 @@ def test_mixed_nonlocal_tiles(dims, radius):
         assert T % 128 != 0
     else:
         assert max(unions) > 1792   # these tiles take the global-memory path
+    # the tile rule: 64 tets where four CTAs with the largest 128-tet union
+    # (24 B a row) would not fit 227 KB of shared memory
+    tile = 64 if max(unions) * 24 * 4 > 227 * 1024 else 128
+    assert tile == (64 if dims == (8, 8, 12) else 128)
     model0 = oracle_model(w, threshold=math.inf, radius=radius)
     st = deformed_state(w, seed=31)
     d0, _, _, _ = model0.damage_update(st)
     theta = float(np.quantile(d0, 0.95))
     model = oracle_model(w, threshold=theta, radius=radius)
     m = mixed_mesh(w, gpu_material(gf, w, threshold=theta, radius=radius))
+    assert m.info["eq20_tile"] == tile
     m.state_set(x=st.x.ravel(), v=st.v.ravel(), labels=st.labels, chi=st.chi)
     s = m.step(w.dt, w.f_ext.ravel(), w.pinned)
     assert s["status"] == 0
