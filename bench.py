@@ -530,9 +530,11 @@ def run_glass(args, gf, torch, barrier, stream) -> dict:
         err_drv.append(float(np.abs(d32[fin] - d64[fin]).max() / max(np.abs(d64[fin]).max(), 1e-300)))
         lab_diff.append(int((l32 != l64).sum()))
         broken.append(s64["n_broken"])
+    autotune = {"fp64": tuned_schedule(gf, m64, w.dt, f_dev, pins), "mixed": tuned_schedule(gf, mm, w.dt, f_dev, pins)}
     m64.close()
     mm.close()
-    return {"workload": "loaf_bcc_620k_glass: the loaf mesh, E=7e10, nu=0.22, rho=2500, 1e4 N point impact at the "
+    return {"autotune": autotune,
+            "workload": "loaf_bcc_620k_glass: the loaf mesh, E=7e10, nu=0.22, rho=2500, 1e4 N point impact at the "
                         "top apex, lowest 5% of nodes pinned, dt=5e-4, R_d=1.5, CG rtol 1e-6",
             "threshold": theta,
             "threshold_rule": "(1 - 1e-3) quantile of the FP64 step-10 drivers from rest, 3 significant figures",
@@ -771,6 +773,8 @@ def run_ours(args) -> None:
         m.positions_get(out=x_host)
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    autotune = {"loaf_fp64": tuned_schedule(gf, m, w.dt, f_dev, None)}
+    m.tuning_set(assembly=gf.ASSEMBLY_GATHER, step_launch=gf.STEP_GRAPH, solve_loop=gf.SOLVE_KERNELS)
     ext = run_extensions(args, gf, torch, barrier, stream, w, f_dev, m) if not args.no_extensions else None
     m.close()
     # mixed-precision form on the same workload and tolerance
@@ -787,6 +791,7 @@ def run_ours(args) -> None:
     mm.state_set(x=w.nodes.ravel(), v=np.zeros(w.nodes.size), labels=np.zeros(mm.n_edges, np.uint8),
                  chi=np.ones(mm.n_tets))
     mix_k3_ms = timed(mm, min(args.steps, 50))[0]
+    autotune["loaf_mixed"] = tuned_schedule(gf, mm, w.dt, f_dev, None)
     mm.close()
     glass = run_glass(args, gf, torch, barrier, stream) if not args.no_glass else None
     survey_c2 = run_survey_c2(args, gf, torch, barrier, stream) if not args.no_c2 else None
@@ -833,6 +838,7 @@ def run_ours(args) -> None:
                   "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mix_prof.items()},
                   "roofline": mix_roof},
         "mixed_glass": glass,
+        "autotune": autotune,
         "survey_c2": survey_c2,
         "batch": batch,
         "learned": learned,
@@ -846,6 +852,16 @@ def run_ours(args) -> None:
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def tuned_schedule(gf, m, dt, f_dev, pins) -> dict:
+    """gf_mesh_autotune from the mesh's current state (restored afterwards): the
+    schedule it picks and its time per step over 5 trial steps."""
+    forms = {gf.SOLVE_KERNELS: "three-kernel PCG", gf.SOLVE_CG: "two-kernel PCG", gf.SOLVE_NESTED: "nested",
+             gf.SOLVE_PERSISTENT: "persistent"}
+    best, ms = m.autotune(dt, f_dev, pins, trial_steps=5)
+    return {"solve_loop": forms.get(best["solve_loop"], best["solve_loop"]),
+            "assembly": "colour" if best["assembly"] == gf.ASSEMBLY_COLOUR else "gather", "ms_per_step": ms}
 
 
 def summary_scalars(out: dict) -> dict:
@@ -875,6 +891,11 @@ def summary_scalars(out: dict) -> dict:
         "quasistatic_fp64_ms_per_load_step": get("extensions", "quasistatic_pull_fp64", "ms_per_load_step"),
         "quasistatic_nested_ms_per_load_step": get("extensions", "quasistatic_pull_nested_fp32_inner",
                                                    "ms_per_load_step"),
+        "autotune_loaf_fp64_solve": get("autotune", "loaf_fp64", "solve_loop"),
+        "autotune_loaf_mixed_solve": get("autotune", "loaf_mixed", "solve_loop"),
+        "autotune_glass_fp64_solve": get("mixed_glass", "autotune", "fp64", "solve_loop"),
+        "autotune_glass_fp64_ms_per_step": get("mixed_glass", "autotune", "fp64", "ms_per_step"),
+        "autotune_glass_mixed_solve": get("mixed_glass", "autotune", "mixed", "solve_loop"),
     }
 
 

@@ -225,6 +225,19 @@ typedef struct gf_tuning {
 gf_status gf_tuning_set(gf_mesh* mesh, const gf_tuning* tuning);
 gf_status gf_tuning_get(const gf_mesh* mesh, gf_tuning* tuning);
 
+/* Autotuner of one mesh: times `trial_steps` steps (1..64) under each candidate
+ * schedule on the mesh's current state, restoring the state (positions,
+ * velocities, labels, chi and the FP32 copies) after each, and keeps the
+ * fastest.  Candidates: GF_FP64: the two-phase gather and, for the StVK
+ * energy, the colour-ordered assembly, each with the solver-loop forms
+ * GF_SOLVE_KERNELS, GF_SOLVE_CG and GF_SOLVE_NESTED; GF_MIXED: GF_SOLVE_CG,
+ * GF_SOLVE_KERNELS and GF_SOLVE_PERSISTENT; graph launches where the form has
+ * them.  Inputs as in gf_step.  best (nullable) receives the chosen tuning, ms
+ * (nullable) its time per step.  GF_UNSUPPORTED while a network is attached or
+ * with Newton iterations > 1 (their steps carry state between iterations). */
+gf_status gf_mesh_autotune(gf_mesh* mesh, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
+                           const double* pinned_vel, int32_t mem, int32_t trial_steps, gf_tuning* best, double* ms);
+
 /* GF_MIXED: relative tolerance of each inner FP32 PCG solve of the FP64
  * iterative refinement (default 1e-5; 0 < inner_rtol < 1; each inner solve also
  * stops after 32 iterations).  The outer FP64 tolerance stays cg_rtol.  At the
@@ -448,10 +461,11 @@ gf_status gf_batch_tuning_get(const gf_batch* batch, gf_batch_tuning* tuning);
 
 /* Autotuner: times `trial_steps` batch steps under each candidate schedule
  * (graph replay vs stream launches with several host-check intervals, with
- * the single-mesh grids and with grid budgets of 1, 2 and 4 waves) on a
- * copy of the current state, restores the state, keeps the fastest schedule
- * and returns it in *best (may be NULL) and its time per step in *ms (may be
- * NULL).  Inputs as in gf_batch_step. */
+ * the single-mesh grids and with grid budgets of 1, 2 and 4 waves; the
+ * persistent, distributed and two-kernel solver-loop forms; 2 to 16 inner
+ * iterations per loop pass) on a copy of the current state, restores the
+ * state, keeps the fastest schedule and returns it in *best (may be NULL) and
+ * its time per step in *ms (may be NULL).  Inputs as in gf_batch_step. */
 gf_status gf_batch_autotune(gf_batch* batch, double dt, const double* const* f_ext, const int32_t* const* pinned,
                             const int64_t* n_pinned, const double* const* pinned_vel, int32_t mem,
                             int32_t trial_steps, gf_batch_tuning* best, double* ms);

@@ -795,6 +795,104 @@ gf_status gf_tuning_get(const gf_mesh* m, gf_tuning* t) {
   return GF_OK;
 }
 
+gf_status gf_mesh_autotune(gf_mesh* m, double dt, const double* f_ext, const int32_t* pinned, int64_t n_pinned,
+                           const double* pinned_vel, int32_t mem, int32_t trial_steps, gf_tuning* best, double* best_ms) {
+  if (!m || trial_steps < 1 || trial_steps > 64) {
+    set_last_error("autotune: need a mesh and 1 <= trial_steps <= 64");
+    return GF_BAD_ARG;
+  }
+  if (m->gnn || m->newton_iters > 1) {
+    set_last_error("autotune: not with a network attached or Newton iterations > 1");
+    return GF_UNSUPPORTED;
+  }
+  DeviceGuard guard(m->device);
+  cudaStream_t s = m->stream;
+  const DevMesh& d = m->dm;
+  // the state a step reads and writes, saved on the device and put back after each trial
+  struct Saved {
+    void* p;
+    void* dst;
+    size_t bytes;
+  };
+  std::vector<Saved> saved;
+  gf_status st = GF_OK;
+  auto keep = [&](void* src, size_t bytes) {
+    if (st != GF_OK || bytes == 0) return;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      set_last_error("autotune: cannot save the state");
+      st = GF_OOM;
+      return;
+    }
+    saved.push_back({p, src, bytes});
+    if (cudaMemcpyAsync(p, src, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) st = GF_CUDA_ERR;
+  };
+  keep(d.x, sizeof(double) * 3 * d.N);
+  keep(d.v, sizeof(double) * 3 * d.N);
+  keep(d.labels, size_t(d.NE));
+  keep(d.chi, sizeof(double) * d.T);
+  if (m->mixed) {
+    keep(d.mx.u32, sizeof(float) * 3 * d.N);
+    keep(d.mx.v32, sizeof(float) * 3 * d.N);
+    keep(d.mx.chi32, sizeof(float) * d.T);
+  }
+  auto restore = [&]() {
+    for (auto& sv : saved) cudaMemcpyAsync(sv.dst, sv.p, sv.bytes, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+  };
+  const gf_tuning orig = m->tune;
+  std::vector<gf_tuning> cands;
+  auto cand = [&](int assembly, int form) {
+    gf_tuning t = orig;
+    t.assembly = assembly;
+    t.solve_loop = form;
+    t.step_launch = GF_STEP_GRAPH;
+    t.wait_test = 0;
+    cands.push_back(t);
+  };
+  if (m->mixed) {
+    for (int form : {GF_SOLVE_CG, GF_SOLVE_KERNELS, GF_SOLVE_PERSISTENT}) cand(GF_ASSEMBLY_GATHER, form);
+  } else {
+    for (int form : {GF_SOLVE_KERNELS, GF_SOLVE_CG, GF_SOLVE_NESTED}) {
+      cand(GF_ASSEMBLY_GATHER, form);
+      if (m->mat.energy != GF_ENERGY_SNH) cand(GF_ASSEMBLY_COLOUR, form);
+    }
+  }
+  double best_t = 1e300;
+  gf_tuning best_c = orig;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (size_t ci = 0; ci < cands.size() && st == GF_OK; ++ci) {
+    if ((st = gf_tuning_set(m, &cands[ci])) != GF_OK) break;
+    // one untimed step (graph capture, first-use allocations), then the timed trial
+    st = gf_step(m, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
+    restore();
+    if (st != GF_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < trial_steps && st == GF_OK; ++r)
+      st = gf_step(m, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    restore();
+    if (st == GF_OK && ms / trial_steps < best_t) {
+      best_t = ms / trial_steps;
+      best_c = cands[ci];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto& sv : saved) cudaFree(sv.p);
+  const gf_tuning keep_t = st == GF_OK ? best_c : orig;
+  gf_status st2 = gf_tuning_set(m, &keep_t);
+  if (st == GF_OK) st = st2;
+  if (best) *best = m->tune;
+  if (best_ms) *best_ms = best_t;
+  return st;
+}
+
 gf_status gf_refine_set(gf_mesh* m, double inner_rtol) {
   if (!m || !(inner_rtol > 0) || !(inner_rtol < 1)) {
     set_last_error("need 0 < inner_rtol < 1");

@@ -118,6 +118,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "gf_threshold_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_refine_set": (ctypes.c_int, [P, ctypes.c_double]),
         "gf_quasistatic_solver_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
+        "gf_mesh_autotune": (ctypes.c_int, [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32,
+                                            P, P]),
         "gf_newton_set": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_double]),
         "gf_surface_sizes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64)]),
@@ -281,6 +283,20 @@ class Mesh:
             self._log_steps += 1
         _check(status)
         return st.as_dict()
+
+    def autotune(self, dt: float, f_ext=None, pinned=None, pinned_vel=None, trial_steps: int = 3):
+        """gf_mesh_autotune: times the candidate schedules on the current state (restored after
+        each) and keeps the fastest; returns (tuning dict, ms per step)."""
+        pf, kf, kf_ = _arg(f_ext, np.float64, 3 * self.n_nodes, "f_ext")
+        n_pin = 0 if pinned is None else int(np.prod(pinned.shape)) if hasattr(pinned, "shape") else len(pinned)
+        pp, kp, kp_ = _arg(pinned, np.int32, n_pin, "pinned") if n_pin else (None, None, None)
+        pq, kq, kq_ = _arg(pinned_vel, np.float64, 3 * n_pin, "pinned_vel") if n_pin else (None, None, None)
+        best = Tuning()
+        ms = ctypes.c_double(0.0)
+        _check(load_library().gf_mesh_autotune(self._h, float(dt), pf, pp, n_pin, pq, _one_kind(kf, kp, kq),
+                                               int(trial_steps), ctypes.byref(best), ctypes.byref(ms)))
+        return {"assembly": best.assembly, "step_launch": best.step_launch, "solve_loop": best.solve_loop,
+                "wait_test": best.wait_test}, ms.value
 
     def quasistatic_step(self, f_ext=None, pinned=None, pinned_pos=None, max_newton: int = 50,
                          rtol: float = 1e-10) -> dict:
