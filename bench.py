@@ -105,11 +105,13 @@ NCU_TRAFFIC = {
     # k_elem64; k_gather64 + k_diag64
     "assemble": 184.756992e6 + 293.543424e6,
     "assemble_gather": (371.265536e6 + 107.799296e6) + (117.729792e6 + 1.789440e6),
-    # k_nonlocal32 (eight lanes per tet pair); k_elem32; k_gather32 + k_diag32
-    "m:nonlocal_avg": 662.230528e6 + 19.512576e6,
+    # k_nonlocal32 (eight lanes per tet pair, 128-tet tiles); k_elem32; k_gather32 + k_diag32
+    "m:nonlocal_avg": 662.691072e6 + 22.824960e6,
     "m:assemble": 127.145472e6 + 118.654464e6,
     "m:assemble_gather": (191.035136e6 + 42.632448e6) + (59.089408e6 + 0.0),
 }
+# The loaf at R_d = 2 h: k_nonlocal32 with 64-tet tiles (ncu, one launch)
+NCU_TRAFFIC_2H = {"m:nonlocal_avg": 1450.647552e6 + 31.854848e6}
 # Executed FP64 flops per tet of the element-block kernel, off-diagonal blocks
 # and rhs shares only (ncu: 2 DFMA + DADD + DMUL thread instructions per launch /
 # tets = (2 x 264.4 M + 53.3 M + 40.9 M) / 619,300): the tangent has no short
@@ -587,7 +589,8 @@ def run_survey_c2(args, gf, torch, barrier, stream) -> dict:
         prof = out[form].pop("_prof")
         cands = ("tet_stress", "nonlocal_avg", "edge_driver", "assemble", "assemble_gather", "pcg_spmv")
         dom = max(cands, key=lambda k: prof[k][0])
-        out[form]["roofline"] = roofline_for(pre + dom, prof[dom][0], prof[dom][1], inf, pk, None)
+        out[form]["roofline"] = roofline_for(pre + dom, prof[dom][0], prof[dom][1], inf, pk,
+                                             NCU_TRAFFIC_2H.get(pre + dom))
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     return out
 
@@ -934,6 +937,8 @@ def run_profile_step(args) -> None:
         w = glass_config()
     else:
         w = loaf_config()
+        if args.workload == "loaf2h":   # the loaf at R_d = 2 h (the radius sets the Eq. 20 work, not the threshold)
+            w.radius = 2.0
     mat = gf.material(w.young, w.poisson, w.density, threshold=w.threshold, radius=w.radius,
                       energy=gf.ENERGY_SNH if args.precision == "snh" else gf.ENERGY_STVK)
     m = gf.mesh_create(w.nodes, w.tets, mat, cg_rtol=w.cg_rtol,
@@ -1005,8 +1010,9 @@ def main():
     ap.add_argument("--profile-step", action="store_true", help="ncu target: mesh + --steps steps, no timing")
     ap.add_argument("--precision", choices=["fp64", "mixed", "learned", "snh", "qs", "surface", "batch"], default="fp64",
                     help="form run by --profile-step (see run_profile_step)")
-    ap.add_argument("--workload", choices=["loaf", "glass"], default="loaf",
-                    help="--profile-step workload: the loaf or the glass point impact on the loaf mesh")
+    ap.add_argument("--workload", choices=["loaf", "loaf2h", "glass"], default="loaf",
+                    help="--profile-step workload: the loaf (at R_d = 1.5 h, or 2 h) or the glass point impact "
+                         "on the loaf mesh")
     ap.add_argument("--solve", choices=["default", "kernels", "cg", "persistent", "nested"], default="default",
                     help="--profile-step solver-loop form (gf_tuning.solve_loop; default: the mesh's own)")
     ap.add_argument("--qs-solver", choices=["fp64", "nested"], default="fp64",
