@@ -1,5 +1,6 @@
 // C ABI of the graph-FEM fracture step: mesh lifetime, state, one implicit step.
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -392,6 +393,24 @@ gf_status recompute_chi(gf_mesh* m) {
   }
   GF_CK(cudaGetLastError());
   return GF_OK;
+}
+
+// The autotuners' choice: every candidate timed once, then the three fastest
+// timed again, each kept at the lower of its two times (a host stall only ever
+// lengthens a trial), and the fastest of those.  Stops at the first failing
+// trial (status in st).  Returns the index (n if none) and its ms per step.
+template <typename Trial>
+std::pair<size_t, double> pick_fastest(size_t n, Trial&& trial, gf_status& st) {
+  std::vector<double> t(n, 1e300);
+  for (size_t i = 0; i < n && st == GF_OK; ++i) t[i] = trial(i);
+  if (st != GF_OK || n == 0) return {n, 1e300};
+  std::vector<size_t> order(n);
+  for (size_t i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return t[a] < t[b]; });
+  for (size_t k = 0; k < std::min<size_t>(3, n) && st == GF_OK; ++k) t[order[k]] = std::min(t[order[k]], trial(order[k]));
+  if (st != GF_OK) return {n, 1e300};
+  const size_t best = size_t(std::min_element(t.begin(), t.end()) - t.begin());
+  return {best, t[best]};
 }
 
 }  // namespace
@@ -858,17 +877,16 @@ gf_status gf_mesh_autotune(gf_mesh* m, double dt, const double* f_ext, const int
       if (m->mat.energy != GF_ENERGY_SNH) cand(GF_ASSEMBLY_COLOUR, form);
     }
   }
-  double best_t = 1e300;
-  gf_tuning best_c = orig;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (size_t ci = 0; ci < cands.size() && st == GF_OK; ++ci) {
-    if ((st = gf_tuning_set(m, &cands[ci])) != GF_OK) break;
-    // one untimed step (graph capture, first-use allocations), then the timed trial
+  // ms per step of candidate ci: one untimed step (graph capture, first-use
+  // allocations), then the timed trial; the state is put back after each
+  auto trial = [&](size_t ci) -> double {
+    if ((st = gf_tuning_set(m, &cands[ci])) != GF_OK) return 1e300;
     st = gf_step(m, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
     restore();
-    if (st != GF_OK) break;
+    if (st != GF_OK) return 1e300;
     cudaEventRecord(e0, s);
     for (int r = 0; r < trial_steps && st == GF_OK; ++r)
       st = gf_step(m, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
@@ -877,11 +895,11 @@ gf_status gf_mesh_autotune(gf_mesh* m, double dt, const double* f_ext, const int
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     restore();
-    if (st == GF_OK && ms / trial_steps < best_t) {
-      best_t = ms / trial_steps;
-      best_c = cands[ci];
-    }
-  }
+    return st == GF_OK ? double(ms) / trial_steps : 1e300;
+  };
+  const std::pair<size_t, double> pick = pick_fastest(cands.size(), trial, st);
+  const gf_tuning best_c = pick.first < cands.size() ? cands[pick.first] : orig;
+  const double best_t = pick.second;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (auto& sv : saved) cudaFree(sv.p);
@@ -2830,17 +2848,16 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
       cands.push_back(t);
     }
   }
-  double best_t = 1e300;
-  gf_batch_tuning best_c = orig;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (size_t ci = 0; ci < cands.size() && st == GF_OK; ++ci) {
+  // ms per step of candidate ci: one untimed step (graph build, caches), then
+  // the timed trial; the state is put back after each
+  auto trial = [&](size_t ci) -> double {
     b->tune = cands[ci];
-    // one untimed step (graph build, caches), then the timed trial
     st = gf_batch_step(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
     restore();
-    if (st != GF_OK) break;
+    if (st != GF_OK) return 1e300;
     cudaEventRecord(e0, s);
     for (int r = 0; r < trial_steps && st == GF_OK; ++r)
       st = gf_batch_step(b, dt, f_ext, pinned, n_pinned, pinned_vel, mem, nullptr);
@@ -2849,11 +2866,11 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     restore();
-    if (st == GF_OK && ms / trial_steps < best_t) {
-      best_t = ms / trial_steps;
-      best_c = cands[ci];
-    }
-  }
+    return st == GF_OK ? double(ms) / trial_steps : 1e300;
+  };
+  const std::pair<size_t, double> pick = pick_fastest(cands.size(), trial, st);
+  const gf_batch_tuning best_c = pick.first < cands.size() ? cands[pick.first] : orig;
+  const double best_t = pick.second;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (auto& sv : saved) cudaFree(sv.p);
