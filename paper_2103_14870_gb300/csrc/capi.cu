@@ -76,7 +76,6 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_pcg_init: case kB_pcg_spmv: case kB_pcg_update: case kB_true_residual: return {red_grid(N), 256};
     case kB_pcg_p: return {red_grid(3 * N), 256};
     case kB_integrate: case kB_integrate32: case kB_refresh32: return {cdiv(3 * N, 256), 256};
-    case kB_fext32: return {sp.has_fext ? cdiv(3 * N, 256) : 0u, 256};
     case kB_ir_residual: return {ir_grid(8 * N, 5), 256};
     case kB_ir_spmv: case kB_ir_cg_spmv: return {ir_grid(16 * N, 6), 256};
     case kB_ir_inner_init: case kB_ir_update: case kB_ir_cg_update: return {ir_grid(N), 256};
@@ -626,7 +625,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
         (st = scratch(m, 8 * T, &x.sig_in32)) || (st = scratch(m, 8 * T, &x.sig_bar32)) ||
         (st = scratch(m, 9 * NB, &x.val32)) ||
         (st = scratch(m, 70 * T, &x.ebuf)) || (st = scratch(m, 3 * N, &x.rhs32)) ||
-        (st = scratch(m, 3 * N, &x.rres)) || (st = scratch(m, 3 * N, &x.fext32)) ||
+        (st = scratch(m, 3 * N, &x.rres)) ||
         (st = scratch(m, 9 * N, &x.pinv32)) || (st = scratch(m, 3 * N, &x.r32)) || (st = scratch(m, 3 * N, &x.z32)) ||
         (st = scratch(m, 3 * N, &x.p32)) || (st = scratch(m, 3 * N, &x.p32b)) || (st = scratch(m, 3 * N, &x.w32)) || (st = scratch(m, N, &x.z4)) || (st = scratch(m, 3 * N, &x.q32)) || (st = scratch(m, 3 * N, &x.d32)) ||
         (st = scratch(m, 3 * N, &x.dv_hi)) || (st = scratch(m, 3 * N, &x.dv_lo)) ||
@@ -1181,7 +1180,6 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
   {
     Prof p(m, kPAssemble);
     L += launch_kind(kB_elem32, d, mt, sp, s);
-    L += launch_kind(kB_fext32, d, mt, sp, s);
   }
   {
     Prof p(m, kPGather);
@@ -1284,7 +1282,7 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
     if (!(mt.radius > 0.0)) d.mx.sig_bar32 = d.mx.sig_in32;
     L += launch_kind(kB_tet_stress32, d, mt, sp, s);
     if (mt.radius > 0.0) L += launch_kind(kB_nonlocal32, d, mt, sp, s);
-    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32, kB_gather32, kB_diag32, kB_pinv32})
+    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_diag32, kB_pinv32})
       L += launch_kind(kind, d, mt, sp, s);
     GF_CK(cudaMemcpyAsync(d.mx.ir, m->h_init, sizeof(IrState), cudaMemcpyHostToDevice, s));
   } else {
@@ -2317,7 +2315,7 @@ const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_ch
                            kB_set_pinned, kB_pcg_init};
 const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
 const int kSuffixFp64[] = {kB_true_residual, kB_integrate};
-const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_fext32,
+const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32,
                             kB_gather32, kB_diag32, kB_pinv32, kB_set_pinned, kB_refresh32};
 const int kSuffixMixed[] = {kB_integrate32};
 

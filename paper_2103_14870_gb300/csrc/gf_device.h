@@ -63,7 +63,6 @@ struct MixDev {
   float* ebuf = nullptr;              // [4T][4] node rows (rhs), then [6T][9] edge rows (two-phase assembly)
   float* rhs32 = nullptr;             // [3N]
   float* rres = nullptr;              // [3N] leading float of the refinement residual
-  float* fext32 = nullptr;            // [3N]
   float* pinv32 = nullptr;            // [N][9]
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;   // [3N]
   float* p32b = nullptr;              // [3N] second search-direction buffer of the persistent solve
@@ -172,7 +171,7 @@ constexpr int kTickets = 16;
 enum BatchKind : int {
   kB_tet_stress = 0, kB_nonlocal, kB_edge_driver, kB_tet_chi, kB_node_init, kB_elem64, kB_gather64, kB_diag64, kB_set_pinned,
   kB_pcg_init, kB_pcg_spmv, kB_pcg_update, kB_pcg_p, kB_true_residual, kB_integrate,
-  kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_fext32,
+  kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32,
   kB_ir_residual, kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_integrate32, kB_refresh32,
   kB_chi_to32, kB_pinv32, kB_diag32, kB_step_begin, kB_ir_cg_spmv, kB_ir_cg_update, kBKinds
 };

@@ -638,7 +638,7 @@ __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& 
   const int64_t i = u / 3;
   const int c3 = int(u - 3 * i);
   const float acc = row_sum<8>(x.ebuf + c3, kNodeRow, m.np_ptr[i], m.np_ptr[i + 1]);
-  const float fe = sp.has_fext ? x.fext32[3 * i + c3] : 0.f;
+  const float fe = sp.has_fext ? float(m.f_ext[3 * i + c3]) : 0.f;   // f_ext in FP32
   float mv = x.mass32[i] * x.v32[3 * i + c3];
   if (x.mass_blk32) {
     mv = 0.f;
@@ -708,22 +708,6 @@ __global__ void __launch_bounds__(256) kb_gather32(const BatchTab* __restrict__ 
   unsigned bid, nb;
   const int k = batch_locate(tab, kB_gather32, blockIdx.x, bid, nb);
   gather32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
-}
-
-// f_ext in FP32 for the gather (one conversion per entry)
-__device__ __forceinline__ void fext32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-  const double* f = m.f_ext;
-
-  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (i < 3 * m.N) m.mx.fext32[i] = float(f[i]);
-}
-__global__ void __launch_bounds__(kThreads) k_fext32(DevMesh m, Material mt, StepScalars sp) {
-  fext32_body(m, mt, sp, blockIdx.x, gridDim.x);
-}
-__global__ void __launch_bounds__(kThreads) kb_fext32(const BatchTab* __restrict__ tab) {
-  unsigned bid, nb;
-  const int k = batch_locate(tab, kB_fext32, blockIdx.x, bid, nb);
-  fext32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -1354,7 +1338,6 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
     case kB_gather32: k_gather32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_diag32: k_diag32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_pinv32: k_pinv32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_fext32: k_fext32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_residual: k_ir_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp, first); break;
     case kB_ir_inner_init: k_ir_inner_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_spmv: k_ir_spmv<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
@@ -1385,7 +1368,6 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
     case kB_gather32: kb_gather32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_diag32: kb_diag32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_pinv32: kb_pinv32<<<blocks, threads, 0, s>>>(tab); break;
-    case kB_fext32: kb_fext32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_residual: kb_ir_residual<<<blocks, threads, 0, s>>>(tab, first); break;
     case kB_ir_inner_init: kb_ir_inner_init<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_spmv: kb_ir_spmv<<<blocks, threads, 0, s>>>(tab); break;

@@ -9,6 +9,7 @@ built library or a CUDA device, calls raise.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import json
 import weakref
@@ -27,6 +28,22 @@ FP64, MIXED = 0, 1
 
 STATUS = {0: "ok", 1: "bad argument", 2: "CUDA error", 3: "CG breakdown", 4: "CG max iterations", 5: "non-finite",
           6: "timeout", 7: "out of memory", 8: "unsupported"}
+
+
+# Live handles, closed at interpreter exit (batches before the meshes they step,
+# learned models before theirs) while the allocator callbacks into torch still
+# work; a destroy left to __del__ during finalisation can call a freed callback.
+_LIVE = {"batch": weakref.WeakSet(), "gnn": weakref.WeakSet(), "mesh": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_live():
+    for kind in ("batch", "gnn", "mesh"):
+        for obj in list(_LIVE[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
 
 
 class GraphFEMError(RuntimeError):
@@ -222,6 +239,7 @@ class Mesh:
         self.n_nodes, self.n_tets, self.n_edges = n_nodes, n_tets, n_edges
         self._keep = keep
         self._log, self._log_steps = None, 0
+        _LIVE["mesh"].add(self)
 
     def metrics_log(self, path: Optional[str]):
         """Append one JSON line per step (step number, wall time, dt and the
@@ -432,6 +450,7 @@ class Batch:
         h = P()
         _check(load_library().gf_batch_create(arr, self.n, ctypes.byref(h)))
         self._h = h
+        _LIVE["batch"].add(self)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -646,6 +665,7 @@ class Gnn:
         self._h = h
         self.mesh = mesh
         mesh._gnn = weakref.ref(self)
+        _LIVE["gnn"].add(self)
         self.n_params = int(lib.gf_gnn_n_params())
         self.n_graph_edges = mesh.info["n_blocks"] - mesh.n_nodes
         if params is not None:
