@@ -105,13 +105,13 @@ NCU_TRAFFIC = {
     # k_elem64; k_gather64 + k_diag64
     "assemble": 184.756992e6 + 293.543424e6,
     "assemble_gather": (371.265536e6 + 107.799296e6) + (117.729792e6 + 1.789440e6),
-    # k_nonlocal32 (eight lanes per tet pair, 128-tet tiles); k_elem32; k_gather32 + k_diag32
-    "m:nonlocal_avg": 662.691072e6 + 22.824960e6,
+    # k_nonlocal32 (eight lanes per tet pair, four-entry list groups, 128-tet tiles); k_elem32; k_gather32 + k_diag32
+    "m:nonlocal_avg": 666.984448e6 + 20.107264e6,
     "m:assemble": 127.145472e6 + 118.654464e6,
     "m:assemble_gather": (191.035136e6 + 42.632448e6) + (59.089408e6 + 0.0),
 }
 # The loaf at R_d = 2 h: k_nonlocal32 with 64-tet tiles (ncu, one launch)
-NCU_TRAFFIC_2H = {"m:nonlocal_avg": 1450.647552e6 + 31.854848e6}
+NCU_TRAFFIC_2H = {"m:nonlocal_avg": 1451.600896e6 + 20.998400e6}
 # Executed FP64 flops per tet of the element-block kernel, off-diagonal blocks
 # and rhs shares only (ncu: 2 DFMA + DADD + DMUL thread instructions per launch /
 # tets = (2 x 264.4 M + 53.3 M + 40.9 M) / 619,300): the tangent has no short

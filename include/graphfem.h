@@ -122,7 +122,8 @@ typedef struct gf_mesh_info {
   int64_t n_colours;     /* tet colours of the conflict-free assembly scatter */
   int64_t n_nbr_pairs;   /* (tet, neighbour) pairs of Eq. 20 within R_d */
   int64_t device_bytes;  /* device memory held by the mesh */
-  int64_t n_joint_entries; /* GF_MIXED: entries of the Eq. 20 joint lists of tet pairs (0 otherwise) */
+  int64_t n_joint_entries; /* GF_MIXED: entries of the Eq. 20 joint lists of tet pairs, not counting the
+                              padding of each list to a multiple of four (0 otherwise) */
   int64_t n_union_rows;  /* GF_MIXED: tet ids in the per-tile neighbour unions of Eq. 20 (0 otherwise) */
   int64_t eq20_tile;     /* GF_MIXED: tets per tile of the Eq. 20 kernel, 128 or 64 for a wide radius (0 otherwise) */
 } gf_mesh_info;

@@ -588,7 +588,7 @@ gf_status gf_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* te
     UP(d.mx.nl_uidx, mxh.nl_uidx, int32_t);
     d.mx.nl_cap = mxh.nl_cap;
     d.mx.nl_tile = mxh.nl_tile;
-    m->joint_entries = int64_t(mxh.nb_loc.size());
+    m->joint_entries = mxh.nb_real;
     m->union_rows = int64_t(mxh.nl_uidx.size());
     std::vector<float> m32(hm.mass.begin(), hm.mass.end());
     UP(d.mx.mass32, m32, float);

@@ -46,7 +46,7 @@ struct MixDev {
   const float* edge_e0 = nullptr;     // [NE][3]
   const int64_t* nb_ptr = nullptr;    // [ceil(T/2)+1] Eq. 20 joint lists of tet pairs (2q, 2q+1)
   const uint16_t* nb_loc = nullptr;   // per entry: the neighbour's position in its tile's union
-  const float2* nb_w2 = nullptr;      // per entry: the FP32 weights of tets 2q and 2q+1 (0 if not a neighbour)
+  const float2* nb_w2 = nullptr;      // per entry: the FP32 weights of tets 2q and 2q+1 (0 if not a neighbour), per block of 32 entries in two planes
   const int64_t* nl_uptr = nullptr;   // [ceil(T / nl_tile) + 1] tile unions
   const int32_t* nl_uidx = nullptr;   // union members (global tet ids, ascending per tile)
   int32_t nl_cap = 0;                 // rows a single-mesh launch stages (its shared memory: 24 B a row)

@@ -71,11 +71,14 @@ struct MixedHost {
   // Eq. 20 lists of the mixed kernel, per pair of consecutive tets (2q, 2q+1):
   // the union of the two neighbour sets, entries [nb_ptr[q], nb_ptr[q+1]),
   // each with the neighbour's position in its tile's union (nb_loc) and the
-  // two FP32 weights (nb_w2, zero where a tet lacks that neighbour); per tile
-  // the union's global tet ids nl_uidx[nl_uptr[g], nl_uptr[g+1]), ascending
-  std::vector<int64_t> nb_ptr;      // [ceil(T/2) + 1]
+  // two FP32 weights (nb_w2, zero where a tet lacks that neighbour), padded to
+  // a multiple of four entries (pads: a position of the list, zero weights);
+  // per tile the union's global tet ids nl_uidx[nl_uptr[g], nl_uptr[g+1]),
+  // ascending
+  std::vector<int64_t> nb_ptr;      // [ceil(T/2) + 1], multiples of 4
   std::vector<uint16_t> nb_loc;
-  std::vector<float> nb_w2;         // [entries][2]
+  std::vector<float> nb_w2;         // [entries][2], per block of 32 entries in two planes (see build_mixed_host)
+  int64_t nb_real = 0;              // entries without the pads
   std::vector<int64_t> nl_uptr;
   std::vector<int32_t> nl_uidx;
   int32_t nl_cap = 0;               // rows a single-mesh launch stages: the largest union, at most kNlCapMax

@@ -465,49 +465,67 @@ gf_status build_host_mesh(const double* X, int64_t N, const int32_t* tets_in, in
   return GF_OK;
 }
 
-// Order of the joint list of pair q for the shared-memory reads of the mixed
-// Eq. 20 kernel.  Eight lanes read a pair's list, lane s the entries 8c + s
-// (chunk c), and a lane reads the six floats of union row loc as three 8-byte
-// words at bank pair (3 loc + h) mod 16; a half-warp (two pairs, q even and
-// q + 1) is one shared-memory wavefront per word.  So each chunk of eight
-// entries takes distinct residues loc mod 16 from one half of the residues,
-// the low half when q + c is even and the high half otherwise (the two pairs
-// of a half-warp take opposite halves), the residues with the most entries
-// left first; what a half cannot supply comes from the other half.  Only the
-// order of the terms changes.
+// Order of the joint list of pair q for the mixed Eq. 20 kernel.  The list is
+// padded to a multiple of four entries (a pad repeats a real position of the
+// list with zero weights, so it adds +0 and reads a row the pair already
+// reads) and read in groups of four consecutive entries: eight lanes take a
+// pair, lane s the groups s, s + 8, s + 16, ..., each with one 8-byte load of
+// its four positions and two 16-byte loads of their weights.  Within the block
+// of 32 entries of round r (groups 8r .. 8r + 7) the eight lanes sum their
+// k-th entries together, entries 32r + 4s + k: one chunk per (r, k), eight
+// entries (m in a last block of 4m entries).  A lane reads the six floats of
+// union row loc as three 8-byte words at bank pair (3 loc + h) mod 16; a
+// half-warp (two pairs, q even and q + 1) is one shared-memory wavefront per
+// word.  So each chunk takes distinct residues loc mod 16 from one half of the
+// residues, the low half when q + c is even and the high half otherwise (c the
+// chunk's ordinal 4r + k: the two pairs of a half-warp take opposite halves),
+// the residues with the most entries left first; what a half cannot supply
+// comes from the other half.  Only the order of the terms changes.
 struct JointEntry {
   uint16_t loc;
   float w[2];
 };
 void deal_entries(std::vector<JointEntry>& e, int64_t q) {
   const int64_t n = int64_t(e.size());
-  if (n <= 1) return;
+  if (n == 0) return;
+  const int64_t n4 = (n + 3) / 4 * 4;
   std::vector<JointEntry> bucket[16];
   for (const auto& x : e) bucket[x.loc % 16].push_back(x);
   size_t next[16] = {};
   auto left = [&](int r) { return bucket[r].size() - next[r]; };
-  std::vector<JointEntry> out;
-  out.reserve(size_t(n));
-  for (int64_t c = 0; int64_t(out.size()) < n; ++c) {
-    const int64_t want = std::min<int64_t>(8, n - int64_t(out.size()));
-    const int half = ((q + c) & 1) ? 8 : 0;
-    bool used[16] = {};
-    int64_t got = 0;
-    auto take_from = [&](int lo, bool distinct) {
-      while (got < want) {
-        int best = -1;
-        for (int r = lo; r < lo + 8; ++r)
-          if (left(r) > 0 && !(distinct && used[r]) && (best < 0 || left(r) > left(best))) best = r;
-        if (best < 0) return;
-        out.push_back(bucket[best][next[best]++]);
-        used[best] = true;
+  std::vector<JointEntry> out(static_cast<size_t>(n4));
+  int64_t placed = 0;
+  uint16_t last_loc = e[0].loc;
+  for (int64_t r = 0; 32 * r < n4; ++r) {
+    const int64_t m = std::min<int64_t>(8, (n4 - 32 * r) / 4);   // lanes with a group in this block
+    for (int k = 0; k < 4; ++k) {
+      const int64_t c = 4 * r + k;
+      const int half = ((q + c) & 1) ? 8 : 0;
+      bool used[16] = {};
+      int64_t got = 0;
+      const int64_t want = std::min<int64_t>(m, n - placed);
+      auto put = [&](const JointEntry& x) {
+        out[size_t(32 * r + 4 * got + k)] = x;
+        last_loc = x.loc;
         ++got;
-      }
-    };
-    take_from(half, true);
-    take_from(8 - half, true);
-    take_from(half, false);
-    take_from(8 - half, false);
+        ++placed;
+      };
+      auto take_from = [&](int lo, bool distinct) {
+        while (got < want) {
+          int best = -1;
+          for (int b = lo; b < lo + 8; ++b)
+            if (left(b) > 0 && !(distinct && used[b]) && (best < 0 || left(b) > left(best))) best = b;
+          if (best < 0) return;
+          used[best] = true;
+          put(bucket[best][next[best]++]);
+        }
+      };
+      take_from(half, true);
+      take_from(8 - half, true);
+      take_from(half, false);
+      take_from(8 - half, false);
+      for (; got < m; ++got) out[size_t(32 * r + 4 * got + k)] = {last_loc, {0.f, 0.f}};   // pads
+    }
   }
   e.swap(out);
 }
@@ -561,8 +579,9 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
       const int64_t NT = (T + tile - 1) / tile, NQ = (T + 1) / 2;
       std::vector<std::vector<int32_t>> U(NT);
       std::vector<std::vector<JointEntry>> J(NQ);
-      std::atomic<int64_t> too_big{-1};
+      std::atomic<int64_t> too_big{-1}, n_real{0};
       parallel_for(NT, [&](int64_t b, int64_t e) {
+        int64_t real = 0;
         for (int64_t g = b; g < e; ++g) {
           const int64_t t0 = tile * g, t1 = std::min(T, tile * (g + 1));
           std::vector<int32_t>& u = U[g];
@@ -592,9 +611,11 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
               }
               jq.push_back(x);
             }
+            real += int64_t(jq.size());
             deal_entries(jq, a / 2);
           }
         }
+        n_real += real;
       });
       if (too_big >= 0) {
         err = "Eq. 20 neighbour sets too large for the mixed-precision path (a tile of " + std::to_string(tile) +
@@ -602,6 +623,7 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
         return GF_UNSUPPORTED;
       }
       mx.nl_tile = tile;
+      mx.nb_real = n_real;
       mx.nl_uptr.assign(NT + 1, 0);
       int64_t largest = 0;
       for (int64_t g = 0; g < NT; ++g) {
@@ -615,14 +637,21 @@ gf_status build_mixed_host(const double* X, const HostMesh& hm, MixedHost& mx, s
       for (int64_t q = 0; q < NQ; ++q) mx.nb_ptr[q + 1] = mx.nb_ptr[q] + int64_t(J[q].size());
       mx.nb_loc.resize(mx.nb_ptr[NQ]);
       mx.nb_w2.resize(2 * mx.nb_ptr[NQ]);
+      // weights of a block of 32 entries (m lanes' groups) in two planes: lane
+      // s's entries 4s, 4s + 1 at 4 s floats, its entries 4s + 2, 4s + 3 after
+      // the first plane (at 4 m + 4 s)
       parallel_for(NQ, [&](int64_t b, int64_t e) {
-        for (int64_t q = b; q < e; ++q)
-          for (size_t k = 0; k < J[q].size(); ++k) {
-            const int64_t o = mx.nb_ptr[q] + int64_t(k);
-            mx.nb_loc[o] = J[q][k].loc;
-            mx.nb_w2[2 * o] = J[q][k].w[0];
-            mx.nb_w2[2 * o + 1] = J[q][k].w[1];
+        for (int64_t q = b; q < e; ++q) {
+          const int64_t n = int64_t(J[q].size());
+          for (int64_t k = 0; k < n; ++k) {
+            const int64_t o = mx.nb_ptr[q] + k, r = k / 32, sl = (k % 32) / 4, c = k % 4;
+            const int64_t m = std::min<int64_t>(8, (n - 32 * r) / 4);
+            const int64_t w = 2 * (mx.nb_ptr[q] + 32 * r) + (c < 2 ? 4 * sl : 4 * m + 4 * sl) + 2 * (c & 1);
+            mx.nb_loc[o] = J[q][size_t(k)].loc;
+            mx.nb_w2[w] = J[q][size_t(k)].w[0];
+            mx.nb_w2[w + 1] = J[q][size_t(k)].w[1];
           }
+        }
       });
       return GF_OK;
     };

@@ -167,31 +167,44 @@ __global__ void __launch_bounds__(kThreads) kb_tet_stress32(const BatchTab* __re
 // the union of the two neighbour lists, per entry a 16-bit union position and
 // the two FP32 weights (zero where a tet lacks that neighbour), so one staged
 // row read serves both tets (0.61 row reads per (tet, neighbour) pair on the
-// loaf instead of 1).  A warp works on four pairs at once, eight lanes per
-// pair: lane s of a pair takes the entries s, s + 8, s + 16, ... of its list,
-// a batch of kNlBatch of them loaded while the previous batch is summed.  The
-// twelve sums of a pair are then reduced over its eight lanes by a transposing
-// butterfly (three steps, each lane keeping half of its values), which leaves
-// two output columns in each lane: one 8-byte store per lane writes the two
-// 32-byte output rows.  The host orders each list so that the eight entries a
-// pair reads at once fall on distinct shared-memory bank pairs, and the two
-// pairs of a half-warp on opposite halves of the banks.
+// loaf instead of 1).  Each list is padded to a multiple of four entries (pads
+// repeat a position of the list with zero weights) and read in groups of four
+// consecutive entries.  A warp works on four pairs at once, eight lanes per
+// pair: lane s of a pair takes the groups s, s + 8, s + 16, ..., each with one
+// 8-byte load of its four positions and two 16-byte loads of their weights
+// (a block of 32 entries keeps the weights of the lanes' first two entries,
+// then of their last two, so each load of a pair's eight lanes is one
+// contiguous 128-byte line), kNlGroups groups loaded while the previous ones
+// are summed.  The twelve sums
+// of a pair are then reduced over its eight lanes by a transposing butterfly
+// (three steps, each lane keeping half of its values), which leaves two output
+// columns in each lane: one 8-byte store per lane writes the two 32-byte
+// output rows.  The host orders each list so that the eight entries a pair
+// sums at once fall on distinct shared-memory bank pairs, and the two pairs of
+// a half-warp on opposite halves of the banks.
 constexpr int kNlThreads = 256;
 constexpr unsigned kNlSmem = kNlCap * 24;           // batched launches
 constexpr unsigned kNlSmemMax = kNlCapMax * 24;     // single-mesh launches at most
-constexpr int kNlBatch = 6;   // entries of a lane in flight per load batch
+constexpr int kNlGroups = 1;  // groups of four entries of a lane in flight per load batch
 
 struct NlBatch {
-  int loc[kNlBatch];
-  float2 wt[kNlBatch];
+  uint2 loc[kNlGroups];       // four 16-bit positions per group
+  float4 wt[kNlGroups][2];    // (w_2q, w_2q+1) of entries 0, 1 and of entries 2, 3
+  bool ok[kNlGroups];
 };
-// lane entries p, p + 8, ..., p + 8 (kNlBatch - 1); loc -1 past the list end
-__device__ __forceinline__ void nl_load(const MixDev& x, int64_t p, int64_t end, NlBatch& q) {
+// groups G, G + 8, ..., G + 8 (kNlGroups - 1) of a list of n entries at beg
+__device__ __forceinline__ void nl_load(const MixDev& x, int64_t beg, int64_t n, int64_t G, NlBatch& q) {
 #pragma unroll
-  for (int c = 0; c < kNlBatch; ++c) {
-    const int64_t pc = p + 8 * c;
-    q.loc[c] = pc < end ? int(__ldg(x.nb_loc + pc)) : -1;
-    q.wt[c] = pc < end ? __ldg(x.nb_w2 + pc) : make_float2(0.f, 0.f);
+  for (int c = 0; c < kNlGroups; ++c) {
+    const int64_t e = 4 * (G + 8 * c);
+    q.ok[c] = e < n;
+    if (q.ok[c]) {
+      const int64_t blk = e & ~int64_t(31), sl = (e & 31) >> 2;
+      const int64_t m = n - blk < 32 ? (n - blk) >> 2 : 8;   // lanes with a group in this block
+      q.loc[c] = __ldg(reinterpret_cast<const uint2*>(x.nb_loc + beg + e));
+      q.wt[c][0] = __ldg(reinterpret_cast<const float4*>(x.nb_w2 + beg + blk + 2 * sl));
+      q.wt[c][1] = __ldg(reinterpret_cast<const float4*>(x.nb_w2 + beg + blk + 2 * m + 2 * sl));
+    }
   }
 }
 __device__ __forceinline__ void nl_row(const MixDev& x, const float2* su, bool staged, int64_t u0, int loc, float2& r0,
@@ -221,17 +234,24 @@ __device__ __forceinline__ void fma2(float2& c, float2 a, float2 b) {
 __device__ __forceinline__ void nl_accumulate(const MixDev& x, const float2* su, bool staged, int64_t u0, const NlBatch& q,
                                               float2 (&acc)[6]) {
 #pragma unroll
-  for (int c = 0; c < kNlBatch; ++c) {
-    if (q.loc[c] < 0) continue;
-    float2 r0, r1, r2;
-    nl_row(x, su, staged, u0, q.loc[c], r0, r1, r2);
-    const float2 wa = make_float2(q.wt[c].x, q.wt[c].x), wb = make_float2(q.wt[c].y, q.wt[c].y);
-    fma2(acc[0], wa, r0);
-    fma2(acc[1], wa, r1);
-    fma2(acc[2], wa, r2);
-    fma2(acc[3], wb, r0);
-    fma2(acc[4], wb, r1);
-    fma2(acc[5], wb, r2);
+  for (int c = 0; c < kNlGroups; ++c) {
+    if (!q.ok[c]) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned word = k < 2 ? q.loc[c].x : q.loc[c].y;
+      const int loc = int((word >> (16 * (k & 1))) & 0xffffu);
+      const float4 w = q.wt[c][k >> 1];
+      const float w0 = (k & 1) ? w.z : w.x, w1 = (k & 1) ? w.w : w.y;
+      float2 r0, r1, r2;
+      nl_row(x, su, staged, u0, loc, r0, r1, r2);
+      const float2 wa = make_float2(w0, w0), wb = make_float2(w1, w1);
+      fma2(acc[0], wa, r0);
+      fma2(acc[1], wa, r1);
+      fma2(acc[2], wa, r2);
+      fma2(acc[3], wb, r0);
+      fma2(acc[4], wb, r1);
+      fma2(acc[5], wb, r2);
+    }
   }
 }
 // Reduce v[0..15] (columns 0-7 of the first tet, then of the second) over the
@@ -297,17 +317,18 @@ __device__ __forceinline__ void nonlocal32_body(const DevMesh& m, const Material
   for (int r0 = 0; r0 < np; r0 += 4) {
     const int64_t q = qw + r0 + g;
     const bool live = r0 + g < np;
-    const int64_t beg = live ? x.nb_ptr[q] : 0, end = live ? x.nb_ptr[q + 1] : 0;
-    // batches of this lane's entries; every lane of the warp runs the longest group's count
-    const int mine = end - beg > sl ? int((end - beg - sl + 7) / 8) : 0;
-    const int rounds = __reduce_max_sync(0xffffffffu, (mine + kNlBatch - 1) / kNlBatch);
+    const int64_t beg = live ? x.nb_ptr[q] : 0, n = live ? x.nb_ptr[q + 1] - beg : 0;
+    // batches of this lane's groups; every lane of the warp runs the longest lane's count
+    const int64_t groups = n / 4;
+    const int mine = groups > sl ? int((groups - sl + 7) / 8) : 0;
+    const int rounds = __reduce_max_sync(0xffffffffu, (mine + kNlGroups - 1) / kNlGroups);
     float2 acc2[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v) acc2[v] = make_float2(0.f, 0.f);
     NlBatch cur, nxt;
-    nl_load(x, beg + sl, end, cur);
+    nl_load(x, beg, n, sl, cur);
     for (int b = 0; b < rounds; ++b) {
-      if (b + 1 < rounds) nl_load(x, beg + sl + 8 * kNlBatch * (b + 1), end, nxt);
+      if (b + 1 < rounds) nl_load(x, beg, n, sl + 8 * kNlGroups * (b + 1), nxt);
       nl_accumulate(x, su, staged, u0, cur, acc2);
       cur = nxt;
     }
