@@ -461,9 +461,11 @@ __global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restr
 constexpr int kElemW = 68;   // 54 block floats + 12 rhs floats + 2 pad
 constexpr int kNodeRow = 4, kEdgeRow = 9;
 // Each thread's row is built in shared memory (stride 69 floats: conflict-free
-// for 32 consecutive threads); each warp then writes its 32 rows out, the node rows as one 16-byte store each and
-// the edge rows as runs of 9 consecutive floats, with the destination rows
-// passed between lanes by shuffles.
+// for 32 consecutive threads), each block already oriented for its global edge
+// (transposed where the tet's local order of the edge's nodes is the reverse
+// of the global one); each warp then writes its 32 rows out, the node rows as
+// one 16-byte store each and the edge rows as runs of 9 consecutive floats,
+// with the destination rows passed between lanes by shuffles.
 constexpr int kElemThreads = 128, kElemSS = kElemW + 1;
 constexpr unsigned kElemSmem = kElemThreads * kElemSS * 4;
 
@@ -499,6 +501,13 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
 #pragma unroll
     for (int l = 0; l < 6; ++l) s += h(k, l) * ds[l];
     g[k] = s;
+  }
+  unsigned flip = 0u;   // bit q: local edge q runs against the global (i < j) order
+  {
+    const int4 n2 = m.tets[t];
+    const int nid2[4] = {n2.x, n2.y, n2.z, n2.w};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) flip |= nid2[edge_a(k)] > nid2[edge_b(k)] ? (1u << k) : 0u;
   }
   // Y_b[k][c] = sum_{l in b} H_kl sgn_lb e_l[c]  (sgn = -1 if b is the first node of l)
   // only the off-diagonal blocks (a < b): the block rows sum to zero, and
@@ -555,10 +564,12 @@ __device__ __forceinline__ void elem32_row(const DevMesh& m, const StepScalars& 
       }
       const int q = a == 0 ? b - 1 : a + b;   // local edge of (a, b)
       const float sk = sKv * chi;
+      const bool tr = (flip >> q) & 1u;
+      float* ob = o + 9 * q;
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) o[9 * q + 3 * r + c] = sk * blk[r][c];
+        for (int c = 0; c < 3; ++c) ob[tr ? 3 * c + r : 3 * r + c] = sk * blk[r][c];
     }
   }
   // rhs shares: dt chi (f_a - cv (K v)_a), f_a = -2 sum_{k in a} sgn_ka g_k e_k
@@ -583,16 +594,10 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   const MixDev& x = m.mx;
   int32_t nr[4] = {0, 0, 0, 0}, er[6] = {0, 0, 0, 0, 0, 0};
-  unsigned fl = 0u;
   if (t < m.T) {
     elem32_row(m, sp, t, sh_rows + threadIdx.x * kElemSS);
-    const int4 n = m.tets[t];
-    const int nid[4] = {n.x, n.y, n.z, n.w};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      fl |= nid[edge_a(k)] > nid[edge_b(k)] ? (1u << k) : 0u;
-      er[k] = m.erow[6 * t + k];
-    }
+    for (int k = 0; k < 6; ++k) er[k] = m.erow[6 * t + k];
 #pragma unroll
     for (int a = 0; a < 4; ++a) nr[a] = m.nrow[4 * t + a];
   }
@@ -611,17 +616,15 @@ __device__ __forceinline__ void elem32_body(const DevMesh& m, const Material& mt
     for (int a = 0; a < 4; ++a)
       nbuf[nr[a]] = make_float4(src[54 + 3 * a], src[54 + 3 * a + 1], src[54 + 3 * a + 2], 0.f);
   }
-  // edge rows: 9 consecutive floats each, transposed where the global order flips the edge
+  // edge rows: 9 consecutive floats each (float q of row r is j = 9 r + q)
   float* ebuf = x.ebuf + int64_t(kNodeRow) * 4 * m.T;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const int bq = 9 * k;
 #pragma unroll
     for (int j = lane; j < 288; j += 32) {
       const int r = j / 9, q = j - 9 * r;
       const int32_t row = __shfl_sync(0xffffffffu, er[k], r);
-      const unsigned f = __shfl_sync(0xffffffffu, fl, r);
-      if (r < nw) ebuf[int64_t(kEdgeRow) * row + q] = wrows[r * kElemSS + bq + (((f >> k) & 1u) ? 3 * (q % 3) + q / 3 : q)];
+      if (r < nw) ebuf[int64_t(kEdgeRow) * row + q] = wrows[r * kElemSS + 9 * k + q];
     }
   }
 }
