@@ -85,14 +85,14 @@ MIXED_BYTES = {
     "m:nonlocal_avg": lambda i: 10 * i["n_joint_entries"] + 4 * i["n_union_rows"] + i["n_tets"] * (4 + 32 + 32),
     "m:edge_driver": lambda i: i["n_edges"] * (8 + 12 + 8 + 1) + 6 * i["n_tets"] * 4 + 24 * i["n_tets"] + 12 * i["n_nodes"],
     # phase 1: tet, rest row (128 B), chi, its ten row indices in; 6 edge rows
-    # (36 B) + 4 node rows (16 B) out; u, v and the external force per node
-    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 40 + 280) + i["n_nodes"] * (24 + 24),
+    # (36 B) + 4 node rows (16 B) out; u and v (FP32) per node
+    "m:assemble": lambda i: i["n_tets"] * (16 + 128 + 4 + 40 + 280) + i["n_nodes"] * (12 + 12),
     # phases 2 and 3: every row once (280 B per tet); per edge its row pointer
     # and two slots; the off-diagonal blocks written, then read back for the
-    # diagonal sums; per node pointers, mass, v, f_ext, rhs and the diagonal
-    # block; the block-Jacobi inverse reads the diagonal blocks and writes D^-1
+    # diagonal sums; per node its row pointers and diagonal slot, mass, v, f_ext
+    # (FP64), rhs, and the diagonal block and its block-Jacobi inverse written
     "m:assemble_gather": lambda i: i["n_tets"] * 280 + i["n_edges"] * (4 + 8) + i["n_blocks"] * (36 + 36)
-                                   + i["n_nodes"] * (4 + 4 + 4 + 12 + 12 + 12 + 36 + 36 + 36),
+                                   + i["n_nodes"] * (4 + 4 + 4 + 4 + 12 + 24 + 12 + 36 + 36),
     "m:pcg_spmv": lambda i: i["n_blocks"] * 40 + i["n_nodes"] * (4 + 12 + 12 + 12),
 }
 
@@ -107,8 +107,8 @@ NCU_TRAFFIC = {
     "assemble_gather": (371.265536e6 + 107.799296e6) + (117.729792e6 + 1.789440e6),
     # k_nonlocal32 (eight lanes per tet pair, four-entry list groups, 128-tet tiles); k_elem32; k_gather32 + k_diag32
     "m:nonlocal_avg": 666.984448e6 + 20.107264e6,
-    "m:assemble": 127.145472e6 + 118.654464e6,
-    "m:assemble_gather": (191.035136e6 + 42.632448e6) + (59.089408e6 + 0.0),
+    "m:assemble": None,
+    "m:assemble_gather": None,
 }
 # The loaf at R_d = 2 h: k_nonlocal32 with 64-tet tiles (ncu, one launch)
 NCU_TRAFFIC_2H = {"m:nonlocal_avg": 1451.600896e6 + 20.998400e6}

@@ -70,8 +70,7 @@ LaunchDims launch_dims(int kind, const DevMesh& m, const Material& mt, const Ste
     case kB_gather64: return {cdiv(9 * m.NE + 3 * N, 256), 256};
     case kB_diag64: return {cdiv(9 * N, 256), 256};
     case kB_gather32: return {cdiv(9 * m.NE + 3 * N, 256), 256};
-    case kB_diag32: return {cdiv(9 * N, 256), 256};
-    case kB_pinv32: return {cdiv(N, 256), 256};
+    case kB_diag32: return {cdiv(9 * N, 288), 288};   // 32 nodes x 9 entries per CTA
     case kB_set_pinned: return {cdiv(sp.n_pinned, 256), 256};
     case kB_pcg_init: case kB_pcg_spmv: case kB_pcg_update: case kB_true_residual: return {red_grid(N), 256};
     case kB_pcg_p: return {red_grid(3 * N), 256};
@@ -90,7 +89,7 @@ int launch_kind(int kind, const DevMesh& m, const Material& mt, const StepScalar
 }
 
 int launch_batch(int kind, const BatchTab* tab, unsigned blocks, cudaStream_t s, int first) {
-  const unsigned threads = (kind == kB_elem64 || kind == kB_elem32) ? 128u : 256u;
+  const unsigned threads = (kind == kB_elem64 || kind == kB_elem32) ? 128u : kind == kB_diag32 ? 288u : 256u;
   return kind < kB_tet_stress32 ? launch_batch_fp64(kind, tab, blocks, threads, s)
                                 : launch_batch_mixed(kind, tab, blocks, threads, s, first);
 }
@@ -1185,7 +1184,6 @@ gf_status step_mixed(gf_mesh* m, DevMesh& d, double dt, bool has_fext, int64_t n
     Prof p(m, kPGather);
     L += launch_kind(kB_gather32, d, mt, sp, s);
     L += launch_kind(kB_diag32, d, mt, sp, s);
-    L += launch_kind(kB_pinv32, d, mt, sp, s);
   }
   IrState init{};
   init.tol2 = m->opt.cg_rtol * m->opt.cg_rtol;
@@ -1282,7 +1280,7 @@ gf_status build_step_graph(gf_mesh* m, DevMesh d, const StepScalars& sp, int loo
     if (!(mt.radius > 0.0)) d.mx.sig_bar32 = d.mx.sig_in32;
     L += launch_kind(kB_tet_stress32, d, mt, sp, s);
     if (mt.radius > 0.0) L += launch_kind(kB_nonlocal32, d, mt, sp, s);
-    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_diag32, kB_pinv32})
+    for (int kind : {kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32, kB_diag32})
       L += launch_kind(kind, d, mt, sp, s);
     GF_CK(cudaMemcpyAsync(d.mx.ir, m->h_init, sizeof(IrState), cudaMemcpyHostToDevice, s));
   } else {
@@ -2316,7 +2314,7 @@ const int kPrefixFp64[] = {kB_tet_stress, kB_nonlocal, kB_edge_driver, kB_tet_ch
 const int kBodyFp64[] = {kB_pcg_spmv, kB_pcg_update, kB_pcg_p};
 const int kSuffixFp64[] = {kB_true_residual, kB_integrate};
 const int kPrefixMixed[] = {kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32,
-                            kB_gather32, kB_diag32, kB_pinv32, kB_set_pinned, kB_refresh32};
+                            kB_gather32, kB_diag32, kB_set_pinned, kB_refresh32};
 const int kSuffixMixed[] = {kB_integrate32};
 
 template <size_t K>

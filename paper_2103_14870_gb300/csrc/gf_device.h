@@ -173,7 +173,7 @@ enum BatchKind : int {
   kB_pcg_init, kB_pcg_spmv, kB_pcg_update, kB_pcg_p, kB_true_residual, kB_integrate,
   kB_tet_stress32, kB_nonlocal32, kB_edge_driver32, kB_tet_chi32, kB_elem32, kB_gather32,
   kB_ir_residual, kB_ir_inner_init, kB_ir_spmv, kB_ir_update, kB_ir_p, kB_ir_apply, kB_integrate32, kB_refresh32,
-  kB_chi_to32, kB_pinv32, kB_diag32, kB_step_begin, kB_ir_cg_spmv, kB_ir_cg_update, kBKinds
+  kB_chi_to32, kB_diag32, kB_step_begin, kB_ir_cg_spmv, kB_ir_cg_update, kBKinds
 };
 constexpr int kMaxBatch = 256;
 

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) kb_tet_chi32(const BatchTab* __restr
 // ascending tet order and adds the external and damping terms.
 // Phase 3 (k_diag32): the diagonal blocks as minus the sum of their row's
 // off-diagonal blocks (every block row of the stiffness sums to zero) plus
-// the mass; k_pinv32 then inverts them (block Jacobi).
+// the mass, and their inverses (block Jacobi).
 // ---------------------------------------------------------------------------
 
 constexpr int kElemW = 68;   // 54 block floats + 12 rhs floats + 2 pad
@@ -673,57 +673,53 @@ __device__ __forceinline__ void gather32_body(const DevMesh& m, const Material& 
 
 // Phase 3: A_ii = -sum_{j != i} A_ij (zero block-row sums of the stiffness)
 // plus the mass (lumped on the diagonal, or the consistent m_ij of Eq. 5 on
-// every block of the row, added after the sum).  Thread per (node, entry).
+// every block of the row, added after the sum), then the block-Jacobi inverse
+// of A_ii in FP32.  Nine threads per node (entry q), 32 nodes per CTA of
+// kDiagThreads: the node's nine entries meet in shared memory and thread q
+// writes entry q of the inverse (cofactor q over the determinant).
+constexpr int kDiagThreads = 288;
 __device__ __forceinline__ void diag32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
+  __shared__ float dsh[kDiagThreads];
   const MixDev& x = m.mx;
-  const int64_t t = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= 9 * m.N) return;
+  const int64_t t = bid * int64_t(kDiagThreads) + threadIdx.x;
+  const bool live = t < 9 * m.N;
   const int64_t i = t / 9;
   const int q = int(t - 9 * i);
-  const int d = m.diag_blk[i], b0 = m.row_ptr[i], b1 = m.row_ptr[i + 1];
-  float acc = 0.f;
-  for (int b = b0; b < b1; ++b)
-    if (b != d) acc += x.val32[9 * int64_t(b) + q];
-  float diag = -acc;
-  if (q == 0 || q == 4 || q == 8) {
-    const float cmf = sp.cmf;
-    diag += cmf * (x.mass_blk32 ? x.mass_blk32[d] : x.mass32[i]);
-    if (x.mass_blk32)
-      for (int b = b0; b < b1; ++b)
-        if (b != d) x.val32[9 * int64_t(b) + q] += cmf * x.mass_blk32[b];   // Eq. 5
+  float diag = 0.f;
+  if (live) {
+    const int d = m.diag_blk[i], b0 = m.row_ptr[i], b1 = m.row_ptr[i + 1];
+    float acc = 0.f;
+    for (int b = b0; b < b1; ++b)
+      if (b != d) acc += x.val32[9 * int64_t(b) + q];
+    diag = -acc;
+    if (q == 0 || q == 4 || q == 8) {
+      const float cmf = sp.cmf;
+      diag += cmf * (x.mass_blk32 ? x.mass_blk32[d] : x.mass32[i]);
+      if (x.mass_blk32)
+        for (int b = b0; b < b1; ++b)
+          if (b != d) x.val32[9 * int64_t(b) + q] += cmf * x.mass_blk32[b];   // Eq. 5
+    }
+    x.val32[9 * int64_t(d) + q] = diag;
   }
-  x.val32[9 * int64_t(d) + q] = diag;
-}
-__global__ void __launch_bounds__(256) k_diag32(DevMesh m, Material mt, StepScalars sp) {
-  diag32_body(m, mt, sp, blockIdx.x, gridDim.x);
-}
-__global__ void __launch_bounds__(256) kb_diag32(const BatchTab* __restrict__ tab) {
-  unsigned bid, nb;
-  const int k = batch_locate(tab, kB_diag32, blockIdx.x, bid, nb);
-  diag32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
-}
-
-// block-Jacobi inverse of every node's assembled diagonal block (FP32)
-__device__ __forceinline__ void pinv32_body(const DevMesh& m, const Material& mt, const StepScalars& sp, unsigned bid, unsigned nb) {
-  const int64_t i = bid * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= m.N) return;
-  const float* d = m.mx.val32 + 9 * int64_t(m.diag_blk[i]);
+  dsh[threadIdx.x] = diag;
+  __syncthreads();
+  if (!live) return;
+  const float* d = dsh + (threadIdx.x - q);
   const float c00 = d[4] * d[8] - d[5] * d[7], c01 = d[2] * d[7] - d[1] * d[8], c02 = d[1] * d[5] - d[2] * d[4];
   const float c10 = d[5] * d[6] - d[3] * d[8], c11 = d[0] * d[8] - d[2] * d[6], c12 = d[2] * d[3] - d[0] * d[5];
   const float c20 = d[3] * d[7] - d[4] * d[6], c21 = d[1] * d[6] - d[0] * d[7], c22 = d[0] * d[4] - d[1] * d[3];
   const float id = 1.f / (d[0] * c00 + d[1] * c10 + d[2] * c20);
-  float* pi = m.mx.pinv32 + 9 * i;
-  pi[0] = c00 * id; pi[1] = c01 * id; pi[2] = c02 * id;
-  pi[3] = c10 * id; pi[4] = c11 * id; pi[5] = c12 * id;
-  pi[6] = c20 * id; pi[7] = c21 * id; pi[8] = c22 * id;
+  const float cq = q == 0 ? c00 : q == 1 ? c01 : q == 2 ? c02 : q == 3 ? c10 : q == 4 ? c11 : q == 5 ? c12
+                 : q == 6 ? c20 : q == 7 ? c21 : c22;
+  x.pinv32[9 * i + q] = cq * id;
 }
-__global__ void __launch_bounds__(256) k_pinv32(DevMesh m, Material mt, StepScalars sp) {
-  pinv32_body(m, mt, sp, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kDiagThreads) k_diag32(DevMesh m, Material mt, StepScalars sp) {
+  diag32_body(m, mt, sp, blockIdx.x, gridDim.x);
 }
-__global__ void __launch_bounds__(256) kb_pinv32(const BatchTab* __restrict__ tab) {
+__global__ void __launch_bounds__(kDiagThreads) kb_diag32(const BatchTab* __restrict__ tab) {
   unsigned bid, nb;
-  const int k = batch_locate(tab, kB_pinv32, blockIdx.x, bid, nb);
-  pinv32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
+  const int k = batch_locate(tab, kB_diag32, blockIdx.x, bid, nb);
+  diag32_body(tab->mesh[k], tab->mt[k], tab->sp[k], bid, nb);
 }
 __global__ void __launch_bounds__(256) k_gather32(DevMesh m, Material mt, StepScalars sp) {
   gather32_body(m, mt, sp, blockIdx.x, gridDim.x);
@@ -1361,7 +1357,6 @@ int launch_kind_mixed(int kind, const DevMesh& m, const Material& mt, const Step
       break;
     case kB_gather32: k_gather32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_diag32: k_diag32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
-    case kB_pinv32: k_pinv32<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_residual: k_ir_residual<<<d.blocks, d.threads, 0, s>>>(m, mt, sp, first); break;
     case kB_ir_inner_init: k_ir_inner_init<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
     case kB_ir_spmv: k_ir_spmv<<<d.blocks, d.threads, 0, s>>>(m, mt, sp); break;
@@ -1391,7 +1386,6 @@ int launch_batch_mixed(int kind, const BatchTab* tab, unsigned blocks, unsigned 
       break;
     case kB_gather32: kb_gather32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_diag32: kb_diag32<<<blocks, threads, 0, s>>>(tab); break;
-    case kB_pinv32: kb_pinv32<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_residual: kb_ir_residual<<<blocks, threads, 0, s>>>(tab, first); break;
     case kB_ir_inner_init: kb_ir_inner_init<<<blocks, threads, 0, s>>>(tab); break;
     case kB_ir_spmv: kb_ir_spmv<<<blocks, threads, 0, s>>>(tab); break;
