@@ -107,8 +107,8 @@ NCU_TRAFFIC = {
     "assemble_gather": (371.265536e6 + 107.799296e6) + (117.729792e6 + 1.789440e6),
     # k_nonlocal32 (eight lanes per tet pair, four-entry list groups, 128-tet tiles); k_elem32; k_gather32 + k_diag32
     "m:nonlocal_avg": 666.984448e6 + 20.107264e6,
-    "m:assemble": None,
-    "m:assemble_gather": None,
+    "m:assemble": 126.746624e6 + 132.611584e6,
+    "m:assemble_gather": (192.428032e6 + 43.098368e6) + (59.091200e6 + 0.014080e6),
 }
 # The loaf at R_d = 2 h: k_nonlocal32 with 64-tet tiles (ncu, one launch)
 NCU_TRAFFIC_2H = {"m:nonlocal_avg": 1451.600896e6 + 20.998400e6}
@@ -256,7 +256,7 @@ def run_batch(args, gf, torch, barrier, stream, world=1, rank=0, dist=None) -> d
     f = [torch.tensor(w.f_ext.ravel(), dtype=torch.float64, device="cuda") for w in ws]
     pins = [torch.tensor(w.pinned, dtype=torch.int32, device="cuda") for w in ws]
     dt = ws[0].dt
-    tuned, tuned_ms = b.autotune(dt, f, pins, trial_steps=6)
+    tuned, tuned_ms = b.autotune(dt, f, pins, trial_steps=10)
     out = {"workload": "64 Kuhn boxes, 2k-80k tets (log-uniform, seed 2), E in [1e4, 1e8]",
            "n_meshes": len(ws_all), "n_tets_total": int(sum(w.n_tets for w in ws_all)), "precision": "mixed",
            "cg_rtol": 1e-6, "tuning": tuned, "autotune_ms_per_step": tuned_ms,

@@ -2791,7 +2791,9 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
   const gf_batch_tuning orig = b->tune;
   std::vector<gf_batch_tuning> cands;
   {
-    const int wave = 4 * 152;   // one wave of a loop kernel at 4 CTAs per SM
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const int wave = 4 * sms;   // one wave of a loop kernel at 4 CTAs per SM
     for (int budget : {0, wave, 2 * wave, 4 * wave}) {
       gf_batch_tuning t{};
       t.graph = 1;
@@ -2816,7 +2818,8 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
         cands.push_back(t);
       }
       // the two-kernel inner form, and both forms with shorter and longer passes
-      for (int budget : {0, wave, 2 * wave}) {
+      // at budgets of two and four waves
+      for (int budget : {0, wave, 2 * wave, 4 * wave}) {
         gf_batch_tuning t{};
         t.graph = 1;
         t.chunk = 8;
@@ -2824,16 +2827,17 @@ gf_status gf_batch_autotune(gf_batch* b, double dt, const double* const* f_ext, 
         t.solve_loop = GF_SOLVE_CG;
         cands.push_back(t);
       }
-      for (int form : {GF_SOLVE_KERNELS, GF_SOLVE_CG})
-        for (int inner : {2, 4, 16}) {
-          gf_batch_tuning t{};
-          t.graph = 1;
-          t.chunk = 8;
-          t.grid_budget = 2 * wave;
-          t.solve_loop = form;
-          t.inner = inner;
-          cands.push_back(t);
-        }
+      for (int budget : {2 * wave, 4 * wave})
+        for (int form : {GF_SOLVE_KERNELS, GF_SOLVE_CG})
+          for (int inner : {2, 4, 16}) {
+            gf_batch_tuning t{};
+            t.graph = 1;
+            t.chunk = 8;
+            t.grid_budget = budget;
+            t.solve_loop = form;
+            t.inner = inner;
+            cands.push_back(t);
+          }
     }
     for (int g : {wave / 2, wave, 2 * wave, 4 * wave}) {   // the distributed loop: its launch grid
       gf_batch_tuning t{};
