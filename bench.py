@@ -103,7 +103,7 @@ MIXED_BYTES = {
 NCU_TRAFFIC = {
     "nonlocal_avg": 1.236900864e9 + 30.863872e6,
     # k_elem64; k_gather64 + k_diag64
-    "assemble": 184.756992e6 + 293.543424e6,
+    "assemble": 184.009984e6 + 293.395456e6,
     "assemble_gather": (371.265536e6 + 107.799296e6) + (117.729792e6 + 1.789440e6),
     # k_nonlocal32 (eight lanes per tet pair, four-entry list groups, 128-tet tiles); k_elem32; k_gather32 + k_diag32
     "m:nonlocal_avg": 666.984448e6 + 20.107264e6,
@@ -114,9 +114,9 @@ NCU_TRAFFIC = {
 NCU_TRAFFIC_2H = {"m:nonlocal_avg": 1451.600896e6 + 20.998400e6}
 # Executed FP64 flops per tet of the element-block kernel, off-diagonal blocks
 # and rhs shares only (ncu: 2 DFMA + DADD + DMUL thread instructions per launch /
-# tets = (2 x 264.4 M + 53.3 M + 40.9 M) / 619,300): the tangent has no short
+# tets = (2 x 251.4 M + 52.0 M + 47.1 M) / 619,300): the tangent has no short
 # closed count.
-ELEM64_FLOPS_PER_TET = 1006.0
+ELEM64_FLOPS_PER_TET = 972.0
 
 
 def broken_summary(broken: list) -> dict:

@@ -352,13 +352,13 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
       du[c] = U[edge_b(k)][c] - U[edge_a(k)][c];
     }
     ds[k] = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2] - m.rest[(kRestS0 + k) * m.T + t];
-    Dv[k] = 2.0 * (e[k][0] * du[0] + e[k][1] * du[1] + e[k][2] * du[2]);
+    Dv[k] = e[k][0] * du[0] + e[k][1] * du[1] + e[k][2] * du[2];   // half ds/dt (the 2 is taken with cv below)
   }
   double H[21];
 #pragma unroll
   for (int f = 0; f < 21; ++f) H[f] = m.rest[(kRestH + f) * m.T + t];
   auto h = [&](int k, int l) { return k <= l ? H[tri6(k, l)] : H[tri6(l, k)]; };
-  // g = dV Psi/ds = Hs (s - s0);  w = Hs (ds/dx . v)
+  // g = dV Psi/ds = Hs (s - s0);  w = Hs (ds/dx . v) / 2
   double g[6], w[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -371,13 +371,13 @@ __global__ void __launch_bounds__(128) k_assemble(DevMesh m, double dt, double b
     g[k] = gk;
     w[k] = wk;
   }
-  // right-hand side: per edge k (a->b), t_k = 2 dt chi [e_k (g_k + c w_k) + c g_k (v_b - v_a)], c = beta + dt
+  // right-hand side: per edge k (a->b), t_k = 2 dt chi [e_k (g_k + 2 c w_k) + c g_k (v_b - v_a)], c = beta + dt
   {
-    const double cv = beta + dt, sc = 2.0 * dt * chi;
+    const double cv = beta + dt, cv2 = 2.0 * cv, sc = 2.0 * dt * chi;
     double f[4][3] = {};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const double a1 = sc * (g[k] + cv * w[k]), a2 = sc * cv * g[k];
+      const double a1 = sc * (g[k] + cv2 * w[k]), a2 = sc * cv * g[k];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double tk = a1 * e[k][c] + a2 * (U[edge_b(k)][c] - U[edge_a(k)][c]);
@@ -654,8 +654,10 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
       e[k][c] = P[edge_b(k)][c] - P[edge_a(k)][c];
       du[k][c] = U[edge_b(k)][c] - U[edge_a(k)][c];
     }
+    // summed in the order of the rest lengths' sums, so a tet at rest gives exactly 0
     ds[k] = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2] - m.rest[(kRestS0 + k) * m.T + t];
-    Dv[k] = 2.0 * (e[k][0] * du[k][0] + e[k][1] * du[k][1] + e[k][2] * du[k][2]);
+    // half the rate of change of the squared length (the factor 2 is taken with cv below)
+    Dv[k] = e[k][0] * du[k][0] + e[k][1] * du[k][1] + e[k][2] * du[k][2];
   }
   double H[21];
 #pragma unroll
@@ -674,11 +676,11 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
     w[k] = wk;
   }
   {
-    const double cv = beta + dt, sc = 2.0 * dt * chi;
+    const double cv = beta + dt, cv2 = 2.0 * cv, sc = 2.0 * dt * chi;
     double f[4][3] = {};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const double a1 = sc * (g[k] + cv * w[k]), a2 = sc * cv * g[k];
+      const double a1 = sc * (g[k] + cv2 * w[k]), a2 = sc * cv * g[k];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double tk = a1 * e[k][c] + a2 * du[k][c];
@@ -709,20 +711,18 @@ __device__ __forceinline__ void elem64_body(const DevMesh& m, const Material& mt
       }
 #pragma unroll
     for (int a = 0; a < b; ++a) {
+      // the geometric term -2 sK g_ab I starts the diagonal entries' sums
+      const double geo = -2.0 * sK * g[kab[a][b]];
       double blk[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          double v = 0.0;
+          double v = r == c ? geo : 0.0;
 #pragma unroll
           for (int i = 0; i < 3; ++i) v += sgn[a][i] * e[inc[a][i]][r] * Y[inc[a][i]][c];
           blk[r][c] = v;
         }
-      const double geo = -2.0 * sK * g[kab[a][b]];
-      blk[0][0] += geo;
-      blk[1][1] += geo;
-      blk[2][2] += geo;
       out.block(a, b, blk);
     }
   }
